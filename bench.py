@@ -1,0 +1,356 @@
+"""Benchmark of the fused shallow-water step on one GB300 (or N replicas).
+
+A bench step is one explicit Euler time step of the whole hot path over the
+workload's mesh: edge fluxes with hydrostatic reconstruction and HLLC,
+boundary fluxes, semi-implicit friction, update and the CFL min-reduction
+(one fused kernel launch, replayed from CUDA graphs).
+
+Default workload: the 12,999,168-cell synthetic river reach (20 km x 2 km,
+partially dry, Q = 2000 m^3/s inflow, fixed-stage outflow), FP32 state with
+FP64 time step.  Its working set (~1 GB) is far larger than L2, so no flush
+is needed between steps.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle instead, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+# algorithmic bytes per cell-update: state in (3) + state out (3) + z, m,
+# 1/|Omega|, inscribed radius (4) + L n of three edges (6) values, plus three
+# int32 neighbour indices
+ALG_BYTES = {"f32": 16 * 4 + 12, "f64": 16 * 8 + 12}
+
+WORKLOADS = {
+    "river13m_fp32": dict(maker="river_13m", precision="f32", steps=1000,
+                          desc="synthetic river reach 20 km x 2 km, 12,999,168 triangles, partially dry, "
+                               "Q=2000 m3/s inflow, stage outflow, Manning U[0.02,0.06]; FP32 state, FP64 dt"),
+    "canal1m_fp64": dict(maker="dam_break_dry_1m", precision="f64", steps=2000,
+                         desc="dry-bed dam break, canal 200 m x 10 m, 1,000,000 triangles, n=0.03; FP64"),
+    "canal1m_fp32": dict(maker="dam_break_dry_1m", precision="f32", steps=2000,
+                         desc="dry-bed dam break, canal 200 m x 10 m, 1,000,000 triangles, n=0.03; FP32"),
+    "dam4k_fp64": dict(maker="dam_break_4k", precision="f64", steps=500,
+                       desc="wet dam break, canal 200 m x 10 m, 4,000 triangles; FP64"),
+}
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        return self.summary()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for _, line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return None, 0, 1, 0
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    dist.init_process_group("gloo")
+    return dist, rank, ws, local
+
+
+def _make_input(name):
+    from paper_2010_14416_gb300 import meshgen
+    return getattr(meshgen, WORKLOADS[name]["maker"])()
+
+
+def cpu_baseline(mi, budget_s=20.0):
+    """The FP64 oracle as it stands, on all host cores: whole-mesh steps until
+    the time budget is used (at least two)."""
+    import oracle
+    M = oracle.Mesh(mi.nodes, mi.tris, mi.z, mi.manning)
+    for pairs, kind, value in mi.bcs:
+        M.set_bc(pairs, kind, value)
+    h, hu, hv = mi.h.astype(np.float64), mi.hu.astype(np.float64), mi.hv.astype(np.float64)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        dt = M.dt(h, hu, hv, 0.9)
+        h, hu, hv, _ = M.step(h, hu, hv, dt)
+        steps += 1
+        el = time.perf_counter() - t0
+        if steps >= 2 and el >= budget_s:
+            break
+    return {"value": mi.n_cells * steps / el, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+            "sample": f"{steps} whole-mesh FP64 oracle steps from the initial state "
+                      f"({mi.n_cells:,} cells, {el:.1f} s, OpenMP over cells)"}
+
+
+def run_reference(args, name):
+    """--impl reference: the oracle timed on the host cores; each bench step is
+    one oracle step over a fixed seeded sample of 2^20 cells of the mesh."""
+    dist, rank, ws, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    mi = _make_input(name)
+    M = oracle.Mesh(mi.nodes, mi.tris, mi.z, mi.manning)
+    for pairs, kind, value in mi.bcs:
+        M.set_bc(pairs, kind, value)
+    n_s = min(1 << 20, mi.n_cells)
+    cells = np.sort(np.random.default_rng(0).choice(mi.n_cells, n_s, replace=False))
+    h, hu, hv = mi.h.astype(np.float64), mi.hu.astype(np.float64), mi.hv.astype(np.float64)
+    dt = M.dt(h, hu, hv, 0.9)
+    for _ in range(args.warmup):
+        M.step_cells(h, hu, hv, dt, cells)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        M.step_cells(h, hu, hv, dt, cells)
+    el = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    val = n_s * args.steps / el
+    line = {"impl": "reference", "metric": "cell-updates/s", "value": val, "unit": "cell-updates/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS[name]["desc"], "cells": mi.n_cells},
+            "cpu_baseline": {"value": val, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+                             "sample": f"each step: one FP64 oracle step over a seeded sample of {n_s:,} "
+                                       f"of the {mi.n_cells:,} cells"},
+            "e2e": {"value": val, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args, name):
+    import torch
+
+    from paper_2010_14416_gb300 import build as libbuild
+    from paper_2010_14416_gb300 import capi
+
+    dist, rank, ws, local = _dist()
+    wl = WORKLOADS[name]
+    prec = capi.SWE_FP32 if wl["precision"] == "f32" else capi.SWE_FP64
+    npdt = np.float32 if prec == capi.SWE_FP32 else np.float64
+    tdt = torch.float32 if prec == capi.SWE_FP32 else torch.float64
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        libbuild.build()
+    if dist:
+        dist.barrier()
+    mi = _make_input(name)
+    m = capi.Mesh(mi.nodes, mi.tris, mi.z, mi.manning, precision=prec, device=local)
+    for pairs, kind, value in mi.bcs:
+        m.set_bc(pairs, kind, value)
+    stream = torch.cuda.Stream(device=dev)
+    m.set_stream(stream)
+    h0 = torch.tensor(mi.h.astype(npdt), device=dev)
+    hu0 = torch.tensor(mi.hu.astype(npdt), device=dev)
+    hv0 = torch.tensor(mi.hv.astype(npdt), device=dev)
+    torch.cuda.synchronize(dev)
+    m.set_state(h0, hu0, hv0)
+    # warm-up: at least two graph lengths, so the CUDA graph is captured and
+    # replayed before the timed region
+    args.warmup = max(args.warmup, 96)
+    m.step(args.warmup, 0.9, sync=True)
+    n = mi.n_cells
+
+    # ---- device-resident timed region ----
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    if rank == 0:
+        clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    m.step(args.steps, 0.9, sync=False)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop() if rank == 0 else None
+    t_sim = m.info()["t"]
+    m.synchronize()
+    if dist:
+        import torch.distributed as d
+        tt = torch.tensor([ms], dtype=torch.float64)
+        d.all_reduce(tt, op=d.ReduceOp.MAX)
+        ms = float(tt.item())
+
+    # ---- end to end through the C ABI with pinned host buffers ----
+    hp = [torch.from_numpy(a.astype(npdt)).pin_memory() for a in (mi.h, mi.hu, mi.hv)]
+    out = [torch.empty(n, dtype=tdt).pin_memory() for _ in range(3)]
+    m2 = capi.Mesh(mi.nodes, mi.tris, mi.z, mi.manning, precision=prec, device=local)
+    for pairs, kind, value in mi.bcs:
+        m2.set_bc(pairs, kind, value)
+    m2.set_stream(stream)
+    m2.set_state(*hp)
+    m2.step(max(args.warmup, 6), 0.9)
+    m2.get_state(out)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    m2.set_state(*hp)
+    m2.step(args.steps, 0.9, sync=False)
+    m2.get_state(out)
+    e2e_s = time.perf_counter() - t0
+    m2.close()
+    if dist:
+        import torch.distributed as d
+        tt = torch.tensor([e2e_s], dtype=torch.float64)
+        d.all_reduce(tt, op=d.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+
+    peak, peak_kind = _peaks()
+    ab = ALG_BYTES[wl["precision"]]
+    kernel_ms = ms / args.steps
+    achieved = ab * n / (kernel_ms * 1e-3) / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", f"traffic_{name}.json")
+    if os.path.exists(tpath):
+        with open(tpath) as f:
+            tr = json.load(f)
+        if tr.get("kernel_hash") == _kernel_hash():
+            traffic = tr.get("bytes_per_launch")
+    line = {
+        "metric": "cell-updates/s",
+        "value": ws * n * args.steps / (ms * 1e-3),
+        "unit": "cell-updates/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": kernel_ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": wl["precision"],
+        "data": "synthetic",
+        "config": {"workload": wl["desc"], "cells": n, "parallelism": f"replicas{ws}",
+                   "l2": "working set ~%.2f GB > 129 MB L2, no flush needed" % (
+                       (2 * 4 + 8) * n * (4 if wl["precision"] == "f32" else 8) / 1e9 + 16 * n / 1e9),
+                   "simulated_time_s": t_sim, "reorder": "hilbert", "graph_steps": 48},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
+                     "alg_bytes_per_cell": ab},
+        "e2e": {"value": ws * n * args.steps / e2e_s, "unit": "cell-updates/s",
+                "h2d_bytes_per_step": 3 * n * np.dtype(npdt).itemsize / args.steps,
+                "d2h_bytes_per_step": 3 * n * np.dtype(npdt).itemsize / args.steps,
+                "note": "one job: swe_set_state from pinned host arrays, swe_step(steps), swe_get_state to "
+                        "pinned host arrays; bytes averaged per step"},
+        "gpu_launches": args.steps,
+        "clocks": clk,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(mi, args.cpu_budget)
+    m.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def _kernel_hash():
+    import hashlib
+    hsh = hashlib.sha1()
+    for f in ("swe_kernels.cuh", "swe_launch.cuh"):
+        with open(os.path.join(ROOT, "paper_2010_14416_gb300", "csrc", f), "rb") as fh:
+            hsh.update(fh.read())
+    return hsh.hexdigest()[:12]
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=12)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="river13m_fp32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    if args.steps is None:
+        args.steps = WORKLOADS[args.workload]["steps"]
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args, args.workload)
+    return run_gpu(args, args.workload)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

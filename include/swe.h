@@ -1,0 +1,213 @@
+/*
+ * swe.h -- C ABI of libswe, a single-GPU (GB300, sm_103a) time-explicit
+ * finite-volume solver for the 2D shallow-water equations on unstructured
+ * triangular meshes.
+ *
+ * The method is the one of Delmas & Soulaimani, "Multi-GPU implementation of
+ * a time-explicit finite volume solver for the Shallow-Water Equations using
+ * CUDA and a CUDA-Aware version of OpenMPI", Sections 2-3:
+ *   U = (h, hu, hv) cell averages on triangles (Eq 1-11), edge fluxes by the
+ *   HLLC Riemann solver in the edge-normal frame (Eq 12-14, 17-26), bed slope
+ *   by hydrostatic reconstruction (Eq 28-30), semi-implicit Manning friction
+ *   (Eq 31-37), explicit Euler with the CFL step on the inscribed radius
+ *   (Eq 15-16), boundary conditions of Section 3.1.
+ *
+ * Conventions for every call:
+ *   - Return value: SWE_OK (0) or one of the SWE_E* codes below.  A message
+ *     for the last failure of the calling thread is in swe_last_error().
+ *     No C++ exception crosses this interface.
+ *   - Arrays are dense, C order, in the caller's own cell/node numbering.
+ *     The library keeps an internal locality ordering of the cells and never
+ *     exposes it except through swe_get_permutation().
+ *   - The library copies every input array; no caller pointer is retained
+ *     after a call returns.
+ *   - Floating-point state arrays are double for SWE_FP64 meshes and float for
+ *     SWE_FP32 meshes (FP32 state, FP64 time step and time).
+ *   - Device pointers (where = SWE_DEVICE) must be on the mesh's device and
+ *     are used in stream order on the mesh's stream.
+ *   - Calls on one mesh are not thread-safe; distinct meshes are independent.
+ */
+#ifndef SWE_H
+#define SWE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SWE_API __attribute__((visibility("default")))
+#else
+#define SWE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define SWE_OK 0
+#define SWE_EINVAL 1     /* bad argument */
+#define SWE_EMESH 2      /* malformed mesh: bad index, zero area, edge shared by > 2 cells */
+#define SWE_ENOMEM 3     /* host or device allocation failed */
+#define SWE_ECUDA 4      /* a CUDA runtime call failed */
+#define SWE_ENONFINITE 5 /* a step produced a non-finite state */
+#define SWE_EDRY 6       /* every cell is dry: the CFL step (Eq 15) does not exist */
+#define SWE_ETIMEOUT 7   /* a bounded device-side wait gave up */
+
+/* ---- enums ---- */
+#define SWE_FP64 0
+#define SWE_FP32 1
+
+#define SWE_REORDER_NONE 0
+#define SWE_REORDER_RCM 1     /* reverse Cuthill-McKee on the cell adjacency graph */
+#define SWE_REORDER_HILBERT 2 /* Hilbert curve through the cell centroids */
+
+#define SWE_BC_WALL 0         /* Section 3.1: inflow with Q = 0, G~ = (0, g h^2/2, 0) */
+#define SWE_BC_INFLOW 1       /* Section 3.1: G~ = (-q, q^2/h + g h^2/2, 0), q = Q / group length */
+#define SWE_BC_TRANSMISSIVE 2 /* Section 3.1: Riemann problem with U_R = U_L */
+#define SWE_BC_STAGE 3        /* fixed free surface eta_s: ghost depth max(0, eta_s - z) */
+
+#define SWE_HOST 0
+#define SWE_DEVICE 1
+
+typedef struct swe_mesh swe_mesh;
+
+typedef struct swe_config {
+    int precision;    /* SWE_FP64 (default) or SWE_FP32 */
+    double g;         /* gravitational acceleration, default 9.81 m/s^2 */
+    double h_dry;     /* wet/dry threshold, default 1e-6 m */
+    int reorder;      /* SWE_REORDER_*, default SWE_REORDER_HILBERT */
+    int block_size;   /* threads per block of the step kernel; 0 = library default */
+    int graph_steps;  /* steps captured per CUDA graph; 0 = default, < 0 = no graphs */
+    int device;       /* CUDA device ordinal, default 0 */
+} swe_config;
+
+/* Fills *cfg with the defaults listed above. */
+SWE_API void swe_config_default(swe_config* cfg);
+
+/*
+ * Builds a mesh (Section 3.1): orients every triangle counter-clockwise, finds
+ * the neighbour across each edge, computes |Omega_i|, L_ij n_ij (Eq 9) and the
+ * inscribed radius 2|Omega_i|/perimeter (Eq 15), reorders the cells for
+ * locality and uploads everything to the device.  Every boundary edge starts
+ * as a wall.
+ *   nodes   [n_nodes][2] double, metres
+ *   tris    [n_tris][3] int32, 0-based node indices, either orientation
+ *   bathy   [n_tris] double, cell-centred bed elevation z (m)
+ *   manning [n_tris] double, Manning coefficient m (s m^-1/3), >= 0
+ *   cfg     NULL for defaults
+ *   out     receives the new mesh (owned by the caller; free with swe_mesh_destroy)
+ * Errors: SWE_EINVAL (NULL pointers, n < 1, n_tris >= 2^30, negative Manning),
+ * SWE_EMESH, SWE_ENOMEM, SWE_ECUDA.
+ */
+SWE_API int swe_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* tris, int64_t n_tris,
+                    const double* bathy, const double* manning, const swe_config* cfg,
+                    swe_mesh** out);
+
+/* Releases the mesh and all its host and device memory.  NULL is ignored. */
+SWE_API void swe_mesh_destroy(swe_mesh* mesh);
+
+/*
+ * Puts the boundary edges given as node pairs into a new boundary group of
+ * the given kind (Section 3.1).  value is the discharge Q (m^3/s) for
+ * SWE_BC_INFLOW, spread uniformly over the group's total edge length, the
+ * free-surface elevation eta_s (m) for SWE_BC_STAGE, and ignored otherwise.
+ * An edge already in another group moves to the new one.
+ *   node_pairs [n][2] int32 node indices of boundary edges, either order
+ * Errors: SWE_EINVAL (a pair that is not a boundary edge, more than 63 groups).
+ */
+SWE_API int swe_set_bc(swe_mesh* mesh, const int32_t* node_pairs, int64_t n, int kind, double value);
+
+/* Sets the CUDA stream (a cudaStream_t, NULL = legacy default stream) used by
+ * all later calls on this mesh. */
+SWE_API int swe_set_stream(swe_mesh* mesh, void* cuda_stream);
+
+/*
+ * Sets the state U = (h, hu, hv) and the time t, then computes the first CFL
+ * step from it (Eq 15).  h, hu, hv: [n_tris] arrays of the mesh precision, on
+ * the host (where = SWE_HOST; copied before return) or on the device
+ * (SWE_DEVICE; read in stream order).  h must be >= 0 and finite.
+ * Errors: SWE_EINVAL, SWE_ECUDA.
+ */
+SWE_API int swe_set_state(swe_mesh* mesh, const void* h, const void* hu, const void* hv, int where,
+                  double t);
+
+/*
+ * Advances nsteps explicit Euler steps (Eq 37) with the time step recomputed
+ * after every update as cfl * min_i R_i / (sqrt(g h_i) + |u_i|) over wet cells
+ * (Eq 15).  Each step is one fused kernel: edge fluxes with hydrostatic
+ * reconstruction and HLLC, boundary fluxes, semi-implicit friction, update,
+ * and the next step's min-reduction.  Launches are asynchronous on the mesh
+ * stream and replayed from CUDA graphs.  If t_out is not NULL the call waits
+ * for the steps, checks the device status word and stores the time reached.
+ * Errors: SWE_EINVAL (no state set, cfl <= 0), SWE_ECUDA; with t_out also
+ * SWE_ENONFINITE and SWE_EDRY.
+ */
+SWE_API int swe_step(swe_mesh* mesh, int64_t nsteps, double cfl, double* t_out);
+
+/*
+ * Copies the current state out, in the caller's cell numbering, to host
+ * (waits for completion) or device (stream-ordered) arrays of the mesh
+ * precision.  Errors: SWE_EINVAL, SWE_ECUDA.
+ */
+SWE_API int swe_get_state(swe_mesh* mesh, void* h, void* hu, void* hv, int where);
+
+/* Waits for the mesh stream and reports the device status word: SWE_OK,
+ * SWE_ENONFINITE or SWE_EDRY. */
+SWE_API int swe_synchronize(swe_mesh* mesh);
+
+typedef struct swe_info {
+    int64_t n_cells;
+    int64_t n_steps;        /* steps taken since the last swe_set_state */
+    int64_t n_clamped;      /* cells whose depth was clamped from < 0 to 0 */
+    double t;               /* time reached */
+    double dt_next;         /* CFL step for the next update (+inf if all dry) */
+    int precision;
+    int status;             /* device status word mapped to an SWE_* code */
+    int64_t device_bytes;   /* device memory held by the mesh */
+} swe_info;
+
+/* Waits for the mesh stream and fills *info. */
+SWE_API int swe_get_info(swe_mesh* mesh, swe_info* info);
+
+/* perm[new] = caller's index of the cell stored at internal position new
+ * (the locality ordering).  perm: [n_tris] int64 host array. */
+SWE_API int swe_get_permutation(swe_mesh* mesh, int64_t* perm);
+
+/*
+ * Evaluates the edge Riemann flux of the step kernel on n independent
+ * normal-frame states (Eq 17-26, with the readings of the step kernel):
+ * G~(U_L, U_R) with U_K = (h_K, h_K un_K, h_K ut_K).  All twelve pointers are
+ * device arrays of n elements of the given precision, used on `cuda_stream`.
+ * G1..G3 receive the flux, S (may be NULL) receives [n][3] = S_L, S_R, S*.
+ * Errors: SWE_EINVAL, SWE_ECUDA.
+ */
+SWE_API int swe_riemann_flux(int precision, int64_t n, const void* hL, const void* unL, const void* utL,
+                     const void* hR, const void* unR, const void* utR, double g, double h_dry,
+                     void* G1, void* G2, void* G3, void* S, void* cuda_stream);
+
+/*
+ * Runs only the host preprocessing of swe_mesh_create (validation,
+ * orientation, neighbours, geometry, locality order) and returns its result
+ * in the internal order, without touching a GPU.  Any output may be NULL.
+ *   perm     [n_tris] int64: caller index of internal cell c
+ *   code     [n_tris][3] int32: per local edge j (edge from vertex j to j+1 of
+ *            the counter-clockwise triangle), the internal index of the
+ *            neighbour, with bit 0x40000000 set when the neighbour has the
+ *            lower caller index (it is the edge's left state), or -1 on the
+ *            boundary
+ *   ln       [n_tris][3][2] double: L_ij n_ij, outward normal times length
+ *   inv_area [n_tris] double: 1/|Omega_i|;  rin [n_tris] double: 2|Omega_i|/perimeter
+ * Errors: as swe_mesh_create, without SWE_ECUDA.
+ */
+SWE_API int swe_mesh_preprocess(const double* nodes, int64_t n_nodes, const int32_t* tris, int64_t n_tris,
+                                int reorder, int64_t* perm, int32_t* code, double* ln, double* inv_area,
+                                double* rin);
+
+/* Message of the last failed call on this thread ("" if none). */
+SWE_API const char* swe_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SWE_H */

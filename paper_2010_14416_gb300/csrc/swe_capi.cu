@@ -1,0 +1,584 @@
+// swe_capi.cu -- the C ABI of libswe (declared in include/swe.h).
+//
+// Device layout of one mesh (n cells, precision T, internal locality order):
+//   state[2]  V4<T>[n]   (h, hu, hv, z) ping-pong pair
+//   geoA      V4<T>[n]   L n of edges 0 and 1
+//   geoB      V4<T>[n]   L n of edge 2, 1/|Omega|, inscribed radius
+//   topo      int4[n]    neighbour codes
+//   gm2       T[n]       g m^2
+//   perm      int64[n]   internal -> caller index
+//   small     u64[8]     dt slots 0..2 (double bits), t, status, clamp count
+// Step n reads state[n % 2] and dt slot n % 3, writes state[(n+1) % 2] and
+// slot (n+1) % 3, and clears slot (n+2) % 3, so a graph of a multiple of six
+// steps replays from any step index that is a multiple of six.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "swe_internal.h"
+
+namespace swe {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+namespace {
+
+constexpr int kSmallWords = 8;
+constexpr int kSlotT = 3, kSlotStatus = 4, kSlotClamp = 5;
+constexpr int kDefaultGraphSteps = 48;
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int cuda_fail(cudaError_t e, const char* what) {
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return SWE_ECUDA;
+}
+
+__global__ void init_small_kernel(unsigned long long* small, double t) {
+    if (threadIdx.x == 0) {
+        small[0] = kInfBits; small[1] = kInfBits; small[2] = kInfBits;
+        small[kSlotT] = (unsigned long long)__double_as_longlong(t);
+        small[kSlotStatus] = 0ULL;
+        small[kSlotClamp] = 0ULL;
+        small[6] = 0ULL; small[7] = 0ULL;
+    }
+}
+
+}  // namespace
+}  // namespace swe
+
+using namespace swe;
+
+struct swe_mesh {
+    swe_config cfg{};
+    HostMesh hm;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    size_t esz = 8;                    // sizeof(T)
+    void* state[2] = {nullptr, nullptr};
+    void* geoA = nullptr;
+    void* geoB = nullptr;
+    int4* topo = nullptr;
+    void* gm2 = nullptr;
+    void* zdev = nullptr;
+    long long* perm = nullptr;
+    void* stage[3] = {nullptr, nullptr, nullptr};
+    unsigned long long* small = nullptr;
+    BcTable bc{};
+    std::vector<double> group_len;     // total edge length per group
+    std::vector<double> group_value;   // Q or eta_s as given
+    int n_groups = 1;
+    bool topo_dirty = false;
+    bool have_state = false;
+    int64_t nstep = 0;
+    cudaGraphExec_t graph = nullptr;
+    int graph_len = 0;
+    double graph_cfl = -1.0;
+    int64_t device_bytes = 0;
+};
+
+namespace {
+
+int dev_alloc(swe_mesh* m, void** p, size_t bytes, const char* what) {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        set_error(std::string("device allocation failed for ") + what + ": " + cudaGetErrorString(e));
+        return SWE_ENOMEM;
+    }
+    m->device_bytes += (int64_t)bytes;
+    return SWE_OK;
+}
+
+void drop_graph(swe_mesh* m) {
+    if (m->graph) cudaGraphExecDestroy(m->graph);
+    m->graph = nullptr;
+    m->graph_len = 0;
+    m->graph_cfl = -1.0;
+}
+
+template <typename T>
+int upload_static(swe_mesh* m) {
+    const HostMesh& H = m->hm;
+    const int64_t n = H.n_cells;
+    std::vector<V4<T>> A(n), B(n);
+    std::vector<T> gm2(n), zt(n);
+    std::vector<int4> topo(n);
+    for (int64_t c = 0; c < n; ++c) {
+        A[c].x = (T)H.ln[6 * c + 0]; A[c].y = (T)H.ln[6 * c + 1];
+        A[c].z = (T)H.ln[6 * c + 2]; A[c].w = (T)H.ln[6 * c + 3];
+        B[c].x = (T)H.ln[6 * c + 4]; B[c].y = (T)H.ln[6 * c + 5];
+        B[c].z = (T)H.inv_area[c]; B[c].w = (T)H.rin[c];
+        gm2[c] = (T)(m->cfg.g * H.m[c] * H.m[c]);
+        zt[c] = (T)H.z[c];
+        topo[c] = make_int4(H.code[3 * c], H.code[3 * c + 1], H.code[3 * c + 2], 0);
+    }
+    cudaError_t e;
+    if ((e = cudaMemcpy(m->geoA, A.data(), n * sizeof(V4<T>), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(m->geoB, B.data(), n * sizeof(V4<T>), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(m->gm2, gm2.data(), n * sizeof(T), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(m->zdev, zt.data(), n * sizeof(T), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(m->topo, topo.data(), n * sizeof(int4), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(m->perm, H.perm.data(), n * sizeof(long long), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(e, "swe_mesh_create: upload");
+    return SWE_OK;
+}
+
+int flush_topo(swe_mesh* m) {
+    if (!m->topo_dirty) return SWE_OK;
+    const HostMesh& H = m->hm;
+    const int64_t n = H.n_cells;
+    std::vector<int4> topo(n);
+    for (int64_t c = 0; c < n; ++c)
+        topo[c] = make_int4(H.code[3 * c], H.code[3 * c + 1], H.code[3 * c + 2], 0);
+    cudaError_t e = cudaMemcpyAsync(m->topo, topo.data(), n * sizeof(int4), cudaMemcpyHostToDevice, m->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "swe_set_bc: upload");
+    for (int gI = 0; gI < m->n_groups; ++gI) {
+        if (m->bc.kind[gI] == kBcInflow)
+            m->bc.value[gI] = m->group_len[gI] > 0.0 ? m->group_value[gI] / m->group_len[gI] : 0.0;
+        else
+            m->bc.value[gI] = m->group_value[gI];
+    }
+    m->topo_dirty = false;
+    drop_graph(m);
+    return SWE_OK;
+}
+
+template <typename T>
+StepArgs<T> make_args(swe_mesh* m, int64_t step_index, double cfl) {
+    StepArgs<T> a;
+    const int p2 = (int)(step_index % 2), p3 = (int)(step_index % 3);
+    a.s_in = (const V4<T>*)m->state[p2];
+    a.s_out = (V4<T>*)m->state[1 - p2];
+    a.geoA = (const V4<T>*)m->geoA;
+    a.geoB = (const V4<T>*)m->geoB;
+    a.topo = m->topo;
+    a.gm2 = (const T*)m->gm2;
+    a.dt_read = (const double*)(m->small + p3);
+    a.dt_write = m->small + (p3 + 1) % 3;
+    a.dt_reset = m->small + (p3 + 2) % 3;
+    a.t = (double*)(m->small + kSlotT);
+    a.status = (unsigned*)(m->small + kSlotStatus);
+    a.n_clamped = m->small + kSlotClamp;
+    a.n = m->hm.n_cells;
+    a.cfl = cfl;
+    a.g = (T)m->cfg.g;
+    a.h_dry = (T)m->cfg.h_dry;
+    a.bc = m->bc;
+    return a;
+}
+
+template <typename T>
+cudaError_t launch_one(swe_mesh* m, int64_t step_index, double cfl, cudaStream_t st) {
+    return Launch<T>::step(make_args<T>(m, step_index, cfl), m->cfg.block_size, st);
+}
+
+template <typename T>
+int capture_graph(swe_mesh* m, int len, double cfl) {
+    drop_graph(m);
+    cudaError_t e = cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "swe_step: begin capture");
+    cudaError_t le = cudaSuccess;
+    for (int s = 0; s < len && le == cudaSuccess; ++s) le = launch_one<T>(m, s, cfl, m->cap_stream);
+    cudaGraph_t gr = nullptr;
+    e = cudaStreamEndCapture(m->cap_stream, &gr);
+    if (le != cudaSuccess) { if (gr) cudaGraphDestroy(gr); return cuda_fail(le, "swe_step: capture launch"); }
+    if (e != cudaSuccess) return cuda_fail(e, "swe_step: end capture");
+    e = cudaGraphInstantiate(&m->graph, gr, 0);
+    cudaGraphDestroy(gr);
+    if (e != cudaSuccess) { m->graph = nullptr; return cuda_fail(e, "swe_step: instantiate"); }
+    m->graph_len = len;
+    m->graph_cfl = cfl;
+    return SWE_OK;
+}
+
+template <typename T>
+int run_steps(swe_mesh* m, int64_t nsteps, double cfl) {
+    int64_t left = nsteps;
+    const int gsteps = m->cfg.graph_steps;
+    // singles until the step index is a multiple of six
+    while (left > 0 && (m->nstep % 6 != 0 || gsteps <= 0 || left < gsteps)) {
+        cudaError_t e = launch_one<T>(m, m->nstep, cfl, m->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "swe_step: launch");
+        ++m->nstep;
+        --left;
+        if (m->nstep % 6 == 0 && gsteps > 0 && left >= gsteps) break;
+    }
+    if (left >= gsteps && gsteps > 0) {
+        if (!m->graph || m->graph_len != gsteps || m->graph_cfl != cfl) {
+            int rc = capture_graph<T>(m, gsteps, cfl);
+            if (rc) return rc;
+        }
+        while (left >= gsteps) {
+            cudaError_t e = cudaGraphLaunch(m->graph, m->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "swe_step: graph launch");
+            m->nstep += gsteps;
+            left -= gsteps;
+        }
+    }
+    while (left > 0) {
+        cudaError_t e = launch_one<T>(m, m->nstep, cfl, m->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "swe_step: launch");
+        ++m->nstep;
+        --left;
+    }
+    return SWE_OK;
+}
+
+int read_small(swe_mesh* m, unsigned long long out[kSmallWords]) {
+    cudaError_t e = cudaMemcpyAsync(out, m->small, sizeof(unsigned long long) * kSmallWords,
+                                    cudaMemcpyDeviceToHost, m->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "swe: reading the status block");
+    return SWE_OK;
+}
+
+int status_code(unsigned long long st) {
+    if (st & kStatusNonFinite) { set_error("swe_step: non-finite state"); return SWE_ENONFINITE; }
+    if (st & kStatusDry) { set_error("swe_step: every cell is dry, no CFL time step"); return SWE_EDRY; }
+    return SWE_OK;
+}
+
+double bits_to_double(unsigned long long b) {
+    double d;
+    std::memcpy(&d, &b, sizeof d);
+    return d;
+}
+
+int ensure_stage(swe_mesh* m) {
+    for (int k = 0; k < 3; ++k) {
+        if (!m->stage[k]) {
+            int rc = dev_alloc(m, &m->stage[k], m->hm.n_cells * m->esz, "staging");
+            if (rc) return rc;
+        }
+    }
+    return SWE_OK;
+}
+
+template <typename T>
+int set_state_t(swe_mesh* m, const void* h, const void* hu, const void* hv, int where, double t) {
+    const int64_t n = m->hm.n_cells;
+    const T* src[3] = {(const T*)h, (const T*)hu, (const T*)hv};
+    cudaError_t e;
+    if (where == SWE_HOST) {
+        int rc = ensure_stage(m);
+        if (rc) return rc;
+        for (int k = 0; k < 3; ++k) {
+            e = cudaMemcpyAsync(m->stage[k], src[k], n * sizeof(T), cudaMemcpyHostToDevice, m->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "swe_set_state: copy");
+            src[k] = (const T*)m->stage[k];
+        }
+    }
+    // z rides in the state record (copied from the static z array)
+    e = Launch<T>::pack(src[0], src[1], src[2], m->perm, (const T*)m->zdev, (V4<T>*)m->state[0], n, m->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(m->state[1], m->state[0], n * sizeof(V4<T>),
+                                              cudaMemcpyDeviceToDevice, m->stream);
+    if (e == cudaSuccess) { init_small_kernel<<<1, 32, 0, m->stream>>>(m->small, t); e = cudaGetLastError(); }
+    if (e == cudaSuccess)
+        e = Launch<T>::dt((const V4<T>*)m->state[0], (const V4<T>*)m->geoB, n, (T)m->cfg.g, (T)m->cfg.h_dry,
+                          m->small + 0, m->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "swe_set_state");
+    m->have_state = true;
+    m->nstep = 0;
+    return SWE_OK;
+}
+
+template <typename T>
+int get_state_t(swe_mesh* m, void* h, void* hu, void* hv, int where) {
+    const int64_t n = m->hm.n_cells;
+    const V4<T>* cur = (const V4<T>*)m->state[m->nstep % 2];
+    cudaError_t e;
+    if (where == SWE_DEVICE) {
+        e = Launch<T>::unpack(cur, m->perm, (T*)h, (T*)hu, (T*)hv, n, m->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "swe_get_state");
+        return SWE_OK;
+    }
+    int rc = ensure_stage(m);
+    if (rc) return rc;
+    e = Launch<T>::unpack(cur, m->perm, (T*)m->stage[0], (T*)m->stage[1], (T*)m->stage[2], n, m->stream);
+    void* dst[3] = {h, hu, hv};
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k)
+        e = cudaMemcpyAsync(dst[k], m->stage[k], n * sizeof(T), cudaMemcpyDeviceToHost, m->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "swe_get_state");
+    return SWE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void swe_config_default(swe_config* cfg) {
+    if (!cfg) return;
+    cfg->precision = SWE_FP64;
+    cfg->g = 9.81;
+    cfg->h_dry = 1e-6;
+    cfg->reorder = SWE_REORDER_HILBERT;
+    cfg->block_size = 0;
+    cfg->graph_steps = 0;
+    cfg->device = 0;
+}
+
+const char* swe_last_error(void) { return g_last_error.c_str(); }
+
+void swe_mesh_destroy(swe_mesh* m) {
+    if (!m) return;
+    DeviceGuard dg(m->cfg.device);
+    if (m->stream) cudaStreamSynchronize(m->stream);
+    drop_graph(m);
+    void* bufs[] = {m->state[0], m->state[1], m->geoA, m->geoB, m->topo, m->gm2, m->zdev, m->perm,
+                    m->stage[0], m->stage[1], m->stage[2], m->small};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
+    delete m;
+}
+
+int swe_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* tris, int64_t n_tris,
+                    const double* bathy, const double* manning, const swe_config* cfg, swe_mesh** out) {
+    if (!out) { set_error("swe_mesh_create: out is NULL"); return SWE_EINVAL; }
+    *out = nullptr;
+    swe_config c;
+    swe_config_default(&c);
+    if (cfg) c = *cfg;
+    if (c.precision != SWE_FP64 && c.precision != SWE_FP32) { set_error("swe_mesh_create: bad precision"); return SWE_EINVAL; }
+    if (!(c.g > 0.0) || !(c.h_dry > 0.0)) { set_error("swe_mesh_create: g and h_dry must be > 0"); return SWE_EINVAL; }
+    if (c.block_size == 0) c.block_size = c.precision == SWE_FP32 ? 256 : 128;
+    if (c.block_size != 128 && c.block_size != 256 && c.block_size != 512) {
+        set_error("swe_mesh_create: block_size must be 128, 256 or 512");
+        return SWE_EINVAL;
+    }
+    if (c.graph_steps == 0) c.graph_steps = kDefaultGraphSteps;
+    if (c.graph_steps > 0) c.graph_steps = std::max(6, (c.graph_steps / 6) * 6);
+    swe_mesh* m = new (std::nothrow) swe_mesh();
+    if (!m) { set_error("swe_mesh_create: out of host memory"); return SWE_ENOMEM; }
+    m->cfg = c;
+    m->esz = c.precision == SWE_FP32 ? 4 : 8;
+    std::string err;
+    int rc;
+    try {
+        rc = build_host_mesh(nodes, n_nodes, tris, n_tris, bathy, manning, c.reorder, m->hm, err);
+    } catch (const std::bad_alloc&) {
+        rc = SWE_ENOMEM;
+        err = "swe_mesh_create: out of host memory";
+    }
+    if (rc) { set_error(err); delete m; return rc; }
+    DeviceGuard dg(c.device);
+    if (!dg.ok) { set_error("swe_mesh_create: cannot select the device"); delete m; return SWE_ECUDA; }
+    cudaError_t e = cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { delete m; return cuda_fail(e, "swe_mesh_create: stream"); }
+    const int64_t n = n_tris;
+    const size_t v4 = 4 * m->esz;
+    if ((rc = dev_alloc(m, &m->state[0], n * v4, "state")) || (rc = dev_alloc(m, &m->state[1], n * v4, "state")) ||
+        (rc = dev_alloc(m, &m->geoA, n * v4, "geometry")) || (rc = dev_alloc(m, &m->geoB, n * v4, "geometry")) ||
+        (rc = dev_alloc(m, (void**)&m->topo, n * sizeof(int4), "topology")) ||
+        (rc = dev_alloc(m, &m->gm2, n * m->esz, "manning")) ||
+        (rc = dev_alloc(m, &m->zdev, n * m->esz, "bed")) ||
+        (rc = dev_alloc(m, (void**)&m->perm, n * sizeof(long long), "permutation")) ||
+        (rc = dev_alloc(m, (void**)&m->small, kSmallWords * sizeof(unsigned long long), "status"))) {
+        swe_mesh_destroy(m);
+        return rc;
+    }
+    rc = c.precision == SWE_FP32 ? upload_static<float>(m) : upload_static<double>(m);
+    if (rc) { swe_mesh_destroy(m); return rc; }
+    m->bc.kind[0] = kBcWall;
+    m->bc.value[0] = 0.0;
+    m->group_len.assign(1, 0.0);
+    m->group_value.assign(1, 0.0);
+    for (int64_t s = 0; s < 3 * n; ++s)
+        if (m->hm.code[s] < 0) m->group_len[0] += m->hm.len[s];
+    *out = m;
+    return SWE_OK;
+}
+
+int swe_set_bc(swe_mesh* m, const int32_t* pairs, int64_t n, int kind, double value) {
+    if (!m || (!pairs && n > 0) || n < 0) { set_error("swe_set_bc: bad arguments"); return SWE_EINVAL; }
+    if (kind < SWE_BC_WALL || kind > SWE_BC_STAGE) { set_error("swe_set_bc: unknown kind"); return SWE_EINVAL; }
+    if (m->n_groups >= kMaxGroups - 1) { set_error("swe_set_bc: too many boundary groups"); return SWE_EINVAL; }
+    if (!std::isfinite(value)) { set_error("swe_set_bc: non-finite value"); return SWE_EINVAL; }
+    HostMesh& H = m->hm;
+    const int grp = m->n_groups;
+    std::vector<int64_t> slots;
+    slots.reserve(n);
+    for (int64_t e = 0; e < n; ++e) {
+        const int32_t a = pairs[2 * e], b = pairs[2 * e + 1];
+        const uint64_t key = ((uint64_t)std::min(a, b) << 32) | (uint64_t)std::max(a, b);
+        auto it = std::lower_bound(H.bkey.begin(), H.bkey.end(), key);
+        if (it == H.bkey.end() || *it != key) {
+            set_error("swe_set_bc: node pair " + std::to_string(a) + "," + std::to_string(b) +
+                      " is not a boundary edge");
+            return SWE_EINVAL;
+        }
+        slots.push_back(H.bslot[it - H.bkey.begin()]);
+    }
+    double total = 0.0;
+    for (int64_t s : slots) {
+        const int old = -1 - H.code[s];
+        if (old == grp) continue;
+        m->group_len[old] -= H.len[s];
+        total += H.len[s];
+        H.code[s] = -1 - grp;
+    }
+    m->group_len.push_back(total);
+    m->group_value.push_back(value);
+    m->bc.kind[grp] = kind;
+    m->n_groups = grp + 1;
+    m->topo_dirty = true;
+    DeviceGuard dg(m->cfg.device);
+    return flush_topo(m);
+}
+
+int swe_set_stream(swe_mesh* m, void* stream) {
+    if (!m) { set_error("swe_set_stream: NULL mesh"); return SWE_EINVAL; }
+    m->stream = (cudaStream_t)stream;
+    return SWE_OK;
+}
+
+int swe_set_state(swe_mesh* m, const void* h, const void* hu, const void* hv, int where, double t) {
+    if (!m || !h || !hu || !hv || (where != SWE_HOST && where != SWE_DEVICE) || !std::isfinite(t)) {
+        set_error("swe_set_state: bad arguments");
+        return SWE_EINVAL;
+    }
+    DeviceGuard dg(m->cfg.device);
+    int rc = flush_topo(m);
+    if (rc) return rc;
+    return m->cfg.precision == SWE_FP32 ? set_state_t<float>(m, h, hu, hv, where, t)
+                                        : set_state_t<double>(m, h, hu, hv, where, t);
+}
+
+int swe_step(swe_mesh* m, int64_t nsteps, double cfl, double* t_out) {
+    if (!m || nsteps < 0 || !(cfl > 0.0) || !std::isfinite(cfl)) { set_error("swe_step: bad arguments"); return SWE_EINVAL; }
+    if (!m->have_state) { set_error("swe_step: no state set"); return SWE_EINVAL; }
+    DeviceGuard dg(m->cfg.device);
+    int rc = flush_topo(m);
+    if (rc) return rc;
+    rc = m->cfg.precision == SWE_FP32 ? run_steps<float>(m, nsteps, cfl) : run_steps<double>(m, nsteps, cfl);
+    if (rc) return rc;
+    if (t_out) {
+        unsigned long long s[kSmallWords];
+        rc = read_small(m, s);
+        if (rc) return rc;
+        *t_out = bits_to_double(s[kSlotT]);
+        return status_code(s[kSlotStatus]);
+    }
+    return SWE_OK;
+}
+
+int swe_get_state(swe_mesh* m, void* h, void* hu, void* hv, int where) {
+    if (!m || !h || !hu || !hv || (where != SWE_HOST && where != SWE_DEVICE)) {
+        set_error("swe_get_state: bad arguments");
+        return SWE_EINVAL;
+    }
+    if (!m->have_state) { set_error("swe_get_state: no state set"); return SWE_EINVAL; }
+    DeviceGuard dg(m->cfg.device);
+    return m->cfg.precision == SWE_FP32 ? get_state_t<float>(m, h, hu, hv, where)
+                                        : get_state_t<double>(m, h, hu, hv, where);
+}
+
+int swe_synchronize(swe_mesh* m) {
+    if (!m) { set_error("swe_synchronize: NULL mesh"); return SWE_EINVAL; }
+    DeviceGuard dg(m->cfg.device);
+    unsigned long long s[kSmallWords];
+    int rc = read_small(m, s);
+    if (rc) return rc;
+    return status_code(s[kSlotStatus]);
+}
+
+int swe_get_info(swe_mesh* m, swe_info* info) {
+    if (!m || !info) { set_error("swe_get_info: bad arguments"); return SWE_EINVAL; }
+    DeviceGuard dg(m->cfg.device);
+    std::memset(info, 0, sizeof *info);
+    info->n_cells = m->hm.n_cells;
+    info->precision = m->cfg.precision;
+    info->device_bytes = m->device_bytes;
+    info->n_steps = m->nstep;
+    if (!m->have_state) {
+        info->dt_next = INFINITY;
+        return SWE_OK;
+    }
+    unsigned long long s[kSmallWords];
+    int rc = read_small(m, s);
+    if (rc) return rc;
+    info->t = bits_to_double(s[kSlotT]);
+    // the slot holds min_i R_i / (c_i + |u_i|); the CFL number of the next
+    // swe_step call multiplies it
+    info->dt_next = bits_to_double(s[m->nstep % 3]);
+    info->n_clamped = (int64_t)s[kSlotClamp];
+    info->status = s[kSlotStatus] & kStatusNonFinite ? SWE_ENONFINITE
+                   : (s[kSlotStatus] & kStatusDry ? SWE_EDRY : SWE_OK);
+    return SWE_OK;
+}
+
+int swe_get_permutation(swe_mesh* m, int64_t* perm) {
+    if (!m || !perm) { set_error("swe_get_permutation: bad arguments"); return SWE_EINVAL; }
+    std::memcpy(perm, m->hm.perm.data(), sizeof(int64_t) * m->hm.n_cells);
+    return SWE_OK;
+}
+
+int swe_mesh_preprocess(const double* nodes, int64_t n_nodes, const int32_t* tris, int64_t n_tris, int reorder,
+                        int64_t* perm, int32_t* code, double* ln, double* inv_area, double* rin) {
+    if (n_tris < 1) { set_error("swe_mesh_preprocess: empty mesh"); return SWE_EINVAL; }
+    HostMesh H;
+    std::string err;
+    int rc;
+    try {
+        std::vector<double> zeros((size_t)n_tris, 0.0);
+        rc = build_host_mesh(nodes, n_nodes, tris, n_tris, zeros.data(), zeros.data(), reorder, H, err);
+    } catch (const std::bad_alloc&) {
+        rc = SWE_ENOMEM;
+        err = "swe_mesh_preprocess: out of host memory";
+    }
+    if (rc) { set_error(err); return rc; }
+    const size_t n = (size_t)n_tris;
+    if (perm) std::memcpy(perm, H.perm.data(), n * sizeof(int64_t));
+    if (code) std::memcpy(code, H.code.data(), 3 * n * sizeof(int32_t));
+    if (ln) std::memcpy(ln, H.ln.data(), 6 * n * sizeof(double));
+    if (inv_area) std::memcpy(inv_area, H.inv_area.data(), n * sizeof(double));
+    if (rin) std::memcpy(rin, H.rin.data(), n * sizeof(double));
+    return SWE_OK;
+}
+
+int swe_riemann_flux(int precision, int64_t n, const void* hL, const void* unL, const void* utL,
+                     const void* hR, const void* unR, const void* utR, double g, double h_dry, void* G1,
+                     void* G2, void* G3, void* S, void* stream) {
+    if (n < 0 || (n > 0 && (!hL || !unL || !utL || !hR || !unR || !utR || !G1 || !G2 || !G3))) {
+        set_error("swe_riemann_flux: bad arguments");
+        return SWE_EINVAL;
+    }
+    cudaError_t e;
+    if (precision == SWE_FP32)
+        e = Launch<float>::riemann(n, (const float*)hL, (const float*)unL, (const float*)utL, (const float*)hR,
+                                   (const float*)unR, (const float*)utR, (float)g, (float)h_dry, (float*)G1,
+                                   (float*)G2, (float*)G3, (float*)S, (cudaStream_t)stream);
+    else if (precision == SWE_FP64)
+        e = Launch<double>::riemann(n, (const double*)hL, (const double*)unL, (const double*)utL,
+                                    (const double*)hR, (const double*)unR, (const double*)utR, g, h_dry,
+                                    (double*)G1, (double*)G2, (double*)G3, (double*)S, (cudaStream_t)stream);
+    else {
+        set_error("swe_riemann_flux: bad precision");
+        return SWE_EINVAL;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "swe_riemann_flux");
+    return SWE_OK;
+}
+
+}  // extern "C"

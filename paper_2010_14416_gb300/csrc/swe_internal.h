@@ -1,0 +1,45 @@
+// swe_internal.h -- host-side structures shared by the mesh preprocessing and
+// the C ABI of libswe.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/swe.h"
+#include "swe_kernels.cuh"
+
+namespace swe {
+
+// Result of the host preprocessing (Section 3.1 geometry, neighbours across
+// shared edges, locality order), in the internal cell order.
+struct HostMesh {
+    int64_t n_cells = 0, n_nodes = 0;
+    std::vector<int64_t> perm;      // perm[new] = caller index
+    std::vector<int64_t> inv;       // inv[caller] = new
+    std::vector<int32_t> tri;       // [n][3] counter-clockwise, internal order
+    std::vector<double> ln;         // [n][3][2] L_ij n_ij (outward, times edge length)
+    std::vector<double> inv_area;   // 1/|Omega_i|
+    std::vector<double> rin;        // inscribed radius 2|Omega|/perimeter
+    std::vector<double> z, m;       // bed elevation, Manning n
+    std::vector<int32_t> code;      // [n][3] neighbour code: k | flip bit, or -1 - group
+    std::vector<double> len;        // [n][3] edge length (FP64, for BC group lengths)
+    std::vector<int64_t> bslot;     // boundary half-edge slots (3 i + j), sorted by node key
+    std::vector<uint64_t> bkey;     // matching sorted keys (min node << 32 | max node)
+};
+
+// Builds the host mesh; returns SWE_OK or an error code with a message.
+int build_host_mesh(const double* nodes, int64_t n_nodes, const int32_t* tris, int64_t n_tris,
+                    const double* bathy, const double* manning, int reorder, HostMesh& out,
+                    std::string& err);
+
+// Locality orderings of the cells; each returns order[new] = old.
+std::vector<int64_t> order_hilbert(const std::vector<double>& cx, const std::vector<double>& cy);
+std::vector<int64_t> order_rcm(int64_t n, const std::vector<int64_t>& nbr /* [n][3], -1 = none */);
+
+// Thread-local error message of the C ABI.
+void set_error(const std::string& msg);
+
+}  // namespace swe

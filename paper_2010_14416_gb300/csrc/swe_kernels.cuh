@@ -1,0 +1,391 @@
+// swe_kernels.cuh -- device code of the fused shallow-water step (sm_103a).
+//
+// One thread owns one cell (in the locality order chosen at mesh build time)
+// and gathers its three neighbours, so every cell's sum of edge fluxes is
+// formed in a fixed order without atomics.  Each interior edge has a
+// canonical orientation: the cell with the lower caller index is the left
+// state and its outward normal is the edge normal.  Both cells of an edge run
+// the identical instruction sequence on identical operands (the edge loop is
+// kept rolled so there is a single code path) and apply the result with
+// opposite signs, so the two contributions cancel bit for bit and the result
+// does not depend on the cell ordering.
+//
+// Method: Delmas & Soulaimani, Sections 2-3 (Eq 12-37); readings of the
+// garbled equations are the same as the oracle's and are listed where used.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace swe {
+
+constexpr int kMaxGroups = 64;
+constexpr int kNbrMask = 0x3FFFFFFF;   // neighbour index bits
+constexpr int kFlipBit = 0x40000000;   // set when this cell is the right side of the edge
+constexpr unsigned long long kInfBits = 0x7FF0000000000000ULL;  // +inf as double bits
+
+// status word bits
+constexpr unsigned kStatusNonFinite = 1u;
+constexpr unsigned kStatusDry = 2u;
+
+constexpr int kBcWall = 0, kBcInflow = 1, kBcTransmissive = 2, kBcStage = 3;
+
+template <typename T>
+struct alignas(4 * sizeof(T)) V4 {
+    T x, y, z, w;
+};
+
+// Boundary groups: for group g, kind[g] and value[g] = q (m^2/s, inflow per
+// unit length) or eta_s (m, stage).
+struct BcTable {
+    int kind[kMaxGroups];
+    double value[kMaxGroups];
+};
+
+template <typename T>
+struct StepArgs {
+    const V4<T>* __restrict__ s_in;    // (h, hu, hv, z) per cell
+    V4<T>* __restrict__ s_out;
+    const V4<T>* __restrict__ geoA;    // (L n)_0 x, y, (L n)_1 x, y : outward normals times length
+    const V4<T>* __restrict__ geoB;    // (L n)_2 x, y, 1/|Omega|, inscribed radius
+    const int4* __restrict__ topo;     // neighbour codes of the 3 edges, .w unused
+    const T* __restrict__ gm2;         // g m^2 per cell (Manning factor of Eq 32)
+    const double* dt_read;             // min_i R_i/(c_i+|u_i|) of the current state
+    unsigned long long* dt_write;      // same quantity for the new state (atomicMin on bits)
+    unsigned long long* dt_reset;      // slot cleared to +inf for the step after next
+    double* t;                         // simulated time
+    unsigned* status;                  // kStatus* bits
+    unsigned long long* n_clamped;     // cells clamped from h < 0
+    long long n;                       // number of cells
+    double cfl;
+    T g, h_dry;
+    BcTable bc;
+};
+
+// ---- precision-specific arithmetic ------------------------------------------------
+// The FP32 instantiation is compiled with fast-math: division, reciprocal and
+// square root map to the hardware approximations (a few ulp), which the
+// 1e-4 FP32 tolerance absorbs.  The FP64 instantiation keeps IEEE division
+// and square root.
+template <typename T> struct Ar;
+template <> struct Ar<float> {
+    static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+    static __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+    static __device__ __forceinline__ float div_(float a, float b) { return __fdividef(a, b); }
+    static __device__ __forceinline__ float rcp_(float x) { return __fdividef(1.0f, x); }
+    // h^(-7/3) through the hardware base-2 exp/log pair
+    static __device__ __forceinline__ float pow_m73(float h) { return exp2f(-7.0f / 3.0f * __log2f(h)); }
+};
+template <> struct Ar<double> {
+    static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+    static __device__ __forceinline__ double rsqrt_(double x) { return 1.0 / sqrt(x); }
+    static __device__ __forceinline__ double div_(double a, double b) { return a / b; }
+    static __device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
+    static __device__ __forceinline__ double pow_m73(double h) { return 1.0 / (h * h * cbrt(h)); }
+};
+
+template <typename T>
+__device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
+template <typename T>
+__device__ __forceinline__ T tmin(T a, T b) { return a < b ? a : b; }
+
+// ---- Riemann flux in the edge-normal frame (Eq 14, 17-26) -------------------------
+// Input U_K = (h_K, h_K un_K, h_K ut_K) given as depth and normal/tangential
+// velocity.  Readings: Eq 20 p_K = sqrt(h*(h*+h_K)/2)/h_K; Eq 21-22 use the
+// normal velocity jump; the two-rarefaction base is clamped at 0; Eq 24 is
+// upwinded (ut_L when S* >= 0); Eq 26 line 2 is the right-dry case; both dry
+// gives no flux.
+template <typename T>
+__device__ __forceinline__ void riemann_hllc(T hL, T unL, T utL, T hR, T unR, T utR, T g, T h_dry,
+                                             T& G1, T& G2, T& G3, T* speeds = nullptr) {
+    using A = Ar<T>;
+    const bool wetL = hL > h_dry, wetR = hR > h_dry;
+    if (!wetL && !wetR) {
+        G1 = T(0); G2 = T(0); G3 = T(0);
+        if (speeds) { speeds[0] = T(0); speeds[1] = T(0); speeds[2] = T(0); }
+        return;
+    }
+    const T aL = A::sqrt_(g * hL), aR = A::sqrt_(g * hR);
+    T SL, SR, Ss;
+    if (!wetL) {
+        SL = unR - T(2) * aR; SR = unR + aR; Ss = SL;
+    } else if (!wetR) {
+        SL = unL - aL; SR = unL + T(2) * aL; Ss = SR;
+    } else {
+        const T hsum = hL + hR;
+        const T h0 = T(0.5) * hsum - T(0.25) * A::div_((unR - unL) * hsum, aL + aR);  // Eq 21
+        T hs;
+        if (h0 <= tmin(hL, hR)) {                                                   // Eq 22
+            const T b = tmax(T(0), T(0.5) * (aL + aR) + T(0.25) * (unL - unR));
+            hs = A::div_(b * b, g);
+        } else {                                                                    // Eq 23
+            const T r2h0 = A::rcp_(T(2) * h0);
+            const T gL = A::sqrt_(g * (h0 + hL) * r2h0 * A::rcp_(hL));
+            const T gR = A::sqrt_(g * (h0 + hR) * r2h0 * A::rcp_(hR));
+            hs = A::div_(hL * gL + hR * gR + unL - unR, gL + gR);
+        }
+        const T pL = hs > hL ? A::div_(A::sqrt_(T(0.5) * hs * (hs + hL)), hL) : T(1);  // Eq 20
+        const T pR = hs > hR ? A::div_(A::sqrt_(T(0.5) * hs * (hs + hR)), hR) : T(1);
+        SL = unL - aL * pL;                                                          // Eq 19
+        SR = unR + aR * pR;
+        const T mL = hL * (unL - SL), mR = hR * (unR - SR);
+        Ss = A::div_(SL * mR - SR * mL, mR - mL);                                    // Eq 25
+    }
+    const T qL = hL * unL, qR = hR * unR;
+    const T PL = qL * unL + T(0.5) * g * hL * hL;
+    const T PR = qR * unR + T(0.5) * g * hR * hR;
+    if (SL >= T(0)) {                                                                // Eq 17
+        G1 = qL; G2 = PL;
+    } else if (SR <= T(0)) {
+        G1 = qR; G2 = PR;
+    } else {                                                                         // Eq 18
+        const T r = A::rcp_(SR - SL);
+        const T ss = SR * SL;
+        G1 = (SR * qL - SL * qR + ss * (hR - hL)) * r;
+        G2 = (SR * PL - SL * PR + ss * (qR - qL)) * r;
+    }
+    G3 = G1 * (Ss >= T(0) ? utL : utR);                                              // Eq 24
+    if (speeds) { speeds[0] = SL; speeds[1] = SR; speeds[2] = Ss; }
+}
+
+// ---- block min of a non-negative double, published with one atomicMin -------------
+template <int BLOCK>
+__device__ __forceinline__ void block_min_publish(double cand, unsigned long long* dst) {
+    __shared__ double warp_min[BLOCK / 32];
+    for (int o = 16; o > 0; o >>= 1) cand = fmin(cand, __shfl_xor_sync(0xffffffffu, cand, o));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) warp_min[wid] = cand;
+    __syncthreads();
+    if (wid == 0) {
+        double v = lane < BLOCK / 32 ? warp_min[lane] : __longlong_as_double((long long)kInfBits);
+        for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+        // non-negative doubles order like their bit patterns: the min is exact
+        if (lane == 0 && v < __longlong_as_double((long long)kInfBits))
+            atomicMin(dst, (unsigned long long)__double_as_longlong(v));
+    }
+}
+
+// ---- the fused step: fluxes + bed source + BCs + friction + update + next dt ------
+template <typename T, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) step_kernel(const StepArgs<T> a) {
+    using A = Ar<T>;
+    const double dt_d = a.cfl * (*a.dt_read);
+    const bool have_dt = dt_d < __longlong_as_double((long long)kInfBits);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *a.dt_reset = kInfBits;
+        if (have_dt) *a.t += dt_d;
+        else atomicOr(a.status, kStatusDry);
+    }
+    const long long i = (long long)blockIdx.x * BLOCK + threadIdx.x;
+    double cand = __longlong_as_double((long long)kInfBits);
+    if (i < a.n) {
+        const V4<T> own = a.s_in[i];
+        if (!have_dt) {
+            a.s_out[i] = own;
+        } else {
+            const T g = a.g, h_dry = a.h_dry, dt = T(dt_d);
+            const V4<T> gA = a.geoA[i], gB = a.geoB[i];
+            const int4 tp = a.topo[i];
+            const T hi = own.x, zi = own.w;
+            T ui = T(0), vi = T(0);
+            if (hi > h_dry) { const T r = A::rcp_(hi); ui = own.y * r; vi = own.z * r; }
+            // issue the three neighbour gathers before any arithmetic
+            V4<T> nb[3];
+            const int code[3] = {tp.x, tp.y, tp.z};
+#pragma unroll
+            for (int j = 0; j < 3; ++j) nb[j] = code[j] >= 0 ? a.s_in[code[j] & kNbrMask] : own;
+            T f0 = T(0), f1 = T(0), f2 = T(0), sx = T(0), sy = T(0);
+#pragma unroll 1
+            for (int j = 0; j < 3; ++j) {
+                const int c = j == 0 ? code[0] : (j == 1 ? code[1] : code[2]);
+                const V4<T> o = j == 0 ? nb[0] : (j == 1 ? nb[1] : nb[2]);
+                const T lx = j == 0 ? gA.x : (j == 1 ? gA.z : gB.x);
+                const T ly = j == 0 ? gA.y : (j == 1 ? gA.w : gB.y);
+                const T l2 = lx * lx + ly * ly;
+                const T rl = A::rsqrt_(l2);
+                const T len = l2 * rl;
+                const T n1 = lx * rl, n2 = ly * rl;     // this cell's outward unit normal
+                T F0, F1, F2;
+                if (c >= 0) {
+                    const bool flip = (c & kFlipBit) != 0;
+                    const T hk = o.x, zk = o.w;
+                    T uk = T(0), vk = T(0);
+                    if (hk > h_dry) { const T r = A::rcp_(hk); uk = o.y * r; vk = o.z * r; }
+                    // hydrostatic reconstruction (Eq 28): z* = max(z_i, z_k)
+                    const T zs = tmax(zi, zk);
+                    const T hsi = tmax(T(0), hi + zi - zs);
+                    const T hsk = tmax(T(0), hk + zk - zs);
+                    // canonical orientation: left = lower caller index
+                    const T hL = flip ? hsk : hsi, hR = flip ? hsi : hsk;
+                    const T uL = flip ? uk : ui, vL = flip ? vk : vi;
+                    const T uR = flip ? ui : uk, vR = flip ? vi : vk;
+                    const T c1 = flip ? -n1 : n1, c2 = flip ? -n2 : n2;
+                    // rotate into the edge frame (Eq 12)
+                    const T unL = uL * c1 + vL * c2, utL = vL * c1 - uL * c2;
+                    const T unR = uR * c1 + vR * c2, utR = vR * c1 - uR * c2;
+                    T G1, G2, G3;
+                    riemann_hllc<T>(hL, unL, utL, hR, unR, utR, g, h_dry, G1, G2, G3);
+                    // back to (x, y) (Eq 12 inverse), as the flux leaving this cell
+                    const T s = flip ? T(-1) : T(1);
+                    F0 = s * G1;
+                    F1 = s * (G2 * c1 - G3 * c2);
+                    F2 = s * (G2 * c2 + G3 * c1);
+                    // bed source of this edge (Eq 30 with the factor 1/2)
+                    const T src = T(0.5) * g * (hsi * hsi - hi * hi);
+                    sx += src * lx;
+                    sy += src * ly;
+                } else {
+                    const int grp = -1 - c;
+                    const int kind = a.bc.kind[grp];
+                    const T un = ui * n1 + vi * n2, ut = vi * n1 - ui * n2;
+                    T G1, G2, G3;
+                    if (kind == kBcWall) {
+                        G1 = T(0); G2 = T(0.5) * g * hi * hi; G3 = T(0);
+                    } else if (kind == kBcInflow) {
+                        const T q = T(a.bc.value[grp]);
+                        G1 = -q;
+                        G2 = T(0.5) * g * hi * hi + (hi > h_dry ? A::div_(q * q, hi) : T(0));
+                        G3 = T(0);
+                    } else {
+                        T hg = hi;
+                        if (kind == kBcStage) hg = tmax(T(0), T(a.bc.value[grp]) - zi);
+                        riemann_hllc<T>(hi, un, ut, hg, un, ut, g, h_dry, G1, G2, G3);
+                    }
+                    F0 = G1;
+                    F1 = G2 * n1 - G3 * n2;
+                    F2 = G2 * n2 + G3 * n1;
+                }
+                f0 += len * F0;
+                f1 += len * F1;
+                f2 += len * F2;
+            }
+            const T ia = gB.z;
+            const T Rh = -f0 * ia;
+            const T Rx = (sx - f1) * ia;
+            const T Ry = (sy - f2) * ia;
+            // semi-implicit friction (Eq 33-37): [I - dt/2 J_f] dU = dt (R + S_f)
+            const T dh = dt * Rh;
+            T dqx = dt * Rx, dqy = dt * Ry;
+            const T gm2 = a.gm2[i];
+            const T qx = own.y, qy = own.z;
+            if (hi > h_dry && gm2 > T(0)) {
+                const T qq = qx * qx + qy * qy;
+                if (qq > T(0)) {
+                    const T qn = A::sqrt_(qq);
+                    const T cf = gm2 * A::pow_m73(hi);             // c = g m^2 h^(-7/3)
+                    const T al = T(0.5) * dt * cf;                  // alpha = dt c / 2
+                    // rhs: dt (R_q + S_f) + dt/2 J_qh dh, with S_f = -c|q|q and
+                    // J_qh = (7/3) c |q| q / h
+                    const T k = dt * cf * qn * (T(7.0 / 6.0) * dh * A::rcp_(hi) - T(1));
+                    const T bx = dqx + k * qx, by = dqy + k * qy;
+                    // (1 + a|q|) I + a q q^T/|q| has eigenvalue 1 + 2a|q| along q
+                    // and 1 + a|q| across it
+                    const T d1 = T(1) + al * qn, d2 = d1 + al * qn;
+                    const T proj = (bx * qx + by * qy) * al * A::rcp_(qn * d2);
+                    const T rd1 = A::rcp_(d1);
+                    dqx = (bx - proj * qx) * rd1;
+                    dqy = (by - proj * qy) * rd1;
+                }
+            }
+            V4<T> out;
+            out.x = hi + dh;
+            out.y = qx + dqx;
+            out.z = qy + dqy;
+            out.w = zi;
+            if (out.x < T(0)) {
+                out.x = T(0); out.y = T(0); out.z = T(0);
+                atomicAdd(a.n_clamped, 1ULL);
+            } else if (out.x <= h_dry) {
+                out.y = T(0); out.z = T(0);
+            }
+            const T big = T(3.0e38);
+            if (!(out.x < big) || !(fabs(out.y) < big) || !(fabs(out.z) < big))
+                atomicOr(a.status, kStatusNonFinite);
+            a.s_out[i] = out;
+            // next CFL candidate (Eq 15), R_i / (sqrt(g h) + |u|) on the new state
+            if (out.x > h_dry) {
+                const T r = A::rcp_(out.x);
+                const T u = out.y * r, v = out.z * r;
+                const T den = A::sqrt_(g * out.x) + A::sqrt_(u * u + v * v);
+                cand = (double)A::div_(gB.w, den);
+            }
+        }
+    }
+    block_min_publish<BLOCK>(cand, a.dt_write);
+}
+
+// ---- CFL min of a given state (used after swe_set_state) --------------------------
+template <typename T, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) dt_kernel(const V4<T>* __restrict__ s, const V4<T>* __restrict__ geoB,
+                                                   long long n, T g, T h_dry, unsigned long long* dt_write) {
+    using A = Ar<T>;
+    const long long i = (long long)blockIdx.x * BLOCK + threadIdx.x;
+    double cand = __longlong_as_double((long long)kInfBits);
+    if (i < n) {
+        const V4<T> c = s[i];
+        if (c.x > h_dry) {
+            const T r = A::rcp_(c.x);
+            const T u = c.y * r, v = c.z * r;
+            cand = (double)A::div_(geoB[i].w, A::sqrt_(g * c.x) + A::sqrt_(u * u + v * v));
+        }
+    }
+    block_min_publish<BLOCK>(cand, dt_write);
+}
+
+// ---- layout conversion between caller arrays and the packed internal state --------
+// pack: s[new] = (h[perm[new]], hu[..], hv[..], z[new])
+template <typename T>
+__global__ void pack_state_kernel(const T* __restrict__ h, const T* __restrict__ hu, const T* __restrict__ hv,
+                                  const long long* __restrict__ perm, const T* __restrict__ z,
+                                  V4<T>* __restrict__ s, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const long long o = perm[i];
+        V4<T> v;
+        v.x = h[o]; v.y = hu[o]; v.z = hv[o]; v.w = z[i];
+        s[i] = v;
+    }
+}
+
+template <typename T>
+__global__ void unpack_state_kernel(const V4<T>* __restrict__ s, const long long* __restrict__ perm,
+                                    T* __restrict__ h, T* __restrict__ hu, T* __restrict__ hv, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const long long o = perm[i];
+        const V4<T> v = s[i];
+        h[o] = v.x; hu[o] = v.y; hv[o] = v.z;
+    }
+}
+
+// ---- batched Riemann flux (parity entry point) --------------------------------------
+template <typename T>
+__global__ void riemann_batch_kernel(long long n, const T* __restrict__ hL, const T* __restrict__ unL,
+                                     const T* __restrict__ utL, const T* __restrict__ hR,
+                                     const T* __restrict__ unR, const T* __restrict__ utR, T g, T h_dry,
+                                     T* __restrict__ G1, T* __restrict__ G2, T* __restrict__ G3, T* __restrict__ S) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        T a, b, c, sp[3];
+        riemann_hllc<T>(hL[i], unL[i], utL[i], hR[i], unR[i], utR[i], g, h_dry, a, b, c, sp);
+        G1[i] = a; G2[i] = b; G3[i] = c;
+        if (S) { S[3 * i] = sp[0]; S[3 * i + 1] = sp[1]; S[3 * i + 2] = sp[2]; }
+    }
+}
+
+// ---- host-side launchers, one set per precision ------------------------------------
+template <typename T>
+struct Launch {
+    static cudaError_t step(const StepArgs<T>& a, int block, cudaStream_t st);
+    static cudaError_t dt(const V4<T>* s, const V4<T>* geoB, long long n, T g, T h_dry,
+                          unsigned long long* dt_write, cudaStream_t st);
+    static cudaError_t pack(const T* h, const T* hu, const T* hv, const long long* perm, const T* z,
+                            V4<T>* s, long long n, cudaStream_t st);
+    static cudaError_t unpack(const V4<T>* s, const long long* perm, T* h, T* hu, T* hv, long long n,
+                              cudaStream_t st);
+    static cudaError_t riemann(long long n, const T* hL, const T* unL, const T* utL, const T* hR,
+                               const T* unR, const T* utR, T g, T h_dry, T* G1, T* G2, T* G3, T* S,
+                               cudaStream_t st);
+};
+
+}  // namespace swe

@@ -1,0 +1,123 @@
+"""CPU-side checks of the CUDA library: it loads, exports every symbol the
+header declares, and its host preprocessing (Section 3.1 geometry,
+neighbours across shared edges, canonical edge orientation, locality order)
+agrees with the oracle's independent mesh build.  No GPU is used."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2010_14416_gb300 import build as libbuild
+from paper_2010_14416_gb300 import capi
+from paper_2010_14416_gb300 import meshgen as mg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    libbuild.build()
+    return capi.load()
+
+
+def _declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            names |= set(re.findall(r"SWE_API\s+[\w\s\*]*?\b(swe_\w+)\s*\(", src))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    declared = _declared_symbols()
+    assert len(declared) >= 14
+    lib = capi.load()
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert declared == set(capi.EXPORTS)
+
+
+def test_no_gpu_needed_for_config_default():
+    cfg = capi.config_default()
+    assert cfg.precision == capi.SWE_FP64 and cfg.g == 9.81 and cfg.h_dry == 1e-6
+    assert cfg.reorder == capi.SWE_REORDER_HILBERT
+
+
+@pytest.mark.parametrize("reorder", [capi.SWE_REORDER_NONE, capi.SWE_REORDER_RCM,
+                                     capi.SWE_REORDER_HILBERT])
+def test_preprocess_agrees_with_oracle_geometry(reorder):
+    mi = mg.river(60, 12, seed=4, shuffle=True)
+    P = capi.mesh_preprocess(mi.nodes, mi.tris, reorder)
+    perm = P["perm"]
+    n = mi.n_cells
+    assert np.array_equal(np.sort(perm), np.arange(n))          # bijection
+    inv = np.empty(n, np.int64)
+    inv[perm] = np.arange(n)
+    O = oracle.Mesh(mi.nodes, mi.tris, mi.z, mi.manning).geometry()
+    # per cell: area, inscribed radius
+    assert np.allclose(1.0 / P["inv_area"], O["area"][perm], rtol=1e-13)
+    assert np.allclose(P["rin"], O["rin"][perm], rtol=1e-13)
+    # per edge: the set of (neighbour, L n) pairs matches the oracle's
+    code = P["code"]
+    for c in range(0, n, 7):
+        o = perm[c]
+        lib_edges = []
+        for j in range(3):
+            k = code[c, j]
+            nb = -1 if k < 0 else int(perm[k & 0x3FFFFFFF])
+            lib_edges.append((nb, round(P["ln"][c, j, 0], 9), round(P["ln"][c, j, 1], 9)))
+            if k >= 0:
+                # canonical orientation: flip bit set iff the neighbour has the lower caller index
+                assert bool(k & 0x40000000) == (nb < o)
+        orc_edges = [(int(O["nbr"][o, j]) if O["nbr"][o, j] >= 0 else -1,
+                      round(O["len"][o, j] * O["nx"][o, j], 9), round(O["len"][o, j] * O["ny"][o, j], 9))
+                     for j in range(3)]
+        assert sorted(lib_edges) == sorted(orc_edges)
+
+
+def test_shared_edges_have_bitwise_opposite_normals():
+    mi = mg.river(40, 8, seed=2, shuffle=True)
+    P = capi.mesh_preprocess(mi.nodes, mi.tris, capi.SWE_REORDER_HILBERT)
+    code, ln = P["code"], P["ln"]
+    n = mi.n_cells
+    for c in range(n):
+        for j in range(3):
+            k = code[c, j]
+            if k < 0:
+                continue
+            k &= 0x3FFFFFFF
+            jj = [q for q in range(3) if code[k, q] >= 0 and (code[k, q] & 0x3FFFFFFF) == c]
+            assert len(jj) == 1
+            assert ln[k, jj[0], 0] == -ln[c, j, 0] and ln[k, jj[0], 1] == -ln[c, j, 1]
+
+
+def test_locality_orders_shrink_neighbour_distance():
+    mi = mg.river(200, 40, seed=1, shuffle=True)
+    spans = {}
+    for r in (capi.SWE_REORDER_NONE, capi.SWE_REORDER_RCM, capi.SWE_REORDER_HILBERT):
+        code = capi.mesh_preprocess(mi.nodes, mi.tris, r)["code"]
+        c = np.repeat(np.arange(mi.n_cells), 3).reshape(-1, 3)
+        valid = code >= 0
+        d = np.abs((code & 0x3FFFFFFF) - c)[valid]
+        spans[r] = np.median(d)
+    assert spans[capi.SWE_REORDER_HILBERT] < spans[capi.SWE_REORDER_NONE] / 50
+    assert spans[capi.SWE_REORDER_RCM] < spans[capi.SWE_REORDER_NONE] / 50
+
+
+def test_malformed_meshes_rejected_by_host_preprocessing():
+    nodes = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0], [1.0, 1.0], [0.5, -1.0]])
+    with pytest.raises(capi.SWEError) as e:
+        capi.mesh_preprocess(nodes, np.array([[0, 1, 2], [0, 1, 3], [0, 4, 1]]))
+    assert e.value.code == capi.SWE_EMESH
+    with pytest.raises(capi.SWEError) as e:
+        capi.mesh_preprocess(np.array([[0.0, 0.0], [1.0, 0.0], [2.0, 0.0]]), np.array([[0, 1, 2]]))
+    assert e.value.code == capi.SWE_EMESH
+    with pytest.raises(capi.SWEError) as e:
+        capi.mesh_preprocess(nodes, np.array([[0, 1, 9]]))
+    assert e.value.code == capi.SWE_EMESH
+    with pytest.raises(capi.SWEError) as e:
+        capi.mesh_preprocess(nodes, np.zeros((0, 3), np.int32))
+    assert e.value.code == capi.SWE_EINVAL

@@ -1,0 +1,298 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances: FP64 GPU vs oracle <= 1e-10 max relative error per field
+(max_i |f_i - f_i^ref| / max_i |f_i^ref|) after 1000 steps; FP32 GPU vs FP64
+<= 1e-4 with the same norm.  Integer results (clamp counts, status codes)
+are exact."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import rel_err
+from paper_2010_14416_gb300 import build as libbuild
+from paper_2010_14416_gb300 import capi
+from paper_2010_14416_gb300 import meshgen as mg
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+FP32_TOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    libbuild.build()
+    return capi.load()
+
+
+def _gpu_mesh(mi, precision=capi.SWE_FP64, **kw):
+    m = capi.Mesh(mi.nodes, mi.tris, mi.z, mi.manning, precision=precision, **kw)
+    for pairs, kind, value in mi.bcs:
+        m.set_bc(pairs, kind, value)
+    return m
+
+
+def _orc_mesh(mi):
+    M = oracle.Mesh(mi.nodes, mi.tris, mi.z, mi.manning)
+    for pairs, kind, value in mi.bcs:
+        M.set_bc(pairs, kind, value)
+    return M
+
+
+def _gpu_run(mi, nsteps, precision=capi.SWE_FP64, cfl=0.9, state=None, **kw):
+    m = _gpu_mesh(mi, precision, **kw)
+    dt = np.float32 if precision == capi.SWE_FP32 else np.float64
+    h, hu, hv = state if state is not None else (mi.h, mi.hu, mi.hv)
+    m.set_state(h.astype(dt), hu.astype(dt), hv.astype(dt))
+    t = m.step(nsteps, cfl)
+    out = m.get_state()
+    info = m.info()
+    m.close()
+    return [o.astype(np.float64) for o in out], t, info
+
+
+# ---------------------------------------------------------------------------
+# Riemann flux (Eq 17-26) on random normal-frame states
+# ---------------------------------------------------------------------------
+
+def _random_states(n, seed):
+    rng = np.random.default_rng(seed)
+    hL = rng.uniform(0, 10, n)
+    hR = rng.uniform(0, 10, n)
+    hL[rng.random(n) < 0.1] = 0.0
+    hR[rng.random(n) < 0.1] = 0.0
+    hL[rng.random(n) < 0.05] = 5e-7       # below h_dry
+    unL, unR = rng.uniform(-15, 15, n), rng.uniform(-15, 15, n)
+    utL, utR = rng.uniform(-3, 3, n), rng.uniform(-3, 3, n)
+    same = rng.random(n) < 0.05          # consistency cases
+    hR[same], unR[same], utR[same] = hL[same], unL[same], utL[same]
+    hL[0], hR[0], unL[0], unR[0] = 10.0, 1.0, 0.0, 0.0  # the dam-break state
+    return hL, unL, utL, hR, unR, utR
+
+
+@pytest.mark.parametrize("precision", [capi.SWE_FP64, capi.SWE_FP32])
+def test_riemann_flux_matches_oracle(precision):
+    n = 4000
+    st = _random_states(n, 7)
+    tdt = torch.float64 if precision == capi.SWE_FP64 else torch.float32
+    dev = [torch.tensor(a, dtype=tdt, device="cuda") for a in st]
+    G = [torch.empty(n, dtype=tdt, device="cuda") for _ in range(3)]
+    S = torch.empty((n, 3), dtype=tdt, device="cuda")
+    capi.riemann_flux(precision, *dev, *G, S)
+    torch.cuda.synchronize()
+    got = np.stack([g.double().cpu().numpy() for g in G], axis=1)
+    ref = np.zeros((n, 3))
+    for i in range(n):
+        ref[i], _ = oracle.hllc(*(float(a[i]) for a in st))
+    scale = np.maximum(np.abs(ref).max(axis=1), 1.0)
+    err = (np.abs(got - ref).max(axis=1) / scale)
+    tol = 1e-13 if precision == capi.SWE_FP64 else 2e-5
+    # ties at S* = 0 or at the branch points may take either side in FP32
+    bad = err > tol
+    assert bad.sum() <= (0 if precision == capi.SWE_FP64 else n // 500), (err.max(), np.where(bad))
+    # the dam-break state of Section 6.3: h* = 3.9529... gives S_L = -sqrt(g h_L)
+    s0 = S[0].double().cpu().numpy()
+    assert s0[0] == pytest.approx(-math.sqrt(9.81 * 10.0), rel=1e-12 if precision == 0 else 1e-6)
+
+
+# ---------------------------------------------------------------------------
+# Whole-step parity on small meshes (several tiles plus a ragged tail)
+# ---------------------------------------------------------------------------
+
+def test_dam_break_4k_fp64_1000_steps_all_orderings_bitwise_equal():
+    mi = mg.dam_break_4k()
+    M = _orc_mesh(mi)
+    oh, ohu, ohv, ot, oc = M.run(mi.h, mi.hu, mi.hv, 1000, 0.9)
+    results = {}
+    for r in (capi.SWE_REORDER_NONE, capi.SWE_REORDER_RCM, capi.SWE_REORDER_HILBERT):
+        (gh, ghu, ghv), t, info = _gpu_run(mi, 1000, reorder=r)
+        assert info["n_clamped"] == oc == 0
+        assert t == pytest.approx(ot, rel=1e-12)
+        assert rel_err(gh, oh) <= FP64_TOL
+        assert rel_err(ghu, ohu) <= FP64_TOL
+        assert rel_err(ghv, ohv) <= FP64_TOL
+        results[r] = (gh, ghu, ghv, t)
+    a = results[capi.SWE_REORDER_NONE]
+    for r in (capi.SWE_REORDER_RCM, capi.SWE_REORDER_HILBERT):
+        b = results[r]
+        assert all(np.array_equal(x, y) for x, y in zip(a[:3], b[:3])), "ordering changed the result"
+        assert a[3] == b[3]
+
+
+def test_river_with_all_boundary_kinds_fp64():
+    # partially dry reach: wet/dry fronts, inflow, stage, walls, friction,
+    # bumps, shuffled numbering
+    mi = mg.river(160, 32, seed=5, shuffle=True)
+    M = _orc_mesh(mi)
+    oh, ohu, ohv, ot, oc = M.run(mi.h, mi.hu, mi.hv, 1000, 0.9)
+    (gh, ghu, ghv), t, info = _gpu_run(mi, 1000)
+    assert t == pytest.approx(ot, rel=1e-12)
+    assert info["n_clamped"] == oc
+    for a, b in ((gh, oh), (ghu, ohu), (ghv, ohv)):
+        assert rel_err(a, b) <= FP64_TOL
+
+
+def test_transmissive_and_friction_fp64():
+    mi = mg.canal(50, 8, 50.0, 8.0, 0.2, 6, side_bc=mg.BC_TRANSMISSIVE, hL=3.0, hR=1.0,
+                  x_dam=25.0, manning=0.05)
+    rng = np.random.default_rng(3)
+    h0 = mi.h.copy()
+    hu0 = rng.uniform(-1, 1, mi.n_cells) * h0
+    hv0 = rng.uniform(-1, 1, mi.n_cells) * h0
+    M = _orc_mesh(mi)
+    oh, ohu, ohv, ot, oc = M.run(h0, hu0, hv0, 1000, 0.9)
+    (gh, ghu, ghv), t, info = _gpu_run(mi, 1000, state=(h0, hu0, hv0))
+    assert t == pytest.approx(ot, rel=1e-12)
+    for a, b in ((gh, oh), (ghu, ohu), (ghv, ohv)):
+        assert rel_err(a, b) <= FP64_TOL
+
+
+@pytest.mark.parametrize("maker", [mg.dam_break_4k, lambda: mg.river(160, 32, seed=5)])
+def test_fp32_against_fp64(maker):
+    mi = maker()
+    M = _orc_mesh(mi)
+    oh, ohu, ohv, ot, oc = M.run(mi.h, mi.hu, mi.hv, 1000, 0.9)
+    (gh, ghu, ghv), t, info = _gpu_run(mi, 1000, precision=capi.SWE_FP32)
+    assert t == pytest.approx(ot, rel=1e-4)
+    for a, b in ((gh, oh), (ghu, ohu), (ghv, ohv)):
+        assert rel_err(a, b) <= FP32_TOL
+
+
+def test_mass_conserved_and_lake_at_rest_on_gpu():
+    mi = mg.dam_break_4k()
+    area = oracle.Mesh(mi.nodes, mi.tris, mi.z, mi.manning).geometry()["area"]
+    (gh, _, _), t, _ = _gpu_run(mi, 1000)
+    m0 = (area * mi.h).sum()
+    assert abs((area * gh).sum() - m0) / m0 < 1e-13
+    lake = mg.river(120, 24, seed=2)
+    eta0 = lake.meta["eta0"]
+    lake.bcs = [(lake.bcs[1][0], mg.BC_STAGE, eta0)]
+    h0 = np.maximum(eta0 - lake.z, 0.0)
+    z0 = np.zeros_like(h0)
+    (gh, ghu, ghv), t, _ = _gpu_run(lake, 1000, state=(h0, z0, z0))
+    wet = h0 > 0
+    assert np.abs(gh + lake.z - eta0)[wet].max() < 1e-12
+    assert np.all(gh[~wet] == 0.0)
+    assert np.abs(ghu).max() < 1e-10 and np.abs(ghv).max() < 1e-10
+
+
+def test_graphs_block_sizes_and_device_io_are_bitwise_neutral():
+    mi = mg.river(100, 20, seed=8)
+    ref, tref, _ = _gpu_run(mi, 301, graph_steps=-1, block_size=128)
+    for kw in (dict(graph_steps=12, block_size=256), dict(graph_steps=48, block_size=512)):
+        got, t, _ = _gpu_run(mi, 301, **kw)
+        assert t == tref
+        assert all(np.array_equal(a, b) for a, b in zip(ref, got))
+    # device tensors in and out, split step calls
+    m = _gpu_mesh(mi)
+    dev = [torch.tensor(a, device="cuda") for a in (mi.h, mi.hu, mi.hv)]
+    m.set_state(*dev)
+    m.step(100, sync=False)
+    m.step(0)
+    m.step(201, sync=False)
+    out = [torch.empty(mi.n_cells, dtype=torch.float64, device="cuda") for _ in range(3)]
+    m.get_state(out)
+    torch.cuda.synchronize()
+    assert m.info()["t"] == tref
+    assert all(np.array_equal(a, b.cpu().numpy()) for a, b in zip(ref, out))
+    m.close()
+
+
+def test_edge_cases():
+    # one triangle with walls: stays at rest exactly
+    nodes = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]])
+    m = capi.Mesh(nodes, [[0, 1, 2]], [0.0], [0.0])
+    m.set_state(np.array([1.0]), np.array([0.0]), np.array([0.0]))
+    m.step(10)
+    h, hu, hv = m.get_state()
+    assert h[0] == 1.0 and abs(hu[0]) < 1e-14 and abs(hv[0]) < 1e-14
+    m.close()
+    # all dry: no CFL step
+    mi = mg.dam_break_4k()
+    m = _gpu_mesh(mi)
+    zero = np.zeros(mi.n_cells)
+    m.set_state(zero, zero, zero)
+    with pytest.raises(capi.SWEError) as e:
+        m.step(3)
+    assert e.value.code == capi.SWE_EDRY
+    m.close()
+    # bad arguments are rejected on the host
+    m = _gpu_mesh(mi)
+    with pytest.raises(capi.SWEError) as e:
+        m.step(1)
+    assert e.value.code == capi.SWE_EINVAL        # no state yet
+    with pytest.raises(capi.SWEError) as e:
+        m.set_bc(np.array([[0, 5000]]), capi.SWE_BC_WALL)
+    assert e.value.code == capi.SWE_EINVAL
+    m.set_state(mi.h, mi.hu, mi.hv)
+    with pytest.raises(capi.SWEError):
+        m.step(1, cfl=-1.0)
+    assert m.step(0) == 0.0
+    m.close()
+
+
+# ---------------------------------------------------------------------------
+# Full-size workloads, in the launch configuration the bench times
+# ---------------------------------------------------------------------------
+
+def _sampled_one_step(mi, m, precision, n_sample=20000, seed=0):
+    """State U^K from the GPU, then one more GPU step; the oracle recomputes
+    that step at sampled cells from the same U^K (FP64)."""
+    h, hu, hv = [a.astype(np.float64) for a in m.get_state()]
+    t0 = m.info()["t"]
+    t1 = m.step(1)
+    dt = t1 - t0
+    g1 = [a.astype(np.float64) for a in m.get_state()]
+    M = _orc_mesh(mi)
+    cells = np.random.default_rng(seed).choice(mi.n_cells, size=min(n_sample, mi.n_cells),
+                                                replace=False)
+    o = M.step_cells(h, hu, hv, dt, cells)
+    odt = M.dt(h, hu, hv, 0.9)
+    return g1, o, cells, dt, odt
+
+
+def test_full_size_dry_canal_1m_fp64_and_fp32():
+    mi = mg.dam_break_dry_1m()
+    m = _gpu_mesh(mi)
+    m.set_state(mi.h, mi.hu, mi.hv)
+    t = m.step(2000)
+    info = m.info()
+    assert info["status"] == 0
+    g1, o, cells, dt, odt = _sampled_one_step(mi, m, capi.SWE_FP64)
+    assert dt == pytest.approx(odt, rel=1e-13)
+    for k in range(3):
+        assert rel_err(g1[k][cells], o[k]) <= 1e-12
+    # Ritter: the wet front never passes 2 c0 t beyond the dam
+    h64 = g1[0]
+    cx = mi.centroids()[:, 0]
+    front = cx[h64 > 1e-3].max()
+    assert front <= 100.0 + 2 * math.sqrt(9.81 * 10.0) * t + 0.2
+    assert front > 100.0 + 0.5 * 2 * math.sqrt(9.81 * 10.0) * t
+    m.close()
+    # FP32 against FP64, same 2000 steps
+    (f32, _, _), t32, _ = _gpu_run(mi, 2000, precision=capi.SWE_FP32)
+    (f64, _, _), t64, _ = _gpu_run(mi, 2000)
+    assert t32 == pytest.approx(t64, rel=1e-4)
+    assert rel_err(f32, f64) <= FP32_TOL
+
+
+def test_full_size_river_13m_fp32_sampled_and_against_fp64():
+    mi = mg.river_13m()
+    m = _gpu_mesh(mi, precision=capi.SWE_FP32)
+    m.set_state(mi.h.astype(np.float32), mi.hu.astype(np.float32), mi.hv.astype(np.float32))
+    m.step(1000)
+    assert m.info()["status"] == 0
+    g1, o, cells, dt, odt = _sampled_one_step(mi, m, capi.SWE_FP32)
+    assert dt == pytest.approx(odt, rel=1e-5)
+    for k in range(3):
+        assert rel_err(g1[k][cells], o[k]) <= 1e-5
+    s32 = [a.astype(np.float64) for a in m.get_state()]
+    m.close()
+    (s64, t64, info64) = _gpu_run(mi, 1001)
+    assert info64["status"] == 0
+    for a, b in zip(s32, s64):
+        assert rel_err(a, b) <= FP32_TOL
