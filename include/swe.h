@@ -203,6 +203,33 @@ SWE_API int swe_mesh_preprocess(const double* nodes, int64_t n_nodes, const int3
                                 int reorder, int64_t* perm, int32_t* code, double* ln, double* inv_area,
                                 double* rin);
 
+/*
+ * Allocation-free CFL time step.  The paper has no counterpart: this entry
+ * point exists for callers that cannot let the library call cudaMalloc (code
+ * that owns all device memory through its own arena, or that runs while a
+ * CUDA graph is being captured, where allocation is not allowed).
+ *
+ * Writes to *dt_out (a device double) cfl * min_i R_i / (sqrt(g h_i) + |u_i|)
+ * over the cells with h_i > h_dry (Eq 15), or +inf when every cell is dry --
+ * the same value swe_set_state computes for its first step.  It allocates
+ * nothing and calls no allocating routine.
+ *   precision  SWE_FP64 (double arrays) or SWE_FP32 (float arrays)
+ *   n          number of cells, 1 <= n <= 16,777,216 (larger n: SWE_EINVAL)
+ *   h, hu, hv  [n] device arrays of the state, any cell order
+ *   rin        [n] device array of inscribed radii 2|Omega_i|/perimeter, same order
+ *   dt_out     one device double; written in stream order on `cuda_stream`
+ * Runs on the calling thread's current device.  Its scratch is a 512 KiB
+ * static device array that every GPU loading the library holds until the
+ * process exits; the first call on each device looks up that array's
+ * address, so make the first call on a device before any stream capture.
+ * All calls share the array: calls that overlap on the GPU (for instance on
+ * two streams) race and may return wrong values.
+ * Errors: SWE_EINVAL, SWE_ECUDA.
+ */
+SWE_API int swe_cfl_dt_noalloc(int precision, int64_t n, const void* h, const void* hu, const void* hv,
+                               const void* rin, double g, double h_dry, double cfl, double* dt_out,
+                               void* cuda_stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 SWE_API const char* swe_last_error(void);
 

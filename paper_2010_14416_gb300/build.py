@@ -23,6 +23,7 @@ UNITS = [
     ("swe_step_f64.cu", []),
     ("swe_capi.cu", []),
     ("swe_mesh.cu", []),
+    ("swe_noalloc.cu", ["--use_fast_math"]),
 ]
 
 

@@ -29,7 +29,7 @@ ERROR_NAMES = {1: "SWE_EINVAL", 2: "SWE_EMESH", 3: "SWE_ENOMEM", 4: "SWE_ECUDA",
 EXPORTS = ["swe_config_default", "swe_mesh_create", "swe_mesh_destroy", "swe_set_bc",
            "swe_set_stream", "swe_set_state", "swe_step", "swe_get_state", "swe_synchronize",
            "swe_get_info", "swe_get_permutation", "swe_mesh_preprocess", "swe_riemann_flux",
-           "swe_last_error"]
+           "swe_cfl_dt_noalloc", "swe_last_error"]
 
 
 class swe_config(C.Structure):
@@ -80,6 +80,8 @@ def load():
     lib.swe_riemann_flux.argtypes = [C.c_int, C.c_int64] + [vp] * 6 + [C.c_double, C.c_double] + \
         [vp] * 4 + [vp]
     lib.swe_mesh_preprocess.argtypes = [vp, C.c_int64, vp, C.c_int64, C.c_int, vp, vp, vp, vp, vp]
+    lib.swe_cfl_dt_noalloc.argtypes = [C.c_int, C.c_int64, vp, vp, vp, vp, C.c_double, C.c_double,
+                                       C.c_double, vp, vp]
     lib.swe_last_error.argtypes = []
     lib.swe_last_error.restype = C.c_char_p
     for name in EXPORTS:
@@ -240,3 +242,13 @@ def riemann_flux(precision, hL, unL, utL, hR, unR, utR, G1, G2, G3, S=None, g=9.
         import torch
         stream = torch.cuda.current_stream().cuda_stream
     check(load().swe_riemann_flux(precision, n, *ptrs, g, h_dry, *outs, sp, C.c_void_p(stream)))
+
+
+def cfl_dt_noalloc(precision, h, hu, hv, rin, dt_out, cfl=0.9, g=9.81, h_dry=1e-6, stream=None):
+    """Allocation-free CFL step of a state held in device tensors; writes
+    cfl * min R/(c+|u|) into the one-element device tensor dt_out."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    check(load().swe_cfl_dt_noalloc(precision, h.numel(), h.data_ptr(), hu.data_ptr(), hv.data_ptr(),
+                                    rin.data_ptr(), g, h_dry, cfl, dt_out.data_ptr(), C.c_void_p(stream)))
