@@ -234,13 +234,16 @@ def run_gpu(args, name):
     if dist:
         dist.barrier()
     torch.cuda.synchronize(dev)
+    active0 = m.info()["n_active"]
     ev0.record(stream)
     m.step(args.steps, 0.9, sync=False)
     ev1.record(stream)
     torch.cuda.synchronize(dev)
     ms = ev0.elapsed_time(ev1)
     clk = clocks.stop() if rank == 0 else None
-    t_sim = m.info()["t"]
+    info = m.info()
+    t_sim = info["t"]
+    active_frac = (info["n_active"] - active0) / float(n * args.steps)
     m.synchronize()
     if dist:
         import torch.distributed as d
@@ -277,6 +280,13 @@ def run_gpu(args, name):
     ab = ALG_BYTES[wl["precision"]]
     kernel_ms = ms / args.steps
     achieved = ab * n / (kernel_ms * 1e-3) / 1e9
+    # bytes this layout must move per launch: an active cell reads its state,
+    # topology and geometry records and writes its state; a quiet cell (dry,
+    # all neighbours dry, no inflow/stage edge) needs no geometry
+    rec = 16 if wl["precision"] == "f32" else 32
+    layout_bytes = n * (active_frac * (4 * rec + 16 + (0 if wl["precision"] == "f32" else 8)) +
+                        (1 - active_frac) * (2 * rec + 16))
+    layout_achieved = layout_bytes / (kernel_ms * 1e-3) / 1e9
     traffic = None
     tpath = os.path.join(ROOT, "profiles", f"traffic_{name}.json")
     if os.path.exists(tpath):
@@ -304,7 +314,12 @@ def run_gpu(args, name):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
-                     "alg_bytes_per_cell": ab},
+                     "alg_bytes_per_cell": ab,
+                     "active_cell_fraction": active_frac,
+                     "layout_bytes_per_launch": layout_bytes,
+                     "layout_achieved": layout_achieved,
+                     "layout_frac": layout_achieved / peak,
+                     "traffic_frac": (traffic / (kernel_ms * 1e-3) / 1e9 / peak) if traffic else None},
         "e2e": {"value": ws * n * args.steps / e2e_s, "unit": "cell-updates/s",
                 "h2d_bytes_per_step": 3 * n * np.dtype(npdt).itemsize / args.steps,
                 "d2h_bytes_per_step": 3 * n * np.dtype(npdt).itemsize / args.steps,

@@ -79,6 +79,9 @@ typedef struct swe_config {
     int block_size;   /* threads per block of the step kernel; 0 = library default */
     int graph_steps;  /* steps captured per CUDA graph; 0 = default, < 0 = no graphs */
     int device;       /* CUDA device ordinal, default 0 */
+    int min_blocks;   /* resident blocks per SM the step kernel is compiled for; 0 = default.
+                         Compiled (block_size, min_blocks) pairs: (128|256|512, 1), (128, 8),
+                         (256, 4|5|6), (512, 2); others give SWE_EINVAL */
 } swe_config;
 
 /* Fills *cfg with the defaults listed above. */
@@ -164,6 +167,8 @@ typedef struct swe_info {
     int precision;
     int status;             /* device status word mapped to an SWE_* code */
     int64_t device_bytes;   /* device memory held by the mesh */
+    int64_t n_active;       /* cell updates since swe_set_state that ran the full flux path
+                               (the others were dry cells among dry neighbours: no flux) */
 } swe_info;
 
 /* Waits for the mesh stream and fills *info. */

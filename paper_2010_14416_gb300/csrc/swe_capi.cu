@@ -30,7 +30,7 @@ void set_error(const std::string& msg) { g_last_error = msg; }
 namespace {
 
 constexpr int kSmallWords = 8;
-constexpr int kSlotT = 3, kSlotStatus = 4, kSlotClamp = 5;
+constexpr int kSlotT = 3, kSlotStatus = 4, kSlotClamp = 5, kSlotActive = 6;
 constexpr int kDefaultGraphSteps = 48;
 
 struct DeviceGuard {
@@ -92,6 +92,7 @@ struct swe_mesh {
     int graph_len = 0;
     double graph_cfl = -1.0;
     int64_t device_bytes = 0;
+    unsigned grid = 0;                 // blocks of the step kernel (about one resident wave)
 };
 
 namespace {
@@ -114,13 +115,29 @@ void drop_graph(swe_mesh* m) {
     m->graph_cfl = -1.0;
 }
 
+// topo[c] = (neighbour codes, and for FP32 the bits of g m^2 in .w)
+std::vector<int4> make_topo(const swe_mesh* m) {
+    const HostMesh& H = m->hm;
+    const int64_t n = H.n_cells;
+    std::vector<int4> topo(n);
+    for (int64_t c = 0; c < n; ++c) {
+        int w = 0;
+        if (m->esz == 4) {
+            const float gm2 = (float)(m->cfg.g * H.m[c] * H.m[c]);
+            std::memcpy(&w, &gm2, sizeof w);
+        }
+        topo[c] = make_int4(H.code[3 * c], H.code[3 * c + 1], H.code[3 * c + 2], w);
+    }
+    return topo;
+}
+
 template <typename T>
 int upload_static(swe_mesh* m) {
     const HostMesh& H = m->hm;
     const int64_t n = H.n_cells;
     std::vector<V4<T>> A(n), B(n);
     std::vector<T> gm2(n), zt(n);
-    std::vector<int4> topo(n);
+    const std::vector<int4> topo = make_topo(m);
     for (int64_t c = 0; c < n; ++c) {
         A[c].x = (T)H.ln[6 * c + 0]; A[c].y = (T)H.ln[6 * c + 1];
         A[c].z = (T)H.ln[6 * c + 2]; A[c].w = (T)H.ln[6 * c + 3];
@@ -128,7 +145,6 @@ int upload_static(swe_mesh* m) {
         B[c].z = (T)H.inv_area[c]; B[c].w = (T)H.rin[c];
         gm2[c] = (T)(m->cfg.g * H.m[c] * H.m[c]);
         zt[c] = (T)H.z[c];
-        topo[c] = make_int4(H.code[3 * c], H.code[3 * c + 1], H.code[3 * c + 2], 0);
     }
     cudaError_t e;
     if ((e = cudaMemcpy(m->geoA, A.data(), n * sizeof(V4<T>), cudaMemcpyHostToDevice)) != cudaSuccess ||
@@ -143,11 +159,8 @@ int upload_static(swe_mesh* m) {
 
 int flush_topo(swe_mesh* m) {
     if (!m->topo_dirty) return SWE_OK;
-    const HostMesh& H = m->hm;
-    const int64_t n = H.n_cells;
-    std::vector<int4> topo(n);
-    for (int64_t c = 0; c < n; ++c)
-        topo[c] = make_int4(H.code[3 * c], H.code[3 * c + 1], H.code[3 * c + 2], 0);
+    const int64_t n = m->hm.n_cells;
+    const std::vector<int4> topo = make_topo(m);
     cudaError_t e = cudaMemcpyAsync(m->topo, topo.data(), n * sizeof(int4), cudaMemcpyHostToDevice, m->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
     if (e != cudaSuccess) return cuda_fail(e, "swe_set_bc: upload");
@@ -178,7 +191,9 @@ StepArgs<T> make_args(swe_mesh* m, int64_t step_index, double cfl) {
     a.t = (double*)(m->small + kSlotT);
     a.status = (unsigned*)(m->small + kSlotStatus);
     a.n_clamped = m->small + kSlotClamp;
+    a.n_active = m->small + kSlotActive;
     a.n = m->hm.n_cells;
+    a.grid = m->grid;
     a.cfl = cfl;
     a.g = (T)m->cfg.g;
     a.h_dry = (T)m->cfg.h_dry;
@@ -188,7 +203,7 @@ StepArgs<T> make_args(swe_mesh* m, int64_t step_index, double cfl) {
 
 template <typename T>
 cudaError_t launch_one(swe_mesh* m, int64_t step_index, double cfl, cudaStream_t st) {
-    return Launch<T>::step(make_args<T>(m, step_index, cfl), m->cfg.block_size, st);
+    return Launch<T>::step(make_args<T>(m, step_index, cfl), m->cfg.block_size, m->cfg.min_blocks, st);
 }
 
 template <typename T>
@@ -336,6 +351,7 @@ void swe_config_default(swe_config* cfg) {
     cfg->block_size = 0;
     cfg->graph_steps = 0;
     cfg->device = 0;
+    cfg->min_blocks = 0;
 }
 
 const char* swe_last_error(void) { return g_last_error.c_str(); }
@@ -367,6 +383,9 @@ int swe_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* tris, i
         set_error("swe_mesh_create: block_size must be 128, 256 or 512");
         return SWE_EINVAL;
     }
+    if (c.min_blocks == 0)
+        c.min_blocks = c.precision == SWE_FP32 ? Launch<float>::default_min_blocks(c.block_size)
+                                               : Launch<double>::default_min_blocks(c.block_size);
     if (c.graph_steps == 0) c.graph_steps = kDefaultGraphSteps;
     if (c.graph_steps > 0) c.graph_steps = std::max(6, (c.graph_steps / 6) * 6);
     swe_mesh* m = new (std::nothrow) swe_mesh();
@@ -400,6 +419,21 @@ int swe_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* tris, i
     }
     rc = c.precision == SWE_FP32 ? upload_static<float>(m) : upload_static<double>(m);
     if (rc) { swe_mesh_destroy(m); return rc; }
+    {
+        int per_sm = 0, sms = 0;
+        e = c.precision == SWE_FP32 ? Launch<float>::resident_blocks(c.block_size, c.min_blocks, &per_sm)
+                                    : Launch<double>::resident_blocks(c.block_size, c.min_blocks, &per_sm);
+        if (e == cudaErrorInvalidValue) {
+            swe_mesh_destroy(m);
+            set_error("swe_mesh_create: no compiled step kernel for this block_size / min_blocks pair");
+            return SWE_EINVAL;
+        }
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device);
+        if (e != cudaSuccess) { swe_mesh_destroy(m); return cuda_fail(e, "swe_mesh_create: occupancy"); }
+        const long long need = (n + c.block_size - 1) / c.block_size;
+        const long long wave = (long long)std::max(per_sm, 1) * std::max(sms, 1);
+        m->grid = (unsigned)std::min(need, wave);
+    }
     m->bc.kind[0] = kBcWall;
     m->bc.value[0] = 0.0;
     m->group_len.assign(1, 0.0);
@@ -523,6 +557,7 @@ int swe_get_info(swe_mesh* m, swe_info* info) {
     // swe_step call multiplies it
     info->dt_next = bits_to_double(s[m->nstep % 3]);
     info->n_clamped = (int64_t)s[kSlotClamp];
+    info->n_active = (int64_t)s[kSlotActive];
     info->status = s[kSlotStatus] & kStatusNonFinite ? SWE_ENONFINITE
                    : (s[kSlotStatus] & kStatusDry ? SWE_EDRY : SWE_OK);
     return SWE_OK;

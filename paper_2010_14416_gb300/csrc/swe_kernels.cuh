@@ -48,15 +48,17 @@ struct StepArgs {
     V4<T>* __restrict__ s_out;
     const V4<T>* __restrict__ geoA;    // (L n)_0 x, y, (L n)_1 x, y : outward normals times length
     const V4<T>* __restrict__ geoB;    // (L n)_2 x, y, 1/|Omega|, inscribed radius
-    const int4* __restrict__ topo;     // neighbour codes of the 3 edges, .w unused
-    const T* __restrict__ gm2;         // g m^2 per cell (Manning factor of Eq 32)
+    const int4* __restrict__ topo;     // neighbour codes of the 3 edges; .w = g m^2 bits (FP32)
+    const T* __restrict__ gm2;         // g m^2 per cell (Manning factor of Eq 32), FP64 only
     const double* dt_read;             // min_i R_i/(c_i+|u_i|) of the current state
     unsigned long long* dt_write;      // same quantity for the new state (atomicMin on bits)
     unsigned long long* dt_reset;      // slot cleared to +inf for the step after next
     double* t;                         // simulated time
     unsigned* status;                  // kStatus* bits
     unsigned long long* n_clamped;     // cells clamped from h < 0
+    unsigned long long* n_active;      // cells that ran the full flux path (diagnostic)
     long long n;                       // number of cells
+    unsigned grid;                     // blocks launched (grid-stride)
     double cfl;
     T g, h_dry;
     BcTable bc;
@@ -149,26 +151,206 @@ __device__ __forceinline__ void riemann_hllc(T hL, T unL, T utL, T hR, T unR, T 
 }
 
 // ---- block min of a non-negative double, published with one atomicMin -------------
+// Optionally also sums a per-thread counter into *count_dst (one atomicAdd per block).
 template <int BLOCK>
-__device__ __forceinline__ void block_min_publish(double cand, unsigned long long* dst) {
+__device__ __forceinline__ void block_min_publish(double cand, unsigned long long* dst,
+                                                  unsigned cnt = 0u, unsigned long long* count_dst = nullptr) {
     __shared__ double warp_min[BLOCK / 32];
+    __shared__ unsigned warp_cnt[BLOCK / 32];
     for (int o = 16; o > 0; o >>= 1) cand = fmin(cand, __shfl_xor_sync(0xffffffffu, cand, o));
+    if (count_dst) cnt = __reduce_add_sync(0xffffffffu, cnt);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) warp_min[wid] = cand;
+    if (lane == 0) { warp_min[wid] = cand; warp_cnt[wid] = cnt; }
     __syncthreads();
     if (wid == 0) {
         double v = lane < BLOCK / 32 ? warp_min[lane] : __longlong_as_double((long long)kInfBits);
+        unsigned c = lane < BLOCK / 32 ? warp_cnt[lane] : 0u;
         for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (count_dst) c = __reduce_add_sync(0xffffffffu, c);
         // non-negative doubles order like their bit patterns: the min is exact
         if (lane == 0 && v < __longlong_as_double((long long)kInfBits))
             atomicMin(dst, (unsigned long long)__double_as_longlong(v));
+        if (lane == 0 && count_dst && c) atomicAdd(count_dst, (unsigned long long)c);
     }
 }
 
-// ---- the fused step: fluxes + bed source + BCs + friction + update + next dt ------
-template <typename T, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) step_kernel(const StepArgs<T> a) {
+// ---- Manning factor g m^2: packed in topo.w (FP32) or its own array (FP64) --------
+template <typename T>
+__device__ __forceinline__ T load_gm2(const StepArgs<T>& a, long long i, const int4& tp);
+template <>
+__device__ __forceinline__ float load_gm2<float>(const StepArgs<float>&, long long, const int4& tp) {
+    return __int_as_float(tp.w);
+}
+template <>
+__device__ __forceinline__ double load_gm2<double>(const StepArgs<double>& a, long long i, const int4&) {
+    return a.gm2[i];
+}
+
+// ---- one cell of the fused step -----------------------------------------------------
+// Returns the cell's CFL candidate R_i/(sqrt(g h)+|u|) of the new state (+inf
+// when the new state is dry); sets `active` when the full flux path ran.
+//
+// A dry cell whose neighbours are all dry and whose boundary edges are walls
+// or transmissive is "quiet": every mass flux it sees is exactly +-0 (both
+// sides dry give G = 0; walls carry no mass), so its depth is unchanged, and
+// its momentum is set to zero by the dry-cell rule after the update.  Its new
+// state is therefore (h, 0, 0) bit for bit whatever the momentum terms were,
+// and the edge loop, geometry and friction are skipped.
+template <typename T>
+__device__ __forceinline__ double update_cell(const StepArgs<T>& a, long long i, T dt, unsigned& active) {
     using A = Ar<T>;
+    const T g = a.g, h_dry = a.h_dry;
+    const V4<T> own = a.s_in[i];
+    const int4 tp = a.topo[i];
+    const T hi = own.x, zi = own.w;
+    const int code[3] = {tp.x, tp.y, tp.z};
+    // issue the three neighbour gathers before any arithmetic
+    V4<T> nb[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) nb[j] = code[j] >= 0 ? a.s_in[code[j] & kNbrMask] : own;
+    bool quiet = !(hi > h_dry);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        if (code[j] >= 0) {
+            quiet = quiet && !(nb[j].x > h_dry);
+        } else {
+            const int kind = a.bc.kind[-1 - code[j]];
+            quiet = quiet && (kind == kBcWall || kind == kBcTransmissive);
+        }
+    }
+    V4<T> out;
+    out.w = zi;
+    if (quiet) {
+        out.x = hi; out.y = T(0); out.z = T(0);
+        a.s_out[i] = out;
+        return __longlong_as_double((long long)kInfBits);
+    }
+    active += 1u;
+    const V4<T> gA = a.geoA[i], gB = a.geoB[i];
+    const T gm2 = load_gm2<T>(a, i, tp);
+    T ui = T(0), vi = T(0);
+    if (hi > h_dry) { const T r = A::rcp_(hi); ui = own.y * r; vi = own.z * r; }
+    T f0 = T(0), f1 = T(0), f2 = T(0), sx = T(0), sy = T(0);
+#pragma unroll 1
+    for (int j = 0; j < 3; ++j) {
+        const int c = j == 0 ? code[0] : (j == 1 ? code[1] : code[2]);
+        const V4<T> o = j == 0 ? nb[0] : (j == 1 ? nb[1] : nb[2]);
+        const T lx = j == 0 ? gA.x : (j == 1 ? gA.z : gB.x);
+        const T ly = j == 0 ? gA.y : (j == 1 ? gA.w : gB.y);
+        const T l2 = lx * lx + ly * ly;
+        const T rl = A::rsqrt_(l2);
+        const T len = l2 * rl;
+        const T n1 = lx * rl, n2 = ly * rl;     // this cell's outward unit normal
+        T F0, F1, F2;
+        if (c >= 0) {
+            const bool flip = (c & kFlipBit) != 0;
+            const T hk = o.x, zk = o.w;
+            T uk = T(0), vk = T(0);
+            if (hk > h_dry) { const T r = A::rcp_(hk); uk = o.y * r; vk = o.z * r; }
+            // hydrostatic reconstruction (Eq 28): z* = max(z_i, z_k)
+            const T zs = tmax(zi, zk);
+            const T hsi = tmax(T(0), hi + zi - zs);
+            const T hsk = tmax(T(0), hk + zk - zs);
+            // canonical orientation: left = lower caller index
+            const T hL = flip ? hsk : hsi, hR = flip ? hsi : hsk;
+            const T uL = flip ? uk : ui, vL = flip ? vk : vi;
+            const T uR = flip ? ui : uk, vR = flip ? vi : vk;
+            const T c1 = flip ? -n1 : n1, c2 = flip ? -n2 : n2;
+            // rotate into the edge frame (Eq 12)
+            const T unL = uL * c1 + vL * c2, utL = vL * c1 - uL * c2;
+            const T unR = uR * c1 + vR * c2, utR = vR * c1 - uR * c2;
+            T G1, G2, G3;
+            riemann_hllc<T>(hL, unL, utL, hR, unR, utR, g, h_dry, G1, G2, G3);
+            // back to (x, y) (Eq 12 inverse), as the flux leaving this cell
+            const T s = flip ? T(-1) : T(1);
+            F0 = s * G1;
+            F1 = s * (G2 * c1 - G3 * c2);
+            F2 = s * (G2 * c2 + G3 * c1);
+            // bed source of this edge (Eq 30 with the factor 1/2)
+            const T src = T(0.5) * g * (hsi * hsi - hi * hi);
+            sx += src * lx;
+            sy += src * ly;
+        } else {
+            const int grp = -1 - c;
+            const int kind = a.bc.kind[grp];
+            const T un = ui * n1 + vi * n2, ut = vi * n1 - ui * n2;
+            T G1, G2, G3;
+            if (kind == kBcWall) {
+                G1 = T(0); G2 = T(0.5) * g * hi * hi; G3 = T(0);
+            } else if (kind == kBcInflow) {
+                const T q = T(a.bc.value[grp]);
+                G1 = -q;
+                G2 = T(0.5) * g * hi * hi + (hi > h_dry ? A::div_(q * q, hi) : T(0));
+                G3 = T(0);
+            } else {
+                T hg = hi;
+                if (kind == kBcStage) hg = tmax(T(0), T(a.bc.value[grp]) - zi);
+                riemann_hllc<T>(hi, un, ut, hg, un, ut, g, h_dry, G1, G2, G3);
+            }
+            F0 = G1;
+            F1 = G2 * n1 - G3 * n2;
+            F2 = G2 * n2 + G3 * n1;
+        }
+        f0 += len * F0;
+        f1 += len * F1;
+        f2 += len * F2;
+    }
+    const T ia = gB.z;
+    const T Rh = -f0 * ia;
+    const T Rx = (sx - f1) * ia;
+    const T Ry = (sy - f2) * ia;
+    // semi-implicit friction (Eq 33-37): [I - dt/2 J_f] dU = dt (R + S_f)
+    const T dh = dt * Rh;
+    T dqx = dt * Rx, dqy = dt * Ry;
+    const T qx = own.y, qy = own.z;
+    if (hi > h_dry && gm2 > T(0)) {
+        const T qq = qx * qx + qy * qy;
+        if (qq > T(0)) {
+            const T qn = A::sqrt_(qq);
+            const T cf = gm2 * A::pow_m73(hi);             // c = g m^2 h^(-7/3)
+            const T al = T(0.5) * dt * cf;                  // alpha = dt c / 2
+            // rhs: dt (R_q + S_f) + dt/2 J_qh dh, with S_f = -c|q|q and
+            // J_qh = (7/3) c |q| q / h
+            const T k = dt * cf * qn * (T(7.0 / 6.0) * dh * A::rcp_(hi) - T(1));
+            const T bx = dqx + k * qx, by = dqy + k * qy;
+            // (1 + a|q|) I + a q q^T/|q| has eigenvalue 1 + 2a|q| along q
+            // and 1 + a|q| across it
+            const T d1 = T(1) + al * qn, d2 = d1 + al * qn;
+            const T proj = (bx * qx + by * qy) * al * A::rcp_(qn * d2);
+            const T rd1 = A::rcp_(d1);
+            dqx = (bx - proj * qx) * rd1;
+            dqy = (by - proj * qy) * rd1;
+        }
+    }
+    out.x = hi + dh;
+    out.y = qx + dqx;
+    out.z = qy + dqy;
+    if (out.x < T(0)) {
+        out.x = T(0); out.y = T(0); out.z = T(0);
+        atomicAdd(a.n_clamped, 1ULL);
+    } else if (out.x <= h_dry) {
+        out.y = T(0); out.z = T(0);
+    }
+    const T big = T(3.0e38);
+    if (!(out.x < big) || !(fabs(out.y) < big) || !(fabs(out.z) < big))
+        atomicOr(a.status, kStatusNonFinite);
+    a.s_out[i] = out;
+    // next CFL candidate (Eq 15), R_i / (sqrt(g h) + |u|) on the new state
+    double cand = __longlong_as_double((long long)kInfBits);
+    if (out.x > h_dry) {
+        const T r = A::rcp_(out.x);
+        const T u = out.y * r, v = out.z * r;
+        const T den = A::sqrt_(g * out.x) + A::sqrt_(u * u + v * v);
+        cand = (double)A::div_(gB.w, den);
+    }
+    return cand;
+}
+
+// ---- the fused step: fluxes + bed source + BCs + friction + update + next dt ------
+// Grid-stride over cells with about one resident wave of blocks, so the block
+// reduction (and its barrier) runs once per block.
+template <typename T, int BLOCK, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) step_kernel(const StepArgs<T> a) {
     const double dt_d = a.cfl * (*a.dt_read);
     const bool have_dt = dt_d < __longlong_as_double((long long)kInfBits);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -176,142 +358,18 @@ __global__ void __launch_bounds__(BLOCK) step_kernel(const StepArgs<T> a) {
         if (have_dt) *a.t += dt_d;
         else atomicOr(a.status, kStatusDry);
     }
-    const long long i = (long long)blockIdx.x * BLOCK + threadIdx.x;
     double cand = __longlong_as_double((long long)kInfBits);
-    if (i < a.n) {
-        const V4<T> own = a.s_in[i];
-        if (!have_dt) {
-            a.s_out[i] = own;
-        } else {
-            const T g = a.g, h_dry = a.h_dry, dt = T(dt_d);
-            const V4<T> gA = a.geoA[i], gB = a.geoB[i];
-            const int4 tp = a.topo[i];
-            const T hi = own.x, zi = own.w;
-            T ui = T(0), vi = T(0);
-            if (hi > h_dry) { const T r = A::rcp_(hi); ui = own.y * r; vi = own.z * r; }
-            // issue the three neighbour gathers before any arithmetic
-            V4<T> nb[3];
-            const int code[3] = {tp.x, tp.y, tp.z};
-#pragma unroll
-            for (int j = 0; j < 3; ++j) nb[j] = code[j] >= 0 ? a.s_in[code[j] & kNbrMask] : own;
-            T f0 = T(0), f1 = T(0), f2 = T(0), sx = T(0), sy = T(0);
-#pragma unroll 1
-            for (int j = 0; j < 3; ++j) {
-                const int c = j == 0 ? code[0] : (j == 1 ? code[1] : code[2]);
-                const V4<T> o = j == 0 ? nb[0] : (j == 1 ? nb[1] : nb[2]);
-                const T lx = j == 0 ? gA.x : (j == 1 ? gA.z : gB.x);
-                const T ly = j == 0 ? gA.y : (j == 1 ? gA.w : gB.y);
-                const T l2 = lx * lx + ly * ly;
-                const T rl = A::rsqrt_(l2);
-                const T len = l2 * rl;
-                const T n1 = lx * rl, n2 = ly * rl;     // this cell's outward unit normal
-                T F0, F1, F2;
-                if (c >= 0) {
-                    const bool flip = (c & kFlipBit) != 0;
-                    const T hk = o.x, zk = o.w;
-                    T uk = T(0), vk = T(0);
-                    if (hk > h_dry) { const T r = A::rcp_(hk); uk = o.y * r; vk = o.z * r; }
-                    // hydrostatic reconstruction (Eq 28): z* = max(z_i, z_k)
-                    const T zs = tmax(zi, zk);
-                    const T hsi = tmax(T(0), hi + zi - zs);
-                    const T hsk = tmax(T(0), hk + zk - zs);
-                    // canonical orientation: left = lower caller index
-                    const T hL = flip ? hsk : hsi, hR = flip ? hsi : hsk;
-                    const T uL = flip ? uk : ui, vL = flip ? vk : vi;
-                    const T uR = flip ? ui : uk, vR = flip ? vi : vk;
-                    const T c1 = flip ? -n1 : n1, c2 = flip ? -n2 : n2;
-                    // rotate into the edge frame (Eq 12)
-                    const T unL = uL * c1 + vL * c2, utL = vL * c1 - uL * c2;
-                    const T unR = uR * c1 + vR * c2, utR = vR * c1 - uR * c2;
-                    T G1, G2, G3;
-                    riemann_hllc<T>(hL, unL, utL, hR, unR, utR, g, h_dry, G1, G2, G3);
-                    // back to (x, y) (Eq 12 inverse), as the flux leaving this cell
-                    const T s = flip ? T(-1) : T(1);
-                    F0 = s * G1;
-                    F1 = s * (G2 * c1 - G3 * c2);
-                    F2 = s * (G2 * c2 + G3 * c1);
-                    // bed source of this edge (Eq 30 with the factor 1/2)
-                    const T src = T(0.5) * g * (hsi * hsi - hi * hi);
-                    sx += src * lx;
-                    sy += src * ly;
-                } else {
-                    const int grp = -1 - c;
-                    const int kind = a.bc.kind[grp];
-                    const T un = ui * n1 + vi * n2, ut = vi * n1 - ui * n2;
-                    T G1, G2, G3;
-                    if (kind == kBcWall) {
-                        G1 = T(0); G2 = T(0.5) * g * hi * hi; G3 = T(0);
-                    } else if (kind == kBcInflow) {
-                        const T q = T(a.bc.value[grp]);
-                        G1 = -q;
-                        G2 = T(0.5) * g * hi * hi + (hi > h_dry ? A::div_(q * q, hi) : T(0));
-                        G3 = T(0);
-                    } else {
-                        T hg = hi;
-                        if (kind == kBcStage) hg = tmax(T(0), T(a.bc.value[grp]) - zi);
-                        riemann_hllc<T>(hi, un, ut, hg, un, ut, g, h_dry, G1, G2, G3);
-                    }
-                    F0 = G1;
-                    F1 = G2 * n1 - G3 * n2;
-                    F2 = G2 * n2 + G3 * n1;
-                }
-                f0 += len * F0;
-                f1 += len * F1;
-                f2 += len * F2;
-            }
-            const T ia = gB.z;
-            const T Rh = -f0 * ia;
-            const T Rx = (sx - f1) * ia;
-            const T Ry = (sy - f2) * ia;
-            // semi-implicit friction (Eq 33-37): [I - dt/2 J_f] dU = dt (R + S_f)
-            const T dh = dt * Rh;
-            T dqx = dt * Rx, dqy = dt * Ry;
-            const T gm2 = a.gm2[i];
-            const T qx = own.y, qy = own.z;
-            if (hi > h_dry && gm2 > T(0)) {
-                const T qq = qx * qx + qy * qy;
-                if (qq > T(0)) {
-                    const T qn = A::sqrt_(qq);
-                    const T cf = gm2 * A::pow_m73(hi);             // c = g m^2 h^(-7/3)
-                    const T al = T(0.5) * dt * cf;                  // alpha = dt c / 2
-                    // rhs: dt (R_q + S_f) + dt/2 J_qh dh, with S_f = -c|q|q and
-                    // J_qh = (7/3) c |q| q / h
-                    const T k = dt * cf * qn * (T(7.0 / 6.0) * dh * A::rcp_(hi) - T(1));
-                    const T bx = dqx + k * qx, by = dqy + k * qy;
-                    // (1 + a|q|) I + a q q^T/|q| has eigenvalue 1 + 2a|q| along q
-                    // and 1 + a|q| across it
-                    const T d1 = T(1) + al * qn, d2 = d1 + al * qn;
-                    const T proj = (bx * qx + by * qy) * al * A::rcp_(qn * d2);
-                    const T rd1 = A::rcp_(d1);
-                    dqx = (bx - proj * qx) * rd1;
-                    dqy = (by - proj * qy) * rd1;
-                }
-            }
-            V4<T> out;
-            out.x = hi + dh;
-            out.y = qx + dqx;
-            out.z = qy + dqy;
-            out.w = zi;
-            if (out.x < T(0)) {
-                out.x = T(0); out.y = T(0); out.z = T(0);
-                atomicAdd(a.n_clamped, 1ULL);
-            } else if (out.x <= h_dry) {
-                out.y = T(0); out.z = T(0);
-            }
-            const T big = T(3.0e38);
-            if (!(out.x < big) || !(fabs(out.y) < big) || !(fabs(out.z) < big))
-                atomicOr(a.status, kStatusNonFinite);
-            a.s_out[i] = out;
-            // next CFL candidate (Eq 15), R_i / (sqrt(g h) + |u|) on the new state
-            if (out.x > h_dry) {
-                const T r = A::rcp_(out.x);
-                const T u = out.y * r, v = out.z * r;
-                const T den = A::sqrt_(g * out.x) + A::sqrt_(u * u + v * v);
-                cand = (double)A::div_(gB.w, den);
-            }
-        }
+    unsigned active = 0u;
+    const long long stride = (long long)gridDim.x * BLOCK;
+    if (have_dt) {
+        const T dt = T(dt_d);
+        for (long long i = (long long)blockIdx.x * BLOCK + threadIdx.x; i < a.n; i += stride)
+            cand = fmin(cand, update_cell<T>(a, i, dt, active));
+    } else {
+        for (long long i = (long long)blockIdx.x * BLOCK + threadIdx.x; i < a.n; i += stride)
+            a.s_out[i] = a.s_in[i];
     }
-    block_min_publish<BLOCK>(cand, a.dt_write);
+    block_min_publish<BLOCK>(cand, a.dt_write, active, a.n_active);
 }
 
 // ---- CFL min of a given state (used after swe_set_state) --------------------------
@@ -376,7 +434,10 @@ __global__ void riemann_batch_kernel(long long n, const T* __restrict__ hL, cons
 // ---- host-side launchers, one set per precision ------------------------------------
 template <typename T>
 struct Launch {
-    static cudaError_t step(const StepArgs<T>& a, int block, cudaStream_t st);
+    // (block, min_blocks) pairs with a compiled kernel; see step_variants()
+    static cudaError_t step(const StepArgs<T>& a, int block, int min_blocks, cudaStream_t st);
+    static cudaError_t resident_blocks(int block, int min_blocks, int* per_sm);
+    static int default_min_blocks(int block);
     static cudaError_t dt(const V4<T>* s, const V4<T>* geoB, long long n, T g, T h_dry,
                           unsigned long long* dt_write, cudaStream_t st);
     static cudaError_t pack(const T* h, const T* hu, const T* hv, const long long* perm, const T* z,

@@ -11,16 +11,36 @@ static inline unsigned grid_for(long long n, int block) {
     return (unsigned)((n + block - 1) / block);
 }
 
+// Compiled (block, minimum resident blocks per SM) variants of the step
+// kernel.  FP32 variants trade registers for occupancy; FP64 keeps its
+// registers (its FP64 pipe, not memory latency, is the limit).
+#define SWE_STEP_VARIANTS(X) \
+    X(128, 1) X(256, 1) X(512, 1) X(128, 8) X(256, 4) X(256, 5) X(256, 6) X(512, 2)
+
 template <typename T>
-cudaError_t Launch<T>::step(const StepArgs<T>& a, int block, cudaStream_t st) {
-    const long long n = a.n;
-    switch (block) {
-        case 128: step_kernel<T, 128><<<grid_for<T>(n, 128), 128, 0, st>>>(a); break;
-        case 256: step_kernel<T, 256><<<grid_for<T>(n, 256), 256, 0, st>>>(a); break;
-        case 512: step_kernel<T, 512><<<grid_for<T>(n, 512), 512, 0, st>>>(a); break;
-        default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
+int Launch<T>::default_min_blocks(int block) {
+    if (sizeof(T) == 8) return 1;
+    return block == 128 ? 8 : (block == 256 ? 4 : 2);
+}
+
+template <typename T>
+cudaError_t Launch<T>::step(const StepArgs<T>& a, int block, int min_blocks, cudaStream_t st) {
+    const unsigned grid = a.grid;
+    if (grid == 0) return cudaErrorInvalidValue;
+#define SWE_LAUNCH(B, M) \
+    if (block == B && min_blocks == M) { step_kernel<T, B, M><<<grid, B, 0, st>>>(a); return cudaGetLastError(); }
+    SWE_STEP_VARIANTS(SWE_LAUNCH)
+#undef SWE_LAUNCH
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t Launch<T>::resident_blocks(int block, int min_blocks, int* per_sm) {
+#define SWE_OCC(B, M) \
+    if (block == B && min_blocks == M) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, step_kernel<T, B, M>, B, 0);
+    SWE_STEP_VARIANTS(SWE_OCC)
+#undef SWE_OCC
+    return cudaErrorInvalidValue;
 }
 
 template <typename T>
