@@ -80,8 +80,13 @@ typedef struct swe_config {
     int graph_steps;  /* steps captured per CUDA graph; 0 = default, < 0 = no graphs */
     int device;       /* CUDA device ordinal, default 0 */
     int min_blocks;   /* resident blocks per SM the step kernel is compiled for; 0 = default.
-                         Compiled (block_size, min_blocks) pairs: (128|256|512, 1), (128, 8),
-                         (256, 4|5|6), (512, 2); others give SWE_EINVAL */
+                         0 = default (FP32: 2048 / (2 block_size), FP64: 1) */
+    int stages;       /* depth of the per-thread cp.async pipeline that stages the next cells'
+                         state and topology records in shared memory; 1 = direct loads;
+                         0 = default (FP32: 3, FP64: 1).  Compiled (block_size, min_blocks,
+                         stages): FP32 (128|256|512, 1, 1), (128, 8, 1), (256, 4|5, 1),
+                         (512, 2, 1), (256, 4, 2|3|4), (128, 8, 3|4); FP64 (128|256|512, 1, 1),
+                         (128|256, 1, 2); others give SWE_EINVAL */
 } swe_config;
 
 /* Fills *cfg with the defaults listed above. */

@@ -35,7 +35,7 @@ EXPORTS = ["swe_config_default", "swe_mesh_create", "swe_mesh_destroy", "swe_set
 class swe_config(C.Structure):
     _fields_ = [("precision", C.c_int), ("g", C.c_double), ("h_dry", C.c_double),
                 ("reorder", C.c_int), ("block_size", C.c_int), ("graph_steps", C.c_int),
-                ("device", C.c_int), ("min_blocks", C.c_int)]
+                ("device", C.c_int), ("min_blocks", C.c_int), ("stages", C.c_int)]
 
 
 class swe_info(C.Structure):
@@ -125,7 +125,7 @@ class Mesh:
     """An owned swe_mesh handle (thin wrapper over the C ABI)."""
 
     def __init__(self, nodes, tris, bathy, manning, precision=SWE_FP64, reorder=None,
-                 block_size=0, graph_steps=0, device=0, g=9.81, h_dry=1e-6, min_blocks=0):
+                 block_size=0, graph_steps=0, device=0, g=9.81, h_dry=1e-6, min_blocks=0, stages=0):
         lib = load()
         cfg = config_default()
         cfg.precision = precision
@@ -133,6 +133,7 @@ class Mesh:
             cfg.reorder = reorder
         cfg.block_size, cfg.graph_steps, cfg.device = block_size, graph_steps, device
         cfg.min_blocks = min_blocks
+        cfg.stages = stages
         cfg.g, cfg.h_dry = g, h_dry
         nodes = np.ascontiguousarray(nodes, dtype=np.float64).reshape(-1, 2)
         tris = np.ascontiguousarray(tris, dtype=np.int32).reshape(-1, 3)

@@ -203,7 +203,8 @@ StepArgs<T> make_args(swe_mesh* m, int64_t step_index, double cfl) {
 
 template <typename T>
 cudaError_t launch_one(swe_mesh* m, int64_t step_index, double cfl, cudaStream_t st) {
-    return Launch<T>::step(make_args<T>(m, step_index, cfl), m->cfg.block_size, m->cfg.min_blocks, st);
+    return Launch<T>::step(make_args<T>(m, step_index, cfl), m->cfg.block_size, m->cfg.min_blocks,
+                           m->cfg.stages, st);
 }
 
 template <typename T>
@@ -352,6 +353,7 @@ void swe_config_default(swe_config* cfg) {
     cfg->graph_steps = 0;
     cfg->device = 0;
     cfg->min_blocks = 0;
+    cfg->stages = 0;
 }
 
 const char* swe_last_error(void) { return g_last_error.c_str(); }
@@ -386,6 +388,7 @@ int swe_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* tris, i
     if (c.min_blocks == 0)
         c.min_blocks = c.precision == SWE_FP32 ? Launch<float>::default_min_blocks(c.block_size)
                                                : Launch<double>::default_min_blocks(c.block_size);
+    if (c.stages == 0) c.stages = c.precision == SWE_FP32 ? 3 : 1;
     if (c.graph_steps == 0) c.graph_steps = kDefaultGraphSteps;
     if (c.graph_steps > 0) c.graph_steps = std::max(6, (c.graph_steps / 6) * 6);
     swe_mesh* m = new (std::nothrow) swe_mesh();
@@ -421,11 +424,11 @@ int swe_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* tris, i
     if (rc) { swe_mesh_destroy(m); return rc; }
     {
         int per_sm = 0, sms = 0;
-        e = c.precision == SWE_FP32 ? Launch<float>::resident_blocks(c.block_size, c.min_blocks, &per_sm)
-                                    : Launch<double>::resident_blocks(c.block_size, c.min_blocks, &per_sm);
+        e = c.precision == SWE_FP32 ? Launch<float>::resident_blocks(c.block_size, c.min_blocks, c.stages, &per_sm)
+                                    : Launch<double>::resident_blocks(c.block_size, c.min_blocks, c.stages, &per_sm);
         if (e == cudaErrorInvalidValue) {
             swe_mesh_destroy(m);
-            set_error("swe_mesh_create: no compiled step kernel for this block_size / min_blocks pair");
+            set_error("swe_mesh_create: no compiled step kernel for this block_size / min_blocks / stages");
             return SWE_EINVAL;
         }
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device);

@@ -186,6 +186,32 @@ __device__ __forceinline__ double load_gm2<double>(const StepArgs<double>& a, lo
     return a.gm2[i];
 }
 
+template <typename T>
+__device__ __forceinline__ T inf_of();
+template <>
+__device__ __forceinline__ float inf_of<float>() { return __int_as_float(0x7F800000); }
+template <>
+__device__ __forceinline__ double inf_of<double>() { return __longlong_as_double((long long)kInfBits); }
+
+// ---- asynchronous global -> shared copies (cp.async, 16 B, L2 only) ------------------
+// Each thread stages its own future cells' records; it alone reads them back,
+// so the per-thread wait_group is the only synchronisation needed.
+template <int BYTES>
+__device__ __forceinline__ void cp_async_record(void* smem_dst, const void* gmem_src) {
+    static_assert(BYTES % 16 == 0, "records are whole 16-byte chunks");
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(smem_dst);
+#pragma unroll
+    for (int b = 0; b < BYTES; b += 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst + b),
+                     "l"((const char*)gmem_src + b)
+                     : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory");
+}
+
 // ---- one cell of the fused step -----------------------------------------------------
 // Returns the cell's CFL candidate R_i/(sqrt(g h)+|u|) of the new state (+inf
 // when the new state is dry); sets `active` when the full flux path ran.
@@ -197,11 +223,10 @@ __device__ __forceinline__ double load_gm2<double>(const StepArgs<double>& a, lo
 // state is therefore (h, 0, 0) bit for bit whatever the momentum terms were,
 // and the edge loop, geometry and friction are skipped.
 template <typename T>
-__device__ __forceinline__ double update_cell(const StepArgs<T>& a, long long i, T dt, unsigned& active) {
+__device__ __forceinline__ T update_cell(const StepArgs<T>& a, long long i, const V4<T>& own, const int4& tp,
+                                         T dt, unsigned& active) {
     using A = Ar<T>;
     const T g = a.g, h_dry = a.h_dry;
-    const V4<T> own = a.s_in[i];
-    const int4 tp = a.topo[i];
     const T hi = own.x, zi = own.w;
     const int code[3] = {tp.x, tp.y, tp.z};
     // issue the three neighbour gathers before any arithmetic
@@ -223,7 +248,7 @@ __device__ __forceinline__ double update_cell(const StepArgs<T>& a, long long i,
     if (quiet) {
         out.x = hi; out.y = T(0); out.z = T(0);
         a.s_out[i] = out;
-        return __longlong_as_double((long long)kInfBits);
+        return inf_of<T>();
     }
     active += 1u;
     const V4<T> gA = a.geoA[i], gB = a.geoB[i];
@@ -336,20 +361,22 @@ __device__ __forceinline__ double update_cell(const StepArgs<T>& a, long long i,
         atomicOr(a.status, kStatusNonFinite);
     a.s_out[i] = out;
     // next CFL candidate (Eq 15), R_i / (sqrt(g h) + |u|) on the new state
-    double cand = __longlong_as_double((long long)kInfBits);
+    T cand = inf_of<T>();
     if (out.x > h_dry) {
         const T r = A::rcp_(out.x);
         const T u = out.y * r, v = out.z * r;
         const T den = A::sqrt_(g * out.x) + A::sqrt_(u * u + v * v);
-        cand = (double)A::div_(gB.w, den);
+        cand = A::div_(gB.w, den);
     }
     return cand;
 }
 
 // ---- the fused step: fluxes + bed source + BCs + friction + update + next dt ------
 // Grid-stride over cells with about one resident wave of blocks, so the block
-// reduction (and its barrier) runs once per block.
-template <typename T, int BLOCK, int MINB>
+// reduction (and its barrier) runs once per block.  With STAGES > 1 each
+// thread keeps its next STAGES-1 cells' state and topology records in flight
+// through cp.async into its own shared-memory slots.
+template <typename T, int BLOCK, int MINB, int STAGES>
 __global__ void __launch_bounds__(BLOCK, MINB) step_kernel(const StepArgs<T> a) {
     const double dt_d = a.cfl * (*a.dt_read);
     const bool have_dt = dt_d < __longlong_as_double((long long)kInfBits);
@@ -358,18 +385,51 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_kernel(const StepArgs<T> a) 
         if (have_dt) *a.t += dt_d;
         else atomicOr(a.status, kStatusDry);
     }
-    double cand = __longlong_as_double((long long)kInfBits);
+    T cand = inf_of<T>();
     unsigned active = 0u;
     const long long stride = (long long)gridDim.x * BLOCK;
-    if (have_dt) {
+    long long i = (long long)blockIdx.x * BLOCK + threadIdx.x;
+    if (!have_dt) {
+        for (; i < a.n; i += stride) a.s_out[i] = a.s_in[i];
+    } else if constexpr (STAGES <= 1) {
         const T dt = T(dt_d);
-        for (long long i = (long long)blockIdx.x * BLOCK + threadIdx.x; i < a.n; i += stride)
-            cand = fmin(cand, update_cell<T>(a, i, dt, active));
+        for (; i < a.n; i += stride) {
+            const V4<T> own = a.s_in[i];
+            const int4 tp = a.topo[i];
+            cand = tmin(cand, update_cell<T>(a, i, own, tp, dt, active));
+        }
     } else {
-        for (long long i = (long long)blockIdx.x * BLOCK + threadIdx.x; i < a.n; i += stride)
-            a.s_out[i] = a.s_in[i];
+        __shared__ V4<T> st_own[STAGES][BLOCK];
+        __shared__ int4 st_topo[STAGES][BLOCK];
+        const T dt = T(dt_d);
+        const int tid = threadIdx.x;
+#pragma unroll
+        for (int s = 0; s < STAGES - 1; ++s) {
+            const long long c = i + (long long)s * stride;
+            if (c < a.n) {
+                cp_async_record<sizeof(V4<T>)>(&st_own[s][tid], &a.s_in[c]);
+                cp_async_record<16>(&st_topo[s][tid], &a.topo[c]);
+            }
+            cp_async_commit();
+        }
+        int slot = 0;
+        for (; i < a.n; i += stride) {
+            const long long c = i + (long long)(STAGES - 1) * stride;
+            const int fill = slot == 0 ? STAGES - 1 : slot - 1;
+            if (c < a.n) {
+                cp_async_record<sizeof(V4<T>)>(&st_own[fill][tid], &a.s_in[c]);
+                cp_async_record<16>(&st_topo[fill][tid], &a.topo[c]);
+            }
+            cp_async_commit();
+            cp_async_wait<STAGES - 1>();
+            const V4<T> own = st_own[slot][tid];
+            const int4 tp = st_topo[slot][tid];
+            cand = tmin(cand, update_cell<T>(a, i, own, tp, dt, active));
+            slot = slot == STAGES - 1 ? 0 : slot + 1;
+        }
+        cp_async_wait<0>();
     }
-    block_min_publish<BLOCK>(cand, a.dt_write, active, a.n_active);
+    block_min_publish<BLOCK>((double)cand, a.dt_write, active, a.n_active);
 }
 
 // ---- CFL min of a given state (used after swe_set_state) --------------------------
@@ -435,8 +495,8 @@ __global__ void riemann_batch_kernel(long long n, const T* __restrict__ hL, cons
 template <typename T>
 struct Launch {
     // (block, min_blocks) pairs with a compiled kernel; see step_variants()
-    static cudaError_t step(const StepArgs<T>& a, int block, int min_blocks, cudaStream_t st);
-    static cudaError_t resident_blocks(int block, int min_blocks, int* per_sm);
+    static cudaError_t step(const StepArgs<T>& a, int block, int min_blocks, int stages, cudaStream_t st);
+    static cudaError_t resident_blocks(int block, int min_blocks, int stages, int* per_sm);
     static int default_min_blocks(int block);
     static cudaError_t dt(const V4<T>* s, const V4<T>* geoB, long long n, T g, T h_dry,
                           unsigned long long* dt_write, cudaStream_t st);

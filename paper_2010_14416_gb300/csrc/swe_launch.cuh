@@ -14,8 +14,12 @@ static inline unsigned grid_for(long long n, int block) {
 // Compiled (block, minimum resident blocks per SM) variants of the step
 // kernel.  FP32 variants trade registers for occupancy; FP64 keeps its
 // registers (its FP64 pipe, not memory latency, is the limit).
-#define SWE_STEP_VARIANTS(X) \
-    X(128, 1) X(256, 1) X(512, 1) X(128, 8) X(256, 4) X(256, 5) X(256, 6) X(512, 2)
+// (block, min blocks per SM, stages); every FP32 variant stays within the
+// 48 KB of static shared memory a block may declare.
+#define SWE_STEP_VARIANTS_F32(X)                                                             \
+    X(128, 1, 1) X(256, 1, 1) X(512, 1, 1) X(128, 8, 1) X(256, 4, 1) X(256, 5, 1) X(512, 2, 1) \
+    X(256, 4, 2) X(256, 4, 3) X(256, 4, 4) X(128, 8, 3) X(128, 8, 4)
+#define SWE_STEP_VARIANTS_F64(X) X(128, 1, 1) X(256, 1, 1) X(512, 1, 1) X(128, 1, 2) X(256, 1, 2)
 
 template <typename T>
 int Launch<T>::default_min_blocks(int block) {
@@ -24,21 +28,33 @@ int Launch<T>::default_min_blocks(int block) {
 }
 
 template <typename T>
-cudaError_t Launch<T>::step(const StepArgs<T>& a, int block, int min_blocks, cudaStream_t st) {
+cudaError_t Launch<T>::step(const StepArgs<T>& a, int block, int min_blocks, int stages, cudaStream_t st) {
     const unsigned grid = a.grid;
     if (grid == 0) return cudaErrorInvalidValue;
-#define SWE_LAUNCH(B, M) \
-    if (block == B && min_blocks == M) { step_kernel<T, B, M><<<grid, B, 0, st>>>(a); return cudaGetLastError(); }
-    SWE_STEP_VARIANTS(SWE_LAUNCH)
+#define SWE_LAUNCH(B, M, S) \
+    if (block == B && min_blocks == M && stages == S) {                          \
+        step_kernel<T, B, M, S><<<grid, B, 0, st>>>(a);                           \
+        return cudaGetLastError();                                                \
+    }
+    if constexpr (sizeof(T) == 4) {
+        SWE_STEP_VARIANTS_F32(SWE_LAUNCH)
+    } else {
+        SWE_STEP_VARIANTS_F64(SWE_LAUNCH)
+    }
 #undef SWE_LAUNCH
     return cudaErrorInvalidValue;
 }
 
 template <typename T>
-cudaError_t Launch<T>::resident_blocks(int block, int min_blocks, int* per_sm) {
-#define SWE_OCC(B, M) \
-    if (block == B && min_blocks == M) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, step_kernel<T, B, M>, B, 0);
-    SWE_STEP_VARIANTS(SWE_OCC)
+cudaError_t Launch<T>::resident_blocks(int block, int min_blocks, int stages, int* per_sm) {
+#define SWE_OCC(B, M, S) \
+    if (block == B && min_blocks == M && stages == S)                             \
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, step_kernel<T, B, M, S>, B, 0);
+    if constexpr (sizeof(T) == 4) {
+        SWE_STEP_VARIANTS_F32(SWE_OCC)
+    } else {
+        SWE_STEP_VARIANTS_F64(SWE_OCC)
+    }
 #undef SWE_OCC
     return cudaErrorInvalidValue;
 }

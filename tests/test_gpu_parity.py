@@ -180,6 +180,24 @@ def test_mass_conserved_and_lake_at_rest_on_gpu():
     assert np.abs(ghu).max() < 1e-10 and np.abs(ghv).max() < 1e-10
 
 
+@pytest.mark.parametrize("precision,variants", [
+    (capi.SWE_FP64, [(128, 1, 1), (256, 1, 1), (512, 1, 1), (128, 1, 2), (256, 1, 2)]),
+    (capi.SWE_FP32, [(256, 4, 1), (256, 4, 2), (256, 4, 3), (256, 4, 4), (128, 8, 3), (128, 8, 4),
+                     (512, 2, 1), (256, 5, 1)]),
+])
+def test_kernel_variants_are_bitwise_identical(precision, variants):
+    # launch shape, register cap and cp.async staging depth change nothing
+    mi = mg.river(100, 20, seed=8)
+    ref = None
+    for b, mb, st in variants:
+        got, t, _ = _gpu_run(mi, 301, precision=precision, block_size=b, min_blocks=mb, stages=st)
+        if ref is None:
+            ref, tref = got, t
+            continue
+        assert t == tref, (b, mb, st)
+        assert all(np.array_equal(x, y) for x, y in zip(ref, got)), (b, mb, st)
+
+
 def test_graphs_block_sizes_and_device_io_are_bitwise_neutral():
     mi = mg.river(100, 20, seed=8)
     ref, tref, _ = _gpu_run(mi, 301, graph_steps=-1, block_size=128)
