@@ -61,6 +61,8 @@ def _load():
         lib.orc_mesh_set_bc.argtypes = [vp, ip, C.c_int64, C.c_int, C.c_double]
         lib.orc_mesh_geometry.argtypes = [vp, dp, dp, lp, dp, dp, dp]
         lib.orc_mesh_set_fields.argtypes = [vp, dp, dp]
+        lib.orc_mesh_groups.restype = C.c_int
+        lib.orc_mesh_groups.argtypes = [vp, C.POINTER(C.c_int), dp, dp]
         lib.orc_hstar.restype = C.c_double
         lib.orc_hstar.argtypes = [C.c_double] * 5 + [dp]
         lib.orc_hllc.argtypes = [C.c_double] * 8 + [dp, dp]
@@ -144,6 +146,13 @@ class Mesh:
         _load().orc_mesh_geometry(self._h, _d(area), _d(rin),
                                   nbr.ctypes.data_as(C.POINTER(C.c_int64)), _d(ln), _d(nx), _d(ny))
         return dict(area=area, rin=rin, nbr=nbr, len=ln, nx=nx, ny=ny)
+
+    def groups(self):
+        """Boundary groups as (kind[], value[], total length[]); group 0 is the wall."""
+        kind = np.zeros(64, np.int32)
+        value, glen = np.zeros(64), np.zeros(64)
+        ng = _load().orc_mesh_groups(self._h, kind.ctypes.data_as(C.POINTER(C.c_int)), _d(value), _d(glen))
+        return kind[:ng].copy(), value[:ng].copy(), glen[:ng].copy()
 
     def dt(self, h, hu, hv, cfl):
         h, hu, hv = _f64(h), _f64(hu), _f64(hv)

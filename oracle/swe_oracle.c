@@ -182,6 +182,8 @@ orc_mesh* orc_mesh_new(const double* nodes, int64_t n_nodes, const int32_t* tris
     M->kind[0] = ORC_BC_WALL;
     M->value[0] = 0.0;
     M->glen[0] = 0.0;
+    for (int64_t s = 0; s < 3 * n_cells; ++s)
+        if (M->nbr[s] < 0) M->glen[0] += M->len[s];
     return M;
 }
 
@@ -242,6 +244,17 @@ void orc_mesh_geometry(const orc_mesh* M, double* area, double* rin, int64_t* nb
 }
 
 int64_t orc_mesh_n_cells(const orc_mesh* M) { return M->n_cells; }
+
+/* Boundary groups: kind, value (Q or eta_s) and total edge length of each;
+ * returns the number of groups. */
+int orc_mesh_groups(const orc_mesh* M, int* kind, double* value, double* glen) {
+    for (int g = 0; g < M->n_groups; ++g) {
+        if (kind) kind[g] = M->kind[g];
+        if (value) value[g] = M->value[g];
+        if (glen) glen[g] = M->glen[g];
+    }
+    return M->n_groups;
+}
 
 /* ------------------------------------------------------------------------ */
 /* Riemann solver in the edge-normal frame (Eq 14, 17-26)                    */
