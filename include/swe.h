@@ -183,6 +183,44 @@ SWE_API int swe_get_info(swe_mesh* mesh, swe_info* info);
  * (the locality ordering).  perm: [n_tris] int64 host array. */
 SWE_API int swe_get_permutation(swe_mesh* mesh, int64_t* perm);
 
+/* ---- batched ensemble (uncertainty propagation: many runs of the same solver) ---- */
+
+typedef struct swe_ensemble swe_ensemble;
+
+/*
+ * Builds an ensemble from n_members meshes that all have a state (and the
+ * same precision, device, g and h_dry).  The members' device arrays are
+ * copied into one concatenated layout; the member meshes are not modified and
+ * may be destroyed afterwards.  Each member keeps its own CFL time step and
+ * time, continuing from its current state, and receives exactly the updates
+ * the plain solver (swe_step) would give it.  The ensemble uses the first
+ * member's stream until swe_ensemble_set_stream.
+ * Errors: SWE_EINVAL, SWE_ENOMEM, SWE_ECUDA.
+ */
+SWE_API int swe_ensemble_create(swe_mesh* const* members, int n_members, swe_ensemble** out);
+
+/* Releases the ensemble.  NULL is ignored. */
+SWE_API void swe_ensemble_destroy(swe_ensemble* ens);
+
+/* Sets the CUDA stream of all later ensemble calls. */
+SWE_API int swe_ensemble_set_stream(swe_ensemble* ens, void* cuda_stream);
+
+/*
+ * Advances every member nsteps steps (Eq 37, each with its own CFL step of
+ * Eq 15) as one CUDA-graph launch: each step is one kernel over all members'
+ * cells.  cfl: [n_members] host array, or NULL for 0.9.  t_out: NULL, or a
+ * [n_members] host array that receives each member's time (the call then
+ * waits and reports SWE_ENONFINITE / SWE_EDRY for the first failing member).
+ */
+SWE_API int swe_ensemble_step(swe_ensemble* ens, int64_t nsteps, const double* cfl, double* t_out);
+
+/* Copies member `member`'s state out in that member's caller cell order
+ * (host arrays: waits; device arrays: stream-ordered). */
+SWE_API int swe_ensemble_get_state(swe_ensemble* ens, int member, void* h, void* hu, void* hv, int where);
+
+/* Fills *info for one member (n_active counts all members together). */
+SWE_API int swe_ensemble_get_info(swe_ensemble* ens, int member, swe_info* info);
+
 /*
  * Evaluates the edge Riemann flux of the step kernel on n independent
  * normal-frame states (Eq 17-26, with the readings of the step kernel):

@@ -24,6 +24,7 @@ UNITS = [
     ("swe_capi.cu", []),
     ("swe_mesh.cu", []),
     ("swe_noalloc.cu", ["--use_fast_math"]),
+    ("swe_ensemble.cu", []),
 ]
 
 

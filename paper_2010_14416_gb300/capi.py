@@ -29,7 +29,8 @@ ERROR_NAMES = {1: "SWE_EINVAL", 2: "SWE_EMESH", 3: "SWE_ENOMEM", 4: "SWE_ECUDA",
 EXPORTS = ["swe_config_default", "swe_mesh_create", "swe_mesh_destroy", "swe_set_bc",
            "swe_set_stream", "swe_set_state", "swe_step", "swe_get_state", "swe_synchronize",
            "swe_get_info", "swe_get_permutation", "swe_mesh_preprocess", "swe_riemann_flux",
-           "swe_cfl_dt_noalloc", "swe_last_error"]
+           "swe_cfl_dt_noalloc", "swe_ensemble_create", "swe_ensemble_destroy", "swe_ensemble_set_stream",
+           "swe_ensemble_step", "swe_ensemble_get_state", "swe_ensemble_get_info", "swe_last_error"]
 
 
 class swe_config(C.Structure):
@@ -82,10 +83,17 @@ def load():
     lib.swe_mesh_preprocess.argtypes = [vp, C.c_int64, vp, C.c_int64, C.c_int, vp, vp, vp, vp, vp]
     lib.swe_cfl_dt_noalloc.argtypes = [C.c_int, C.c_int64, vp, vp, vp, vp, C.c_double, C.c_double,
                                        C.c_double, vp, vp]
+    lib.swe_ensemble_create.argtypes = [vp, C.c_int, C.POINTER(vp)]
+    lib.swe_ensemble_destroy.argtypes = [vp]
+    lib.swe_ensemble_destroy.restype = None
+    lib.swe_ensemble_set_stream.argtypes = [vp, vp]
+    lib.swe_ensemble_step.argtypes = [vp, C.c_int64, vp, vp]
+    lib.swe_ensemble_get_state.argtypes = [vp, C.c_int, vp, vp, vp, C.c_int]
+    lib.swe_ensemble_get_info.argtypes = [vp, C.c_int, C.POINTER(swe_info)]
     lib.swe_last_error.argtypes = []
     lib.swe_last_error.restype = C.c_char_p
     for name in EXPORTS:
-        if name not in ("swe_config_default", "swe_mesh_destroy", "swe_last_error"):
+        if name not in ("swe_config_default", "swe_mesh_destroy", "swe_ensemble_destroy", "swe_last_error"):
             getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -215,6 +223,53 @@ class Mesh:
         p = np.empty(self.n_cells, np.int64)
         check(load().swe_get_permutation(self._h, p.ctypes.data))
         return p
+
+
+class Ensemble:
+    """Members advanced together in one CUDA-graph launch per call."""
+
+    def __init__(self, meshes):
+        self.meshes = list(meshes)
+        arr = (C.c_void_p * len(self.meshes))(*[m.handle.value for m in self.meshes])
+        h = C.c_void_p()
+        check(load().swe_ensemble_create(arr, len(self.meshes), C.byref(h)))
+        self._h = h
+        self.n_members = len(self.meshes)
+        self.dtype = self.meshes[0].dtype
+
+    def close(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.swe_ensemble_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def set_stream(self, stream):
+        raw = getattr(stream, "cuda_stream", stream)
+        check(load().swe_ensemble_set_stream(self._h, C.c_void_p(raw or 0)))
+
+    def step(self, nsteps, cfl=None, sync=True):
+        c = None
+        if cfl is not None:
+            c = np.ascontiguousarray(np.broadcast_to(np.asarray(cfl, np.float64), (self.n_members,)))
+        t = np.zeros(self.n_members) if sync else None
+        check(load().swe_ensemble_step(self._h, int(nsteps), c.ctypes.data if c is not None else None,
+                                       t.ctypes.data if sync else None))
+        return t
+
+    def get_state(self, member, out=None):
+        n = self.meshes[member].n_cells
+        if out is None:
+            out = tuple(np.empty(n, self.dtype) for _ in range(3))
+        ptrs = [_ptr(o, self.dtype) for o in out]
+        check(load().swe_ensemble_get_state(self._h, int(member), ptrs[0][0], ptrs[1][0], ptrs[2][0], ptrs[0][1]))
+        return out
+
+    def info(self, member):
+        inf = swe_info()
+        check(load().swe_ensemble_get_info(self._h, int(member), C.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in swe_info._fields_}
 
 
 def mesh_preprocess(nodes, tris, reorder=SWE_REORDER_HILBERT):

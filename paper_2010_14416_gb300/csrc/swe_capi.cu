@@ -29,8 +29,6 @@ void set_error(const std::string& msg) { g_last_error = msg; }
 
 namespace {
 
-constexpr int kSmallWords = 8;
-constexpr int kSlotT = 3, kSlotStatus = 4, kSlotClamp = 5, kSlotActive = 6;
 constexpr int kDefaultGraphSteps = 48;
 
 struct DeviceGuard {
@@ -66,34 +64,6 @@ __global__ void init_small_kernel(unsigned long long* small, double t) {
 
 using namespace swe;
 
-struct swe_mesh {
-    swe_config cfg{};
-    HostMesh hm;
-    cudaStream_t stream = nullptr;
-    cudaStream_t cap_stream = nullptr;
-    size_t esz = 8;                    // sizeof(T)
-    void* state[2] = {nullptr, nullptr};
-    void* geoA = nullptr;
-    void* geoB = nullptr;
-    int4* topo = nullptr;
-    void* gm2 = nullptr;
-    void* zdev = nullptr;
-    long long* perm = nullptr;
-    void* stage[3] = {nullptr, nullptr, nullptr};
-    unsigned long long* small = nullptr;
-    BcTable bc{};
-    std::vector<double> group_len;     // total edge length per group
-    std::vector<double> group_value;   // Q or eta_s as given
-    int n_groups = 1;
-    bool topo_dirty = false;
-    bool have_state = false;
-    int64_t nstep = 0;
-    cudaGraphExec_t graph = nullptr;
-    int graph_len = 0;
-    double graph_cfl = -1.0;
-    int64_t device_bytes = 0;
-    unsigned grid = 0;                 // blocks of the step kernel (about one resident wave)
-};
 
 namespace {
 

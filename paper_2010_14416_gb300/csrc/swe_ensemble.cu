@@ -1,0 +1,490 @@
+// swe_ensemble.cu -- batched ensemble of meshes advanced together
+// (swe_ensemble_* in include/swe.h).
+//
+// The members' device arrays are copied into one concatenated layout, each
+// member padded to whole tiles of kEnsBlock cells.  Padding cells are dry
+// cells with three wall edges: they take the quiet path and never change.
+// Neighbour codes are offset to the concatenated numbering and boundary
+// groups to one global table (group 0 = wall).  Every member keeps its own
+// status block (dt slots, time, status, clamps) and CFL number, so each member
+// takes exactly the steps the plain solver would take on it.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "swe_internal.h"
+
+using namespace swe;
+
+struct swe_ensemble {
+    int precision = SWE_FP64;
+    int device = 0;
+    size_t esz = 8;
+    int n_members = 0;
+    double g = 9.81, h_dry = 1e-6;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    std::vector<int64_t> base, n_cells, first_tile;
+    int64_t n_total = 0, n_tiles = 0;
+    void* state[2] = {nullptr, nullptr};
+    void* geoA = nullptr;
+    void* geoB = nullptr;
+    int4* topo = nullptr;
+    void* gm2 = nullptr;
+    long long* perm = nullptr;        // per member, relative to the member's base
+    int* tile_member = nullptr;
+    long long* member_first_tile = nullptr;
+    double* cfl = nullptr;
+    unsigned long long* small = nullptr;
+    unsigned long long* n_active = nullptr;
+    int* kind = nullptr;
+    double* value = nullptr;
+    void* stage[3] = {nullptr, nullptr, nullptr};
+    int64_t stage_cells = 0;
+    unsigned grid = 0;
+    int64_t nstep = 0;
+    std::vector<double> cfl_host;
+    // graphs keyed by (start step mod 6, length)
+    std::map<std::pair<int, int64_t>, cudaGraphExec_t> graphs;
+    int64_t device_bytes = 0;
+};
+
+namespace {
+
+int efail(cudaError_t e, const char* what) {
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return SWE_ECUDA;
+}
+
+struct EnsDeviceGuard {
+    int prev = -1;
+    explicit EnsDeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~EnsDeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int ens_alloc(swe_ensemble* E, void** p, size_t bytes, const char* what) {
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        set_error(std::string("swe_ensemble_create: device allocation failed for ") + what);
+        return SWE_ENOMEM;
+    }
+    E->device_bytes += (int64_t)bytes;
+    return SWE_OK;
+}
+
+void drop_graphs(swe_ensemble* E) {
+    for (auto& kv : E->graphs) cudaGraphExecDestroy(kv.second);
+    E->graphs.clear();
+}
+
+__global__ void ens_init_small_kernel(unsigned long long* small, const unsigned long long* first_slot,
+                                      const double* t0, int n_members) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n_members) {
+        unsigned long long* s = small + 8 * (long long)k;
+        s[0] = first_slot[k];
+        s[1] = kInfBits;
+        s[2] = kInfBits;
+        s[3] = (unsigned long long)__double_as_longlong(t0[k]);
+        s[4] = 0ULL; s[5] = 0ULL; s[6] = 0ULL; s[7] = 0ULL;
+    }
+}
+
+template <typename T>
+__global__ void ens_unpack_kernel(const V4<T>* __restrict__ s, const long long* __restrict__ perm, long long base,
+                                  T* __restrict__ h, T* __restrict__ hu, T* __restrict__ hv, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const long long o = perm[base + i];
+        const V4<T> v = s[base + i];
+        h[o] = v.x; hu[o] = v.y; hv[o] = v.z;
+    }
+}
+
+template <typename T>
+EnsArgs<T> ens_args(swe_ensemble* E, int64_t step_index) {
+    EnsArgs<T> a;
+    const int p2 = (int)(step_index % 2), p3 = (int)(step_index % 3);
+    a.s_in = (const V4<T>*)E->state[p2];
+    a.s_out = (V4<T>*)E->state[1 - p2];
+    a.geoA = (const V4<T>*)E->geoA;
+    a.geoB = (const V4<T>*)E->geoB;
+    a.topo = E->topo;
+    a.gm2 = (const T*)E->gm2;
+    a.tile_member = E->tile_member;
+    a.member_first_tile = E->member_first_tile;
+    a.cfl = E->cfl;
+    a.small = E->small;
+    a.kind_ = E->kind;
+    a.value_ = E->value;
+    a.n_active = E->n_active;
+    a.n_tiles = E->n_tiles;
+    a.slot_read = p3;
+    a.slot_write = (p3 + 1) % 3;
+    a.slot_reset = (p3 + 2) % 3;
+    a.g = (T)9.81;
+    a.h_dry = (T)1e-6;
+    return a;
+}
+
+struct EnsPhysics {
+    double g, h_dry;
+};
+
+template <typename T>
+cudaError_t ens_launch(swe_ensemble* E, int64_t step_index, const EnsPhysics& ph, cudaStream_t st) {
+    EnsArgs<T> a = ens_args<T>(E, step_index);
+    a.g = (T)ph.g;
+    a.h_dry = (T)ph.h_dry;
+    return Launch<T>::ensemble_step(a, E->grid, st);
+}
+
+template <typename T>
+int ens_build(swe_ensemble* E, swe_mesh* const* M) {
+    const int nm = E->n_members;
+    const size_t v4 = sizeof(V4<T>);
+    // offsets, padded to whole tiles
+    E->base.resize(nm);
+    E->n_cells.resize(nm);
+    E->first_tile.resize(nm);
+    int64_t off = 0;
+    for (int k = 0; k < nm; ++k) {
+        E->base[k] = off;
+        E->n_cells[k] = M[k]->hm.n_cells;
+        E->first_tile[k] = off / kEnsBlock;
+        off += (M[k]->hm.n_cells + kEnsBlock - 1) / kEnsBlock * kEnsBlock;
+    }
+    E->n_total = off;
+    E->n_tiles = off / kEnsBlock;
+    if (E->n_total >= (int64_t)kNbrMask) { set_error("swe_ensemble_create: too many cells in total"); return SWE_EINVAL; }
+    int rc;
+    if ((rc = ens_alloc(E, &E->state[0], off * v4, "state")) || (rc = ens_alloc(E, &E->state[1], off * v4, "state")) ||
+        (rc = ens_alloc(E, &E->geoA, off * v4, "geometry")) || (rc = ens_alloc(E, &E->geoB, off * v4, "geometry")) ||
+        (rc = ens_alloc(E, (void**)&E->topo, off * sizeof(int4), "topology")) ||
+        (rc = ens_alloc(E, &E->gm2, off * sizeof(T), "manning")) ||
+        (rc = ens_alloc(E, (void**)&E->perm, off * sizeof(long long), "permutation")) ||
+        (rc = ens_alloc(E, (void**)&E->tile_member, E->n_tiles * sizeof(int), "tiles")) ||
+        (rc = ens_alloc(E, (void**)&E->member_first_tile, nm * sizeof(long long), "tiles")) ||
+        (rc = ens_alloc(E, (void**)&E->cfl, nm * sizeof(double), "cfl")) ||
+        (rc = ens_alloc(E, (void**)&E->small, nm * 8 * sizeof(unsigned long long), "status")) ||
+        (rc = ens_alloc(E, (void**)&E->n_active, sizeof(unsigned long long), "status")))
+        return rc;
+    cudaStream_t st = E->stream;
+    cudaError_t e = cudaSuccess;
+    // zero everything that padding cells read (state, topology filled below)
+    for (void* p : {E->state[0], E->state[1], E->geoA, E->geoB, E->gm2})
+        if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, p == E->gm2 ? off * sizeof(T) : off * v4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(E->n_active, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return efail(e, "swe_ensemble_create: clear");
+    // global boundary groups: 0 = wall, then each member's groups
+    std::vector<int> kinds{kBcWall};
+    std::vector<double> values{0.0};
+    std::vector<int> gbase(nm);
+    for (int k = 0; k < nm; ++k) {
+        gbase[k] = (int)kinds.size();
+        for (int gI = 0; gI < M[k]->n_groups; ++gI) {
+            kinds.push_back(M[k]->bc.kind[gI]);
+            values.push_back(M[k]->bc.value[gI]);
+        }
+    }
+    if ((rc = ens_alloc(E, (void**)&E->kind, kinds.size() * sizeof(int), "boundary groups")) ||
+        (rc = ens_alloc(E, (void**)&E->value, values.size() * sizeof(double), "boundary groups")))
+        return rc;
+    e = cudaMemcpy(E->kind, kinds.data(), kinds.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(E->value, values.data(), values.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return efail(e, "swe_ensemble_create: boundary groups");
+    // per-member device copies and host-built topology / tile tables
+    std::vector<int4> topo(off);
+    std::vector<long long> perm(off, 0);
+    std::vector<int> tile_member(E->n_tiles);
+    const int wall_code = -1;  // global group 0
+    for (int k = 0; k < nm; ++k) {
+        const swe_mesh* m = M[k];
+        const int64_t b = E->base[k], n = E->n_cells[k];
+        const void* cur = m->state[m->nstep % 2];
+        e = cudaMemcpyAsync((char*)E->state[0] + b * v4, cur, n * v4, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync((char*)E->geoA + b * v4, m->geoA, n * v4, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync((char*)E->geoB + b * v4, m->geoB, n * v4, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync((char*)E->gm2 + b * sizeof(T), m->gm2, n * sizeof(T),
+                                                  cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return efail(e, "swe_ensemble_create: copy");
+        for (int64_t c = 0; c < n; ++c) {
+            int code[3];
+            for (int j = 0; j < 3; ++j) {
+                const int32_t v = m->hm.code[3 * c + j];
+                code[j] = v >= 0 ? (int)((v & kNbrMask) + b) | (v & kFlipBit) : -1 - (gbase[k] + (-1 - v));
+            }
+            int w = 0;
+            if (sizeof(T) == 4) {
+                const float gm2 = (float)(m->cfg.g * m->hm.m[c] * m->hm.m[c]);
+                std::memcpy(&w, &gm2, sizeof w);
+            }
+            topo[b + c] = make_int4(code[0], code[1], code[2], w);
+            perm[b + c] = m->hm.perm[c];
+        }
+        for (int64_t c = n; c < (E->n_cells[k] + kEnsBlock - 1) / kEnsBlock * kEnsBlock; ++c)
+            topo[b + c] = make_int4(wall_code, wall_code, wall_code, 0);
+        const int64_t t0 = E->first_tile[k];
+        const int64_t t1 = (b + (n + kEnsBlock - 1) / kEnsBlock * kEnsBlock) / kEnsBlock;
+        for (int64_t t = t0; t < t1; ++t) tile_member[t] = k;
+    }
+    std::vector<long long> mft(E->first_tile.begin(), E->first_tile.end());
+    e = cudaMemcpyAsync(E->topo, topo.data(), off * sizeof(int4), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(E->perm, perm.data(), off * sizeof(long long), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(E->tile_member, tile_member.data(), E->n_tiles * sizeof(int), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(E->member_first_tile, mft.data(), nm * sizeof(long long), cudaMemcpyHostToDevice, st);
+    // each member's status block starts from its current CFL minimum and time
+    std::vector<unsigned long long> first(nm);
+    std::vector<double> t0(nm);
+    for (int k = 0; k < nm && e == cudaSuccess; ++k) {
+        unsigned long long s[kSmallWords];
+        e = cudaMemcpy(s, M[k]->small, sizeof s, cudaMemcpyDeviceToHost);
+        first[k] = s[M[k]->nstep % 3];
+        std::memcpy(&t0[k], &s[kSlotT], sizeof(double));
+    }
+    unsigned long long* d_first = nullptr;
+    double* d_t0 = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&d_first, nm * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&d_t0, nm * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpy(d_first, first.data(), nm * sizeof(unsigned long long), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_t0, t0.data(), nm * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        ens_init_small_kernel<<<(nm + 127) / 128, 128, 0, st>>>(E->small, d_first, d_t0, nm);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(E->state[1], E->state[0], off * v4, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (d_first) cudaFree(d_first);
+    if (d_t0) cudaFree(d_t0);
+    if (e != cudaSuccess) return efail(e, "swe_ensemble_create: upload");
+    int per_sm = 0, sms = 0;
+    e = Launch<T>::ensemble_resident_blocks(&per_sm);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, E->device);
+    if (e != cudaSuccess) return efail(e, "swe_ensemble_create: occupancy");
+    E->grid = (unsigned)std::min<long long>(E->n_tiles, (long long)std::max(per_sm, 1) * std::max(sms, 1));
+    E->cfl_host.assign(nm, -1.0);
+    return SWE_OK;
+}
+
+template <typename T>
+int ens_capture(swe_ensemble* E, int64_t start, int64_t len, const EnsPhysics& ph, cudaGraphExec_t* out) {
+    cudaError_t e = cudaStreamBeginCapture(E->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return efail(e, "swe_ensemble_step: begin capture");
+    cudaError_t le = cudaSuccess;
+    for (int64_t s = 0; s < len && le == cudaSuccess; ++s) le = ens_launch<T>(E, start + s, ph, E->cap_stream);
+    cudaGraph_t gr = nullptr;
+    e = cudaStreamEndCapture(E->cap_stream, &gr);
+    if (le != cudaSuccess) { if (gr) cudaGraphDestroy(gr); return efail(le, "swe_ensemble_step: capture launch"); }
+    if (e != cudaSuccess) return efail(e, "swe_ensemble_step: end capture");
+    e = cudaGraphInstantiate(out, gr, 0);
+    cudaGraphDestroy(gr);
+    if (e != cudaSuccess) return efail(e, "swe_ensemble_step: instantiate");
+    return SWE_OK;
+}
+
+template <typename T>
+int ens_get_state(swe_ensemble* E, int k, void* h, void* hu, void* hv, int where) {
+    const int64_t n = E->n_cells[k];
+    const V4<T>* cur = (const V4<T>*)E->state[E->nstep % 2];
+    cudaError_t e;
+    const unsigned grid = (unsigned)((n + 255) / 256);
+    if (where == SWE_DEVICE) {
+        ens_unpack_kernel<T><<<grid, 256, 0, E->stream>>>(cur, E->perm, E->base[k], (T*)h, (T*)hu, (T*)hv, n);
+        e = cudaGetLastError();
+        return e == cudaSuccess ? SWE_OK : efail(e, "swe_ensemble_get_state");
+    }
+    if (E->stage_cells < n) {
+        for (int j = 0; j < 3; ++j) {
+            if (E->stage[j]) cudaFree(E->stage[j]);
+            E->stage[j] = nullptr;
+            e = cudaMalloc(&E->stage[j], n * sizeof(T));
+            if (e != cudaSuccess) { E->stage_cells = 0; return efail(e, "swe_ensemble_get_state: staging"); }
+        }
+        E->stage_cells = n;
+    }
+    ens_unpack_kernel<T><<<grid, 256, 0, E->stream>>>(cur, E->perm, E->base[k], (T*)E->stage[0], (T*)E->stage[1],
+                                                      (T*)E->stage[2], n);
+    e = cudaGetLastError();
+    void* dst[3] = {h, hu, hv};
+    for (int j = 0; j < 3 && e == cudaSuccess; ++j)
+        e = cudaMemcpyAsync(dst[j], E->stage[j], n * sizeof(T), cudaMemcpyDeviceToHost, E->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(E->stream);
+    return e == cudaSuccess ? SWE_OK : efail(e, "swe_ensemble_get_state");
+}
+
+}  // namespace
+
+extern "C" {
+
+void swe_ensemble_destroy(swe_ensemble* E) {
+    if (!E) return;
+    EnsDeviceGuard dg(E->device);
+    if (E->stream) cudaStreamSynchronize(E->stream);
+    drop_graphs(E);
+    void* bufs[] = {E->state[0], E->state[1], E->geoA, E->geoB, E->topo, E->gm2, E->perm, E->tile_member,
+                    E->member_first_tile, E->cfl, E->small, E->n_active, E->kind, E->value,
+                    E->stage[0], E->stage[1], E->stage[2]};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    if (E->cap_stream) cudaStreamDestroy(E->cap_stream);
+    delete E;
+}
+
+int swe_ensemble_create(swe_mesh* const* members, int n_members, swe_ensemble** out) {
+    if (!out) { set_error("swe_ensemble_create: out is NULL"); return SWE_EINVAL; }
+    *out = nullptr;
+    if (!members || n_members < 1) { set_error("swe_ensemble_create: no members"); return SWE_EINVAL; }
+    for (int k = 0; k < n_members; ++k) {
+        const swe_mesh* m = members[k];
+        if (!m) { set_error("swe_ensemble_create: NULL member"); return SWE_EINVAL; }
+        if (!m->have_state) { set_error("swe_ensemble_create: member " + std::to_string(k) + " has no state"); return SWE_EINVAL; }
+        if (m->cfg.precision != members[0]->cfg.precision || m->cfg.device != members[0]->cfg.device ||
+            m->cfg.g != members[0]->cfg.g || m->cfg.h_dry != members[0]->cfg.h_dry) {
+            set_error("swe_ensemble_create: members differ in precision, device, g or h_dry");
+            return SWE_EINVAL;
+        }
+        if (m->topo_dirty) { set_error("swe_ensemble_create: member boundary groups not applied"); return SWE_EINVAL; }
+    }
+    swe_ensemble* E = new (std::nothrow) swe_ensemble();
+    if (!E) { set_error("swe_ensemble_create: out of host memory"); return SWE_ENOMEM; }
+    E->precision = members[0]->cfg.precision;
+    E->device = members[0]->cfg.device;
+    E->esz = E->precision == SWE_FP32 ? 4 : 8;
+    E->n_members = n_members;
+    E->g = members[0]->cfg.g;
+    E->h_dry = members[0]->cfg.h_dry;
+    E->stream = members[0]->stream;
+    EnsDeviceGuard dg(E->device);
+    for (int k = 0; k < n_members; ++k) {
+        cudaError_t e = cudaStreamSynchronize(members[k]->stream);
+        if (e != cudaSuccess) { swe_ensemble_destroy(E); return efail(e, "swe_ensemble_create: member stream"); }
+    }
+    cudaError_t e = cudaStreamCreateWithFlags(&E->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { swe_ensemble_destroy(E); return efail(e, "swe_ensemble_create: stream"); }
+    int rc;
+    try {
+        rc = E->precision == SWE_FP32 ? ens_build<float>(E, members) : ens_build<double>(E, members);
+    } catch (const std::bad_alloc&) {
+        set_error("swe_ensemble_create: out of host memory");
+        rc = SWE_ENOMEM;
+    }
+    if (rc) { swe_ensemble_destroy(E); return rc; }
+    *out = E;
+    return SWE_OK;
+}
+
+int swe_ensemble_set_stream(swe_ensemble* E, void* stream) {
+    if (!E) { set_error("swe_ensemble_set_stream: NULL ensemble"); return SWE_EINVAL; }
+    E->stream = (cudaStream_t)stream;
+    return SWE_OK;
+}
+
+int swe_ensemble_step(swe_ensemble* E, int64_t nsteps, const double* cfl, double* t_out) {
+    if (!E || nsteps < 0) { set_error("swe_ensemble_step: bad arguments"); return SWE_EINVAL; }
+    EnsDeviceGuard dg(E->device);
+    std::vector<double> c(E->n_members, 0.9);
+    if (cfl)
+        for (int k = 0; k < E->n_members; ++k) {
+            if (!(cfl[k] > 0.0) || !std::isfinite(cfl[k])) { set_error("swe_ensemble_step: bad cfl"); return SWE_EINVAL; }
+            c[k] = cfl[k];
+        }
+    cudaError_t e;
+    if (c != E->cfl_host) {
+        e = cudaMemcpyAsync(E->cfl, c.data(), c.size() * sizeof(double), cudaMemcpyHostToDevice, E->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(E->stream);
+        if (e != cudaSuccess) return efail(e, "swe_ensemble_step: cfl");
+        E->cfl_host = c;
+    }
+    const EnsPhysics ph{E->g, E->h_dry};
+    if (nsteps > 0) {
+        // the whole call is one CUDA graph: nsteps step kernels over all members
+        const auto key = std::make_pair((int)(E->nstep % 6), nsteps);
+        auto it = E->graphs.find(key);
+        cudaGraphExec_t ge = nullptr;
+        if (it == E->graphs.end()) {
+            if (E->graphs.size() >= 8) drop_graphs(E);
+            int rc = E->precision == SWE_FP32 ? ens_capture<float>(E, E->nstep % 6, nsteps, ph, &ge)
+                                              : ens_capture<double>(E, E->nstep % 6, nsteps, ph, &ge);
+            if (rc) return rc;
+            E->graphs[key] = ge;
+        } else {
+            ge = it->second;
+        }
+        e = cudaGraphLaunch(ge, E->stream);
+        if (e != cudaSuccess) return efail(e, "swe_ensemble_step: graph launch");
+        E->nstep += nsteps;
+    }
+    if (t_out) {
+        std::vector<unsigned long long> s(8 * (size_t)E->n_members);
+        e = cudaMemcpyAsync(s.data(), E->small, s.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                            E->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(E->stream);
+        if (e != cudaSuccess) return efail(e, "swe_ensemble_step: status");
+        int rc = SWE_OK;
+        for (int k = 0; k < E->n_members; ++k) {
+            std::memcpy(&t_out[k], &s[8 * k + kSlotT], sizeof(double));
+            if ((s[8 * k + kSlotStatus] & kStatusNonFinite) && !rc) {
+                set_error("swe_ensemble_step: member " + std::to_string(k) + " has a non-finite state");
+                rc = SWE_ENONFINITE;
+            } else if ((s[8 * k + kSlotStatus] & kStatusDry) && !rc) {
+                set_error("swe_ensemble_step: member " + std::to_string(k) + " is completely dry");
+                rc = SWE_EDRY;
+            }
+        }
+        return rc;
+    }
+    return SWE_OK;
+}
+
+int swe_ensemble_get_state(swe_ensemble* E, int member, void* h, void* hu, void* hv, int where) {
+    if (!E || member < 0 || member >= E->n_members || !h || !hu || !hv || (where != SWE_HOST && where != SWE_DEVICE)) {
+        set_error("swe_ensemble_get_state: bad arguments");
+        return SWE_EINVAL;
+    }
+    EnsDeviceGuard dg(E->device);
+    return E->precision == SWE_FP32 ? ens_get_state<float>(E, member, h, hu, hv, where)
+                                    : ens_get_state<double>(E, member, h, hu, hv, where);
+}
+
+int swe_ensemble_get_info(swe_ensemble* E, int member, swe_info* info) {
+    if (!E || !info || member < 0 || member >= E->n_members) {
+        set_error("swe_ensemble_get_info: bad arguments");
+        return SWE_EINVAL;
+    }
+    EnsDeviceGuard dg(E->device);
+    unsigned long long s[8];
+    unsigned long long act = 0;
+    cudaError_t e = cudaMemcpyAsync(s, E->small + 8 * (size_t)member, sizeof s, cudaMemcpyDeviceToHost, E->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&act, E->n_active, sizeof act, cudaMemcpyDeviceToHost, E->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(E->stream);
+    if (e != cudaSuccess) return efail(e, "swe_ensemble_get_info");
+    std::memset(info, 0, sizeof *info);
+    info->n_cells = E->n_cells[member];
+    info->n_steps = E->nstep;
+    info->n_clamped = (int64_t)s[kSlotClamp];
+    std::memcpy(&info->t, &s[kSlotT], sizeof(double));
+    std::memcpy(&info->dt_next, &s[E->nstep % 3], sizeof(double));
+    info->precision = E->precision;
+    info->status = (s[kSlotStatus] & kStatusNonFinite) ? SWE_ENONFINITE : ((s[kSlotStatus] & kStatusDry) ? SWE_EDRY : SWE_OK);
+    info->device_bytes = E->device_bytes;
+    info->n_active = (int64_t)act;  // all members together
+    return SWE_OK;
+}
+
+}  // extern "C"

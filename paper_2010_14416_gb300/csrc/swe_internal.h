@@ -42,4 +42,40 @@ std::vector<int64_t> order_rcm(int64_t n, const std::vector<int64_t>& nbr /* [n]
 // Thread-local error message of the C ABI.
 void set_error(const std::string& msg);
 
+// Words of a mesh's device status block.
+constexpr int kSmallWords = 8;
+constexpr int kSlotT = 3, kSlotStatus = 4, kSlotClamp = 5, kSlotActive = 6;
+
 }  // namespace swe
+
+// One mesh: host preprocessing result, device arrays and stepping state.
+struct swe_mesh {
+    swe_config cfg{};
+    swe::HostMesh hm;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    size_t esz = 8;                    // sizeof(T)
+    void* state[2] = {nullptr, nullptr};
+    void* geoA = nullptr;
+    void* geoB = nullptr;
+    int4* topo = nullptr;
+    void* gm2 = nullptr;
+    void* zdev = nullptr;
+    long long* perm = nullptr;
+    void* stage[3] = {nullptr, nullptr, nullptr};
+    unsigned long long* small = nullptr;
+    swe::BcTable bc{};
+    std::vector<double> group_len;     // total edge length per group
+    std::vector<double> group_value;   // Q or eta_s as given
+    int n_groups = 1;
+    bool topo_dirty = false;
+    bool have_state = false;
+    int64_t nstep = 0;
+    cudaGraphExec_t graph = nullptr;
+    int graph_len = 0;
+    double graph_cfl = -1.0;
+    int64_t device_bytes = 0;
+    unsigned grid = 0;                 // blocks of the step kernel (about one resident wave)
+};
+
+

@@ -30,6 +30,8 @@ constexpr unsigned kStatusDry = 2u;
 
 constexpr int kBcWall = 0, kBcInflow = 1, kBcTransmissive = 2, kBcStage = 3;
 
+constexpr int kEnsBlock = 256;  // tile of the batched ensemble step (one member per tile)
+
 template <typename T>
 struct alignas(4 * sizeof(T)) V4 {
     T x, y, z, w;
@@ -62,6 +64,33 @@ struct StepArgs {
     double cfl;
     T g, h_dry;
     BcTable bc;
+    __device__ __forceinline__ int bc_kind(int grp) const { return bc.kind[grp]; }
+    __device__ __forceinline__ double bc_value(int grp) const { return bc.value[grp]; }
+};
+
+// Arguments of the batched ensemble step: the members' cells are concatenated,
+// each member padded to whole tiles of BLOCK cells (padding cells are dry and
+// walled in, so they take the quiet path); every tile belongs to one member.
+template <typename T>
+struct EnsArgs {
+    const V4<T>* __restrict__ s_in;
+    V4<T>* __restrict__ s_out;
+    const V4<T>* __restrict__ geoA;
+    const V4<T>* __restrict__ geoB;
+    const int4* __restrict__ topo;     // neighbour codes offset to the concatenated numbering
+    const T* __restrict__ gm2;         // FP64 only
+    const int* __restrict__ tile_member;
+    const long long* __restrict__ member_first_tile;
+    const double* __restrict__ cfl;    // per member
+    unsigned long long* small;         // per member: 8 words (dt slots 0..2, t, status, clamps, -, -)
+    const int* __restrict__ kind_;     // global boundary groups (0 = wall)
+    const double* __restrict__ value_;
+    unsigned long long* n_active;      // all members (diagnostic)
+    long long n_tiles;
+    int slot_read, slot_write, slot_reset;
+    T g, h_dry;
+    __device__ __forceinline__ int bc_kind(int grp) const { return kind_[grp]; }
+    __device__ __forceinline__ double bc_value(int grp) const { return value_[grp]; }
 };
 
 // ---- precision-specific arithmetic ------------------------------------------------
@@ -175,14 +204,12 @@ __device__ __forceinline__ void block_min_publish(double cand, unsigned long lon
 }
 
 // ---- Manning factor g m^2: packed in topo.w (FP32) or its own array (FP64) --------
-template <typename T>
-__device__ __forceinline__ T load_gm2(const StepArgs<T>& a, long long i, const int4& tp);
-template <>
-__device__ __forceinline__ float load_gm2<float>(const StepArgs<float>&, long long, const int4& tp) {
+template <typename Args>
+__device__ __forceinline__ float load_gm2(const Args&, long long, const int4& tp, float) {
     return __int_as_float(tp.w);
 }
-template <>
-__device__ __forceinline__ double load_gm2<double>(const StepArgs<double>& a, long long i, const int4&) {
+template <typename Args>
+__device__ __forceinline__ double load_gm2(const Args& a, long long i, const int4&, double) {
     return a.gm2[i];
 }
 
@@ -222,9 +249,9 @@ __device__ __forceinline__ void cp_async_wait() {
 // its momentum is set to zero by the dry-cell rule after the update.  Its new
 // state is therefore (h, 0, 0) bit for bit whatever the momentum terms were,
 // and the edge loop, geometry and friction are skipped.
-template <typename T>
-__device__ __forceinline__ T update_cell(const StepArgs<T>& a, long long i, const V4<T>& own, const int4& tp,
-                                         T dt, unsigned& active) {
+template <typename T, typename Args>
+__device__ __forceinline__ T update_cell(const Args& a, long long i, const V4<T>& own, const int4& tp, T dt,
+                                         unsigned& active, unsigned long long* n_clamped, unsigned* status) {
     using A = Ar<T>;
     const T g = a.g, h_dry = a.h_dry;
     const T hi = own.x, zi = own.w;
@@ -239,7 +266,7 @@ __device__ __forceinline__ T update_cell(const StepArgs<T>& a, long long i, cons
         if (code[j] >= 0) {
             quiet = quiet && !(nb[j].x > h_dry);
         } else {
-            const int kind = a.bc.kind[-1 - code[j]];
+            const int kind = a.bc_kind(-1 - code[j]);
             quiet = quiet && (kind == kBcWall || kind == kBcTransmissive);
         }
     }
@@ -252,7 +279,7 @@ __device__ __forceinline__ T update_cell(const StepArgs<T>& a, long long i, cons
     }
     active += 1u;
     const V4<T> gA = a.geoA[i], gB = a.geoB[i];
-    const T gm2 = load_gm2<T>(a, i, tp);
+    const T gm2 = load_gm2(a, i, tp, T(0));
     T ui = T(0), vi = T(0);
     if (hi > h_dry) { const T r = A::rcp_(hi); ui = own.y * r; vi = own.z * r; }
     T f0 = T(0), f1 = T(0), f2 = T(0), sx = T(0), sy = T(0);
@@ -297,19 +324,19 @@ __device__ __forceinline__ T update_cell(const StepArgs<T>& a, long long i, cons
             sy += src * ly;
         } else {
             const int grp = -1 - c;
-            const int kind = a.bc.kind[grp];
+            const int kind = a.bc_kind(grp);
             const T un = ui * n1 + vi * n2, ut = vi * n1 - ui * n2;
             T G1, G2, G3;
             if (kind == kBcWall) {
                 G1 = T(0); G2 = T(0.5) * g * hi * hi; G3 = T(0);
             } else if (kind == kBcInflow) {
-                const T q = T(a.bc.value[grp]);
+                const T q = T(a.bc_value(grp));
                 G1 = -q;
                 G2 = T(0.5) * g * hi * hi + (hi > h_dry ? A::div_(q * q, hi) : T(0));
                 G3 = T(0);
             } else {
                 T hg = hi;
-                if (kind == kBcStage) hg = tmax(T(0), T(a.bc.value[grp]) - zi);
+                if (kind == kBcStage) hg = tmax(T(0), T(a.bc_value(grp)) - zi);
                 riemann_hllc<T>(hi, un, ut, hg, un, ut, g, h_dry, G1, G2, G3);
             }
             F0 = G1;
@@ -352,13 +379,13 @@ __device__ __forceinline__ T update_cell(const StepArgs<T>& a, long long i, cons
     out.z = qy + dqy;
     if (out.x < T(0)) {
         out.x = T(0); out.y = T(0); out.z = T(0);
-        atomicAdd(a.n_clamped, 1ULL);
+        atomicAdd(n_clamped, 1ULL);
     } else if (out.x <= h_dry) {
         out.y = T(0); out.z = T(0);
     }
     const T big = T(3.0e38);
     if (!(out.x < big) || !(fabs(out.y) < big) || !(fabs(out.z) < big))
-        atomicOr(a.status, kStatusNonFinite);
+        atomicOr(status, kStatusNonFinite);
     a.s_out[i] = out;
     // next CFL candidate (Eq 15), R_i / (sqrt(g h) + |u|) on the new state
     T cand = inf_of<T>();
@@ -396,7 +423,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_kernel(const StepArgs<T> a) 
         for (; i < a.n; i += stride) {
             const V4<T> own = a.s_in[i];
             const int4 tp = a.topo[i];
-            cand = tmin(cand, update_cell<T>(a, i, own, tp, dt, active));
+            cand = tmin(cand, update_cell<T>(a, i, own, tp, dt, active, a.n_clamped, a.status));
         }
     } else {
         __shared__ V4<T> st_own[STAGES][BLOCK];
@@ -424,12 +451,113 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_kernel(const StepArgs<T> a) 
             cp_async_wait<STAGES - 1>();
             const V4<T> own = st_own[slot][tid];
             const int4 tp = st_topo[slot][tid];
-            cand = tmin(cand, update_cell<T>(a, i, own, tp, dt, active));
+            cand = tmin(cand, update_cell<T>(a, i, own, tp, dt, active, a.n_clamped, a.status));
             slot = slot == STAGES - 1 ? 0 : slot + 1;
         }
         cp_async_wait<0>();
     }
     block_min_publish<BLOCK>((double)cand, a.dt_write, active, a.n_active);
+}
+
+// ---- batched ensemble step -------------------------------------------------------
+// Members advance together, each with its own CFL step: one launch covers every
+// member's cells.  When a block moves on to another member, its warps publish
+// the finished member's CFL minimum (warp shuffle, one atomicMin per warp, no
+// barrier).
+template <typename T>
+__device__ __forceinline__ void warp_min_publish(T cand, unsigned long long* dst) {
+    double v = (double)cand;
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0 && v < __longlong_as_double((long long)kInfBits))
+        atomicMin(dst, (unsigned long long)__double_as_longlong(v));
+}
+
+// Tiles are dealt to blocks in round-robin chunks of kEnsChunk tiles, which
+// balances wet (expensive) and dry (cheap) members across the GPU while the
+// member still changes only at chunk or member boundaries.
+constexpr int kEnsChunk = 8;
+
+__device__ __forceinline__ long long ens_tile_of(long long k, long long nchunk_stride, long long b) {
+    return (b + (k / kEnsChunk) * nchunk_stride) * kEnsChunk + (k % kEnsChunk);
+}
+
+template <typename T, int BLOCK, int MINB, int STAGES>
+__global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel(const EnsArgs<T> a) {
+    const long long G = gridDim.x, b = blockIdx.x;
+    const long long n_chunks = (a.n_tiles + kEnsChunk - 1) / kEnsChunk;
+    // this block's chunks: b, b + G, b + 2G, ... ; k counts its tiles
+    const long long my_chunks = b < n_chunks ? (n_chunks - 1 - b) / G + 1 : 0;
+    const long long k_end = my_chunks * kEnsChunk;
+    const int tid = threadIdx.x;
+    int member = -1;
+    unsigned long long* sm = nullptr;
+    bool have_dt = false;
+    T dt = T(0);
+    T cand = inf_of<T>();
+    unsigned active = 0u;
+    __shared__ V4<T> st_own[STAGES > 1 ? STAGES : 1][BLOCK];
+    __shared__ int4 st_topo[STAGES > 1 ? STAGES : 1][BLOCK];
+    if constexpr (STAGES > 1) {
+#pragma unroll
+        for (int s = 0; s < STAGES - 1; ++s) {
+            const long long tile = ens_tile_of(s, G, b);
+            if (s < k_end && tile < a.n_tiles) {
+                const long long c = tile * BLOCK + tid;
+                cp_async_record<sizeof(V4<T>)>(&st_own[s][tid], &a.s_in[c]);
+                cp_async_record<16>(&st_topo[s][tid], &a.topo[c]);
+            }
+            cp_async_commit();
+        }
+    }
+    int slot = 0;
+    for (long long k = 0; k < k_end; ++k) {
+        const long long tile = ens_tile_of(k, G, b);
+        if (tile >= a.n_tiles) break;                      // ragged last chunk
+        const int mk = a.tile_member[tile];                // uniform across the block
+        if (mk != member) {
+            if (member >= 0) warp_min_publish<T>(cand, sm + a.slot_write);
+            cand = inf_of<T>();
+            member = mk;
+            sm = a.small + 8 * (long long)mk;
+            const double dt_d = a.cfl[mk] * __longlong_as_double((long long)sm[a.slot_read]);
+            have_dt = dt_d < __longlong_as_double((long long)kInfBits);
+            dt = T(dt_d);
+            if (tile == a.member_first_tile[mk] && tid == 0) {
+                sm[a.slot_reset] = kInfBits;
+                if (have_dt) *(double*)(sm + 3) += dt_d;
+                else atomicOr((unsigned*)(sm + 4), kStatusDry);
+            }
+        }
+        const long long i = tile * BLOCK + tid;
+        V4<T> own;
+        int4 tp;
+        if constexpr (STAGES > 1) {
+            const long long kn = k + STAGES - 1;
+            const long long nt = ens_tile_of(kn, G, b);
+            const int fill = slot == 0 ? STAGES - 1 : slot - 1;
+            if (kn < k_end && nt < a.n_tiles) {
+                const long long c = nt * BLOCK + tid;
+                cp_async_record<sizeof(V4<T>)>(&st_own[fill][tid], &a.s_in[c]);
+                cp_async_record<16>(&st_topo[fill][tid], &a.topo[c]);
+            }
+            cp_async_commit();
+            cp_async_wait<STAGES - 1>();
+            own = st_own[slot][tid];
+            tp = st_topo[slot][tid];
+            slot = slot == STAGES - 1 ? 0 : slot + 1;
+        } else {
+            own = a.s_in[i];
+            tp = a.topo[i];
+        }
+        if (have_dt)
+            cand = tmin(cand, update_cell<T>(a, i, own, tp, dt, active, sm + 5, (unsigned*)(sm + 4)));
+        else
+            a.s_out[i] = own;
+    }
+    if constexpr (STAGES > 1) cp_async_wait<0>();
+    if (member >= 0) warp_min_publish<T>(cand, sm + a.slot_write);
+    active = __reduce_add_sync(0xffffffffu, active);
+    if ((tid & 31) == 0 && active) atomicAdd(a.n_active, (unsigned long long)active);
 }
 
 // ---- CFL min of a given state (used after swe_set_state) --------------------------
@@ -497,6 +625,9 @@ struct Launch {
     // (block, min_blocks) pairs with a compiled kernel; see step_variants()
     static cudaError_t step(const StepArgs<T>& a, int block, int min_blocks, int stages, cudaStream_t st);
     static cudaError_t resident_blocks(int block, int min_blocks, int stages, int* per_sm);
+    // batched ensemble step: block 256, the default min_blocks and stages of the precision
+    static cudaError_t ensemble_step(const EnsArgs<T>& a, unsigned grid, cudaStream_t st);
+    static cudaError_t ensemble_resident_blocks(int* per_sm);
     static int default_min_blocks(int block);
     static cudaError_t dt(const V4<T>* s, const V4<T>* geoB, long long n, T g, T h_dry,
                           unsigned long long* dt_write, cudaStream_t st);

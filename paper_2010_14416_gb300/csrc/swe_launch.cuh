@@ -60,6 +60,25 @@ cudaError_t Launch<T>::resident_blocks(int block, int min_blocks, int stages, in
 }
 
 template <typename T>
+struct EnsShape {
+    static constexpr int minb = sizeof(T) == 4 ? 4 : 1;
+    static constexpr int stages = sizeof(T) == 4 ? 3 : 1;
+};
+
+template <typename T>
+cudaError_t Launch<T>::ensemble_step(const EnsArgs<T>& a, unsigned grid, cudaStream_t st) {
+    if (grid == 0) return cudaErrorInvalidValue;
+    ensemble_step_kernel<T, kEnsBlock, EnsShape<T>::minb, EnsShape<T>::stages><<<grid, kEnsBlock, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::ensemble_resident_blocks(int* per_sm) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        per_sm, ensemble_step_kernel<T, kEnsBlock, EnsShape<T>::minb, EnsShape<T>::stages>, kEnsBlock, 0);
+}
+
+template <typename T>
 cudaError_t Launch<T>::dt(const V4<T>* s, const V4<T>* geoB, long long n, T g, T h_dry,
                           unsigned long long* dt_write, cudaStream_t st) {
     dt_kernel<T, 256><<<grid_for<T>(n, 256), 256, 0, st>>>(s, geoB, n, g, h_dry, dt_write);

@@ -1,0 +1,96 @@
+"""Batched ensemble (uncertainty propagation, Section 6.4.3's sampled runs):
+members of uneven sizes advanced together must receive exactly the updates
+the plain solver gives each of them alone, bit for bit, with their own CFL
+steps."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import rel_err
+from paper_2010_14416_gb300 import build as libbuild
+from paper_2010_14416_gb300 import capi
+from paper_2010_14416_gb300 import meshgen as mg
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    libbuild.build()
+    return capi.load()
+
+
+def _members(n=8, seed=3):
+    return mg.ensemble_members(n, seed=seed, lo=1500, hi=30000)
+
+
+def _mesh(mi, precision):
+    m = capi.Mesh(mi.nodes, mi.tris, mi.z, mi.manning, precision=precision)
+    for pairs, kind, value in mi.bcs:
+        m.set_bc(pairs, kind, value)
+    dt = m.dtype
+    m.set_state(mi.h.astype(dt), mi.hu.astype(dt), mi.hv.astype(dt))
+    return m
+
+
+@pytest.mark.parametrize("precision", [capi.SWE_FP64, capi.SWE_FP32])
+def test_ensemble_matches_plain_solver_bitwise(precision):
+    mis = _members()
+    assert len({mi.n_cells % 256 for mi in mis}) > 1          # uneven, ragged sizes
+    rng = np.random.default_rng(1)
+    cfl = rng.uniform(0.5, 0.9, len(mis))
+    meshes = [_mesh(mi, precision) for mi in mis]
+    ens = capi.Ensemble(meshes)
+    t_a = ens.step(100, cfl)
+    t_b = ens.step(101, cfl)                                   # second call starts mid-phase
+    for k, (mi, m) in enumerate(zip(mis, meshes)):
+        t_plain = m.step(201, cfl[k])
+        assert t_b[k] == t_plain and t_a[k] < t_b[k]
+        got = ens.get_state(k)
+        ref = m.get_state()
+        assert all(np.array_equal(a, b) for a, b in zip(got, ref)), f"member {k}"
+        assert ens.info(k)["status"] == 0
+    ens.close()
+    for m in meshes:
+        m.close()
+
+
+def test_ensemble_member_against_oracle_fp64():
+    mis = _members(4, seed=5)
+    meshes = [_mesh(mi, capi.SWE_FP64) for mi in mis]
+    ens = capi.Ensemble(meshes)
+    t = ens.step(300)
+    for k in (0, 3):
+        mi = mis[k]
+        M = oracle.Mesh(mi.nodes, mi.tris, mi.z, mi.manning)
+        for pairs, kind, value in mi.bcs:
+            M.set_bc(pairs, kind, value)
+        oh, ohu, ohv, ot, _ = M.run(mi.h, mi.hu, mi.hv, 300, 0.9)
+        assert t[k] == pytest.approx(ot, rel=1e-12)
+        for a, b in zip(ens.get_state(k), (oh, ohu, ohv)):
+            assert rel_err(a, b) <= 1e-10
+    ens.close()
+
+
+def test_ensemble_device_output_and_errors():
+    mis = _members(3, seed=7)
+    meshes = [_mesh(mi, capi.SWE_FP64) for mi in mis]
+    ens = capi.Ensemble(meshes)
+    ens.step(12)
+    out = [torch.empty(mis[1].n_cells, dtype=torch.float64, device="cuda") for _ in range(3)]
+    ens.get_state(1, out)
+    torch.cuda.synchronize()
+    host = ens.get_state(1)
+    assert all(np.array_equal(a.cpu().numpy(), b) for a, b in zip(out, host))
+    ens.close()
+    # a member without a state, or of another precision, is refused
+    bare = capi.Mesh(mis[0].nodes, mis[0].tris, mis[0].z, mis[0].manning)
+    with pytest.raises(capi.SWEError) as e:
+        capi.Ensemble([meshes[0], bare])
+    assert e.value.code == capi.SWE_EINVAL
+    f32 = _mesh(mis[0], capi.SWE_FP32)
+    with pytest.raises(capi.SWEError) as e:
+        capi.Ensemble([meshes[0], f32])
+    assert e.value.code == capi.SWE_EINVAL
