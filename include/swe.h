@@ -183,6 +183,44 @@ SWE_API int swe_get_info(swe_mesh* mesh, swe_info* info);
  * (the locality ordering).  perm: [n_tris] int64 host array. */
 SWE_API int swe_get_permutation(swe_mesh* mesh, int64_t* perm);
 
+/* ---- discrete adjoint (inverse analysis) ---- */
+
+/*
+ * Gradient of a gauge misfit with respect to the per-cell Manning coefficient
+ * and bed elevation, by the discrete adjoint of the FP64 step (Eq 37 and
+ * everything it calls).  The paper motivates inverse analysis (Section 1) but
+ * gives no adjoint; this is the adjoint of the discrete map as implemented.
+ *
+ * From the mesh's current state U^0, runs nsteps forward steps with the CFL
+ * number cfl (the mesh state advances to U^N exactly as swe_step would move
+ * it), then
+ *   loss = sum_k (h[gauge_cells[k]]^N - target_h[k])^2
+ * and its gradient with the step sizes held at the forward run's values
+ * (the dt sequence is not differentiated; dts_out, if not NULL, receives it:
+ * [nsteps] host doubles).  States are checkpointed every checkpoint_every
+ * steps (0 = 50) and recomputed segment by segment in the reverse sweep.
+ *   gauge_cells [n_gauges] caller cell indices; target_h [n_gauges] (host)
+ *   loss        one host double
+ *   grad_manning, grad_bathy: [n_tris] doubles in the caller's cell order, on
+ *               the host (where = SWE_HOST) or device (SWE_DEVICE); either may be NULL
+ * Device memory: about (nsteps/checkpoint_every + checkpoint_every + 4) x 32 B per cell.
+ * Errors: SWE_EINVAL (FP32 mesh, no state, bad gauge), SWE_ENOMEM, SWE_ECUDA,
+ * SWE_ENONFINITE, SWE_EDRY.
+ */
+SWE_API int swe_adjoint(swe_mesh* mesh, int64_t nsteps, double cfl, const int32_t* gauge_cells, int n_gauges,
+                        const double* target_h, int checkpoint_every, double* loss, double* grad_manning,
+                        double* grad_bathy, int where, double* dts_out);
+
+/* Advances nsteps steps with prescribed step sizes dts[nsteps] (host array,
+ * each > 0) instead of the CFL step: the frozen-dt map that swe_adjoint
+ * differentiates.  t_out (nullable) receives the time reached; waits. */
+SWE_API int swe_step_dt(swe_mesh* mesh, int64_t nsteps, const double* dts, double* t_out);
+
+/* Replaces the bed elevation and/or Manning coefficients ([n_tris] host
+ * doubles in the caller's order; NULL keeps the current field).  The state's
+ * h, hu, hv are kept.  Waits for the mesh stream. */
+SWE_API int swe_set_fields(swe_mesh* mesh, const double* bathy, const double* manning);
+
 /* ---- batched ensemble (uncertainty propagation: many runs of the same solver) ---- */
 
 typedef struct swe_ensemble swe_ensemble;

@@ -205,7 +205,7 @@ def loss_and_gradient(M: "oracle.Mesh", h0, hu0, hv0, dts, gauges, target, segme
     gi = torch.tensor(np.asarray(gauges, np.int64))
     L = ((hN[gi] - torch.tensor(np.asarray(target, np.float64))) ** 2).sum()
     gz, gm = torch.autograd.grad(L, [z, m])
-    return float(L), gm.numpy(), gz.numpy()
+    return float(L.detach()), gm.numpy(), gz.numpy()
 
 
 def loss_only(M: "oracle.Mesh", h0, hu0, hv0, dts, gauges, target, z=None, m=None):

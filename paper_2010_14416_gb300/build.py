@@ -25,6 +25,7 @@ UNITS = [
     ("swe_mesh.cu", []),
     ("swe_noalloc.cu", ["--use_fast_math"]),
     ("swe_ensemble.cu", []),
+    ("swe_adjoint.cu", []),
 ]
 
 

@@ -30,7 +30,8 @@ EXPORTS = ["swe_config_default", "swe_mesh_create", "swe_mesh_destroy", "swe_set
            "swe_set_stream", "swe_set_state", "swe_step", "swe_get_state", "swe_synchronize",
            "swe_get_info", "swe_get_permutation", "swe_mesh_preprocess", "swe_riemann_flux",
            "swe_cfl_dt_noalloc", "swe_ensemble_create", "swe_ensemble_destroy", "swe_ensemble_set_stream",
-           "swe_ensemble_step", "swe_ensemble_get_state", "swe_ensemble_get_info", "swe_last_error"]
+           "swe_ensemble_step", "swe_ensemble_get_state", "swe_ensemble_get_info", "swe_adjoint",
+           "swe_step_dt", "swe_set_fields", "swe_last_error"]
 
 
 class swe_config(C.Structure):
@@ -90,6 +91,9 @@ def load():
     lib.swe_ensemble_step.argtypes = [vp, C.c_int64, vp, vp]
     lib.swe_ensemble_get_state.argtypes = [vp, C.c_int, vp, vp, vp, C.c_int]
     lib.swe_ensemble_get_info.argtypes = [vp, C.c_int, C.POINTER(swe_info)]
+    lib.swe_adjoint.argtypes = [vp, C.c_int64, C.c_double, vp, C.c_int, vp, C.c_int, vp, vp, vp, C.c_int, vp]
+    lib.swe_step_dt.argtypes = [vp, C.c_int64, vp, vp]
+    lib.swe_set_fields.argtypes = [vp, vp, vp]
     lib.swe_last_error.argtypes = []
     lib.swe_last_error.restype = C.c_char_p
     for name in EXPORTS:
@@ -218,6 +222,36 @@ class Mesh:
         inf = swe_info()
         check(load().swe_get_info(self._h, C.byref(inf)))
         return {k: getattr(inf, k) for k, _ in swe_info._fields_}
+
+    def adjoint(self, nsteps, gauges, target, cfl=0.9, checkpoint_every=50, out=None):
+        """Gauge-misfit loss after nsteps and its gradient w.r.t. (manning,
+        bathy); returns (loss, grad_manning, grad_bathy, dts).  `out` may give
+        two device tensors for the gradients."""
+        g = np.ascontiguousarray(gauges, dtype=np.int32)
+        t = np.ascontiguousarray(target, dtype=np.float64)
+        loss = C.c_double(0.0)
+        dts = np.zeros(int(nsteps))
+        if out is None:
+            gm, gz = np.zeros(self.n_cells), np.zeros(self.n_cells)
+            pm, pz, where = gm.ctypes.data, gz.ctypes.data, SWE_HOST
+        else:
+            gm, gz = out
+            pm, pz, where = gm.data_ptr(), gz.data_ptr(), SWE_DEVICE
+        check(load().swe_adjoint(self._h, int(nsteps), float(cfl), g.ctypes.data, g.shape[0], t.ctypes.data,
+                                 int(checkpoint_every), C.byref(loss), pm, pz, where, dts.ctypes.data))
+        return loss.value, gm, gz, dts
+
+    def step_dt(self, dts):
+        d = np.ascontiguousarray(dts, dtype=np.float64)
+        t = C.c_double(0.0)
+        check(load().swe_step_dt(self._h, d.shape[0], d.ctypes.data, C.byref(t)))
+        return t.value
+
+    def set_fields(self, bathy=None, manning=None):
+        b = np.ascontiguousarray(bathy, dtype=np.float64) if bathy is not None else None
+        mm = np.ascontiguousarray(manning, dtype=np.float64) if manning is not None else None
+        check(load().swe_set_fields(self._h, b.ctypes.data if b is not None else None,
+                                    mm.ctypes.data if mm is not None else None))
 
     def permutation(self):
         p = np.empty(self.n_cells, np.int64)

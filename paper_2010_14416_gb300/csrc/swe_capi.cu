@@ -165,6 +165,8 @@ StepArgs<T> make_args(swe_mesh* m, int64_t step_index, double cfl) {
     a.n = m->hm.n_cells;
     a.grid = m->grid;
     a.cfl = cfl;
+    a.dt_fixed = nullptr;
+    a.dt_log = nullptr;
     a.g = (T)m->cfg.g;
     a.h_dry = (T)m->cfg.h_dry;
     a.bc = m->bc;
@@ -310,6 +312,48 @@ int get_state_t(swe_mesh* m, void* h, void* hu, void* hv, int where) {
 }
 
 }  // namespace
+
+namespace swe {
+
+// One step of mesh m from state buffer `in` to `out`, with the given status
+// block and step index (dt slot rotation), taking dt from *dt_fixed when set.
+cudaError_t launch_step_raw(swe_mesh* m, const void* in, void* out, unsigned long long* small, int64_t step_index,
+                            double cfl, const double* dt_fixed, double* dt_log, cudaStream_t st) {
+    if (m->cfg.precision == SWE_FP32) {
+        StepArgs<float> a = make_args<float>(m, step_index, cfl);
+        a.s_in = (const V4<float>*)in;
+        a.s_out = (V4<float>*)out;
+        const int p3 = (int)(step_index % 3);
+        a.dt_read = (const double*)(small + p3);
+        a.dt_write = small + (p3 + 1) % 3;
+        a.dt_reset = small + (p3 + 2) % 3;
+        a.t = (double*)(small + kSlotT);
+        a.status = (unsigned*)(small + kSlotStatus);
+        a.n_clamped = small + kSlotClamp;
+        a.n_active = small + kSlotActive;
+        a.dt_fixed = dt_fixed;
+        a.dt_log = dt_log;
+        return Launch<float>::step(a, m->cfg.block_size, m->cfg.min_blocks, m->cfg.stages, st);
+    }
+    StepArgs<double> a = make_args<double>(m, step_index, cfl);
+    a.s_in = (const V4<double>*)in;
+    a.s_out = (V4<double>*)out;
+    const int p3 = (int)(step_index % 3);
+    a.dt_read = (const double*)(small + p3);
+    a.dt_write = small + (p3 + 1) % 3;
+    a.dt_reset = small + (p3 + 2) % 3;
+    a.t = (double*)(small + kSlotT);
+    a.status = (unsigned*)(small + kSlotStatus);
+    a.n_clamped = small + kSlotClamp;
+    a.n_active = small + kSlotActive;
+    a.dt_fixed = dt_fixed;
+    a.dt_log = dt_log;
+    return Launch<double>::step(a, m->cfg.block_size, m->cfg.min_blocks, m->cfg.stages, st);
+}
+
+int flush_mesh_bc(swe_mesh* m) { return flush_topo(m); }
+
+}  // namespace swe
 
 extern "C" {
 

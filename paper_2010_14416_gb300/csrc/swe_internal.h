@@ -48,6 +48,16 @@ constexpr int kSlotT = 3, kSlotStatus = 4, kSlotClamp = 5, kSlotActive = 6;
 
 }  // namespace swe
 
+struct swe_mesh;
+
+namespace swe {
+// One step of mesh m from state buffer `in` to `out` (see swe_capi.cu).
+cudaError_t launch_step_raw(swe_mesh* m, const void* in, void* out, unsigned long long* small, int64_t step_index,
+                            double cfl, const double* dt_fixed, double* dt_log, cudaStream_t st);
+// Applies pending boundary-group changes of m to the device.
+int flush_mesh_bc(swe_mesh* m);
+}  // namespace swe
+
 // One mesh: host preprocessing result, device arrays and stepping state.
 struct swe_mesh {
     swe_config cfg{};

@@ -62,6 +62,8 @@ struct StepArgs {
     long long n;                       // number of cells
     unsigned grid;                     // blocks launched (grid-stride)
     double cfl;
+    const double* dt_fixed;            // if set: the step size to take (frozen time steps)
+    double* dt_log;                    // if set: receives the step size taken
     T g, h_dry;
     BcTable bc;
     __device__ __forceinline__ int bc_kind(int grp) const { return bc.kind[grp]; }
@@ -239,6 +241,102 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory");
 }
 
+// ---- pieces of one cell update, shared by the step kernels and the adjoint ----------
+// Templated on the scalar so the discrete adjoint can run them on forward-mode
+// dual numbers: it then differentiates exactly the arithmetic, and takes
+// exactly the branches, of the forward step.
+
+template <typename T>
+__device__ __forceinline__ void cell_velocity(T h, T hu, T hv, T h_dry, T& u, T& v) {
+    u = T(0);
+    v = T(0);
+    if (h > h_dry) { const T r = Ar<T>::rcp_(h); u = hu * r; v = hv * r; }
+}
+
+// Flux leaving cell i through an interior edge (per unit length, x-y frame)
+// and the edge's bed source factor (g/2)(h**_i^2 - h_i^2) (Eq 30 with 1/2).
+// (n1, n2) is cell i's outward unit normal; flip says cell i is the right
+// state of the edge's canonical orientation.
+template <typename T>
+__device__ __forceinline__ void edge_interior(T hi, T ui, T vi, T zi, T hk, T huk, T hvk, T zk, T n1, T n2,
+                                              bool flip, T g, T h_dry, T& F0, T& F1, T& F2, T& src) {
+    T uk, vk;
+    cell_velocity<T>(hk, huk, hvk, h_dry, uk, vk);
+    // hydrostatic reconstruction (Eq 28): z* = max(z_i, z_k)
+    const T zs = tmax(zi, zk);
+    const T hsi = tmax(T(0), hi + zi - zs);
+    const T hsk = tmax(T(0), hk + zk - zs);
+    // canonical orientation: left = lower caller index
+    const T hL = flip ? hsk : hsi, hR = flip ? hsi : hsk;
+    const T uL = flip ? uk : ui, vL = flip ? vk : vi;
+    const T uR = flip ? ui : uk, vR = flip ? vi : vk;
+    const T c1 = flip ? -n1 : n1, c2 = flip ? -n2 : n2;
+    // rotate into the edge frame (Eq 12)
+    const T unL = uL * c1 + vL * c2, utL = vL * c1 - uL * c2;
+    const T unR = uR * c1 + vR * c2, utR = vR * c1 - uR * c2;
+    T G1, G2, G3;
+    riemann_hllc<T>(hL, unL, utL, hR, unR, utR, g, h_dry, G1, G2, G3);
+    // back to (x, y) (Eq 12 inverse), as the flux leaving this cell
+    const T s = flip ? T(-1) : T(1);
+    F0 = s * G1;
+    F1 = s * (G2 * c1 - G3 * c2);
+    F2 = s * (G2 * c2 + G3 * c1);
+    src = T(0.5) * g * (hsi * hsi - hi * hi);
+}
+
+// Flux leaving cell i through a boundary edge of the given kind (Section 3.1).
+template <typename T>
+__device__ __forceinline__ void edge_boundary(int kind, double value, T hi, T ui, T vi, T zi, T n1, T n2, T g,
+                                              T h_dry, T& F0, T& F1, T& F2) {
+    const T un = ui * n1 + vi * n2, ut = vi * n1 - ui * n2;
+    T G1, G2, G3;
+    if (kind == kBcWall) {
+        G1 = T(0); G2 = T(0.5) * g * hi * hi; G3 = T(0);
+    } else if (kind == kBcInflow) {
+        const T q = T(value);
+        G1 = -q;
+        G2 = T(0.5) * g * hi * hi + (hi > h_dry ? Ar<T>::div_(q * q, hi) : T(0));
+        G3 = T(0);
+    } else {
+        T hg = hi;
+        if (kind == kBcStage) hg = tmax(T(0), T(value) - zi);
+        riemann_hllc<T>(hi, un, ut, hg, un, ut, g, h_dry, G1, G2, G3);
+    }
+    F0 = G1;
+    F1 = G2 * n1 - G3 * n2;
+    F2 = G2 * n2 + G3 * n1;
+}
+
+// Semi-implicit friction (Eq 33-37): dU solving [I - dt/2 J_f] dU = dt (R + S_f)
+// with R = (Rh, Rx, Ry) the explicit right-hand side per unit area.
+template <typename T>
+__device__ __forceinline__ void friction_update(T hi, T qx, T qy, T gm2, T Rh, T Rx, T Ry, T dt, T h_dry, T& dh,
+                                                T& dqx, T& dqy) {
+    using A = Ar<T>;
+    dh = dt * Rh;
+    dqx = dt * Rx;
+    dqy = dt * Ry;
+    if (hi > h_dry && gm2 > T(0)) {
+        const T qq = qx * qx + qy * qy;
+        if (qq > T(0)) {
+            const T qn = A::sqrt_(qq);
+            const T cf = gm2 * A::pow_m73(hi);             // c = g m^2 h^(-7/3)
+            const T al = T(0.5) * dt * cf;                  // alpha = dt c / 2
+            // rhs: dt (R_q + S_f) + dt/2 J_qh dh, with S_f = -c|q|q and
+            // J_qh = (7/3) c |q| q / h
+            const T k = dt * cf * qn * (T(7.0 / 6.0) * dh * A::rcp_(hi) - T(1));
+            const T bx = dqx + k * qx, by = dqy + k * qy;
+            // (1 + a|q|) I + a q q^T/|q| has eigenvalue 1 + 2a|q| along q
+            // and 1 + a|q| across it
+            const T d1 = T(1) + al * qn, d2 = d1 + al * qn;
+            const T proj = (bx * qx + by * qy) * al * A::rcp_(qn * d2);
+            const T rd1 = A::rcp_(d1);
+            dqx = (bx - proj * qx) * rd1;
+            dqy = (by - proj * qy) * rd1;
+        }
+    }
+}
+
 // ---- one cell of the fused step -----------------------------------------------------
 // Returns the cell's CFL candidate R_i/(sqrt(g h)+|u|) of the new state (+inf
 // when the new state is dry); sets `active` when the full flux path ran.
@@ -280,8 +378,8 @@ __device__ __forceinline__ T update_cell(const Args& a, long long i, const V4<T>
     active += 1u;
     const V4<T> gA = a.geoA[i], gB = a.geoB[i];
     const T gm2 = load_gm2(a, i, tp, T(0));
-    T ui = T(0), vi = T(0);
-    if (hi > h_dry) { const T r = A::rcp_(hi); ui = own.y * r; vi = own.z * r; }
+    T ui, vi;
+    cell_velocity<T>(hi, own.y, own.z, h_dry, ui, vi);
     T f0 = T(0), f1 = T(0), f2 = T(0), sx = T(0), sy = T(0);
 #pragma unroll 1
     for (int j = 0; j < 3; ++j) {
@@ -295,53 +393,14 @@ __device__ __forceinline__ T update_cell(const Args& a, long long i, const V4<T>
         const T n1 = lx * rl, n2 = ly * rl;     // this cell's outward unit normal
         T F0, F1, F2;
         if (c >= 0) {
-            const bool flip = (c & kFlipBit) != 0;
-            const T hk = o.x, zk = o.w;
-            T uk = T(0), vk = T(0);
-            if (hk > h_dry) { const T r = A::rcp_(hk); uk = o.y * r; vk = o.z * r; }
-            // hydrostatic reconstruction (Eq 28): z* = max(z_i, z_k)
-            const T zs = tmax(zi, zk);
-            const T hsi = tmax(T(0), hi + zi - zs);
-            const T hsk = tmax(T(0), hk + zk - zs);
-            // canonical orientation: left = lower caller index
-            const T hL = flip ? hsk : hsi, hR = flip ? hsi : hsk;
-            const T uL = flip ? uk : ui, vL = flip ? vk : vi;
-            const T uR = flip ? ui : uk, vR = flip ? vi : vk;
-            const T c1 = flip ? -n1 : n1, c2 = flip ? -n2 : n2;
-            // rotate into the edge frame (Eq 12)
-            const T unL = uL * c1 + vL * c2, utL = vL * c1 - uL * c2;
-            const T unR = uR * c1 + vR * c2, utR = vR * c1 - uR * c2;
-            T G1, G2, G3;
-            riemann_hllc<T>(hL, unL, utL, hR, unR, utR, g, h_dry, G1, G2, G3);
-            // back to (x, y) (Eq 12 inverse), as the flux leaving this cell
-            const T s = flip ? T(-1) : T(1);
-            F0 = s * G1;
-            F1 = s * (G2 * c1 - G3 * c2);
-            F2 = s * (G2 * c2 + G3 * c1);
-            // bed source of this edge (Eq 30 with the factor 1/2)
-            const T src = T(0.5) * g * (hsi * hsi - hi * hi);
+            T src;
+            edge_interior<T>(hi, ui, vi, zi, o.x, o.y, o.z, o.w, n1, n2, (c & kFlipBit) != 0, g, h_dry, F0, F1, F2,
+                             src);
             sx += src * lx;
             sy += src * ly;
         } else {
             const int grp = -1 - c;
-            const int kind = a.bc_kind(grp);
-            const T un = ui * n1 + vi * n2, ut = vi * n1 - ui * n2;
-            T G1, G2, G3;
-            if (kind == kBcWall) {
-                G1 = T(0); G2 = T(0.5) * g * hi * hi; G3 = T(0);
-            } else if (kind == kBcInflow) {
-                const T q = T(a.bc_value(grp));
-                G1 = -q;
-                G2 = T(0.5) * g * hi * hi + (hi > h_dry ? A::div_(q * q, hi) : T(0));
-                G3 = T(0);
-            } else {
-                T hg = hi;
-                if (kind == kBcStage) hg = tmax(T(0), T(a.bc_value(grp)) - zi);
-                riemann_hllc<T>(hi, un, ut, hg, un, ut, g, h_dry, G1, G2, G3);
-            }
-            F0 = G1;
-            F1 = G2 * n1 - G3 * n2;
-            F2 = G2 * n2 + G3 * n1;
+            edge_boundary<T>(a.bc_kind(grp), a.bc_value(grp), hi, ui, vi, zi, n1, n2, g, h_dry, F0, F1, F2);
         }
         f0 += len * F0;
         f1 += len * F1;
@@ -351,29 +410,9 @@ __device__ __forceinline__ T update_cell(const Args& a, long long i, const V4<T>
     const T Rh = -f0 * ia;
     const T Rx = (sx - f1) * ia;
     const T Ry = (sy - f2) * ia;
-    // semi-implicit friction (Eq 33-37): [I - dt/2 J_f] dU = dt (R + S_f)
-    const T dh = dt * Rh;
-    T dqx = dt * Rx, dqy = dt * Ry;
     const T qx = own.y, qy = own.z;
-    if (hi > h_dry && gm2 > T(0)) {
-        const T qq = qx * qx + qy * qy;
-        if (qq > T(0)) {
-            const T qn = A::sqrt_(qq);
-            const T cf = gm2 * A::pow_m73(hi);             // c = g m^2 h^(-7/3)
-            const T al = T(0.5) * dt * cf;                  // alpha = dt c / 2
-            // rhs: dt (R_q + S_f) + dt/2 J_qh dh, with S_f = -c|q|q and
-            // J_qh = (7/3) c |q| q / h
-            const T k = dt * cf * qn * (T(7.0 / 6.0) * dh * A::rcp_(hi) - T(1));
-            const T bx = dqx + k * qx, by = dqy + k * qy;
-            // (1 + a|q|) I + a q q^T/|q| has eigenvalue 1 + 2a|q| along q
-            // and 1 + a|q| across it
-            const T d1 = T(1) + al * qn, d2 = d1 + al * qn;
-            const T proj = (bx * qx + by * qy) * al * A::rcp_(qn * d2);
-            const T rd1 = A::rcp_(d1);
-            dqx = (bx - proj * qx) * rd1;
-            dqy = (by - proj * qy) * rd1;
-        }
-    }
+    T dh, dqx, dqy;
+    friction_update<T>(hi, qx, qy, gm2, Rh, Rx, Ry, dt, h_dry, dh, dqx, dqy);
     out.x = hi + dh;
     out.y = qx + dqx;
     out.z = qy + dqy;
@@ -405,12 +444,13 @@ __device__ __forceinline__ T update_cell(const Args& a, long long i, const V4<T>
 // through cp.async into its own shared-memory slots.
 template <typename T, int BLOCK, int MINB, int STAGES>
 __global__ void __launch_bounds__(BLOCK, MINB) step_kernel(const StepArgs<T> a) {
-    const double dt_d = a.cfl * (*a.dt_read);
+    const double dt_d = a.dt_fixed ? *a.dt_fixed : a.cfl * (*a.dt_read);
     const bool have_dt = dt_d < __longlong_as_double((long long)kInfBits);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         *a.dt_reset = kInfBits;
         if (have_dt) *a.t += dt_d;
         else atomicOr(a.status, kStatusDry);
+        if (a.dt_log) *a.dt_log = dt_d;
     }
     T cand = inf_of<T>();
     unsigned active = 0u;

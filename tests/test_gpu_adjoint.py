@@ -1,0 +1,131 @@
+"""Discrete adjoint (gradient of the gauge misfit w.r.t. Manning n and bed
+elevation) against the FP64 reference gradient of oracle/adjoint_torch.py,
+against central differences of the GPU's own frozen-dt forward map, and
+through the torch.autograd.Function."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import adjoint_torch as at
+from paper_2010_14416_gb300 import build as libbuild
+from paper_2010_14416_gb300 import capi
+from paper_2010_14416_gb300 import meshgen as mg
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    libbuild.build()
+    return capi.load()
+
+
+def _setup(fully_wet=True, nx=40, ny=8, steps=80, seed=2, n_gauges=12):
+    mi = mg.river(nx, ny, Lx=50.0 * nx, Ly=50.0 * ny, seed=seed, fully_wet=fully_wet, n_bumps=30, Q=300.0)
+    M = oracle.Mesh(mi.nodes, mi.tris, mi.z, mi.manning)
+    for pairs, kind, value in mi.bcs:
+        M.set_bc(pairs, kind, value)
+    _, _, _, _, _, dts = M.run(mi.h, mi.hu, mi.hv, steps, 0.9, log_dt=True)
+    if fully_wet:
+        gauges = mg.gauge_cells(mi.n_cells, n_gauges, seed=seed)
+    else:  # gauges in the wet channel, so the misfit depends on the parameters
+        wet = np.flatnonzero(mi.h > 0.5)
+        gauges = np.sort(wet[mg.gauge_cells(wet.shape[0], n_gauges, seed=seed)])
+    xi = mg.perturbation(mi.n_cells, seed + 100)
+    T = oracle.Mesh(mi.nodes, mi.tris, mi.z + 0.05 * xi, mi.manning * (1 + 0.1 * xi))
+    for pairs, kind, value in mi.bcs:
+        T.set_bc(pairs, kind, value)
+    th, _, _, _, _ = T.run(mi.h, mi.hu, mi.hv, steps, 0.9)
+    return mi, M, dts, gauges, th[gauges]
+
+
+def _gpu_mesh(mi):
+    m = capi.Mesh(mi.nodes, mi.tris, mi.z, mi.manning, precision=capi.SWE_FP64)
+    for pairs, kind, value in mi.bcs:
+        m.set_bc(pairs, kind, value)
+    m.set_state(mi.h, mi.hu, mi.hv)
+    return m
+
+
+def _rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+@pytest.mark.parametrize("fully_wet,ckpt", [(True, 50), (True, 7), (False, 50)])
+def test_adjoint_matches_reference_gradient(fully_wet, ckpt):
+    mi, M, dts, gauges, target = _setup(fully_wet)
+    L_ref, gm_ref, gz_ref = at.loss_and_gradient(M, mi.h, mi.hu, mi.hv, dts, gauges, target)
+    m = _gpu_mesh(mi)
+    L, gm, gz, gdts = m.adjoint(len(dts), gauges, target, cfl=0.9, checkpoint_every=ckpt)
+    assert np.allclose(gdts, dts, rtol=1e-12)
+    assert L == pytest.approx(L_ref, rel=1e-9)
+    assert _rel(gm, gm_ref) <= TOL
+    assert _rel(gz, gz_ref) <= TOL
+    # the mesh state advanced to U^N like swe_step
+    assert m.info()["n_steps"] == len(dts)
+    m.close()
+
+
+def test_adjoint_directional_derivatives_match_central_differences():
+    # The discrete map has tiny jumps where the h* estimate switches between
+    # its rarefaction and shock forms (Eq 22/23), so differences use a small
+    # step that rarely straddles a switch; the full gradient is also checked
+    # against the reference gradient on the same case.
+    mi, M, dts, gauges, target = _setup(True, nx=120, ny=24, steps=150, seed=4, n_gauges=32)
+    m = _gpu_mesh(mi)
+    L0, gm, gz, gdts = m.adjoint(len(dts), gauges, target, checkpoint_every=50)
+    L_ref, gm_ref, gz_ref = at.loss_and_gradient(M, mi.h, mi.hu, mi.hv, dts, gauges, target)
+    assert _rel(gm, gm_ref) <= TOL and _rel(gz, gz_ref) <= TOL
+    rng = np.random.default_rng(12)
+
+    def loss(z, man):
+        m.set_fields(bathy=z, manning=man)
+        m.set_state(mi.h, mi.hu, mi.hv)
+        m.step_dt(gdts)
+        h, _, _ = m.get_state()
+        return float(((h[gauges] - target) ** 2).sum())
+
+    errs = []
+    for _ in range(32):
+        vz = rng.standard_normal(mi.n_cells)
+        vm = 0.01 * rng.standard_normal(mi.n_cells)
+        eps = 1e-6
+        fd = (loss(mi.z + eps * vz, mi.manning + eps * vm) - loss(mi.z - eps * vz, mi.manning - eps * vm)) / (2 * eps)
+        ad = float(gz @ vz + gm @ vm)
+        errs.append(abs(fd - ad) / abs(ad))
+    errs = np.array(errs)
+    assert np.median(errs) <= TOL, errs
+    assert (errs <= 1e-5).mean() >= 0.9, errs
+    m.close()
+
+
+def test_autograd_function():
+    from paper_2010_14416_gb300.autograd import SWEAdjoint
+    mi, M, dts, gauges, target = _setup(True, steps=40)
+    m = _gpu_mesh(mi)
+    man = torch.tensor(mi.manning, device="cuda", requires_grad=True)
+    bed = torch.tensor(mi.z, device="cuda", requires_grad=True)
+    loss = SWEAdjoint.apply(man, bed, m, (mi.h, mi.hu, mi.hv), 40, gauges, target)
+    (3.0 * loss).backward()
+    L_ref, gm_ref, gz_ref = at.loss_and_gradient(M, mi.h, mi.hu, mi.hv, dts[:40], gauges, target)
+    assert float(loss.detach()) == pytest.approx(L_ref, rel=1e-9)
+    assert _rel(man.grad.cpu().numpy(), 3.0 * gm_ref) <= TOL
+    assert _rel(bed.grad.cpu().numpy(), 3.0 * gz_ref) <= TOL
+    m.close()
+
+
+def test_adjoint_refuses_fp32_and_bad_gauges():
+    mi = mg.river(20, 4, seed=1, fully_wet=True)
+    m32 = capi.Mesh(mi.nodes, mi.tris, mi.z, mi.manning, precision=capi.SWE_FP32)
+    m32.set_state(mi.h.astype(np.float32), mi.hu.astype(np.float32), mi.hv.astype(np.float32))
+    with pytest.raises(capi.SWEError) as e:
+        m32.adjoint(5, [0], [1.0])
+    assert e.value.code == capi.SWE_EINVAL
+    m = _gpu_mesh(mi)
+    with pytest.raises(capi.SWEError) as e:
+        m.adjoint(5, [mi.n_cells], [1.0])
+    assert e.value.code == capi.SWE_EINVAL
