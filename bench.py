@@ -48,10 +48,17 @@ WORKLOADS = {
     "ensemble256_fp32": dict(maker="ensemble", precision="f32", steps=1000,
                              desc="256-member ensemble, canal and river members of 20k-500k triangles "
                                   "(log-uniform), Manning U[0.015,0.08], Q U[500,3000]; FP32 state, FP64 dt"),
+    "adjoint1m_fp64": dict(maker="river_adjoint_1m", precision="f64", steps=2000,
+                           desc="adjoint of the gauge misfit (64 gauges) after 2000 FP64 steps on the 1,001,728-"
+                                "triangle fully wet river, checkpoints every 50 steps, gradient w.r.t. Manning "
+                                "and bed"),
     "ensemble256_fp64": dict(maker="ensemble", precision="f64", steps=1000,
                              desc="256-member ensemble, canal and river members of 20k-500k triangles "
                                   "(log-uniform), Manning U[0.015,0.08], Q U[500,3000]; FP64"),
 }
+
+
+MEMBERS = [256]
 
 
 def _peaks():
@@ -133,10 +140,20 @@ def _dist():
     return dist, rank, ws, local
 
 
+def max_over_ranks(dist, values):
+    """Element-wise max of per-rank timings (the slowest rank sets the time)."""
+    if not dist:
+        return [float(v) for v in values]
+    import torch
+    tt = torch.tensor([float(v) for v in values], dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return [float(v) for v in tt.tolist()]
+
+
 def _make_input(name):
     from paper_2010_14416_gb300 import meshgen
     if WORKLOADS[name]["maker"] == "ensemble":
-        return meshgen.ensemble_members(256)
+        return meshgen.ensemble_members(MEMBERS[0])
     return getattr(meshgen, WORKLOADS[name]["maker"])()
 
 
@@ -253,11 +270,7 @@ def run_gpu(args, name):
     t_sim = info["t"]
     active_frac = (info["n_active"] - active0) / float(n * args.steps)
     m.synchronize()
-    if dist:
-        import torch.distributed as d
-        tt = torch.tensor([ms], dtype=torch.float64)
-        d.all_reduce(tt, op=d.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(dist, [ms])[0]
 
     # ---- end to end through the C ABI with pinned host buffers ----
     hp = [torch.from_numpy(a.astype(npdt)).pin_memory() for a in (mi.h, mi.hu, mi.hv)]
@@ -278,11 +291,7 @@ def run_gpu(args, name):
     m2.get_state(out)
     e2e_s = time.perf_counter() - t0
     m2.close()
-    if dist:
-        import torch.distributed as d
-        tt = torch.tensor([e2e_s], dtype=torch.float64)
-        d.all_reduce(tt, op=d.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s = max_over_ranks(dist, [e2e_s])[0]
 
     peak, peak_kind = _peaks()
     ab = ALG_BYTES[wl["precision"]]
@@ -409,11 +418,7 @@ def run_gpu_ensemble(args, name):
     ev1.record(stream)
     torch.cuda.synchronize(dev)
     ms_plain = ev0.elapsed_time(ev1)
-    if dist:
-        import torch.distributed as d
-        tt = torch.tensor([ms, ms_plain], dtype=torch.float64)
-        d.all_reduce(tt, op=d.ReduceOp.MAX)
-        ms, ms_plain = float(tt[0]), float(tt[1])
+    ms, ms_plain = max_over_ranks(dist, [ms, ms_plain])
     peak, peak_kind = _peaks()
     ab = ALG_BYTES[wl["precision"]]
     kernel_ms = ms / args.steps
@@ -447,6 +452,95 @@ def run_gpu_ensemble(args, name):
     return 0
 
 
+def run_gpu_adjoint(args, name):
+    """Forward run plus reverse sweep of the discrete adjoint, timed with
+    CUDA events; a bench step is one time step of the forward and its
+    reverse (recompute + two adjoint kernels)."""
+    import torch
+
+    from paper_2010_14416_gb300 import build as libbuild
+    from paper_2010_14416_gb300 import capi, meshgen
+
+    dist, rank, ws, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        libbuild.build()
+    if dist:
+        dist.barrier()
+    mi = _make_input(name)
+    n = mi.n_cells
+    gauges = meshgen.gauge_cells(n, 64, seed=1)
+    xi = meshgen.perturbation(n, 101)
+    stream = torch.cuda.Stream(device=dev)
+
+    def mesh(z, man):
+        m = capi.Mesh(mi.nodes, mi.tris, z, man, precision=capi.SWE_FP64, device=local)
+        for pairs, kind, value in mi.bcs:
+            m.set_bc(pairs, kind, value)
+        m.set_stream(stream)
+        m.set_state(mi.h, mi.hu, mi.hv)
+        return m
+
+    # seeded target: the same run with perturbed Manning and bed
+    tm = mesh(mi.z + 0.05 * xi, mi.manning * (1 + 0.1 * xi))
+    tm.step(args.steps, 0.9)
+    target = tm.get_state()[0][gauges]
+    tm.close()
+    m = mesh(mi.z, mi.manning)
+    gm = torch.empty(n, dtype=torch.float64, device=dev)
+    gz = torch.empty(n, dtype=torch.float64, device=dev)
+    warm = max(args.warmup, 3)
+    m.adjoint(warm, gauges, target, checkpoint_every=50, out=(gm, gz))
+    m.set_state(mi.h, mi.hu, mi.hv)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    if rank == 0:
+        clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    loss, _, _, dts = m.adjoint(args.steps, gauges, target, checkpoint_every=50, out=(gm, gz))
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop() if rank == 0 else None
+    # forward alone, same steps, for the ratio
+    m.set_state(mi.h, mi.hu, mi.hv)
+    m.step(96, 0.9)
+    m.set_state(mi.h, mi.hu, mi.hv)
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    m.step(args.steps, 0.9, sync=False)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_fwd = ev0.elapsed_time(ev1)
+    ms, ms_fwd = max_over_ranks(dist, [ms, ms_fwd])
+    line = {
+        "metric": "cell-updates/s", "value": ws * n * args.steps / (ms * 1e-3), "unit": "cell-updates/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": warm, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOADS[name]["desc"], "cells": n, "parallelism": f"replicas{ws}",
+                   "checkpoint_every": 50, "gauges": 64},
+        "loss": loss,
+        "grad_norms": {"manning": float(gm.norm()), "bathy": float(gz.norm())},
+        "forward_only": {"value": n * args.steps / (ms_fwd * 1e-3), "ms_per_step": ms_fwd / args.steps},
+        "adjoint_over_forward": ms / ms_fwd,
+        "roofline": {"bound": "alu", "note": "FP64 arithmetic on forward-mode duals; see DESIGN.md"},
+        "gpu_launches": args.steps * 4,
+        "clocks": clk,
+    }
+    m.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
 def _kernel_hash():
     import hashlib
     hsh = hashlib.sha1()
@@ -465,6 +559,7 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="river13m_fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--members", type=int, default=256, help="ensemble workloads: number of members")
     args = ap.parse_args()
     if args.steps is None:
         args.steps = WORKLOADS[args.workload]["steps"]
@@ -472,8 +567,11 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args, args.workload)
+    MEMBERS[0] = args.members
     if WORKLOADS[args.workload]["maker"] == "ensemble":
         return run_gpu_ensemble(args, args.workload)
+    if args.workload.startswith("adjoint"):
+        return run_gpu_adjoint(args, args.workload)
     return run_gpu(args, args.workload)
 
 

@@ -504,18 +504,19 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_kernel(const StepArgs<T> a) 
 // member's cells.  When a block moves on to another member, its warps publish
 // the finished member's CFL minimum (warp shuffle, one atomicMin per warp, no
 // barrier).
+// The warp minimum is taken in the state precision and widened once (exact:
+// widening is monotone), which keeps FP32 kernels off the FP64 pipe.
 template <typename T>
 __device__ __forceinline__ void warp_min_publish(T cand, unsigned long long* dst) {
-    double v = (double)cand;
-    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if ((threadIdx.x & 31) == 0 && v < __longlong_as_double((long long)kInfBits))
-        atomicMin(dst, (unsigned long long)__double_as_longlong(v));
+    for (int o = 16; o > 0; o >>= 1) cand = tmin(cand, __shfl_xor_sync(0xffffffffu, cand, o));
+    if ((threadIdx.x & 31) == 0 && cand < inf_of<T>())
+        atomicMin(dst, (unsigned long long)__double_as_longlong((double)cand));
 }
 
 // Tiles are dealt to blocks in round-robin chunks of kEnsChunk tiles, which
 // balances wet (expensive) and dry (cheap) members across the GPU while the
 // member still changes only at chunk or member boundaries.
-constexpr int kEnsChunk = 8;
+constexpr int kEnsChunk = 32;
 
 __device__ __forceinline__ long long ens_tile_of(long long k, long long nchunk_stride, long long b) {
     return (b + (k / kEnsChunk) * nchunk_stride) * kEnsChunk + (k % kEnsChunk);

@@ -129,3 +129,36 @@ def test_adjoint_refuses_fp32_and_bad_gauges():
     with pytest.raises(capi.SWEError) as e:
         m.adjoint(5, [mi.n_cells], [1.0])
     assert e.value.code == capi.SWE_EINVAL
+
+
+def test_full_size_adjoint_1m_cells_2000_steps():
+    # the adjoint workload itself: 1,001,728 cells, 2000 FP64 steps, 64
+    # gauges, checkpoints every 50; directional derivatives against central
+    # differences of the frozen-dt map (a property that holds at any size)
+    mi = mg.river_adjoint_1m()
+    gauges = mg.gauge_cells(mi.n_cells, 64, seed=1)
+    target = mi.h[gauges] + 0.02 * mg.perturbation(64, 77)
+    m = _gpu_mesh(mi)
+    L0, gm, gz, dts = m.adjoint(2000, gauges, target, checkpoint_every=50)
+    assert np.isfinite(L0) and L0 > 0 and np.all(np.isfinite(gm)) and np.all(np.isfinite(gz))
+    h_end, _, _ = m.get_state()
+    assert float(((h_end[gauges] - target) ** 2).sum()) == pytest.approx(L0, rel=1e-12)
+    rng = np.random.default_rng(3)
+
+    def loss(z, man):
+        m.set_fields(bathy=z, manning=man)
+        m.set_state(mi.h, mi.hu, mi.hv)
+        m.step_dt(dts)
+        h, _, _ = m.get_state()
+        return float(((h[gauges] - target) ** 2).sum())
+
+    errs = []
+    for _ in range(3):
+        vz = rng.standard_normal(mi.n_cells)
+        vm = 0.01 * rng.standard_normal(mi.n_cells)
+        eps = 1e-6
+        fd = (loss(mi.z + eps * vz, mi.manning + eps * vm) - loss(mi.z - eps * vz, mi.manning - eps * vm)) / (2 * eps)
+        ad = float(gz @ vz + gm @ vm)
+        errs.append(abs(fd - ad) / abs(ad))
+    assert np.median(errs) <= 1e-5, errs
+    m.close()
