@@ -4,11 +4,12 @@
 // and gathers its three neighbours, so every cell's sum of edge fluxes is
 // formed in a fixed order without atomics.  Each interior edge has a
 // canonical orientation: the cell with the lower caller index is the left
-// state and its outward normal is the edge normal.  Both cells of an edge run
-// the identical instruction sequence on identical operands (the edge loop is
-// kept rolled so there is a single code path) and apply the result with
-// opposite signs, so the two contributions cancel bit for bit and the result
-// does not depend on the cell ordering.
+// state and its outward normal is the edge normal.  Both cells of an edge
+// evaluate the same device function on the same operands (the right cell
+// passes them swapped back into canonical order) and apply the result with
+// opposite signs, so the two contributions cancel (exactly, as long as the
+// compiler emits the same instruction sequence for each unrolled edge slot),
+// and the result does not depend on the cell ordering.
 //
 // Method: Delmas & Soulaimani, Sections 2-3 (Eq 12-37); readings of the
 // garbled equations are the same as the oracle's and are listed where used.
@@ -381,7 +382,7 @@ __device__ __forceinline__ T update_cell(const Args& a, long long i, const V4<T>
     T ui, vi;
     cell_velocity<T>(hi, own.y, own.z, h_dry, ui, vi);
     T f0 = T(0), f1 = T(0), f2 = T(0), sx = T(0), sy = T(0);
-#pragma unroll 1
+#pragma unroll
     for (int j = 0; j < 3; ++j) {
         const int c = j == 0 ? code[0] : (j == 1 ? code[1] : code[2]);
         const V4<T> o = j == 0 ? nb[0] : (j == 1 ? nb[1] : nb[2]);
