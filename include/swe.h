@@ -183,6 +183,41 @@ SWE_API int swe_get_info(swe_mesh* mesh, swe_info* info);
  * (the locality ordering).  perm: [n_tris] int64 host array. */
 SWE_API int swe_get_permutation(swe_mesh* mesh, int64_t* perm);
 
+/* ---- diagnostics and steady state ---- */
+
+typedef struct swe_diag {
+    double t;               /* time of the state */
+    double dt_last;         /* size of the last step (0 before the first) */
+    double volume;          /* stored water, sum_i |Omega_i| h_i (m^3) */
+    double dh_max;          /* max_i |h_i^n - h_i^{n-1}| over the last step (m) */
+    double h_max;           /* largest depth (m) */
+    double speed_max;       /* largest |u| over wet cells (m/s) */
+    int64_t n_wet;          /* cells with h > h_dry */
+    int n_groups;           /* boundary groups, group 0 = the default wall */
+    double discharge[64];   /* outward discharge through each group (m^3/s) for the current
+                               state: what leaves through those edges in the next step per
+                               unit time (an inflow group of discharge Q gives -Q) */
+} swe_diag;
+
+/*
+ * Diagnostics of the current state: stored volume, depth change over the last
+ * step, extremes, wet cells, and the inflow/outflow rates of Section 5.3.2
+ * (per boundary group, with the step's own boundary fluxes of Section 3.1).
+ * Since interior fluxes cancel, volume after a step minus volume before it
+ * equals -dt times the sum of the discharges of the state before it.
+ * Deterministic; waits for the mesh stream.  Errors: SWE_EINVAL, SWE_ECUDA.
+ */
+SWE_API int swe_diagnostics(swe_mesh* mesh, swe_diag* out);
+
+/*
+ * Runs until the state is steady (the paper's first phase, a stabilised
+ * solution before production runs, Section 6.3.2): steps of check_every,
+ * stopping when max_i |h_i^{n+1} - h_i^n| / dt < tol (m/s) or after
+ * max_steps.  steps_done, converged (1/0) and t_out may be NULL.
+ */
+SWE_API int swe_run_to_steady(swe_mesh* mesh, double cfl, double tol, int64_t check_every, int64_t max_steps,
+                              int64_t* steps_done, int* converged, double* t_out);
+
 /* ---- discrete adjoint (inverse analysis) ---- */
 
 /*

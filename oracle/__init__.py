@@ -61,6 +61,8 @@ def _load():
         lib.orc_mesh_set_bc.argtypes = [vp, ip, C.c_int64, C.c_int, C.c_double]
         lib.orc_mesh_geometry.argtypes = [vp, dp, dp, lp, dp, dp, dp]
         lib.orc_mesh_set_fields.argtypes = [vp, dp, dp]
+        lib.orc_boundary_discharge.restype = C.c_int
+        lib.orc_boundary_discharge.argtypes = [vp, dp, dp, dp, dp]
         lib.orc_mesh_groups.restype = C.c_int
         lib.orc_mesh_groups.argtypes = [vp, C.POINTER(C.c_int), dp, dp]
         lib.orc_hstar.restype = C.c_double
@@ -153,6 +155,13 @@ class Mesh:
         value, glen = np.zeros(64), np.zeros(64)
         ng = _load().orc_mesh_groups(self._h, kind.ctypes.data_as(C.POINTER(C.c_int)), _d(value), _d(glen))
         return kind[:ng].copy(), value[:ng].copy(), glen[:ng].copy()
+
+    def discharge(self, h, hu, hv):
+        """Outward discharge (m^3/s) through each boundary group for this state."""
+        h, hu, hv = _f64(h), _f64(hu), _f64(hv)
+        Q = np.zeros(64)
+        ng = _load().orc_boundary_discharge(self._h, _d(h), _d(hu), _d(hv), _d(Q))
+        return Q[:ng].copy()
 
     def dt(self, h, hu, hv, cfl):
         h, hu, hv = _f64(h), _f64(hu), _f64(hv)

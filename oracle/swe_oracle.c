@@ -504,6 +504,41 @@ double orc_dt(const orc_mesh* M, const double* h, const double* hu, const double
     return cfl * best;
 }
 
+/* Outward discharge through each boundary group for the state (h, hu, hv):
+ * Q_g = sum over the group's edges of L * (mass flux of Section 3.1's boundary
+ * treatment), i.e. the mass leaving through those edges in the next step per
+ * unit time.  Returns the number of groups written to Q. */
+int orc_boundary_discharge(const orc_mesh* M, const double* h, const double* hu, const double* hv, double* Q) {
+    const double g = M->g, h_dry = M->h_dry;
+    for (int k = 0; k < M->n_groups; ++k) Q[k] = 0.0;
+    for (int64_t i = 0; i < M->n_cells; ++i) {
+        for (int j = 0; j < 3; ++j) {
+            int64_t k = M->nbr[3 * i + j];
+            if (k >= 0) continue;
+            int grp = (int)(-1 - k);
+            int kind = M->kind[grp];
+            double hi = h[i], ui = 0.0, vi = 0.0;
+            if (hi > h_dry) { ui = hu[i] / hi; vi = hv[i] / hi; }
+            double n1 = M->nx[3 * i + j], n2 = M->ny[3 * i + j];
+            double G0;
+            if (kind == ORC_BC_WALL) {
+                G0 = 0.0;
+            } else if (kind == ORC_BC_INFLOW) {
+                G0 = -M->value[grp] / M->glen[grp];
+            } else {
+                double un = ui * n1 + vi * n2, ut = -ui * n2 + vi * n1;
+                double hg = hi;
+                if (kind == ORC_BC_STAGE) { hg = M->value[grp] - M->z[i]; if (hg < 0.0) hg = 0.0; }
+                double G[3];
+                orc_hllc(hi, un, ut, hg, un, ut, g, h_dry, G, NULL);
+                G0 = G[0];
+            }
+            Q[grp] += M->len[3 * i + j] * G0;
+        }
+    }
+    return M->n_groups;
+}
+
 /* nsteps steps in place, the time step recomputed after every update.
  * t is advanced by the sum of the steps.  Returns the number of clamps, or
  * -1 if every cell is dry (no time step exists). */

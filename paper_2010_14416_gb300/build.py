@@ -26,6 +26,7 @@ UNITS = [
     ("swe_noalloc.cu", ["--use_fast_math"]),
     ("swe_ensemble.cu", []),
     ("swe_adjoint.cu", []),
+    ("swe_diag.cu", ["--use_fast_math"]),
 ]
 
 

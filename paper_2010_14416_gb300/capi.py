@@ -31,7 +31,7 @@ EXPORTS = ["swe_config_default", "swe_mesh_create", "swe_mesh_destroy", "swe_set
            "swe_get_info", "swe_get_permutation", "swe_mesh_preprocess", "swe_riemann_flux",
            "swe_cfl_dt_noalloc", "swe_ensemble_create", "swe_ensemble_destroy", "swe_ensemble_set_stream",
            "swe_ensemble_step", "swe_ensemble_get_state", "swe_ensemble_get_info", "swe_adjoint",
-           "swe_step_dt", "swe_set_fields", "swe_last_error"]
+           "swe_step_dt", "swe_set_fields", "swe_diagnostics", "swe_run_to_steady", "swe_last_error"]
 
 
 class swe_config(C.Structure):
@@ -44,6 +44,12 @@ class swe_info(C.Structure):
     _fields_ = [("n_cells", C.c_int64), ("n_steps", C.c_int64), ("n_clamped", C.c_int64),
                 ("t", C.c_double), ("dt_next", C.c_double), ("precision", C.c_int),
                 ("status", C.c_int), ("device_bytes", C.c_int64), ("n_active", C.c_int64)]
+
+
+class swe_diag(C.Structure):
+    _fields_ = [("t", C.c_double), ("dt_last", C.c_double), ("volume", C.c_double), ("dh_max", C.c_double),
+                ("h_max", C.c_double), ("speed_max", C.c_double), ("n_wet", C.c_int64), ("n_groups", C.c_int),
+                ("discharge", C.c_double * 64)]
 
 
 class SWEError(RuntimeError):
@@ -94,6 +100,9 @@ def load():
     lib.swe_adjoint.argtypes = [vp, C.c_int64, C.c_double, vp, C.c_int, vp, C.c_int, vp, vp, vp, C.c_int, vp]
     lib.swe_step_dt.argtypes = [vp, C.c_int64, vp, vp]
     lib.swe_set_fields.argtypes = [vp, vp, vp]
+    lib.swe_diagnostics.argtypes = [vp, C.POINTER(swe_diag)]
+    lib.swe_run_to_steady.argtypes = [vp, C.c_double, C.c_double, C.c_int64, C.c_int64, C.POINTER(C.c_int64),
+                                      C.POINTER(C.c_int), C.POINTER(C.c_double)]
     lib.swe_last_error.argtypes = []
     lib.swe_last_error.restype = C.c_char_p
     for name in EXPORTS:
@@ -252,6 +261,24 @@ class Mesh:
         mm = np.ascontiguousarray(manning, dtype=np.float64) if manning is not None else None
         check(load().swe_set_fields(self._h, b.ctypes.data if b is not None else None,
                                     mm.ctypes.data if mm is not None else None))
+
+    def diagnostics(self):
+        """Volume, last-step depth change, extremes, wet cells and the outward
+        discharge of each boundary group (group 0 = default wall)."""
+        d = swe_diag()
+        check(load().swe_diagnostics(self._h, C.byref(d)))
+        out = {k: getattr(d, k) for k, _ in swe_diag._fields_ if k != "discharge"}
+        out["discharge"] = np.array(d.discharge[: d.n_groups])
+        return out
+
+    def run_to_steady(self, tol, cfl=0.9, check_every=100, max_steps=100000):
+        """Steps until max |dh|/dt < tol; returns (steps, converged, t)."""
+        n = C.c_int64(0)
+        conv = C.c_int(0)
+        t = C.c_double(0.0)
+        check(load().swe_run_to_steady(self._h, float(cfl), float(tol), int(check_every), int(max_steps),
+                                       C.byref(n), C.byref(conv), C.byref(t)))
+        return n.value, bool(conv.value), t.value
 
     def permutation(self):
         p = np.empty(self.n_cells, np.int64)

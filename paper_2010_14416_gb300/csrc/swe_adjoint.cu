@@ -410,7 +410,7 @@ int swe_step_dt(swe_mesh* m, int64_t nsteps, const double* dts, double* t_out) {
         e = cudaMemcpyAsync(d.p, dts, nsteps * sizeof(double), cudaMemcpyHostToDevice, st);
     for (int64_t s = 0; s < nsteps && e == cudaSuccess; ++s) {
         e = launch_step_raw(m, m->state[m->nstep % 2], m->state[(m->nstep + 1) % 2], m->small, m->nstep, 1.0,
-                            (const double*)d.p + s, nullptr, st);
+                            (const double*)d.p + s, (double*)(m->small + kSlotDtLast), st);
         ++m->nstep;
     }
     unsigned long long sm[kSmallWords];

@@ -166,7 +166,7 @@ StepArgs<T> make_args(swe_mesh* m, int64_t step_index, double cfl) {
     a.grid = m->grid;
     a.cfl = cfl;
     a.dt_fixed = nullptr;
-    a.dt_log = nullptr;
+    a.dt_log = (double*)(m->small + kSlotDtLast);  // size of the last step, for diagnostics
     a.g = (T)m->cfg.g;
     a.h_dry = (T)m->cfg.h_dry;
     a.bc = m->bc;

@@ -44,7 +44,7 @@ void set_error(const std::string& msg);
 
 // Words of a mesh's device status block.
 constexpr int kSmallWords = 8;
-constexpr int kSlotT = 3, kSlotStatus = 4, kSlotClamp = 5, kSlotActive = 6;
+constexpr int kSlotT = 3, kSlotStatus = 4, kSlotClamp = 5, kSlotActive = 6, kSlotDtLast = 7;
 
 }  // namespace swe
 

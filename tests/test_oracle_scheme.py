@@ -242,3 +242,28 @@ def test_rotation_invariance():
     assert oracle.rel_err(hb, ha) < 1e-10
     assert oracle.rel_err(c * hua - s * hva, hub) < 1e-9
     assert oracle.rel_err(s * hua + c * hva, hvb) < 1e-9
+
+
+def test_boundary_discharge_closed_forms_and_discrete_volume_balance():
+    # inflow group carries exactly -Q outward, walls carry nothing, and the
+    # stored volume changes by exactly -dt * (sum of outward discharges) in
+    # one step, because interior fluxes cancel (Eq 9)
+    mi = mg.river(60, 12, Lx=1200.0, Ly=240.0, seed=3, Q=150.0, n_bumps=10)
+    M = _mesh(mi)
+    area = M.geometry()["area"]
+    h, hu, hv = mi.h, mi.hu, mi.hv
+    for _ in range(30):
+        Q = M.discharge(h, hu, hv)
+        assert Q[0] == 0.0                                  # walls
+        assert Q[1] == pytest.approx(-150.0, rel=1e-13)     # inflow
+        dt = M.dt(h, hu, hv, 0.9)
+        h2, hu2, hv2, c = M.step(h, hu, hv, dt)
+        assert c == 0
+        dV = (area * h2).sum() - (area * h).sum()
+        assert dV == pytest.approx(-dt * Q.sum(), rel=1e-9, abs=1e-9 * (area * h).sum())
+        h, hu, hv = h2, hu2, hv2
+    # the outflow through the stage edge is positive once water reaches it
+    mi2 = mg.canal(40, 4, 40.0, 4.0, 0.2, 2, hL=2.0, hR=2.0)
+    M2 = oracle.Mesh(mi2.nodes, mi2.tris, mi2.z, mi2.manning)
+    M2.set_bc(mg._side_pairs(40, 4)["right"].astype(np.int32), oracle.BC_STAGE, 1.0)
+    assert M2.discharge(mi2.h, mi2.hu, mi2.hv)[1] > 0.0
