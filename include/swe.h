@@ -69,6 +69,9 @@ extern "C" {
 #define SWE_HOST 0
 #define SWE_DEVICE 1
 
+#define SWE_FLUX_HLLC 0       /* Eq 17-25 with the HLLC third component (Eq 24), the paper's scheme */
+#define SWE_FLUX_HLL 1        /* Eq 17-18 for all three components (the HLL flux the paper starts from) */
+
 typedef struct swe_mesh swe_mesh;
 
 typedef struct swe_config {
@@ -87,6 +90,7 @@ typedef struct swe_config {
                          stages): FP32 (128|256|512, 1, 1), (128, 8, 1), (256, 4|5, 1),
                          (512, 2, 1), (256, 4, 2|3|4), (128, 8, 3|4); FP64 (128|256|512, 1, 1),
                          (128|256, 1, 2); others give SWE_EINVAL */
+    int flux;         /* SWE_FLUX_HLLC (default) or SWE_FLUX_HLL */
 } swe_config;
 
 /* Fills *cfg with the defaults listed above. */
@@ -246,6 +250,19 @@ SWE_API int swe_adjoint(swe_mesh* mesh, int64_t nsteps, double cfl, const int32_
                         const double* target_h, int checkpoint_every, double* loss, double* grad_manning,
                         double* grad_bathy, int where, double* dts_out);
 
+/*
+ * Same as swe_adjoint for a time-series misfit: observations every obs_every
+ * steps (obs_every must divide nsteps),
+ *   loss = sum_{o=1..nsteps/obs_every} sum_k (h[gauge_cells[k]]^{o obs_every} - targets[o-1][k])^2,
+ *   targets: [nsteps/obs_every][n_gauges] host doubles.
+ * The adjoint adds each observation's residual to the adjoint state as the
+ * reverse sweep passes its step.  swe_adjoint is the case obs_every = nsteps.
+ */
+SWE_API int swe_adjoint_series(swe_mesh* mesh, int64_t nsteps, double cfl, const int32_t* gauge_cells,
+                               int n_gauges, const double* targets, int64_t obs_every, int checkpoint_every,
+                               double* loss, double* grad_manning, double* grad_bathy, int where,
+                               double* dts_out);
+
 /* Advances nsteps steps with prescribed step sizes dts[nsteps] (host array,
  * each > 0) instead of the CFL step: the frozen-dt map that swe_adjoint
  * differentiates.  t_out (nullable) receives the time reached; waits. */
@@ -350,6 +367,11 @@ SWE_API int swe_mesh_preprocess(const double* nodes, int64_t n_nodes, const int3
 SWE_API int swe_cfl_dt_noalloc(int precision, int64_t n, const void* h, const void* hu, const void* hv,
                                const void* rin, double g, double h_dry, double cfl, double* dt_out,
                                void* cuda_stream);
+
+/* swe_riemann_flux with a choice of flux (SWE_FLUX_HLLC or SWE_FLUX_HLL). */
+SWE_API int swe_riemann_flux_kind(int precision, int flux, int64_t n, const void* hL, const void* unL,
+                                  const void* utL, const void* hR, const void* unR, const void* utR, double g,
+                                  double h_dry, void* G1, void* G2, void* G3, void* S, void* cuda_stream);
 
 /* Message of the last failed call on this thread ("" if none). */
 SWE_API const char* swe_last_error(void);

@@ -68,6 +68,8 @@ def _load():
         lib.orc_hstar.restype = C.c_double
         lib.orc_hstar.argtypes = [C.c_double] * 5 + [dp]
         lib.orc_hllc.argtypes = [C.c_double] * 8 + [dp, dp]
+        lib.orc_hll.argtypes = [C.c_double] * 8 + [dp]
+        lib.orc_mesh_set_flux.argtypes = [vp, C.c_int]
         lib.orc_friction_update.argtypes = [C.c_double] * 10 + [dp]
         lib.orc_step.restype = C.c_int64
         lib.orc_step.argtypes = [vp, dp, dp, dp, C.c_double, dp, dp, dp]
@@ -149,6 +151,10 @@ class Mesh:
                                   nbr.ctypes.data_as(C.POINTER(C.c_int64)), _d(ln), _d(nx), _d(ny))
         return dict(area=area, rin=rin, nbr=nbr, len=ln, nx=nx, ny=ny)
 
+    def set_flux(self, hll_only):
+        """0: HLLC (default), 1: HLL for all three components."""
+        _load().orc_mesh_set_flux(self._h, int(bool(hll_only)))
+
     def groups(self):
         """Boundary groups as (kind[], value[], total length[]); group 0 is the wall."""
         kind = np.zeros(64, np.int32)
@@ -227,6 +233,14 @@ def hllc(hL, unL, utL, hR, unR, utR, g=G_DEFAULT, h_dry=H_DRY_DEFAULT):
     _load().orc_hllc(float(hL), float(unL), float(utL), float(hR), float(unR), float(utR),
                      float(g), float(h_dry), _d(G), _d(S))
     return G, S
+
+
+def hll(hL, unL, utL, hR, unR, utR, g=G_DEFAULT, h_dry=H_DRY_DEFAULT):
+    """HLL flux (Eq 17-18) for all three components in the normal frame."""
+    G = np.zeros(3)
+    _load().orc_hll(float(hL), float(unL), float(utL), float(hR), float(unR), float(utR),
+                    float(g), float(h_dry), _d(G))
+    return G
 
 
 def friction_update(h, hu, hv, Rh, Rhu, Rhv, m, dt, g=G_DEFAULT, h_dry=H_DRY_DEFAULT):

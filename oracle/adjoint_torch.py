@@ -208,6 +208,25 @@ def loss_and_gradient(M: "oracle.Mesh", h0, hu0, hv0, dts, gauges, target, segme
     return float(L.detach()), gm.numpy(), gz.numpy()
 
 
+def loss_and_gradient_series(M: "oracle.Mesh", h0, hu0, hv0, dts, gauges, targets, obs_every, segment=None):
+    """Time-series misfit sum_o sum_g (h_g^{o k} - targets[o-1, g])^2 with
+    observations every k = obs_every steps, and its gradient w.r.t.
+    (manning, bathy)."""
+    step = TorchStep(M)
+    z = torch.tensor(M.z, requires_grad=True)
+    m = torch.tensor(M.m, requires_grad=True)
+    h, hu, hv = (torch.tensor(np.asarray(a, np.float64)) for a in (h0, hu0, hv0))
+    gi = torch.tensor(np.asarray(gauges, np.int64))
+    tg = torch.tensor(np.asarray(targets, np.float64))
+    L = torch.zeros((), dtype=torch.float64)
+    for o in range(len(dts) // obs_every):
+        d = dts[o * obs_every:(o + 1) * obs_every]
+        h, hu, hv = run(step, h, hu, hv, z, m, d, segment or obs_every)
+        L = L + ((h[gi] - tg[o]) ** 2).sum()
+    gz, gm = torch.autograd.grad(L, [z, m])
+    return float(L.detach()), gm.numpy(), gz.numpy()
+
+
 def loss_only(M: "oracle.Mesh", h0, hu0, hv0, dts, gauges, target, z=None, m=None):
     step = TorchStep(M)
     zz = torch.tensor(M.z if z is None else z)

@@ -70,6 +70,7 @@ typedef struct {
     int kind[ORC_MAX_GROUPS];
     double value[ORC_MAX_GROUPS];  /* Q (m^3/s) for inflow, eta_s (m) for stage */
     double glen[ORC_MAX_GROUPS];   /* total edge length of the group */
+    int hll_only;                  /* 1: HLL for all three components (Eq 17-18) */
 } orc_mesh;
 
 /* ------------------------------------------------------------------------ */
@@ -329,6 +330,23 @@ void orc_hllc(double hL, double unL, double utL, double hR, double unR, double u
     if (speeds) { speeds[0] = SL; speeds[1] = SR; speeds[2] = Sstar; }
 }
 
+/* HLL flux for all three components (Eq 17-18 applied to U_3 = h ut as
+ * well), with the same wave-speed estimates as orc_hllc. */
+void orc_hll(double hL, double unL, double utL, double hR, double unR, double utR,
+             double g, double h_dry, double G[3]) {
+    double S[3];
+    orc_hllc(hL, unL, utL, hR, unR, utR, g, h_dry, G, S);
+    if ((hL <= h_dry && hR <= h_dry)) return;          /* both dry: zero flux */
+    double SL = S[0], SR = S[1];
+    double GL3 = hL * unL * utL, GR3 = hR * unR * utR;
+    if (SL >= 0.0) G[2] = GL3;
+    else if (SR <= 0.0) G[2] = GR3;
+    else G[2] = (SR * GL3 - SL * GR3 + SR * SL * (hR * utR - hL * utL)) / (SR - SL);
+}
+
+/* Selects the flux: 0 = HLLC (default), 1 = HLL. */
+void orc_mesh_set_flux(orc_mesh* M, int hll_only) { M->hll_only = hll_only ? 1 : 0; }
+
 /* ------------------------------------------------------------------------ */
 /* Semi-implicit Manning friction (Eq 31-37)                                 */
 /* ------------------------------------------------------------------------ */
@@ -401,7 +419,8 @@ static void orc_cell_rhs(const orc_mesh* M, int64_t i, const double* h, const do
             double hRs = hk + zk - zs; if (hRs < 0.0) hRs = 0.0; /* h**_ji */
             double unL = ui * n1 + vi * n2, utL = -ui * n2 + vi * n1;   /* T_n (Eq 12) */
             double unR = uk * n1 + vk * n2, utR = -uk * n2 + vk * n1;
-            orc_hllc(hLs, unL, utL, hRs, unR, utR, g, h_dry, G, NULL);
+            if (M->hll_only) orc_hll(hLs, unL, utL, hRs, unR, utR, g, h_dry, G);
+            else orc_hllc(hLs, unL, utL, hRs, unR, utR, g, h_dry, G, NULL);
             double s = 0.5 * g * (hLs * hLs - hi * hi);          /* Eq 30 with 1/2 */
             src[0] += L * s * n1;
             src[1] += L * s * n2;
@@ -419,7 +438,8 @@ static void orc_cell_rhs(const orc_mesh* M, int64_t i, const double* h, const do
                 double unL = ui * n1 + vi * n2, utL = -ui * n2 + vi * n1;
                 double hg = hi;
                 if (kind == ORC_BC_STAGE) { hg = M->value[grp] - zi; if (hg < 0.0) hg = 0.0; }
-                orc_hllc(hi, unL, utL, hg, unL, utL, g, h_dry, G, NULL);
+                if (M->hll_only) orc_hll(hi, unL, utL, hg, unL, utL, g, h_dry, G);
+                else orc_hllc(hi, unL, utL, hg, unL, utL, g, h_dry, G, NULL);
             }
         }
         /* back to (x, y): T_n^{-1} G (Eq 12) */

@@ -21,6 +21,7 @@ SWE_FP64, SWE_FP32 = 0, 1
 SWE_REORDER_NONE, SWE_REORDER_RCM, SWE_REORDER_HILBERT = 0, 1, 2
 SWE_BC_WALL, SWE_BC_INFLOW, SWE_BC_TRANSMISSIVE, SWE_BC_STAGE = 0, 1, 2, 3
 SWE_HOST, SWE_DEVICE = 0, 1
+SWE_FLUX_HLLC, SWE_FLUX_HLL = 0, 1
 
 ERROR_NAMES = {1: "SWE_EINVAL", 2: "SWE_EMESH", 3: "SWE_ENOMEM", 4: "SWE_ECUDA",
                5: "SWE_ENONFINITE", 6: "SWE_EDRY", 7: "SWE_ETIMEOUT"}
@@ -28,16 +29,17 @@ ERROR_NAMES = {1: "SWE_EINVAL", 2: "SWE_EMESH", 3: "SWE_ENOMEM", 4: "SWE_ECUDA",
 # every symbol include/swe.h declares
 EXPORTS = ["swe_config_default", "swe_mesh_create", "swe_mesh_destroy", "swe_set_bc",
            "swe_set_stream", "swe_set_state", "swe_step", "swe_get_state", "swe_synchronize",
-           "swe_get_info", "swe_get_permutation", "swe_mesh_preprocess", "swe_riemann_flux",
+           "swe_get_info", "swe_get_permutation", "swe_mesh_preprocess", "swe_riemann_flux", "swe_riemann_flux_kind",
            "swe_cfl_dt_noalloc", "swe_ensemble_create", "swe_ensemble_destroy", "swe_ensemble_set_stream",
            "swe_ensemble_step", "swe_ensemble_get_state", "swe_ensemble_get_info", "swe_adjoint",
+           "swe_adjoint_series",
            "swe_step_dt", "swe_set_fields", "swe_diagnostics", "swe_run_to_steady", "swe_last_error"]
 
 
 class swe_config(C.Structure):
     _fields_ = [("precision", C.c_int), ("g", C.c_double), ("h_dry", C.c_double),
                 ("reorder", C.c_int), ("block_size", C.c_int), ("graph_steps", C.c_int),
-                ("device", C.c_int), ("min_blocks", C.c_int), ("stages", C.c_int)]
+                ("device", C.c_int), ("min_blocks", C.c_int), ("stages", C.c_int), ("flux", C.c_int)]
 
 
 class swe_info(C.Structure):
@@ -87,6 +89,8 @@ def load():
     lib.swe_get_permutation.argtypes = [vp, vp]
     lib.swe_riemann_flux.argtypes = [C.c_int, C.c_int64] + [vp] * 6 + [C.c_double, C.c_double] + \
         [vp] * 4 + [vp]
+    lib.swe_riemann_flux_kind.argtypes = [C.c_int, C.c_int, C.c_int64] + [vp] * 6 + [C.c_double, C.c_double] + \
+        [vp] * 4 + [vp]
     lib.swe_mesh_preprocess.argtypes = [vp, C.c_int64, vp, C.c_int64, C.c_int, vp, vp, vp, vp, vp]
     lib.swe_cfl_dt_noalloc.argtypes = [C.c_int, C.c_int64, vp, vp, vp, vp, C.c_double, C.c_double,
                                        C.c_double, vp, vp]
@@ -98,6 +102,8 @@ def load():
     lib.swe_ensemble_get_state.argtypes = [vp, C.c_int, vp, vp, vp, C.c_int]
     lib.swe_ensemble_get_info.argtypes = [vp, C.c_int, C.POINTER(swe_info)]
     lib.swe_adjoint.argtypes = [vp, C.c_int64, C.c_double, vp, C.c_int, vp, C.c_int, vp, vp, vp, C.c_int, vp]
+    lib.swe_adjoint_series.argtypes = [vp, C.c_int64, C.c_double, vp, C.c_int, vp, C.c_int64, C.c_int, vp, vp,
+                                       vp, C.c_int, vp]
     lib.swe_step_dt.argtypes = [vp, C.c_int64, vp, vp]
     lib.swe_set_fields.argtypes = [vp, vp, vp]
     lib.swe_diagnostics.argtypes = [vp, C.POINTER(swe_diag)]
@@ -146,7 +152,8 @@ class Mesh:
     """An owned swe_mesh handle (thin wrapper over the C ABI)."""
 
     def __init__(self, nodes, tris, bathy, manning, precision=SWE_FP64, reorder=None,
-                 block_size=0, graph_steps=0, device=0, g=9.81, h_dry=1e-6, min_blocks=0, stages=0):
+                 block_size=0, graph_steps=0, device=0, g=9.81, h_dry=1e-6, min_blocks=0, stages=0,
+                 flux=SWE_FLUX_HLLC):
         lib = load()
         cfg = config_default()
         cfg.precision = precision
@@ -155,6 +162,7 @@ class Mesh:
         cfg.block_size, cfg.graph_steps, cfg.device = block_size, graph_steps, device
         cfg.min_blocks = min_blocks
         cfg.stages = stages
+        cfg.flux = flux
         cfg.g, cfg.h_dry = g, h_dry
         nodes = np.ascontiguousarray(nodes, dtype=np.float64).reshape(-1, 2)
         tris = np.ascontiguousarray(tris, dtype=np.int32).reshape(-1, 3)
@@ -248,6 +256,20 @@ class Mesh:
             pm, pz, where = gm.data_ptr(), gz.data_ptr(), SWE_DEVICE
         check(load().swe_adjoint(self._h, int(nsteps), float(cfl), g.ctypes.data, g.shape[0], t.ctypes.data,
                                  int(checkpoint_every), C.byref(loss), pm, pz, where, dts.ctypes.data))
+        return loss.value, gm, gz, dts
+
+    def adjoint_series(self, nsteps, gauges, targets, obs_every, cfl=0.9, checkpoint_every=50):
+        """Time-series misfit over observations every obs_every steps and its
+        gradient; targets: [nsteps // obs_every, n_gauges].  Returns
+        (loss, grad_manning, grad_bathy, dts)."""
+        g = np.ascontiguousarray(gauges, dtype=np.int32)
+        t = np.ascontiguousarray(targets, dtype=np.float64)
+        loss = C.c_double(0.0)
+        dts = np.zeros(int(nsteps))
+        gm, gz = np.zeros(self.n_cells), np.zeros(self.n_cells)
+        check(load().swe_adjoint_series(self._h, int(nsteps), float(cfl), g.ctypes.data, g.shape[0], t.ctypes.data,
+                                        int(obs_every), int(checkpoint_every), C.byref(loss), gm.ctypes.data,
+                                        gz.ctypes.data, SWE_HOST, dts.ctypes.data))
         return loss.value, gm, gz, dts
 
     def step_dt(self, dts):
@@ -350,7 +372,7 @@ def mesh_preprocess(nodes, tris, reorder=SWE_REORDER_HILBERT):
 
 
 def riemann_flux(precision, hL, unL, utL, hR, unR, utR, G1, G2, G3, S=None, g=9.81, h_dry=1e-6,
-                 stream=None):
+                 stream=None, flux=SWE_FLUX_HLLC):
     """Batched normal-frame Riemann flux on device tensors (parity entry)."""
     n = hL.numel()
     ptrs = [t.data_ptr() for t in (hL, unL, utL, hR, unR, utR)]
@@ -359,7 +381,7 @@ def riemann_flux(precision, hL, unL, utL, hR, unR, utR, G1, G2, G3, S=None, g=9.
     if stream is None:
         import torch
         stream = torch.cuda.current_stream().cuda_stream
-    check(load().swe_riemann_flux(precision, n, *ptrs, g, h_dry, *outs, sp, C.c_void_p(stream)))
+    check(load().swe_riemann_flux_kind(precision, flux, n, *ptrs, g, h_dry, *outs, sp, C.c_void_p(stream)))
 
 
 def cfl_dt_noalloc(precision, h, hu, hv, rin, dt_out, cfl=0.9, g=9.81, h_dry=1e-6, stream=None):

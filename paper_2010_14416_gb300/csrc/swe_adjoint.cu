@@ -48,6 +48,7 @@ struct AdjArgs {
     double* __restrict__ gz;              // dL/dz, accumulated
     long long n;
     double dt, g, h_dry;
+    int hll;
     BcTable bc;
 };
 
@@ -87,12 +88,13 @@ __global__ void __launch_bounds__(128) adj_phase1_kernel(const AdjArgs a) {
             const V4<double> o = a.U[c & kNbrMask];
             double src;
             edge_interior<double>(hi, ui, vi, zi, o.x, o.y, o.z, o.w, n1, n2, (c & kFlipBit) != 0, g, h_dry, F0, F1,
-                                  F2, src);
+                                  F2, src, a.hll != 0);
             sx += src * lx;
             sy += src * ly;
         } else {
             const int grp = -1 - c;
-            edge_boundary<double>(a.bc.kind[grp], a.bc.value[grp], hi, ui, vi, zi, n1, n2, g, h_dry, F0, F1, F2);
+            edge_boundary<double>(a.bc.kind[grp], a.bc.value[grp], hi, ui, vi, zi, n1, n2, g, h_dry, F0, F1, F2,
+                                  a.hll != 0);
         }
         f0 += len * F0;
         f1 += len * F1;
@@ -153,7 +155,7 @@ __global__ void __launch_bounds__(128) adj_phase2_kernel(const AdjArgs a) {
             const V4<double> o = a.U[i];
             D4 src;
             edge_interior<D4>(H, U, V, Z, D4(o.x), D4(o.y), D4(o.z), D4(o.w), D4(n1), D4(n2), (c & kFlipBit) != 0,
-                              D4(g), D4(h_dry), F0, F1, F2, src);
+                              D4(g), D4(h_dry), F0, F1, F2, src, a.hll != 0);
             // this cell's term E_je = (-len F0, -len F1 + src lx, -len F2 + src ly)
             // the neighbour's E_ie = (len F0, len F1 - src_i lx, len F2 - src_i ly),
             // src_i = (g/2)(h**_i^2 - h_i^2) with z* = max(z_i, z_j) as the neighbour forms it
@@ -174,7 +176,7 @@ __global__ void __launch_bounds__(128) adj_phase2_kernel(const AdjArgs a) {
         } else {
             const int grp = -1 - c;
             edge_boundary<D4>(a.bc.kind[grp], a.bc.value[grp], H, U, V, Z, D4(n1), D4(n2), D4(g), D4(h_dry), F0, F1,
-                              F2);
+                              F2, a.hll != 0);
 #pragma unroll
             for (int k = 0; k < 4; ++k)
                 acc[k] += -len * (nuj.x * F0.d[k] + nuj.y * F1.d[k] + nuj.z * F2.d[k]);
@@ -190,19 +192,27 @@ __global__ void __launch_bounds__(128) adj_phase2_kernel(const AdjArgs a) {
     a.gz[jc] += acc[3];
 }
 
-// L = sum_g (h_g - target_g)^2 and lambda^N = dL/dU^N (lambda zeroed before)
+// loss += sum_g (h_g - target_g)^2 for one observation (one thread: fixed order)
 __global__ void adj_loss_kernel(const V4<double>* __restrict__ U, const long long* __restrict__ gauges,
-                                const double* __restrict__ target, int n_gauges, V4<double>* __restrict__ lam,
-                                double* __restrict__ loss) {
+                                const double* __restrict__ target, int n_gauges, double* __restrict__ loss) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        double L = 0.0;
+        double L = *loss;
         for (int k = 0; k < n_gauges; ++k) {
-            const long long c = gauges[k];
-            const double r = U[c].x - target[k];
+            const double r = U[gauges[k]].x - target[k];
             L += r * r;
-            lam[c].x += 2.0 * r;
         }
         *loss = L;
+    }
+}
+
+// lambda^n += d(observation)/dU^n: 2 (h_g - target_g) on the gauges' depths
+__global__ void adj_inject_kernel(const V4<double>* __restrict__ U, const long long* __restrict__ gauges,
+                                  const double* __restrict__ target, int n_gauges, V4<double>* __restrict__ lam) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        for (int k = 0; k < n_gauges; ++k) {
+            const long long c = gauges[k];
+            lam[c].x += 2.0 * (U[c].x - target[k]);
+        }
     }
 }
 
@@ -254,18 +264,18 @@ __global__ void small_init_kernel(unsigned long long* small) {
     if (threadIdx.x < kSmallWords) small[threadIdx.x] = threadIdx.x < 3 ? kInfBits : 0ULL;
 }
 
-}  // namespace
-
-extern "C" {
-
-int swe_adjoint(swe_mesh* m, int64_t nsteps, double cfl, const int32_t* gauge_cells, int n_gauges,
-                const double* target_h, int checkpoint_every, double* loss, double* grad_manning,
-                double* grad_bathy, int where, double* dts_out) {
-    if (!m || nsteps < 1 || !(cfl > 0.0) || !gauge_cells || n_gauges < 1 || !target_h || !loss ||
-        (where != SWE_HOST && where != SWE_DEVICE) || checkpoint_every < 0) {
+// Observations every obs_every steps (obs_every divides nsteps); targets:
+// [nsteps / obs_every][n_gauges].
+int adjoint_impl(swe_mesh* m, int64_t nsteps, double cfl, const int32_t* gauge_cells, int n_gauges,
+                 const double* targets, int64_t obs_every, int checkpoint_every, double* loss,
+                 double* grad_manning, double* grad_bathy, int where, double* dts_out) {
+    if (!m || nsteps < 1 || !(cfl > 0.0) || !gauge_cells || n_gauges < 1 || !targets || !loss ||
+        (where != SWE_HOST && where != SWE_DEVICE) || checkpoint_every < 0 || obs_every < 1 ||
+        nsteps % obs_every != 0) {
         set_error("swe_adjoint: bad arguments");
         return SWE_EINVAL;
     }
+    const int64_t n_obs = nsteps / obs_every;
     if (m->cfg.precision != SWE_FP64) { set_error("swe_adjoint: the adjoint runs on FP64 meshes"); return SWE_EINVAL; }
     if (!m->have_state) { set_error("swe_adjoint: no state set"); return SWE_EINVAL; }
     const int64_t n = m->hm.n_cells;
@@ -296,13 +306,20 @@ int swe_adjoint(swe_mesh* m, int64_t nsteps, double cfl, const int32_t* gauge_ce
     alloc(gmv, n * sizeof(double));
     alloc(gzv, n * sizeof(double));
     alloc(dg_idx, n_gauges * sizeof(long long));
-    alloc(dtarget, n_gauges * sizeof(double));
+    alloc(dtarget, (size_t)n_obs * n_gauges * sizeof(double));
     alloc(dloss, sizeof(double));
     if (e != cudaSuccess) {
         set_error(std::string("swe_adjoint: device allocation failed: ") + cudaGetErrorString(e));
         return SWE_ENOMEM;
     }
-    // forward run: checkpoints every K steps, step sizes logged
+    if (e == cudaSuccess) e = cudaMemsetAsync(dloss.p, 0, sizeof(double), st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dg_idx.p, gint.data(), n_gauges * sizeof(long long), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dtarget.p, targets, (size_t)n_obs * n_gauges * sizeof(double), cudaMemcpyHostToDevice, st);
+    const long long* gi = (const long long*)dg_idx.p;
+    const double* tg = (const double*)dtarget.p;
+    // forward run: checkpoints every K steps, step sizes logged, loss summed
+    // over the observations
     for (int64_t s = 0; s < nsteps && e == cudaSuccess; ++s) {
         void* cur = m->state[m->nstep % 2];
         void* nxt = m->state[(m->nstep + 1) % 2];
@@ -310,6 +327,11 @@ int swe_adjoint(swe_mesh* m, int64_t nsteps, double cfl, const int32_t* gauge_ce
         if (e == cudaSuccess)
             e = launch_step_raw(m, cur, nxt, m->small, m->nstep, cfl, nullptr, (double*)dtlog.p + s, st);
         ++m->nstep;
+        if (e == cudaSuccess && (s + 1) % obs_every == 0) {
+            adj_loss_kernel<<<1, 32, 0, st>>>((const V4<double>*)nxt, gi, tg + ((s + 1) / obs_every - 1) * n_gauges,
+                                             n_gauges, (double*)dloss.p);
+            e = cudaGetLastError();
+        }
     }
     if (e != cudaSuccess) return afail(e, "swe_adjoint: forward");
     std::vector<double> dts(nsteps);
@@ -322,15 +344,13 @@ int swe_adjoint(swe_mesh* m, int64_t nsteps, double cfl, const int32_t* gauge_ce
     for (double d : dts)
         if (!std::isfinite(d)) { set_error("swe_adjoint: forward run went dry"); return SWE_EDRY; }
     if (dts_out) std::memcpy(dts_out, dts.data(), nsteps * sizeof(double));
-    // loss and lambda^N
+    // lambda^N = d(last observation)/dU^N
     e = cudaMemsetAsync(lam.p, 0, sb, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(gmv.p, 0, n * sizeof(double), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(gzv.p, 0, n * sizeof(double), st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dg_idx.p, gint.data(), n_gauges * sizeof(long long), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dtarget.p, target_h, n_gauges * sizeof(double), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) {
-        adj_loss_kernel<<<1, 32, 0, st>>>((const V4<double>*)m->state[m->nstep % 2], (const long long*)dg_idx.p,
-                                         (const double*)dtarget.p, n_gauges, (V4<double>*)lam.p, (double*)dloss.p);
+        adj_inject_kernel<<<1, 32, 0, st>>>((const V4<double>*)m->state[m->nstep % 2], gi,
+                                           tg + (n_obs - 1) * n_gauges, n_gauges, (V4<double>*)lam.p);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) { small_init_kernel<<<1, 32, 0, st>>>((unsigned long long*)small.p); e = cudaGetLastError(); }
@@ -348,6 +368,7 @@ int swe_adjoint(swe_mesh* m, int64_t nsteps, double cfl, const int32_t* gauge_ce
     a.n = n;
     a.g = m->cfg.g;
     a.h_dry = m->cfg.h_dry;
+    a.hll = m->cfg.flux == SWE_FLUX_HLL ? 1 : 0;
     a.bc = m->bc;
     const unsigned grid = (unsigned)((n + 127) / 128);
     // reverse sweep, segment by segment
@@ -363,6 +384,9 @@ int swe_adjoint(swe_mesh* m, int64_t nsteps, double cfl, const int32_t* gauge_ce
             a.dt = dts[n0 + k];
             adj_phase1_kernel<<<grid, 128, 0, st>>>(a);
             adj_phase2_kernel<<<grid, 128, 0, st>>>(a);
+            const int64_t nn = n0 + k;  // lambda now holds lambda^nn
+            if (nn > 0 && nn % obs_every == 0)
+                adj_inject_kernel<<<1, 32, 0, st>>>(a.U, gi, tg + (nn / obs_every - 1) * n_gauges, n_gauges, a.lam);
             e = cudaGetLastError();
         }
     }
@@ -393,6 +417,24 @@ int swe_adjoint(swe_mesh* m, int64_t nsteps, double cfl, const int32_t* gauge_ce
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return afail(e, "swe_adjoint: output");
     return SWE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int swe_adjoint(swe_mesh* m, int64_t nsteps, double cfl, const int32_t* gauge_cells, int n_gauges,
+                const double* target_h, int checkpoint_every, double* loss, double* grad_manning,
+                double* grad_bathy, int where, double* dts_out) {
+    return adjoint_impl(m, nsteps, cfl, gauge_cells, n_gauges, target_h, nsteps, checkpoint_every, loss,
+                        grad_manning, grad_bathy, where, dts_out);
+}
+
+int swe_adjoint_series(swe_mesh* m, int64_t nsteps, double cfl, const int32_t* gauge_cells, int n_gauges,
+                       const double* targets, int64_t obs_every, int checkpoint_every, double* loss,
+                       double* grad_manning, double* grad_bathy, int where, double* dts_out) {
+    return adjoint_impl(m, nsteps, cfl, gauge_cells, n_gauges, targets, obs_every, checkpoint_every, loss,
+                        grad_manning, grad_bathy, where, dts_out);
 }
 
 int swe_step_dt(swe_mesh* m, int64_t nsteps, const double* dts, double* t_out) {

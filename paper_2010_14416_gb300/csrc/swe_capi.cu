@@ -165,6 +165,7 @@ StepArgs<T> make_args(swe_mesh* m, int64_t step_index, double cfl) {
     a.n = m->hm.n_cells;
     a.grid = m->grid;
     a.cfl = cfl;
+    a.hll = m->cfg.flux == SWE_FLUX_HLL ? 1 : 0;
     a.dt_fixed = nullptr;
     a.dt_log = (double*)(m->small + kSlotDtLast);  // size of the last step, for diagnostics
     a.g = (T)m->cfg.g;
@@ -368,6 +369,7 @@ void swe_config_default(swe_config* cfg) {
     cfg->device = 0;
     cfg->min_blocks = 0;
     cfg->stages = 0;
+    cfg->flux = SWE_FLUX_HLLC;
 }
 
 const char* swe_last_error(void) { return g_last_error.c_str(); }
@@ -394,6 +396,7 @@ int swe_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* tris, i
     if (cfg) c = *cfg;
     if (c.precision != SWE_FP64 && c.precision != SWE_FP32) { set_error("swe_mesh_create: bad precision"); return SWE_EINVAL; }
     if (!(c.g > 0.0) || !(c.h_dry > 0.0)) { set_error("swe_mesh_create: g and h_dry must be > 0"); return SWE_EINVAL; }
+    if (c.flux != SWE_FLUX_HLLC && c.flux != SWE_FLUX_HLL) { set_error("swe_mesh_create: unknown flux"); return SWE_EINVAL; }
     if (c.block_size == 0) c.block_size = c.precision == SWE_FP32 ? 256 : 128;
     if (c.block_size != 128 && c.block_size != 256 && c.block_size != 512) {
         set_error("swe_mesh_create: block_size must be 128, 256 or 512");
@@ -612,6 +615,15 @@ int swe_mesh_preprocess(const double* nodes, int64_t n_nodes, const int32_t* tri
 int swe_riemann_flux(int precision, int64_t n, const void* hL, const void* unL, const void* utL,
                      const void* hR, const void* unR, const void* utR, double g, double h_dry, void* G1,
                      void* G2, void* G3, void* S, void* stream) {
+    return swe_riemann_flux_kind(precision, SWE_FLUX_HLLC, n, hL, unL, utL, hR, unR, utR, g, h_dry, G1, G2, G3, S,
+                                 stream);
+}
+
+int swe_riemann_flux_kind(int precision, int flux, int64_t n, const void* hL, const void* unL, const void* utL,
+                          const void* hR, const void* unR, const void* utR, double g, double h_dry, void* G1,
+                          void* G2, void* G3, void* S, void* stream) {
+    if (flux != SWE_FLUX_HLLC && flux != SWE_FLUX_HLL) { set_error("swe_riemann_flux: unknown flux"); return SWE_EINVAL; }
+    const int hll = flux == SWE_FLUX_HLL ? 1 : 0;
     if (n < 0 || (n > 0 && (!hL || !unL || !utL || !hR || !unR || !utR || !G1 || !G2 || !G3))) {
         set_error("swe_riemann_flux: bad arguments");
         return SWE_EINVAL;
@@ -620,11 +632,11 @@ int swe_riemann_flux(int precision, int64_t n, const void* hL, const void* unL, 
     if (precision == SWE_FP32)
         e = Launch<float>::riemann(n, (const float*)hL, (const float*)unL, (const float*)utL, (const float*)hR,
                                    (const float*)unR, (const float*)utR, (float)g, (float)h_dry, (float*)G1,
-                                   (float*)G2, (float*)G3, (float*)S, (cudaStream_t)stream);
+                                   (float*)G2, (float*)G3, (float*)S, hll, (cudaStream_t)stream);
     else if (precision == SWE_FP64)
         e = Launch<double>::riemann(n, (const double*)hL, (const double*)unL, (const double*)utL,
                                     (const double*)hR, (const double*)unR, (const double*)utR, g, h_dry,
-                                    (double*)G1, (double*)G2, (double*)G3, (double*)S, (cudaStream_t)stream);
+                                    (double*)G1, (double*)G2, (double*)G3, (double*)S, hll, (cudaStream_t)stream);
     else {
         set_error("swe_riemann_flux: bad precision");
         return SWE_EINVAL;

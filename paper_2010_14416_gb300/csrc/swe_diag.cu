@@ -85,7 +85,7 @@ template <typename T>
 __global__ void diag_boundary_kernel(const V4<T>* __restrict__ cur, const V4<T>* __restrict__ geoA,
                                      const V4<T>* __restrict__ geoB, const long long* __restrict__ slots,
                                      const int* __restrict__ groups, long long nb, BcTable bc, T g, T h_dry,
-                                     double* __restrict__ q) {
+                                     int hll, double* __restrict__ q) {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nb) return;
     const long long s = slots[k];
@@ -102,7 +102,7 @@ __global__ void diag_boundary_kernel(const V4<T>* __restrict__ cur, const V4<T>*
     cell_velocity<T>(c.x, c.y, c.z, h_dry, ui, vi);
     const int grp = groups[k];
     T F0, F1, F2;
-    edge_boundary<T>(bc.kind[grp], bc.value[grp], c.x, ui, vi, c.w, lx * rl, ly * rl, g, h_dry, F0, F1, F2);
+    edge_boundary<T>(bc.kind[grp], bc.value[grp], c.x, ui, vi, c.w, lx * rl, ly * rl, g, h_dry, F0, F1, F2, hll != 0);
     q[k] = (double)len * (double)F0;
 }
 
@@ -158,7 +158,7 @@ int diagnostics_t(swe_mesh* m, swe_diag* out) {
         if (nb)
             diag_boundary_kernel<T><<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(
                 cur, (const V4<T>*)m->geoA, (const V4<T>*)m->geoB, (const long long*)dslots, (const int*)dgroups, nb,
-                m->bc, (T)m->cfg.g, (T)m->cfg.h_dry, (double*)dq);
+                m->bc, (T)m->cfg.g, (T)m->cfg.h_dry, m->cfg.flux == SWE_FLUX_HLL ? 1 : 0, (double*)dq);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(r.data(), res, kDiagWords * sizeof(double), cudaMemcpyDeviceToHost, st);

@@ -29,6 +29,7 @@ struct swe_ensemble {
     size_t esz = 8;
     int n_members = 0;
     double g = 9.81, h_dry = 1e-6;
+    int hll = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;
     std::vector<int64_t> base, n_cells, first_tile;
@@ -136,6 +137,7 @@ EnsArgs<T> ens_args(swe_ensemble* E, int64_t step_index) {
     a.slot_read = p3;
     a.slot_write = (p3 + 1) % 3;
     a.slot_reset = (p3 + 2) % 3;
+    a.hll = E->hll;
     a.g = (T)9.81;
     a.h_dry = (T)1e-6;
     return a;
@@ -355,8 +357,9 @@ int swe_ensemble_create(swe_mesh* const* members, int n_members, swe_ensemble** 
         if (!m) { set_error("swe_ensemble_create: NULL member"); return SWE_EINVAL; }
         if (!m->have_state) { set_error("swe_ensemble_create: member " + std::to_string(k) + " has no state"); return SWE_EINVAL; }
         if (m->cfg.precision != members[0]->cfg.precision || m->cfg.device != members[0]->cfg.device ||
-            m->cfg.g != members[0]->cfg.g || m->cfg.h_dry != members[0]->cfg.h_dry) {
-            set_error("swe_ensemble_create: members differ in precision, device, g or h_dry");
+            m->cfg.g != members[0]->cfg.g || m->cfg.h_dry != members[0]->cfg.h_dry ||
+            m->cfg.flux != members[0]->cfg.flux) {
+            set_error("swe_ensemble_create: members differ in precision, device, flux, g or h_dry");
             return SWE_EINVAL;
         }
         if (m->topo_dirty) { set_error("swe_ensemble_create: member boundary groups not applied"); return SWE_EINVAL; }
@@ -369,6 +372,7 @@ int swe_ensemble_create(swe_mesh* const* members, int n_members, swe_ensemble** 
     E->n_members = n_members;
     E->g = members[0]->cfg.g;
     E->h_dry = members[0]->cfg.h_dry;
+    E->hll = members[0]->cfg.flux == SWE_FLUX_HLL ? 1 : 0;
     E->stream = members[0]->stream;
     EnsDeviceGuard dg(E->device);
     for (int k = 0; k < n_members; ++k) {

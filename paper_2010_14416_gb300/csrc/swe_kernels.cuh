@@ -63,6 +63,7 @@ struct StepArgs {
     long long n;                       // number of cells
     unsigned grid;                     // blocks launched (grid-stride)
     double cfl;
+    int hll;                           // 1: HLL flux for all components, 0: HLLC
     const double* dt_fixed;            // if set: the step size to take (frozen time steps)
     double* dt_log;                    // if set: receives the step size taken
     T g, h_dry;
@@ -91,6 +92,7 @@ struct EnsArgs {
     unsigned long long* n_active;      // all members (diagnostic)
     long long n_tiles;
     int slot_read, slot_write, slot_reset;
+    int hll;
     T g, h_dry;
     __device__ __forceinline__ int bc_kind(int grp) const { return kind_[grp]; }
     __device__ __forceinline__ double bc_value(int grp) const { return value_[grp]; }
@@ -129,9 +131,11 @@ __device__ __forceinline__ T tmin(T a, T b) { return a < b ? a : b; }
 // normal velocity jump; the two-rarefaction base is clamped at 0; Eq 24 is
 // upwinded (ut_L when S* >= 0); Eq 26 line 2 is the right-dry case; both dry
 // gives no flux.
+// With hll_only the third component is the HLL flux of U_3 = h ut (Eq 18
+// applied to it) instead of the HLLC upwinding of Eq 24.
 template <typename T>
 __device__ __forceinline__ void riemann_hllc(T hL, T unL, T utL, T hR, T unR, T utR, T g, T h_dry,
-                                             T& G1, T& G2, T& G3, T* speeds = nullptr) {
+                                             T& G1, T& G2, T& G3, T* speeds = nullptr, bool hll_only = false) {
     using A = Ar<T>;
     const bool wetL = hL > h_dry, wetR = hR > h_dry;
     if (!wetL && !wetR) {
@@ -170,15 +174,18 @@ __device__ __forceinline__ void riemann_hllc(T hL, T unL, T utL, T hR, T unR, T 
     const T PR = qR * unR + T(0.5) * g * hR * hR;
     if (SL >= T(0)) {                                                                // Eq 17
         G1 = qL; G2 = PL;
+        if (hll_only) G3 = qL * utL;
     } else if (SR <= T(0)) {
         G1 = qR; G2 = PR;
+        if (hll_only) G3 = qR * utR;
     } else {                                                                         // Eq 18
         const T r = A::rcp_(SR - SL);
         const T ss = SR * SL;
         G1 = (SR * qL - SL * qR + ss * (hR - hL)) * r;
         G2 = (SR * PL - SL * PR + ss * (qR - qL)) * r;
+        if (hll_only) G3 = (SR * (qL * utL) - SL * (qR * utR) + ss * (hR * utR - hL * utL)) * r;
     }
-    G3 = G1 * (Ss >= T(0) ? utL : utR);                                              // Eq 24
+    if (!hll_only) G3 = G1 * (Ss >= T(0) ? utL : utR);                               // Eq 24
     if (speeds) { speeds[0] = SL; speeds[1] = SR; speeds[2] = Ss; }
 }
 
@@ -260,7 +267,8 @@ __device__ __forceinline__ void cell_velocity(T h, T hu, T hv, T h_dry, T& u, T&
 // state of the edge's canonical orientation.
 template <typename T>
 __device__ __forceinline__ void edge_interior(T hi, T ui, T vi, T zi, T hk, T huk, T hvk, T zk, T n1, T n2,
-                                              bool flip, T g, T h_dry, T& F0, T& F1, T& F2, T& src) {
+                                              bool flip, T g, T h_dry, T& F0, T& F1, T& F2, T& src,
+                                              bool hll_only = false) {
     T uk, vk;
     cell_velocity<T>(hk, huk, hvk, h_dry, uk, vk);
     // hydrostatic reconstruction (Eq 28): z* = max(z_i, z_k)
@@ -276,7 +284,7 @@ __device__ __forceinline__ void edge_interior(T hi, T ui, T vi, T zi, T hk, T hu
     const T unL = uL * c1 + vL * c2, utL = vL * c1 - uL * c2;
     const T unR = uR * c1 + vR * c2, utR = vR * c1 - uR * c2;
     T G1, G2, G3;
-    riemann_hllc<T>(hL, unL, utL, hR, unR, utR, g, h_dry, G1, G2, G3);
+    riemann_hllc<T>(hL, unL, utL, hR, unR, utR, g, h_dry, G1, G2, G3, nullptr, hll_only);
     // back to (x, y) (Eq 12 inverse), as the flux leaving this cell
     const T s = flip ? T(-1) : T(1);
     F0 = s * G1;
@@ -288,7 +296,7 @@ __device__ __forceinline__ void edge_interior(T hi, T ui, T vi, T zi, T hk, T hu
 // Flux leaving cell i through a boundary edge of the given kind (Section 3.1).
 template <typename T>
 __device__ __forceinline__ void edge_boundary(int kind, double value, T hi, T ui, T vi, T zi, T n1, T n2, T g,
-                                              T h_dry, T& F0, T& F1, T& F2) {
+                                              T h_dry, T& F0, T& F1, T& F2, bool hll_only = false) {
     const T un = ui * n1 + vi * n2, ut = vi * n1 - ui * n2;
     T G1, G2, G3;
     if (kind == kBcWall) {
@@ -301,7 +309,7 @@ __device__ __forceinline__ void edge_boundary(int kind, double value, T hi, T ui
     } else {
         T hg = hi;
         if (kind == kBcStage) hg = tmax(T(0), T(value) - zi);
-        riemann_hllc<T>(hi, un, ut, hg, un, ut, g, h_dry, G1, G2, G3);
+        riemann_hllc<T>(hi, un, ut, hg, un, ut, g, h_dry, G1, G2, G3, nullptr, hll_only);
     }
     F0 = G1;
     F1 = G2 * n1 - G3 * n2;
@@ -396,12 +404,13 @@ __device__ __forceinline__ T update_cell(const Args& a, long long i, const V4<T>
         if (c >= 0) {
             T src;
             edge_interior<T>(hi, ui, vi, zi, o.x, o.y, o.z, o.w, n1, n2, (c & kFlipBit) != 0, g, h_dry, F0, F1, F2,
-                             src);
+                             src, a.hll != 0);
             sx += src * lx;
             sy += src * ly;
         } else {
             const int grp = -1 - c;
-            edge_boundary<T>(a.bc_kind(grp), a.bc_value(grp), hi, ui, vi, zi, n1, n2, g, h_dry, F0, F1, F2);
+            edge_boundary<T>(a.bc_kind(grp), a.bc_value(grp), hi, ui, vi, zi, n1, n2, g, h_dry, F0, F1, F2,
+                             a.hll != 0);
         }
         f0 += len * F0;
         f1 += len * F1;
@@ -651,11 +660,12 @@ template <typename T>
 __global__ void riemann_batch_kernel(long long n, const T* __restrict__ hL, const T* __restrict__ unL,
                                      const T* __restrict__ utL, const T* __restrict__ hR,
                                      const T* __restrict__ unR, const T* __restrict__ utR, T g, T h_dry,
-                                     T* __restrict__ G1, T* __restrict__ G2, T* __restrict__ G3, T* __restrict__ S) {
+                                     T* __restrict__ G1, T* __restrict__ G2, T* __restrict__ G3, T* __restrict__ S,
+                                     int hll) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
         T a, b, c, sp[3];
-        riemann_hllc<T>(hL[i], unL[i], utL[i], hR[i], unR[i], utR[i], g, h_dry, a, b, c, sp);
+        riemann_hllc<T>(hL[i], unL[i], utL[i], hR[i], unR[i], utR[i], g, h_dry, a, b, c, sp, hll != 0);
         G1[i] = a; G2[i] = b; G3[i] = c;
         if (S) { S[3 * i] = sp[0]; S[3 * i + 1] = sp[1]; S[3 * i + 2] = sp[2]; }
     }
@@ -679,7 +689,7 @@ struct Launch {
                               cudaStream_t st);
     static cudaError_t riemann(long long n, const T* hL, const T* unL, const T* utL, const T* hR,
                                const T* unR, const T* utR, T g, T h_dry, T* G1, T* G2, T* G3, T* S,
-                               cudaStream_t st);
+                               int hll, cudaStream_t st);
 };
 
 }  // namespace swe

@@ -102,10 +102,10 @@ cudaError_t Launch<T>::unpack(const V4<T>* s, const long long* perm, T* h, T* hu
 template <typename T>
 cudaError_t Launch<T>::riemann(long long n, const T* hL, const T* unL, const T* utL, const T* hR,
                                const T* unR, const T* utR, T g, T h_dry, T* G1, T* G2, T* G3, T* S,
-                               cudaStream_t st) {
+                               int hll, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     riemann_batch_kernel<T><<<grid_for<T>(n, 256), 256, 0, st>>>(n, hL, unL, utL, hR, unR, utR, g, h_dry,
-                                                                   G1, G2, G3, S);
+                                                                   G1, G2, G3, S, hll);
     return cudaGetLastError();
 }
 

@@ -262,3 +262,33 @@ def gauge_cells(n_cells, n_gauges=64, seed=1):
 def perturbation(n, seed):
     """Seeded standard-normal field xi (used for target runs and directions)."""
     return np.random.default_rng(seed).standard_normal(n)
+
+
+# --------------------------------------------------------------------------
+# Initial conditions of the paper's river experiments, on the synthetic reach
+# --------------------------------------------------------------------------
+
+def inclined_plane(mi: MeshInput, eta_up: float, eta_down: float) -> MeshInput:
+    """Free surface on an inclined plane from eta_up at x = 0 to eta_down at
+    x = Lx, zero velocity (the Montreal initialisation, Section 6.5.1: water
+    gains speed downstream sooner than from a horizontal plane)."""
+    x = mi.centroids()[:, 0]
+    Lx = mi.meta.get("Lx", float(x.max()))
+    eta = eta_up + (eta_down - eta_up) * x / Lx
+    mi.h = np.maximum(eta - mi.z, 0.0)
+    mi.hu = np.zeros_like(mi.h)
+    mi.hv = np.zeros_like(mi.h)
+    mi.meta.update(init="inclined_plane", eta_up=eta_up, eta_down=eta_down)
+    return mi
+
+
+def dam_failure(mi: MeshInput, x_dam: float, h_up: float = 30.0, h_down: float = 29.0) -> MeshInput:
+    """One-dimensional Riemann problem on the reach: water depth h_up upstream
+    of x_dam and h_down downstream, zero velocity (the fictitious dam failure,
+    Section 6.4.2, 30 m / 29 m)."""
+    x = mi.centroids()[:, 0]
+    mi.h = np.where(x < x_dam, h_up, h_down).astype(np.float64)
+    mi.hu = np.zeros_like(mi.h)
+    mi.hv = np.zeros_like(mi.h)
+    mi.meta.update(init="dam_failure", x_dam=x_dam, h_up=h_up, h_down=h_down)
+    return mi

@@ -162,3 +162,15 @@ def test_full_size_adjoint_1m_cells_2000_steps():
         errs.append(abs(fd - ad) / abs(ad))
     assert np.median(errs) <= 1e-5, errs
     m.close()
+
+
+def test_adjoint_time_series_matches_reference_gradient():
+    from tests.test_oracle_adjoint import _series_targets
+    mi, M, dts, gauges, target = _setup(True, steps=90)
+    targets = _series_targets(mi, 90, 30)[:, gauges]
+    L_ref, gm_ref, gz_ref = at.loss_and_gradient_series(M, mi.h, mi.hu, mi.hv, dts, gauges, targets, 30)
+    m = _gpu_mesh(mi)
+    L, gm, gz, _ = m.adjoint_series(90, gauges, targets, 30, checkpoint_every=20)
+    assert L == pytest.approx(L_ref, rel=1e-9)
+    assert _rel(gm, gm_ref) <= TOL and _rel(gz, gz_ref) <= TOL
+    m.close()

@@ -332,3 +332,46 @@ def test_full_size_river_13m_first_step_and_fp32_against_fp64():
     assert t32 == pytest.approx(t64, rel=1e-4)
     for a, b in zip(s32, s64):
         assert rel_err(a, b) <= FP32_TOL
+
+
+@pytest.mark.parametrize("init", ["inclined_plane", "dam_failure"])
+def test_river_initialisations_fp64(init):
+    # the paper's other river initial states (Sections 6.5.1 and 6.4.2) on
+    # the synthetic reach: GPU against the oracle after 600 steps
+    mi = mg.river(160, 32, seed=9)
+    if init == "inclined_plane":
+        mi = mg.inclined_plane(mi, eta_up=3.0, eta_down=1.0)
+    else:
+        mi = mg.dam_failure(mi, x_dam=10000.0)
+    M = _orc_mesh(mi)
+    oh, ohu, ohv, ot, oc = M.run(mi.h, mi.hu, mi.hv, 600, 0.9)
+    (gh, ghu, ghv), t, info = _gpu_run(mi, 600)
+    assert t == pytest.approx(ot, rel=1e-12) and info["n_clamped"] == oc
+    for a, b in ((gh, oh), (ghu, ohu), (ghv, ohv)):
+        assert rel_err(a, b) <= FP64_TOL
+
+
+@pytest.mark.parametrize("precision", [capi.SWE_FP64, capi.SWE_FP32])
+def test_hll_flux_variant(precision):
+    # the HLL flux (Eq 17-18 for all components) against the oracle's
+    n = 3000
+    st = _random_states(n, 11)
+    tdt = torch.float64 if precision == capi.SWE_FP64 else torch.float32
+    dev = [torch.tensor(a, dtype=tdt, device="cuda") for a in st]
+    G = [torch.empty(n, dtype=tdt, device="cuda") for _ in range(3)]
+    capi.riemann_flux(precision, *dev, *G, flux=capi.SWE_FLUX_HLL)
+    torch.cuda.synchronize()
+    got = np.stack([g.double().cpu().numpy() for g in G], axis=1)
+    ref = np.array([oracle.hll(*(float(a[i]) for a in st)) for i in range(n)])
+    err = np.abs(got - ref).max(axis=1) / np.maximum(np.abs(ref).max(axis=1), 1.0)
+    tol = 1e-13 if precision == capi.SWE_FP64 else 2e-5
+    assert (err > tol).sum() <= (0 if precision == capi.SWE_FP64 else n // 500)
+    if precision == capi.SWE_FP64:
+        mi = mg.river(160, 32, seed=5)
+        M = _orc_mesh(mi)
+        M.set_flux(1)
+        oh, ohu, ohv, ot, oc = M.run(mi.h, mi.hu, mi.hv, 1000, 0.9)
+        (gh, ghu, ghv), t, info = _gpu_run(mi, 1000, flux=capi.SWE_FLUX_HLL)
+        assert t == pytest.approx(ot, rel=1e-12)
+        for a, b in ((gh, oh), (ghu, ohu), (ghv, ohv)):
+            assert rel_err(a, b) <= FP64_TOL

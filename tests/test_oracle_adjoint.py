@@ -84,3 +84,47 @@ def test_reverse_gradient_matches_forward_mode():
         _, d = torch.func.jvp(loss, (torch.tensor(M.z), torch.tensor(M.m)), (vz, vm))
         ad = float(gz @ vz.numpy() + gm @ vm.numpy())
         assert abs(float(d) - ad) <= 1e-10 * max(abs(ad), 1e-12), (float(d), ad)
+
+
+def _series_targets(mi, steps, every, seed=2):
+    xi = mg.perturbation(mi.n_cells, seed + 100)
+    T = oracle.Mesh(mi.nodes, mi.tris, mi.z + 0.05 * xi, mi.manning * (1 + 0.1 * xi))
+    for pairs, kind, value in mi.bcs:
+        T.set_bc(pairs, kind, value)
+    h, hu, hv = mi.h, mi.hu, mi.hv
+    out = []
+    for _ in range(steps // every):
+        h, hu, hv, _, _ = T.run(h, hu, hv, every, 0.9)
+        out.append(h)
+    return np.array(out)
+
+
+def test_series_reference_reduces_to_final_loss_and_matches_differences():
+    mi, M, dts, gauges, target, _ = _case(True, steps=60)
+    L1, gm1, gz1 = at.loss_and_gradient(M, mi.h, mi.hu, mi.hv, dts, gauges, target)
+    L2, gm2, gz2 = at.loss_and_gradient_series(M, mi.h, mi.hu, mi.hv, dts, gauges, target[None, :], 60)
+    assert L2 == pytest.approx(L1, rel=1e-14)
+    assert np.allclose(gm2, gm1, rtol=1e-12, atol=0) and np.allclose(gz2, gz1, rtol=1e-12, atol=0)
+    targets = _series_targets(mi, 60, 20)[:, gauges]
+    L, gm, gz = at.loss_and_gradient_series(M, mi.h, mi.hu, mi.hv, dts, gauges, targets, 20)
+
+    def c_loss(z, m):
+        M.set_fields(z=z, m=m)
+        h, hu, hv = mi.h, mi.hu, mi.hv
+        tot = 0.0
+        for o in range(3):
+            h, hu, hv, _ = M.run_fixed_dt(h, hu, hv, dts[20 * o:20 * (o + 1)])
+            tot += float(((h[gauges] - targets[o]) ** 2).sum())
+        return tot
+
+    rng = np.random.default_rng(3)
+    z0, m0 = mi.z.copy(), mi.manning.copy()
+    assert c_loss(z0, m0) == pytest.approx(L, rel=1e-10)
+    for _ in range(3):
+        vz = rng.standard_normal(mi.n_cells)
+        vm = 0.01 * rng.standard_normal(mi.n_cells)
+        eps = 1e-4
+        fd = (c_loss(z0 + eps * vz, m0 + eps * vm) - c_loss(z0 - eps * vz, m0 - eps * vm)) / (2 * eps)
+        ad = float(gz @ vz + gm @ vm)
+        assert abs(fd - ad) <= 1e-6 * abs(ad), (fd, ad)
+    M.set_fields(z=z0, m=m0)

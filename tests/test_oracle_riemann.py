@@ -155,3 +155,31 @@ def test_supersonic_branches():
     Gf, S = oracle.hllc(1.0, -12.0, 0.5, 2.0, -13.0, -0.5)
     assert S[1] <= 0
     assert np.allclose(Gf, _phys(2.0, -13.0, -0.5), rtol=1e-14)
+
+
+def test_hll_third_component_closed_form():
+    # a shear wave with equal depth and normal velocity u (subsonic): S_L = u - a,
+    # S_R = u + a (p = 1), and Eq 18 applied to h ut gives by hand
+    # h [ (u+a) u ut_L - (u-a) u ut_R + (u^2 - a^2)(ut_R - ut_L) ] / (2a)
+    h, u, utl, utr = 2.0, 0.7, 1.5, -0.5
+    a = math.sqrt(G * h)
+    Gf = oracle.hll(h, u, utl, h, u, utr)
+    expect = h * ((u + a) * u * utl - (u - a) * u * utr + (u * u - a * a) * (utr - utl)) / (2 * a)
+    assert Gf[2] == pytest.approx(expect, rel=1e-13)
+    # components 1-2 equal HLLC's; consistency and the supersonic branch
+    Gc, _ = oracle.hllc(h, u, utl, h, u, utr)
+    assert np.allclose(Gf[:2], Gc[:2], rtol=0, atol=0)
+    assert np.allclose(oracle.hll(1.3, 0.4, 0.9, 1.3, 0.4, 0.9), _phys(1.3, 0.4, 0.9), rtol=1e-12)
+    assert np.allclose(oracle.hll(1.0, 12.0, 0.5, 2.0, 11.0, -0.5), _phys(1.0, 12.0, 0.5), rtol=1e-14)
+
+
+def test_hll_conservation_symmetry():
+    rng = np.random.default_rng(8)
+    for _ in range(300):
+        hL, hR = rng.uniform(1e-3, 10, 2)
+        unL, unR, utL, utR = rng.uniform(-8, 8, 4)
+        Gf = oracle.hll(hL, unL, utL, hR, unR, utR)
+        Gb = oracle.hll(hR, -unR, -utR, hL, -unL, -utL)
+        assert Gb[0] == pytest.approx(-Gf[0], rel=1e-11, abs=1e-11)
+        assert Gb[1] == pytest.approx(Gf[1], rel=1e-11, abs=1e-11)
+        assert Gb[2] == pytest.approx(Gf[2], rel=1e-11, abs=1e-11)

@@ -267,3 +267,25 @@ def test_boundary_discharge_closed_forms_and_discrete_volume_balance():
     M2 = oracle.Mesh(mi2.nodes, mi2.tris, mi2.z, mi2.manning)
     M2.set_bc(mg._side_pairs(40, 4)["right"].astype(np.int32), oracle.BC_STAGE, 1.0)
     assert M2.discharge(mi2.h, mi2.hu, mi2.hv)[1] > 0.0
+
+
+def test_hll_scheme_conserves_and_balances():
+    # the HLL variant keeps the well-balanced and conservative properties
+    mi = mg.river(60, 12, seed=2, fully_wet=True)
+    eta0 = mi.meta["eta0"]
+    M = oracle.Mesh(mi.nodes, mi.tris, mi.z, mi.manning)
+    M.set_flux(1)
+    M.set_bc(mi.bcs[1][0], oracle.BC_STAGE, eta0)
+    h0 = np.maximum(eta0 - mi.z, 0.0)
+    h, hu, hv, t, c = M.run(h0, np.zeros_like(h0), np.zeros_like(h0), 300, 0.9)
+    assert np.abs(h + mi.z - eta0).max() < 1e-12 and np.abs(hu).max() < 1e-10
+    mi = mg.dam_break_4k()
+    M = oracle.Mesh(mi.nodes, mi.tris, mi.z, mi.manning)
+    M.set_flux(1)
+    area = M.geometry()["area"]
+    h, hu, hv, t, c = M.run(mi.h, mi.hu, mi.hv, 300, 0.9)
+    assert abs((area * h).sum() - (area * mi.h).sum()) / (area * mi.h).sum() < 1e-13
+    # HLL and HLLC differ only through the tangential momentum flux
+    M2 = oracle.Mesh(mi.nodes, mi.tris, mi.z, mi.manning)
+    h2, hu2, hv2, t2, c2 = M2.run(mi.h, mi.hu, mi.hv, 300, 0.9)
+    assert not np.array_equal(hv, hv2)
