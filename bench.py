@@ -34,6 +34,12 @@ import numpy as np  # noqa: E402
 # 1/|Omega|, inscribed radius (4) + L n of three edges (6) values, plus three
 # int32 neighbour indices
 ALG_BYTES = {"f32": 16 * 4 + 12, "f64": 16 * 8 + 12}
+# FP64 flops (2 x DFMA + DADD + DMUL) per cell that runs the flux path, counted
+# by ncu on the 1M-cell canal (profiles/step_kernel_canal1m_fp64.md); quiet
+# cells take no flux path and do no FP64 arithmetic
+FP64_FLOPS_PER_ACTIVE_CELL = 855
+# GB300 FP64: 2 DFMA per clock per SM, 152 SMs
+FP64_DFMA_PER_CLK_SM, N_SM = 2, 152
 
 WORKLOADS = {
     "river13m_fp32": dict(maker="river_13m", precision="f32", steps=1000,
@@ -59,6 +65,14 @@ WORKLOADS = {
 
 
 MEMBERS = [256]
+
+
+def _peak_clock():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return float(json.load(f).get("sm_max_mhz", 2070.0))
+    return 2070.0
 
 
 def _peaks():
@@ -248,6 +262,10 @@ def run_gpu(args, name):
     # replayed before the timed region
     args.warmup = max(args.warmup, 96)
     m.step(args.warmup, 0.9, sync=True)
+    # launch shape chosen by the library's autotuner on the warmed-up state
+    # (the tuning call leaves the state untouched), then the graph is recaptured
+    shape = m.autotune(8)
+    m.step(96, 0.9, sync=True)
     n = mi.n_cells
 
     # ---- device-resident timed region ----
@@ -281,6 +299,7 @@ def run_gpu(args, name):
     m2.set_stream(stream)
     m2.set_state(*hp)
     m2.step(max(args.warmup, 6), 0.9)
+    m2.autotune(8)
     m2.get_state(out)
     if dist:
         dist.barrier()
@@ -309,7 +328,7 @@ def run_gpu(args, name):
     if os.path.exists(tpath):
         with open(tpath) as f:
             tr = json.load(f)
-        if tr.get("kernel_hash") == _kernel_hash():
+        if tr.get("kernel_hash") == _kernel_hash() and tr.get("shape") == _shape_key(shape):
             traffic = tr.get("bytes_per_launch")
     line = {
         "metric": "cell-updates/s",
@@ -327,7 +346,8 @@ def run_gpu(args, name):
         "config": {"workload": wl["desc"], "cells": n, "parallelism": f"replicas{ws}",
                    "l2": "working set ~%.2f GB > 129 MB L2, no flush needed" % (
                        (2 * 4 + 8) * n * (4 if wl["precision"] == "f32" else 8) / 1e9 + 16 * n / 1e9),
-                   "simulated_time_s": t_sim, "reorder": "hilbert", "graph_steps": 48},
+                   "simulated_time_s": t_sim, "reorder": "hilbert", "graph_steps": 48,
+                   "launch_shape": _shape_key(shape), "autotune": shape},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
@@ -345,6 +365,21 @@ def run_gpu(args, name):
         "gpu_launches": args.steps,
         "clocks": clk,
     }
+    if wl["precision"] == "f64":
+        # the FP64 step is bound by the FP64 pipe, not HBM: report it against
+        # the FP64 ALU peak at the maximum SM clock; the HBM figures stay as context
+        sm_mhz = _peak_clock()
+        peak64 = FP64_DFMA_PER_CLK_SM * 2 * N_SM * sm_mhz * 1e6 / 1e12
+        flops = FP64_FLOPS_PER_ACTIVE_CELL * active_frac * n
+        ach64 = flops / (kernel_ms * 1e-3) / 1e12
+        hbm = line["roofline"]
+        line["roofline"] = {"bound": "alu", "achieved": ach64, "peak": peak64, "unit": "TFLOP/s",
+                            "frac": ach64 / peak64, "traffic": traffic,
+                            "peak_source": f"derived: {FP64_DFMA_PER_CLK_SM} DFMA/clk/SM x 2 flops x {N_SM} SMs x "
+                                           f"{sm_mhz:.0f} MHz (FP64 pipe)",
+                            "flops_per_active_cell": FP64_FLOPS_PER_ACTIVE_CELL,
+                            "active_cell_fraction": active_frac,
+                            "hbm": {k: v for k, v in hbm.items() if k not in ("bound", "traffic")}}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(mi, args.cpu_budget)
     m.close()
@@ -389,6 +424,8 @@ def run_gpu_ensemble(args, name):
     ens.set_stream(stream)
     args.warmup = max(args.warmup, 6)
     ens.step(args.warmup)
+    shape = ens.autotune(4)       # launch shape chosen by the library's autotuner
+    ens.step(6)
     # the timed call is captured once (untimed) for its step phase, then replayed
     ens.step(args.steps)
     realign = (-args.steps) % 6          # back to the same step phase mod 6
@@ -408,9 +445,13 @@ def run_gpu_ensemble(args, name):
     torch.cuda.synchronize(dev)
     ms = ev0.elapsed_time(ev1)
     clk = clocks.stop() if rank == 0 else None
-    # per-member launches of the plain solver, same steps
+    # per-member launches of the plain solver, same steps; each member's launch
+    # shape is autotuned on its own mesh as well
+    member_shapes = []
     for m in meshes:
         m.step(96)
+        member_shapes.append(m.autotune(4))
+        m.step(48)
     torch.cuda.synchronize(dev)
     ev0.record(stream)
     for m in meshes:
@@ -431,7 +472,9 @@ def run_gpu_ensemble(args, name):
         "ms_per_step": kernel_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": wl["precision"], "data": "synthetic",
         "config": {"workload": wl["desc"], "cells": n, "members": len(mis), "parallelism": f"replicas{ws}",
-                   "l2": "working set > 129 MB L2, no flush needed"},
+                   "l2": "working set > 129 MB L2, no flush needed",
+                   "launch_shape": _shape_key(shape), "autotune": shape,
+                   "member_shapes": sorted({tuple(_shape_key(t)[:3]) for t in member_shapes})},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None, "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
                      "alg_bytes_per_cell": ab},
@@ -539,6 +582,12 @@ def run_gpu_adjoint(args, name):
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def _shape_key(t):
+    """(block, min_blocks, stages, grid[, chunk]) of an autotuner choice."""
+    k = [t["block_size"], t["min_blocks"], t["stages"], t["grid"]]
+    return k + [t["chunk"]] if t.get("chunk") else k
 
 
 def _kernel_hash():

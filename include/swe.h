@@ -373,6 +373,45 @@ SWE_API int swe_riemann_flux_kind(int precision, int flux, int64_t n, const void
                                   const void* utL, const void* hR, const void* unR, const void* utR, double g,
                                   double h_dry, void* G1, void* G2, void* G3, void* S, void* cuda_stream);
 
+/* ---- launch-shape autotuner ---- */
+
+typedef struct swe_tune {
+    int block_size;          /* chosen threads per block */
+    int min_blocks;          /* chosen resident-block target the kernel is compiled for */
+    int stages;              /* chosen cp.async staging depth (1 = direct loads) */
+    int chunk;               /* ensembles: tiles per round-robin chunk; 0 for a mesh */
+    int64_t grid;            /* blocks launched per step */
+    double cells_per_thread; /* cells each thread updates per step: cells / (grid * block_size) */
+    double ms_best;          /* measured time per step of the chosen shape (ms) */
+    double ms_before;        /* measured time per step of the shape in use before the call (ms) */
+    int n_candidates;        /* shapes timed */
+} swe_tune;
+
+/*
+ * Chooses the step kernel's launch shape for this mesh by measurement: every
+ * compiled (block_size, min_blocks, stages) shape (see swe_config) with several
+ * grid sizes -- one or two resident waves looping over the cells, or 1, 2 or 4
+ * cells per thread -- is timed with CUDA events over trial_steps steps
+ * (>= 1; 0 = 8), twice, and the fastest is kept for all later steps.  The
+ * paper fixes no launch shape; every shape evaluates the same arithmetic on
+ * every cell, so the choice changes the speed only: states, times and time
+ * steps are bit for bit the same whatever is chosen.  The trial steps read the
+ * current state and write scratch copies of the state and status block, so
+ * the mesh's state, time and step count do not change.  Allocates one state
+ * buffer for the duration of the call and waits for the mesh stream.
+ * out may be NULL.  Errors: SWE_EINVAL (no state set), SWE_ENOMEM, SWE_ECUDA.
+ */
+SWE_API int swe_autotune(swe_mesh* mesh, int trial_steps, swe_tune* out);
+
+/*
+ * The same for an ensemble's batched step: its compiled (block_size,
+ * min_blocks, stages) shapes (FP32: (256, 4, 3|1|2), (128, 8, 3|1); FP64:
+ * (256|128, 1, 1|2)) times chunks of 4 to 64 tiles, then grids of half, one
+ * and two resident waves for the best of those.  Members' states, times and
+ * steps are unchanged by the call and by the choice.  trial_steps 0 = 4.
+ */
+SWE_API int swe_ensemble_autotune(swe_ensemble* ens, int trial_steps, swe_tune* out);
+
 /* Message of the last failed call on this thread ("" if none). */
 SWE_API const char* swe_last_error(void);
 

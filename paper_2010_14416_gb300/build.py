@@ -27,6 +27,7 @@ UNITS = [
     ("swe_ensemble.cu", []),
     ("swe_adjoint.cu", []),
     ("swe_diag.cu", ["--use_fast_math"]),
+    ("swe_tune.cu", []),
 ]
 
 

@@ -33,7 +33,8 @@ EXPORTS = ["swe_config_default", "swe_mesh_create", "swe_mesh_destroy", "swe_set
            "swe_cfl_dt_noalloc", "swe_ensemble_create", "swe_ensemble_destroy", "swe_ensemble_set_stream",
            "swe_ensemble_step", "swe_ensemble_get_state", "swe_ensemble_get_info", "swe_adjoint",
            "swe_adjoint_series",
-           "swe_step_dt", "swe_set_fields", "swe_diagnostics", "swe_run_to_steady", "swe_last_error"]
+           "swe_step_dt", "swe_set_fields", "swe_diagnostics", "swe_run_to_steady", "swe_autotune",
+           "swe_ensemble_autotune", "swe_last_error"]
 
 
 class swe_config(C.Structure):
@@ -52,6 +53,12 @@ class swe_diag(C.Structure):
     _fields_ = [("t", C.c_double), ("dt_last", C.c_double), ("volume", C.c_double), ("dh_max", C.c_double),
                 ("h_max", C.c_double), ("speed_max", C.c_double), ("n_wet", C.c_int64), ("n_groups", C.c_int),
                 ("discharge", C.c_double * 64)]
+
+
+class swe_tune(C.Structure):
+    _fields_ = [("block_size", C.c_int), ("min_blocks", C.c_int), ("stages", C.c_int), ("chunk", C.c_int),
+                ("grid", C.c_int64), ("cells_per_thread", C.c_double), ("ms_best", C.c_double),
+                ("ms_before", C.c_double), ("n_candidates", C.c_int)]
 
 
 class SWEError(RuntimeError):
@@ -109,6 +116,8 @@ def load():
     lib.swe_diagnostics.argtypes = [vp, C.POINTER(swe_diag)]
     lib.swe_run_to_steady.argtypes = [vp, C.c_double, C.c_double, C.c_int64, C.c_int64, C.POINTER(C.c_int64),
                                       C.POINTER(C.c_int), C.POINTER(C.c_double)]
+    lib.swe_autotune.argtypes = [vp, C.c_int, C.POINTER(swe_tune)]
+    lib.swe_ensemble_autotune.argtypes = [vp, C.c_int, C.POINTER(swe_tune)]
     lib.swe_last_error.argtypes = []
     lib.swe_last_error.restype = C.c_char_p
     for name in EXPORTS:
@@ -302,6 +311,13 @@ class Mesh:
                                        C.byref(n), C.byref(conv), C.byref(t)))
         return n.value, bool(conv.value), t.value
 
+    def autotune(self, trial_steps=8):
+        """Times the step kernel's compiled launch shapes on the current state
+        (which does not change) and keeps the fastest; returns the choice."""
+        t = swe_tune()
+        check(load().swe_autotune(self._h, int(trial_steps), C.byref(t)))
+        return {k: getattr(t, k) for k, _ in swe_tune._fields_}
+
     def permutation(self):
         p = np.empty(self.n_cells, np.int64)
         check(load().swe_get_permutation(self._h, p.ctypes.data))
@@ -348,6 +364,13 @@ class Ensemble:
         ptrs = [_ptr(o, self.dtype) for o in out]
         check(load().swe_ensemble_get_state(self._h, int(member), ptrs[0][0], ptrs[1][0], ptrs[2][0], ptrs[0][1]))
         return out
+
+    def autotune(self, trial_steps=4):
+        """Times the batched kernel's launch shapes (tile size, staging, chunk,
+        grid) on the current states and keeps the fastest; returns the choice."""
+        t = swe_tune()
+        check(load().swe_ensemble_autotune(self._h, int(trial_steps), C.byref(t)))
+        return {k: getattr(t, k) for k, _ in swe_tune._fields_}
 
     def info(self, member):
         inf = swe_info()

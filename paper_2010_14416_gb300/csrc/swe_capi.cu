@@ -354,6 +354,8 @@ cudaError_t launch_step_raw(swe_mesh* m, const void* in, void* out, unsigned lon
 
 int flush_mesh_bc(swe_mesh* m) { return flush_topo(m); }
 
+void drop_mesh_graph(swe_mesh* m) { drop_graph(m); }
+
 }  // namespace swe
 
 extern "C" {

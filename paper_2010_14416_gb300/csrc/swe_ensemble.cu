@@ -2,7 +2,7 @@
 // (swe_ensemble_* in include/swe.h).
 //
 // The members' device arrays are copied into one concatenated layout, each
-// member padded to whole tiles of kEnsBlock cells.  Padding cells are dry
+// member padded to a whole multiple of kEnsPad cells.  Padding cells are dry
 // cells with three wall edges: they take the quiet path and never change.
 // Neighbour codes are offset to the concatenated numbering and boundary
 // groups to one global table (group 0 = wall).  Every member keeps its own
@@ -33,7 +33,7 @@ struct swe_ensemble {
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;
     std::vector<int64_t> base, n_cells, first_tile;
-    int64_t n_total = 0, n_tiles = 0;
+    int64_t n_total = 0, n_tiles = 0;    // n_tiles counts kEnsPad-cell spans
     void* state[2] = {nullptr, nullptr};
     void* geoA = nullptr;
     void* geoB = nullptr;
@@ -49,6 +49,8 @@ struct swe_ensemble {
     double* value = nullptr;
     void* stage[3] = {nullptr, nullptr, nullptr};
     int64_t stage_cells = 0;
+    // launch shape (autotuned by swe_ensemble_autotune; none changes the results)
+    int block = 256, min_blocks = 1, stages = 1, chunk_log2 = 5;
     unsigned grid = 0;
     int64_t nstep = 0;
     std::vector<double> cfl_host;
@@ -133,7 +135,8 @@ EnsArgs<T> ens_args(swe_ensemble* E, int64_t step_index) {
     a.kind_ = E->kind;
     a.value_ = E->value;
     a.n_active = E->n_active;
-    a.n_tiles = E->n_tiles;
+    a.n_total = E->n_total;
+    a.chunk_log2 = E->chunk_log2;
     a.slot_read = p3;
     a.slot_write = (p3 + 1) % 3;
     a.slot_reset = (p3 + 2) % 3;
@@ -152,7 +155,17 @@ cudaError_t ens_launch(swe_ensemble* E, int64_t step_index, const EnsPhysics& ph
     EnsArgs<T> a = ens_args<T>(E, step_index);
     a.g = (T)ph.g;
     a.h_dry = (T)ph.h_dry;
-    return Launch<T>::ensemble_step(a, E->grid, st);
+    return Launch<T>::ensemble_step(a, E->block, E->min_blocks, E->stages, E->grid, st);
+}
+
+// blocks of one resident wave of the given ensemble kernel shape
+template <typename T>
+cudaError_t ens_wave(swe_ensemble* E, int block, int min_blocks, int stages, long long* wave) {
+    int per_sm = 0, sms = 0;
+    cudaError_t e = Launch<T>::ensemble_resident_blocks(block, min_blocks, stages, &per_sm);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, E->device);
+    *wave = (long long)std::max(per_sm, 1) * std::max(sms, 1);
+    return e;
 }
 
 template <typename T>
@@ -167,11 +180,11 @@ int ens_build(swe_ensemble* E, swe_mesh* const* M) {
     for (int k = 0; k < nm; ++k) {
         E->base[k] = off;
         E->n_cells[k] = M[k]->hm.n_cells;
-        E->first_tile[k] = off / kEnsBlock;
-        off += (M[k]->hm.n_cells + kEnsBlock - 1) / kEnsBlock * kEnsBlock;
+        E->first_tile[k] = off / kEnsPad;
+        off += (M[k]->hm.n_cells + kEnsPad - 1) / kEnsPad * kEnsPad;
     }
     E->n_total = off;
-    E->n_tiles = off / kEnsBlock;
+    E->n_tiles = off / kEnsPad;
     if (E->n_total >= (int64_t)kNbrMask) { set_error("swe_ensemble_create: too many cells in total"); return SWE_EINVAL; }
     int rc;
     if ((rc = ens_alloc(E, &E->state[0], off * v4, "state")) || (rc = ens_alloc(E, &E->state[1], off * v4, "state")) ||
@@ -238,10 +251,10 @@ int ens_build(swe_ensemble* E, swe_mesh* const* M) {
             topo[b + c] = make_int4(code[0], code[1], code[2], w);
             perm[b + c] = m->hm.perm[c];
         }
-        for (int64_t c = n; c < (E->n_cells[k] + kEnsBlock - 1) / kEnsBlock * kEnsBlock; ++c)
+        for (int64_t c = n; c < (E->n_cells[k] + kEnsPad - 1) / kEnsPad * kEnsPad; ++c)
             topo[b + c] = make_int4(wall_code, wall_code, wall_code, 0);
         const int64_t t0 = E->first_tile[k];
-        const int64_t t1 = (b + (n + kEnsBlock - 1) / kEnsBlock * kEnsBlock) / kEnsBlock;
+        const int64_t t1 = (b + (n + kEnsPad - 1) / kEnsPad * kEnsPad) / kEnsPad;
         for (int64_t t = t0; t < t1; ++t) tile_member[t] = k;
     }
     std::vector<long long> mft(E->first_tile.begin(), E->first_tile.end());
@@ -275,11 +288,11 @@ int ens_build(swe_ensemble* E, swe_mesh* const* M) {
     if (d_first) cudaFree(d_first);
     if (d_t0) cudaFree(d_t0);
     if (e != cudaSuccess) return efail(e, "swe_ensemble_create: upload");
-    int per_sm = 0, sms = 0;
-    e = Launch<T>::ensemble_resident_blocks(&per_sm);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, E->device);
+    Launch<T>::ensemble_default(&E->block, &E->min_blocks, &E->stages);
+    long long wave = 0;
+    e = ens_wave<T>(E, E->block, E->min_blocks, E->stages, &wave);
     if (e != cudaSuccess) return efail(e, "swe_ensemble_create: occupancy");
-    E->grid = (unsigned)std::min<long long>(E->n_tiles, (long long)std::max(per_sm, 1) * std::max(sms, 1));
+    E->grid = (unsigned)std::min<long long>((long long)(E->n_total / E->block), wave);
     E->cfl_host.assign(nm, -1.0);
     return SWE_OK;
 }
@@ -328,6 +341,131 @@ int ens_get_state(swe_ensemble* E, int k, void* h, void* hu, void* hv, int where
         e = cudaMemcpyAsync(dst[j], E->stage[j], n * sizeof(T), cudaMemcpyDeviceToHost, E->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(E->stream);
     return e == cudaSuccess ? SWE_OK : efail(e, "swe_ensemble_get_state");
+}
+
+// ---- launch-shape autotuner (swe_ensemble_autotune) --------------------------------
+// Trial steps read the current state and write a scratch state buffer, a
+// scratch copy of the members' status blocks and a scratch activity counter:
+// nothing the ensemble holds changes.  First every compiled (block,
+// min_blocks, stages) shape with every chunk size at one resident wave, then
+// grids of half, one and two waves for the best of those.
+
+struct EnsShape {
+    int block, min_blocks, stages, chunk_log2;
+    unsigned grid;
+};
+
+template <typename T>
+int ens_time_shapes(swe_ensemble* E, const std::vector<EnsShape>& cand, int trial_steps, void* scratch,
+                    unsigned long long* small, unsigned long long* act, std::vector<double>& ms) {
+    cudaStream_t st = E->stream;
+    const int rounds = 2;
+    std::vector<cudaEvent_t> ev(2 * rounds * cand.size(), nullptr);
+    cudaError_t e = cudaSuccess;
+    for (auto& x : ev)
+        if (e == cudaSuccess) e = cudaEventCreate(&x);
+    for (int r = 0; r < rounds && e == cudaSuccess; ++r)
+        for (size_t c = 0; c < cand.size() && e == cudaSuccess; ++c) {
+            EnsArgs<T> a = ens_args<T>(E, E->nstep);
+            a.s_out = (V4<T>*)scratch;
+            a.small = small;
+            a.n_active = act;
+            a.chunk_log2 = cand[c].chunk_log2;
+            a.g = (T)E->g;
+            a.h_dry = (T)E->h_dry;
+            const EnsShape& sh = cand[c];
+            e = Launch<T>::ensemble_step(a, sh.block, sh.min_blocks, sh.stages, sh.grid, st);  // warm-up
+            if (e == cudaSuccess) e = cudaEventRecord(ev[2 * (r * cand.size() + c)], st);
+            for (int s = 0; s < trial_steps && e == cudaSuccess; ++s)
+                e = Launch<T>::ensemble_step(a, sh.block, sh.min_blocks, sh.stages, sh.grid, st);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[2 * (r * cand.size() + c) + 1], st);
+        }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    ms.assign(cand.size(), 1e300);
+    for (int r = 0; r < rounds && e == cudaSuccess; ++r)
+        for (size_t c = 0; c < cand.size() && e == cudaSuccess; ++c) {
+            float t = 0.f;
+            e = cudaEventElapsedTime(&t, ev[2 * (r * cand.size() + c)], ev[2 * (r * cand.size() + c) + 1]);
+            ms[c] = std::min(ms[c], (double)t / trial_steps);
+        }
+    for (auto& x : ev)
+        if (x) cudaEventDestroy(x);
+    return e == cudaSuccess ? SWE_OK : efail(e, "swe_ensemble_autotune: trial steps");
+}
+
+template <typename T>
+int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
+    const EnsShape before{E->block, E->min_blocks, E->stages, E->chunk_log2, E->grid};
+    std::vector<EnsShape> cand{before};
+    int v[16][3];
+    const int nv = std::min(Launch<T>::ensemble_variants(v, 16), 16);
+    for (int k = 0; k < nv; ++k) {
+        long long wave = 0;
+        cudaError_t e = ens_wave<T>(E, v[k][0], v[k][1], v[k][2], &wave);
+        if (e != cudaSuccess) return efail(e, "swe_ensemble_autotune: occupancy");
+        const unsigned gr = (unsigned)std::max(1LL, std::min((long long)(E->n_total / v[k][0]), wave));
+        for (int cl2 = 2; cl2 <= 6; ++cl2) {
+            const EnsShape sh{v[k][0], v[k][1], v[k][2], cl2, gr};
+            if (!(sh.block == before.block && sh.min_blocks == before.min_blocks && sh.stages == before.stages &&
+                  sh.chunk_log2 == before.chunk_log2 && sh.grid == before.grid))
+                cand.push_back(sh);
+        }
+    }
+    void* scratch = nullptr;
+    unsigned long long *small = nullptr, *act = nullptr;
+    const size_t small_bytes = 8 * (size_t)E->n_members * sizeof(unsigned long long);
+    if (cudaMalloc(&scratch, (size_t)E->n_total * sizeof(V4<T>)) != cudaSuccess ||
+        cudaMalloc(&small, small_bytes) != cudaSuccess || cudaMalloc(&act, sizeof(unsigned long long)) != cudaSuccess) {
+        for (void* p : {scratch, (void*)small, (void*)act})
+            if (p) cudaFree(p);
+        set_error("swe_ensemble_autotune: no device memory for the scratch state");
+        return SWE_ENOMEM;
+    }
+    cudaError_t e = cudaMemcpyAsync(small, E->small, small_bytes, cudaMemcpyDeviceToDevice, E->stream);
+    int rc = e == cudaSuccess ? SWE_OK : efail(e, "swe_ensemble_autotune: status copy");
+    std::vector<double> ms;
+    if (!rc) rc = ens_time_shapes<T>(E, cand, trial_steps, scratch, small, act, ms);
+    size_t best = 0;
+    std::vector<EnsShape> cand2;
+    std::vector<double> ms2;
+    if (!rc) {
+        for (size_t c = 1; c < cand.size(); ++c)
+            if (ms[c] < ms[best]) best = c;
+        long long wave = 0;
+        const EnsShape b = cand[best];
+        e = ens_wave<T>(E, b.block, b.min_blocks, b.stages, &wave);
+        if (e != cudaSuccess) rc = efail(e, "swe_ensemble_autotune: occupancy");
+        const long long tiles = (long long)(E->n_total / b.block);
+        for (long long gsz : {wave / 2, 2 * wave}) {
+            const unsigned gr = (unsigned)std::max(1LL, std::min(tiles, gsz));
+            if (!rc && gr != b.grid) cand2.push_back({b.block, b.min_blocks, b.stages, b.chunk_log2, gr});
+        }
+        if (!rc && !cand2.empty()) rc = ens_time_shapes<T>(E, cand2, trial_steps, scratch, small, act, ms2);
+    }
+    for (void* p : {scratch, (void*)small, (void*)act}) cudaFree(p);
+    if (rc) return rc;
+    EnsShape pick = cand[best];
+    double ms_pick = ms[best];
+    for (size_t c = 0; c < cand2.size(); ++c)
+        if (ms2[c] < ms_pick) { pick = cand2[c]; ms_pick = ms2[c]; }
+    E->block = pick.block;
+    E->min_blocks = pick.min_blocks;
+    E->stages = pick.stages;
+    E->chunk_log2 = pick.chunk_log2;
+    E->grid = pick.grid;
+    drop_graphs(E);
+    if (out) {
+        out->block_size = pick.block;
+        out->min_blocks = pick.min_blocks;
+        out->stages = pick.stages;
+        out->chunk = 1 << pick.chunk_log2;
+        out->grid = pick.grid;
+        out->cells_per_thread = (double)E->n_total / ((double)pick.grid * pick.block);
+        out->ms_best = ms_pick;
+        out->ms_before = ms[0];
+        out->n_candidates = (int)(cand.size() + cand2.size());
+    }
+    return SWE_OK;
 }
 
 }  // namespace
@@ -454,6 +592,14 @@ int swe_ensemble_step(swe_ensemble* E, int64_t nsteps, const double* cfl, double
         return rc;
     }
     return SWE_OK;
+}
+
+int swe_ensemble_autotune(swe_ensemble* E, int trial_steps, swe_tune* out) {
+    if (!E || trial_steps < 0) { set_error("swe_ensemble_autotune: bad arguments"); return SWE_EINVAL; }
+    if (trial_steps == 0) trial_steps = 4;
+    EnsDeviceGuard dg(E->device);
+    return E->precision == SWE_FP32 ? ens_autotune_t<float>(E, trial_steps, out)
+                                    : ens_autotune_t<double>(E, trial_steps, out);
 }
 
 int swe_ensemble_get_state(swe_ensemble* E, int member, void* h, void* hu, void* hv, int where) {

@@ -56,6 +56,8 @@ cudaError_t launch_step_raw(swe_mesh* m, const void* in, void* out, unsigned lon
                             double cfl, const double* dt_fixed, double* dt_log, cudaStream_t st);
 // Applies pending boundary-group changes of m to the device.
 int flush_mesh_bc(swe_mesh* m);
+// Drops m's captured CUDA graph (after a change of launch shape).
+void drop_mesh_graph(swe_mesh* m);
 }  // namespace swe
 
 // One mesh: host preprocessing result, device arrays and stepping state.

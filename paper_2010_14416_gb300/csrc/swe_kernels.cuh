@@ -31,7 +31,7 @@ constexpr unsigned kStatusDry = 2u;
 
 constexpr int kBcWall = 0, kBcInflow = 1, kBcTransmissive = 2, kBcStage = 3;
 
-constexpr int kEnsBlock = 256;  // tile of the batched ensemble step (one member per tile)
+constexpr int kEnsPad = 256;  // ensemble members are padded to whole multiples of this many cells
 
 template <typename T>
 struct alignas(4 * sizeof(T)) V4 {
@@ -73,8 +73,9 @@ struct StepArgs {
 };
 
 // Arguments of the batched ensemble step: the members' cells are concatenated,
-// each member padded to whole tiles of BLOCK cells (padding cells are dry and
-// walled in, so they take the quiet path); every tile belongs to one member.
+// each member padded to a whole multiple of kEnsPad cells (padding cells are
+// dry and walled in, so they take the quiet path).  A block works on tiles of
+// BLOCK cells (BLOCK divides kEnsPad), so every tile belongs to one member.
 template <typename T>
 struct EnsArgs {
     const V4<T>* __restrict__ s_in;
@@ -83,14 +84,15 @@ struct EnsArgs {
     const V4<T>* __restrict__ geoB;
     const int4* __restrict__ topo;     // neighbour codes offset to the concatenated numbering
     const T* __restrict__ gm2;         // FP64 only
-    const int* __restrict__ tile_member;
-    const long long* __restrict__ member_first_tile;
+    const int* __restrict__ tile_member;               // member of each kEnsPad-cell span
+    const long long* __restrict__ member_first_tile;   // first kEnsPad-cell span of each member
     const double* __restrict__ cfl;    // per member
     unsigned long long* small;         // per member: 8 words (dt slots 0..2, t, status, clamps, -, -)
     const int* __restrict__ kind_;     // global boundary groups (0 = wall)
     const double* __restrict__ value_;
     unsigned long long* n_active;      // all members (diagnostic)
-    long long n_tiles;
+    long long n_total;                 // cells of the padded layout (a multiple of kEnsPad)
+    int chunk_log2;                    // tiles per round-robin chunk = 2^chunk_log2
     int slot_read, slot_write, slot_reset;
     int hll;
     T g, h_dry;
@@ -523,22 +525,26 @@ __device__ __forceinline__ void warp_min_publish(T cand, unsigned long long* dst
         atomicMin(dst, (unsigned long long)__double_as_longlong((double)cand));
 }
 
-// Tiles are dealt to blocks in round-robin chunks of kEnsChunk tiles, which
-// balances wet (expensive) and dry (cheap) members across the GPU while the
-// member still changes only at chunk or member boundaries.
-constexpr int kEnsChunk = 32;
-
-__device__ __forceinline__ long long ens_tile_of(long long k, long long nchunk_stride, long long b) {
-    return (b + (k / kEnsChunk) * nchunk_stride) * kEnsChunk + (k % kEnsChunk);
+// Tiles are dealt to blocks in round-robin chunks of 2^chunk_log2 tiles,
+// which balances wet (expensive) and dry (cheap) members across the GPU while
+// the member still changes only at chunk or member boundaries.  The chunk
+// size, the tile size BLOCK and the grid are launch shapes chosen by the
+// autotuner; none of them changes any cell's arithmetic.
+__device__ __forceinline__ long long ens_tile_of(long long k, long long nchunk_stride, long long b, int cl2) {
+    const long long mask = (1LL << cl2) - 1;
+    return ((b + (k >> cl2) * nchunk_stride) << cl2) + (k & mask);
 }
 
 template <typename T, int BLOCK, int MINB, int STAGES>
 __global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel(const EnsArgs<T> a) {
+    static_assert(kEnsPad % BLOCK == 0, "a tile must not straddle two members");
     const long long G = gridDim.x, b = blockIdx.x;
-    const long long n_chunks = (a.n_tiles + kEnsChunk - 1) / kEnsChunk;
+    const int cl2 = a.chunk_log2;
+    const long long n_tiles = a.n_total / BLOCK;
+    const long long n_chunks = (n_tiles + (1LL << cl2) - 1) >> cl2;
     // this block's chunks: b, b + G, b + 2G, ... ; k counts its tiles
     const long long my_chunks = b < n_chunks ? (n_chunks - 1 - b) / G + 1 : 0;
-    const long long k_end = my_chunks * kEnsChunk;
+    const long long k_end = my_chunks << cl2;
     const int tid = threadIdx.x;
     int member = -1;
     unsigned long long* sm = nullptr;
@@ -551,8 +557,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel(const EnsArg
     if constexpr (STAGES > 1) {
 #pragma unroll
         for (int s = 0; s < STAGES - 1; ++s) {
-            const long long tile = ens_tile_of(s, G, b);
-            if (s < k_end && tile < a.n_tiles) {
+            const long long tile = ens_tile_of(s, G, b, cl2);
+            if (s < k_end && tile < n_tiles) {
                 const long long c = tile * BLOCK + tid;
                 cp_async_record<sizeof(V4<T>)>(&st_own[s][tid], &a.s_in[c]);
                 cp_async_record<16>(&st_topo[s][tid], &a.topo[c]);
@@ -562,9 +568,10 @@ __global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel(const EnsArg
     }
     int slot = 0;
     for (long long k = 0; k < k_end; ++k) {
-        const long long tile = ens_tile_of(k, G, b);
-        if (tile >= a.n_tiles) break;                      // ragged last chunk
-        const int mk = a.tile_member[tile];                // uniform across the block
+        const long long tile = ens_tile_of(k, G, b, cl2);
+        if (tile >= n_tiles) break;                        // ragged last chunk
+        const long long cell0 = tile * BLOCK;
+        const int mk = a.tile_member[cell0 / kEnsPad];     // uniform across the block
         if (mk != member) {
             if (member >= 0) warp_min_publish<T>(cand, sm + a.slot_write);
             cand = inf_of<T>();
@@ -573,7 +580,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel(const EnsArg
             const double dt_d = a.cfl[mk] * __longlong_as_double((long long)sm[a.slot_read]);
             have_dt = dt_d < __longlong_as_double((long long)kInfBits);
             dt = T(dt_d);
-            if (tile == a.member_first_tile[mk] && tid == 0) {
+            if (cell0 == a.member_first_tile[mk] * kEnsPad && tid == 0) {
                 sm[a.slot_reset] = kInfBits;
                 if (have_dt) *(double*)(sm + 3) += dt_d;
                 else atomicOr((unsigned*)(sm + 4), kStatusDry);
@@ -584,9 +591,9 @@ __global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel(const EnsArg
         int4 tp;
         if constexpr (STAGES > 1) {
             const long long kn = k + STAGES - 1;
-            const long long nt = ens_tile_of(kn, G, b);
+            const long long nt = ens_tile_of(kn, G, b, cl2);
             const int fill = slot == 0 ? STAGES - 1 : slot - 1;
-            if (kn < k_end && nt < a.n_tiles) {
+            if (kn < k_end && nt < n_tiles) {
                 const long long c = nt * BLOCK + tid;
                 cp_async_record<sizeof(V4<T>)>(&st_own[fill][tid], &a.s_in[c]);
                 cp_async_record<16>(&st_topo[fill][tid], &a.topo[c]);
@@ -677,9 +684,14 @@ struct Launch {
     // (block, min_blocks) pairs with a compiled kernel; see step_variants()
     static cudaError_t step(const StepArgs<T>& a, int block, int min_blocks, int stages, cudaStream_t st);
     static cudaError_t resident_blocks(int block, int min_blocks, int stages, int* per_sm);
-    // batched ensemble step: block 256, the default min_blocks and stages of the precision
-    static cudaError_t ensemble_step(const EnsArgs<T>& a, unsigned grid, cudaStream_t st);
-    static cudaError_t ensemble_resident_blocks(int* per_sm);
+    // compiled (block, min_blocks, stages) shapes of the step kernel; returns their number
+    static int step_variants(int (*out)[3], int max);
+    // batched ensemble step with one of its compiled (block, min_blocks, stages) shapes
+    static cudaError_t ensemble_step(const EnsArgs<T>& a, int block, int min_blocks, int stages, unsigned grid,
+                                     cudaStream_t st);
+    static cudaError_t ensemble_resident_blocks(int block, int min_blocks, int stages, int* per_sm);
+    static int ensemble_variants(int (*out)[3], int max);
+    static void ensemble_default(int* block, int* min_blocks, int* stages);
     static int default_min_blocks(int block);
     static cudaError_t dt(const V4<T>* s, const V4<T>* geoB, long long n, T g, T h_dry,
                           unsigned long long* dt_write, cudaStream_t st);

@@ -60,22 +60,79 @@ cudaError_t Launch<T>::resident_blocks(int block, int min_blocks, int stages, in
 }
 
 template <typename T>
-struct EnsShape {
-    static constexpr int minb = sizeof(T) == 4 ? 4 : 1;
-    static constexpr int stages = sizeof(T) == 4 ? 3 : 1;
-};
+int Launch<T>::step_variants(int (*out)[3], int max) {
+    int k = 0;
+#define SWE_LIST(B, M, S) \
+    if (k < max) { out[k][0] = B; out[k][1] = M; out[k][2] = S; } \
+    ++k;
+    if constexpr (sizeof(T) == 4) {
+        SWE_STEP_VARIANTS_F32(SWE_LIST)
+    } else {
+        SWE_STEP_VARIANTS_F64(SWE_LIST)
+    }
+#undef SWE_LIST
+    return k;
+}
+
+// Compiled (block, min blocks per SM, stages) shapes of the ensemble kernel;
+// the first of each list is the default.  Blocks divide the 256-cell padding.
+#define SWE_ENS_VARIANTS_F32(X) X(256, 4, 3) X(256, 4, 1) X(256, 4, 2) X(128, 8, 3) X(128, 8, 1)
+#define SWE_ENS_VARIANTS_F64(X) X(256, 1, 1) X(128, 1, 1) X(256, 1, 2) X(128, 1, 2)
 
 template <typename T>
-cudaError_t Launch<T>::ensemble_step(const EnsArgs<T>& a, unsigned grid, cudaStream_t st) {
-    if (grid == 0) return cudaErrorInvalidValue;
-    ensemble_step_kernel<T, kEnsBlock, EnsShape<T>::minb, EnsShape<T>::stages><<<grid, kEnsBlock, 0, st>>>(a);
-    return cudaGetLastError();
+void Launch<T>::ensemble_default(int* block, int* min_blocks, int* stages) {
+    int v[1][3];
+    ensemble_variants(v, 1);
+    *block = v[0][0];
+    *min_blocks = v[0][1];
+    *stages = v[0][2];
 }
 
 template <typename T>
-cudaError_t Launch<T>::ensemble_resident_blocks(int* per_sm) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        per_sm, ensemble_step_kernel<T, kEnsBlock, EnsShape<T>::minb, EnsShape<T>::stages>, kEnsBlock, 0);
+int Launch<T>::ensemble_variants(int (*out)[3], int max) {
+    int k = 0;
+#define SWE_LIST(B, M, S) \
+    if (k < max) { out[k][0] = B; out[k][1] = M; out[k][2] = S; } \
+    ++k;
+    if constexpr (sizeof(T) == 4) {
+        SWE_ENS_VARIANTS_F32(SWE_LIST)
+    } else {
+        SWE_ENS_VARIANTS_F64(SWE_LIST)
+    }
+#undef SWE_LIST
+    return k;
+}
+
+template <typename T>
+cudaError_t Launch<T>::ensemble_step(const EnsArgs<T>& a, int block, int min_blocks, int stages, unsigned grid,
+                                     cudaStream_t st) {
+    if (grid == 0) return cudaErrorInvalidValue;
+#define SWE_LAUNCH(B, M, S) \
+    if (block == B && min_blocks == M && stages == S) {                          \
+        ensemble_step_kernel<T, B, M, S><<<grid, B, 0, st>>>(a);                  \
+        return cudaGetLastError();                                                \
+    }
+    if constexpr (sizeof(T) == 4) {
+        SWE_ENS_VARIANTS_F32(SWE_LAUNCH)
+    } else {
+        SWE_ENS_VARIANTS_F64(SWE_LAUNCH)
+    }
+#undef SWE_LAUNCH
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t Launch<T>::ensemble_resident_blocks(int block, int min_blocks, int stages, int* per_sm) {
+#define SWE_OCC(B, M, S) \
+    if (block == B && min_blocks == M && stages == S)                             \
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, ensemble_step_kernel<T, B, M, S>, B, 0);
+    if constexpr (sizeof(T) == 4) {
+        SWE_ENS_VARIANTS_F32(SWE_OCC)
+    } else {
+        SWE_ENS_VARIANTS_F64(SWE_OCC)
+    }
+#undef SWE_OCC
+    return cudaErrorInvalidValue;
 }
 
 template <typename T>

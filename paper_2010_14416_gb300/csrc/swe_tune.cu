@@ -1,0 +1,166 @@
+// swe_tune.cu -- launch-shape autotuner of the step kernel (swe_autotune).
+//
+// The paper fixes one thread per cell (Section 5.3.2) and no block size; here
+// the shape of the fused step kernel is a measured choice per mesh: every
+// compiled (block, min_blocks, stages) shape, each with several grid sizes
+// (one or two resident waves looping over the cells, or 1, 2 or 4 cells per
+// thread), is timed with CUDA events on the mesh's current state.  The trial
+// steps read the current state and write a scratch state buffer and a scratch
+// copy of the status block, so nothing the mesh holds changes.  Every shape
+// evaluates the same arithmetic on every cell, so the choice changes speed
+// only, never results (the GPU tests check this bit for bit).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "swe_internal.h"
+
+using namespace swe;
+
+namespace {
+
+struct Shape {
+    int block, min_blocks, stages;
+    unsigned grid;
+};
+
+int tfail(cudaError_t e, const char* what) {
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return SWE_ECUDA;
+}
+
+struct TuneDeviceGuard {
+    int prev = -1;
+    explicit TuneDeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~TuneDeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+template <typename T>
+int candidate_shapes(const swe_mesh* m, std::vector<Shape>& cand) {
+    const long long n = m->hm.n_cells;
+    int sms = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->cfg.device);
+    if (e != cudaSuccess) return tfail(e, "swe_autotune: device attribute");
+    cand.push_back({m->cfg.block_size, m->cfg.min_blocks, m->cfg.stages, m->grid});  // the shape in use first
+    int v[64][3];
+    const int nv = std::min(Launch<T>::step_variants(v, 64), 64);
+    for (int k = 0; k < nv; ++k) {
+        int per_sm = 0;
+        e = Launch<T>::resident_blocks(v[k][0], v[k][1], v[k][2], &per_sm);
+        if (e != cudaSuccess) return tfail(e, "swe_autotune: occupancy");
+        const long long need = (n + v[k][0] - 1) / v[k][0];
+        const long long wave = (long long)std::max(per_sm, 1) * std::max(sms, 1);
+        const long long grids[] = {wave, 2 * wave, need, (need + 1) / 2, (need + 3) / 4};
+        for (long long gsz : grids) {
+            const unsigned gr = (unsigned)std::max(1LL, std::min(gsz, need));
+            bool seen = false;
+            for (const Shape& c : cand)
+                seen = seen || (c.block == v[k][0] && c.min_blocks == v[k][1] && c.stages == v[k][2] && c.grid == gr);
+            if (!seen) cand.push_back({v[k][0], v[k][1], v[k][2], gr});
+        }
+    }
+    return SWE_OK;
+}
+
+template <typename T>
+int autotune_t(swe_mesh* m, int trial_steps, swe_tune* out) {
+    const int64_t n = m->hm.n_cells;
+    std::vector<Shape> cand;
+    int rc = candidate_shapes<T>(m, cand);
+    if (rc) return rc;
+    const Shape before = cand[0];
+    cudaStream_t st = m->stream;
+    void* scratch = nullptr;
+    unsigned long long* small = nullptr;
+    cudaError_t e = cudaMalloc(&scratch, (size_t)n * sizeof(V4<T>));
+    if (e != cudaSuccess) {
+        set_error("swe_autotune: no device memory for the scratch state");
+        return SWE_ENOMEM;
+    }
+    e = cudaMalloc(&small, kSmallWords * sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+        cudaFree(scratch);
+        set_error("swe_autotune: no device memory for the scratch status block");
+        return SWE_ENOMEM;
+    }
+    const int rounds = 2;
+    std::vector<cudaEvent_t> ev(2 * rounds * cand.size(), nullptr);
+    for (auto& x : ev)
+        if (e == cudaSuccess) e = cudaEventCreate(&x);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(small, m->small, kSmallWords * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st);
+    const void* cur = m->state[m->nstep % 2];
+    for (int r = 0; r < rounds && e == cudaSuccess; ++r) {
+        for (size_t c = 0; c < cand.size() && e == cudaSuccess; ++c) {
+            m->cfg.block_size = cand[c].block;
+            m->cfg.min_blocks = cand[c].min_blocks;
+            m->cfg.stages = cand[c].stages;
+            m->grid = cand[c].grid;
+            e = launch_step_raw(m, cur, scratch, small, m->nstep, 0.9, nullptr, nullptr, st);  // warm-up
+            if (e == cudaSuccess) e = cudaEventRecord(ev[2 * (r * cand.size() + c)], st);
+            for (int s = 0; s < trial_steps && e == cudaSuccess; ++s)
+                e = launch_step_raw(m, cur, scratch, small, m->nstep, 0.9, nullptr, nullptr, st);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[2 * (r * cand.size() + c) + 1], st);
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    std::vector<double> ms(cand.size(), 1e300);
+    for (int r = 0; r < rounds && e == cudaSuccess; ++r)
+        for (size_t c = 0; c < cand.size() && e == cudaSuccess; ++c) {
+            float t = 0.f;
+            e = cudaEventElapsedTime(&t, ev[2 * (r * cand.size() + c)], ev[2 * (r * cand.size() + c) + 1]);
+            ms[c] = std::min(ms[c], (double)t / trial_steps);
+        }
+    for (auto& x : ev)
+        if (x) cudaEventDestroy(x);
+    cudaFree(scratch);
+    cudaFree(small);
+    size_t best = 0;
+    if (e == cudaSuccess)
+        for (size_t c = 1; c < cand.size(); ++c)
+            if (ms[c] < ms[best]) best = c;
+    const Shape pick = e == cudaSuccess ? cand[best] : before;
+    m->cfg.block_size = pick.block;
+    m->cfg.min_blocks = pick.min_blocks;
+    m->cfg.stages = pick.stages;
+    m->grid = pick.grid;
+    drop_mesh_graph(m);
+    if (e != cudaSuccess) return tfail(e, "swe_autotune: trial steps");
+    if (out) {
+        out->block_size = pick.block;
+        out->min_blocks = pick.min_blocks;
+        out->stages = pick.stages;
+        out->chunk = 0;
+        out->grid = pick.grid;
+        out->cells_per_thread = (double)n / ((double)pick.grid * pick.block);
+        out->ms_best = ms[best];
+        out->ms_before = ms[0];
+        out->n_candidates = (int)cand.size();
+    }
+    return SWE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int swe_autotune(swe_mesh* m, int trial_steps, swe_tune* out) {
+    if (!m || trial_steps < 0) { set_error("swe_autotune: bad arguments"); return SWE_EINVAL; }
+    if (!m->have_state) { set_error("swe_autotune: no state set"); return SWE_EINVAL; }
+    if (trial_steps == 0) trial_steps = 8;
+    TuneDeviceGuard dg(m->cfg.device);
+    int rc = flush_mesh_bc(m);
+    if (rc) return rc;
+    return m->cfg.precision == SWE_FP32 ? autotune_t<float>(m, trial_steps, out)
+                                        : autotune_t<double>(m, trial_steps, out);
+}
+
+}  // extern "C"
