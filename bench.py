@@ -474,7 +474,7 @@ def run_gpu_ensemble(args, name):
         "config": {"workload": wl["desc"], "cells": n, "members": len(mis), "parallelism": f"replicas{ws}",
                    "l2": "working set > 129 MB L2, no flush needed",
                    "launch_shape": _shape_key(shape), "autotune": shape,
-                   "member_shapes": sorted({tuple(_shape_key(t)[:3]) for t in member_shapes})},
+                   "member_shapes": sorted({tuple(_shape_key(t)[:4]) for t in member_shapes})},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None, "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
                      "alg_bytes_per_cell": ab},
@@ -585,8 +585,8 @@ def run_gpu_adjoint(args, name):
 
 
 def _shape_key(t):
-    """(block, min_blocks, stages, grid[, chunk]) of an autotuner choice."""
-    k = [t["block_size"], t["min_blocks"], t["stages"], t["grid"]]
+    """(block, min_blocks, stages, geometry_early, grid[, chunk]) of an autotuner choice."""
+    k = [t["block_size"], t["min_blocks"], t["stages"], t["geometry_early"], t["grid"]]
     return k + [t["chunk"]] if t.get("chunk") else k
 
 

@@ -91,6 +91,11 @@ typedef struct swe_config {
                          (512, 2, 1), (256, 4, 2|3|4), (128, 8, 3|4); FP64 (128|256|512, 1, 1),
                          (128|256, 1, 2); others give SWE_EINVAL */
     int flux;         /* SWE_FLUX_HLLC (default) or SWE_FLUX_HLL */
+    int geometry_early; /* 1: a cell's geometry is loaded together with its neighbours' states
+                           (one memory round trip fewer on wet meshes); 0 (default): only
+                           after the test that skips dry cells among dry neighbours (no
+                           geometry traffic for those).  Compiled with 1: FP32 (256, 4, 1|3),
+                           (128, 8, 1|3); FP64 (128|256, 1, 1).  Results do not depend on it */
 } swe_config;
 
 /* Fills *cfg with the defaults listed above. */
@@ -379,6 +384,7 @@ typedef struct swe_tune {
     int block_size;          /* chosen threads per block */
     int min_blocks;          /* chosen resident-block target the kernel is compiled for */
     int stages;              /* chosen cp.async staging depth (1 = direct loads) */
+    int geometry_early;      /* chosen geometry load placement (swe_config.geometry_early) */
     int chunk;               /* ensembles: tiles per round-robin chunk; 0 for a mesh */
     int64_t grid;            /* blocks launched per step */
     double cells_per_thread; /* cells each thread updates per step: cells / (grid * block_size) */
@@ -389,7 +395,8 @@ typedef struct swe_tune {
 
 /*
  * Chooses the step kernel's launch shape for this mesh by measurement: every
- * compiled (block_size, min_blocks, stages) shape (see swe_config) with several
+ * compiled (block_size, min_blocks, stages, geometry_early) shape (see
+ * swe_config) with several
  * grid sizes -- one or two resident waves looping over the cells, or 1, 2 or 4
  * cells per thread -- is timed with CUDA events over trial_steps steps
  * (>= 1; 0 = 8), twice, and the fastest is kept for all later steps.  The
@@ -405,9 +412,10 @@ SWE_API int swe_autotune(swe_mesh* mesh, int trial_steps, swe_tune* out);
 
 /*
  * The same for an ensemble's batched step: its compiled (block_size,
- * min_blocks, stages) shapes (FP32: (256, 4, 3|1|2), (128, 8, 3|1); FP64:
- * (256|128, 1, 1|2)) times chunks of 4 to 64 tiles, then grids of half, one
- * and two resident waves for the best of those.  Members' states, times and
+ * min_blocks, stages, geometry_early) shapes (FP32: (256, 4, 3|1|2, 0),
+ * (128, 8, 3|1, 0), (256, 4, 3|1, 1), (128, 8, 3|1, 1); FP64: (256|128, 1,
+ * 1|2, 0), (256|128, 1, 1, 1)) times chunks of 4 to 64 tiles, then grids of
+ * half, one and two resident waves for the best of those.  Members' states, times and
  * steps are unchanged by the call and by the choice.  trial_steps 0 = 4.
  */
 SWE_API int swe_ensemble_autotune(swe_ensemble* ens, int trial_steps, swe_tune* out);

@@ -177,7 +177,7 @@ StepArgs<T> make_args(swe_mesh* m, int64_t step_index, double cfl) {
 template <typename T>
 cudaError_t launch_one(swe_mesh* m, int64_t step_index, double cfl, cudaStream_t st) {
     return Launch<T>::step(make_args<T>(m, step_index, cfl), m->cfg.block_size, m->cfg.min_blocks,
-                           m->cfg.stages, st);
+                           m->cfg.stages, m->cfg.geometry_early, st);
 }
 
 template <typename T>
@@ -334,7 +334,8 @@ cudaError_t launch_step_raw(swe_mesh* m, const void* in, void* out, unsigned lon
         a.n_active = small + kSlotActive;
         a.dt_fixed = dt_fixed;
         a.dt_log = dt_log;
-        return Launch<float>::step(a, m->cfg.block_size, m->cfg.min_blocks, m->cfg.stages, st);
+        return Launch<float>::step(a, m->cfg.block_size, m->cfg.min_blocks, m->cfg.stages, m->cfg.geometry_early,
+                                   st);
     }
     StepArgs<double> a = make_args<double>(m, step_index, cfl);
     a.s_in = (const V4<double>*)in;
@@ -349,7 +350,7 @@ cudaError_t launch_step_raw(swe_mesh* m, const void* in, void* out, unsigned lon
     a.n_active = small + kSlotActive;
     a.dt_fixed = dt_fixed;
     a.dt_log = dt_log;
-    return Launch<double>::step(a, m->cfg.block_size, m->cfg.min_blocks, m->cfg.stages, st);
+    return Launch<double>::step(a, m->cfg.block_size, m->cfg.min_blocks, m->cfg.stages, m->cfg.geometry_early, st);
 }
 
 int flush_mesh_bc(swe_mesh* m) { return flush_topo(m); }
@@ -371,6 +372,7 @@ void swe_config_default(swe_config* cfg) {
     cfg->device = 0;
     cfg->min_blocks = 0;
     cfg->stages = 0;
+    cfg->geometry_early = 0;
     cfg->flux = SWE_FLUX_HLLC;
 }
 
@@ -399,6 +401,10 @@ int swe_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* tris, i
     if (c.precision != SWE_FP64 && c.precision != SWE_FP32) { set_error("swe_mesh_create: bad precision"); return SWE_EINVAL; }
     if (!(c.g > 0.0) || !(c.h_dry > 0.0)) { set_error("swe_mesh_create: g and h_dry must be > 0"); return SWE_EINVAL; }
     if (c.flux != SWE_FLUX_HLLC && c.flux != SWE_FLUX_HLL) { set_error("swe_mesh_create: unknown flux"); return SWE_EINVAL; }
+    if (c.geometry_early != 0 && c.geometry_early != 1) {
+        set_error("swe_mesh_create: geometry_early must be 0 or 1");
+        return SWE_EINVAL;
+    }
     if (c.block_size == 0) c.block_size = c.precision == SWE_FP32 ? 256 : 128;
     if (c.block_size != 128 && c.block_size != 256 && c.block_size != 512) {
         set_error("swe_mesh_create: block_size must be 128, 256 or 512");
@@ -443,11 +449,13 @@ int swe_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* tris, i
     if (rc) { swe_mesh_destroy(m); return rc; }
     {
         int per_sm = 0, sms = 0;
-        e = c.precision == SWE_FP32 ? Launch<float>::resident_blocks(c.block_size, c.min_blocks, c.stages, &per_sm)
-                                    : Launch<double>::resident_blocks(c.block_size, c.min_blocks, c.stages, &per_sm);
+        e = c.precision == SWE_FP32
+                ? Launch<float>::resident_blocks(c.block_size, c.min_blocks, c.stages, c.geometry_early, &per_sm)
+                : Launch<double>::resident_blocks(c.block_size, c.min_blocks, c.stages, c.geometry_early, &per_sm);
         if (e == cudaErrorInvalidValue) {
             swe_mesh_destroy(m);
-            set_error("swe_mesh_create: no compiled step kernel for this block_size / min_blocks / stages");
+            set_error("swe_mesh_create: no compiled step kernel for this block_size / min_blocks / stages / "
+                      "geometry_early");
             return SWE_EINVAL;
         }
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device);

@@ -50,7 +50,7 @@ struct swe_ensemble {
     void* stage[3] = {nullptr, nullptr, nullptr};
     int64_t stage_cells = 0;
     // launch shape (autotuned by swe_ensemble_autotune; none changes the results)
-    int block = 256, min_blocks = 1, stages = 1, chunk_log2 = 5;
+    int block = 256, min_blocks = 1, stages = 1, geo_early = 0, chunk_log2 = 5;
     unsigned grid = 0;
     int64_t nstep = 0;
     std::vector<double> cfl_host;
@@ -155,14 +155,14 @@ cudaError_t ens_launch(swe_ensemble* E, int64_t step_index, const EnsPhysics& ph
     EnsArgs<T> a = ens_args<T>(E, step_index);
     a.g = (T)ph.g;
     a.h_dry = (T)ph.h_dry;
-    return Launch<T>::ensemble_step(a, E->block, E->min_blocks, E->stages, E->grid, st);
+    return Launch<T>::ensemble_step(a, E->block, E->min_blocks, E->stages, E->geo_early, E->grid, st);
 }
 
 // blocks of one resident wave of the given ensemble kernel shape
 template <typename T>
-cudaError_t ens_wave(swe_ensemble* E, int block, int min_blocks, int stages, long long* wave) {
+cudaError_t ens_wave(swe_ensemble* E, int block, int min_blocks, int stages, int geo_early, long long* wave) {
     int per_sm = 0, sms = 0;
-    cudaError_t e = Launch<T>::ensemble_resident_blocks(block, min_blocks, stages, &per_sm);
+    cudaError_t e = Launch<T>::ensemble_resident_blocks(block, min_blocks, stages, geo_early, &per_sm);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, E->device);
     *wave = (long long)std::max(per_sm, 1) * std::max(sms, 1);
     return e;
@@ -288,9 +288,9 @@ int ens_build(swe_ensemble* E, swe_mesh* const* M) {
     if (d_first) cudaFree(d_first);
     if (d_t0) cudaFree(d_t0);
     if (e != cudaSuccess) return efail(e, "swe_ensemble_create: upload");
-    Launch<T>::ensemble_default(&E->block, &E->min_blocks, &E->stages);
+    Launch<T>::ensemble_default(&E->block, &E->min_blocks, &E->stages, &E->geo_early);
     long long wave = 0;
-    e = ens_wave<T>(E, E->block, E->min_blocks, E->stages, &wave);
+    e = ens_wave<T>(E, E->block, E->min_blocks, E->stages, E->geo_early, &wave);
     if (e != cudaSuccess) return efail(e, "swe_ensemble_create: occupancy");
     E->grid = (unsigned)std::min<long long>((long long)(E->n_total / E->block), wave);
     E->cfl_host.assign(nm, -1.0);
@@ -347,11 +347,12 @@ int ens_get_state(swe_ensemble* E, int k, void* h, void* hu, void* hv, int where
 // Trial steps read the current state and write a scratch state buffer, a
 // scratch copy of the members' status blocks and a scratch activity counter:
 // nothing the ensemble holds changes.  First every compiled (block,
-// min_blocks, stages) shape with every chunk size at one resident wave, then
+// min_blocks, stages, geometry early) shape with every chunk size at one
+// resident wave, then
 // grids of half, one and two waves for the best of those.
 
 struct EnsShape {
-    int block, min_blocks, stages, chunk_log2;
+    int block, min_blocks, stages, geo_early, chunk_log2;
     unsigned grid;
 };
 
@@ -374,10 +375,10 @@ int ens_time_shapes(swe_ensemble* E, const std::vector<EnsShape>& cand, int tria
             a.g = (T)E->g;
             a.h_dry = (T)E->h_dry;
             const EnsShape& sh = cand[c];
-            e = Launch<T>::ensemble_step(a, sh.block, sh.min_blocks, sh.stages, sh.grid, st);  // warm-up
+            e = Launch<T>::ensemble_step(a, sh.block, sh.min_blocks, sh.stages, sh.geo_early, sh.grid, st);  // warm-up
             if (e == cudaSuccess) e = cudaEventRecord(ev[2 * (r * cand.size() + c)], st);
             for (int s = 0; s < trial_steps && e == cudaSuccess; ++s)
-                e = Launch<T>::ensemble_step(a, sh.block, sh.min_blocks, sh.stages, sh.grid, st);
+                e = Launch<T>::ensemble_step(a, sh.block, sh.min_blocks, sh.stages, sh.geo_early, sh.grid, st);
             if (e == cudaSuccess) e = cudaEventRecord(ev[2 * (r * cand.size() + c) + 1], st);
         }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -395,19 +396,19 @@ int ens_time_shapes(swe_ensemble* E, const std::vector<EnsShape>& cand, int tria
 
 template <typename T>
 int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
-    const EnsShape before{E->block, E->min_blocks, E->stages, E->chunk_log2, E->grid};
+    const EnsShape before{E->block, E->min_blocks, E->stages, E->geo_early, E->chunk_log2, E->grid};
     std::vector<EnsShape> cand{before};
-    int v[16][3];
-    const int nv = std::min(Launch<T>::ensemble_variants(v, 16), 16);
+    int v[32][4];
+    const int nv = std::min(Launch<T>::ensemble_variants(v, 32), 32);
     for (int k = 0; k < nv; ++k) {
         long long wave = 0;
-        cudaError_t e = ens_wave<T>(E, v[k][0], v[k][1], v[k][2], &wave);
+        cudaError_t e = ens_wave<T>(E, v[k][0], v[k][1], v[k][2], v[k][3], &wave);
         if (e != cudaSuccess) return efail(e, "swe_ensemble_autotune: occupancy");
         const unsigned gr = (unsigned)std::max(1LL, std::min((long long)(E->n_total / v[k][0]), wave));
         for (int cl2 = 2; cl2 <= 6; ++cl2) {
-            const EnsShape sh{v[k][0], v[k][1], v[k][2], cl2, gr};
+            const EnsShape sh{v[k][0], v[k][1], v[k][2], v[k][3], cl2, gr};
             if (!(sh.block == before.block && sh.min_blocks == before.min_blocks && sh.stages == before.stages &&
-                  sh.chunk_log2 == before.chunk_log2 && sh.grid == before.grid))
+                  sh.geo_early == before.geo_early && sh.chunk_log2 == before.chunk_log2 && sh.grid == before.grid))
                 cand.push_back(sh);
         }
     }
@@ -433,12 +434,12 @@ int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
             if (ms[c] < ms[best]) best = c;
         long long wave = 0;
         const EnsShape b = cand[best];
-        e = ens_wave<T>(E, b.block, b.min_blocks, b.stages, &wave);
+        e = ens_wave<T>(E, b.block, b.min_blocks, b.stages, b.geo_early, &wave);
         if (e != cudaSuccess) rc = efail(e, "swe_ensemble_autotune: occupancy");
         const long long tiles = (long long)(E->n_total / b.block);
         for (long long gsz : {wave / 2, 2 * wave}) {
             const unsigned gr = (unsigned)std::max(1LL, std::min(tiles, gsz));
-            if (!rc && gr != b.grid) cand2.push_back({b.block, b.min_blocks, b.stages, b.chunk_log2, gr});
+            if (!rc && gr != b.grid) cand2.push_back({b.block, b.min_blocks, b.stages, b.geo_early, b.chunk_log2, gr});
         }
         if (!rc && !cand2.empty()) rc = ens_time_shapes<T>(E, cand2, trial_steps, scratch, small, act, ms2);
     }
@@ -451,6 +452,7 @@ int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
     E->block = pick.block;
     E->min_blocks = pick.min_blocks;
     E->stages = pick.stages;
+    E->geo_early = pick.geo_early;
     E->chunk_log2 = pick.chunk_log2;
     E->grid = pick.grid;
     drop_graphs(E);
@@ -458,6 +460,7 @@ int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
         out->block_size = pick.block;
         out->min_blocks = pick.min_blocks;
         out->stages = pick.stages;
+        out->geometry_early = pick.geo_early;
         out->chunk = 1 << pick.chunk_log2;
         out->grid = pick.grid;
         out->cells_per_thread = (double)E->n_total / ((double)pick.grid * pick.block);

@@ -358,7 +358,12 @@ __device__ __forceinline__ void friction_update(T hi, T qx, T qy, T gm2, T Rh, T
 // its momentum is set to zero by the dry-cell rule after the update.  Its new
 // state is therefore (h, 0, 0) bit for bit whatever the momentum terms were,
 // and the edge loop, geometry and friction are skipped.
-template <typename T, typename Args>
+//
+// GEO_EARLY issues the cell's geometry loads together with the neighbour
+// gathers (one memory round trip fewer for a cell that runs the flux path,
+// at the price of geometry traffic for quiet cells too); otherwise they are
+// issued after the quiet test.  Both give the same results.
+template <typename T, bool GEO_EARLY, typename Args>
 __device__ __forceinline__ T update_cell(const Args& a, long long i, const V4<T>& own, const int4& tp, T dt,
                                          unsigned& active, unsigned long long* n_clamped, unsigned* status) {
     using A = Ar<T>;
@@ -369,6 +374,13 @@ __device__ __forceinline__ T update_cell(const Args& a, long long i, const V4<T>
     V4<T> nb[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) nb[j] = code[j] >= 0 ? a.s_in[code[j] & kNbrMask] : own;
+    V4<T> gA, gB;
+    T gm2;
+    if constexpr (GEO_EARLY) {
+        gA = a.geoA[i];
+        gB = a.geoB[i];
+        gm2 = load_gm2(a, i, tp, T(0));
+    }
     bool quiet = !(hi > h_dry);
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
@@ -387,8 +399,11 @@ __device__ __forceinline__ T update_cell(const Args& a, long long i, const V4<T>
         return inf_of<T>();
     }
     active += 1u;
-    const V4<T> gA = a.geoA[i], gB = a.geoB[i];
-    const T gm2 = load_gm2(a, i, tp, T(0));
+    if constexpr (!GEO_EARLY) {
+        gA = a.geoA[i];
+        gB = a.geoB[i];
+        gm2 = load_gm2(a, i, tp, T(0));
+    }
     T ui, vi;
     cell_velocity<T>(hi, own.y, own.z, h_dry, ui, vi);
     T f0 = T(0), f1 = T(0), f2 = T(0), sx = T(0), sy = T(0);
@@ -454,7 +469,7 @@ __device__ __forceinline__ T update_cell(const Args& a, long long i, const V4<T>
 // reduction (and its barrier) runs once per block.  With STAGES > 1 each
 // thread keeps its next STAGES-1 cells' state and topology records in flight
 // through cp.async into its own shared-memory slots.
-template <typename T, int BLOCK, int MINB, int STAGES>
+template <typename T, int BLOCK, int MINB, int STAGES, bool GEO_EARLY>
 __global__ void __launch_bounds__(BLOCK, MINB) step_kernel(const StepArgs<T> a) {
     const double dt_d = a.dt_fixed ? *a.dt_fixed : a.cfl * (*a.dt_read);
     const bool have_dt = dt_d < __longlong_as_double((long long)kInfBits);
@@ -475,7 +490,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_kernel(const StepArgs<T> a) 
         for (; i < a.n; i += stride) {
             const V4<T> own = a.s_in[i];
             const int4 tp = a.topo[i];
-            cand = tmin(cand, update_cell<T>(a, i, own, tp, dt, active, a.n_clamped, a.status));
+            cand = tmin(cand, update_cell<T, GEO_EARLY>(a, i, own, tp, dt, active, a.n_clamped, a.status));
         }
     } else {
         __shared__ V4<T> st_own[STAGES][BLOCK];
@@ -503,7 +518,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_kernel(const StepArgs<T> a) 
             cp_async_wait<STAGES - 1>();
             const V4<T> own = st_own[slot][tid];
             const int4 tp = st_topo[slot][tid];
-            cand = tmin(cand, update_cell<T>(a, i, own, tp, dt, active, a.n_clamped, a.status));
+            cand = tmin(cand, update_cell<T, GEO_EARLY>(a, i, own, tp, dt, active, a.n_clamped, a.status));
             slot = slot == STAGES - 1 ? 0 : slot + 1;
         }
         cp_async_wait<0>();
@@ -535,7 +550,7 @@ __device__ __forceinline__ long long ens_tile_of(long long k, long long nchunk_s
     return ((b + (k >> cl2) * nchunk_stride) << cl2) + (k & mask);
 }
 
-template <typename T, int BLOCK, int MINB, int STAGES>
+template <typename T, int BLOCK, int MINB, int STAGES, bool GEO_EARLY>
 __global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel(const EnsArgs<T> a) {
     static_assert(kEnsPad % BLOCK == 0, "a tile must not straddle two members");
     const long long G = gridDim.x, b = blockIdx.x;
@@ -608,7 +623,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel(const EnsArg
             tp = a.topo[i];
         }
         if (have_dt)
-            cand = tmin(cand, update_cell<T>(a, i, own, tp, dt, active, sm + 5, (unsigned*)(sm + 4)));
+            cand = tmin(cand, update_cell<T, GEO_EARLY>(a, i, own, tp, dt, active, sm + 5, (unsigned*)(sm + 4)));
         else
             a.s_out[i] = own;
     }
@@ -682,16 +697,17 @@ __global__ void riemann_batch_kernel(long long n, const T* __restrict__ hL, cons
 template <typename T>
 struct Launch {
     // (block, min_blocks) pairs with a compiled kernel; see step_variants()
-    static cudaError_t step(const StepArgs<T>& a, int block, int min_blocks, int stages, cudaStream_t st);
-    static cudaError_t resident_blocks(int block, int min_blocks, int stages, int* per_sm);
-    // compiled (block, min_blocks, stages) shapes of the step kernel; returns their number
-    static int step_variants(int (*out)[3], int max);
-    // batched ensemble step with one of its compiled (block, min_blocks, stages) shapes
-    static cudaError_t ensemble_step(const EnsArgs<T>& a, int block, int min_blocks, int stages, unsigned grid,
-                                     cudaStream_t st);
-    static cudaError_t ensemble_resident_blocks(int block, int min_blocks, int stages, int* per_sm);
-    static int ensemble_variants(int (*out)[3], int max);
-    static void ensemble_default(int* block, int* min_blocks, int* stages);
+    static cudaError_t step(const StepArgs<T>& a, int block, int min_blocks, int stages, int geo_early,
+                            cudaStream_t st);
+    static cudaError_t resident_blocks(int block, int min_blocks, int stages, int geo_early, int* per_sm);
+    // compiled (block, min_blocks, stages, geo_early) shapes of the step kernel; returns their number
+    static int step_variants(int (*out)[4], int max);
+    // batched ensemble step with one of its compiled (block, min_blocks, stages, geo_early) shapes
+    static cudaError_t ensemble_step(const EnsArgs<T>& a, int block, int min_blocks, int stages, int geo_early,
+                                     unsigned grid, cudaStream_t st);
+    static cudaError_t ensemble_resident_blocks(int block, int min_blocks, int stages, int geo_early, int* per_sm);
+    static int ensemble_variants(int (*out)[4], int max);
+    static void ensemble_default(int* block, int* min_blocks, int* stages, int* geo_early);
     static int default_min_blocks(int block);
     static cudaError_t dt(const V4<T>* s, const V4<T>* geoB, long long n, T g, T h_dry,
                           unsigned long long* dt_write, cudaStream_t st);

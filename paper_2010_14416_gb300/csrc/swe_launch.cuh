@@ -11,15 +11,19 @@ static inline unsigned grid_for(long long n, int block) {
     return (unsigned)((n + block - 1) / block);
 }
 
-// Compiled (block, minimum resident blocks per SM) variants of the step
-// kernel.  FP32 variants trade registers for occupancy; FP64 keeps its
-// registers (its FP64 pipe, not memory latency, is the limit).
-// (block, min blocks per SM, stages); every FP32 variant stays within the
-// 48 KB of static shared memory a block may declare.
-#define SWE_STEP_VARIANTS_F32(X)                                                             \
-    X(128, 1, 1) X(256, 1, 1) X(512, 1, 1) X(128, 8, 1) X(256, 4, 1) X(256, 5, 1) X(512, 2, 1) \
-    X(256, 4, 2) X(256, 4, 3) X(256, 4, 4) X(128, 8, 3) X(128, 8, 4)
-#define SWE_STEP_VARIANTS_F64(X) X(128, 1, 1) X(256, 1, 1) X(512, 1, 1) X(128, 1, 2) X(256, 1, 2)
+// Compiled (block, min blocks per SM, stages, geometry early) variants of
+// the step kernel.  FP32 variants trade registers for occupancy; FP64 keeps
+// its registers (its FP64 pipe, not memory latency, is the limit).  Every
+// FP32 variant stays within the 48 KB of static shared memory a block may
+// declare.  Geometry-early variants suit wet meshes (one memory round trip
+// fewer per active cell), the others mostly dry ones (no geometry traffic for
+// quiet cells); the autotuner chooses.
+#define SWE_STEP_VARIANTS_F32(X)                                                                       \
+    X(128, 1, 1, 0) X(256, 1, 1, 0) X(512, 1, 1, 0) X(128, 8, 1, 0) X(256, 4, 1, 0) X(256, 5, 1, 0)    \
+    X(512, 2, 1, 0) X(256, 4, 2, 0) X(256, 4, 3, 0) X(256, 4, 4, 0) X(128, 8, 3, 0) X(128, 8, 4, 0)    \
+    X(256, 4, 1, 1) X(256, 4, 3, 1) X(128, 8, 1, 1) X(128, 8, 3, 1)
+#define SWE_STEP_VARIANTS_F64(X) \
+    X(128, 1, 1, 0) X(256, 1, 1, 0) X(512, 1, 1, 0) X(128, 1, 2, 0) X(256, 1, 2, 0) X(128, 1, 1, 1) X(256, 1, 1, 1)
 
 template <typename T>
 int Launch<T>::default_min_blocks(int block) {
@@ -28,12 +32,13 @@ int Launch<T>::default_min_blocks(int block) {
 }
 
 template <typename T>
-cudaError_t Launch<T>::step(const StepArgs<T>& a, int block, int min_blocks, int stages, cudaStream_t st) {
+cudaError_t Launch<T>::step(const StepArgs<T>& a, int block, int min_blocks, int stages, int geo_early,
+                            cudaStream_t st) {
     const unsigned grid = a.grid;
     if (grid == 0) return cudaErrorInvalidValue;
-#define SWE_LAUNCH(B, M, S) \
-    if (block == B && min_blocks == M && stages == S) {                          \
-        step_kernel<T, B, M, S><<<grid, B, 0, st>>>(a);                           \
+#define SWE_LAUNCH(B, M, S, G) \
+    if (block == B && min_blocks == M && stages == S && geo_early == G) {        \
+        step_kernel<T, B, M, S, G != 0><<<grid, B, 0, st>>>(a);                  \
         return cudaGetLastError();                                                \
     }
     if constexpr (sizeof(T) == 4) {
@@ -46,10 +51,10 @@ cudaError_t Launch<T>::step(const StepArgs<T>& a, int block, int min_blocks, int
 }
 
 template <typename T>
-cudaError_t Launch<T>::resident_blocks(int block, int min_blocks, int stages, int* per_sm) {
-#define SWE_OCC(B, M, S) \
-    if (block == B && min_blocks == M && stages == S)                             \
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, step_kernel<T, B, M, S>, B, 0);
+cudaError_t Launch<T>::resident_blocks(int block, int min_blocks, int stages, int geo_early, int* per_sm) {
+#define SWE_OCC(B, M, S, G) \
+    if (block == B && min_blocks == M && stages == S && geo_early == G)          \
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, step_kernel<T, B, M, S, G != 0>, B, 0);
     if constexpr (sizeof(T) == 4) {
         SWE_STEP_VARIANTS_F32(SWE_OCC)
     } else {
@@ -60,10 +65,10 @@ cudaError_t Launch<T>::resident_blocks(int block, int min_blocks, int stages, in
 }
 
 template <typename T>
-int Launch<T>::step_variants(int (*out)[3], int max) {
+int Launch<T>::step_variants(int (*out)[4], int max) {
     int k = 0;
-#define SWE_LIST(B, M, S) \
-    if (k < max) { out[k][0] = B; out[k][1] = M; out[k][2] = S; } \
+#define SWE_LIST(B, M, S, G) \
+    if (k < max) { out[k][0] = B; out[k][1] = M; out[k][2] = S; out[k][3] = G; } \
     ++k;
     if constexpr (sizeof(T) == 4) {
         SWE_STEP_VARIANTS_F32(SWE_LIST)
@@ -74,25 +79,30 @@ int Launch<T>::step_variants(int (*out)[3], int max) {
     return k;
 }
 
-// Compiled (block, min blocks per SM, stages) shapes of the ensemble kernel;
-// the first of each list is the default.  Blocks divide the 256-cell padding.
-#define SWE_ENS_VARIANTS_F32(X) X(256, 4, 3) X(256, 4, 1) X(256, 4, 2) X(128, 8, 3) X(128, 8, 1)
-#define SWE_ENS_VARIANTS_F64(X) X(256, 1, 1) X(128, 1, 1) X(256, 1, 2) X(128, 1, 2)
+// Compiled (block, min blocks per SM, stages, geometry early) shapes of the
+// ensemble kernel; the first of each list is the default.  Blocks divide the
+// 256-cell padding.
+#define SWE_ENS_VARIANTS_F32(X)                                                                    \
+    X(256, 4, 3, 0) X(256, 4, 1, 0) X(256, 4, 2, 0) X(128, 8, 3, 0) X(128, 8, 1, 0) X(256, 4, 3, 1) \
+    X(256, 4, 1, 1) X(128, 8, 3, 1) X(128, 8, 1, 1)
+#define SWE_ENS_VARIANTS_F64(X) \
+    X(256, 1, 1, 0) X(128, 1, 1, 0) X(256, 1, 2, 0) X(128, 1, 2, 0) X(256, 1, 1, 1) X(128, 1, 1, 1)
 
 template <typename T>
-void Launch<T>::ensemble_default(int* block, int* min_blocks, int* stages) {
-    int v[1][3];
+void Launch<T>::ensemble_default(int* block, int* min_blocks, int* stages, int* geo_early) {
+    int v[1][4];
     ensemble_variants(v, 1);
     *block = v[0][0];
     *min_blocks = v[0][1];
     *stages = v[0][2];
+    *geo_early = v[0][3];
 }
 
 template <typename T>
-int Launch<T>::ensemble_variants(int (*out)[3], int max) {
+int Launch<T>::ensemble_variants(int (*out)[4], int max) {
     int k = 0;
-#define SWE_LIST(B, M, S) \
-    if (k < max) { out[k][0] = B; out[k][1] = M; out[k][2] = S; } \
+#define SWE_LIST(B, M, S, G) \
+    if (k < max) { out[k][0] = B; out[k][1] = M; out[k][2] = S; out[k][3] = G; } \
     ++k;
     if constexpr (sizeof(T) == 4) {
         SWE_ENS_VARIANTS_F32(SWE_LIST)
@@ -104,12 +114,12 @@ int Launch<T>::ensemble_variants(int (*out)[3], int max) {
 }
 
 template <typename T>
-cudaError_t Launch<T>::ensemble_step(const EnsArgs<T>& a, int block, int min_blocks, int stages, unsigned grid,
-                                     cudaStream_t st) {
+cudaError_t Launch<T>::ensemble_step(const EnsArgs<T>& a, int block, int min_blocks, int stages, int geo_early,
+                                     unsigned grid, cudaStream_t st) {
     if (grid == 0) return cudaErrorInvalidValue;
-#define SWE_LAUNCH(B, M, S) \
-    if (block == B && min_blocks == M && stages == S) {                          \
-        ensemble_step_kernel<T, B, M, S><<<grid, B, 0, st>>>(a);                  \
+#define SWE_LAUNCH(B, M, S, G) \
+    if (block == B && min_blocks == M && stages == S && geo_early == G) {        \
+        ensemble_step_kernel<T, B, M, S, G != 0><<<grid, B, 0, st>>>(a);         \
         return cudaGetLastError();                                                \
     }
     if constexpr (sizeof(T) == 4) {
@@ -122,10 +132,11 @@ cudaError_t Launch<T>::ensemble_step(const EnsArgs<T>& a, int block, int min_blo
 }
 
 template <typename T>
-cudaError_t Launch<T>::ensemble_resident_blocks(int block, int min_blocks, int stages, int* per_sm) {
-#define SWE_OCC(B, M, S) \
-    if (block == B && min_blocks == M && stages == S)                             \
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, ensemble_step_kernel<T, B, M, S>, B, 0);
+cudaError_t Launch<T>::ensemble_resident_blocks(int block, int min_blocks, int stages, int geo_early,
+                                                int* per_sm) {
+#define SWE_OCC(B, M, S, G) \
+    if (block == B && min_blocks == M && stages == S && geo_early == G)          \
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, ensemble_step_kernel<T, B, M, S, G != 0>, B, 0);
     if constexpr (sizeof(T) == 4) {
         SWE_ENS_VARIANTS_F32(SWE_OCC)
     } else {

@@ -2,7 +2,7 @@
 //
 // The paper fixes one thread per cell (Section 5.3.2) and no block size; here
 // the shape of the fused step kernel is a measured choice per mesh: every
-// compiled (block, min_blocks, stages) shape, each with several grid sizes
+// compiled (block, min_blocks, stages, geometry early) shape, each with several grid sizes
 // (one or two resident waves looping over the cells, or 1, 2 or 4 cells per
 // thread), is timed with CUDA events on the mesh's current state.  The trial
 // steps read the current state and write a scratch state buffer and a scratch
@@ -22,7 +22,7 @@ using namespace swe;
 namespace {
 
 struct Shape {
-    int block, min_blocks, stages;
+    int block, min_blocks, stages, geo_early;
     unsigned grid;
 };
 
@@ -49,12 +49,13 @@ int candidate_shapes(const swe_mesh* m, std::vector<Shape>& cand) {
     int sms = 0;
     cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->cfg.device);
     if (e != cudaSuccess) return tfail(e, "swe_autotune: device attribute");
-    cand.push_back({m->cfg.block_size, m->cfg.min_blocks, m->cfg.stages, m->grid});  // the shape in use first
-    int v[64][3];
+    // the shape in use first
+    cand.push_back({m->cfg.block_size, m->cfg.min_blocks, m->cfg.stages, m->cfg.geometry_early, m->grid});
+    int v[64][4];
     const int nv = std::min(Launch<T>::step_variants(v, 64), 64);
     for (int k = 0; k < nv; ++k) {
         int per_sm = 0;
-        e = Launch<T>::resident_blocks(v[k][0], v[k][1], v[k][2], &per_sm);
+        e = Launch<T>::resident_blocks(v[k][0], v[k][1], v[k][2], v[k][3], &per_sm);
         if (e != cudaSuccess) return tfail(e, "swe_autotune: occupancy");
         const long long need = (n + v[k][0] - 1) / v[k][0];
         const long long wave = (long long)std::max(per_sm, 1) * std::max(sms, 1);
@@ -63,8 +64,9 @@ int candidate_shapes(const swe_mesh* m, std::vector<Shape>& cand) {
             const unsigned gr = (unsigned)std::max(1LL, std::min(gsz, need));
             bool seen = false;
             for (const Shape& c : cand)
-                seen = seen || (c.block == v[k][0] && c.min_blocks == v[k][1] && c.stages == v[k][2] && c.grid == gr);
-            if (!seen) cand.push_back({v[k][0], v[k][1], v[k][2], gr});
+                seen = seen || (c.block == v[k][0] && c.min_blocks == v[k][1] && c.stages == v[k][2] &&
+                                c.geo_early == v[k][3] && c.grid == gr);
+            if (!seen) cand.push_back({v[k][0], v[k][1], v[k][2], v[k][3], gr});
         }
     }
     return SWE_OK;
@@ -103,6 +105,7 @@ int autotune_t(swe_mesh* m, int trial_steps, swe_tune* out) {
             m->cfg.block_size = cand[c].block;
             m->cfg.min_blocks = cand[c].min_blocks;
             m->cfg.stages = cand[c].stages;
+            m->cfg.geometry_early = cand[c].geo_early;
             m->grid = cand[c].grid;
             e = launch_step_raw(m, cur, scratch, small, m->nstep, 0.9, nullptr, nullptr, st);  // warm-up
             if (e == cudaSuccess) e = cudaEventRecord(ev[2 * (r * cand.size() + c)], st);
@@ -131,6 +134,7 @@ int autotune_t(swe_mesh* m, int trial_steps, swe_tune* out) {
     m->cfg.block_size = pick.block;
     m->cfg.min_blocks = pick.min_blocks;
     m->cfg.stages = pick.stages;
+    m->cfg.geometry_early = pick.geo_early;
     m->grid = pick.grid;
     drop_mesh_graph(m);
     if (e != cudaSuccess) return tfail(e, "swe_autotune: trial steps");
@@ -138,6 +142,7 @@ int autotune_t(swe_mesh* m, int trial_steps, swe_tune* out) {
         out->block_size = pick.block;
         out->min_blocks = pick.min_blocks;
         out->stages = pick.stages;
+        out->geometry_early = pick.geo_early;
         out->chunk = 0;
         out->grid = pick.grid;
         out->cells_per_thread = (double)n / ((double)pick.grid * pick.block);

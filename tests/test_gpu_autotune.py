@@ -33,9 +33,11 @@ def _same(a, b):
     return all(np.array_equal(x, y) for x, y in zip(a, b))
 
 
-F32_SHAPES = {(128, 1, 1), (256, 1, 1), (512, 1, 1), (128, 8, 1), (256, 4, 1), (256, 5, 1), (512, 2, 1),
-              (256, 4, 2), (256, 4, 3), (256, 4, 4), (128, 8, 3), (128, 8, 4)}
-F64_SHAPES = {(128, 1, 1), (256, 1, 1), (512, 1, 1), (128, 1, 2), (256, 1, 2)}
+F32_SHAPES = {(128, 1, 1, 0), (256, 1, 1, 0), (512, 1, 1, 0), (128, 8, 1, 0), (256, 4, 1, 0), (256, 5, 1, 0),
+              (512, 2, 1, 0), (256, 4, 2, 0), (256, 4, 3, 0), (256, 4, 4, 0), (128, 8, 3, 0), (128, 8, 4, 0),
+              (256, 4, 1, 1), (256, 4, 3, 1), (128, 8, 1, 1), (128, 8, 3, 1)}
+F64_SHAPES = {(128, 1, 1, 0), (256, 1, 1, 0), (512, 1, 1, 0), (128, 1, 2, 0), (256, 1, 2, 0), (128, 1, 1, 1),
+              (256, 1, 1, 1)}
 
 
 @pytest.mark.parametrize("precision,maker", [(capi.SWE_FP64, "dam"), (capi.SWE_FP32, "dam"),
@@ -52,7 +54,7 @@ def test_mesh_autotune_keeps_state_and_results(precision, maker):
     assert info1["t"] == info0["t"] and info1["n_steps"] == info0["n_steps"]
     assert info1["dt_next"] == info0["dt_next"] and info1["n_active"] == info0["n_active"]
     shapes = F32_SHAPES if precision == capi.SWE_FP32 else F64_SHAPES
-    assert (ch["block_size"], ch["min_blocks"], ch["stages"]) in shapes
+    assert (ch["block_size"], ch["min_blocks"], ch["stages"], ch["geometry_early"]) in shapes
     assert ch["n_candidates"] > len(shapes) and ch["chunk"] == 0
     assert 0 < ch["ms_best"] <= ch["ms_before"]
     assert ch["grid"] >= 1
@@ -87,6 +89,7 @@ def test_ensemble_autotune_keeps_state_and_results(precision):
         assert inf["t"] == infos[k]["t"] and inf["dt_next"] == infos[k]["dt_next"]
         assert inf["n_active"] == infos[k]["n_active"]
     assert ch["block_size"] in (128, 256) and ch["chunk"] in (4, 8, 16, 32, 64)
+    assert ch["geometry_early"] in (0, 1)
     assert ch["n_candidates"] >= 20 and 0 < ch["ms_best"] <= ch["ms_before"]
     t_ens = ens.step(90, cfl)
     for k, m in enumerate(meshes):

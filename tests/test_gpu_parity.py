@@ -181,21 +181,25 @@ def test_mass_conserved_and_lake_at_rest_on_gpu():
 
 
 @pytest.mark.parametrize("precision,variants", [
-    (capi.SWE_FP64, [(128, 1, 1), (256, 1, 1), (512, 1, 1), (128, 1, 2), (256, 1, 2)]),
-    (capi.SWE_FP32, [(256, 4, 1), (256, 4, 2), (256, 4, 3), (256, 4, 4), (128, 8, 3), (128, 8, 4),
-                     (512, 2, 1), (256, 5, 1)]),
+    (capi.SWE_FP64, [(128, 1, 1, 0), (256, 1, 1, 0), (512, 1, 1, 0), (128, 1, 2, 0), (256, 1, 2, 0),
+                     (128, 1, 1, 1), (256, 1, 1, 1)]),
+    (capi.SWE_FP32, [(256, 4, 1, 0), (256, 4, 2, 0), (256, 4, 3, 0), (256, 4, 4, 0), (128, 8, 3, 0),
+                     (128, 8, 4, 0), (512, 2, 1, 0), (256, 5, 1, 0), (256, 4, 1, 1), (256, 4, 3, 1),
+                     (128, 8, 1, 1), (128, 8, 3, 1)]),
 ])
 def test_kernel_variants_are_bitwise_identical(precision, variants):
-    # launch shape, register cap and cp.async staging depth change nothing
+    # launch shape, register cap, cp.async staging depth and the placement of
+    # the geometry loads change nothing
     mi = mg.river(100, 20, seed=8)
     ref = None
-    for b, mb, st in variants:
-        got, t, _ = _gpu_run(mi, 301, precision=precision, block_size=b, min_blocks=mb, stages=st)
+    for b, mb, st, ge in variants:
+        got, t, _ = _gpu_run(mi, 301, precision=precision, block_size=b, min_blocks=mb, stages=st,
+                             geometry_early=ge)
         if ref is None:
             ref, tref = got, t
             continue
-        assert t == tref, (b, mb, st)
-        assert all(np.array_equal(x, y) for x, y in zip(ref, got)), (b, mb, st)
+        assert t == tref, (b, mb, st, ge)
+        assert all(np.array_equal(x, y) for x, y in zip(ref, got)), (b, mb, st, ge)
 
 
 def test_graphs_block_sizes_and_device_io_are_bitwise_neutral():
