@@ -319,9 +319,12 @@ def run_gpu(args, name):
     # bytes this layout must move per launch: an active cell reads its state,
     # topology and geometry records and writes its state; a quiet cell (dry,
     # all neighbours dry, no inflow/stage edge) needs no geometry
+    # With activity bytes a quiet cell reads its state record and its own
+    # activity byte and writes its state and one cleared byte: no topology.
     rec = 16 if wl["precision"] == "f32" else 32
-    layout_bytes = n * (active_frac * (4 * rec + 16 + (0 if wl["precision"] == "f32" else 8)) +
-                        (1 - active_frac) * (2 * rec + 16))
+    act_bytes = 2 if shape.get("activity") else 0
+    layout_bytes = n * (active_frac * (4 * rec + 16 + (0 if wl["precision"] == "f32" else 8) + act_bytes) +
+                        (1 - active_frac) * (2 * rec + (act_bytes if act_bytes else 16)))
     layout_achieved = layout_bytes / (kernel_ms * 1e-3) / 1e9
     traffic = None
     tpath = os.path.join(ROOT, "profiles", f"traffic_{name}.json")

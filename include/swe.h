@@ -96,6 +96,15 @@ typedef struct swe_config {
                            after the test that skips dry cells among dry neighbours (no
                            geometry traffic for those).  Compiled with 1: FP32 (256, 4, 1|3),
                            (128, 8, 1|3); FP64 (128|256, 1, 1).  Results do not depend on it */
+    int activity;     /* 1: keep one activity byte per cell (three rotating buffers, 3 bytes per
+                         cell of device memory): a cell is active when it or a neighbour is wet
+                         or it has an inflow/stage edge, and an inactive cell takes its update
+                         (h, 0, 0) without reading its topology or its neighbours; each step
+                         marks the cells that the next one must treat as active.  0 (default):
+                         every cell tests its neighbours.  Compiled with 1: FP32 (128, 8),
+                         (256, 4), (512, 2) with geometry_early 0, (128, 8), (256, 4) with 1;
+                         FP64 (128|256, 1) with 0, (128, 1) with 1 (stages ignored).  Results
+                         do not depend on it */
 } swe_config;
 
 /* Fills *cfg with the defaults listed above. */
@@ -385,6 +394,7 @@ typedef struct swe_tune {
     int min_blocks;          /* chosen resident-block target the kernel is compiled for */
     int stages;              /* chosen cp.async staging depth (1 = direct loads) */
     int geometry_early;      /* chosen geometry load placement (swe_config.geometry_early) */
+    int activity;            /* chosen activity mode (swe_config.activity; 0 for ensembles) */
     int chunk;               /* ensembles: tiles per round-robin chunk; 0 for a mesh */
     int64_t grid;            /* blocks launched per step */
     double cells_per_thread; /* cells each thread updates per step: cells / (grid * block_size) */
@@ -395,8 +405,8 @@ typedef struct swe_tune {
 
 /*
  * Chooses the step kernel's launch shape for this mesh by measurement: every
- * compiled (block_size, min_blocks, stages, geometry_early) shape (see
- * swe_config) with several
+ * compiled (block_size, min_blocks, stages, geometry_early, activity) shape
+ * (see swe_config) with several
  * grid sizes -- one or two resident waves looping over the cells, or 1, 2 or 4
  * cells per thread -- is timed with CUDA events over trial_steps steps
  * (>= 1; 0 = 8), twice, and the fastest is kept for all later steps.  The

@@ -327,6 +327,7 @@ int adjoint_impl(swe_mesh* m, int64_t nsteps, double cfl, const int32_t* gauge_c
         if (e == cudaSuccess)
             e = launch_step_raw(m, cur, nxt, m->small, m->nstep, cfl, nullptr, (double*)dtlog.p + s, st);
         ++m->nstep;
+        m->act_valid = false;   // stepped without the activity bytes
         if (e == cudaSuccess && (s + 1) % obs_every == 0) {
             adj_loss_kernel<<<1, 32, 0, st>>>((const V4<double>*)nxt, gi, tg + ((s + 1) / obs_every - 1) * n_gauges,
                                              n_gauges, (double*)dloss.p);
@@ -454,6 +455,7 @@ int swe_step_dt(swe_mesh* m, int64_t nsteps, const double* dts, double* t_out) {
         e = launch_step_raw(m, m->state[m->nstep % 2], m->state[(m->nstep + 1) % 2], m->small, m->nstep, 1.0,
                             (const double*)d.p + s, (double*)(m->small + kSlotDtLast), st);
         ++m->nstep;
+        m->act_valid = false;   // stepped without the activity bytes
     }
     unsigned long long sm[kSmallWords];
     if (e == cudaSuccess) e = cudaMemcpyAsync(sm, m->small, sizeof sm, cudaMemcpyDeviceToHost, st);

@@ -96,6 +96,16 @@ std::vector<int4> make_topo(const swe_mesh* m) {
             const float gm2 = (float)(m->cfg.g * H.m[c] * H.m[c]);
             std::memcpy(&w, &gm2, sizeof w);
         }
+        // static activity: an inflow or fixed-stage edge keeps the cell out of the quiet path
+        bool fixed = false;
+        for (int j = 0; j < 3; ++j) {
+            const int32_t code = H.code[3 * c + j];
+            if (code < 0) {
+                const int kind = m->bc.kind[-1 - code];
+                fixed = fixed || kind == kBcInflow || kind == kBcStage;
+            }
+        }
+        if (fixed) w |= kStaticBit;
         topo[c] = make_int4(H.code[3 * c], H.code[3 * c + 1], H.code[3 * c + 2], w);
     }
     return topo;
@@ -141,6 +151,7 @@ int flush_topo(swe_mesh* m) {
             m->bc.value[gI] = m->group_value[gI];
     }
     m->topo_dirty = false;
+    m->act_valid = false;   // static activity may have changed
     drop_graph(m);
     return SWE_OK;
 }
@@ -168,6 +179,14 @@ StepArgs<T> make_args(swe_mesh* m, int64_t step_index, double cfl) {
     a.hll = m->cfg.flux == SWE_FLUX_HLL ? 1 : 0;
     a.dt_fixed = nullptr;
     a.dt_log = (double*)(m->small + kSlotDtLast);  // size of the last step, for diagnostics
+    a.act_in = nullptr;
+    a.act_next = nullptr;
+    a.act_clear = nullptr;
+    if (m->cfg.activity && m->act[0]) {
+        a.act_in = m->act[p3];
+        a.act_next = m->act[(p3 + 1) % 3];
+        a.act_clear = m->act[(p3 + 2) % 3];
+    }
     a.g = (T)m->cfg.g;
     a.h_dry = (T)m->cfg.h_dry;
     a.bc = m->bc;
@@ -201,6 +220,14 @@ int capture_graph(swe_mesh* m, int len, double cfl) {
 
 template <typename T>
 int run_steps(swe_mesh* m, int64_t nsteps, double cfl) {
+    if (m->cfg.activity) {
+        if (!m->act_valid) {
+            int rc = init_activity(m);
+            if (rc) return rc;
+        }
+    } else {
+        m->act_valid = false;   // steps without activity bytes do not maintain them
+    }
     int64_t left = nsteps;
     const int gsteps = m->cfg.graph_steps;
     // singles until the step index is a multiple of six
@@ -288,6 +315,7 @@ int set_state_t(swe_mesh* m, const void* h, const void* hu, const void* hv, int 
     if (e != cudaSuccess) return cuda_fail(e, "swe_set_state");
     m->have_state = true;
     m->nstep = 0;
+    m->act_valid = false;
     return SWE_OK;
 }
 
@@ -316,30 +344,12 @@ int get_state_t(swe_mesh* m, void* h, void* hu, void* hv, int where) {
 
 namespace swe {
 
-// One step of mesh m from state buffer `in` to `out`, with the given status
-// block and step index (dt slot rotation), taking dt from *dt_fixed when set.
-cudaError_t launch_step_raw(swe_mesh* m, const void* in, void* out, unsigned long long* small, int64_t step_index,
-                            double cfl, const double* dt_fixed, double* dt_log, cudaStream_t st) {
-    if (m->cfg.precision == SWE_FP32) {
-        StepArgs<float> a = make_args<float>(m, step_index, cfl);
-        a.s_in = (const V4<float>*)in;
-        a.s_out = (V4<float>*)out;
-        const int p3 = (int)(step_index % 3);
-        a.dt_read = (const double*)(small + p3);
-        a.dt_write = small + (p3 + 1) % 3;
-        a.dt_reset = small + (p3 + 2) % 3;
-        a.t = (double*)(small + kSlotT);
-        a.status = (unsigned*)(small + kSlotStatus);
-        a.n_clamped = small + kSlotClamp;
-        a.n_active = small + kSlotActive;
-        a.dt_fixed = dt_fixed;
-        a.dt_log = dt_log;
-        return Launch<float>::step(a, m->cfg.block_size, m->cfg.min_blocks, m->cfg.stages, m->cfg.geometry_early,
-                                   st);
-    }
-    StepArgs<double> a = make_args<double>(m, step_index, cfl);
-    a.s_in = (const V4<double>*)in;
-    a.s_out = (V4<double>*)out;
+template <typename T>
+cudaError_t launch_raw_t(swe_mesh* m, const void* in, void* out, unsigned long long* small, int64_t step_index,
+                         double cfl, const double* dt_fixed, double* dt_log, cudaStream_t st, bool with_activity) {
+    StepArgs<T> a = make_args<T>(m, step_index, cfl);
+    a.s_in = (const V4<T>*)in;
+    a.s_out = (V4<T>*)out;
     const int p3 = (int)(step_index % 3);
     a.dt_read = (const double*)(small + p3);
     a.dt_write = small + (p3 + 1) % 3;
@@ -350,7 +360,56 @@ cudaError_t launch_step_raw(swe_mesh* m, const void* in, void* out, unsigned lon
     a.n_active = small + kSlotActive;
     a.dt_fixed = dt_fixed;
     a.dt_log = dt_log;
-    return Launch<double>::step(a, m->cfg.block_size, m->cfg.min_blocks, m->cfg.stages, m->cfg.geometry_early, st);
+    if (with_activity && a.act_in)
+        return Launch<T>::step(a, m->cfg.block_size, m->cfg.min_blocks, m->cfg.stages, m->cfg.geometry_early, st);
+    a.act_in = nullptr;
+    a.act_next = nullptr;
+    a.act_clear = nullptr;
+    a.grid = m->plain.grid;
+    return Launch<T>::step(a, m->plain.block, m->plain.min_blocks, m->plain.stages, m->plain.geo, st);
+}
+
+// One step of mesh m from buffer `in` to buffer `out` with the given status
+// block and step index (dt slot rotation), taking dt from *dt_fixed when set.
+cudaError_t launch_step_raw(swe_mesh* m, const void* in, void* out, unsigned long long* small, int64_t step_index,
+                            double cfl, const double* dt_fixed, double* dt_log, cudaStream_t st, bool with_activity) {
+    return m->cfg.precision == SWE_FP32
+               ? launch_raw_t<float>(m, in, out, small, step_index, cfl, dt_fixed, dt_log, st, with_activity)
+               : launch_raw_t<double>(m, in, out, small, step_index, cfl, dt_fixed, dt_log, st, with_activity);
+}
+
+int init_activity(swe_mesh* m) {
+    const int64_t n = m->hm.n_cells;
+    cudaError_t e = cudaSuccess;
+    if (!m->act[0]) {
+        const int64_t len = (n + 31) / 32 * 32 + 32;
+        for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+            e = cudaMalloc((void**)&m->act[k], len);
+            if (e == cudaSuccess) e = cudaMemsetAsync(m->act[k], 0, len, m->stream);
+        }
+        if (e != cudaSuccess) {
+            for (auto& p : m->act) {
+                if (p) cudaFree(p);
+                p = nullptr;
+            }
+            set_error("activity bytes: device allocation failed");
+            return SWE_ENOMEM;
+        }
+        m->act_len = len;
+        m->device_bytes += 3 * len;
+    }
+    const int p3 = (int)(m->nstep % 3);
+    e = cudaMemsetAsync(m->act[p3], 0, m->act_len, m->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->act[(p3 + 1) % 3], 0, m->act_len, m->stream);
+    if (e == cudaSuccess)
+        e = m->cfg.precision == SWE_FP32
+                ? Launch<float>::act_init((const V4<float>*)m->state[m->nstep % 2], m->topo, n, (float)m->cfg.h_dry,
+                                          m->act[p3], m->stream)
+                : Launch<double>::act_init((const V4<double>*)m->state[m->nstep % 2], m->topo, n, m->cfg.h_dry,
+                                           m->act[p3], m->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "activity bytes: initialisation");
+    m->act_valid = true;
+    return SWE_OK;
 }
 
 int flush_mesh_bc(swe_mesh* m) { return flush_topo(m); }
@@ -373,6 +432,7 @@ void swe_config_default(swe_config* cfg) {
     cfg->min_blocks = 0;
     cfg->stages = 0;
     cfg->geometry_early = 0;
+    cfg->activity = 0;
     cfg->flux = SWE_FLUX_HLLC;
 }
 
@@ -384,7 +444,7 @@ void swe_mesh_destroy(swe_mesh* m) {
     if (m->stream) cudaStreamSynchronize(m->stream);
     drop_graph(m);
     void* bufs[] = {m->state[0], m->state[1], m->geoA, m->geoB, m->topo, m->gm2, m->zdev, m->perm,
-                    m->stage[0], m->stage[1], m->stage[2], m->small};
+                    m->stage[0], m->stage[1], m->stage[2], m->small, m->act[0], m->act[1], m->act[2]};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
@@ -405,6 +465,10 @@ int swe_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* tris, i
         set_error("swe_mesh_create: geometry_early must be 0 or 1");
         return SWE_EINVAL;
     }
+    if (c.activity != 0 && c.activity != 1) {
+        set_error("swe_mesh_create: activity must be 0 or 1");
+        return SWE_EINVAL;
+    }
     if (c.block_size == 0) c.block_size = c.precision == SWE_FP32 ? 256 : 128;
     if (c.block_size != 128 && c.block_size != 256 && c.block_size != 512) {
         set_error("swe_mesh_create: block_size must be 128, 256 or 512");
@@ -416,6 +480,10 @@ int swe_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* tris, i
     if (c.stages == 0) c.stages = c.precision == SWE_FP32 ? 3 : 1;
     if (c.graph_steps == 0) c.graph_steps = kDefaultGraphSteps;
     if (c.graph_steps > 0) c.graph_steps = std::max(6, (c.graph_steps / 6) * 6);
+    if (c.activity && n_tris >= kActivityMaxCells) {
+        set_error("swe_mesh_create: activity needs fewer than 2^29 cells");
+        return SWE_EINVAL;
+    }
     swe_mesh* m = new (std::nothrow) swe_mesh();
     if (!m) { set_error("swe_mesh_create: out of host memory"); return SWE_ENOMEM; }
     m->cfg = c;
@@ -450,12 +518,14 @@ int swe_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* tris, i
     {
         int per_sm = 0, sms = 0;
         e = c.precision == SWE_FP32
-                ? Launch<float>::resident_blocks(c.block_size, c.min_blocks, c.stages, c.geometry_early, &per_sm)
-                : Launch<double>::resident_blocks(c.block_size, c.min_blocks, c.stages, c.geometry_early, &per_sm);
+                ? Launch<float>::resident_blocks(c.block_size, c.min_blocks, c.stages, c.geometry_early, c.activity,
+                                                 &per_sm)
+                : Launch<double>::resident_blocks(c.block_size, c.min_blocks, c.stages, c.geometry_early, c.activity,
+                                                  &per_sm);
         if (e == cudaErrorInvalidValue) {
             swe_mesh_destroy(m);
             set_error("swe_mesh_create: no compiled step kernel for this block_size / min_blocks / stages / "
-                      "geometry_early");
+                      "geometry_early / activity");
             return SWE_EINVAL;
         }
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device);
@@ -463,6 +533,23 @@ int swe_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* tris, i
         const long long need = (n + c.block_size - 1) / c.block_size;
         const long long wave = (long long)std::max(per_sm, 1) * std::max(sms, 1);
         m->grid = (unsigned)std::min(need, wave);
+        // launches without activity bytes: the same shape, or the default one
+        // when the configured shape exists only as an activity kernel
+        m->plain = LaunchShape{c.block_size, c.min_blocks, c.stages, c.geometry_early, m->grid};
+        if (c.activity) {
+            LaunchShape d;
+            d.block = c.precision == SWE_FP32 ? 256 : 128;
+            d.min_blocks = c.precision == SWE_FP32 ? Launch<float>::default_min_blocks(d.block)
+                                                   : Launch<double>::default_min_blocks(d.block);
+            d.stages = c.precision == SWE_FP32 ? 3 : 1;
+            d.geo = 0;
+            int pb = 0;
+            e = c.precision == SWE_FP32 ? Launch<float>::resident_blocks(d.block, d.min_blocks, d.stages, 0, 0, &pb)
+                                        : Launch<double>::resident_blocks(d.block, d.min_blocks, d.stages, 0, 0, &pb);
+            if (e != cudaSuccess) { swe_mesh_destroy(m); return cuda_fail(e, "swe_mesh_create: occupancy"); }
+            d.grid = (unsigned)std::min((long long)((n + d.block - 1) / d.block), (long long)std::max(pb, 1) * std::max(sms, 1));
+            m->plain = d;
+        }
     }
     m->bc.kind[0] = kBcWall;
     m->bc.value[0] = 0.0;

@@ -42,6 +42,12 @@ std::vector<int64_t> order_rcm(int64_t n, const std::vector<int64_t>& nbr /* [n]
 // Thread-local error message of the C ABI.
 void set_error(const std::string& msg);
 
+// A launch shape of the step kernel.
+struct LaunchShape {
+    int block = 0, min_blocks = 0, stages = 0, geo = 0;
+    unsigned grid = 0;
+};
+
 // Words of a mesh's device status block.
 constexpr int kSmallWords = 8;
 constexpr int kSlotT = 3, kSlotStatus = 4, kSlotClamp = 5, kSlotActive = 6, kSlotDtLast = 7;
@@ -51,9 +57,16 @@ constexpr int kSlotT = 3, kSlotStatus = 4, kSlotClamp = 5, kSlotActive = 6, kSlo
 struct swe_mesh;
 
 namespace swe {
-// One step of mesh m from state buffer `in` to `out` (see swe_capi.cu).
+// One step of mesh m from state buffer `in` to `out` (see swe_capi.cu).  With
+// with_activity (and the mesh's activity mode on) the step reads and maintains
+// the mesh's activity bytes: only for `in` = the mesh's current state.
 cudaError_t launch_step_raw(swe_mesh* m, const void* in, void* out, unsigned long long* small, int64_t step_index,
-                            double cfl, const double* dt_fixed, double* dt_log, cudaStream_t st);
+                            double cfl, const double* dt_fixed, double* dt_log, cudaStream_t st,
+                            bool with_activity = false);
+// Allocates (once) and fills the activity bytes of m's current state.
+int init_activity(swe_mesh* m);
+// The activity kernel indexes cells with 32 bits: meshes below this size.
+constexpr int64_t kActivityMaxCells = int64_t(1) << 29;
 // Applies pending boundary-group changes of m to the device.
 int flush_mesh_bc(swe_mesh* m);
 // Drops m's captured CUDA graph (after a change of launch shape).
@@ -88,6 +101,15 @@ struct swe_mesh {
     double graph_cfl = -1.0;
     int64_t device_bytes = 0;
     unsigned grid = 0;                 // blocks of the step kernel (about one resident wave)
+    // activity bytes (cfg.activity): three rotating buffers of act_len bytes;
+    // act_valid says that the one step nstep reads describes the current state
+    unsigned char* act[3] = {nullptr, nullptr, nullptr};
+    int64_t act_len = 0;
+    bool act_valid = false;
+    // shape of the steps that run without activity bytes (launch_step_raw for
+    // other buffers: adjoint, frozen time steps); equals the cfg shape when
+    // activity is off
+    swe::LaunchShape plain;
 };
 
 

@@ -23,6 +23,7 @@ namespace swe {
 constexpr int kMaxGroups = 64;
 constexpr int kNbrMask = 0x3FFFFFFF;   // neighbour index bits
 constexpr int kFlipBit = 0x40000000;   // set when this cell is the right side of the edge
+constexpr int kStaticBit = (int)0x80000000;  // in topo.w: the cell has an inflow or fixed-stage edge
 constexpr unsigned long long kInfBits = 0x7FF0000000000000ULL;  // +inf as double bits
 
 // status word bits
@@ -66,6 +67,11 @@ struct StepArgs {
     int hll;                           // 1: HLL flux for all components, 0: HLLC
     const double* dt_fixed;            // if set: the step size to take (frozen time steps)
     double* dt_log;                    // if set: receives the step size taken
+    // activity bytes (step_kernel_act only): read, marked for the next step,
+    // cleared for the step after next
+    const unsigned char* act_in;
+    unsigned char* act_next;
+    unsigned char* act_clear;
     T g, h_dry;
     BcTable bc;
     __device__ __forceinline__ int bc_kind(int grp) const { return bc.kind[grp]; }
@@ -216,9 +222,10 @@ __device__ __forceinline__ void block_min_publish(double cand, unsigned long lon
 }
 
 // ---- Manning factor g m^2: packed in topo.w (FP32) or its own array (FP64) --------
+// (the sign bit of topo.w is the static-activity flag; g m^2 >= 0 leaves it free)
 template <typename Args>
 __device__ __forceinline__ float load_gm2(const Args&, long long, const int4& tp, float) {
-    return __int_as_float(tp.w);
+    return __int_as_float(tp.w & 0x7FFFFFFF);
 }
 template <typename Args>
 __device__ __forceinline__ double load_gm2(const Args& a, long long i, const int4&, double) {
@@ -526,6 +533,144 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_kernel(const StepArgs<T> a) 
     block_min_publish<BLOCK>((double)cand, a.dt_write, active, a.n_active);
 }
 
+// ---- the fused step with activity bytes ------------------------------------------
+// One byte per cell in three rotating buffers.  In the buffer a step reads, a
+// cell's byte is non-zero exactly when the cell is not quiet: it is wet, or a
+// neighbour is wet, or it has an inflow or fixed-stage edge.  The step marks
+// in the next buffer (plain stores of 1, so concurrent marks of one byte
+// agree) every cell that is wet after its update together with its
+// neighbours, and every cell with an inflow/stage edge; and it clears each
+// cell's byte in the third buffer, which the step after next fills.  A cell
+// whose byte is 0 takes the quiet update (h, 0, 0) without its topology
+// record or its neighbours' states -- the same result the neighbour test of
+// update_cell gives, bit for bit.
+//
+// Per-thread cp.async pipeline over the thread's cells c_k = i0 + k stride:
+// iteration k issues the topology of c_{k+1} (only if its byte is set), then
+// the activity bytes of c_{k+3} (8 lanes copy the warp's 32 bytes) and the
+// state record of c_{k+2}; it then processes c_k.
+template <typename T, int BLOCK, int MINB, bool GEO_EARLY>
+__global__ void __launch_bounds__(BLOCK, MINB) step_kernel_act(const StepArgs<T> a) {
+    static_assert(BLOCK % 32 == 0, "warps of whole cells");
+    const double dt_d = a.dt_fixed ? *a.dt_fixed : a.cfl * (*a.dt_read);
+    const bool have_dt = dt_d < __longlong_as_double((long long)kInfBits);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *a.dt_reset = kInfBits;
+        if (have_dt) *a.t += dt_d;
+        else atomicOr(a.status, kStatusDry);
+        if (a.dt_log) *a.dt_log = dt_d;
+    }
+    T cand = inf_of<T>();
+    unsigned active = 0u;
+    // 32-bit cell indices: the host allows this kernel only for n < 2^29, so
+    // c + 3 stride < 2^32 with stride <= n + BLOCK
+    const unsigned stride = gridDim.x * BLOCK;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned i0 = blockIdx.x * BLOCK + tid;
+    const unsigned n = (unsigned)a.n;
+    if (!have_dt) {
+        // no step: the state and its activity carry over unchanged
+        for (unsigned c = i0; c < n; c += stride) {
+            a.s_out[c] = a.s_in[c];
+            a.act_next[c] = a.act_in[c];
+            a.act_clear[c] = 0;
+        }
+    } else {
+        __shared__ V4<T> st_own[3][BLOCK];
+        __shared__ int4 st_topo[2][BLOCK];
+        __shared__ unsigned st_act[3][BLOCK / 4];  // 32 activity bytes per warp per stage
+        const T dt = T(dt_d);
+        // warp w of the block owns st_act[.][8 w .. 8 w + 7]; lanes 0..7 copy 4 bytes each
+        auto act_copy = [&](int slot, unsigned c) {
+            const unsigned base = c - lane;
+            if (lane < 8 && base < n)
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(
+                                 (unsigned)__cvta_generic_to_shared(&st_act[slot][warp * 8 + lane])),
+                             "l"(a.act_in + base + 4 * lane)
+                             : "memory");
+        };
+        auto act_byte = [&](int slot) -> unsigned {
+            return ((const unsigned char*)&st_act[slot][warp * 8])[lane];
+        };
+        // prologue: activity of c_0, c_1, c_2 and states of c_0, c_1; then topology of c_0
+        act_copy(0, i0);
+        act_copy(1, i0 + stride);
+        act_copy(2, i0 + 2 * stride);
+        if (i0 < n) cp_async_record<sizeof(V4<T>)>(&st_own[0][tid], &a.s_in[i0]);
+        if (i0 + stride < n) cp_async_record<sizeof(V4<T>)>(&st_own[1][tid], &a.s_in[i0 + stride]);
+        cp_async_commit();
+        cp_async_wait<0>();
+        __syncwarp();
+        unsigned f_cur = act_byte(0);
+        if (f_cur && i0 < n) cp_async_record<16>(&st_topo[0][tid], &a.topo[i0]);
+        cp_async_commit();                                       // T_{-1}
+        cp_async_commit();                                       // H_{-1} (empty: its copies were in the first group)
+        int k3 = 0, k2 = 0;  // k mod 3, k mod 2
+        for (unsigned c = i0; c - lane < n; c += stride) {
+            const int k3n = k3 == 2 ? 0 : k3 + 1, k3nn = k3n == 2 ? 0 : k3n + 1;
+            // groups so far: ..., T_{k-1}, H_{k-1}; H_{k-2} (activity of c_{k+1}, state of c_k) must be complete
+            cp_async_wait<2>();
+            __syncwarp();
+            const unsigned f_next = act_byte(k3n);
+            const unsigned c1 = c + stride, c2 = c + 2 * stride, c3 = c + 3 * stride;
+            if (f_next && c1 < n) cp_async_record<16>(&st_topo[k2 ^ 1][tid], &a.topo[c1]);
+            cp_async_commit();                                   // T_k
+            __syncwarp();                                        // every lane has read slot k3 before it refills
+            act_copy(k3, c3);
+            if (c2 < n) cp_async_record<sizeof(V4<T>)>(&st_own[k3nn][tid], &a.s_in[c2]);
+            cp_async_commit();                                   // H_k
+            cp_async_wait<3>();                                  // T_{k-1}: the topology of c_k
+            if (c < n) {
+                const V4<T> own = st_own[k3][tid];
+                if (!f_cur) {
+                    V4<T> out;
+                    out.x = own.x; out.y = T(0); out.z = T(0); out.w = own.w;
+                    a.s_out[c] = out;
+                } else {
+                    const T r = update_cell<T, GEO_EARLY>(a, c, own, st_topo[k2][tid], dt, active, a.n_clamped,
+                                                          a.status);
+                    cand = tmin(cand, r);
+                    const bool wet = r < inf_of<T>();
+                    // the topology record is read again from shared memory rather than kept
+                    // live in registers across the update
+                    const volatile int* tv = (const volatile int*)&st_topo[k2][tid];
+                    if (wet || (tv[3] & kStaticBit)) a.act_next[c] = 1;
+                    if (wet) {
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) {
+                            const int code = tv[j];
+                            if (code >= 0) a.act_next[code & kNbrMask] = 1;
+                        }
+                    }
+                }
+                a.act_clear[c] = 0;
+            }
+            f_cur = f_next;
+            k3 = k3n;
+            k2 ^= 1;
+        }
+        cp_async_wait<0>();
+    }
+    block_min_publish<BLOCK>((double)cand, a.dt_write, active, a.n_active);
+}
+
+// Activity bytes of a state (into a zeroed buffer): a wet cell marks itself and
+// its neighbours, a cell with an inflow/stage edge marks itself.
+template <typename T>
+__global__ void act_init_kernel(const V4<T>* __restrict__ s, const int4* __restrict__ topo, long long n, T h_dry,
+                                unsigned char* __restrict__ act) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    const bool wet = s[c].x > h_dry;
+    const int4 tp = topo[c];
+    if (wet || (tp.w & kStaticBit)) act[c] = 1;
+    if (wet) {
+        if (tp.x >= 0) act[tp.x & kNbrMask] = 1;
+        if (tp.y >= 0) act[tp.y & kNbrMask] = 1;
+        if (tp.z >= 0) act[tp.z & kNbrMask] = 1;
+    }
+}
+
 // ---- batched ensemble step -------------------------------------------------------
 // Members advance together, each with its own CFL step: one launch covers every
 // member's cells.  When a block moves on to another member, its warps publish
@@ -697,9 +842,15 @@ __global__ void riemann_batch_kernel(long long n, const T* __restrict__ hL, cons
 template <typename T>
 struct Launch {
     // (block, min_blocks) pairs with a compiled kernel; see step_variants()
+    // with a.act_in set, the activity kernel (stages ignored) runs
     static cudaError_t step(const StepArgs<T>& a, int block, int min_blocks, int stages, int geo_early,
                             cudaStream_t st);
-    static cudaError_t resident_blocks(int block, int min_blocks, int stages, int geo_early, int* per_sm);
+    static cudaError_t resident_blocks(int block, int min_blocks, int stages, int geo_early, int activity,
+                                       int* per_sm);
+    // compiled (block, min_blocks, geo_early) shapes of the activity kernel
+    static int act_variants(int (*out)[3], int max);
+    static cudaError_t act_init(const V4<T>* s, const int4* topo, long long n, T h_dry, unsigned char* act,
+                                cudaStream_t st);
     // compiled (block, min_blocks, stages, geo_early) shapes of the step kernel; returns their number
     static int step_variants(int (*out)[4], int max);
     // batched ensemble step with one of its compiled (block, min_blocks, stages, geo_early) shapes

@@ -25,6 +25,12 @@ static inline unsigned grid_for(long long n, int block) {
 #define SWE_STEP_VARIANTS_F64(X) \
     X(128, 1, 1, 0) X(256, 1, 1, 0) X(512, 1, 1, 0) X(128, 1, 2, 0) X(256, 1, 2, 0) X(128, 1, 1, 1) X(256, 1, 1, 1)
 
+// (block, min blocks per SM, geometry early) shapes of the activity kernel
+// (its pipeline depth is fixed); shared memory: 3 state + 2 topology records
+// and 3 activity bytes per thread.
+#define SWE_ACT_VARIANTS_F32(X) X(128, 8, 0) X(256, 4, 0) X(512, 2, 0) X(128, 8, 1) X(256, 4, 1)
+#define SWE_ACT_VARIANTS_F64(X) X(128, 1, 0) X(256, 1, 0) X(128, 1, 1)
+
 template <typename T>
 int Launch<T>::default_min_blocks(int block) {
     if (sizeof(T) == 8) return 1;
@@ -36,6 +42,20 @@ cudaError_t Launch<T>::step(const StepArgs<T>& a, int block, int min_blocks, int
                             cudaStream_t st) {
     const unsigned grid = a.grid;
     if (grid == 0) return cudaErrorInvalidValue;
+    if (a.act_in) {
+#define SWE_LAUNCH_ACT(B, M, G) \
+    if (block == B && min_blocks == M && geo_early == G) {                        \
+        step_kernel_act<T, B, M, G != 0><<<grid, B, 0, st>>>(a);                 \
+        return cudaGetLastError();                                                \
+    }
+        if constexpr (sizeof(T) == 4) {
+            SWE_ACT_VARIANTS_F32(SWE_LAUNCH_ACT)
+        } else {
+            SWE_ACT_VARIANTS_F64(SWE_LAUNCH_ACT)
+        }
+#undef SWE_LAUNCH_ACT
+        return cudaErrorInvalidValue;
+    }
 #define SWE_LAUNCH(B, M, S, G) \
     if (block == B && min_blocks == M && stages == S && geo_early == G) {        \
         step_kernel<T, B, M, S, G != 0><<<grid, B, 0, st>>>(a);                  \
@@ -51,7 +71,20 @@ cudaError_t Launch<T>::step(const StepArgs<T>& a, int block, int min_blocks, int
 }
 
 template <typename T>
-cudaError_t Launch<T>::resident_blocks(int block, int min_blocks, int stages, int geo_early, int* per_sm) {
+cudaError_t Launch<T>::resident_blocks(int block, int min_blocks, int stages, int geo_early, int activity,
+                                       int* per_sm) {
+    if (activity) {
+#define SWE_OCC_ACT(B, M, G) \
+    if (block == B && min_blocks == M && geo_early == G)                          \
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, step_kernel_act<T, B, M, G != 0>, B, 0);
+        if constexpr (sizeof(T) == 4) {
+            SWE_ACT_VARIANTS_F32(SWE_OCC_ACT)
+        } else {
+            SWE_ACT_VARIANTS_F64(SWE_OCC_ACT)
+        }
+#undef SWE_OCC_ACT
+        return cudaErrorInvalidValue;
+    }
 #define SWE_OCC(B, M, S, G) \
     if (block == B && min_blocks == M && stages == S && geo_early == G)          \
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, step_kernel<T, B, M, S, G != 0>, B, 0);
@@ -77,6 +110,28 @@ int Launch<T>::step_variants(int (*out)[4], int max) {
     }
 #undef SWE_LIST
     return k;
+}
+
+template <typename T>
+int Launch<T>::act_variants(int (*out)[3], int max) {
+    int k = 0;
+#define SWE_LIST(B, M, G) \
+    if (k < max) { out[k][0] = B; out[k][1] = M; out[k][2] = G; } \
+    ++k;
+    if constexpr (sizeof(T) == 4) {
+        SWE_ACT_VARIANTS_F32(SWE_LIST)
+    } else {
+        SWE_ACT_VARIANTS_F64(SWE_LIST)
+    }
+#undef SWE_LIST
+    return k;
+}
+
+template <typename T>
+cudaError_t Launch<T>::act_init(const V4<T>* s, const int4* topo, long long n, T h_dry, unsigned char* act,
+                                cudaStream_t st) {
+    act_init_kernel<T><<<grid_for<T>(n, 256), 256, 0, st>>>(s, topo, n, h_dry, act);
+    return cudaGetLastError();
 }
 
 // Compiled (block, min blocks per SM, stages, geometry early) shapes of the

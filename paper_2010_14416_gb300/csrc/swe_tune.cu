@@ -2,13 +2,16 @@
 //
 // The paper fixes one thread per cell (Section 5.3.2) and no block size; here
 // the shape of the fused step kernel is a measured choice per mesh: every
-// compiled (block, min_blocks, stages, geometry early) shape, each with several grid sizes
-// (one or two resident waves looping over the cells, or 1, 2 or 4 cells per
-// thread), is timed with CUDA events on the mesh's current state.  The trial
-// steps read the current state and write a scratch state buffer and a scratch
-// copy of the status block, so nothing the mesh holds changes.  Every shape
-// evaluates the same arithmetic on every cell, so the choice changes speed
-// only, never results (the GPU tests check this bit for bit).
+// compiled (block, min_blocks, stages, geometry early) shape of the step
+// kernel and every (block, min_blocks, geometry early) shape of the activity
+// kernel, each with several grid sizes (one or two resident waves looping
+// over the cells, or 1, 2 or 4 cells per thread), is timed with CUDA events
+// on the mesh's current state.  The trial steps read the current state and
+// write a scratch state buffer and a scratch copy of the status block; trials
+// of the activity kernel also write the mesh's next activity buffers, with
+// exactly the bytes the next real step writes there.  Every shape evaluates
+// the same arithmetic on every cell, so the choice changes speed only, never
+// results (the GPU tests check this bit for bit).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -22,9 +25,14 @@ using namespace swe;
 namespace {
 
 struct Shape {
-    int block, min_blocks, stages, geo_early;
+    int block, min_blocks, stages, geo_early, activity;
     unsigned grid;
 };
+
+bool same_shape(const Shape& a, const Shape& b) {
+    return a.block == b.block && a.min_blocks == b.min_blocks && a.stages == b.stages && a.geo_early == b.geo_early &&
+           a.activity == b.activity && a.grid == b.grid;
+}
 
 int tfail(cudaError_t e, const char* what) {
     set_error(std::string(what) + ": " + cudaGetErrorString(e));
@@ -50,26 +58,46 @@ int candidate_shapes(const swe_mesh* m, std::vector<Shape>& cand) {
     cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->cfg.device);
     if (e != cudaSuccess) return tfail(e, "swe_autotune: device attribute");
     // the shape in use first
-    cand.push_back({m->cfg.block_size, m->cfg.min_blocks, m->cfg.stages, m->cfg.geometry_early, m->grid});
-    int v[64][4];
-    const int nv = std::min(Launch<T>::step_variants(v, 64), 64);
-    for (int k = 0; k < nv; ++k) {
+    cand.push_back({m->cfg.block_size, m->cfg.min_blocks, m->cfg.stages, m->cfg.geometry_early, m->cfg.activity,
+                    m->grid});
+    auto add = [&](int block, int minb, int stages, int geo, int act) -> int {
         int per_sm = 0;
-        e = Launch<T>::resident_blocks(v[k][0], v[k][1], v[k][2], v[k][3], &per_sm);
-        if (e != cudaSuccess) return tfail(e, "swe_autotune: occupancy");
-        const long long need = (n + v[k][0] - 1) / v[k][0];
+        cudaError_t er = Launch<T>::resident_blocks(block, minb, stages, geo, act, &per_sm);
+        if (er != cudaSuccess) return tfail(er, "swe_autotune: occupancy");
+        const long long need = (n + block - 1) / block;
         const long long wave = (long long)std::max(per_sm, 1) * std::max(sms, 1);
         const long long grids[] = {wave, 2 * wave, need, (need + 1) / 2, (need + 3) / 4};
         for (long long gsz : grids) {
-            const unsigned gr = (unsigned)std::max(1LL, std::min(gsz, need));
+            const Shape sh{block, minb, stages, geo, act, (unsigned)std::max(1LL, std::min(gsz, need))};
             bool seen = false;
-            for (const Shape& c : cand)
-                seen = seen || (c.block == v[k][0] && c.min_blocks == v[k][1] && c.stages == v[k][2] &&
-                                c.geo_early == v[k][3] && c.grid == gr);
-            if (!seen) cand.push_back({v[k][0], v[k][1], v[k][2], v[k][3], gr});
+            for (const Shape& c : cand) seen = seen || same_shape(c, sh);
+            if (!seen) cand.push_back(sh);
         }
+        return SWE_OK;
+    };
+    int v[64][4];
+    const int nv = std::min(Launch<T>::step_variants(v, 64), 64);
+    for (int k = 0; k < nv; ++k) {
+        const int rc = add(v[k][0], v[k][1], v[k][2], v[k][3], 0);
+        if (rc) return rc;
+    }
+    int w[64][3];
+    const int nw = n < kActivityMaxCells ? std::min(Launch<T>::act_variants(w, 64), 64) : 0;
+    for (int k = 0; k < nw; ++k) {
+        const int rc = add(w[k][0], w[k][1], 3, w[k][2], 1);
+        if (rc) return rc;
     }
     return SWE_OK;
+}
+
+void apply_shape(swe_mesh* m, const Shape& sh) {
+    m->cfg.block_size = sh.block;
+    m->cfg.min_blocks = sh.min_blocks;
+    m->cfg.stages = sh.stages;
+    m->cfg.geometry_early = sh.geo_early;
+    m->cfg.activity = sh.activity;
+    m->grid = sh.grid;
+    if (!sh.activity) m->plain = LaunchShape{sh.block, sh.min_blocks, sh.stages, sh.geo_early, sh.grid};
 }
 
 template <typename T>
@@ -79,7 +107,13 @@ int autotune_t(swe_mesh* m, int trial_steps, swe_tune* out) {
     int rc = candidate_shapes<T>(m, cand);
     if (rc) return rc;
     const Shape before = cand[0];
+    const LaunchShape plain_before = m->plain;
     cudaStream_t st = m->stream;
+    // activity bytes of the current state for the activity-kernel trials
+    if (n < kActivityMaxCells) {
+        rc = init_activity(m);
+        if (rc) return rc;
+    }
     void* scratch = nullptr;
     unsigned long long* small = nullptr;
     cudaError_t e = cudaMalloc(&scratch, (size_t)n * sizeof(V4<T>));
@@ -102,15 +136,11 @@ int autotune_t(swe_mesh* m, int trial_steps, swe_tune* out) {
     const void* cur = m->state[m->nstep % 2];
     for (int r = 0; r < rounds && e == cudaSuccess; ++r) {
         for (size_t c = 0; c < cand.size() && e == cudaSuccess; ++c) {
-            m->cfg.block_size = cand[c].block;
-            m->cfg.min_blocks = cand[c].min_blocks;
-            m->cfg.stages = cand[c].stages;
-            m->cfg.geometry_early = cand[c].geo_early;
-            m->grid = cand[c].grid;
-            e = launch_step_raw(m, cur, scratch, small, m->nstep, 0.9, nullptr, nullptr, st);  // warm-up
+            apply_shape(m, cand[c]);
+            e = launch_step_raw(m, cur, scratch, small, m->nstep, 0.9, nullptr, nullptr, st, true);  // warm-up
             if (e == cudaSuccess) e = cudaEventRecord(ev[2 * (r * cand.size() + c)], st);
             for (int s = 0; s < trial_steps && e == cudaSuccess; ++s)
-                e = launch_step_raw(m, cur, scratch, small, m->nstep, 0.9, nullptr, nullptr, st);
+                e = launch_step_raw(m, cur, scratch, small, m->nstep, 0.9, nullptr, nullptr, st, true);
             if (e == cudaSuccess) e = cudaEventRecord(ev[2 * (r * cand.size() + c) + 1], st);
         }
     }
@@ -126,16 +156,20 @@ int autotune_t(swe_mesh* m, int trial_steps, swe_tune* out) {
         if (x) cudaEventDestroy(x);
     cudaFree(scratch);
     cudaFree(small);
-    size_t best = 0;
+    size_t best = 0, best_plain = cand.size();
     if (e == cudaSuccess)
-        for (size_t c = 1; c < cand.size(); ++c)
+        for (size_t c = 0; c < cand.size(); ++c) {
             if (ms[c] < ms[best]) best = c;
+            if (!cand[c].activity && (best_plain == cand.size() || ms[c] < ms[best_plain])) best_plain = c;
+        }
     const Shape pick = e == cudaSuccess ? cand[best] : before;
-    m->cfg.block_size = pick.block;
-    m->cfg.min_blocks = pick.min_blocks;
-    m->cfg.stages = pick.stages;
-    m->cfg.geometry_early = pick.geo_early;
-    m->grid = pick.grid;
+    // launches without activity bytes take the fastest shape of the plain kernel
+    if (e == cudaSuccess && best_plain < cand.size()) apply_shape(m, cand[best_plain]);
+    else m->plain = plain_before;
+    apply_shape(m, pick);
+    // the activity bytes describe the current state (the trials rewrote the next
+    // buffers with the bytes the next step writes); without activity they go stale
+    m->act_valid = pick.activity != 0 && e == cudaSuccess;
     drop_mesh_graph(m);
     if (e != cudaSuccess) return tfail(e, "swe_autotune: trial steps");
     if (out) {
@@ -143,6 +177,7 @@ int autotune_t(swe_mesh* m, int trial_steps, swe_tune* out) {
         out->min_blocks = pick.min_blocks;
         out->stages = pick.stages;
         out->geometry_early = pick.geo_early;
+        out->activity = pick.activity;
         out->chunk = 0;
         out->grid = pick.grid;
         out->cells_per_thread = (double)n / ((double)pick.grid * pick.block);

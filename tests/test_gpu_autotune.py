@@ -33,11 +33,15 @@ def _same(a, b):
     return all(np.array_equal(x, y) for x, y in zip(a, b))
 
 
-F32_SHAPES = {(128, 1, 1, 0), (256, 1, 1, 0), (512, 1, 1, 0), (128, 8, 1, 0), (256, 4, 1, 0), (256, 5, 1, 0),
-              (512, 2, 1, 0), (256, 4, 2, 0), (256, 4, 3, 0), (256, 4, 4, 0), (128, 8, 3, 0), (128, 8, 4, 0),
-              (256, 4, 1, 1), (256, 4, 3, 1), (128, 8, 1, 1), (128, 8, 3, 1)}
-F64_SHAPES = {(128, 1, 1, 0), (256, 1, 1, 0), (512, 1, 1, 0), (128, 1, 2, 0), (256, 1, 2, 0), (128, 1, 1, 1),
-              (256, 1, 1, 1)}
+# (block, min_blocks, stages, geometry_early, activity)
+F32_SHAPES = {s + (0,) for s in [
+    (128, 1, 1, 0), (256, 1, 1, 0), (512, 1, 1, 0), (128, 8, 1, 0), (256, 4, 1, 0), (256, 5, 1, 0), (512, 2, 1, 0),
+    (256, 4, 2, 0), (256, 4, 3, 0), (256, 4, 4, 0), (128, 8, 3, 0), (128, 8, 4, 0), (256, 4, 1, 1), (256, 4, 3, 1),
+    (128, 8, 1, 1), (128, 8, 3, 1)]} | {
+    (128, 8, 3, 0, 1), (256, 4, 3, 0, 1), (512, 2, 3, 0, 1), (128, 8, 3, 1, 1), (256, 4, 3, 1, 1)}
+F64_SHAPES = {s + (0,) for s in [
+    (128, 1, 1, 0), (256, 1, 1, 0), (512, 1, 1, 0), (128, 1, 2, 0), (256, 1, 2, 0), (128, 1, 1, 1), (256, 1, 1, 1)]} | {
+    (128, 1, 3, 0, 1), (256, 1, 3, 0, 1), (128, 1, 3, 1, 1)}
 
 
 @pytest.mark.parametrize("precision,maker", [(capi.SWE_FP64, "dam"), (capi.SWE_FP32, "dam"),
@@ -54,7 +58,7 @@ def test_mesh_autotune_keeps_state_and_results(precision, maker):
     assert info1["t"] == info0["t"] and info1["n_steps"] == info0["n_steps"]
     assert info1["dt_next"] == info0["dt_next"] and info1["n_active"] == info0["n_active"]
     shapes = F32_SHAPES if precision == capi.SWE_FP32 else F64_SHAPES
-    assert (ch["block_size"], ch["min_blocks"], ch["stages"], ch["geometry_early"]) in shapes
+    assert (ch["block_size"], ch["min_blocks"], ch["stages"], ch["geometry_early"], ch["activity"]) in shapes
     assert ch["n_candidates"] > len(shapes) and ch["chunk"] == 0
     assert 0 < ch["ms_best"] <= ch["ms_before"]
     assert ch["grid"] >= 1
@@ -89,7 +93,7 @@ def test_ensemble_autotune_keeps_state_and_results(precision):
         assert inf["t"] == infos[k]["t"] and inf["dt_next"] == infos[k]["dt_next"]
         assert inf["n_active"] == infos[k]["n_active"]
     assert ch["block_size"] in (128, 256) and ch["chunk"] in (4, 8, 16, 32, 64)
-    assert ch["geometry_early"] in (0, 1)
+    assert ch["geometry_early"] in (0, 1) and ch["activity"] == 0
     assert ch["n_candidates"] >= 20 and 0 < ch["ms_best"] <= ch["ms_before"]
     t_ens = ens.step(90, cfl)
     for k, m in enumerate(meshes):
@@ -98,3 +102,23 @@ def test_ensemble_autotune_keeps_state_and_results(precision):
     ens.close()
     for m in meshes:
         m.close()
+
+
+@pytest.mark.parametrize("precision", [capi.SWE_FP64, capi.SWE_FP32])
+def test_autotune_choice_survives_set_state_adjoint_style_calls(precision):
+    # whichever shape (and activity mode) the tuner keeps, later set_state,
+    # boundary changes and frozen-dt steps give the untuned mesh's results
+    mi = mg.river(160, 24, seed=6, n_bumps=20)
+    tuned, plain = _mesh(mi, precision), _mesh(mi, precision)
+    tuned.autotune(trial_steps=2)
+    for m in (tuned, plain):
+        m.step(20)
+        m.set_state(*(x.astype(m.dtype) for x in (mi.h, mi.hu, mi.hv)))
+        m.step(31)
+        m.set_bc(mi.bcs[1][0], mg.BC_WALL)
+        m.step(17)
+    if precision == capi.SWE_FP64:
+        dts = np.full(9, 0.05)
+        assert tuned.step_dt(dts) == plain.step_dt(dts)
+    assert tuned.step(40) == plain.step(40)
+    assert _same(tuned.get_state(), plain.get_state())

@@ -202,6 +202,30 @@ def test_kernel_variants_are_bitwise_identical(precision, variants):
         assert all(np.array_equal(x, y) for x, y in zip(ref, got)), (b, mb, st, ge)
 
 
+@pytest.mark.parametrize("precision", [capi.SWE_FP64, capi.SWE_FP32])
+@pytest.mark.parametrize("maker", ["river", "dry_canal"])
+def test_activity_mode_is_bitwise_neutral(precision, maker):
+    # activity bytes replace the quiet-cell neighbour test: same states, times
+    # and count of cells that ran the flux path, through wetting fronts, an
+    # inflow and a fixed stage, on a cell count that is not a multiple of 32
+    if maker == "river":
+        mi = mg.river(101, 21, seed=8)
+    else:
+        mi = mg.canal(401, 20, Lx=200.0, Ly=10.0, hR=0.0, seed=3, manning=0.03)
+    assert mi.n_cells % 32 != 0
+    ref, tref, iref = _gpu_run(mi, 301, precision=precision)
+    f32 = precision == capi.SWE_FP32
+    shapes = [dict(), dict(block_size=128, min_blocks=8 if f32 else 1), dict(graph_steps=-1),
+              dict(geometry_early=1, block_size=128, min_blocks=8 if f32 else 1)]
+    if f32:
+        shapes.append(dict(block_size=512, min_blocks=2))
+    for kw in shapes:
+        got, t, info = _gpu_run(mi, 301, precision=precision, activity=1, **kw)
+        assert t == tref, kw
+        assert all(np.array_equal(x, y) for x, y in zip(ref, got)), kw
+        assert info["n_active"] == iref["n_active"], kw
+
+
 def test_graphs_block_sizes_and_device_io_are_bitwise_neutral():
     mi = mg.river(100, 20, seed=8)
     ref, tref, _ = _gpu_run(mi, 301, graph_steps=-1, block_size=128)
