@@ -105,6 +105,14 @@ typedef struct swe_config {
                          (256, 4), (512, 2) with geometry_early 0, (128, 8), (256, 4) with 1;
                          FP64 (128|256, 1) with 0, (128, 1) with 1 (stages ignored).  Results
                          do not depend on it */
+    int edge_pass;    /* 1: each step first evaluates every interior edge's flux once (one thread
+                         per edge, from its left cell), then updates the cells from those
+                         fluxes; 0 (default): each cell evaluates its own three edges, so every
+                         interior flux is evaluated twice.  The edge pass halves the flux
+                         arithmetic for more memory traffic: it pays where the arithmetic
+                         bounds the step (FP64).  Compiled cell passes: FP32 (256, 4, 1),
+                         (128, 8, 1); FP64 (128|256, 1, 1), all with geometry_early 0.  Not
+                         with activity.  Results do not depend on it */
 } swe_config;
 
 /* Fills *cfg with the defaults listed above. */
@@ -395,6 +403,7 @@ typedef struct swe_tune {
     int stages;              /* chosen cp.async staging depth (1 = direct loads) */
     int geometry_early;      /* chosen geometry load placement (swe_config.geometry_early) */
     int activity;            /* chosen activity mode (swe_config.activity; 0 for ensembles) */
+    int edge_pass;           /* chosen edge-pass mode (swe_config.edge_pass; 0 for ensembles) */
     int chunk;               /* ensembles: tiles per round-robin chunk; 0 for a mesh */
     int64_t grid;            /* blocks launched per step */
     double cells_per_thread; /* cells each thread updates per step: cells / (grid * block_size) */
@@ -405,8 +414,8 @@ typedef struct swe_tune {
 
 /*
  * Chooses the step kernel's launch shape for this mesh by measurement: every
- * compiled (block_size, min_blocks, stages, geometry_early, activity) shape
- * (see swe_config) with several
+ * compiled (block_size, min_blocks, stages, geometry_early, activity,
+ * edge_pass) shape (see swe_config) with several
  * grid sizes -- one or two resident waves looping over the cells, or 1, 2 or 4
  * cells per thread -- is timed with CUDA events over trial_steps steps
  * (>= 1; 0 = 8), twice, and the fastest is kept for all later steps.  The

@@ -179,6 +179,20 @@ StepArgs<T> make_args(swe_mesh* m, int64_t step_index, double cfl) {
     a.hll = m->cfg.flux == SWE_FLUX_HLL ? 1 : 0;
     a.dt_fixed = nullptr;
     a.dt_log = (double*)(m->small + kSlotDtLast);  // size of the last step, for diagnostics
+    a.ecells = nullptr;
+    a.eln = nullptr;
+    a.eflux = nullptr;
+    a.esrc = nullptr;
+    a.eidx = nullptr;
+    a.n_edges = 0;
+    if (m->cfg.edge_pass && m->eflux) {
+        a.ecells = m->ecells;
+        a.eln = (const T*)m->eln;
+        a.eflux = (V4<T>*)m->eflux;
+        a.esrc = (T*)m->esrc;
+        a.eidx = m->eidx;
+        a.n_edges = m->n_edges;
+    }
     a.act_in = nullptr;
     a.act_next = nullptr;
     a.act_clear = nullptr;
@@ -365,6 +379,13 @@ cudaError_t launch_raw_t(swe_mesh* m, const void* in, void* out, unsigned long l
     a.act_in = nullptr;
     a.act_next = nullptr;
     a.act_clear = nullptr;
+    const bool edges = m->plain.edges && m->eflux;
+    a.ecells = edges ? m->ecells : nullptr;
+    a.eln = edges ? (const T*)m->eln : nullptr;
+    a.eflux = edges ? (V4<T>*)m->eflux : nullptr;
+    a.esrc = edges ? (T*)m->esrc : nullptr;
+    a.eidx = edges ? m->eidx : nullptr;
+    a.n_edges = edges ? m->n_edges : 0;
     a.grid = m->plain.grid;
     return Launch<T>::step(a, m->plain.block, m->plain.min_blocks, m->plain.stages, m->plain.geo, st);
 }
@@ -376,6 +397,61 @@ cudaError_t launch_step_raw(swe_mesh* m, const void* in, void* out, unsigned lon
     return m->cfg.precision == SWE_FP32
                ? launch_raw_t<float>(m, in, out, small, step_index, cfl, dt_fixed, dt_log, st, with_activity)
                : launch_raw_t<double>(m, in, out, small, step_index, cfl, dt_fixed, dt_log, st, with_activity);
+}
+
+int build_edges(swe_mesh* m) {
+    if (m->eflux) return SWE_OK;
+    const HostMesh& H = m->hm;
+    const int64_t n = H.n_cells;
+    std::vector<int2> cells;
+    std::vector<double> ln;
+    std::vector<int4> eidx(n, make_int4(-1, -1, -1, 0));
+    cells.reserve(3 * n / 2 + 1);
+    ln.reserve(3 * n + 2);
+    // edges in the order of their left cell (locality), each once
+    for (int64_t c = 0; c < n; ++c)
+        for (int j = 0; j < 3; ++j) {
+            const int32_t code = H.code[3 * c + j];
+            if (code >= 0 && !(code & kFlipBit)) {
+                const int e = (int)cells.size();
+                const int k = code & kNbrMask;
+                cells.push_back(make_int2((int)c, k));
+                ln.push_back(H.ln[6 * c + 2 * j]);
+                ln.push_back(H.ln[6 * c + 2 * j + 1]);
+                (j == 0 ? eidx[c].x : (j == 1 ? eidx[c].y : eidx[c].z)) = e;
+                for (int jk = 0; jk < 3; ++jk)
+                    if ((H.code[3 * k + jk] & kNbrMask) == (int32_t)c && H.code[3 * k + jk] >= 0)
+                        (jk == 0 ? eidx[k].x : (jk == 1 ? eidx[k].y : eidx[k].z)) = e;
+            }
+        }
+    const int64_t E = (int64_t)cells.size();
+    const size_t esz = m->esz;
+    std::vector<char> lnt(2 * E * esz);
+    for (int64_t q = 0; q < 2 * E; ++q) {
+        if (esz == 4) { const float v = (float)ln[q]; std::memcpy(&lnt[q * 4], &v, 4); }
+        else std::memcpy(&lnt[q * 8], &ln[q], 8);
+    }
+    const size_t Eb = (size_t)std::max<int64_t>(E, 1);
+    cudaError_t e = cudaMalloc((void**)&m->ecells, Eb * sizeof(int2));
+    if (e == cudaSuccess) e = cudaMalloc(&m->eln, 2 * Eb * esz);
+    if (e == cudaSuccess) e = cudaMalloc(&m->eflux, Eb * 4 * esz);
+    if (e == cudaSuccess) e = cudaMalloc(&m->esrc, Eb * esz);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&m->eidx, (size_t)n * sizeof(int4));
+    if (e != cudaSuccess) {
+        void* bufs[] = {m->ecells, m->eln, m->eflux, m->esrc, m->eidx};
+        for (void* b : bufs)
+            if (b) cudaFree(b);
+        m->ecells = nullptr; m->eln = nullptr; m->eflux = nullptr; m->esrc = nullptr; m->eidx = nullptr;
+        set_error("edge pass: device allocation failed");
+        return SWE_ENOMEM;
+    }
+    if (E) e = cudaMemcpy(m->ecells, cells.data(), E * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && E) e = cudaMemcpy(m->eln, lnt.data(), 2 * E * esz, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m->eidx, eidx.data(), n * sizeof(int4), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "edge pass: upload");
+    m->n_edges = E;
+    m->device_bytes += (int64_t)(Eb * (sizeof(int2) + 7 * esz) + n * sizeof(int4));
+    return SWE_OK;
 }
 
 int init_activity(swe_mesh* m) {
@@ -433,6 +509,7 @@ void swe_config_default(swe_config* cfg) {
     cfg->stages = 0;
     cfg->geometry_early = 0;
     cfg->activity = 0;
+    cfg->edge_pass = 0;
     cfg->flux = SWE_FLUX_HLLC;
 }
 
@@ -444,7 +521,8 @@ void swe_mesh_destroy(swe_mesh* m) {
     if (m->stream) cudaStreamSynchronize(m->stream);
     drop_graph(m);
     void* bufs[] = {m->state[0], m->state[1], m->geoA, m->geoB, m->topo, m->gm2, m->zdev, m->perm,
-                    m->stage[0], m->stage[1], m->stage[2], m->small, m->act[0], m->act[1], m->act[2]};
+                    m->stage[0], m->stage[1], m->stage[2], m->small, m->act[0], m->act[1], m->act[2],
+                    m->ecells, m->eln, m->eflux, m->esrc, m->eidx};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
@@ -467,6 +545,14 @@ int swe_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* tris, i
     }
     if (c.activity != 0 && c.activity != 1) {
         set_error("swe_mesh_create: activity must be 0 or 1");
+        return SWE_EINVAL;
+    }
+    if (c.edge_pass != 0 && c.edge_pass != 1) {
+        set_error("swe_mesh_create: edge_pass must be 0 or 1");
+        return SWE_EINVAL;
+    }
+    if (c.edge_pass && c.activity) {
+        set_error("swe_mesh_create: edge_pass and activity exclude each other");
         return SWE_EINVAL;
     }
     if (c.block_size == 0) c.block_size = c.precision == SWE_FP32 ? 256 : 128;
@@ -515,17 +601,21 @@ int swe_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* tris, i
     }
     rc = c.precision == SWE_FP32 ? upload_static<float>(m) : upload_static<double>(m);
     if (rc) { swe_mesh_destroy(m); return rc; }
+    if (c.edge_pass) {
+        rc = build_edges(m);
+        if (rc) { swe_mesh_destroy(m); return rc; }
+    }
     {
         int per_sm = 0, sms = 0;
         e = c.precision == SWE_FP32
                 ? Launch<float>::resident_blocks(c.block_size, c.min_blocks, c.stages, c.geometry_early, c.activity,
-                                                 &per_sm)
+                                                 c.edge_pass, &per_sm)
                 : Launch<double>::resident_blocks(c.block_size, c.min_blocks, c.stages, c.geometry_early, c.activity,
-                                                  &per_sm);
+                                                  c.edge_pass, &per_sm);
         if (e == cudaErrorInvalidValue) {
             swe_mesh_destroy(m);
             set_error("swe_mesh_create: no compiled step kernel for this block_size / min_blocks / stages / "
-                      "geometry_early / activity");
+                      "geometry_early / activity / edge_pass");
             return SWE_EINVAL;
         }
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device);
@@ -535,7 +625,7 @@ int swe_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* tris, i
         m->grid = (unsigned)std::min(need, wave);
         // launches without activity bytes: the same shape, or the default one
         // when the configured shape exists only as an activity kernel
-        m->plain = LaunchShape{c.block_size, c.min_blocks, c.stages, c.geometry_early, m->grid};
+        m->plain = LaunchShape{c.block_size, c.min_blocks, c.stages, c.geometry_early, c.edge_pass, m->grid};
         if (c.activity) {
             LaunchShape d;
             d.block = c.precision == SWE_FP32 ? 256 : 128;
@@ -544,8 +634,9 @@ int swe_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* tris, i
             d.stages = c.precision == SWE_FP32 ? 3 : 1;
             d.geo = 0;
             int pb = 0;
-            e = c.precision == SWE_FP32 ? Launch<float>::resident_blocks(d.block, d.min_blocks, d.stages, 0, 0, &pb)
-                                        : Launch<double>::resident_blocks(d.block, d.min_blocks, d.stages, 0, 0, &pb);
+            e = c.precision == SWE_FP32
+                    ? Launch<float>::resident_blocks(d.block, d.min_blocks, d.stages, 0, 0, 0, &pb)
+                    : Launch<double>::resident_blocks(d.block, d.min_blocks, d.stages, 0, 0, 0, &pb);
             if (e != cudaSuccess) { swe_mesh_destroy(m); return cuda_fail(e, "swe_mesh_create: occupancy"); }
             d.grid = (unsigned)std::min((long long)((n + d.block - 1) / d.block), (long long)std::max(pb, 1) * std::max(sms, 1));
             m->plain = d;

@@ -462,6 +462,7 @@ int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
         out->stages = pick.stages;
         out->geometry_early = pick.geo_early;
         out->activity = 0;
+        out->edge_pass = 0;
         out->chunk = 1 << pick.chunk_log2;
         out->grid = pick.grid;
         out->cells_per_thread = (double)E->n_total / ((double)pick.grid * pick.block);

@@ -44,7 +44,7 @@ void set_error(const std::string& msg);
 
 // A launch shape of the step kernel.
 struct LaunchShape {
-    int block = 0, min_blocks = 0, stages = 0, geo = 0;
+    int block = 0, min_blocks = 0, stages = 0, geo = 0, edges = 0;
     unsigned grid = 0;
 };
 
@@ -65,6 +65,8 @@ cudaError_t launch_step_raw(swe_mesh* m, const void* in, void* out, unsigned lon
                             bool with_activity = false);
 // Allocates (once) and fills the activity bytes of m's current state.
 int init_activity(swe_mesh* m);
+// Builds (once) the interior-edge list of the edge-pass step.
+int build_edges(swe_mesh* m);
 // The activity kernel indexes cells with 32 bits: meshes below this size.
 constexpr int64_t kActivityMaxCells = int64_t(1) << 29;
 // Applies pending boundary-group changes of m to the device.
@@ -110,6 +112,13 @@ struct swe_mesh {
     // other buffers: adjoint, frozen time steps); equals the cfg shape when
     // activity is off
     swe::LaunchShape plain;
+    // edge pass (cfg.edge_pass): interior edges in canonical orientation
+    int64_t n_edges = 0;
+    int2* ecells = nullptr;            // (left, right)
+    void* eln = nullptr;               // [E][2] T, L n outward from the left cell
+    void* eflux = nullptr;             // V4<T>[E]
+    void* esrc = nullptr;              // T[E]
+    int4* eidx = nullptr;              // per cell, the edge of each local edge (-1: boundary)
 };
 
 

@@ -72,6 +72,14 @@ struct StepArgs {
     const unsigned char* act_in;
     unsigned char* act_next;
     unsigned char* act_clear;
+    // edge pass (step_kernel with EDGES): interior edges in canonical orientation,
+    // evaluated once per step by edge_flux_kernel before the cell pass
+    const int2* ecells;                // (left, right) cell of each interior edge
+    const T* eln;                      // [E][2] L n of the edge, outward from the left cell
+    V4<T>* eflux;                      // (F0, F1, F2, bed source factor of the left cell) per edge
+    T* esrc;                           // bed source factor of the right cell per edge
+    const int4* eidx;                  // per cell: the interior edge of each local edge (x, y, z)
+    long long n_edges;
     T g, h_dry;
     BcTable bc;
     __device__ __forceinline__ int bc_kind(int grp) const { return bc.kind[grp]; }
@@ -197,26 +205,36 @@ __device__ __forceinline__ void riemann_hllc(T hL, T unL, T utL, T hR, T unR, T 
     if (speeds) { speeds[0] = SL; speeds[1] = SR; speeds[2] = Ss; }
 }
 
-// ---- block min of a non-negative double, published with one atomicMin -------------
-// Optionally also sums a per-thread counter into *count_dst (one atomicAdd per block).
-template <int BLOCK>
-__device__ __forceinline__ void block_min_publish(double cand, unsigned long long* dst,
-                                                  unsigned cnt = 0u, unsigned long long* count_dst = nullptr) {
-    __shared__ double warp_min[BLOCK / 32];
+template <typename T>
+__device__ __forceinline__ T inf_of();
+template <>
+__device__ __forceinline__ float inf_of<float>() { return __int_as_float(0x7F800000); }
+template <>
+__device__ __forceinline__ double inf_of<double>() { return __longlong_as_double((long long)kInfBits); }
+
+// ---- block min of a non-negative candidate, published with one atomicMin ----------
+// The minimum is taken in the candidate's own precision and widened to double
+// once (exact and monotone, so the result equals a double minimum): an FP32
+// kernel keeps its reduction off the FP64 pipe.  Non-negative doubles order
+// like their bit patterns, so the 64-bit atomicMin is exact.  Optionally also
+// sums a per-thread counter into *count_dst (one atomicAdd per block).
+template <int BLOCK, typename T>
+__device__ __forceinline__ void block_min_publish(T cand, unsigned long long* dst, unsigned cnt = 0u,
+                                                  unsigned long long* count_dst = nullptr) {
+    __shared__ T warp_min[BLOCK / 32];
     __shared__ unsigned warp_cnt[BLOCK / 32];
-    for (int o = 16; o > 0; o >>= 1) cand = fmin(cand, __shfl_xor_sync(0xffffffffu, cand, o));
+    for (int o = 16; o > 0; o >>= 1) cand = tmin(cand, __shfl_xor_sync(0xffffffffu, cand, o));
     if (count_dst) cnt = __reduce_add_sync(0xffffffffu, cnt);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) { warp_min[wid] = cand; warp_cnt[wid] = cnt; }
     __syncthreads();
     if (wid == 0) {
-        double v = lane < BLOCK / 32 ? warp_min[lane] : __longlong_as_double((long long)kInfBits);
+        T v = lane < BLOCK / 32 ? warp_min[lane] : inf_of<T>();
         unsigned c = lane < BLOCK / 32 ? warp_cnt[lane] : 0u;
-        for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+        for (int o = 16; o > 0; o >>= 1) v = tmin(v, __shfl_xor_sync(0xffffffffu, v, o));
         if (count_dst) c = __reduce_add_sync(0xffffffffu, c);
-        // non-negative doubles order like their bit patterns: the min is exact
-        if (lane == 0 && v < __longlong_as_double((long long)kInfBits))
-            atomicMin(dst, (unsigned long long)__double_as_longlong(v));
+        if (lane == 0 && v < inf_of<T>())
+            atomicMin(dst, (unsigned long long)__double_as_longlong((double)v));
         if (lane == 0 && count_dst && c) atomicAdd(count_dst, (unsigned long long)c);
     }
 }
@@ -231,13 +249,6 @@ template <typename Args>
 __device__ __forceinline__ double load_gm2(const Args& a, long long i, const int4&, double) {
     return a.gm2[i];
 }
-
-template <typename T>
-__device__ __forceinline__ T inf_of();
-template <>
-__device__ __forceinline__ float inf_of<float>() { return __int_as_float(0x7F800000); }
-template <>
-__device__ __forceinline__ double inf_of<double>() { return __longlong_as_double((long long)kInfBits); }
 
 // ---- asynchronous global -> shared copies (cp.async, 16 B, L2 only) ------------------
 // Each thread stages its own future cells' records; it alone reads them back,
@@ -277,7 +288,7 @@ __device__ __forceinline__ void cell_velocity(T h, T hu, T hv, T h_dry, T& u, T&
 template <typename T>
 __device__ __forceinline__ void edge_interior(T hi, T ui, T vi, T zi, T hk, T huk, T hvk, T zk, T n1, T n2,
                                               bool flip, T g, T h_dry, T& F0, T& F1, T& F2, T& src,
-                                              bool hll_only = false) {
+                                              bool hll_only = false, T* src_k = nullptr) {
     T uk, vk;
     cell_velocity<T>(hk, huk, hvk, h_dry, uk, vk);
     // hydrostatic reconstruction (Eq 28): z* = max(z_i, z_k)
@@ -300,6 +311,7 @@ __device__ __forceinline__ void edge_interior(T hi, T ui, T vi, T zi, T hk, T hu
     F1 = s * (G2 * c1 - G3 * c2);
     F2 = s * (G2 * c2 + G3 * c1);
     src = T(0.5) * g * (hsi * hsi - hi * hi);
+    if (src_k) *src_k = T(0.5) * g * (hsk * hsk - hk * hk);   // the other cell's bed source factor
 }
 
 // Flux leaving cell i through a boundary edge of the given kind (Section 3.1).
@@ -370,7 +382,12 @@ __device__ __forceinline__ void friction_update(T hi, T qx, T qy, T gm2, T Rh, T
 // gathers (one memory round trip fewer for a cell that runs the flux path,
 // at the price of geometry traffic for quiet cells too); otherwise they are
 // issued after the quiet test.  Both give the same results.
-template <typename T, bool GEO_EARLY, typename Args>
+//
+// EDGES takes the interior fluxes from the edge pass (edge_flux_kernel, the
+// same edge_interior arithmetic evaluated once per edge from the left cell)
+// instead of evaluating them here; an edge with both cells dry has no flux and
+// its bed source factor is formed inline, as edge_interior would form it.
+template <typename T, bool GEO_EARLY, bool EDGES = false, typename Args>
 __device__ __forceinline__ T update_cell(const Args& a, long long i, const V4<T>& own, const int4& tp, T dt,
                                          unsigned& active, unsigned long long* n_clamped, unsigned* status) {
     using A = Ar<T>;
@@ -414,6 +431,8 @@ __device__ __forceinline__ T update_cell(const Args& a, long long i, const V4<T>
     T ui, vi;
     cell_velocity<T>(hi, own.y, own.z, h_dry, ui, vi);
     T f0 = T(0), f1 = T(0), f2 = T(0), sx = T(0), sy = T(0);
+    int4 ei = make_int4(-1, -1, -1, 0);
+    if constexpr (EDGES) ei = a.eidx[i];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         const int c = j == 0 ? code[0] : (j == 1 ? code[1] : code[2]);
@@ -427,8 +446,27 @@ __device__ __forceinline__ T update_cell(const Args& a, long long i, const V4<T>
         T F0, F1, F2;
         if (c >= 0) {
             T src;
-            edge_interior<T>(hi, ui, vi, zi, o.x, o.y, o.z, o.w, n1, n2, (c & kFlipBit) != 0, g, h_dry, F0, F1, F2,
-                             src, a.hll != 0);
+            if constexpr (EDGES) {
+                if (!(hi > h_dry) && !(o.x > h_dry)) {
+                    const T zs = tmax(zi, o.w);
+                    const T hsi = tmax(T(0), hi + zi - zs);
+                    F0 = T(0); F1 = T(0); F2 = T(0);
+                    src = T(0.5) * g * (hsi * hsi - hi * hi);
+                } else {
+                    const int e = j == 0 ? ei.x : (j == 1 ? ei.y : ei.z);
+                    const V4<T> fl = a.eflux[e];
+                    if (c & kFlipBit) {
+                        F0 = -fl.x; F1 = -fl.y; F2 = -fl.z;
+                        src = a.esrc[e];
+                    } else {
+                        F0 = fl.x; F1 = fl.y; F2 = fl.z;
+                        src = fl.w;
+                    }
+                }
+            } else {
+                edge_interior<T>(hi, ui, vi, zi, o.x, o.y, o.z, o.w, n1, n2, (c & kFlipBit) != 0, g, h_dry, F0, F1,
+                                 F2, src, a.hll != 0);
+            }
             sx += src * lx;
             sy += src * ly;
         } else {
@@ -476,7 +514,7 @@ __device__ __forceinline__ T update_cell(const Args& a, long long i, const V4<T>
 // reduction (and its barrier) runs once per block.  With STAGES > 1 each
 // thread keeps its next STAGES-1 cells' state and topology records in flight
 // through cp.async into its own shared-memory slots.
-template <typename T, int BLOCK, int MINB, int STAGES, bool GEO_EARLY>
+template <typename T, int BLOCK, int MINB, int STAGES, bool GEO_EARLY, bool EDGES = false>
 __global__ void __launch_bounds__(BLOCK, MINB) step_kernel(const StepArgs<T> a) {
     const double dt_d = a.dt_fixed ? *a.dt_fixed : a.cfl * (*a.dt_read);
     const bool have_dt = dt_d < __longlong_as_double((long long)kInfBits);
@@ -497,7 +535,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_kernel(const StepArgs<T> a) 
         for (; i < a.n; i += stride) {
             const V4<T> own = a.s_in[i];
             const int4 tp = a.topo[i];
-            cand = tmin(cand, update_cell<T, GEO_EARLY>(a, i, own, tp, dt, active, a.n_clamped, a.status));
+            cand = tmin(cand, update_cell<T, GEO_EARLY, EDGES>(a, i, own, tp, dt, active, a.n_clamped, a.status));
         }
     } else {
         __shared__ V4<T> st_own[STAGES][BLOCK];
@@ -525,12 +563,44 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_kernel(const StepArgs<T> a) 
             cp_async_wait<STAGES - 1>();
             const V4<T> own = st_own[slot][tid];
             const int4 tp = st_topo[slot][tid];
-            cand = tmin(cand, update_cell<T, GEO_EARLY>(a, i, own, tp, dt, active, a.n_clamped, a.status));
+            cand = tmin(cand, update_cell<T, GEO_EARLY, EDGES>(a, i, own, tp, dt, active, a.n_clamped, a.status));
             slot = slot == STAGES - 1 ? 0 : slot + 1;
         }
         cp_async_wait<0>();
     }
-    block_min_publish<BLOCK>((double)cand, a.dt_write, active, a.n_active);
+    block_min_publish<BLOCK>(cand, a.dt_write, active, a.n_active);
+}
+
+// ---- edge pass: each interior edge's flux once per step ----------------------------
+// The canonical evaluation of an interior edge (from its left cell, Eq 12-30)
+// is the one both of its cells make in step_kernel; here one thread makes it
+// and stores the flux leaving the left cell and both cells' bed source
+// factors, which the cell pass (step_kernel with EDGES) applies with the
+// left/right sign.  Edges with both cells dry are skipped: the cells form
+// them inline.  Worth it where the flux arithmetic, not memory, bounds the
+// step (the FP64 pipe).
+template <typename T, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) edge_flux_kernel(const StepArgs<T> a) {
+    const T g = a.g, h_dry = a.h_dry;
+    const long long stride = (long long)gridDim.x * BLOCK;
+    for (long long e = (long long)blockIdx.x * BLOCK + threadIdx.x; e < a.n_edges; e += stride) {
+        const int2 lr = a.ecells[e];
+        const V4<T> L = a.s_in[lr.x], R = a.s_in[lr.y];
+        if (!(L.x > h_dry) && !(R.x > h_dry)) continue;
+        const T lx = a.eln[2 * e], ly = a.eln[2 * e + 1];
+        const T l2 = lx * lx + ly * ly;
+        const T rl = Ar<T>::rsqrt_(l2);
+        const T n1 = lx * rl, n2 = ly * rl;
+        T ui, vi;
+        cell_velocity<T>(L.x, L.y, L.z, h_dry, ui, vi);
+        T F0, F1, F2, sl, sr;
+        edge_interior<T>(L.x, ui, vi, L.w, R.x, R.y, R.z, R.w, n1, n2, false, g, h_dry, F0, F1, F2, sl, a.hll != 0,
+                         &sr);
+        V4<T> f;
+        f.x = F0; f.y = F1; f.z = F2; f.w = sl;
+        a.eflux[e] = f;
+        a.esrc[e] = sr;
+    }
 }
 
 // ---- the fused step with activity bytes ------------------------------------------
@@ -651,7 +721,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_kernel_act(const StepArgs<T>
         }
         cp_async_wait<0>();
     }
-    block_min_publish<BLOCK>((double)cand, a.dt_write, active, a.n_active);
+    block_min_publish<BLOCK>(cand, a.dt_write, active, a.n_active);
 }
 
 // Activity bytes of a state (into a zeroed buffer): a wet cell marks itself and
@@ -784,13 +854,13 @@ __global__ void __launch_bounds__(BLOCK) dt_kernel(const V4<T>* __restrict__ s, 
                                                    long long n, T g, T h_dry, unsigned long long* dt_write) {
     using A = Ar<T>;
     const long long i = (long long)blockIdx.x * BLOCK + threadIdx.x;
-    double cand = __longlong_as_double((long long)kInfBits);
+    T cand = inf_of<T>();
     if (i < n) {
         const V4<T> c = s[i];
         if (c.x > h_dry) {
             const T r = A::rcp_(c.x);
             const T u = c.y * r, v = c.z * r;
-            cand = (double)A::div_(geoB[i].w, A::sqrt_(g * c.x) + A::sqrt_(u * u + v * v));
+            cand = A::div_(geoB[i].w, A::sqrt_(g * c.x) + A::sqrt_(u * u + v * v));
         }
     }
     block_min_publish<BLOCK>(cand, dt_write);
@@ -845,8 +915,11 @@ struct Launch {
     // with a.act_in set, the activity kernel (stages ignored) runs
     static cudaError_t step(const StepArgs<T>& a, int block, int min_blocks, int stages, int geo_early,
                             cudaStream_t st);
+    // with a.eflux set (and a.act_in not), the edge pass then the cell pass run
     static cudaError_t resident_blocks(int block, int min_blocks, int stages, int geo_early, int activity,
-                                       int* per_sm);
+                                       int edges, int* per_sm);
+    // compiled (block, min_blocks, stages, geo_early) shapes of the cell pass of the edge-pass step
+    static int edge_variants(int (*out)[4], int max);
     // compiled (block, min_blocks, geo_early) shapes of the activity kernel
     static int act_variants(int (*out)[3], int max);
     static cudaError_t act_init(const V4<T>* s, const int4* topo, long long n, T h_dry, unsigned char* act,

@@ -25,6 +25,12 @@ static inline unsigned grid_for(long long n, int block) {
 #define SWE_STEP_VARIANTS_F64(X) \
     X(128, 1, 1, 0) X(256, 1, 1, 0) X(512, 1, 1, 0) X(128, 1, 2, 0) X(256, 1, 2, 0) X(128, 1, 1, 1) X(256, 1, 1, 1)
 
+// (block, min blocks per SM, stages, geometry early) shapes of the cell pass of
+// the edge-pass step (edge_flux_kernel runs before it with 256-thread blocks)
+#define SWE_EDGE_VARIANTS_F32(X) X(256, 4, 1, 0) X(128, 8, 1, 0)
+#define SWE_EDGE_VARIANTS_F64(X) X(128, 1, 1, 0) X(256, 1, 1, 0)
+constexpr int kEdgeBlock = 256;
+
 // (block, min blocks per SM, geometry early) shapes of the activity kernel
 // (its pipeline depth is fixed); shared memory: 3 state + 2 topology records
 // and 3 activity bytes per thread.
@@ -56,6 +62,27 @@ cudaError_t Launch<T>::step(const StepArgs<T>& a, int block, int min_blocks, int
 #undef SWE_LAUNCH_ACT
         return cudaErrorInvalidValue;
     }
+    if (a.eflux) {
+        if (a.n_edges > 0) {
+            const long long eb = (a.n_edges + kEdgeBlock - 1) / kEdgeBlock;
+            const unsigned egrid = (unsigned)(eb < 65536 ? eb : 65536);
+            edge_flux_kernel<T, kEdgeBlock><<<egrid, kEdgeBlock, 0, st>>>(a);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
+#define SWE_LAUNCH_EDGE(B, M, S, G) \
+    if (block == B && min_blocks == M && stages == S && geo_early == G) {        \
+        step_kernel<T, B, M, S, G != 0, true><<<grid, B, 0, st>>>(a);            \
+        return cudaGetLastError();                                                \
+    }
+        if constexpr (sizeof(T) == 4) {
+            SWE_EDGE_VARIANTS_F32(SWE_LAUNCH_EDGE)
+        } else {
+            SWE_EDGE_VARIANTS_F64(SWE_LAUNCH_EDGE)
+        }
+#undef SWE_LAUNCH_EDGE
+        return cudaErrorInvalidValue;
+    }
 #define SWE_LAUNCH(B, M, S, G) \
     if (block == B && min_blocks == M && stages == S && geo_early == G) {        \
         step_kernel<T, B, M, S, G != 0><<<grid, B, 0, st>>>(a);                  \
@@ -72,7 +99,19 @@ cudaError_t Launch<T>::step(const StepArgs<T>& a, int block, int min_blocks, int
 
 template <typename T>
 cudaError_t Launch<T>::resident_blocks(int block, int min_blocks, int stages, int geo_early, int activity,
-                                       int* per_sm) {
+                                       int edges, int* per_sm) {
+    if (edges) {
+#define SWE_OCC_EDGE(B, M, S, G) \
+    if (block == B && min_blocks == M && stages == S && geo_early == G)          \
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, step_kernel<T, B, M, S, G != 0, true>, B, 0);
+        if constexpr (sizeof(T) == 4) {
+            SWE_EDGE_VARIANTS_F32(SWE_OCC_EDGE)
+        } else {
+            SWE_EDGE_VARIANTS_F64(SWE_OCC_EDGE)
+        }
+#undef SWE_OCC_EDGE
+        return cudaErrorInvalidValue;
+    }
     if (activity) {
 #define SWE_OCC_ACT(B, M, G) \
     if (block == B && min_blocks == M && geo_early == G)                          \
@@ -107,6 +146,21 @@ int Launch<T>::step_variants(int (*out)[4], int max) {
         SWE_STEP_VARIANTS_F32(SWE_LIST)
     } else {
         SWE_STEP_VARIANTS_F64(SWE_LIST)
+    }
+#undef SWE_LIST
+    return k;
+}
+
+template <typename T>
+int Launch<T>::edge_variants(int (*out)[4], int max) {
+    int k = 0;
+#define SWE_LIST(B, M, S, G) \
+    if (k < max) { out[k][0] = B; out[k][1] = M; out[k][2] = S; out[k][3] = G; } \
+    ++k;
+    if constexpr (sizeof(T) == 4) {
+        SWE_EDGE_VARIANTS_F32(SWE_LIST)
+    } else {
+        SWE_EDGE_VARIANTS_F64(SWE_LIST)
     }
 #undef SWE_LIST
     return k;

@@ -25,13 +25,13 @@ using namespace swe;
 namespace {
 
 struct Shape {
-    int block, min_blocks, stages, geo_early, activity;
+    int block, min_blocks, stages, geo_early, activity, edges;
     unsigned grid;
 };
 
 bool same_shape(const Shape& a, const Shape& b) {
     return a.block == b.block && a.min_blocks == b.min_blocks && a.stages == b.stages && a.geo_early == b.geo_early &&
-           a.activity == b.activity && a.grid == b.grid;
+           a.activity == b.activity && a.edges == b.edges && a.grid == b.grid;
 }
 
 int tfail(cudaError_t e, const char* what) {
@@ -59,16 +59,16 @@ int candidate_shapes(const swe_mesh* m, std::vector<Shape>& cand) {
     if (e != cudaSuccess) return tfail(e, "swe_autotune: device attribute");
     // the shape in use first
     cand.push_back({m->cfg.block_size, m->cfg.min_blocks, m->cfg.stages, m->cfg.geometry_early, m->cfg.activity,
-                    m->grid});
-    auto add = [&](int block, int minb, int stages, int geo, int act) -> int {
+                    m->cfg.edge_pass, m->grid});
+    auto add = [&](int block, int minb, int stages, int geo, int act, int edges) -> int {
         int per_sm = 0;
-        cudaError_t er = Launch<T>::resident_blocks(block, minb, stages, geo, act, &per_sm);
+        cudaError_t er = Launch<T>::resident_blocks(block, minb, stages, geo, act, edges, &per_sm);
         if (er != cudaSuccess) return tfail(er, "swe_autotune: occupancy");
         const long long need = (n + block - 1) / block;
         const long long wave = (long long)std::max(per_sm, 1) * std::max(sms, 1);
         const long long grids[] = {wave, 2 * wave, need, (need + 1) / 2, (need + 3) / 4};
         for (long long gsz : grids) {
-            const Shape sh{block, minb, stages, geo, act, (unsigned)std::max(1LL, std::min(gsz, need))};
+            const Shape sh{block, minb, stages, geo, act, edges, (unsigned)std::max(1LL, std::min(gsz, need))};
             bool seen = false;
             for (const Shape& c : cand) seen = seen || same_shape(c, sh);
             if (!seen) cand.push_back(sh);
@@ -78,13 +78,18 @@ int candidate_shapes(const swe_mesh* m, std::vector<Shape>& cand) {
     int v[64][4];
     const int nv = std::min(Launch<T>::step_variants(v, 64), 64);
     for (int k = 0; k < nv; ++k) {
-        const int rc = add(v[k][0], v[k][1], v[k][2], v[k][3], 0);
+        const int rc = add(v[k][0], v[k][1], v[k][2], v[k][3], 0, 0);
+        if (rc) return rc;
+    }
+    const int ne = std::min(Launch<T>::edge_variants(v, 64), 64);
+    for (int k = 0; k < ne; ++k) {
+        const int rc = add(v[k][0], v[k][1], v[k][2], v[k][3], 0, 1);
         if (rc) return rc;
     }
     int w[64][3];
     const int nw = n < kActivityMaxCells ? std::min(Launch<T>::act_variants(w, 64), 64) : 0;
     for (int k = 0; k < nw; ++k) {
-        const int rc = add(w[k][0], w[k][1], 3, w[k][2], 1);
+        const int rc = add(w[k][0], w[k][1], 3, w[k][2], 1, 0);
         if (rc) return rc;
     }
     return SWE_OK;
@@ -96,8 +101,9 @@ void apply_shape(swe_mesh* m, const Shape& sh) {
     m->cfg.stages = sh.stages;
     m->cfg.geometry_early = sh.geo_early;
     m->cfg.activity = sh.activity;
+    m->cfg.edge_pass = sh.edges;
     m->grid = sh.grid;
-    if (!sh.activity) m->plain = LaunchShape{sh.block, sh.min_blocks, sh.stages, sh.geo_early, sh.grid};
+    if (!sh.activity) m->plain = LaunchShape{sh.block, sh.min_blocks, sh.stages, sh.geo_early, sh.edges, sh.grid};
 }
 
 template <typename T>
@@ -109,7 +115,10 @@ int autotune_t(swe_mesh* m, int trial_steps, swe_tune* out) {
     const Shape before = cand[0];
     const LaunchShape plain_before = m->plain;
     cudaStream_t st = m->stream;
-    // activity bytes of the current state for the activity-kernel trials
+    // the edge list for the edge-pass trials, and the activity bytes of the
+    // current state for the activity-kernel trials
+    rc = build_edges(m);
+    if (rc) return rc;
     if (n < kActivityMaxCells) {
         rc = init_activity(m);
         if (rc) return rc;
@@ -178,6 +187,7 @@ int autotune_t(swe_mesh* m, int trial_steps, swe_tune* out) {
         out->stages = pick.stages;
         out->geometry_early = pick.geo_early;
         out->activity = pick.activity;
+        out->edge_pass = pick.edges;
         out->chunk = 0;
         out->grid = pick.grid;
         out->cells_per_thread = (double)n / ((double)pick.grid * pick.block);

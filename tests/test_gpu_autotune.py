@@ -42,6 +42,8 @@ F32_SHAPES = {s + (0,) for s in [
 F64_SHAPES = {s + (0,) for s in [
     (128, 1, 1, 0), (256, 1, 1, 0), (512, 1, 1, 0), (128, 1, 2, 0), (256, 1, 2, 0), (128, 1, 1, 1), (256, 1, 1, 1)]} | {
     (128, 1, 3, 0, 1), (256, 1, 3, 0, 1), (128, 1, 3, 1, 1)}
+# (block, min_blocks, stages, geometry_early) of the edge pass's cell kernel
+EDGE_CELL_PASS = {capi.SWE_FP32: {(256, 4, 1, 0), (128, 8, 1, 0)}, capi.SWE_FP64: {(128, 1, 1, 0), (256, 1, 1, 0)}}
 
 
 @pytest.mark.parametrize("precision,maker", [(capi.SWE_FP64, "dam"), (capi.SWE_FP32, "dam"),
@@ -58,7 +60,9 @@ def test_mesh_autotune_keeps_state_and_results(precision, maker):
     assert info1["t"] == info0["t"] and info1["n_steps"] == info0["n_steps"]
     assert info1["dt_next"] == info0["dt_next"] and info1["n_active"] == info0["n_active"]
     shapes = F32_SHAPES if precision == capi.SWE_FP32 else F64_SHAPES
-    assert (ch["block_size"], ch["min_blocks"], ch["stages"], ch["geometry_early"], ch["activity"]) in shapes
+    key = (ch["block_size"], ch["min_blocks"], ch["stages"], ch["geometry_early"], ch["activity"])
+    assert key in shapes if ch["edge_pass"] == 0 else key[:4] in EDGE_CELL_PASS[precision]
+    assert not (ch["edge_pass"] and ch["activity"])
     assert ch["n_candidates"] > len(shapes) and ch["chunk"] == 0
     assert 0 < ch["ms_best"] <= ch["ms_before"]
     assert ch["grid"] >= 1
@@ -93,7 +97,7 @@ def test_ensemble_autotune_keeps_state_and_results(precision):
         assert inf["t"] == infos[k]["t"] and inf["dt_next"] == infos[k]["dt_next"]
         assert inf["n_active"] == infos[k]["n_active"]
     assert ch["block_size"] in (128, 256) and ch["chunk"] in (4, 8, 16, 32, 64)
-    assert ch["geometry_early"] in (0, 1) and ch["activity"] == 0
+    assert ch["geometry_early"] in (0, 1) and ch["activity"] == 0 and ch["edge_pass"] == 0
     assert ch["n_candidates"] >= 20 and 0 < ch["ms_best"] <= ch["ms_before"]
     t_ens = ens.step(90, cfl)
     for k, m in enumerate(meshes):

@@ -226,6 +226,36 @@ def test_activity_mode_is_bitwise_neutral(precision, maker):
         assert info["n_active"] == iref["n_active"], kw
 
 
+@pytest.mark.parametrize("precision", [capi.SWE_FP64, capi.SWE_FP32])
+@pytest.mark.parametrize("maker", ["river", "dry_canal", "dam"])
+def test_edge_pass_is_bitwise_neutral(precision, maker):
+    # each interior flux evaluated once by the edge pass and applied with the
+    # left/right sign: the same states, times and active counts as the cells'
+    # own evaluations, through wet/dry fronts and every boundary kind
+    if maker == "river":
+        mi = mg.river(101, 21, seed=8)
+    elif maker == "dry_canal":
+        mi = mg.canal(401, 20, Lx=200.0, Ly=10.0, hR=0.0, seed=3, manning=0.03)
+    else:
+        mi = mg.dam_break_4k()
+    ref, tref, iref = _gpu_run(mi, 301, precision=precision)
+    f32 = precision == capi.SWE_FP32
+    shapes = [dict(), dict(graph_steps=-1),
+              dict(block_size=128, min_blocks=8) if f32 else dict(block_size=256, min_blocks=1)]
+    for kw in shapes:
+        got, t, info = _gpu_run(mi, 301, precision=precision, edge_pass=1,
+                                **({"block_size": 256, "min_blocks": 4, "stages": 1} if f32 else {}) | kw)
+        assert t == tref, kw
+        assert all(np.array_equal(x, y) for x, y in zip(ref, got)), kw
+        assert info["n_active"] == iref["n_active"], kw
+
+
+def test_edge_pass_and_activity_exclude_each_other():
+    mi = mg.dam_break_4k()
+    with pytest.raises(capi.SWEError):
+        capi.Mesh(mi.nodes, mi.tris, mi.z, mi.manning, activity=1, edge_pass=1)
+
+
 def test_graphs_block_sizes_and_device_io_are_bitwise_neutral():
     mi = mg.river(100, 20, seed=8)
     ref, tref, _ = _gpu_run(mi, 301, graph_steps=-1, block_size=128)
