@@ -35,9 +35,10 @@ import numpy as np  # noqa: E402
 # int32 neighbour indices
 ALG_BYTES = {"f32": 16 * 4 + 12, "f64": 16 * 8 + 12}
 # FP64 flops (2 x DFMA + DADD + DMUL) per cell that runs the flux path, counted
-# by ncu on the 1M-cell canal (profiles/step_kernel_canal1m_fp64.md); quiet
-# cells take no flux path and do no FP64 arithmetic
-FP64_FLOPS_PER_ACTIVE_CELL = 855
+# by ncu on the 1M-cell canal (profiles/step_kernel_canal1m_fp64.md): the
+# cell-centric step evaluates every interior flux twice, the edge pass once;
+# quiet cells take no flux path and do no FP64 arithmetic
+FP64_FLOPS_PER_ACTIVE_CELL = {"cell": 855, "edge": 658}
 # GB300 FP64: 2 DFMA per clock per SM, 152 SMs
 FP64_DFMA_PER_CLK_SM, N_SM = 2, 152
 
@@ -373,14 +374,15 @@ def run_gpu(args, name):
         # the FP64 ALU peak at the maximum SM clock; the HBM figures stay as context
         sm_mhz = _peak_clock()
         peak64 = FP64_DFMA_PER_CLK_SM * 2 * N_SM * sm_mhz * 1e6 / 1e12
-        flops = FP64_FLOPS_PER_ACTIVE_CELL * active_frac * n
+        per_cell = FP64_FLOPS_PER_ACTIVE_CELL["edge" if shape.get("edge_pass") else "cell"]
+        flops = per_cell * active_frac * n
         ach64 = flops / (kernel_ms * 1e-3) / 1e12
         hbm = line["roofline"]
         line["roofline"] = {"bound": "alu", "achieved": ach64, "peak": peak64, "unit": "TFLOP/s",
                             "frac": ach64 / peak64, "traffic": traffic,
                             "peak_source": f"derived: {FP64_DFMA_PER_CLK_SM} DFMA/clk/SM x 2 flops x {N_SM} SMs x "
                                            f"{sm_mhz:.0f} MHz (FP64 pipe)",
-                            "flops_per_active_cell": FP64_FLOPS_PER_ACTIVE_CELL,
+                            "flops_per_active_cell": per_cell,
                             "active_cell_fraction": active_frac,
                             "hbm": {k: v for k, v in hbm.items() if k not in ("bound", "traffic")}}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -402,7 +402,7 @@ typedef struct swe_tune {
     int min_blocks;          /* chosen resident-block target the kernel is compiled for */
     int stages;              /* chosen cp.async staging depth (1 = direct loads) */
     int geometry_early;      /* chosen geometry load placement (swe_config.geometry_early) */
-    int activity;            /* chosen activity mode (swe_config.activity; 0 for ensembles) */
+    int activity;            /* chosen activity mode (swe_config.activity) */
     int edge_pass;           /* chosen edge-pass mode (swe_config.edge_pass; 0 for ensembles) */
     int chunk;               /* ensembles: tiles per round-robin chunk; 0 for a mesh */
     int64_t grid;            /* blocks launched per step */
@@ -433,11 +433,23 @@ SWE_API int swe_autotune(swe_mesh* mesh, int trial_steps, swe_tune* out);
  * The same for an ensemble's batched step: its compiled (block_size,
  * min_blocks, stages, geometry_early) shapes (FP32: (256, 4, 3|1|2, 0),
  * (128, 8, 3|1, 0), (256, 4, 3|1, 1), (128, 8, 3|1, 1); FP64: (256|128, 1,
- * 1|2, 0), (256|128, 1, 1, 1)) times chunks of 4 to 64 tiles, then grids of
- * half, one and two resident waves for the best of those.  Members' states, times and
+ * 1|2, 0), (256|128, 1, 1, 1)) and its activity-mode shapes (activity 1,
+ * stages 3: FP32 (128, 8) and (256, 4) with geometry_early 0|1; FP64
+ * (256|128, 1) with 0) times chunks of 4 to 64 tiles, then grids of half, one
+ * and two resident waves for the best of those.  Members' states, times and
  * steps are unchanged by the call and by the choice.  trial_steps 0 = 4.
  */
 SWE_API int swe_ensemble_autotune(swe_ensemble* ens, int trial_steps, swe_tune* out);
+
+/*
+ * Sets an ensemble's launch shape directly (for instance one that
+ * swe_ensemble_autotune chose earlier): block_size, min_blocks, stages,
+ * geometry_early and activity must name a compiled shape (listed above;
+ * stages is ignored with activity), chunk a power of two up to 4096 tiles,
+ * grid the blocks to launch (0 = one resident wave); other fields are
+ * ignored.  Results do not depend on the shape.  Errors: SWE_EINVAL.
+ */
+SWE_API int swe_ensemble_set_shape(swe_ensemble* ens, const swe_tune* shape);
 
 /* Message of the last failed call on this thread ("" if none). */
 SWE_API const char* swe_last_error(void);

@@ -34,7 +34,7 @@ EXPORTS = ["swe_config_default", "swe_mesh_create", "swe_mesh_destroy", "swe_set
            "swe_ensemble_step", "swe_ensemble_get_state", "swe_ensemble_get_info", "swe_adjoint",
            "swe_adjoint_series",
            "swe_step_dt", "swe_set_fields", "swe_diagnostics", "swe_run_to_steady", "swe_autotune",
-           "swe_ensemble_autotune", "swe_last_error"]
+           "swe_ensemble_autotune", "swe_ensemble_set_shape", "swe_last_error"]
 
 
 class swe_config(C.Structure):
@@ -120,6 +120,7 @@ def load():
                                       C.POINTER(C.c_int), C.POINTER(C.c_double)]
     lib.swe_autotune.argtypes = [vp, C.c_int, C.POINTER(swe_tune)]
     lib.swe_ensemble_autotune.argtypes = [vp, C.c_int, C.POINTER(swe_tune)]
+    lib.swe_ensemble_set_shape.argtypes = [vp, C.POINTER(swe_tune)]
     lib.swe_last_error.argtypes = []
     lib.swe_last_error.restype = C.c_char_p
     for name in EXPORTS:
@@ -376,6 +377,12 @@ class Ensemble:
         t = swe_tune()
         check(load().swe_ensemble_autotune(self._h, int(trial_steps), C.byref(t)))
         return {k: getattr(t, k) for k, _ in swe_tune._fields_}
+
+    def set_shape(self, block_size, min_blocks, stages=1, geometry_early=0, activity=0, chunk=4, grid=0):
+        """Sets the batched kernel's launch shape (see swe_ensemble_set_shape)."""
+        t = swe_tune(block_size=block_size, min_blocks=min_blocks, stages=stages, geometry_early=geometry_early,
+                     activity=activity, chunk=chunk, grid=grid)
+        check(load().swe_ensemble_set_shape(self._h, C.byref(t)))
 
     def info(self, member):
         inf = swe_info()

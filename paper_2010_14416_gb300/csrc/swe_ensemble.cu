@@ -50,7 +50,11 @@ struct swe_ensemble {
     void* stage[3] = {nullptr, nullptr, nullptr};
     int64_t stage_cells = 0;
     // launch shape (autotuned by swe_ensemble_autotune; none changes the results)
-    int block = 256, min_blocks = 1, stages = 1, geo_early = 0, chunk_log2 = 5;
+    int block = 256, min_blocks = 1, stages = 1, geo_early = 0, chunk_log2 = 5, activity = 0;
+    // activity bytes over the concatenated layout (activity mode)
+    unsigned char* act[3] = {nullptr, nullptr, nullptr};
+    int64_t act_len = 0;
+    bool act_valid = false;
     unsigned grid = 0;
     int64_t nstep = 0;
     std::vector<double> cfl_host;
@@ -137,6 +141,14 @@ EnsArgs<T> ens_args(swe_ensemble* E, int64_t step_index) {
     a.n_active = E->n_active;
     a.n_total = E->n_total;
     a.chunk_log2 = E->chunk_log2;
+    a.act_in = nullptr;
+    a.act_next = nullptr;
+    a.act_clear = nullptr;
+    if (E->activity && E->act[0]) {
+        a.act_in = E->act[p3];
+        a.act_next = E->act[(p3 + 1) % 3];
+        a.act_clear = E->act[(p3 + 2) % 3];
+    }
     a.slot_read = p3;
     a.slot_write = (p3 + 1) % 3;
     a.slot_reset = (p3 + 2) % 3;
@@ -155,6 +167,7 @@ cudaError_t ens_launch(swe_ensemble* E, int64_t step_index, const EnsPhysics& ph
     EnsArgs<T> a = ens_args<T>(E, step_index);
     a.g = (T)ph.g;
     a.h_dry = (T)ph.h_dry;
+    if (a.act_in) return Launch<T>::ensemble_step_act(a, E->block, E->min_blocks, E->geo_early, E->grid, st);
     return Launch<T>::ensemble_step(a, E->block, E->min_blocks, E->stages, E->geo_early, E->grid, st);
 }
 
@@ -248,6 +261,10 @@ int ens_build(swe_ensemble* E, swe_mesh* const* M) {
                 const float gm2 = (float)(m->cfg.g * m->hm.m[c] * m->hm.m[c]);
                 std::memcpy(&w, &gm2, sizeof w);
             }
+            // static activity: an inflow or fixed-stage edge
+            for (int j = 0; j < 3; ++j)
+                if (code[j] < 0 && (kinds[-1 - code[j]] == kBcInflow || kinds[-1 - code[j]] == kBcStage))
+                    w |= kStaticBit;
             topo[b + c] = make_int4(code[0], code[1], code[2], w);
             perm[b + c] = m->hm.perm[c];
         }
@@ -294,6 +311,38 @@ int ens_build(swe_ensemble* E, swe_mesh* const* M) {
     if (e != cudaSuccess) return efail(e, "swe_ensemble_create: occupancy");
     E->grid = (unsigned)std::min<long long>((long long)(E->n_total / E->block), wave);
     E->cfl_host.assign(nm, -1.0);
+    return SWE_OK;
+}
+
+// Activity bytes of the ensemble's current state (allocated once).
+template <typename T>
+int ens_init_activity(swe_ensemble* E) {
+    cudaError_t e = cudaSuccess;
+    if (!E->act[0]) {
+        const int64_t len = (E->n_total + 31) / 32 * 32 + 32;
+        for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+            e = cudaMalloc((void**)&E->act[k], len);
+            if (e == cudaSuccess) e = cudaMemsetAsync(E->act[k], 0, len, E->stream);
+        }
+        if (e != cudaSuccess) {
+            for (auto& p : E->act) {
+                if (p) cudaFree(p);
+                p = nullptr;
+            }
+            set_error("swe_ensemble: no device memory for the activity bytes");
+            return SWE_ENOMEM;
+        }
+        E->act_len = len;
+        E->device_bytes += 3 * len;
+    }
+    const int p3 = (int)(E->nstep % 3);
+    e = cudaMemsetAsync(E->act[p3], 0, E->act_len, E->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(E->act[(p3 + 1) % 3], 0, E->act_len, E->stream);
+    if (e == cudaSuccess)
+        e = Launch<T>::act_init((const V4<T>*)E->state[E->nstep % 2], E->topo, E->n_total, (T)E->h_dry, E->act[p3],
+                                E->stream);
+    if (e != cudaSuccess) return efail(e, "swe_ensemble: activity bytes");
+    E->act_valid = true;
     return SWE_OK;
 }
 
@@ -354,6 +403,7 @@ int ens_get_state(swe_ensemble* E, int k, void* h, void* hu, void* hv, int where
 struct EnsShape {
     int block, min_blocks, stages, geo_early, chunk_log2;
     unsigned grid;
+    int activity;
 };
 
 template <typename T>
@@ -375,10 +425,20 @@ int ens_time_shapes(swe_ensemble* E, const std::vector<EnsShape>& cand, int tria
             a.g = (T)E->g;
             a.h_dry = (T)E->h_dry;
             const EnsShape& sh = cand[c];
-            e = Launch<T>::ensemble_step(a, sh.block, sh.min_blocks, sh.stages, sh.geo_early, sh.grid, st);  // warm-up
+            // activity trials read the current bytes and rewrite the next buffer with
+            // exactly the bytes the next real step writes there
+            const int p3 = (int)(E->nstep % 3);
+            a.act_in = sh.activity ? E->act[p3] : nullptr;
+            a.act_next = sh.activity ? E->act[(p3 + 1) % 3] : nullptr;
+            a.act_clear = sh.activity ? E->act[(p3 + 2) % 3] : nullptr;
+            auto launch = [&]() {
+                return sh.activity ? Launch<T>::ensemble_step_act(a, sh.block, sh.min_blocks, sh.geo_early, sh.grid, st)
+                                   : Launch<T>::ensemble_step(a, sh.block, sh.min_blocks, sh.stages, sh.geo_early,
+                                                              sh.grid, st);
+            };
+            e = launch();  // warm-up
             if (e == cudaSuccess) e = cudaEventRecord(ev[2 * (r * cand.size() + c)], st);
-            for (int s = 0; s < trial_steps && e == cudaSuccess; ++s)
-                e = Launch<T>::ensemble_step(a, sh.block, sh.min_blocks, sh.stages, sh.geo_early, sh.grid, st);
+            for (int s = 0; s < trial_steps && e == cudaSuccess; ++s) e = launch();
             if (e == cudaSuccess) e = cudaEventRecord(ev[2 * (r * cand.size() + c) + 1], st);
         }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -396,8 +456,13 @@ int ens_time_shapes(swe_ensemble* E, const std::vector<EnsShape>& cand, int tria
 
 template <typename T>
 int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
-    const EnsShape before{E->block, E->min_blocks, E->stages, E->geo_early, E->chunk_log2, E->grid};
+    const EnsShape before{E->block, E->min_blocks, E->stages, E->geo_early, E->chunk_log2, E->grid, E->activity};
     std::vector<EnsShape> cand{before};
+    const bool with_act = E->n_total < kActivityMaxCells;
+    if (with_act) {
+        const int rc = ens_init_activity<T>(E);
+        if (rc) return rc;
+    }
     int v[32][4];
     const int nv = std::min(Launch<T>::ensemble_variants(v, 32), 32);
     for (int k = 0; k < nv; ++k) {
@@ -406,11 +471,23 @@ int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
         if (e != cudaSuccess) return efail(e, "swe_ensemble_autotune: occupancy");
         const unsigned gr = (unsigned)std::max(1LL, std::min((long long)(E->n_total / v[k][0]), wave));
         for (int cl2 = 2; cl2 <= 6; ++cl2) {
-            const EnsShape sh{v[k][0], v[k][1], v[k][2], v[k][3], cl2, gr};
+            const EnsShape sh{v[k][0], v[k][1], v[k][2], v[k][3], cl2, gr, 0};
             if (!(sh.block == before.block && sh.min_blocks == before.min_blocks && sh.stages == before.stages &&
-                  sh.geo_early == before.geo_early && sh.chunk_log2 == before.chunk_log2 && sh.grid == before.grid))
+                  sh.geo_early == before.geo_early && sh.chunk_log2 == before.chunk_log2 && sh.grid == before.grid &&
+                  !before.activity))
                 cand.push_back(sh);
         }
+    }
+    int w[16][3];
+    const int nw = with_act ? std::min(Launch<T>::ensemble_act_variants(w, 16), 16) : 0;
+    for (int k = 0; k < nw; ++k) {
+        int per_sm = 0, sms = 0;
+        cudaError_t e = Launch<T>::ensemble_act_resident_blocks(w[k][0], w[k][1], w[k][2], &per_sm);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, E->device);
+        if (e != cudaSuccess) return efail(e, "swe_ensemble_autotune: occupancy");
+        const long long wave = (long long)std::max(per_sm, 1) * std::max(sms, 1);
+        const unsigned gr = (unsigned)std::max(1LL, std::min((long long)(E->n_total / w[k][0]), wave));
+        for (int cl2 = 2; cl2 <= 6; ++cl2) cand.push_back({w[k][0], w[k][1], 3, w[k][2], cl2, gr, 1});
     }
     void* scratch = nullptr;
     unsigned long long *small = nullptr, *act = nullptr;
@@ -434,12 +511,20 @@ int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
             if (ms[c] < ms[best]) best = c;
         long long wave = 0;
         const EnsShape b = cand[best];
-        e = ens_wave<T>(E, b.block, b.min_blocks, b.stages, b.geo_early, &wave);
+        if (b.activity) {
+            int per_sm = 0, sms = 0;
+            e = Launch<T>::ensemble_act_resident_blocks(b.block, b.min_blocks, b.geo_early, &per_sm);
+            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, E->device);
+            wave = (long long)std::max(per_sm, 1) * std::max(sms, 1);
+        } else {
+            e = ens_wave<T>(E, b.block, b.min_blocks, b.stages, b.geo_early, &wave);
+        }
         if (e != cudaSuccess) rc = efail(e, "swe_ensemble_autotune: occupancy");
         const long long tiles = (long long)(E->n_total / b.block);
         for (long long gsz : {wave / 2, 2 * wave}) {
             const unsigned gr = (unsigned)std::max(1LL, std::min(tiles, gsz));
-            if (!rc && gr != b.grid) cand2.push_back({b.block, b.min_blocks, b.stages, b.geo_early, b.chunk_log2, gr});
+            if (!rc && gr != b.grid)
+                cand2.push_back({b.block, b.min_blocks, b.stages, b.geo_early, b.chunk_log2, gr, b.activity});
         }
         if (!rc && !cand2.empty()) rc = ens_time_shapes<T>(E, cand2, trial_steps, scratch, small, act, ms2);
     }
@@ -453,6 +538,10 @@ int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
     E->min_blocks = pick.min_blocks;
     E->stages = pick.stages;
     E->geo_early = pick.geo_early;
+    E->activity = pick.activity;
+    // the bytes describe the current state (the trials rewrote the next buffer with
+    // what the next step writes there); without activity they would go stale
+    E->act_valid = pick.activity != 0 && E->act[0] != nullptr;
     E->chunk_log2 = pick.chunk_log2;
     E->grid = pick.grid;
     drop_graphs(E);
@@ -461,7 +550,7 @@ int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
         out->min_blocks = pick.min_blocks;
         out->stages = pick.stages;
         out->geometry_early = pick.geo_early;
-        out->activity = 0;
+        out->activity = pick.activity;
         out->edge_pass = 0;
         out->chunk = 1 << pick.chunk_log2;
         out->grid = pick.grid;
@@ -484,7 +573,7 @@ void swe_ensemble_destroy(swe_ensemble* E) {
     drop_graphs(E);
     void* bufs[] = {E->state[0], E->state[1], E->geoA, E->geoB, E->topo, E->gm2, E->perm, E->tile_member,
                     E->member_first_tile, E->cfl, E->small, E->n_active, E->kind, E->value,
-                    E->stage[0], E->stage[1], E->stage[2]};
+                    E->stage[0], E->stage[1], E->stage[2], E->act[0], E->act[1], E->act[2]};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (E->cap_stream) cudaStreamDestroy(E->cap_stream);
@@ -559,6 +648,10 @@ int swe_ensemble_step(swe_ensemble* E, int64_t nsteps, const double* cfl, double
         E->cfl_host = c;
     }
     const EnsPhysics ph{E->g, E->h_dry};
+    if (nsteps > 0 && E->activity && !E->act_valid) {
+        int rc = E->precision == SWE_FP32 ? ens_init_activity<float>(E) : ens_init_activity<double>(E);
+        if (rc) return rc;
+    }
     if (nsteps > 0) {
         // the whole call is one CUDA graph: nsteps step kernels over all members
         const auto key = std::make_pair((int)(E->nstep % 6), nsteps);
@@ -596,6 +689,51 @@ int swe_ensemble_step(swe_ensemble* E, int64_t nsteps, const double* cfl, double
         }
         return rc;
     }
+    return SWE_OK;
+}
+
+int swe_ensemble_set_shape(swe_ensemble* E, const swe_tune* shape) {
+    if (!E || !shape || (shape->activity != 0 && shape->activity != 1) || shape->edge_pass != 0 ||
+        shape->chunk < 1 || (shape->chunk & (shape->chunk - 1)) || shape->chunk > 4096 || shape->grid < 0) {
+        set_error("swe_ensemble_set_shape: bad arguments");
+        return SWE_EINVAL;
+    }
+    if (shape->activity && E->n_total >= kActivityMaxCells) {
+        set_error("swe_ensemble_set_shape: activity needs fewer than 2^29 cells");
+        return SWE_EINVAL;
+    }
+    EnsDeviceGuard dg(E->device);
+    int per_sm = 0, sms = 0;
+    cudaError_t e;
+    if (E->precision == SWE_FP32)
+        e = shape->activity ? Launch<float>::ensemble_act_resident_blocks(shape->block_size, shape->min_blocks,
+                                                                          shape->geometry_early, &per_sm)
+                            : Launch<float>::ensemble_resident_blocks(shape->block_size, shape->min_blocks,
+                                                                      shape->stages, shape->geometry_early, &per_sm);
+    else
+        e = shape->activity ? Launch<double>::ensemble_act_resident_blocks(shape->block_size, shape->min_blocks,
+                                                                           shape->geometry_early, &per_sm)
+                            : Launch<double>::ensemble_resident_blocks(shape->block_size, shape->min_blocks,
+                                                                       shape->stages, shape->geometry_early, &per_sm);
+    if (e == cudaErrorInvalidValue) {
+        set_error("swe_ensemble_set_shape: no compiled ensemble kernel of this shape");
+        return SWE_EINVAL;
+    }
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, E->device);
+    if (e != cudaSuccess) return efail(e, "swe_ensemble_set_shape: occupancy");
+    const long long tiles = (long long)(E->n_total / shape->block_size);
+    const long long wave = (long long)std::max(per_sm, 1) * std::max(sms, 1);
+    long long cl2 = 0;
+    while ((1LL << cl2) < shape->chunk) ++cl2;
+    E->block = shape->block_size;
+    E->min_blocks = shape->min_blocks;
+    E->stages = shape->activity ? 3 : shape->stages;
+    E->geo_early = shape->geometry_early;
+    E->chunk_log2 = (int)cl2;
+    E->grid = (unsigned)std::max(1LL, std::min(tiles, shape->grid > 0 ? (long long)shape->grid : wave));
+    if (E->activity != shape->activity) E->act_valid = false;
+    E->activity = shape->activity;
+    drop_graphs(E);
     return SWE_OK;
 }
 

@@ -107,6 +107,10 @@ struct EnsArgs {
     unsigned long long* n_active;      // all members (diagnostic)
     long long n_total;                 // cells of the padded layout (a multiple of kEnsPad)
     int chunk_log2;                    // tiles per round-robin chunk = 2^chunk_log2
+    // activity bytes over the concatenated layout (ensemble_step_kernel_act)
+    const unsigned char* act_in;
+    unsigned char* act_next;
+    unsigned char* act_clear;
     int slot_read, slot_write, slot_reset;
     int hll;
     T g, h_dry;
@@ -211,6 +215,32 @@ template <>
 __device__ __forceinline__ float inf_of<float>() { return __int_as_float(0x7F800000); }
 template <>
 __device__ __forceinline__ double inf_of<double>() { return __longlong_as_double((long long)kInfBits); }
+
+// ---- the step size, formed once per warp ------------------------------------------
+// dt = cfl * (min of the previous state) in double, and its rounding to the
+// state precision, made by lane 0 and broadcast (all 32 lanes must call):
+// FP32 kernels then run no FP64 instruction per thread for it.  dt is
+// non-negative or +inf, so "has a step" is an integer compare of its bits.
+template <typename T>
+struct WarpDt {
+    double d;
+    T t;
+    bool have;
+};
+template <typename T>
+__device__ __forceinline__ WarpDt<T> warp_step_dt(double cfl, const double* dt_read, const double* dt_fixed) {
+    double v = 0.0;
+    T vt = T(0);
+    if ((threadIdx.x & 31) == 0) {
+        v = dt_fixed ? *dt_fixed : cfl * (*dt_read);
+        vt = T(v);
+    }
+    WarpDt<T> r;
+    r.d = __shfl_sync(0xffffffffu, v, 0);
+    r.t = __shfl_sync(0xffffffffu, vt, 0);
+    r.have = (unsigned long long)__double_as_longlong(r.d) < kInfBits;
+    return r;
+}
 
 // ---- block min of a non-negative candidate, published with one atomicMin ----------
 // The minimum is taken in the candidate's own precision and widened to double
@@ -516,8 +546,9 @@ __device__ __forceinline__ T update_cell(const Args& a, long long i, const V4<T>
 // through cp.async into its own shared-memory slots.
 template <typename T, int BLOCK, int MINB, int STAGES, bool GEO_EARLY, bool EDGES = false>
 __global__ void __launch_bounds__(BLOCK, MINB) step_kernel(const StepArgs<T> a) {
-    const double dt_d = a.dt_fixed ? *a.dt_fixed : a.cfl * (*a.dt_read);
-    const bool have_dt = dt_d < __longlong_as_double((long long)kInfBits);
+    const WarpDt<T> wdt = warp_step_dt<T>(a.cfl, a.dt_read, a.dt_fixed);
+    const double dt_d = wdt.d;
+    const bool have_dt = wdt.have;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         *a.dt_reset = kInfBits;
         if (have_dt) *a.t += dt_d;
@@ -531,7 +562,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_kernel(const StepArgs<T> a) 
     if (!have_dt) {
         for (; i < a.n; i += stride) a.s_out[i] = a.s_in[i];
     } else if constexpr (STAGES <= 1) {
-        const T dt = T(dt_d);
+        const T dt = wdt.t;
         for (; i < a.n; i += stride) {
             const V4<T> own = a.s_in[i];
             const int4 tp = a.topo[i];
@@ -540,7 +571,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_kernel(const StepArgs<T> a) 
     } else {
         __shared__ V4<T> st_own[STAGES][BLOCK];
         __shared__ int4 st_topo[STAGES][BLOCK];
-        const T dt = T(dt_d);
+        const T dt = wdt.t;
         const int tid = threadIdx.x;
 #pragma unroll
         for (int s = 0; s < STAGES - 1; ++s) {
@@ -622,8 +653,9 @@ __global__ void __launch_bounds__(BLOCK) edge_flux_kernel(const StepArgs<T> a) {
 template <typename T, int BLOCK, int MINB, bool GEO_EARLY>
 __global__ void __launch_bounds__(BLOCK, MINB) step_kernel_act(const StepArgs<T> a) {
     static_assert(BLOCK % 32 == 0, "warps of whole cells");
-    const double dt_d = a.dt_fixed ? *a.dt_fixed : a.cfl * (*a.dt_read);
-    const bool have_dt = dt_d < __longlong_as_double((long long)kInfBits);
+    const WarpDt<T> wdt = warp_step_dt<T>(a.cfl, a.dt_read, a.dt_fixed);
+    const double dt_d = wdt.d;
+    const bool have_dt = wdt.have;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         *a.dt_reset = kInfBits;
         if (have_dt) *a.t += dt_d;
@@ -649,7 +681,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_kernel_act(const StepArgs<T>
         __shared__ V4<T> st_own[3][BLOCK];
         __shared__ int4 st_topo[2][BLOCK];
         __shared__ unsigned st_act[3][BLOCK / 4];  // 32 activity bytes per warp per stage
-        const T dt = T(dt_d);
+        const T dt = wdt.t;
         // warp w of the block owns st_act[.][8 w .. 8 w + 7]; lanes 0..7 copy 4 bytes each
         auto act_copy = [&](int slot, unsigned c) {
             const unsigned base = c - lane;
@@ -807,9 +839,11 @@ __global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel(const EnsArg
             cand = inf_of<T>();
             member = mk;
             sm = a.small + 8 * (long long)mk;
-            const double dt_d = a.cfl[mk] * __longlong_as_double((long long)sm[a.slot_read]);
-            have_dt = dt_d < __longlong_as_double((long long)kInfBits);
-            dt = T(dt_d);
+            // mk is uniform across the block, so every lane is here
+            const WarpDt<T> wdt = warp_step_dt<T>(a.cfl[mk], (const double*)(sm + a.slot_read), nullptr);
+            const double dt_d = wdt.d;
+            have_dt = wdt.have;
+            dt = wdt.t;
             if (cell0 == a.member_first_tile[mk] * kEnsPad && tid == 0) {
                 sm[a.slot_reset] = kInfBits;
                 if (have_dt) *(double*)(sm + 3) += dt_d;
@@ -843,6 +877,131 @@ __global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel(const EnsArg
             a.s_out[i] = own;
     }
     if constexpr (STAGES > 1) cp_async_wait<0>();
+    if (member >= 0) warp_min_publish<T>(cand, sm + a.slot_write);
+    active = __reduce_add_sync(0xffffffffu, active);
+    if ((tid & 31) == 0 && active) atomicAdd(a.n_active, (unsigned long long)active);
+}
+
+// ---- batched ensemble step with activity bytes ----------------------------------------
+// The activity mode of step_kernel_act over the concatenated members: the same
+// bytes, marks and per-thread cp.async pipeline, with the thread's cells taken
+// tile by tile in the ensemble's round-robin chunk order.  Tiles are whole
+// (members are padded), so a tile is valid for every lane or for none.  Cells
+// are indexed with 32 bits (the host allows this kernel below 2^29 cells).
+template <typename T, int BLOCK, int MINB, bool GEO_EARLY>
+__global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel_act(const EnsArgs<T> a) {
+    static_assert(kEnsPad % BLOCK == 0, "a tile must not straddle two members");
+    constexpr unsigned kNone = 0xFFFFFFFFu;
+    const unsigned G = gridDim.x, b = blockIdx.x;
+    const int cl2 = a.chunk_log2;
+    const unsigned n_tiles = (unsigned)(a.n_total / BLOCK);
+    const unsigned n_chunks = (n_tiles + (1u << cl2) - 1) >> cl2;
+    const unsigned my_chunks = b < n_chunks ? (n_chunks - 1 - b) / G + 1 : 0;
+    const unsigned k_end = my_chunks << cl2;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // this thread's cell in the block's k-th tile (kNone past the end)
+    auto cell_of = [&](unsigned k) -> unsigned {
+        if (k >= k_end) return kNone;
+        const unsigned t = ((b + (k >> cl2) * G) << cl2) + (k & ((1u << cl2) - 1));
+        return t < n_tiles ? t * BLOCK + tid : kNone;
+    };
+    __shared__ V4<T> st_own[3][BLOCK];
+    __shared__ int4 st_topo[2][BLOCK];
+    __shared__ unsigned st_act[3][BLOCK / 4];
+    auto act_copy = [&](int slot, unsigned c) {
+        if (lane < 8 && c != kNone)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(
+                             (unsigned)__cvta_generic_to_shared(&st_act[slot][warp * 8 + lane])),
+                         "l"(a.act_in + (c - lane) + 4 * lane)
+                         : "memory");
+    };
+    auto act_byte = [&](int slot) -> unsigned {
+        return ((const unsigned char*)&st_act[slot][warp * 8])[lane];
+    };
+    int member = -1;
+    unsigned long long* sm = nullptr;
+    bool have_dt = false;
+    T dt = T(0);
+    T cand = inf_of<T>();
+    unsigned active = 0u;
+    {
+        const unsigned c0 = cell_of(0), c1 = cell_of(1), c2 = cell_of(2);
+        act_copy(0, c0);
+        act_copy(1, c1);
+        act_copy(2, c2);
+        if (c0 != kNone) cp_async_record<sizeof(V4<T>)>(&st_own[0][tid], &a.s_in[c0]);
+        if (c1 != kNone) cp_async_record<sizeof(V4<T>)>(&st_own[1][tid], &a.s_in[c1]);
+        cp_async_commit();
+        cp_async_wait<0>();
+        __syncwarp();
+    }
+    unsigned f_cur = act_byte(0);
+    {
+        const unsigned c0 = cell_of(0);
+        if (f_cur && c0 != kNone) cp_async_record<16>(&st_topo[0][tid], &a.topo[c0]);
+    }
+    cp_async_commit();                                           // T_{-1}
+    cp_async_commit();                                           // H_{-1} (empty)
+    int k3 = 0, k2 = 0;
+    for (unsigned k = 0; k < k_end; ++k) {
+        const unsigned c = cell_of(k);
+        if (c == kNone) break;                                   // ragged last chunk (block-uniform)
+        const int mk = a.tile_member[(c - tid) / kEnsPad];       // uniform across the block
+        if (mk != member) {
+            if (member >= 0) warp_min_publish<T>(cand, sm + a.slot_write);
+            cand = inf_of<T>();
+            member = mk;
+            sm = a.small + 8 * (long long)mk;
+            const WarpDt<T> wdt = warp_step_dt<T>(a.cfl[mk], (const double*)(sm + a.slot_read), nullptr);
+            have_dt = wdt.have;
+            dt = wdt.t;
+            if ((long long)(c - tid) == a.member_first_tile[mk] * kEnsPad && tid == 0) {
+                sm[a.slot_reset] = kInfBits;
+                if (have_dt) *(double*)(sm + 3) += wdt.d;
+                else atomicOr((unsigned*)(sm + 4), kStatusDry);
+            }
+        }
+        const int k3n = k3 == 2 ? 0 : k3 + 1, k3nn = k3n == 2 ? 0 : k3n + 1;
+        cp_async_wait<2>();
+        __syncwarp();
+        const unsigned f_next = act_byte(k3n);
+        const unsigned c1 = cell_of(k + 1), c2 = cell_of(k + 2), c3 = cell_of(k + 3);
+        if (f_next && c1 != kNone) cp_async_record<16>(&st_topo[k2 ^ 1][tid], &a.topo[c1]);
+        cp_async_commit();                                       // T_k
+        __syncwarp();
+        act_copy(k3, c3);
+        if (c2 != kNone) cp_async_record<sizeof(V4<T>)>(&st_own[k3nn][tid], &a.s_in[c2]);
+        cp_async_commit();                                       // H_k
+        cp_async_wait<3>();                                      // T_{k-1}: the topology of c_k
+        const V4<T> own = st_own[k3][tid];
+        if (!have_dt) {
+            a.s_out[c] = own;
+            a.act_next[c] = (unsigned char)f_cur;
+        } else if (!f_cur) {
+            V4<T> out;
+            out.x = own.x; out.y = T(0); out.z = T(0); out.w = own.w;
+            a.s_out[c] = out;
+        } else {
+            const T r = update_cell<T, GEO_EARLY>(a, c, own, st_topo[k2][tid], dt, active, sm + 5,
+                                                  (unsigned*)(sm + 4));
+            cand = tmin(cand, r);
+            const bool wet = r < inf_of<T>();
+            const volatile int* tv = (const volatile int*)&st_topo[k2][tid];
+            if (wet || (tv[3] & kStaticBit)) a.act_next[c] = 1;
+            if (wet) {
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const int code = tv[j];
+                    if (code >= 0) a.act_next[code & kNbrMask] = 1;
+                }
+            }
+        }
+        a.act_clear[c] = 0;
+        f_cur = f_next;
+        k3 = k3n;
+        k2 ^= 1;
+    }
+    cp_async_wait<0>();
     if (member >= 0) warp_min_publish<T>(cand, sm + a.slot_write);
     active = __reduce_add_sync(0xffffffffu, active);
     if ((tid & 31) == 0 && active) atomicAdd(a.n_active, (unsigned long long)active);
@@ -931,6 +1090,11 @@ struct Launch {
                                      unsigned grid, cudaStream_t st);
     static cudaError_t ensemble_resident_blocks(int block, int min_blocks, int stages, int geo_early, int* per_sm);
     static int ensemble_variants(int (*out)[4], int max);
+    // activity kernel of the ensemble: compiled (block, min_blocks, geo_early) shapes
+    static cudaError_t ensemble_step_act(const EnsArgs<T>& a, int block, int min_blocks, int geo_early,
+                                         unsigned grid, cudaStream_t st);
+    static cudaError_t ensemble_act_resident_blocks(int block, int min_blocks, int geo_early, int* per_sm);
+    static int ensemble_act_variants(int (*out)[3], int max);
     static void ensemble_default(int* block, int* min_blocks, int* stages, int* geo_early);
     static int default_min_blocks(int block);
     static cudaError_t dt(const V4<T>* s, const V4<T>* geoB, long long n, T g, T h_dry,

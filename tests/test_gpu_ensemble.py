@@ -94,3 +94,34 @@ def test_ensemble_device_output_and_errors():
     with pytest.raises(capi.SWEError) as e:
         capi.Ensemble([meshes[0], f32])
     assert e.value.code == capi.SWE_EINVAL
+
+
+@pytest.mark.parametrize("precision", [capi.SWE_FP64, capi.SWE_FP32])
+def test_ensemble_launch_shapes_are_bitwise_neutral(precision):
+    # every batched kernel shape -- tile size, staging, geometry placement,
+    # activity bytes, chunk and grid -- gives each member the plain solver's
+    # updates bit for bit, also when the shape changes between calls
+    mis = _members(6, seed=13)
+    meshes = [_mesh(mi, precision) for mi in mis]
+    ens = capi.Ensemble(meshes)
+    f32 = precision == capi.SWE_FP32
+    shapes = [dict(block_size=128, min_blocks=8 if f32 else 1, activity=1, chunk=4),
+              dict(block_size=256, min_blocks=4 if f32 else 1, activity=1, chunk=16, grid=37),
+              dict(block_size=256, min_blocks=4 if f32 else 1, stages=3 if f32 else 1, chunk=8),
+              dict(block_size=128, min_blocks=8 if f32 else 1, geometry_early=1 if f32 else 0, activity=1,
+                   chunk=64, grid=5)]
+    steps = 0
+    for k, sh in enumerate(shapes):
+        ens.set_shape(**sh)
+        ens.step(37 + k)
+        steps += 37 + k
+    t_ens = ens.step(0)
+    for k, m in enumerate(meshes):
+        assert m.step(steps) == t_ens[k]
+        assert all(np.array_equal(a, b) for a, b in zip(ens.get_state(k), m.get_state())), f"member {k}"
+    assert ens.info(0)["n_active"] == sum(m.info()["n_active"] for m in meshes)
+    with pytest.raises(capi.SWEError):
+        ens.set_shape(block_size=512, min_blocks=2, activity=1)
+    ens.close()
+    for m in meshes:
+        m.close()

@@ -355,6 +355,10 @@ def test_full_size_dry_canal_1m_fp64_against_oracle():
     (f32, _, _), t32, _ = _gpu_run(mi, 2000, precision=capi.SWE_FP32)
     assert t32 == pytest.approx(t, rel=1e-4)
     assert rel_err(f32, gh) <= FP32_TOL
+    # the edge pass (each interior flux once) at full size: bit for bit
+    (eh, ehu, ehv), te, _ = _gpu_run(mi, 2000, edge_pass=1)
+    assert te == t
+    assert all(np.array_equal(x, y) for x, y in ((eh, gh), (ehu, ghu), (ehv, ghv)))
 
 
 def test_full_size_wet_river_1m_fp64_against_oracle():
@@ -390,6 +394,12 @@ def test_full_size_river_13m_first_step_and_fp32_against_fp64():
     assert t32 == pytest.approx(t64, rel=1e-4)
     for a, b in zip(s32, s64):
         assert rel_err(a, b) <= FP32_TOL
+    # the activity kernel (the shape the autotuner picks for this mesh) at full
+    # size: bit for bit the neighbour-test kernel, with the same active count
+    (sa, ta, ia) = _gpu_run(mi, 1000, precision=capi.SWE_FP32, activity=1, block_size=128, min_blocks=8,
+                            geometry_early=1)
+    assert ta == t32 and ia["n_active"] == i32["n_active"]
+    assert all(np.array_equal(x, y) for x, y in zip(sa, s32))
 
 
 @pytest.mark.parametrize("init", ["inclined_plane", "dam_failure"])
