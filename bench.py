@@ -366,7 +366,7 @@ def run_gpu(args, name):
                 "d2h_bytes_per_step": 3 * n * np.dtype(npdt).itemsize / args.steps,
                 "note": "one job: swe_set_state from pinned host arrays, swe_step(steps), swe_get_state to "
                         "pinned host arrays; bytes averaged per step"},
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * (2 if shape.get("edge_pass") else 1),
         "clocks": clk,
     }
     if wl["precision"] == "f64":
@@ -541,6 +541,8 @@ def run_gpu_adjoint(args, name):
     warm = max(args.warmup, 3)
     m.adjoint(warm, gauges, target, checkpoint_every=50, out=(gm, gz))
     m.set_state(mi.h, mi.hu, mi.hv)
+    # launch shape of the forward and recomputed steps, chosen by the autotuner
+    shape = m.autotune(4)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local)
@@ -571,13 +573,16 @@ def run_gpu_adjoint(args, name):
         "n_gpus": ws, "steps": args.steps, "warmup": warm, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOADS[name]["desc"], "cells": n, "parallelism": f"replicas{ws}",
-                   "checkpoint_every": 50, "gauges": 64},
+                   "checkpoint_every": 50, "gauges": 64, "autotune": shape},
         "loss": loss,
         "grad_norms": {"manning": float(gm.norm()), "bathy": float(gz.norm())},
         "forward_only": {"value": n * args.steps / (ms_fwd * 1e-3), "ms_per_step": ms_fwd / args.steps},
         "adjoint_over_forward": ms / ms_fwd,
-        "roofline": {"bound": "alu", "note": "FP64 arithmetic on forward-mode duals; see DESIGN.md"},
-        "gpu_launches": args.steps * 4,
+        "roofline": {"bound": "alu", "note": "FP64 arithmetic on forward-mode duals: the adjoint kernels and "
+                                             "the forward steps are bound by the FP64 pipe"},
+        # per step: the forward step and its recomputation (two kernels each with the
+        # edge pass), then the two adjoint kernels
+        "gpu_launches": args.steps * (2 * (2 if shape.get("edge_pass") else 1) + 2),
         "clocks": clk,
     }
     m.close()

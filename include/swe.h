@@ -101,10 +101,12 @@ typedef struct swe_config {
                          or it has an inflow/stage edge, and an inactive cell takes its update
                          (h, 0, 0) without reading its topology or its neighbours; each step
                          marks the cells that the next one must treat as active.  0 (default):
-                         every cell tests its neighbours.  Compiled with 1: FP32 (128, 8),
-                         (256, 4), (512, 2) with geometry_early 0, (128, 8), (256, 4) with 1;
-                         FP64 (128|256, 1) with 0, (128, 1) with 1 (stages ignored).  Results
-                         do not depend on it */
+                         every cell tests its neighbours.  With activity, stages is the
+                         prefetch distance of the streamed state plus one (default 3).
+                         Compiled (block_size, min_blocks, geometry_early, stages) with 1:
+                         FP32 (128, 8, 0, 3|4), (256, 4, 0, 3), (512, 2, 0, 3),
+                         (128, 8, 1, 3|4|5), (256, 4, 1, 3|4); FP64 (128, 1, 0, 3|4),
+                         (256, 1, 0, 3), (128, 1, 1, 3).  Results do not depend on it */
     int edge_pass;    /* 1: each step first evaluates every interior edge's flux once (one thread
                          per edge, from its left cell), then updates the cells from those
                          fluxes; 0 (default): each cell evaluates its own three edges, so every

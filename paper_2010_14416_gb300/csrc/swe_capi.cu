@@ -563,7 +563,7 @@ int swe_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* tris, i
     if (c.min_blocks == 0)
         c.min_blocks = c.precision == SWE_FP32 ? Launch<float>::default_min_blocks(c.block_size)
                                                : Launch<double>::default_min_blocks(c.block_size);
-    if (c.stages == 0) c.stages = c.precision == SWE_FP32 ? 3 : 1;
+    if (c.stages == 0) c.stages = (c.precision == SWE_FP32 || c.activity) ? 3 : 1;
     if (c.graph_steps == 0) c.graph_steps = kDefaultGraphSteps;
     if (c.graph_steps > 0) c.graph_steps = std::max(6, (c.graph_steps / 6) * 6);
     if (c.activity && n_tris >= kActivityMaxCells) {

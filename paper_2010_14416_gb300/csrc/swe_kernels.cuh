@@ -648,11 +648,14 @@ __global__ void __launch_bounds__(BLOCK) edge_flux_kernel(const StepArgs<T> a) {
 //
 // Per-thread cp.async pipeline over the thread's cells c_k = i0 + k stride:
 // iteration k issues the topology of c_{k+1} (only if its byte is set), then
-// the activity bytes of c_{k+3} (8 lanes copy the warp's 32 bytes) and the
-// state record of c_{k+2}; it then processes c_k.
-template <typename T, int BLOCK, int MINB, bool GEO_EARLY>
+// the activity bytes of c_{k+PF+1} (8 lanes copy the warp's 32 bytes) and the
+// state record of c_{k+PF}; it then processes c_k.  PF (the prefetch
+// distance of the streamed state, >= 2) is a compiled shape parameter.
+template <typename T, int BLOCK, int MINB, bool GEO_EARLY, int PF>
 __global__ void __launch_bounds__(BLOCK, MINB) step_kernel_act(const StepArgs<T> a) {
     static_assert(BLOCK % 32 == 0, "warps of whole cells");
+    static_assert(PF >= 2, "the wait counts below assume a prefetch distance of at least two cells");
+    constexpr int NS = PF + 1;  // state and activity slots
     const WarpDt<T> wdt = warp_step_dt<T>(a.cfl, a.dt_read, a.dt_fixed);
     const double dt_d = wdt.d;
     const bool have_dt = wdt.have;
@@ -665,7 +668,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_kernel_act(const StepArgs<T>
     T cand = inf_of<T>();
     unsigned active = 0u;
     // 32-bit cell indices: the host allows this kernel only for n < 2^29, so
-    // c + 3 stride < 2^32 with stride <= n + BLOCK
+    // c + (PF + 1) stride < 2^32 with stride <= n + BLOCK and PF <= 5
     const unsigned stride = gridDim.x * BLOCK;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned i0 = blockIdx.x * BLOCK + tid;
@@ -678,9 +681,10 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_kernel_act(const StepArgs<T>
             a.act_clear[c] = 0;
         }
     } else {
-        __shared__ V4<T> st_own[3][BLOCK];
+        static_assert(PF <= 5, "32-bit indices");
+        __shared__ V4<T> st_own[NS][BLOCK];
         __shared__ int4 st_topo[2][BLOCK];
-        __shared__ unsigned st_act[3][BLOCK / 4];  // 32 activity bytes per warp per stage
+        __shared__ unsigned st_act[NS][BLOCK / 4];  // 32 activity bytes per warp per stage
         const T dt = wdt.t;
         // warp w of the block owns st_act[.][8 w .. 8 w + 7]; lanes 0..7 copy 4 bytes each
         auto act_copy = [&](int slot, unsigned c) {
@@ -694,12 +698,12 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_kernel_act(const StepArgs<T>
         auto act_byte = [&](int slot) -> unsigned {
             return ((const unsigned char*)&st_act[slot][warp * 8])[lane];
         };
-        // prologue: activity of c_0, c_1, c_2 and states of c_0, c_1; then topology of c_0
-        act_copy(0, i0);
-        act_copy(1, i0 + stride);
-        act_copy(2, i0 + 2 * stride);
-        if (i0 < n) cp_async_record<sizeof(V4<T>)>(&st_own[0][tid], &a.s_in[i0]);
-        if (i0 + stride < n) cp_async_record<sizeof(V4<T>)>(&st_own[1][tid], &a.s_in[i0 + stride]);
+        // prologue: activity of c_0 .. c_PF and states of c_0 .. c_{PF-1}; then topology of c_0
+#pragma unroll
+        for (int q = 0; q <= PF; ++q) act_copy(q, i0 + q * stride);
+#pragma unroll
+        for (int q = 0; q < PF; ++q)
+            if (i0 + q * stride < n) cp_async_record<sizeof(V4<T>)>(&st_own[q][tid], &a.s_in[i0 + q * stride]);
         cp_async_commit();
         cp_async_wait<0>();
         __syncwarp();
@@ -707,23 +711,25 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_kernel_act(const StepArgs<T>
         if (f_cur && i0 < n) cp_async_record<16>(&st_topo[0][tid], &a.topo[i0]);
         cp_async_commit();                                       // T_{-1}
         cp_async_commit();                                       // H_{-1} (empty: its copies were in the first group)
-        int k3 = 0, k2 = 0;  // k mod 3, k mod 2
+        int ks = 0, k2 = 0;  // k mod NS, k mod 2
         for (unsigned c = i0; c - lane < n; c += stride) {
-            const int k3n = k3 == 2 ? 0 : k3 + 1, k3nn = k3n == 2 ? 0 : k3n + 1;
-            // groups so far: ..., T_{k-1}, H_{k-1}; H_{k-2} (activity of c_{k+1}, state of c_k) must be complete
+            const int ks1 = ks + 1 == NS ? 0 : ks + 1;          // slot of c_{k+1}
+            const int ksp = ks == 0 ? NS - 1 : ks - 1;          // slot of c_{k+PF} (c_{k-1}'s, consumed)
+            // groups so far: ..., T_{k-1}, H_{k-1}; H_{k-PF} and older (activity of
+            // c_{k+1}, state of c_k) must be complete, which H_{k-2} implies
             cp_async_wait<2>();
             __syncwarp();
-            const unsigned f_next = act_byte(k3n);
-            const unsigned c1 = c + stride, c2 = c + 2 * stride, c3 = c + 3 * stride;
+            const unsigned f_next = act_byte(ks1);
+            const unsigned c1 = c + stride, cp = c + PF * stride, cp1 = c + (PF + 1) * stride;
             if (f_next && c1 < n) cp_async_record<16>(&st_topo[k2 ^ 1][tid], &a.topo[c1]);
             cp_async_commit();                                   // T_k
-            __syncwarp();                                        // every lane has read slot k3 before it refills
-            act_copy(k3, c3);
-            if (c2 < n) cp_async_record<sizeof(V4<T>)>(&st_own[k3nn][tid], &a.s_in[c2]);
+            __syncwarp();                                        // every lane has read slot ks before it refills
+            act_copy(ks, cp1);
+            if (cp < n) cp_async_record<sizeof(V4<T>)>(&st_own[ksp][tid], &a.s_in[cp]);
             cp_async_commit();                                   // H_k
             cp_async_wait<3>();                                  // T_{k-1}: the topology of c_k
             if (c < n) {
-                const V4<T> own = st_own[k3][tid];
+                const V4<T> own = st_own[ks][tid];
                 if (!f_cur) {
                     V4<T> out;
                     out.x = own.x; out.y = T(0); out.z = T(0); out.w = own.w;
@@ -748,7 +754,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_kernel_act(const StepArgs<T>
                 a.act_clear[c] = 0;
             }
             f_cur = f_next;
-            k3 = k3n;
+            ks = ks1;
             k2 ^= 1;
         }
         cp_async_wait<0>();
@@ -1079,8 +1085,8 @@ struct Launch {
                                        int edges, int* per_sm);
     // compiled (block, min_blocks, stages, geo_early) shapes of the cell pass of the edge-pass step
     static int edge_variants(int (*out)[4], int max);
-    // compiled (block, min_blocks, geo_early) shapes of the activity kernel
-    static int act_variants(int (*out)[3], int max);
+    // compiled (block, min_blocks, geo_early, stages = prefetch distance + 1) shapes of the activity kernel
+    static int act_variants(int (*out)[4], int max);
     static cudaError_t act_init(const V4<T>* s, const int4* topo, long long n, T h_dry, unsigned char* act,
                                 cudaStream_t st);
     // compiled (block, min_blocks, stages, geo_early) shapes of the step kernel; returns their number

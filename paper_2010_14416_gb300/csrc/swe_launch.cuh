@@ -31,11 +31,13 @@ static inline unsigned grid_for(long long n, int block) {
 #define SWE_EDGE_VARIANTS_F64(X) X(128, 1, 1, 0) X(256, 1, 1, 0)
 constexpr int kEdgeBlock = 256;
 
-// (block, min blocks per SM, geometry early) shapes of the activity kernel
-// (its pipeline depth is fixed); shared memory: 3 state + 2 topology records
-// and 3 activity bytes per thread.
-#define SWE_ACT_VARIANTS_F32(X) X(128, 8, 0) X(256, 4, 0) X(512, 2, 0) X(128, 8, 1) X(256, 4, 1)
-#define SWE_ACT_VARIANTS_F64(X) X(128, 1, 0) X(256, 1, 0) X(128, 1, 1)
+// (block, min blocks per SM, geometry early, stages) shapes of the activity
+// kernel; stages = the state's prefetch distance + 1.  Shared memory per
+// thread: `stages` state records and activity bytes, 2 topology records.
+#define SWE_ACT_VARIANTS_F32(X)                                                                     \
+    X(128, 8, 0, 3) X(256, 4, 0, 3) X(512, 2, 0, 3) X(128, 8, 1, 3) X(256, 4, 1, 3) X(128, 8, 1, 4) \
+    X(128, 8, 1, 5) X(256, 4, 1, 4) X(128, 8, 0, 4)
+#define SWE_ACT_VARIANTS_F64(X) X(128, 1, 0, 3) X(256, 1, 0, 3) X(128, 1, 1, 3) X(128, 1, 0, 4)
 
 template <typename T>
 int Launch<T>::default_min_blocks(int block) {
@@ -49,9 +51,9 @@ cudaError_t Launch<T>::step(const StepArgs<T>& a, int block, int min_blocks, int
     const unsigned grid = a.grid;
     if (grid == 0) return cudaErrorInvalidValue;
     if (a.act_in) {
-#define SWE_LAUNCH_ACT(B, M, G) \
-    if (block == B && min_blocks == M && geo_early == G) {                        \
-        step_kernel_act<T, B, M, G != 0><<<grid, B, 0, st>>>(a);                 \
+#define SWE_LAUNCH_ACT(B, M, G, S) \
+    if (block == B && min_blocks == M && geo_early == G && stages == S) {         \
+        step_kernel_act<T, B, M, G != 0, S - 1><<<grid, B, 0, st>>>(a);          \
         return cudaGetLastError();                                                \
     }
         if constexpr (sizeof(T) == 4) {
@@ -113,9 +115,9 @@ cudaError_t Launch<T>::resident_blocks(int block, int min_blocks, int stages, in
         return cudaErrorInvalidValue;
     }
     if (activity) {
-#define SWE_OCC_ACT(B, M, G) \
-    if (block == B && min_blocks == M && geo_early == G)                          \
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, step_kernel_act<T, B, M, G != 0>, B, 0);
+#define SWE_OCC_ACT(B, M, G, S) \
+    if (block == B && min_blocks == M && geo_early == G && stages == S)           \
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, step_kernel_act<T, B, M, G != 0, S - 1>, B, 0);
         if constexpr (sizeof(T) == 4) {
             SWE_ACT_VARIANTS_F32(SWE_OCC_ACT)
         } else {
@@ -167,10 +169,10 @@ int Launch<T>::edge_variants(int (*out)[4], int max) {
 }
 
 template <typename T>
-int Launch<T>::act_variants(int (*out)[3], int max) {
+int Launch<T>::act_variants(int (*out)[4], int max) {
     int k = 0;
-#define SWE_LIST(B, M, G) \
-    if (k < max) { out[k][0] = B; out[k][1] = M; out[k][2] = G; } \
+#define SWE_LIST(B, M, G, S) \
+    if (k < max) { out[k][0] = B; out[k][1] = M; out[k][2] = G; out[k][3] = S; } \
     ++k;
     if constexpr (sizeof(T) == 4) {
         SWE_ACT_VARIANTS_F32(SWE_LIST)

@@ -86,10 +86,10 @@ int candidate_shapes(const swe_mesh* m, std::vector<Shape>& cand) {
         const int rc = add(v[k][0], v[k][1], v[k][2], v[k][3], 0, 1);
         if (rc) return rc;
     }
-    int w[64][3];
+    int w[64][4];
     const int nw = n < kActivityMaxCells ? std::min(Launch<T>::act_variants(w, 64), 64) : 0;
     for (int k = 0; k < nw; ++k) {
-        const int rc = add(w[k][0], w[k][1], 3, w[k][2], 1, 0);
+        const int rc = add(w[k][0], w[k][1], w[k][3], w[k][2], 1, 0);
         if (rc) return rc;
     }
     return SWE_OK;

@@ -38,10 +38,11 @@ F32_SHAPES = {s + (0,) for s in [
     (128, 1, 1, 0), (256, 1, 1, 0), (512, 1, 1, 0), (128, 8, 1, 0), (256, 4, 1, 0), (256, 5, 1, 0), (512, 2, 1, 0),
     (256, 4, 2, 0), (256, 4, 3, 0), (256, 4, 4, 0), (128, 8, 3, 0), (128, 8, 4, 0), (256, 4, 1, 1), (256, 4, 3, 1),
     (128, 8, 1, 1), (128, 8, 3, 1)]} | {
-    (128, 8, 3, 0, 1), (256, 4, 3, 0, 1), (512, 2, 3, 0, 1), (128, 8, 3, 1, 1), (256, 4, 3, 1, 1)}
+    (128, 8, 3, 0, 1), (256, 4, 3, 0, 1), (512, 2, 3, 0, 1), (128, 8, 3, 1, 1), (256, 4, 3, 1, 1),
+    (128, 8, 4, 1, 1), (128, 8, 5, 1, 1), (256, 4, 4, 1, 1), (128, 8, 4, 0, 1)}
 F64_SHAPES = {s + (0,) for s in [
     (128, 1, 1, 0), (256, 1, 1, 0), (512, 1, 1, 0), (128, 1, 2, 0), (256, 1, 2, 0), (128, 1, 1, 1), (256, 1, 1, 1)]} | {
-    (128, 1, 3, 0, 1), (256, 1, 3, 0, 1), (128, 1, 3, 1, 1)}
+    (128, 1, 3, 0, 1), (256, 1, 3, 0, 1), (128, 1, 3, 1, 1), (128, 1, 4, 0, 1)}
 # (block, min_blocks, stages, geometry_early) of the edge pass's cell kernel
 EDGE_CELL_PASS = {capi.SWE_FP32: {(256, 4, 1, 0), (128, 8, 1, 0)}, capi.SWE_FP64: {(128, 1, 1, 0), (256, 1, 1, 0)}}
 

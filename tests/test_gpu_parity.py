@@ -216,9 +216,10 @@ def test_activity_mode_is_bitwise_neutral(precision, maker):
     ref, tref, iref = _gpu_run(mi, 301, precision=precision)
     f32 = precision == capi.SWE_FP32
     shapes = [dict(), dict(block_size=128, min_blocks=8 if f32 else 1), dict(graph_steps=-1),
-              dict(geometry_early=1, block_size=128, min_blocks=8 if f32 else 1)]
+              dict(geometry_early=1, block_size=128, min_blocks=8 if f32 else 1),
+              dict(block_size=128, min_blocks=8 if f32 else 1, stages=4)]
     if f32:
-        shapes.append(dict(block_size=512, min_blocks=2))
+        shapes += [dict(block_size=512, min_blocks=2), dict(block_size=128, min_blocks=8, geometry_early=1, stages=5)]
     for kw in shapes:
         got, t, info = _gpu_run(mi, 301, precision=precision, activity=1, **kw)
         assert t == tref, kw
