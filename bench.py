@@ -249,7 +249,8 @@ def run_gpu(args, name):
     if dist:
         dist.barrier()
     mi = _make_input(name)
-    m = capi.Mesh(mi.nodes, mi.tris, mi.z, mi.manning, precision=prec, device=local)
+    fixed = _shape_kwargs(args.shape)
+    m = capi.Mesh(mi.nodes, mi.tris, mi.z, mi.manning, precision=prec, device=local, **fixed)
     for pairs, kind, value in mi.bcs:
         m.set_bc(pairs, kind, value)
     stream = torch.cuda.Stream(device=dev)
@@ -265,7 +266,12 @@ def run_gpu(args, name):
     m.step(args.warmup, 0.9, sync=True)
     # launch shape chosen by the library's autotuner on the warmed-up state
     # (the tuning call leaves the state untouched), then the graph is recaptured
-    shape = m.autotune(8)
+    if fixed:
+        shape = dict(block_size=fixed["block_size"], min_blocks=fixed["min_blocks"], stages=fixed["stages"],
+                     geometry_early=fixed["geometry_early"], activity=fixed["activity"],
+                     edge_pass=fixed["edge_pass"], grid=fixed["grid"], chunk=0, fixed=True)
+    else:
+        shape = m.autotune(8)
     m.step(96, 0.9, sync=True)
     n = mi.n_cells
 
@@ -294,13 +300,14 @@ def run_gpu(args, name):
     # ---- end to end through the C ABI with pinned host buffers ----
     hp = [torch.from_numpy(a.astype(npdt)).pin_memory() for a in (mi.h, mi.hu, mi.hv)]
     out = [torch.empty(n, dtype=tdt).pin_memory() for _ in range(3)]
-    m2 = capi.Mesh(mi.nodes, mi.tris, mi.z, mi.manning, precision=prec, device=local)
+    m2 = capi.Mesh(mi.nodes, mi.tris, mi.z, mi.manning, precision=prec, device=local, **fixed)
     for pairs, kind, value in mi.bcs:
         m2.set_bc(pairs, kind, value)
     m2.set_stream(stream)
     m2.set_state(*hp)
     m2.step(max(args.warmup, 6), 0.9)
-    m2.autotune(8)
+    if not fixed:
+        m2.autotune(8)
     m2.get_state(out)
     if dist:
         dist.barrier()
@@ -332,8 +339,10 @@ def run_gpu(args, name):
     if os.path.exists(tpath):
         with open(tpath) as f:
             tr = json.load(f)
-        if tr.get("kernel_hash") == _kernel_hash() and tr.get("shape") == _shape_key(shape):
-            traffic = tr.get("bytes_per_launch")
+        if tr.get("kernel_hash") == _kernel_hash():
+            for cap in tr.get("captures", []):
+                if cap.get("shape") == _shape_key(shape):
+                    traffic = cap.get("bytes_per_launch")
     line = {
         "metric": "cell-updates/s",
         "value": ws * n * args.steps / (ms * 1e-3),
@@ -479,7 +488,7 @@ def run_gpu_ensemble(args, name):
         "config": {"workload": wl["desc"], "cells": n, "members": len(mis), "parallelism": f"replicas{ws}",
                    "l2": "working set > 129 MB L2, no flush needed",
                    "launch_shape": _shape_key(shape), "autotune": shape,
-                   "member_shapes": sorted({tuple(_shape_key(t)[:4]) for t in member_shapes})},
+                   "member_shapes": sorted({tuple(_shape_key(t)[:6]) for t in member_shapes})},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None, "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
                      "alg_bytes_per_cell": ab},
@@ -594,9 +603,21 @@ def run_gpu_adjoint(args, name):
     return 0
 
 
+def _shape_kwargs(spec):
+    """Mesh keyword arguments of a --shape string (empty: autotune)."""
+    if not spec:
+        return {}
+    v = [int(x) for x in spec.split(",")]
+    if len(v) != 7:
+        raise SystemExit("--shape needs block,min_blocks,stages,geometry_early,activity,edge_pass,grid")
+    keys = ("block_size", "min_blocks", "stages", "geometry_early", "activity", "edge_pass", "grid")
+    return dict(zip(keys, v))
+
+
 def _shape_key(t):
-    """(block, min_blocks, stages, geometry_early, grid[, chunk]) of an autotuner choice."""
-    k = [t["block_size"], t["min_blocks"], t["stages"], t["geometry_early"], t["grid"]]
+    """(block, min_blocks, stages, geometry_early, activity, edge_pass, grid[, chunk]) of an autotuner choice."""
+    k = [t["block_size"], t["min_blocks"], t["stages"], t["geometry_early"], t["activity"], t["edge_pass"],
+         t["grid"]]
     return k + [t["chunk"]] if t.get("chunk") else k
 
 
@@ -619,6 +640,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--members", type=int, default=256, help="ensemble workloads: number of members")
+    ap.add_argument("--shape", default=None,
+                    help="mesh workloads: block,min_blocks,stages,geometry_early,activity,edge_pass,grid -- use "
+                         "this launch shape instead of autotuning (for profiling the shape a tuned run chose)")
     args = ap.parse_args()
     if args.steps is None:
         args.steps = WORKLOADS[args.workload]["steps"]

@@ -115,6 +115,9 @@ typedef struct swe_config {
                          bounds the step (FP64).  Compiled cell passes: FP32 (256, 4, 1),
                          (128, 8, 1); FP64 (128|256, 1, 1), all with geometry_early 0.  Not
                          with activity.  Results do not depend on it */
+    int grid;         /* blocks launched per step by the step kernel (each block loops over its
+                         share of the cells); 0 = default, one resident wave; larger values are
+                         clamped to one cell per thread.  Results do not depend on it */
 } swe_config;
 
 /* Fills *cfg with the defaults listed above. */

@@ -41,7 +41,7 @@ class swe_config(C.Structure):
     _fields_ = [("precision", C.c_int), ("g", C.c_double), ("h_dry", C.c_double),
                 ("reorder", C.c_int), ("block_size", C.c_int), ("graph_steps", C.c_int),
                 ("device", C.c_int), ("min_blocks", C.c_int), ("stages", C.c_int), ("flux", C.c_int),
-                ("geometry_early", C.c_int), ("activity", C.c_int), ("edge_pass", C.c_int)]
+                ("geometry_early", C.c_int), ("activity", C.c_int), ("edge_pass", C.c_int), ("grid", C.c_int)]
 
 
 class swe_info(C.Structure):
@@ -165,7 +165,7 @@ class Mesh:
 
     def __init__(self, nodes, tris, bathy, manning, precision=SWE_FP64, reorder=None,
                  block_size=0, graph_steps=0, device=0, g=9.81, h_dry=1e-6, min_blocks=0, stages=0,
-                 flux=SWE_FLUX_HLLC, geometry_early=0, activity=0, edge_pass=0):
+                 flux=SWE_FLUX_HLLC, geometry_early=0, activity=0, edge_pass=0, grid=0):
         lib = load()
         cfg = config_default()
         cfg.precision = precision
@@ -177,6 +177,7 @@ class Mesh:
         cfg.geometry_early = geometry_early
         cfg.activity = activity
         cfg.edge_pass = edge_pass
+        cfg.grid = grid
         cfg.flux = flux
         cfg.g, cfg.h_dry = g, h_dry
         nodes = np.ascontiguousarray(nodes, dtype=np.float64).reshape(-1, 2)

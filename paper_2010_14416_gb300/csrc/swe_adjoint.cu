@@ -50,6 +50,10 @@ struct AdjArgs {
     double dt, g, h_dry;
     int hll;
     BcTable bc;
+    // phase 1 with the edge pass: the interior fluxes of U^n from edge_flux_kernel
+    const V4<double>* __restrict__ eflux;
+    const double* __restrict__ esrc;
+    const int4* __restrict__ eidx;
 };
 
 __device__ __forceinline__ void unit_normal(double lx, double ly, double& n1, double& n2, double& len) {
@@ -65,6 +69,9 @@ __device__ __forceinline__ void edge_ln(const V4<double>& gA, const V4<double>& 
     ly = j == 0 ? gA.y : (j == 1 ? gA.w : gB.y);
 }
 
+// EDGES reads R_i's interior fluxes from the edge pass (the forward's own
+// edge-pass arithmetic) instead of evaluating them; R_i is the same bit for bit.
+template <bool EDGES>
 __global__ void __launch_bounds__(128) adj_phase1_kernel(const AdjArgs a) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
@@ -78,6 +85,8 @@ __global__ void __launch_bounds__(128) adj_phase1_kernel(const AdjArgs a) {
     cell_velocity<double>(hi, own.y, own.z, h_dry, ui, vi);
     // the forward's explicit right-hand side R_i
     double f0 = 0.0, f1 = 0.0, f2 = 0.0, sx = 0.0, sy = 0.0;
+    int4 ei = make_int4(-1, -1, -1, 0);
+    if constexpr (EDGES) ei = a.eidx[i];
     for (int j = 0; j < 3; ++j) {
         double lx, ly, n1, n2, len;
         edge_ln(gA, gB, j, lx, ly);
@@ -87,8 +96,27 @@ __global__ void __launch_bounds__(128) adj_phase1_kernel(const AdjArgs a) {
         if (c >= 0) {
             const V4<double> o = a.U[c & kNbrMask];
             double src;
-            edge_interior<double>(hi, ui, vi, zi, o.x, o.y, o.z, o.w, n1, n2, (c & kFlipBit) != 0, g, h_dry, F0, F1,
-                                  F2, src, a.hll != 0);
+            if constexpr (EDGES) {
+                if (!(hi > h_dry) && !(o.x > h_dry)) {
+                    const double zs = tmax(zi, o.w);
+                    const double hsi = tmax(0.0, hi + zi - zs);
+                    F0 = 0.0; F1 = 0.0; F2 = 0.0;
+                    src = 0.5 * g * (hsi * hsi - hi * hi);
+                } else {
+                    const int e = j == 0 ? ei.x : (j == 1 ? ei.y : ei.z);
+                    const V4<double> fl = a.eflux[e];
+                    if (c & kFlipBit) {
+                        F0 = -fl.x; F1 = -fl.y; F2 = -fl.z;
+                        src = a.esrc[e];
+                    } else {
+                        F0 = fl.x; F1 = fl.y; F2 = fl.z;
+                        src = fl.w;
+                    }
+                }
+            } else {
+                edge_interior<double>(hi, ui, vi, zi, o.x, o.y, o.z, o.w, n1, n2, (c & kFlipBit) != 0, g, h_dry, F0,
+                                      F1, F2, src, a.hll != 0);
+            }
             sx += src * lx;
             sy += src * ly;
         } else {
@@ -371,6 +399,22 @@ int adjoint_impl(swe_mesh* m, int64_t nsteps, double cfl, const int32_t* gauge_c
     a.h_dry = m->cfg.h_dry;
     a.hll = m->cfg.flux == SWE_FLUX_HLL ? 1 : 0;
     a.bc = m->bc;
+    // with the edge pass, phase 1 takes R's interior fluxes from one evaluation per edge
+    const bool edges = m->plain.edges && m->eflux;
+    a.eflux = edges ? (const V4<double>*)m->eflux : nullptr;
+    a.esrc = edges ? (const double*)m->esrc : nullptr;
+    a.eidx = edges ? m->eidx : nullptr;
+    StepArgs<double> ea{};
+    if (edges) {
+        ea.ecells = m->ecells;
+        ea.eln = (const double*)m->eln;
+        ea.eflux = (V4<double>*)m->eflux;
+        ea.esrc = (double*)m->esrc;
+        ea.n_edges = m->n_edges;
+        ea.g = m->cfg.g;
+        ea.h_dry = m->cfg.h_dry;
+        ea.hll = a.hll;
+    }
     const unsigned grid = (unsigned)((n + 127) / 128);
     // reverse sweep, segment by segment
     for (int64_t sgi = nseg - 1; sgi >= 0 && e == cudaSuccess; --sgi) {
@@ -383,7 +427,14 @@ int adjoint_impl(swe_mesh* m, int64_t nsteps, double cfl, const int32_t* gauge_c
         for (int64_t k = n1 - n0 - 1; k >= 0 && e == cudaSuccess; --k) {
             a.U = (const V4<double>*)(segp + k * sb);
             a.dt = dts[n0 + k];
-            adj_phase1_kernel<<<grid, 128, 0, st>>>(a);
+            if (edges) {
+                ea.s_in = a.U;
+                e = Launch<double>::edge_flux(ea, st);
+                if (e != cudaSuccess) break;
+                adj_phase1_kernel<true><<<grid, 128, 0, st>>>(a);
+            } else {
+                adj_phase1_kernel<false><<<grid, 128, 0, st>>>(a);
+            }
             adj_phase2_kernel<<<grid, 128, 0, st>>>(a);
             const int64_t nn = n0 + k;  // lambda now holds lambda^nn
             if (nn > 0 && nn % obs_every == 0)

@@ -510,6 +510,7 @@ void swe_config_default(swe_config* cfg) {
     cfg->geometry_early = 0;
     cfg->activity = 0;
     cfg->edge_pass = 0;
+    cfg->grid = 0;
     cfg->flux = SWE_FLUX_HLLC;
 }
 
@@ -549,6 +550,10 @@ int swe_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* tris, i
     }
     if (c.edge_pass != 0 && c.edge_pass != 1) {
         set_error("swe_mesh_create: edge_pass must be 0 or 1");
+        return SWE_EINVAL;
+    }
+    if (c.grid < 0) {
+        set_error("swe_mesh_create: grid must be >= 0");
         return SWE_EINVAL;
     }
     if (c.edge_pass && c.activity) {
@@ -622,7 +627,7 @@ int swe_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* tris, i
         if (e != cudaSuccess) { swe_mesh_destroy(m); return cuda_fail(e, "swe_mesh_create: occupancy"); }
         const long long need = (n + c.block_size - 1) / c.block_size;
         const long long wave = (long long)std::max(per_sm, 1) * std::max(sms, 1);
-        m->grid = (unsigned)std::min(need, wave);
+        m->grid = (unsigned)std::min(need, c.grid > 0 ? (long long)c.grid : wave);
         // launches without activity bytes: the same shape, or the default one
         // when the configured shape exists only as an activity kernel
         m->plain = LaunchShape{c.block_size, c.min_blocks, c.stages, c.geometry_early, c.edge_pass, m->grid};

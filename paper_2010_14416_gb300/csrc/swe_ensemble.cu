@@ -507,8 +507,9 @@ int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
     std::vector<EnsShape> cand2;
     std::vector<double> ms2;
     if (!rc) {
-        for (size_t c = 1; c < cand.size(); ++c)
-            if (ms[c] < ms[best]) best = c;
+        // the first candidate within 2 % of the fastest (stable from run to run)
+        const double fastest = *std::min_element(ms.begin(), ms.end());
+        while (ms[best] > fastest * 1.02) ++best;
         long long wave = 0;
         const EnsShape b = cand[best];
         if (b.activity) {
@@ -533,7 +534,7 @@ int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
     EnsShape pick = cand[best];
     double ms_pick = ms[best];
     for (size_t c = 0; c < cand2.size(); ++c)
-        if (ms2[c] < ms_pick) { pick = cand2[c]; ms_pick = ms2[c]; }
+        if (ms2[c] * 1.02 < ms_pick) { pick = cand2[c]; ms_pick = ms2[c]; }
     E->block = pick.block;
     E->min_blocks = pick.min_blocks;
     E->stages = pick.stages;

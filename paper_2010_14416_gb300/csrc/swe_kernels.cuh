@@ -1085,6 +1085,8 @@ struct Launch {
                                        int edges, int* per_sm);
     // compiled (block, min_blocks, stages, geo_early) shapes of the cell pass of the edge-pass step
     static int edge_variants(int (*out)[4], int max);
+    // the edge pass alone (interior fluxes of a.s_in into a.eflux, a.esrc)
+    static cudaError_t edge_flux(const StepArgs<T>& a, cudaStream_t st);
     // compiled (block, min_blocks, geo_early, stages = prefetch distance + 1) shapes of the activity kernel
     static int act_variants(int (*out)[4], int max);
     static cudaError_t act_init(const V4<T>* s, const int4* topo, long long n, T h_dry, unsigned char* act,

@@ -65,13 +65,8 @@ cudaError_t Launch<T>::step(const StepArgs<T>& a, int block, int min_blocks, int
         return cudaErrorInvalidValue;
     }
     if (a.eflux) {
-        if (a.n_edges > 0) {
-            const long long eb = (a.n_edges + kEdgeBlock - 1) / kEdgeBlock;
-            const unsigned egrid = (unsigned)(eb < 65536 ? eb : 65536);
-            edge_flux_kernel<T, kEdgeBlock><<<egrid, kEdgeBlock, 0, st>>>(a);
-            cudaError_t e = cudaGetLastError();
-            if (e != cudaSuccess) return e;
-        }
+        cudaError_t e = edge_flux(a, st);
+        if (e != cudaSuccess) return e;
 #define SWE_LAUNCH_EDGE(B, M, S, G) \
     if (block == B && min_blocks == M && stages == S && geo_early == G) {        \
         step_kernel<T, B, M, S, G != 0, true><<<grid, B, 0, st>>>(a);            \
@@ -151,6 +146,15 @@ int Launch<T>::step_variants(int (*out)[4], int max) {
     }
 #undef SWE_LIST
     return k;
+}
+
+template <typename T>
+cudaError_t Launch<T>::edge_flux(const StepArgs<T>& a, cudaStream_t st) {
+    if (a.n_edges <= 0) return cudaSuccess;
+    const long long eb = (a.n_edges + kEdgeBlock - 1) / kEdgeBlock;
+    const unsigned egrid = (unsigned)(eb < 65536 ? eb : 65536);
+    edge_flux_kernel<T, kEdgeBlock><<<egrid, kEdgeBlock, 0, st>>>(a);
+    return cudaGetLastError();
 }
 
 template <typename T>

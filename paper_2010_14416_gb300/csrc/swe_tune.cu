@@ -24,6 +24,8 @@ using namespace swe;
 
 namespace {
 
+constexpr double kTuneTolerance = 1.02;
+
 struct Shape {
     int block, min_blocks, stages, geo_early, activity, edges;
     unsigned grid;
@@ -165,12 +167,23 @@ int autotune_t(swe_mesh* m, int trial_steps, swe_tune* out) {
         if (x) cudaEventDestroy(x);
     cudaFree(scratch);
     cudaFree(small);
+    // the first candidate (in the fixed order above) within kTuneTolerance of
+    // the fastest: timings within noise of each other then give the same choice
+    // from run to run
     size_t best = 0, best_plain = cand.size();
-    if (e == cudaSuccess)
+    if (e == cudaSuccess) {
+        double fastest = ms[0], fastest_plain = 1e300;
         for (size_t c = 0; c < cand.size(); ++c) {
-            if (ms[c] < ms[best]) best = c;
-            if (!cand[c].activity && (best_plain == cand.size() || ms[c] < ms[best_plain])) best_plain = c;
+            fastest = std::min(fastest, ms[c]);
+            if (!cand[c].activity) fastest_plain = std::min(fastest_plain, ms[c]);
         }
+        best = cand.size();
+        for (size_t c = 0; c < cand.size(); ++c) {
+            if (best == cand.size() && ms[c] <= fastest * kTuneTolerance) best = c;
+            if (best_plain == cand.size() && !cand[c].activity && ms[c] <= fastest_plain * kTuneTolerance)
+                best_plain = c;
+        }
+    }
     const Shape pick = e == cudaSuccess ? cand[best] : before;
     // launches without activity bytes take the fastest shape of the plain kernel
     if (e == cudaSuccess && best_plain < cand.size()) apply_shape(m, cand[best_plain]);

@@ -217,7 +217,8 @@ def test_activity_mode_is_bitwise_neutral(precision, maker):
     f32 = precision == capi.SWE_FP32
     shapes = [dict(), dict(block_size=128, min_blocks=8 if f32 else 1), dict(graph_steps=-1),
               dict(geometry_early=1, block_size=128, min_blocks=8 if f32 else 1),
-              dict(block_size=128, min_blocks=8 if f32 else 1, stages=4)]
+              dict(block_size=128, min_blocks=8 if f32 else 1, stages=4),
+              dict(grid=3), dict(grid=100000)]
     if f32:
         shapes += [dict(block_size=512, min_blocks=2), dict(block_size=128, min_blocks=8, geometry_early=1, stages=5)]
     for kw in shapes:
