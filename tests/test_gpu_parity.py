@@ -281,23 +281,31 @@ def test_graphs_block_sizes_and_device_io_are_bitwise_neutral():
 
 
 def test_edge_cases():
-    # one triangle with walls: stays at rest exactly
+    # one triangle with walls: stays at rest exactly, in every step mode (no
+    # interior edge for the edge pass; one cell in a warp for the activity bytes)
     nodes = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]])
-    m = capi.Mesh(nodes, [[0, 1, 2]], [0.0], [0.0])
-    m.set_state(np.array([1.0]), np.array([0.0]), np.array([0.0]))
-    m.step(10)
-    h, hu, hv = m.get_state()
-    assert h[0] == 1.0 and abs(hu[0]) < 1e-14 and abs(hv[0]) < 1e-14
-    m.close()
-    # all dry: no CFL step
+    for kw in (dict(), dict(activity=1), dict(edge_pass=1), dict(activity=1, precision=capi.SWE_FP32)):
+        m = capi.Mesh(nodes, [[0, 1, 2]], [0.0], [0.0], **kw)
+        m.set_state(*(np.array([v], dtype=m.dtype) for v in (1.0, 0.0, 0.0)))
+        m.step(10)
+        h, hu, hv = m.get_state()
+        assert h[0] == 1.0 and abs(hu[0]) < 1e-14 and abs(hv[0]) < 1e-14, kw
+        ch = m.autotune(trial_steps=1)
+        assert ch["grid"] == 1
+        m.step(5)
+        assert m.get_state()[0][0] == 1.0
+        m.close()
+    # all dry: no CFL step, in every mode
     mi = mg.dam_break_4k()
-    m = _gpu_mesh(mi)
     zero = np.zeros(mi.n_cells)
-    m.set_state(zero, zero, zero)
-    with pytest.raises(capi.SWEError) as e:
-        m.step(3)
-    assert e.value.code == capi.SWE_EDRY
-    m.close()
+    for kw in (dict(), dict(activity=1), dict(edge_pass=1)):
+        m = _gpu_mesh(mi, **kw)
+        m.set_state(zero, zero, zero)
+        with pytest.raises(capi.SWEError) as e:
+            m.step(3)
+        assert e.value.code == capi.SWE_EDRY
+        assert np.array_equal(m.get_state()[0], zero)
+        m.close()
     # bad arguments are rejected on the host
     m = _gpu_mesh(mi)
     with pytest.raises(capi.SWEError) as e:
