@@ -440,8 +440,9 @@ SWE_API int swe_autotune(swe_mesh* mesh, int trial_steps, swe_tune* out);
  * (128, 8, 3|1, 0), (256, 4, 3|1, 1), (128, 8, 3|1, 1); FP64: (256|128, 1,
  * 1|2, 0), (256|128, 1, 1, 1)) and its activity-mode shapes (activity 1,
  * stages 3: FP32 (128, 8) and (256, 4) with geometry_early 0|1; FP64
- * (256|128, 1) with 0) times chunks of 4 to 64 tiles, then grids of half, one
- * and two resident waves for the best of those.  Members' states, times and
+ * (256|128, 1) with 0), and for FP64 ensembles its edge-pass shapes
+ * (edge_pass 1: (256|128, 1, 1, 0)), times chunks of 4 to 64 tiles, then grids
+ * of half, one and two resident waves for the best of those.  Members' states, times and
  * steps are unchanged by the call and by the choice.  trial_steps 0 = 4.
  */
 SWE_API int swe_ensemble_autotune(swe_ensemble* ens, int trial_steps, swe_tune* out);
@@ -449,8 +450,9 @@ SWE_API int swe_ensemble_autotune(swe_ensemble* ens, int trial_steps, swe_tune* 
 /*
  * Sets an ensemble's launch shape directly (for instance one that
  * swe_ensemble_autotune chose earlier): block_size, min_blocks, stages,
- * geometry_early and activity must name a compiled shape (listed above;
- * stages is ignored with activity), chunk a power of two up to 4096 tiles,
+ * geometry_early, activity and edge_pass must name a compiled shape (listed
+ * above; stages is ignored with activity; edge_pass only for FP64 ensembles
+ * and not with activity), chunk a power of two up to 4096 tiles,
  * grid the blocks to launch (0 = one resident wave); other fields are
  * ignored.  Results do not depend on the shape.  Errors: SWE_EINVAL.
  */

@@ -379,10 +379,11 @@ class Ensemble:
         check(load().swe_ensemble_autotune(self._h, int(trial_steps), C.byref(t)))
         return {k: getattr(t, k) for k, _ in swe_tune._fields_}
 
-    def set_shape(self, block_size, min_blocks, stages=1, geometry_early=0, activity=0, chunk=4, grid=0):
+    def set_shape(self, block_size, min_blocks, stages=1, geometry_early=0, activity=0, chunk=4, grid=0,
+                  edge_pass=0):
         """Sets the batched kernel's launch shape (see swe_ensemble_set_shape)."""
         t = swe_tune(block_size=block_size, min_blocks=min_blocks, stages=stages, geometry_early=geometry_early,
-                     activity=activity, chunk=chunk, grid=grid)
+                     activity=activity, edge_pass=edge_pass, chunk=chunk, grid=grid)
         check(load().swe_ensemble_set_shape(self._h, C.byref(t)))
 
     def info(self, member):

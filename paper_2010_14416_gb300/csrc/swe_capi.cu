@@ -399,23 +399,16 @@ cudaError_t launch_step_raw(swe_mesh* m, const void* in, void* out, unsigned lon
                : launch_raw_t<double>(m, in, out, small, step_index, cfl, dt_fixed, dt_log, st, with_activity);
 }
 
-int build_edges(swe_mesh* m) {
-    if (m->eflux) return SWE_OK;
-    const HostMesh& H = m->hm;
+void append_edges(const HostMesh& H, int64_t base, std::vector<int2>& cells, std::vector<double>& ln, int4* eidx) {
     const int64_t n = H.n_cells;
-    std::vector<int2> cells;
-    std::vector<double> ln;
-    std::vector<int4> eidx(n, make_int4(-1, -1, -1, 0));
-    cells.reserve(3 * n / 2 + 1);
-    ln.reserve(3 * n + 2);
-    // edges in the order of their left cell (locality), each once
+    for (int64_t c = 0; c < n; ++c) eidx[c] = make_int4(-1, -1, -1, 0);
     for (int64_t c = 0; c < n; ++c)
         for (int j = 0; j < 3; ++j) {
             const int32_t code = H.code[3 * c + j];
             if (code >= 0 && !(code & kFlipBit)) {
                 const int e = (int)cells.size();
                 const int k = code & kNbrMask;
-                cells.push_back(make_int2((int)c, k));
+                cells.push_back(make_int2((int)(base + c), (int)(base + k)));
                 ln.push_back(H.ln[6 * c + 2 * j]);
                 ln.push_back(H.ln[6 * c + 2 * j + 1]);
                 (j == 0 ? eidx[c].x : (j == 1 ? eidx[c].y : eidx[c].z)) = e;
@@ -424,6 +417,18 @@ int build_edges(swe_mesh* m) {
                         (jk == 0 ? eidx[k].x : (jk == 1 ? eidx[k].y : eidx[k].z)) = e;
             }
         }
+}
+
+int build_edges(swe_mesh* m) {
+    if (m->eflux) return SWE_OK;
+    const HostMesh& H = m->hm;
+    const int64_t n = H.n_cells;
+    std::vector<int2> cells;
+    std::vector<double> ln;
+    std::vector<int4> eidx(n);
+    cells.reserve(3 * n / 2 + 1);
+    ln.reserve(3 * n + 2);
+    append_edges(H, 0, cells, ln, eidx.data());
     const int64_t E = (int64_t)cells.size();
     const size_t esz = m->esz;
     std::vector<char> lnt(2 * E * esz);

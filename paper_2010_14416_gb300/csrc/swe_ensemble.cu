@@ -55,6 +55,14 @@ struct swe_ensemble {
     unsigned char* act[3] = {nullptr, nullptr, nullptr};
     int64_t act_len = 0;
     bool act_valid = false;
+    // edge pass (FP64 ensembles): the members' interior edges, concatenated
+    int edges = 0;
+    int64_t n_edges = 0;
+    int2* ecells = nullptr;
+    void* eln = nullptr;
+    void* eflux = nullptr;
+    void* esrc = nullptr;
+    int4* eidx = nullptr;
     unsigned grid = 0;
     int64_t nstep = 0;
     std::vector<double> cfl_host;
@@ -141,6 +149,20 @@ EnsArgs<T> ens_args(swe_ensemble* E, int64_t step_index) {
     a.n_active = E->n_active;
     a.n_total = E->n_total;
     a.chunk_log2 = E->chunk_log2;
+    a.ecells = nullptr;
+    a.eln = nullptr;
+    a.eflux = nullptr;
+    a.esrc = nullptr;
+    a.eidx = nullptr;
+    a.n_edges = 0;
+    if (E->edges && E->eflux) {
+        a.ecells = E->ecells;
+        a.eln = (const T*)E->eln;
+        a.eflux = (V4<T>*)E->eflux;
+        a.esrc = (T*)E->esrc;
+        a.eidx = E->eidx;
+        a.n_edges = E->n_edges;
+    }
     a.act_in = nullptr;
     a.act_next = nullptr;
     a.act_clear = nullptr;
@@ -311,6 +333,27 @@ int ens_build(swe_ensemble* E, swe_mesh* const* M) {
     if (e != cudaSuccess) return efail(e, "swe_ensemble_create: occupancy");
     E->grid = (unsigned)std::min<long long>((long long)(E->n_total / E->block), wave);
     E->cfl_host.assign(nm, -1.0);
+    // FP64: the members' interior edges for the edge pass (the FP64 pipe bounds
+    // the step, so evaluating each edge once pays; FP32 steps are bound by memory)
+    if (sizeof(T) == 8) {
+        std::vector<int2> cells;
+        std::vector<double> ln;
+        std::vector<int4> eidx(off, make_int4(-1, -1, -1, 0));
+        for (int k = 0; k < nm; ++k) append_edges(M[k]->hm, E->base[k], cells, ln, eidx.data() + E->base[k]);
+        const int64_t ne = (int64_t)cells.size();
+        const size_t nb = (size_t)std::max<int64_t>(ne, 1);
+        if ((rc = ens_alloc(E, (void**)&E->ecells, nb * sizeof(int2), "edges")) ||
+            (rc = ens_alloc(E, &E->eln, 2 * nb * sizeof(T), "edges")) ||
+            (rc = ens_alloc(E, &E->eflux, nb * sizeof(V4<T>), "edges")) ||
+            (rc = ens_alloc(E, &E->esrc, nb * sizeof(T), "edges")) ||
+            (rc = ens_alloc(E, (void**)&E->eidx, off * sizeof(int4), "edges")))
+            return rc;
+        if (ne) e = cudaMemcpy(E->ecells, cells.data(), ne * sizeof(int2), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && ne) e = cudaMemcpy(E->eln, ln.data(), 2 * ne * sizeof(double), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(E->eidx, eidx.data(), off * sizeof(int4), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return efail(e, "swe_ensemble_create: edges");
+        E->n_edges = ne;
+    }
     return SWE_OK;
 }
 
@@ -404,6 +447,7 @@ struct EnsShape {
     int block, min_blocks, stages, geo_early, chunk_log2;
     unsigned grid;
     int activity;
+    int edges;
 };
 
 template <typename T>
@@ -428,6 +472,13 @@ int ens_time_shapes(swe_ensemble* E, const std::vector<EnsShape>& cand, int tria
             // activity trials read the current bytes and rewrite the next buffer with
             // exactly the bytes the next real step writes there
             const int p3 = (int)(E->nstep % 3);
+            if (!sh.edges) {
+                a.ecells = nullptr; a.eln = nullptr; a.eflux = nullptr; a.esrc = nullptr; a.eidx = nullptr;
+                a.n_edges = 0;
+            } else {
+                a.ecells = E->ecells; a.eln = (const T*)E->eln; a.eflux = (V4<T>*)E->eflux; a.esrc = (T*)E->esrc;
+                a.eidx = E->eidx; a.n_edges = E->n_edges;
+            }
             a.act_in = sh.activity ? E->act[p3] : nullptr;
             a.act_next = sh.activity ? E->act[(p3 + 1) % 3] : nullptr;
             a.act_clear = sh.activity ? E->act[(p3 + 2) % 3] : nullptr;
@@ -456,7 +507,8 @@ int ens_time_shapes(swe_ensemble* E, const std::vector<EnsShape>& cand, int tria
 
 template <typename T>
 int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
-    const EnsShape before{E->block, E->min_blocks, E->stages, E->geo_early, E->chunk_log2, E->grid, E->activity};
+    const EnsShape before{E->block,     E->min_blocks, E->stages,   E->geo_early,
+                          E->chunk_log2, E->grid,     E->activity, E->edges};
     std::vector<EnsShape> cand{before};
     const bool with_act = E->n_total < kActivityMaxCells;
     if (with_act) {
@@ -471,10 +523,10 @@ int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
         if (e != cudaSuccess) return efail(e, "swe_ensemble_autotune: occupancy");
         const unsigned gr = (unsigned)std::max(1LL, std::min((long long)(E->n_total / v[k][0]), wave));
         for (int cl2 = 2; cl2 <= 6; ++cl2) {
-            const EnsShape sh{v[k][0], v[k][1], v[k][2], v[k][3], cl2, gr, 0};
+            const EnsShape sh{v[k][0], v[k][1], v[k][2], v[k][3], cl2, gr, 0, 0};
             if (!(sh.block == before.block && sh.min_blocks == before.min_blocks && sh.stages == before.stages &&
                   sh.geo_early == before.geo_early && sh.chunk_log2 == before.chunk_log2 && sh.grid == before.grid &&
-                  !before.activity))
+                  !before.activity && !before.edges))
                 cand.push_back(sh);
         }
     }
@@ -487,7 +539,18 @@ int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
         if (e != cudaSuccess) return efail(e, "swe_ensemble_autotune: occupancy");
         const long long wave = (long long)std::max(per_sm, 1) * std::max(sms, 1);
         const unsigned gr = (unsigned)std::max(1LL, std::min((long long)(E->n_total / w[k][0]), wave));
-        for (int cl2 = 2; cl2 <= 6; ++cl2) cand.push_back({w[k][0], w[k][1], 3, w[k][2], cl2, gr, 1});
+        for (int cl2 = 2; cl2 <= 6; ++cl2) cand.push_back({w[k][0], w[k][1], 3, w[k][2], cl2, gr, 1, 0});
+    }
+    int x[16][4];
+    const int nx = E->eflux ? std::min(Launch<T>::ensemble_edge_variants(x, 16), 16) : 0;
+    for (int k = 0; k < nx; ++k) {
+        int per_sm = 0, sms = 0;
+        cudaError_t e = Launch<T>::ensemble_edge_resident_blocks(x[k][0], x[k][1], x[k][2], x[k][3], &per_sm);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, E->device);
+        if (e != cudaSuccess) return efail(e, "swe_ensemble_autotune: occupancy");
+        const long long wave = (long long)std::max(per_sm, 1) * std::max(sms, 1);
+        const unsigned gr = (unsigned)std::max(1LL, std::min((long long)(E->n_total / x[k][0]), wave));
+        for (int cl2 = 2; cl2 <= 6; ++cl2) cand.push_back({x[k][0], x[k][1], x[k][2], x[k][3], cl2, gr, 0, 1});
     }
     void* scratch = nullptr;
     unsigned long long *small = nullptr, *act = nullptr;
@@ -512,9 +575,11 @@ int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
         while (ms[best] > fastest * 1.02) ++best;
         long long wave = 0;
         const EnsShape b = cand[best];
-        if (b.activity) {
+        if (b.activity || b.edges) {
             int per_sm = 0, sms = 0;
-            e = Launch<T>::ensemble_act_resident_blocks(b.block, b.min_blocks, b.geo_early, &per_sm);
+            e = b.activity ? Launch<T>::ensemble_act_resident_blocks(b.block, b.min_blocks, b.geo_early, &per_sm)
+                           : Launch<T>::ensemble_edge_resident_blocks(b.block, b.min_blocks, b.stages, b.geo_early,
+                                                                      &per_sm);
             if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, E->device);
             wave = (long long)std::max(per_sm, 1) * std::max(sms, 1);
         } else {
@@ -525,7 +590,7 @@ int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
         for (long long gsz : {wave / 2, 2 * wave}) {
             const unsigned gr = (unsigned)std::max(1LL, std::min(tiles, gsz));
             if (!rc && gr != b.grid)
-                cand2.push_back({b.block, b.min_blocks, b.stages, b.geo_early, b.chunk_log2, gr, b.activity});
+                cand2.push_back({b.block, b.min_blocks, b.stages, b.geo_early, b.chunk_log2, gr, b.activity, b.edges});
         }
         if (!rc && !cand2.empty()) rc = ens_time_shapes<T>(E, cand2, trial_steps, scratch, small, act, ms2);
     }
@@ -540,6 +605,7 @@ int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
     E->stages = pick.stages;
     E->geo_early = pick.geo_early;
     E->activity = pick.activity;
+    E->edges = pick.edges;
     // the bytes describe the current state (the trials rewrote the next buffer with
     // what the next step writes there); without activity they would go stale
     E->act_valid = pick.activity != 0 && E->act[0] != nullptr;
@@ -552,7 +618,7 @@ int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
         out->stages = pick.stages;
         out->geometry_early = pick.geo_early;
         out->activity = pick.activity;
-        out->edge_pass = 0;
+        out->edge_pass = pick.edges;
         out->chunk = 1 << pick.chunk_log2;
         out->grid = pick.grid;
         out->cells_per_thread = (double)E->n_total / ((double)pick.grid * pick.block);
@@ -574,7 +640,8 @@ void swe_ensemble_destroy(swe_ensemble* E) {
     drop_graphs(E);
     void* bufs[] = {E->state[0], E->state[1], E->geoA, E->geoB, E->topo, E->gm2, E->perm, E->tile_member,
                     E->member_first_tile, E->cfl, E->small, E->n_active, E->kind, E->value,
-                    E->stage[0], E->stage[1], E->stage[2], E->act[0], E->act[1], E->act[2]};
+                    E->stage[0], E->stage[1], E->stage[2], E->act[0], E->act[1], E->act[2],
+                    E->ecells, E->eln, E->eflux, E->esrc, E->eidx};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (E->cap_stream) cudaStreamDestroy(E->cap_stream);
@@ -694,7 +761,8 @@ int swe_ensemble_step(swe_ensemble* E, int64_t nsteps, const double* cfl, double
 }
 
 int swe_ensemble_set_shape(swe_ensemble* E, const swe_tune* shape) {
-    if (!E || !shape || (shape->activity != 0 && shape->activity != 1) || shape->edge_pass != 0 ||
+    if (!E || !shape || (shape->activity != 0 && shape->activity != 1) || (shape->edge_pass != 0 && shape->edge_pass != 1) ||
+        (shape->edge_pass && (shape->activity || !E->eflux)) ||
         shape->chunk < 1 || (shape->chunk & (shape->chunk - 1)) || shape->chunk > 4096 || shape->grid < 0) {
         set_error("swe_ensemble_set_shape: bad arguments");
         return SWE_EINVAL;
@@ -711,6 +779,9 @@ int swe_ensemble_set_shape(swe_ensemble* E, const swe_tune* shape) {
                                                                           shape->geometry_early, &per_sm)
                             : Launch<float>::ensemble_resident_blocks(shape->block_size, shape->min_blocks,
                                                                       shape->stages, shape->geometry_early, &per_sm);
+    else if (shape->edge_pass)
+        e = Launch<double>::ensemble_edge_resident_blocks(shape->block_size, shape->min_blocks, shape->stages,
+                                                          shape->geometry_early, &per_sm);
     else
         e = shape->activity ? Launch<double>::ensemble_act_resident_blocks(shape->block_size, shape->min_blocks,
                                                                            shape->geometry_early, &per_sm)
@@ -734,6 +805,7 @@ int swe_ensemble_set_shape(swe_ensemble* E, const swe_tune* shape) {
     E->grid = (unsigned)std::max(1LL, std::min(tiles, shape->grid > 0 ? (long long)shape->grid : wave));
     if (E->activity != shape->activity) E->act_valid = false;
     E->activity = shape->activity;
+    E->edges = shape->edge_pass;
     drop_graphs(E);
     return SWE_OK;
 }

@@ -67,6 +67,11 @@ cudaError_t launch_step_raw(swe_mesh* m, const void* in, void* out, unsigned lon
 int init_activity(swe_mesh* m);
 // Builds (once) the interior-edge list of the edge-pass step.
 int build_edges(swe_mesh* m);
+// Appends the interior edges of H, its cells numbered from `base`, in canonical
+// orientation (each once, from its left cell, in the order of that cell):
+// (left, right), the left cell's L n, and into eidx[0 .. H.n_cells) each
+// cell's edge per local edge (-1 on the boundary).
+void append_edges(const HostMesh& H, int64_t base, std::vector<int2>& cells, std::vector<double>& ln, int4* eidx);
 // The activity kernel indexes cells with 32 bits: meshes below this size.
 constexpr int64_t kActivityMaxCells = int64_t(1) << 29;
 // Applies pending boundary-group changes of m to the device.

@@ -111,6 +111,13 @@ struct EnsArgs {
     const unsigned char* act_in;
     unsigned char* act_next;
     unsigned char* act_clear;
+    // edge pass over the concatenated members (ensemble_step_kernel with EDGES)
+    const int2* ecells;
+    const T* eln;
+    V4<T>* eflux;
+    T* esrc;
+    const int4* eidx;
+    long long n_edges;
     int slot_read, slot_write, slot_reset;
     int hll;
     T g, h_dry;
@@ -803,7 +810,7 @@ __device__ __forceinline__ long long ens_tile_of(long long k, long long nchunk_s
     return ((b + (k >> cl2) * nchunk_stride) << cl2) + (k & mask);
 }
 
-template <typename T, int BLOCK, int MINB, int STAGES, bool GEO_EARLY>
+template <typename T, int BLOCK, int MINB, int STAGES, bool GEO_EARLY, bool EDGES = false>
 __global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel(const EnsArgs<T> a) {
     static_assert(kEnsPad % BLOCK == 0, "a tile must not straddle two members");
     const long long G = gridDim.x, b = blockIdx.x;
@@ -878,7 +885,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel(const EnsArg
             tp = a.topo[i];
         }
         if (have_dt)
-            cand = tmin(cand, update_cell<T, GEO_EARLY>(a, i, own, tp, dt, active, sm + 5, (unsigned*)(sm + 4)));
+            cand = tmin(cand, update_cell<T, GEO_EARLY, EDGES>(a, i, own, tp, dt, active, sm + 5, (unsigned*)(sm + 4)));
         else
             a.s_out[i] = own;
     }
@@ -1103,6 +1110,11 @@ struct Launch {
                                          unsigned grid, cudaStream_t st);
     static cudaError_t ensemble_act_resident_blocks(int block, int min_blocks, int geo_early, int* per_sm);
     static int ensemble_act_variants(int (*out)[3], int max);
+    // edge pass of the ensemble (a.eflux set): edge kernel, then the cell pass of
+    // one of its compiled (block, min_blocks, stages, geo_early) shapes
+    static int ensemble_edge_variants(int (*out)[4], int max);
+    static cudaError_t ensemble_edge_resident_blocks(int block, int min_blocks, int stages, int geo_early,
+                                                     int* per_sm);
     static void ensemble_default(int* block, int* min_blocks, int* stages, int* geo_early);
     static int default_min_blocks(int block);
     static cudaError_t dt(const V4<T>* s, const V4<T>* geoB, long long n, T g, T h_dry,

@@ -228,10 +228,72 @@ int Launch<T>::ensemble_variants(int (*out)[4], int max) {
     return k;
 }
 
+// (block, min blocks per SM, stages, geometry early) shapes of the ensemble's
+// edge-pass cell kernel (FP64 only: the edge pass pays where the FP64 pipe bounds the step)
+#define SWE_ENS_EDGE_VARIANTS_F32(X)
+#define SWE_ENS_EDGE_VARIANTS_F64(X) X(256, 1, 1, 0) X(128, 1, 1, 0)
+
+template <typename T>
+int Launch<T>::ensemble_edge_variants(int (*out)[4], int max) {
+    int k = 0;
+#define SWE_LIST(B, M, S, G) \
+    if (k < max) { out[k][0] = B; out[k][1] = M; out[k][2] = S; out[k][3] = G; } \
+    ++k;
+    if constexpr (sizeof(T) == 4) {
+        SWE_ENS_EDGE_VARIANTS_F32(SWE_LIST)
+    } else {
+        SWE_ENS_EDGE_VARIANTS_F64(SWE_LIST)
+    }
+#undef SWE_LIST
+    return k;
+}
+
+template <typename T>
+cudaError_t Launch<T>::ensemble_edge_resident_blocks(int block, int min_blocks, int stages, int geo_early,
+                                                     int* per_sm) {
+#define SWE_OCC(B, M, S, G) \
+    if (block == B && min_blocks == M && stages == S && geo_early == G)          \
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, ensemble_step_kernel<T, B, M, S, G != 0, true>, \
+                                                             B, 0);
+    if constexpr (sizeof(T) == 4) {
+        SWE_ENS_EDGE_VARIANTS_F32(SWE_OCC)
+    } else {
+        SWE_ENS_EDGE_VARIANTS_F64(SWE_OCC)
+    }
+#undef SWE_OCC
+    return cudaErrorInvalidValue;
+}
+
 template <typename T>
 cudaError_t Launch<T>::ensemble_step(const EnsArgs<T>& a, int block, int min_blocks, int stages, int geo_early,
                                      unsigned grid, cudaStream_t st) {
     if (grid == 0) return cudaErrorInvalidValue;
+    if (a.eflux) {
+        StepArgs<T> ea{};
+        ea.s_in = a.s_in;
+        ea.ecells = a.ecells;
+        ea.eln = a.eln;
+        ea.eflux = a.eflux;
+        ea.esrc = a.esrc;
+        ea.n_edges = a.n_edges;
+        ea.g = a.g;
+        ea.h_dry = a.h_dry;
+        ea.hll = a.hll;
+        cudaError_t e = edge_flux(ea, st);
+        if (e != cudaSuccess) return e;
+#define SWE_LAUNCH_EDGE(B, M, S, G) \
+    if (block == B && min_blocks == M && stages == S && geo_early == G) {        \
+        ensemble_step_kernel<T, B, M, S, G != 0, true><<<grid, B, 0, st>>>(a);   \
+        return cudaGetLastError();                                                \
+    }
+        if constexpr (sizeof(T) == 4) {
+            SWE_ENS_EDGE_VARIANTS_F32(SWE_LAUNCH_EDGE)
+        } else {
+            SWE_ENS_EDGE_VARIANTS_F64(SWE_LAUNCH_EDGE)
+        }
+#undef SWE_LAUNCH_EDGE
+        return cudaErrorInvalidValue;
+    }
 #define SWE_LAUNCH(B, M, S, G) \
     if (block == B && min_blocks == M && stages == S && geo_early == G) {        \
         ensemble_step_kernel<T, B, M, S, G != 0><<<grid, B, 0, st>>>(a);         \

@@ -289,7 +289,9 @@ def test_edge_cases():
         m.set_state(*(np.array([v], dtype=m.dtype) for v in (1.0, 0.0, 0.0)))
         m.step(10)
         h, hu, hv = m.get_state()
-        assert h[0] == 1.0 and abs(hu[0]) < 1e-14 and abs(hv[0]) < 1e-14, kw
+        # the three wall pressures cancel to round-off (FP32: ~1e-6 of h sqrt(g h))
+        tol = 1e-5 if m.dtype == np.float32 else 1e-14
+        assert h[0] == 1.0 and abs(hu[0]) < tol and abs(hv[0]) < tol, kw
         ch = m.autotune(trial_steps=1)
         assert ch["grid"] == 1
         m.step(5)
@@ -377,6 +379,7 @@ def test_full_size_wet_river_1m_fp64_against_oracle():
     M = _orc_mesh(mi)
     oh, ohu, ohv, ot, oc = M.run(mi.h, mi.hu, mi.hv, 1000, 0.9)
     (gh, ghu, ghv), t, info = _gpu_run(mi, 1000)
+    assert info["n_clamped"] == oc == 0        # no depth clamped on this workload
     assert t == pytest.approx(ot, rel=1e-12)
     for a, b in ((gh, oh), (ghu, ohu), (ghv, ohv)):
         assert rel_err(a, b) <= FP64_TOL
