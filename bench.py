@@ -308,6 +308,7 @@ def run_gpu(args, name):
     m2.step(max(args.warmup, 6), 0.9)
     if not fixed:
         m2.autotune(8)
+    m2.step(96, 0.9)      # warm-up after tuning: the step graph is captured before the timed job
     m2.get_state(out)
     if dist:
         dist.barrier()
