@@ -39,6 +39,7 @@ struct AdjArgs {
     const V4<double>* __restrict__ U;     // state U^n, internal order
     const V4<double>* __restrict__ geoA;
     const V4<double>* __restrict__ geoB;
+    const V4<double>* __restrict__ geoR;  // 1/|L n| of the three edges (the forward's)
     const int4* __restrict__ topo;
     const double* __restrict__ gm2;
     V4<double>* __restrict__ lam;         // lambda (h, hu, hv, -)
@@ -56,9 +57,9 @@ struct AdjArgs {
     const int4* __restrict__ eidx;
 };
 
-__device__ __forceinline__ void unit_normal(double lx, double ly, double& n1, double& n2, double& len) {
+// the forward's unit normal and length of an edge, from its 1/|L n|
+__device__ __forceinline__ void unit_normal(double lx, double ly, double rl, double& n1, double& n2, double& len) {
     const double l2 = lx * lx + ly * ly;
-    const double rl = 1.0 / sqrt(l2);
     len = l2 * rl;
     n1 = lx * rl;
     n2 = ly * rl;
@@ -77,7 +78,7 @@ __global__ void __launch_bounds__(128) adj_phase1_kernel(const AdjArgs a) {
     if (i >= a.n) return;
     const double g = a.g, h_dry = a.h_dry;
     const V4<double> own = a.U[i];
-    const V4<double> gA = a.geoA[i], gB = a.geoB[i];
+    const V4<double> gA = a.geoA[i], gB = a.geoB[i], gR = a.geoR[i];
     const int4 tp = a.topo[i];
     const int code[3] = {tp.x, tp.y, tp.z};
     const double hi = own.x, zi = own.w;
@@ -90,7 +91,7 @@ __global__ void __launch_bounds__(128) adj_phase1_kernel(const AdjArgs a) {
     for (int j = 0; j < 3; ++j) {
         double lx, ly, n1, n2, len;
         edge_ln(gA, gB, j, lx, ly);
-        unit_normal(lx, ly, n1, n2, len);
+        unit_normal(lx, ly, j == 0 ? gR.x : (j == 1 ? gR.y : gR.z), n1, n2, len);
         double F0, F1, F2;
         const int c = code[j];
         if (c >= 0) {
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(128) adj_phase2_kernel(const AdjArgs a) {
     if (jc >= a.n) return;
     const double g = a.g, h_dry = a.h_dry;
     const V4<double> own = a.U[jc];
-    const V4<double> gA = a.geoA[jc], gB = a.geoB[jc];
+    const V4<double> gA = a.geoA[jc], gB = a.geoB[jc], gR = a.geoR[jc];
     const int4 tp = a.topo[jc];
     const int code[3] = {tp.x, tp.y, tp.z};
     const V4<double> nuj = a.nu[jc];
@@ -175,7 +176,7 @@ __global__ void __launch_bounds__(128) adj_phase2_kernel(const AdjArgs a) {
     for (int j = 0; j < 3; ++j) {
         double lx, ly, n1, n2, len;
         edge_ln(gA, gB, j, lx, ly);
-        unit_normal(lx, ly, n1, n2, len);
+        unit_normal(lx, ly, j == 0 ? gR.x : (j == 1 ? gR.y : gR.z), n1, n2, len);
         const int c = code[j];
         D4 F0, F1, F2;
         if (c >= 0) {
@@ -387,6 +388,7 @@ int adjoint_impl(swe_mesh* m, int64_t nsteps, double cfl, const int32_t* gauge_c
     AdjArgs a;
     a.geoA = (const V4<double>*)m->geoA;
     a.geoB = (const V4<double>*)m->geoB;
+    a.geoR = (const V4<double>*)m->geoR;
     a.topo = m->topo;
     a.gm2 = (const double*)m->gm2;
     a.lam = (V4<double>*)lam.p;
@@ -408,6 +410,7 @@ int adjoint_impl(swe_mesh* m, int64_t nsteps, double cfl, const int32_t* gauge_c
     if (edges) {
         ea.ecells = m->ecells;
         ea.eln = (const double*)m->eln;
+        ea.erl = (const double*)m->erl;
         ea.eflux = (V4<double>*)m->eflux;
         ea.esrc = (double*)m->esrc;
         ea.n_edges = m->n_edges;

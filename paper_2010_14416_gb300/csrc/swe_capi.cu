@@ -115,6 +115,17 @@ template <typename T>
 int upload_static(swe_mesh* m) {
     const HostMesh& H = m->hm;
     const int64_t n = H.n_cells;
+    if (sizeof(T) == 8) {
+        std::vector<V4<double>> R(n);
+        for (int64_t c = 0; c < n; ++c) {
+            R[c].x = host_edge_rl(H.ln[6 * c + 0], H.ln[6 * c + 1]);
+            R[c].y = host_edge_rl(H.ln[6 * c + 2], H.ln[6 * c + 3]);
+            R[c].z = host_edge_rl(H.ln[6 * c + 4], H.ln[6 * c + 5]);
+            R[c].w = 0.0;
+        }
+        cudaError_t e = cudaMemcpy(m->geoR, R.data(), n * sizeof(V4<double>), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "swe_mesh_create: upload");
+    }
     std::vector<V4<T>> A(n), B(n);
     std::vector<T> gm2(n), zt(n);
     const std::vector<int4> topo = make_topo(m);
@@ -164,6 +175,7 @@ StepArgs<T> make_args(swe_mesh* m, int64_t step_index, double cfl) {
     a.s_out = (V4<T>*)m->state[1 - p2];
     a.geoA = (const V4<T>*)m->geoA;
     a.geoB = (const V4<T>*)m->geoB;
+    a.geoR = (const V4<T>*)m->geoR;
     a.topo = m->topo;
     a.gm2 = (const T*)m->gm2;
     a.dt_read = (const double*)(m->small + p3);
@@ -181,6 +193,7 @@ StepArgs<T> make_args(swe_mesh* m, int64_t step_index, double cfl) {
     a.dt_log = (double*)(m->small + kSlotDtLast);  // size of the last step, for diagnostics
     a.ecells = nullptr;
     a.eln = nullptr;
+    a.erl = (const T*)m->erl;
     a.eflux = nullptr;
     a.esrc = nullptr;
     a.eidx = nullptr;
@@ -399,7 +412,10 @@ cudaError_t launch_step_raw(swe_mesh* m, const void* in, void* out, unsigned lon
                : launch_raw_t<double>(m, in, out, small, step_index, cfl, dt_fixed, dt_log, st, with_activity);
 }
 
-void append_edges(const HostMesh& H, int64_t base, std::vector<int2>& cells, std::vector<double>& ln, int4* eidx) {
+double host_edge_rl(double lx, double ly) { return 1.0 / std::sqrt(std::fma(lx, lx, ly * ly)); }
+
+void append_edges(const HostMesh& H, int64_t base, std::vector<int2>& cells, std::vector<double>& ln, int4* eidx,
+                  std::vector<double>* rl) {
     const int64_t n = H.n_cells;
     for (int64_t c = 0; c < n; ++c) eidx[c] = make_int4(-1, -1, -1, 0);
     for (int64_t c = 0; c < n; ++c)
@@ -411,6 +427,7 @@ void append_edges(const HostMesh& H, int64_t base, std::vector<int2>& cells, std
                 cells.push_back(make_int2((int)(base + c), (int)(base + k)));
                 ln.push_back(H.ln[6 * c + 2 * j]);
                 ln.push_back(H.ln[6 * c + 2 * j + 1]);
+                if (rl) rl->push_back(host_edge_rl(H.ln[6 * c + 2 * j], H.ln[6 * c + 2 * j + 1]));
                 (j == 0 ? eidx[c].x : (j == 1 ? eidx[c].y : eidx[c].z)) = e;
                 for (int jk = 0; jk < 3; ++jk)
                     if ((H.code[3 * k + jk] & kNbrMask) == (int32_t)c && H.code[3 * k + jk] >= 0)
@@ -424,11 +441,11 @@ int build_edges(swe_mesh* m) {
     const HostMesh& H = m->hm;
     const int64_t n = H.n_cells;
     std::vector<int2> cells;
-    std::vector<double> ln;
+    std::vector<double> ln, rl;
     std::vector<int4> eidx(n);
     cells.reserve(3 * n / 2 + 1);
     ln.reserve(3 * n + 2);
-    append_edges(H, 0, cells, ln, eidx.data());
+    append_edges(H, 0, cells, ln, eidx.data(), m->esz == 8 ? &rl : nullptr);
     const int64_t E = (int64_t)cells.size();
     const size_t esz = m->esz;
     std::vector<char> lnt(2 * E * esz);
@@ -442,17 +459,20 @@ int build_edges(swe_mesh* m) {
     if (e == cudaSuccess) e = cudaMalloc(&m->eflux, Eb * 4 * esz);
     if (e == cudaSuccess) e = cudaMalloc(&m->esrc, Eb * esz);
     if (e == cudaSuccess) e = cudaMalloc((void**)&m->eidx, (size_t)n * sizeof(int4));
+    if (e == cudaSuccess && esz == 8) e = cudaMalloc(&m->erl, Eb * esz);
     if (e != cudaSuccess) {
-        void* bufs[] = {m->ecells, m->eln, m->eflux, m->esrc, m->eidx};
+        void* bufs[] = {m->ecells, m->eln, m->eflux, m->esrc, m->eidx, m->erl};
         for (void* b : bufs)
             if (b) cudaFree(b);
         m->ecells = nullptr; m->eln = nullptr; m->eflux = nullptr; m->esrc = nullptr; m->eidx = nullptr;
+        m->erl = nullptr;
         set_error("edge pass: device allocation failed");
         return SWE_ENOMEM;
     }
     if (E) e = cudaMemcpy(m->ecells, cells.data(), E * sizeof(int2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && E) e = cudaMemcpy(m->eln, lnt.data(), 2 * E * esz, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(m->eidx, eidx.data(), n * sizeof(int4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && esz == 8 && E) e = cudaMemcpy(m->erl, rl.data(), E * sizeof(double), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "edge pass: upload");
     m->n_edges = E;
     m->device_bytes += (int64_t)(Eb * (sizeof(int2) + 7 * esz) + n * sizeof(int4));
@@ -528,7 +548,7 @@ void swe_mesh_destroy(swe_mesh* m) {
     drop_graph(m);
     void* bufs[] = {m->state[0], m->state[1], m->geoA, m->geoB, m->topo, m->gm2, m->zdev, m->perm,
                     m->stage[0], m->stage[1], m->stage[2], m->small, m->act[0], m->act[1], m->act[2],
-                    m->ecells, m->eln, m->eflux, m->esrc, m->eidx};
+                    m->ecells, m->eln, m->eflux, m->esrc, m->eidx, m->geoR, m->erl};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
@@ -601,6 +621,7 @@ int swe_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* tris, i
     const size_t v4 = 4 * m->esz;
     if ((rc = dev_alloc(m, &m->state[0], n * v4, "state")) || (rc = dev_alloc(m, &m->state[1], n * v4, "state")) ||
         (rc = dev_alloc(m, &m->geoA, n * v4, "geometry")) || (rc = dev_alloc(m, &m->geoB, n * v4, "geometry")) ||
+        (c.precision == SWE_FP64 && (rc = dev_alloc(m, &m->geoR, n * v4, "geometry"))) ||
         (rc = dev_alloc(m, (void**)&m->topo, n * sizeof(int4), "topology")) ||
         (rc = dev_alloc(m, &m->gm2, n * m->esz, "manning")) ||
         (rc = dev_alloc(m, &m->zdev, n * m->esz, "bed")) ||

@@ -83,7 +83,8 @@ __global__ void diag_final_kernel(const double* __restrict__ partial, int nb, do
 // boundary treatment (Section 3.1)
 template <typename T>
 __global__ void diag_boundary_kernel(const V4<T>* __restrict__ cur, const V4<T>* __restrict__ geoA,
-                                     const V4<T>* __restrict__ geoB, const long long* __restrict__ slots,
+                                     const V4<T>* __restrict__ geoB, const V4<T>* __restrict__ geoR,
+                                     const long long* __restrict__ slots,
                                      const int* __restrict__ groups, long long nb, BcTable bc, T g, T h_dry,
                                      int hll, double* __restrict__ q) {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -96,7 +97,12 @@ __global__ void diag_boundary_kernel(const V4<T>* __restrict__ cur, const V4<T>*
     const T lx = j == 0 ? gA.x : (j == 1 ? gA.z : gB.x);
     const T ly = j == 0 ? gA.y : (j == 1 ? gA.w : gB.y);
     const T l2 = lx * lx + ly * ly;
-    const T rl = Ar<T>::rsqrt_(l2);
+    T pre = T(0);
+    if constexpr (sizeof(T) == 8) {
+        const V4<T> gR = geoR[i];
+        pre = j == 0 ? gR.x : (j == 1 ? gR.y : gR.z);
+    }
+    const T rl = edge_rl<T>(pre, l2);   // the step's own edge scale
     const T len = l2 * rl;
     T ui, vi;
     cell_velocity<T>(c.x, c.y, c.z, h_dry, ui, vi);
@@ -157,7 +163,8 @@ int diagnostics_t(swe_mesh* m, swe_diag* out) {
         diag_final_kernel<<<1, 32, 0, st>>>((const double*)partial, nblk, (double*)res);
         if (nb)
             diag_boundary_kernel<T><<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(
-                cur, (const V4<T>*)m->geoA, (const V4<T>*)m->geoB, (const long long*)dslots, (const int*)dgroups, nb,
+                cur, (const V4<T>*)m->geoA, (const V4<T>*)m->geoB, (const V4<T>*)m->geoR, (const long long*)dslots,
+                (const int*)dgroups, nb,
                 m->bc, (T)m->cfg.g, (T)m->cfg.h_dry, m->cfg.flux == SWE_FLUX_HLL ? 1 : 0, (double*)dq);
         e = cudaGetLastError();
     }

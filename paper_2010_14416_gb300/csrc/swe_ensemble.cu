@@ -37,6 +37,7 @@ struct swe_ensemble {
     void* state[2] = {nullptr, nullptr};
     void* geoA = nullptr;
     void* geoB = nullptr;
+    void* geoR = nullptr;             // FP64: 1/|L n| of the three edges
     int4* topo = nullptr;
     void* gm2 = nullptr;
     long long* perm = nullptr;        // per member, relative to the member's base
@@ -60,6 +61,7 @@ struct swe_ensemble {
     int64_t n_edges = 0;
     int2* ecells = nullptr;
     void* eln = nullptr;
+    void* erl = nullptr;
     void* eflux = nullptr;
     void* esrc = nullptr;
     int4* eidx = nullptr;
@@ -138,6 +140,8 @@ EnsArgs<T> ens_args(swe_ensemble* E, int64_t step_index) {
     a.s_out = (V4<T>*)E->state[1 - p2];
     a.geoA = (const V4<T>*)E->geoA;
     a.geoB = (const V4<T>*)E->geoB;
+    a.geoR = (const V4<T>*)E->geoR;
+    a.erl = (const T*)E->erl;
     a.topo = E->topo;
     a.gm2 = (const T*)E->gm2;
     a.tile_member = E->tile_member;
@@ -224,6 +228,7 @@ int ens_build(swe_ensemble* E, swe_mesh* const* M) {
     int rc;
     if ((rc = ens_alloc(E, &E->state[0], off * v4, "state")) || (rc = ens_alloc(E, &E->state[1], off * v4, "state")) ||
         (rc = ens_alloc(E, &E->geoA, off * v4, "geometry")) || (rc = ens_alloc(E, &E->geoB, off * v4, "geometry")) ||
+        (sizeof(T) == 8 && (rc = ens_alloc(E, &E->geoR, off * v4, "geometry"))) ||
         (rc = ens_alloc(E, (void**)&E->topo, off * sizeof(int4), "topology")) ||
         (rc = ens_alloc(E, &E->gm2, off * sizeof(T), "manning")) ||
         (rc = ens_alloc(E, (void**)&E->perm, off * sizeof(long long), "permutation")) ||
@@ -236,8 +241,8 @@ int ens_build(swe_ensemble* E, swe_mesh* const* M) {
     cudaStream_t st = E->stream;
     cudaError_t e = cudaSuccess;
     // zero everything that padding cells read (state, topology filled below)
-    for (void* p : {E->state[0], E->state[1], E->geoA, E->geoB, E->gm2})
-        if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, p == E->gm2 ? off * sizeof(T) : off * v4, st);
+    for (void* p : {E->state[0], E->state[1], E->geoA, E->geoB, E->geoR, E->gm2})
+        if (e == cudaSuccess && p) e = cudaMemsetAsync(p, 0, p == E->gm2 ? off * sizeof(T) : off * v4, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(E->n_active, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return efail(e, "swe_ensemble_create: clear");
     // global boundary groups: 0 = wall, then each member's groups
@@ -269,6 +274,8 @@ int ens_build(swe_ensemble* E, swe_mesh* const* M) {
         e = cudaMemcpyAsync((char*)E->state[0] + b * v4, cur, n * v4, cudaMemcpyDeviceToDevice, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync((char*)E->geoA + b * v4, m->geoA, n * v4, cudaMemcpyDeviceToDevice, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync((char*)E->geoB + b * v4, m->geoB, n * v4, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess && sizeof(T) == 8)
+            e = cudaMemcpyAsync((char*)E->geoR + b * v4, m->geoR, n * v4, cudaMemcpyDeviceToDevice, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync((char*)E->gm2 + b * sizeof(T), m->gm2, n * sizeof(T),
                                                   cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) return efail(e, "swe_ensemble_create: copy");
@@ -337,19 +344,21 @@ int ens_build(swe_ensemble* E, swe_mesh* const* M) {
     // the step, so evaluating each edge once pays; FP32 steps are bound by memory)
     if (sizeof(T) == 8) {
         std::vector<int2> cells;
-        std::vector<double> ln;
+        std::vector<double> ln, rl;
         std::vector<int4> eidx(off, make_int4(-1, -1, -1, 0));
-        for (int k = 0; k < nm; ++k) append_edges(M[k]->hm, E->base[k], cells, ln, eidx.data() + E->base[k]);
+        for (int k = 0; k < nm; ++k) append_edges(M[k]->hm, E->base[k], cells, ln, eidx.data() + E->base[k], &rl);
         const int64_t ne = (int64_t)cells.size();
         const size_t nb = (size_t)std::max<int64_t>(ne, 1);
         if ((rc = ens_alloc(E, (void**)&E->ecells, nb * sizeof(int2), "edges")) ||
             (rc = ens_alloc(E, &E->eln, 2 * nb * sizeof(T), "edges")) ||
+            (rc = ens_alloc(E, &E->erl, nb * sizeof(T), "edges")) ||
             (rc = ens_alloc(E, &E->eflux, nb * sizeof(V4<T>), "edges")) ||
             (rc = ens_alloc(E, &E->esrc, nb * sizeof(T), "edges")) ||
             (rc = ens_alloc(E, (void**)&E->eidx, off * sizeof(int4), "edges")))
             return rc;
         if (ne) e = cudaMemcpy(E->ecells, cells.data(), ne * sizeof(int2), cudaMemcpyHostToDevice);
         if (e == cudaSuccess && ne) e = cudaMemcpy(E->eln, ln.data(), 2 * ne * sizeof(double), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && ne) e = cudaMemcpy(E->erl, rl.data(), ne * sizeof(double), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(E->eidx, eidx.data(), off * sizeof(int4), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return efail(e, "swe_ensemble_create: edges");
         E->n_edges = ne;
@@ -641,7 +650,7 @@ void swe_ensemble_destroy(swe_ensemble* E) {
     void* bufs[] = {E->state[0], E->state[1], E->geoA, E->geoB, E->topo, E->gm2, E->perm, E->tile_member,
                     E->member_first_tile, E->cfl, E->small, E->n_active, E->kind, E->value,
                     E->stage[0], E->stage[1], E->stage[2], E->act[0], E->act[1], E->act[2],
-                    E->ecells, E->eln, E->eflux, E->esrc, E->eidx};
+                    E->ecells, E->eln, E->eflux, E->esrc, E->eidx, E->geoR, E->erl};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (E->cap_stream) cudaStreamDestroy(E->cap_stream);

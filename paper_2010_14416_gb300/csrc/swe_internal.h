@@ -71,7 +71,11 @@ int build_edges(swe_mesh* m);
 // orientation (each once, from its left cell, in the order of that cell):
 // (left, right), the left cell's L n, and into eidx[0 .. H.n_cells) each
 // cell's edge per local edge (-1 on the boundary).
-void append_edges(const HostMesh& H, int64_t base, std::vector<int2>& cells, std::vector<double>& ln, int4* eidx);
+void append_edges(const HostMesh& H, int64_t base, std::vector<int2>& cells, std::vector<double>& ln, int4* eidx,
+                  std::vector<double>* rl = nullptr);
+// 1/|L n| of an edge as every FP64 kernel takes it: 1/sqrt(fma(lx, lx, ly ly)),
+// formed on the host with one rounding per operation (the same on every host).
+double host_edge_rl(double lx, double ly);
 // The activity kernel indexes cells with 32 bits: meshes below this size.
 constexpr int64_t kActivityMaxCells = int64_t(1) << 29;
 // Applies pending boundary-group changes of m to the device.
@@ -90,6 +94,7 @@ struct swe_mesh {
     void* state[2] = {nullptr, nullptr};
     void* geoA = nullptr;
     void* geoB = nullptr;
+    void* geoR = nullptr;              // FP64: V4<double> 1/|L n| of the three edges
     int4* topo = nullptr;
     void* gm2 = nullptr;
     void* zdev = nullptr;
@@ -121,6 +126,7 @@ struct swe_mesh {
     int64_t n_edges = 0;
     int2* ecells = nullptr;            // (left, right)
     void* eln = nullptr;               // [E][2] T, L n outward from the left cell
+    void* erl = nullptr;               // FP64: [E] 1/|L n|
     void* eflux = nullptr;             // V4<T>[E]
     void* esrc = nullptr;              // T[E]
     int4* eidx = nullptr;              // per cell, the edge of each local edge (-1: boundary)

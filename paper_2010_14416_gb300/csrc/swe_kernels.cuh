@@ -52,6 +52,7 @@ struct StepArgs {
     V4<T>* __restrict__ s_out;
     const V4<T>* __restrict__ geoA;    // (L n)_0 x, y, (L n)_1 x, y : outward normals times length
     const V4<T>* __restrict__ geoB;    // (L n)_2 x, y, 1/|Omega|, inscribed radius
+    const V4<T>* __restrict__ geoR;    // FP64: 1/|L n| of the three edges (x, y, z)
     const int4* __restrict__ topo;     // neighbour codes of the 3 edges; .w = g m^2 bits (FP32)
     const T* __restrict__ gm2;         // g m^2 per cell (Manning factor of Eq 32), FP64 only
     const double* dt_read;             // min_i R_i/(c_i+|u_i|) of the current state
@@ -76,6 +77,7 @@ struct StepArgs {
     // evaluated once per step by edge_flux_kernel before the cell pass
     const int2* ecells;                // (left, right) cell of each interior edge
     const T* eln;                      // [E][2] L n of the edge, outward from the left cell
+    const T* erl;                      // FP64: 1/|L n| of the edge
     V4<T>* eflux;                      // (F0, F1, F2, bed source factor of the left cell) per edge
     T* esrc;                           // bed source factor of the right cell per edge
     const int4* eidx;                  // per cell: the interior edge of each local edge (x, y, z)
@@ -96,6 +98,7 @@ struct EnsArgs {
     V4<T>* __restrict__ s_out;
     const V4<T>* __restrict__ geoA;
     const V4<T>* __restrict__ geoB;
+    const V4<T>* __restrict__ geoR;    // FP64: 1/|L n| of the three edges
     const int4* __restrict__ topo;     // neighbour codes offset to the concatenated numbering
     const T* __restrict__ gm2;         // FP64 only
     const int* __restrict__ tile_member;               // member of each kEnsPad-cell span
@@ -114,6 +117,7 @@ struct EnsArgs {
     // edge pass over the concatenated members (ensemble_step_kernel with EDGES)
     const int2* ecells;
     const T* eln;
+    const T* erl;
     V4<T>* eflux;
     T* esrc;
     const int4* eidx;
@@ -151,6 +155,17 @@ template <typename T>
 __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
 template <typename T>
 __device__ __forceinline__ T tmin(T a, T b) { return a < b ? a : b; }
+
+// 1/|L n| of an edge.  FP64 takes it precomputed (the host forms
+// 1/sqrt(fma(lx, lx, ly ly)) once per cell edge, the same on every host): the
+// square root and division are a quarter of the flux pass's FP64 work, and the
+// FP64 pipe bounds that path.  FP32 forms it with the hardware reciprocal
+// square root, since memory bounds that path.
+template <typename T>
+__device__ __forceinline__ T edge_rl(T pre, T l2) {
+    if constexpr (sizeof(T) == 8) return pre;
+    else return Ar<T>::rsqrt_(l2);
+}
 
 // ---- Riemann flux in the edge-normal frame (Eq 14, 17-26) -------------------------
 // Input U_K = (h_K, h_K un_K, h_K ut_K) given as depth and normal/tangential
@@ -435,11 +450,12 @@ __device__ __forceinline__ T update_cell(const Args& a, long long i, const V4<T>
     V4<T> nb[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) nb[j] = code[j] >= 0 ? a.s_in[code[j] & kNbrMask] : own;
-    V4<T> gA, gB;
+    V4<T> gA, gB, gR;
     T gm2;
     if constexpr (GEO_EARLY) {
         gA = a.geoA[i];
         gB = a.geoB[i];
+        if constexpr (sizeof(T) == 8) gR = a.geoR[i];
         gm2 = load_gm2(a, i, tp, T(0));
     }
     bool quiet = !(hi > h_dry);
@@ -463,8 +479,10 @@ __device__ __forceinline__ T update_cell(const Args& a, long long i, const V4<T>
     if constexpr (!GEO_EARLY) {
         gA = a.geoA[i];
         gB = a.geoB[i];
+        if constexpr (sizeof(T) == 8) gR = a.geoR[i];
         gm2 = load_gm2(a, i, tp, T(0));
     }
+    if constexpr (sizeof(T) != 8) gR = gA;   // unused: FP32 forms 1/|L n| itself
     T ui, vi;
     cell_velocity<T>(hi, own.y, own.z, h_dry, ui, vi);
     T f0 = T(0), f1 = T(0), f2 = T(0), sx = T(0), sy = T(0);
@@ -477,7 +495,7 @@ __device__ __forceinline__ T update_cell(const Args& a, long long i, const V4<T>
         const T lx = j == 0 ? gA.x : (j == 1 ? gA.z : gB.x);
         const T ly = j == 0 ? gA.y : (j == 1 ? gA.w : gB.y);
         const T l2 = lx * lx + ly * ly;
-        const T rl = A::rsqrt_(l2);
+        const T rl = edge_rl<T>(j == 0 ? gR.x : (j == 1 ? gR.y : gR.z), l2);
         const T len = l2 * rl;
         const T n1 = lx * rl, n2 = ly * rl;     // this cell's outward unit normal
         T F0, F1, F2;
@@ -627,7 +645,9 @@ __global__ void __launch_bounds__(BLOCK) edge_flux_kernel(const StepArgs<T> a) {
         if (!(L.x > h_dry) && !(R.x > h_dry)) continue;
         const T lx = a.eln[2 * e], ly = a.eln[2 * e + 1];
         const T l2 = lx * lx + ly * ly;
-        const T rl = Ar<T>::rsqrt_(l2);
+        T pre = T(0);
+        if constexpr (sizeof(T) == 8) pre = a.erl[e];
+        const T rl = edge_rl<T>(pre, l2);
         const T n1 = lx * rl, n2 = ly * rl;
         T ui, vi;
         cell_velocity<T>(L.x, L.y, L.z, h_dry, ui, vi);

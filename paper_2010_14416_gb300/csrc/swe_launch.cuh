@@ -273,6 +273,7 @@ cudaError_t Launch<T>::ensemble_step(const EnsArgs<T>& a, int block, int min_blo
         ea.s_in = a.s_in;
         ea.ecells = a.ecells;
         ea.eln = a.eln;
+        ea.erl = a.erl;
         ea.eflux = a.eflux;
         ea.esrc = a.esrc;
         ea.n_edges = a.n_edges;
