@@ -38,7 +38,7 @@ ALG_BYTES = {"f32": 16 * 4 + 12, "f64": 16 * 8 + 12}
 # by ncu on the 1M-cell canal (profiles/step_kernel_canal1m_fp64.md): the
 # cell-centric step evaluates every interior flux twice, the edge pass once;
 # quiet cells take no flux path and do no FP64 arithmetic
-FP64_FLOPS_PER_ACTIVE_CELL = {"cell": 855, "edge": 658}
+FP64_FLOPS_PER_ACTIVE_CELL = {"cell": 788, "edge": 542}
 # GB300 FP64: 2 DFMA per clock per SM, 152 SMs
 FP64_DFMA_PER_CLK_SM, N_SM = 2, 152
 
@@ -454,12 +454,14 @@ def run_gpu_ensemble(args, name):
     if dist:
         dist.barrier()
     torch.cuda.synchronize(dev)
+    active0 = ens.info(0)["n_active"]
     ev0.record(stream)
     ens.step(args.steps, sync=False)
     ev1.record(stream)
     torch.cuda.synchronize(dev)
     ms = ev0.elapsed_time(ev1)
     clk = clocks.stop() if rank == 0 else None
+    active_frac = (ens.info(0)["n_active"] - active0) / float(n * args.steps)
     # per-member launches of the plain solver, same steps; each member's launch
     # shape is autotuned on its own mesh as well
     member_shapes = []
@@ -496,9 +498,22 @@ def run_gpu_ensemble(args, name):
         "per_member_launches": {"value": ws * n * args.steps / (ms_plain * 1e-3), "unit": "cell-updates/s",
                                 "ms_per_step": ms_plain / args.steps},
         "speedup_vs_per_member": ms_plain / ms,
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * (2 if shape.get("edge_pass") else 1),
         "clocks": clk,
     }
+    if wl["precision"] == "f64":
+        # bound by the FP64 pipe, as the plain FP64 step (the HBM figures stay as context)
+        sm_mhz = _peak_clock()
+        peak64 = FP64_DFMA_PER_CLK_SM * 2 * N_SM * sm_mhz * 1e6 / 1e12
+        per_cell = FP64_FLOPS_PER_ACTIVE_CELL["edge" if shape.get("edge_pass") else "cell"]
+        ach64 = per_cell * active_frac * n / (kernel_ms * 1e-3) / 1e12
+        hbm = line["roofline"]
+        line["roofline"] = {"bound": "alu", "achieved": ach64, "peak": peak64, "unit": "TFLOP/s",
+                            "frac": ach64 / peak64, "traffic": None,
+                            "peak_source": f"derived: {FP64_DFMA_PER_CLK_SM} DFMA/clk/SM x 2 flops x {N_SM} SMs x "
+                                           f"{sm_mhz:.0f} MHz (FP64 pipe)",
+                            "flops_per_active_cell": per_cell, "active_cell_fraction": active_frac,
+                            "hbm": {k: v for k, v in hbm.items() if k not in ("bound", "traffic")}}
     ens.close()
     for m in meshes:
         m.close()
