@@ -408,7 +408,9 @@ typedef struct swe_tune {
     int stages;              /* chosen cp.async staging depth (1 = direct loads) */
     int geometry_early;      /* chosen geometry load placement (swe_config.geometry_early) */
     int activity;            /* chosen activity mode (swe_config.activity) */
-    int edge_pass;           /* chosen edge-pass mode (swe_config.edge_pass; 0 for ensembles) */
+    int edge_pass;           /* chosen edge-pass mode (swe_config.edge_pass) */
+    int dynamic;             /* ensembles: 1 = blocks take chunks from a per-step counter as they
+                                finish, 0 = fixed round-robin chunks; 0 for a mesh */
     int chunk;               /* ensembles: tiles per round-robin chunk; 0 for a mesh */
     int64_t grid;            /* blocks launched per step */
     double cells_per_thread; /* cells each thread updates per step: cells / (grid * block_size) */
@@ -441,8 +443,11 @@ SWE_API int swe_autotune(swe_mesh* mesh, int trial_steps, swe_tune* out);
  * 1|2, 0), (256|128, 1, 1, 1)) and its activity-mode shapes (activity 1,
  * stages 3: FP32 (128, 8) and (256, 4) with geometry_early 0|1; FP64
  * (256|128, 1) with 0), and for FP64 ensembles its edge-pass shapes
- * (edge_pass 1: (256|128, 1, 1, 0)), times chunks of 4 to 64 tiles, then grids
- * of half, one and two resident waves for the best of those.  Members' states, times and
+ * (edge_pass 1: (256|128, 1, 1, 0)), times chunks of 4 to 64 tiles; and its
+ * dynamically scheduled shapes (dynamic 1, stages 1: FP32 (128, 8) with
+ * geometry_early 0|1, (256, 4) with 0; FP64 (128|256, 1) with 0) with chunks
+ * of 1 to 32 tiles; then grids of half, one and two resident waves for the
+ * best of those.  Members' states, times and
  * steps are unchanged by the call and by the choice.  trial_steps 0 = 4.
  */
 SWE_API int swe_ensemble_autotune(swe_ensemble* ens, int trial_steps, swe_tune* out);
@@ -450,9 +455,10 @@ SWE_API int swe_ensemble_autotune(swe_ensemble* ens, int trial_steps, swe_tune* 
 /*
  * Sets an ensemble's launch shape directly (for instance one that
  * swe_ensemble_autotune chose earlier): block_size, min_blocks, stages,
- * geometry_early, activity and edge_pass must name a compiled shape (listed
- * above; stages is ignored with activity; edge_pass only for FP64 ensembles
- * and not with activity), chunk a power of two up to 4096 tiles,
+ * geometry_early, activity, edge_pass and dynamic must name a compiled shape
+ * (listed above; stages is ignored with activity; edge_pass only for FP64
+ * ensembles; at most one of activity, edge_pass, dynamic), chunk a power of
+ * two up to 4096 tiles,
  * grid the blocks to launch (0 = one resident wave); other fields are
  * ignored.  Results do not depend on the shape.  Errors: SWE_EINVAL.
  */

@@ -58,7 +58,7 @@ class swe_diag(C.Structure):
 
 class swe_tune(C.Structure):
     _fields_ = [("block_size", C.c_int), ("min_blocks", C.c_int), ("stages", C.c_int), ("geometry_early", C.c_int),
-                ("activity", C.c_int), ("edge_pass", C.c_int), ("chunk", C.c_int),
+                ("activity", C.c_int), ("edge_pass", C.c_int), ("dynamic", C.c_int), ("chunk", C.c_int),
                 ("grid", C.c_int64), ("cells_per_thread", C.c_double), ("ms_best", C.c_double),
                 ("ms_before", C.c_double), ("n_candidates", C.c_int)]
 
@@ -380,10 +380,10 @@ class Ensemble:
         return {k: getattr(t, k) for k, _ in swe_tune._fields_}
 
     def set_shape(self, block_size, min_blocks, stages=1, geometry_early=0, activity=0, chunk=4, grid=0,
-                  edge_pass=0):
+                  edge_pass=0, dynamic=0):
         """Sets the batched kernel's launch shape (see swe_ensemble_set_shape)."""
         t = swe_tune(block_size=block_size, min_blocks=min_blocks, stages=stages, geometry_early=geometry_early,
-                     activity=activity, edge_pass=edge_pass, chunk=chunk, grid=grid)
+                     activity=activity, edge_pass=edge_pass, dynamic=dynamic, chunk=chunk, grid=grid)
         check(load().swe_ensemble_set_shape(self._h, C.byref(t)))
 
     def info(self, member):

@@ -59,6 +59,9 @@ struct swe_ensemble {
     // edge pass (FP64 ensembles): the members' interior edges, concatenated
     int edges = 0;
     int64_t n_edges = 0;
+    // dynamic chunks: three rotating per-step counters
+    int dynamic = 0;
+    unsigned* sched = nullptr;
     int2* ecells = nullptr;
     void* eln = nullptr;
     void* erl = nullptr;
@@ -153,6 +156,9 @@ EnsArgs<T> ens_args(swe_ensemble* E, int64_t step_index) {
     a.n_active = E->n_active;
     a.n_total = E->n_total;
     a.chunk_log2 = E->chunk_log2;
+    a.sched = E->sched;
+    a.sched_slot = p3;
+    a.sched_reset = (p3 + 2) % 3;
     a.ecells = nullptr;
     a.eln = nullptr;
     a.eflux = nullptr;
@@ -194,6 +200,7 @@ cudaError_t ens_launch(swe_ensemble* E, int64_t step_index, const EnsPhysics& ph
     a.g = (T)ph.g;
     a.h_dry = (T)ph.h_dry;
     if (a.act_in) return Launch<T>::ensemble_step_act(a, E->block, E->min_blocks, E->geo_early, E->grid, st);
+    if (E->dynamic) return Launch<T>::ensemble_step_dyn(a, E->block, E->min_blocks, E->geo_early, E->grid, st);
     return Launch<T>::ensemble_step(a, E->block, E->min_blocks, E->stages, E->geo_early, E->grid, st);
 }
 
@@ -236,7 +243,8 @@ int ens_build(swe_ensemble* E, swe_mesh* const* M) {
         (rc = ens_alloc(E, (void**)&E->member_first_tile, nm * sizeof(long long), "tiles")) ||
         (rc = ens_alloc(E, (void**)&E->cfl, nm * sizeof(double), "cfl")) ||
         (rc = ens_alloc(E, (void**)&E->small, nm * 8 * sizeof(unsigned long long), "status")) ||
-        (rc = ens_alloc(E, (void**)&E->n_active, sizeof(unsigned long long), "status")))
+        (rc = ens_alloc(E, (void**)&E->n_active, sizeof(unsigned long long), "status")) ||
+        (rc = ens_alloc(E, (void**)&E->sched, 3 * sizeof(unsigned), "status")))
         return rc;
     cudaStream_t st = E->stream;
     cudaError_t e = cudaSuccess;
@@ -244,6 +252,7 @@ int ens_build(swe_ensemble* E, swe_mesh* const* M) {
     for (void* p : {E->state[0], E->state[1], E->geoA, E->geoB, E->geoR, E->gm2})
         if (e == cudaSuccess && p) e = cudaMemsetAsync(p, 0, p == E->gm2 ? off * sizeof(T) : off * v4, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(E->n_active, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(E->sched, 0, 3 * sizeof(unsigned), st);
     if (e != cudaSuccess) return efail(e, "swe_ensemble_create: clear");
     // global boundary groups: 0 = wall, then each member's groups
     std::vector<int> kinds{kBcWall};
@@ -457,6 +466,7 @@ struct EnsShape {
     unsigned grid;
     int activity;
     int edges;
+    int dynamic;
 };
 
 template <typename T>
@@ -465,7 +475,9 @@ int ens_time_shapes(swe_ensemble* E, const std::vector<EnsShape>& cand, int tria
     cudaStream_t st = E->stream;
     const int rounds = 2;
     std::vector<cudaEvent_t> ev(2 * rounds * cand.size(), nullptr);
-    cudaError_t e = cudaSuccess;
+    // the dynamic kernels' counters rotate per trial launch, as per step
+    cudaError_t e = cudaMemsetAsync(E->sched, 0, 3 * sizeof(unsigned), st);
+    int launch_no = 0;
     for (auto& x : ev)
         if (e == cudaSuccess) e = cudaEventCreate(&x);
     for (int r = 0; r < rounds && e == cudaSuccess; ++r)
@@ -492,9 +504,14 @@ int ens_time_shapes(swe_ensemble* E, const std::vector<EnsShape>& cand, int tria
             a.act_next = sh.activity ? E->act[(p3 + 1) % 3] : nullptr;
             a.act_clear = sh.activity ? E->act[(p3 + 2) % 3] : nullptr;
             auto launch = [&]() {
-                return sh.activity ? Launch<T>::ensemble_step_act(a, sh.block, sh.min_blocks, sh.geo_early, sh.grid, st)
-                                   : Launch<T>::ensemble_step(a, sh.block, sh.min_blocks, sh.stages, sh.geo_early,
-                                                              sh.grid, st);
+                a.sched_slot = launch_no % 3;
+                a.sched_reset = (launch_no + 2) % 3;
+                ++launch_no;
+                if (sh.activity)
+                    return Launch<T>::ensemble_step_act(a, sh.block, sh.min_blocks, sh.geo_early, sh.grid, st);
+                if (sh.dynamic)
+                    return Launch<T>::ensemble_step_dyn(a, sh.block, sh.min_blocks, sh.geo_early, sh.grid, st);
+                return Launch<T>::ensemble_step(a, sh.block, sh.min_blocks, sh.stages, sh.geo_early, sh.grid, st);
             };
             e = launch();  // warm-up
             if (e == cudaSuccess) e = cudaEventRecord(ev[2 * (r * cand.size() + c)], st);
@@ -516,8 +533,8 @@ int ens_time_shapes(swe_ensemble* E, const std::vector<EnsShape>& cand, int tria
 
 template <typename T>
 int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
-    const EnsShape before{E->block,     E->min_blocks, E->stages,   E->geo_early,
-                          E->chunk_log2, E->grid,     E->activity, E->edges};
+    const EnsShape before{E->block, E->min_blocks, E->stages,   E->geo_early, E->chunk_log2,
+                          E->grid,  E->activity,   E->edges,    E->dynamic};
     std::vector<EnsShape> cand{before};
     const bool with_act = E->n_total < kActivityMaxCells;
     if (with_act) {
@@ -532,10 +549,10 @@ int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
         if (e != cudaSuccess) return efail(e, "swe_ensemble_autotune: occupancy");
         const unsigned gr = (unsigned)std::max(1LL, std::min((long long)(E->n_total / v[k][0]), wave));
         for (int cl2 = 2; cl2 <= 6; ++cl2) {
-            const EnsShape sh{v[k][0], v[k][1], v[k][2], v[k][3], cl2, gr, 0, 0};
+            const EnsShape sh{v[k][0], v[k][1], v[k][2], v[k][3], cl2, gr, 0, 0, 0};
             if (!(sh.block == before.block && sh.min_blocks == before.min_blocks && sh.stages == before.stages &&
                   sh.geo_early == before.geo_early && sh.chunk_log2 == before.chunk_log2 && sh.grid == before.grid &&
-                  !before.activity && !before.edges))
+                  !before.activity && !before.edges && !before.dynamic))
                 cand.push_back(sh);
         }
     }
@@ -548,7 +565,18 @@ int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
         if (e != cudaSuccess) return efail(e, "swe_ensemble_autotune: occupancy");
         const long long wave = (long long)std::max(per_sm, 1) * std::max(sms, 1);
         const unsigned gr = (unsigned)std::max(1LL, std::min((long long)(E->n_total / w[k][0]), wave));
-        for (int cl2 = 2; cl2 <= 6; ++cl2) cand.push_back({w[k][0], w[k][1], 3, w[k][2], cl2, gr, 1, 0});
+        for (int cl2 = 2; cl2 <= 6; ++cl2) cand.push_back({w[k][0], w[k][1], 3, w[k][2], cl2, gr, 1, 0, 0});
+    }
+    int y[16][3];
+    const int ny = std::min(Launch<T>::ensemble_dyn_variants(y, 16), 16);
+    for (int k = 0; k < ny; ++k) {
+        int per_sm = 0, sms = 0;
+        cudaError_t e = Launch<T>::ensemble_dyn_resident_blocks(y[k][0], y[k][1], y[k][2], &per_sm);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, E->device);
+        if (e != cudaSuccess) return efail(e, "swe_ensemble_autotune: occupancy");
+        const long long wave = (long long)std::max(per_sm, 1) * std::max(sms, 1);
+        const unsigned gr = (unsigned)std::max(1LL, std::min((long long)(E->n_total / y[k][0]), wave));
+        for (int cl2 = 0; cl2 <= 5; ++cl2) cand.push_back({y[k][0], y[k][1], 1, y[k][2], cl2, gr, 0, 0, 1});
     }
     int x[16][4];
     const int nx = E->eflux ? std::min(Launch<T>::ensemble_edge_variants(x, 16), 16) : 0;
@@ -559,7 +587,7 @@ int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
         if (e != cudaSuccess) return efail(e, "swe_ensemble_autotune: occupancy");
         const long long wave = (long long)std::max(per_sm, 1) * std::max(sms, 1);
         const unsigned gr = (unsigned)std::max(1LL, std::min((long long)(E->n_total / x[k][0]), wave));
-        for (int cl2 = 2; cl2 <= 6; ++cl2) cand.push_back({x[k][0], x[k][1], x[k][2], x[k][3], cl2, gr, 0, 1});
+        for (int cl2 = 2; cl2 <= 6; ++cl2) cand.push_back({x[k][0], x[k][1], x[k][2], x[k][3], cl2, gr, 0, 1, 0});
     }
     void* scratch = nullptr;
     unsigned long long *small = nullptr, *act = nullptr;
@@ -584,11 +612,12 @@ int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
         while (ms[best] > fastest * 1.02) ++best;
         long long wave = 0;
         const EnsShape b = cand[best];
-        if (b.activity || b.edges) {
+        if (b.activity || b.edges || b.dynamic) {
             int per_sm = 0, sms = 0;
-            e = b.activity ? Launch<T>::ensemble_act_resident_blocks(b.block, b.min_blocks, b.geo_early, &per_sm)
-                           : Launch<T>::ensemble_edge_resident_blocks(b.block, b.min_blocks, b.stages, b.geo_early,
-                                                                      &per_sm);
+            e = b.activity  ? Launch<T>::ensemble_act_resident_blocks(b.block, b.min_blocks, b.geo_early, &per_sm)
+                : b.dynamic ? Launch<T>::ensemble_dyn_resident_blocks(b.block, b.min_blocks, b.geo_early, &per_sm)
+                            : Launch<T>::ensemble_edge_resident_blocks(b.block, b.min_blocks, b.stages, b.geo_early,
+                                                                       &per_sm);
             if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, E->device);
             wave = (long long)std::max(per_sm, 1) * std::max(sms, 1);
         } else {
@@ -599,11 +628,17 @@ int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
         for (long long gsz : {wave / 2, 2 * wave}) {
             const unsigned gr = (unsigned)std::max(1LL, std::min(tiles, gsz));
             if (!rc && gr != b.grid)
-                cand2.push_back({b.block, b.min_blocks, b.stages, b.geo_early, b.chunk_log2, gr, b.activity, b.edges});
+                cand2.push_back(
+                    {b.block, b.min_blocks, b.stages, b.geo_early, b.chunk_log2, gr, b.activity, b.edges, b.dynamic});
         }
         if (!rc && !cand2.empty()) rc = ens_time_shapes<T>(E, cand2, trial_steps, scratch, small, act, ms2);
     }
     for (void* p : {scratch, (void*)small, (void*)act}) cudaFree(p);
+    // the trials consumed the dynamic kernels' counters: the steps start from zero
+    if (!rc) {
+        const cudaError_t ze = cudaMemsetAsync(E->sched, 0, 3 * sizeof(unsigned), E->stream);
+        if (ze != cudaSuccess) rc = efail(ze, "swe_ensemble_autotune: counters");
+    }
     if (rc) return rc;
     EnsShape pick = cand[best];
     double ms_pick = ms[best];
@@ -615,6 +650,7 @@ int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
     E->geo_early = pick.geo_early;
     E->activity = pick.activity;
     E->edges = pick.edges;
+    E->dynamic = pick.dynamic;
     // the bytes describe the current state (the trials rewrote the next buffer with
     // what the next step writes there); without activity they would go stale
     E->act_valid = pick.activity != 0 && E->act[0] != nullptr;
@@ -628,6 +664,7 @@ int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
         out->geometry_early = pick.geo_early;
         out->activity = pick.activity;
         out->edge_pass = pick.edges;
+        out->dynamic = pick.dynamic;
         out->chunk = 1 << pick.chunk_log2;
         out->grid = pick.grid;
         out->cells_per_thread = (double)E->n_total / ((double)pick.grid * pick.block);
@@ -650,7 +687,7 @@ void swe_ensemble_destroy(swe_ensemble* E) {
     void* bufs[] = {E->state[0], E->state[1], E->geoA, E->geoB, E->topo, E->gm2, E->perm, E->tile_member,
                     E->member_first_tile, E->cfl, E->small, E->n_active, E->kind, E->value,
                     E->stage[0], E->stage[1], E->stage[2], E->act[0], E->act[1], E->act[2],
-                    E->ecells, E->eln, E->eflux, E->esrc, E->eidx, E->geoR, E->erl};
+                    E->ecells, E->eln, E->eflux, E->esrc, E->eidx, E->geoR, E->erl, E->sched};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (E->cap_stream) cudaStreamDestroy(E->cap_stream);
@@ -771,7 +808,8 @@ int swe_ensemble_step(swe_ensemble* E, int64_t nsteps, const double* cfl, double
 
 int swe_ensemble_set_shape(swe_ensemble* E, const swe_tune* shape) {
     if (!E || !shape || (shape->activity != 0 && shape->activity != 1) || (shape->edge_pass != 0 && shape->edge_pass != 1) ||
-        (shape->edge_pass && (shape->activity || !E->eflux)) ||
+        (shape->dynamic != 0 && shape->dynamic != 1) || shape->activity + shape->edge_pass + shape->dynamic > 1 ||
+        (shape->edge_pass && !E->eflux) ||
         shape->chunk < 1 || (shape->chunk & (shape->chunk - 1)) || shape->chunk > 4096 || shape->grid < 0) {
         set_error("swe_ensemble_set_shape: bad arguments");
         return SWE_EINVAL;
@@ -783,19 +821,17 @@ int swe_ensemble_set_shape(swe_ensemble* E, const swe_tune* shape) {
     EnsDeviceGuard dg(E->device);
     int per_sm = 0, sms = 0;
     cudaError_t e;
-    if (E->precision == SWE_FP32)
-        e = shape->activity ? Launch<float>::ensemble_act_resident_blocks(shape->block_size, shape->min_blocks,
-                                                                          shape->geometry_early, &per_sm)
-                            : Launch<float>::ensemble_resident_blocks(shape->block_size, shape->min_blocks,
-                                                                      shape->stages, shape->geometry_early, &per_sm);
-    else if (shape->edge_pass)
-        e = Launch<double>::ensemble_edge_resident_blocks(shape->block_size, shape->min_blocks, shape->stages,
-                                                          shape->geometry_early, &per_sm);
-    else
-        e = shape->activity ? Launch<double>::ensemble_act_resident_blocks(shape->block_size, shape->min_blocks,
-                                                                           shape->geometry_early, &per_sm)
-                            : Launch<double>::ensemble_resident_blocks(shape->block_size, shape->min_blocks,
-                                                                       shape->stages, shape->geometry_early, &per_sm);
+    const int B = shape->block_size, M = shape->min_blocks, S = shape->stages, Gx = shape->geometry_early;
+    if (E->precision == SWE_FP32) {
+        if (shape->dynamic) e = Launch<float>::ensemble_dyn_resident_blocks(B, M, Gx, &per_sm);
+        else if (shape->activity) e = Launch<float>::ensemble_act_resident_blocks(B, M, Gx, &per_sm);
+        else e = Launch<float>::ensemble_resident_blocks(B, M, S, Gx, &per_sm);
+    } else {
+        if (shape->dynamic) e = Launch<double>::ensemble_dyn_resident_blocks(B, M, Gx, &per_sm);
+        else if (shape->activity) e = Launch<double>::ensemble_act_resident_blocks(B, M, Gx, &per_sm);
+        else if (shape->edge_pass) e = Launch<double>::ensemble_edge_resident_blocks(B, M, S, Gx, &per_sm);
+        else e = Launch<double>::ensemble_resident_blocks(B, M, S, Gx, &per_sm);
+    }
     if (e == cudaErrorInvalidValue) {
         set_error("swe_ensemble_set_shape: no compiled ensemble kernel of this shape");
         return SWE_EINVAL;
@@ -808,13 +844,18 @@ int swe_ensemble_set_shape(swe_ensemble* E, const swe_tune* shape) {
     while ((1LL << cl2) < shape->chunk) ++cl2;
     E->block = shape->block_size;
     E->min_blocks = shape->min_blocks;
-    E->stages = shape->activity ? 3 : shape->stages;
+    E->stages = shape->activity ? 3 : (shape->dynamic ? 1 : shape->stages);
     E->geo_early = shape->geometry_early;
     E->chunk_log2 = (int)cl2;
     E->grid = (unsigned)std::max(1LL, std::min(tiles, shape->grid > 0 ? (long long)shape->grid : wave));
     if (E->activity != shape->activity) E->act_valid = false;
     E->activity = shape->activity;
     E->edges = shape->edge_pass;
+    E->dynamic = shape->dynamic;
+    if (E->dynamic) {   // counters from zero (earlier steps may have left them used)
+        e = cudaMemsetAsync(E->sched, 0, 3 * sizeof(unsigned), E->stream);
+        if (e != cudaSuccess) return efail(e, "swe_ensemble_set_shape: counters");
+    }
     drop_graphs(E);
     return SWE_OK;
 }

@@ -110,6 +110,10 @@ struct EnsArgs {
     unsigned long long* n_active;      // all members (diagnostic)
     long long n_total;                 // cells of the padded layout (a multiple of kEnsPad)
     int chunk_log2;                    // tiles per round-robin chunk = 2^chunk_log2
+    // dynamic chunks (ensemble_step_kernel_dyn): three rotating counters; the
+    // step takes chunks from sched[sched_slot] and zeroes sched[sched_reset]
+    unsigned* sched;
+    int sched_slot, sched_reset;
     // activity bytes over the concatenated layout (ensemble_step_kernel_act)
     const unsigned char* act_in;
     unsigned char* act_next;
@@ -915,6 +919,69 @@ __global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel(const EnsArg
     if ((tid & 31) == 0 && active) atomicAdd(a.n_active, (unsigned long long)active);
 }
 
+// ---- batched ensemble step with dynamically taken chunks ------------------------------
+// Each block takes its next chunk of 2^chunk_log2 tiles from a per-step
+// counter (one atomicAdd per chunk, taken one chunk ahead), so blocks that
+// drew cheap (dry) chunks take more of them and the grid finishes together.
+// Which block updates a cell changes nothing in the cell's arithmetic, and the
+// per-member minimum and the counters are order-independent: the results are
+// those of the static schedule bit for bit.
+template <typename T, int BLOCK, int MINB, bool GEO_EARLY>
+__global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel_dyn(const EnsArgs<T> a) {
+    static_assert(kEnsPad % BLOCK == 0, "a tile must not straddle two members");
+    const int cl2 = a.chunk_log2;
+    const long long n_tiles = a.n_total / BLOCK;
+    const unsigned n_chunks = (unsigned)((n_tiles + (1LL << cl2) - 1) >> cl2);
+    const int tid = threadIdx.x;
+    __shared__ unsigned s_chunk[2];
+    if (blockIdx.x == 0 && tid == 0) a.sched[a.sched_reset] = 0u;   // the counter of the step after next
+    if (tid == 0) s_chunk[0] = atomicAdd(&a.sched[a.sched_slot], 1u);
+    __syncthreads();
+    int member = -1;
+    unsigned long long* sm = nullptr;
+    bool have_dt = false;
+    T dt = T(0);
+    T cand = inf_of<T>();
+    unsigned active = 0u;
+    unsigned chunk = s_chunk[0];
+    for (int it = 0; chunk < n_chunks; ++it) {
+        if (tid == 0) s_chunk[(it + 1) & 1] = atomicAdd(&a.sched[a.sched_slot], 1u);   // the next chunk, ahead
+        const long long t0 = (long long)chunk << cl2;
+        for (int q = 0; q < (1 << cl2); ++q) {
+            const long long tile = t0 + q;
+            if (tile >= n_tiles) break;                    // ragged last chunk
+            const long long cell0 = tile * BLOCK;
+            const int mk = a.tile_member[cell0 / kEnsPad];  // uniform across the block
+            if (mk != member) {
+                if (member >= 0) warp_min_publish<T>(cand, sm + a.slot_write);
+                cand = inf_of<T>();
+                member = mk;
+                sm = a.small + 8 * (long long)mk;
+                const WarpDt<T> wdt = warp_step_dt<T>(a.cfl[mk], (const double*)(sm + a.slot_read), nullptr);
+                have_dt = wdt.have;
+                dt = wdt.t;
+                if (cell0 == a.member_first_tile[mk] * kEnsPad && tid == 0) {
+                    sm[a.slot_reset] = kInfBits;
+                    if (have_dt) *(double*)(sm + 3) += wdt.d;
+                    else atomicOr((unsigned*)(sm + 4), kStatusDry);
+                }
+            }
+            const long long i = cell0 + tid;
+            const V4<T> own = a.s_in[i];
+            const int4 tp = a.topo[i];
+            if (have_dt)
+                cand = tmin(cand, update_cell<T, GEO_EARLY>(a, i, own, tp, dt, active, sm + 5, (unsigned*)(sm + 4)));
+            else
+                a.s_out[i] = own;
+        }
+        __syncthreads();   // the next chunk's index is visible, and every thread has read this one
+        chunk = s_chunk[(it + 1) & 1];
+    }
+    if (member >= 0) warp_min_publish<T>(cand, sm + a.slot_write);
+    active = __reduce_add_sync(0xffffffffu, active);
+    if ((tid & 31) == 0 && active) atomicAdd(a.n_active, (unsigned long long)active);
+}
+
 // ---- batched ensemble step with activity bytes ----------------------------------------
 // The activity mode of step_kernel_act over the concatenated members: the same
 // bytes, marks and per-thread cp.async pipeline, with the thread's cells taken
@@ -1133,6 +1200,11 @@ struct Launch {
     // edge pass of the ensemble (a.eflux set): edge kernel, then the cell pass of
     // one of its compiled (block, min_blocks, stages, geo_early) shapes
     static int ensemble_edge_variants(int (*out)[4], int max);
+    // dynamically scheduled ensemble kernel: compiled (block, min_blocks, geo_early) shapes
+    static cudaError_t ensemble_step_dyn(const EnsArgs<T>& a, int block, int min_blocks, int geo_early,
+                                         unsigned grid, cudaStream_t st);
+    static cudaError_t ensemble_dyn_resident_blocks(int block, int min_blocks, int geo_early, int* per_sm);
+    static int ensemble_dyn_variants(int (*out)[3], int max);
     static cudaError_t ensemble_edge_resident_blocks(int block, int min_blocks, int stages, int geo_early,
                                                      int* per_sm);
     static void ensemble_default(int* block, int* min_blocks, int* stages, int* geo_early);

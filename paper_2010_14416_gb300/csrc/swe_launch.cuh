@@ -375,6 +375,57 @@ int Launch<T>::ensemble_act_variants(int (*out)[3], int max) {
     return k;
 }
 
+// (block, min blocks per SM, geometry early) shapes of the dynamically scheduled ensemble kernel
+#define SWE_ENS_DYN_VARIANTS_F32(X) X(128, 8, 0) X(128, 8, 1) X(256, 4, 0)
+#define SWE_ENS_DYN_VARIANTS_F64(X) X(128, 1, 0) X(256, 1, 0)
+
+template <typename T>
+cudaError_t Launch<T>::ensemble_step_dyn(const EnsArgs<T>& a, int block, int min_blocks, int geo_early,
+                                         unsigned grid, cudaStream_t st) {
+    if (grid == 0 || !a.sched) return cudaErrorInvalidValue;
+#define SWE_LAUNCH(B, M, G) \
+    if (block == B && min_blocks == M && geo_early == G) {                        \
+        ensemble_step_kernel_dyn<T, B, M, G != 0><<<grid, B, 0, st>>>(a);        \
+        return cudaGetLastError();                                                \
+    }
+    if constexpr (sizeof(T) == 4) {
+        SWE_ENS_DYN_VARIANTS_F32(SWE_LAUNCH)
+    } else {
+        SWE_ENS_DYN_VARIANTS_F64(SWE_LAUNCH)
+    }
+#undef SWE_LAUNCH
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t Launch<T>::ensemble_dyn_resident_blocks(int block, int min_blocks, int geo_early, int* per_sm) {
+#define SWE_OCC(B, M, G) \
+    if (block == B && min_blocks == M && geo_early == G)                          \
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, ensemble_step_kernel_dyn<T, B, M, G != 0>, B, 0);
+    if constexpr (sizeof(T) == 4) {
+        SWE_ENS_DYN_VARIANTS_F32(SWE_OCC)
+    } else {
+        SWE_ENS_DYN_VARIANTS_F64(SWE_OCC)
+    }
+#undef SWE_OCC
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+int Launch<T>::ensemble_dyn_variants(int (*out)[3], int max) {
+    int k = 0;
+#define SWE_LIST(B, M, G) \
+    if (k < max) { out[k][0] = B; out[k][1] = M; out[k][2] = G; } \
+    ++k;
+    if constexpr (sizeof(T) == 4) {
+        SWE_ENS_DYN_VARIANTS_F32(SWE_LIST)
+    } else {
+        SWE_ENS_DYN_VARIANTS_F64(SWE_LIST)
+    }
+#undef SWE_LIST
+    return k;
+}
+
 template <typename T>
 cudaError_t Launch<T>::dt(const V4<T>* s, const V4<T>* geoB, long long n, T g, T h_dry,
                           unsigned long long* dt_write, cudaStream_t st) {

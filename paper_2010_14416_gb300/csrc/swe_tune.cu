@@ -201,6 +201,7 @@ int autotune_t(swe_mesh* m, int trial_steps, swe_tune* out) {
         out->geometry_early = pick.geo_early;
         out->activity = pick.activity;
         out->edge_pass = pick.edges;
+        out->dynamic = 0;
         out->chunk = 0;
         out->grid = pick.grid;
         out->cells_per_thread = (double)n / ((double)pick.grid * pick.block);

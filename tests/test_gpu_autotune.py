@@ -97,10 +97,11 @@ def test_ensemble_autotune_keeps_state_and_results(precision):
         inf = ens.info(k)
         assert inf["t"] == infos[k]["t"] and inf["dt_next"] == infos[k]["dt_next"]
         assert inf["n_active"] == infos[k]["n_active"]
-    assert ch["block_size"] in (128, 256) and ch["chunk"] in (4, 8, 16, 32, 64)
+    assert ch["block_size"] in (128, 256) and ch["chunk"] in (1, 2, 4, 8, 16, 32, 64)
     assert ch["geometry_early"] in (0, 1) and ch["activity"] in (0, 1) and ch["edge_pass"] in (0, 1)
     assert not (ch["activity"] and ch["edge_pass"])
     assert ch["edge_pass"] == 0 or precision == capi.SWE_FP64
+    assert ch["dynamic"] in (0, 1) and ch["activity"] + ch["edge_pass"] + ch["dynamic"] <= 1
     assert ch["n_candidates"] >= 20 and 0 < ch["ms_best"] <= ch["ms_before"]
     t_ens = ens.step(90, cfl)
     for k, m in enumerate(meshes):
