@@ -289,3 +289,32 @@ def test_hll_scheme_conserves_and_balances():
     M2 = oracle.Mesh(mi.nodes, mi.tris, mi.z, mi.manning)
     h2, hu2, hv2, t2, c2 = M2.run(mi.h, mi.hu, mi.hv, 300, 0.9)
     assert not np.array_equal(hv, hv2)
+
+
+def test_quiet_cells_keep_their_depth_and_come_to_rest_exactly():
+    # A dry cell (h <= h_dry) whose neighbours are all dry and whose boundary
+    # edges are walls sees only mass fluxes of exactly zero (both Riemann
+    # states dry, walls carry no mass): its depth is unchanged bit for bit and
+    # the dry-cell rule leaves it at rest.  The GPU kernels' quiet path and
+    # activity bytes skip such cells' fluxes on exactly this property.
+    mi = mg.river(120, 24, seed=3)
+    M = _mesh(mi)
+    rng = np.random.default_rng(5)
+    h = mi.h.copy()
+    dry = h <= 1e-6
+    h[dry] = rng.choice([0.0, 3e-7, 9e-7], size=int(dry.sum()))     # dry, some not exactly empty
+    hu = mi.hu.copy()
+    hv = mi.hv.copy()
+    hu[dry] = rng.uniform(-1e-6, 1e-6, int(dry.sum()))             # stray momentum on dry cells
+    hv[dry] = rng.uniform(-1e-6, 1e-6, int(dry.sum()))
+    nbr = M.geometry()["nbr"]
+    interior = nbr >= 0
+    nbr_dry = np.where(interior, dry[np.where(interior, nbr, 0)], True).all(axis=1)
+    walls_only = ((nbr >= 0) | (nbr == -1)).all(axis=1)               # -1: the wall group
+    quiet = dry & nbr_dry & walls_only
+    assert quiet.sum() > 1000 and (dry & ~quiet).sum() > 10          # both kinds of dry cell occur
+    dt = M.dt(h, hu, hv, 0.9)
+    h1, hu1, hv1, c = M.step(h, hu, hv, dt)
+    assert c == 0
+    assert np.array_equal(h1[quiet], h[quiet])
+    assert np.all(hu1[quiet] == 0.0) and np.all(hv1[quiet] == 0.0)
