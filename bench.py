@@ -313,13 +313,16 @@ def run_gpu(args, name):
     if dist:
         dist.barrier()
     torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    m2.set_state(*hp)
-    m2.step(args.steps, 0.9, sync=False)
-    m2.get_state(out)
-    e2e_s = time.perf_counter() - t0
+    # three identical jobs, each timed whole; the median is reported
+    jobs = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        m2.set_state(*hp)
+        m2.step(args.steps, 0.9, sync=False)
+        m2.get_state(out)
+        jobs.append(time.perf_counter() - t0)
     m2.close()
-    e2e_s = max_over_ranks(dist, [e2e_s])[0]
+    e2e_s = max_over_ranks(dist, [sorted(jobs)[1]])[0]
 
     peak, peak_kind = _peaks()
     ab = ALG_BYTES[wl["precision"]]
@@ -374,8 +377,9 @@ def run_gpu(args, name):
         "e2e": {"value": ws * n * args.steps / e2e_s, "unit": "cell-updates/s",
                 "h2d_bytes_per_step": 3 * n * np.dtype(npdt).itemsize / args.steps,
                 "d2h_bytes_per_step": 3 * n * np.dtype(npdt).itemsize / args.steps,
+                "jobs_s": jobs,
                 "note": "one job: swe_set_state from pinned host arrays, swe_step(steps), swe_get_state to "
-                        "pinned host arrays; bytes averaged per step"},
+                        "pinned host arrays, timed whole; median of three jobs; bytes averaged per step"},
         "gpu_launches": args.steps * (2 if shape.get("edge_pass") else 1),
         "clocks": clk,
     }
