@@ -443,7 +443,17 @@ def run_gpu_ensemble(args, name):
     ens.set_stream(stream)
     args.warmup = max(args.warmup, 6)
     ens.step(args.warmup)
-    shape = ens.autotune(4)       # launch shape chosen by the library's autotuner
+    if args.ens_shape:
+        v = [int(x) for x in args.ens_shape.split(",")]
+        keys = ("block_size", "min_blocks", "stages", "geometry_early", "activity", "edge_pass", "dynamic", "chunk",
+                "grid")
+        if len(v) != len(keys):
+            raise SystemExit("--ens-shape needs " + ",".join(keys))
+        shape = dict(zip(keys, v))
+        ens.set_shape(**shape)
+        shape["fixed"] = True
+    else:
+        shape = ens.autotune(4)   # launch shape chosen by the library's autotuner
     ens.step(6)
     # the timed call is captured once (untimed) for its step phase, then replayed
     ens.step(args.steps)
@@ -551,8 +561,10 @@ def run_gpu_adjoint(args, name):
     xi = meshgen.perturbation(n, 101)
     stream = torch.cuda.Stream(device=dev)
 
+    fixed = _shape_kwargs(args.shape)
+
     def mesh(z, man):
-        m = capi.Mesh(mi.nodes, mi.tris, z, man, precision=capi.SWE_FP64, device=local)
+        m = capi.Mesh(mi.nodes, mi.tris, z, man, precision=capi.SWE_FP64, device=local, **fixed)
         for pairs, kind, value in mi.bcs:
             m.set_bc(pairs, kind, value)
         m.set_stream(stream)
@@ -571,7 +583,10 @@ def run_gpu_adjoint(args, name):
     m.adjoint(warm, gauges, target, checkpoint_every=50, out=(gm, gz))
     m.set_state(mi.h, mi.hu, mi.hv)
     # launch shape of the forward and recomputed steps, chosen by the autotuner
-    shape = m.autotune(4)
+    if fixed:
+        shape = dict(fixed, chunk=0, fixed=True)
+    else:
+        shape = m.autotune(4)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local)
@@ -635,10 +650,11 @@ def _shape_kwargs(spec):
 
 
 def _shape_key(t):
-    """(block, min_blocks, stages, geometry_early, activity, edge_pass, grid[, chunk]) of an autotuner choice."""
+    """(block, min_blocks, stages, geometry_early, activity, edge_pass, grid[, chunk, dynamic]) of an autotuner
+    choice."""
     k = [t["block_size"], t["min_blocks"], t["stages"], t["geometry_early"], t["activity"], t["edge_pass"],
          t["grid"]]
-    return k + [t["chunk"]] if t.get("chunk") else k
+    return k + [t["chunk"], t.get("dynamic", 0)] if t.get("chunk") else k
 
 
 def _kernel_hash():
@@ -660,6 +676,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--members", type=int, default=256, help="ensemble workloads: number of members")
+    ap.add_argument("--ens-shape", default=None,
+                    help="ensemble workloads: block,min_blocks,stages,geometry_early,activity,edge_pass,dynamic,chunk,grid "
+                         "-- use this launch shape instead of autotuning (for profiling)")
     ap.add_argument("--shape", default=None,
                     help="mesh workloads: block,min_blocks,stages,geometry_early,activity,edge_pass,grid -- use "
                          "this launch shape instead of autotuning (for profiling the shape a tuned run chose)")
