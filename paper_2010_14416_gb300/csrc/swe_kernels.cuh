@@ -18,6 +18,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace swe {
 
 constexpr int kMaxGroups = 64;
@@ -160,6 +162,117 @@ __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
 template <typename T>
 __device__ __forceinline__ T tmin(T a, T b) { return a < b ? a : b; }
 
+// ---- comparisons of the flux path ------------------------------------------------
+// On GB300 the FP64 unit (2 operations per clock per SM) executes compares and
+// min/max of doubles as well as their arithmetic, and it bounds the FP64 step.
+// For doubles each helper below forms exactly the IEEE result of its
+// comparison (NaN, infinities and signed zeros included) from the bit
+// patterns, with 64-bit integer operations, which the FP64 kernels leave
+// idle; the selects return the same operand the plain expression returns, so
+// results are bit for bit those of the plain operators.  Other scalars (float,
+// the adjoint's dual numbers) use the plain operators.
+namespace cmp {
+constexpr unsigned long long kPosInf = 0x7FF0000000000000ULL;   // bits of +inf
+constexpr unsigned long long kNegZero = 0x8000000000000000ULL;  // bits of -0
+__device__ __forceinline__ unsigned long long bits(double x) { return (unsigned long long)__double_as_longlong(x); }
+template <typename T>
+constexpr bool kInt = std::is_same<T, double>::value;
+}  // namespace cmp
+
+// x > c for c finite and > 0
+template <typename T>
+__device__ __forceinline__ bool gt_pos(T x, T c) {
+    if constexpr (cmp::kInt<T>) {
+        const unsigned long long xb = cmp::bits(x), cb = cmp::bits(c);
+        return xb - cb - 1ULL < cmp::kPosInf - cb;          // c < x <= +inf
+    } else {
+        return x > c;
+    }
+}
+// x <= c for c finite and > 0
+template <typename T>
+__device__ __forceinline__ bool le_pos(T x, T c) {
+    if constexpr (cmp::kInt<T>) {
+        const unsigned long long xb = cmp::bits(x), cb = cmp::bits(c);
+        return xb <= cb || xb - cmp::kNegZero <= cmp::kPosInf;   // +0 <= x <= c, or -inf <= x <= -0
+    } else {
+        return x <= c;
+    }
+}
+// x < c for c finite and > 0
+template <typename T>
+__device__ __forceinline__ bool lt_pos(T x, T c) {
+    if constexpr (cmp::kInt<T>) {
+        const unsigned long long xb = cmp::bits(x), cb = cmp::bits(c);
+        return xb < cb || xb - cmp::kNegZero <= cmp::kPosInf;
+    } else {
+        return x < c;
+    }
+}
+// |x| < c for c finite and > 0
+template <typename T>
+__device__ __forceinline__ bool abs_lt_pos(T x, T c) {
+    if constexpr (cmp::kInt<T>) {
+        return (cmp::bits(x) & ~cmp::kNegZero) < cmp::bits(c);
+    } else {
+        return fabs(x) < c;
+    }
+}
+template <typename T>
+__device__ __forceinline__ bool gt_zero(T x) {
+    if constexpr (cmp::kInt<T>) return cmp::bits(x) - 1ULL < cmp::kPosInf;            // smallest denormal .. +inf
+    else return x > T(0);
+}
+template <typename T>
+__device__ __forceinline__ bool ge_zero(T x) {
+    if constexpr (cmp::kInt<T>) {
+        const unsigned long long xb = cmp::bits(x);
+        return xb <= cmp::kPosInf || xb == cmp::kNegZero;
+    } else {
+        return x >= T(0);
+    }
+}
+template <typename T>
+__device__ __forceinline__ bool le_zero(T x) {
+    if constexpr (cmp::kInt<T>) {
+        const unsigned long long xb = cmp::bits(x);
+        return xb == 0ULL || xb - cmp::kNegZero <= cmp::kPosInf;
+    } else {
+        return x <= T(0);
+    }
+}
+template <typename T>
+__device__ __forceinline__ bool lt_zero(T x) {
+    if constexpr (cmp::kInt<T>) return cmp::bits(x) - (cmp::kNegZero + 1ULL) < cmp::kPosInf;  // -inf .. -denormal
+    else return x < T(0);
+}
+// tmax(0, x)
+template <typename T>
+__device__ __forceinline__ T max_zero(T x) {
+    if constexpr (cmp::kInt<T>) return lt_zero(x) ? T(0) : x;
+    else return tmax(T(0), x);
+}
+// tmin(a, b) for a, b >= +0 (or +inf), e.g. CFL candidates and depths
+template <typename T>
+__device__ __forceinline__ T min_nonneg(T a, T b) {
+    if constexpr (cmp::kInt<T>) return cmp::bits(a) < cmp::bits(b) ? a : b;
+    else return tmin(a, b);
+}
+// tmax(a, b) for finite a, b (bed elevations)
+template <typename T>
+__device__ __forceinline__ T max_finite(T a, T b) {
+    if constexpr (cmp::kInt<T>) {
+        // the sign-magnitude bits, turned into a two's-complement key, order
+        // finite doubles except that -0 sorts below +0, where IEEE has a tie
+        const long long ab = __double_as_longlong(a), bb = __double_as_longlong(b);
+        const long long ka = ab ^ ((ab >> 63) & 0x7FFFFFFFFFFFFFFFLL), kb = bb ^ ((bb >> 63) & 0x7FFFFFFFFFFFFFFFLL);
+        const bool both_zero = (((unsigned long long)ab | (unsigned long long)bb) << 1) == 0ULL;
+        return (ka > kb && !both_zero) ? a : b;
+    } else {
+        return tmax(a, b);
+    }
+}
+
 // 1/|L n| of an edge.  FP64 takes it precomputed (the host forms
 // 1/sqrt(fma(lx, lx, ly ly)) once per cell edge, the same on every host): the
 // square root and division are a quarter of the flux pass's FP64 work, and the
@@ -183,7 +296,7 @@ template <typename T>
 __device__ __forceinline__ void riemann_hllc(T hL, T unL, T utL, T hR, T unR, T utR, T g, T h_dry,
                                              T& G1, T& G2, T& G3, T* speeds = nullptr, bool hll_only = false) {
     using A = Ar<T>;
-    const bool wetL = hL > h_dry, wetR = hR > h_dry;
+    const bool wetL = gt_pos(hL, h_dry), wetR = gt_pos(hR, h_dry);
     if (!wetL && !wetR) {
         G1 = T(0); G2 = T(0); G3 = T(0);
         if (speeds) { speeds[0] = T(0); speeds[1] = T(0); speeds[2] = T(0); }
@@ -199,8 +312,8 @@ __device__ __forceinline__ void riemann_hllc(T hL, T unL, T utL, T hR, T unR, T 
         const T hsum = hL + hR;
         const T h0 = T(0.5) * hsum - T(0.25) * A::div_((unR - unL) * hsum, aL + aR);  // Eq 21
         T hs;
-        if (h0 <= tmin(hL, hR)) {                                                   // Eq 22
-            const T b = tmax(T(0), T(0.5) * (aL + aR) + T(0.25) * (unL - unR));
+        if (le_pos(h0, min_nonneg(hL, hR))) {                                      // Eq 22
+            const T b = max_zero(T(0.5) * (aL + aR) + T(0.25) * (unL - unR));
             hs = A::div_(b * b, g);
         } else {                                                                    // Eq 23
             const T r2h0 = A::rcp_(T(2) * h0);
@@ -208,8 +321,8 @@ __device__ __forceinline__ void riemann_hllc(T hL, T unL, T utL, T hR, T unR, T 
             const T gR = A::sqrt_(g * (h0 + hR) * r2h0 * A::rcp_(hR));
             hs = A::div_(hL * gL + hR * gR + unL - unR, gL + gR);
         }
-        const T pL = hs > hL ? A::div_(A::sqrt_(T(0.5) * hs * (hs + hL)), hL) : T(1);  // Eq 20
-        const T pR = hs > hR ? A::div_(A::sqrt_(T(0.5) * hs * (hs + hR)), hR) : T(1);
+        const T pL = gt_pos(hs, hL) ? A::div_(A::sqrt_(T(0.5) * hs * (hs + hL)), hL) : T(1);  // Eq 20
+        const T pR = gt_pos(hs, hR) ? A::div_(A::sqrt_(T(0.5) * hs * (hs + hR)), hR) : T(1);
         SL = unL - aL * pL;                                                          // Eq 19
         SR = unR + aR * pR;
         const T mL = hL * (unL - SL), mR = hR * (unR - SR);
@@ -218,10 +331,10 @@ __device__ __forceinline__ void riemann_hllc(T hL, T unL, T utL, T hR, T unR, T 
     const T qL = hL * unL, qR = hR * unR;
     const T PL = qL * unL + T(0.5) * g * hL * hL;
     const T PR = qR * unR + T(0.5) * g * hR * hR;
-    if (SL >= T(0)) {                                                                // Eq 17
+    if (ge_zero(SL)) {                                                               // Eq 17
         G1 = qL; G2 = PL;
         if (hll_only) G3 = qL * utL;
-    } else if (SR <= T(0)) {
+    } else if (le_zero(SR)) {
         G1 = qR; G2 = PR;
         if (hll_only) G3 = qR * utR;
     } else {                                                                         // Eq 18
@@ -231,7 +344,7 @@ __device__ __forceinline__ void riemann_hllc(T hL, T unL, T utL, T hR, T unR, T 
         G2 = (SR * PL - SL * PR + ss * (qR - qL)) * r;
         if (hll_only) G3 = (SR * (qL * utL) - SL * (qR * utR) + ss * (hR * utR - hL * utL)) * r;
     }
-    if (!hll_only) G3 = G1 * (Ss >= T(0) ? utL : utR);                               // Eq 24
+    if (!hll_only) G3 = G1 * (ge_zero(Ss) ? utL : utR);                              // Eq 24
     if (speeds) { speeds[0] = SL; speeds[1] = SR; speeds[2] = Ss; }
 }
 
@@ -334,7 +447,7 @@ template <typename T>
 __device__ __forceinline__ void cell_velocity(T h, T hu, T hv, T h_dry, T& u, T& v) {
     u = T(0);
     v = T(0);
-    if (h > h_dry) { const T r = Ar<T>::rcp_(h); u = hu * r; v = hv * r; }
+    if (gt_pos(h, h_dry)) { const T r = Ar<T>::rcp_(h); u = hu * r; v = hv * r; }
 }
 
 // Flux leaving cell i through an interior edge (per unit length, x-y frame)
@@ -348,9 +461,9 @@ __device__ __forceinline__ void edge_interior(T hi, T ui, T vi, T zi, T hk, T hu
     T uk, vk;
     cell_velocity<T>(hk, huk, hvk, h_dry, uk, vk);
     // hydrostatic reconstruction (Eq 28): z* = max(z_i, z_k)
-    const T zs = tmax(zi, zk);
-    const T hsi = tmax(T(0), hi + zi - zs);
-    const T hsk = tmax(T(0), hk + zk - zs);
+    const T zs = max_finite(zi, zk);
+    const T hsi = max_zero(hi + zi - zs);
+    const T hsk = max_zero(hk + zk - zs);
     // canonical orientation: left = lower caller index
     const T hL = flip ? hsk : hsi, hR = flip ? hsi : hsk;
     const T uL = flip ? uk : ui, vL = flip ? vk : vi;
@@ -381,11 +494,11 @@ __device__ __forceinline__ void edge_boundary(int kind, double value, T hi, T ui
     } else if (kind == kBcInflow) {
         const T q = T(value);
         G1 = -q;
-        G2 = T(0.5) * g * hi * hi + (hi > h_dry ? Ar<T>::div_(q * q, hi) : T(0));
+        G2 = T(0.5) * g * hi * hi + (gt_pos(hi, h_dry) ? Ar<T>::div_(q * q, hi) : T(0));
         G3 = T(0);
     } else {
         T hg = hi;
-        if (kind == kBcStage) hg = tmax(T(0), T(value) - zi);
+        if (kind == kBcStage) hg = max_zero(T(value) - zi);
         riemann_hllc<T>(hi, un, ut, hg, un, ut, g, h_dry, G1, G2, G3, nullptr, hll_only);
     }
     F0 = G1;
@@ -402,9 +515,9 @@ __device__ __forceinline__ void friction_update(T hi, T qx, T qy, T gm2, T Rh, T
     dh = dt * Rh;
     dqx = dt * Rx;
     dqy = dt * Ry;
-    if (hi > h_dry && gm2 > T(0)) {
+    if (gt_pos(hi, h_dry) && gt_zero(gm2)) {
         const T qq = qx * qx + qy * qy;
-        if (qq > T(0)) {
+        if (gt_zero(qq)) {
             const T qn = A::sqrt_(qq);
             const T cf = gm2 * A::pow_m73(hi);             // c = g m^2 h^(-7/3)
             const T al = T(0.5) * dt * cf;                  // alpha = dt c / 2
@@ -462,11 +575,11 @@ __device__ __forceinline__ T update_cell(const Args& a, long long i, const V4<T>
         if constexpr (sizeof(T) == 8) gR = a.geoR[i];
         gm2 = load_gm2(a, i, tp, T(0));
     }
-    bool quiet = !(hi > h_dry);
+    bool quiet = !gt_pos(hi, h_dry);
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         if (code[j] >= 0) {
-            quiet = quiet && !(nb[j].x > h_dry);
+            quiet = quiet && !gt_pos(nb[j].x, h_dry);
         } else {
             const int kind = a.bc_kind(-1 - code[j]);
             quiet = quiet && (kind == kBcWall || kind == kBcTransmissive);
@@ -506,9 +619,9 @@ __device__ __forceinline__ T update_cell(const Args& a, long long i, const V4<T>
         if (c >= 0) {
             T src;
             if constexpr (EDGES) {
-                if (!(hi > h_dry) && !(o.x > h_dry)) {
-                    const T zs = tmax(zi, o.w);
-                    const T hsi = tmax(T(0), hi + zi - zs);
+                if (!gt_pos(hi, h_dry) && !gt_pos(o.x, h_dry)) {
+                    const T zs = max_finite(zi, o.w);
+                    const T hsi = max_zero(hi + zi - zs);
                     F0 = T(0); F1 = T(0); F2 = T(0);
                     src = T(0.5) * g * (hsi * hsi - hi * hi);
                 } else {
@@ -547,19 +660,19 @@ __device__ __forceinline__ T update_cell(const Args& a, long long i, const V4<T>
     out.x = hi + dh;
     out.y = qx + dqx;
     out.z = qy + dqy;
-    if (out.x < T(0)) {
+    if (lt_zero(out.x)) {
         out.x = T(0); out.y = T(0); out.z = T(0);
         atomicAdd(n_clamped, 1ULL);
-    } else if (out.x <= h_dry) {
+    } else if (le_pos(out.x, h_dry)) {
         out.y = T(0); out.z = T(0);
     }
     const T big = T(3.0e38);
-    if (!(out.x < big) || !(fabs(out.y) < big) || !(fabs(out.z) < big))
+    if (!lt_pos(out.x, big) || !abs_lt_pos(out.y, big) || !abs_lt_pos(out.z, big))
         atomicOr(status, kStatusNonFinite);
     a.s_out[i] = out;
     // next CFL candidate (Eq 15), R_i / (sqrt(g h) + |u|) on the new state
     T cand = inf_of<T>();
-    if (out.x > h_dry) {
+    if (gt_pos(out.x, h_dry)) {
         const T r = A::rcp_(out.x);
         const T u = out.y * r, v = out.z * r;
         const T den = A::sqrt_(g * out.x) + A::sqrt_(u * u + v * v);
@@ -595,7 +708,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_kernel(const StepArgs<T> a) 
         for (; i < a.n; i += stride) {
             const V4<T> own = a.s_in[i];
             const int4 tp = a.topo[i];
-            cand = tmin(cand, update_cell<T, GEO_EARLY, EDGES>(a, i, own, tp, dt, active, a.n_clamped, a.status));
+            cand = min_nonneg(cand, update_cell<T, GEO_EARLY, EDGES>(a, i, own, tp, dt, active, a.n_clamped, a.status));
         }
     } else {
         __shared__ V4<T> st_own[STAGES][BLOCK];
@@ -623,7 +736,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_kernel(const StepArgs<T> a) 
             cp_async_wait<STAGES - 1>();
             const V4<T> own = st_own[slot][tid];
             const int4 tp = st_topo[slot][tid];
-            cand = tmin(cand, update_cell<T, GEO_EARLY, EDGES>(a, i, own, tp, dt, active, a.n_clamped, a.status));
+            cand = min_nonneg(cand, update_cell<T, GEO_EARLY, EDGES>(a, i, own, tp, dt, active, a.n_clamped, a.status));
             slot = slot == STAGES - 1 ? 0 : slot + 1;
         }
         cp_async_wait<0>();
@@ -646,7 +759,7 @@ __global__ void __launch_bounds__(BLOCK) edge_flux_kernel(const StepArgs<T> a) {
     for (long long e = (long long)blockIdx.x * BLOCK + threadIdx.x; e < a.n_edges; e += stride) {
         const int2 lr = a.ecells[e];
         const V4<T> L = a.s_in[lr.x], R = a.s_in[lr.y];
-        if (!(L.x > h_dry) && !(R.x > h_dry)) continue;
+        if (!gt_pos(L.x, h_dry) && !gt_pos(R.x, h_dry)) continue;
         const T lx = a.eln[2 * e], ly = a.eln[2 * e + 1];
         const T l2 = lx * lx + ly * ly;
         T pre = T(0);
@@ -768,7 +881,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_kernel_act(const StepArgs<T>
                 } else {
                     const T r = update_cell<T, GEO_EARLY>(a, c, own, st_topo[k2][tid], dt, active, a.n_clamped,
                                                           a.status);
-                    cand = tmin(cand, r);
+                    cand = min_nonneg(cand, r);
                     const bool wet = r < inf_of<T>();
                     // the topology record is read again from shared memory rather than kept
                     // live in registers across the update
@@ -909,7 +1022,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel(const EnsArg
             tp = a.topo[i];
         }
         if (have_dt)
-            cand = tmin(cand, update_cell<T, GEO_EARLY, EDGES>(a, i, own, tp, dt, active, sm + 5, (unsigned*)(sm + 4)));
+            cand = min_nonneg(cand, update_cell<T, GEO_EARLY, EDGES>(a, i, own, tp, dt, active, sm + 5, (unsigned*)(sm + 4)));
         else
             a.s_out[i] = own;
     }
@@ -970,7 +1083,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel_dyn(const En
             const V4<T> own = a.s_in[i];
             const int4 tp = a.topo[i];
             if (have_dt)
-                cand = tmin(cand, update_cell<T, GEO_EARLY>(a, i, own, tp, dt, active, sm + 5, (unsigned*)(sm + 4)));
+                cand = min_nonneg(cand, update_cell<T, GEO_EARLY>(a, i, own, tp, dt, active, sm + 5, (unsigned*)(sm + 4)));
             else
                 a.s_out[i] = own;
         }
@@ -1084,7 +1197,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel_act(const En
         } else {
             const T r = update_cell<T, GEO_EARLY>(a, c, own, st_topo[k2][tid], dt, active, sm + 5,
                                                   (unsigned*)(sm + 4));
-            cand = tmin(cand, r);
+            cand = min_nonneg(cand, r);
             const bool wet = r < inf_of<T>();
             const volatile int* tv = (const volatile int*)&st_topo[k2][tid];
             if (wet || (tv[3] & kStaticBit)) a.act_next[c] = 1;
