@@ -162,6 +162,16 @@ __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
 template <typename T>
 __device__ __forceinline__ T tmin(T a, T b) { return a < b ? a : b; }
 
+// FP64 (the double instantiation only): where the paper's formulas divide by
+// several quantities in turn, one division by their product and
+// multiplications replace them.  A double division or square root is an
+// iteration of several operations on the FP64 unit, which bounds that path;
+// the products stay far inside the double range for depths of 1e-6 to 1e4 m.
+// Results move by a few ulps.  FP32 divisions are single hardware
+// approximations, and the adjoint's duals keep the formulas as written.
+template <typename T>
+constexpr bool kOneDivision = std::is_same<T, double>::value;
+
 // ---- comparisons of the flux path ------------------------------------------------
 // On GB300 the FP64 unit (2 operations per clock per SM) executes compares and
 // min/max of doubles as well as their arithmetic, and it bounds the FP64 step.
@@ -315,14 +325,36 @@ __device__ __forceinline__ void riemann_hllc(T hL, T unL, T utL, T hR, T unR, T 
         if (le_pos(h0, min_nonneg(hL, hR))) {                                      // Eq 22
             const T b = max_zero(T(0.5) * (aL + aR) + T(0.25) * (unL - unR));
             hs = A::div_(b * b, g);
-        } else {                                                                    // Eq 23
+        } else if constexpr (!kOneDivision<T>) {                                    // Eq 23
             const T r2h0 = A::rcp_(T(2) * h0);
             const T gL = A::sqrt_(g * (h0 + hL) * r2h0 * A::rcp_(hL));
             const T gR = A::sqrt_(g * (h0 + hR) * r2h0 * A::rcp_(hR));
             hs = A::div_(hL * gL + hR * gR + unL - unR, gL + gR);
+        } else {
+            // one division gives 1/(2 h0 h_L) and 1/(2 h0 h_R) (h0 > min(h_L, h_R) > 0 here)
+            const T h02 = T(2) * h0;
+            const T inv = A::rcp_(h02 * hL * hR);
+            const T gL = A::sqrt_(g * (h0 + hL) * (hR * inv));
+            const T gR = A::sqrt_(g * (h0 + hR) * (hL * inv));
+            hs = A::div_(hL * gL + hR * gR + unL - unR, gL + gR);
         }
-        const T pL = gt_pos(hs, hL) ? A::div_(A::sqrt_(T(0.5) * hs * (hs + hL)), hL) : T(1);  // Eq 20
-        const T pR = gt_pos(hs, hR) ? A::div_(A::sqrt_(T(0.5) * hs * (hs + hR)), hR) : T(1);
+        T pL = T(1), pR = T(1);                                                     // Eq 20
+        if constexpr (!kOneDivision<T>) {
+            if (gt_pos(hs, hL)) pL = A::div_(A::sqrt_(T(0.5) * hs * (hs + hL)), hL);
+            if (gt_pos(hs, hR)) pR = A::div_(A::sqrt_(T(0.5) * hs * (hs + hR)), hR);
+        } else {
+            // sqrt(h*(h*+h_K)/2)/h_K = sqrt(h*(h*+h_K)/(2 h_K^2)); both shocks share a division
+            const bool shL = gt_pos(hs, hL), shR = gt_pos(hs, hR);
+            if (shL && shR) {
+                const T inv = A::rcp_(hL * hR);
+                pL = A::sqrt_(T(0.5) * hs * (hs + hL)) * (hR * inv);
+                pR = A::sqrt_(T(0.5) * hs * (hs + hR)) * (hL * inv);
+            } else if (shL) {
+                pL = A::div_(A::sqrt_(T(0.5) * hs * (hs + hL)), hL);
+            } else if (shR) {
+                pR = A::div_(A::sqrt_(T(0.5) * hs * (hs + hR)), hR);
+            }
+        }
         SL = unL - aL * pL;                                                          // Eq 19
         SR = unR + aR * pR;
         const T mL = hL * (unL - SL), mR = hR * (unR - SR);
@@ -519,17 +551,33 @@ __device__ __forceinline__ void friction_update(T hi, T qx, T qy, T gm2, T Rh, T
         const T qq = qx * qx + qy * qy;
         if (gt_zero(qq)) {
             const T qn = A::sqrt_(qq);
-            const T cf = gm2 * A::pow_m73(hi);             // c = g m^2 h^(-7/3)
+            T cf, rh;                                       // c = g m^2 h^(-7/3), 1/h
+            if constexpr (kOneDivision<T>) {
+                const T c3 = cbrt(hi), p = A::rcp_(hi * hi * c3);   // h^(-7/3); 1/h = h cbrt(h) h^(-7/3)
+                cf = gm2 * p;
+                rh = hi * c3 * p;
+            } else {
+                cf = gm2 * A::pow_m73(hi);
+                rh = A::rcp_(hi);
+            }
             const T al = T(0.5) * dt * cf;                  // alpha = dt c / 2
             // rhs: dt (R_q + S_f) + dt/2 J_qh dh, with S_f = -c|q|q and
             // J_qh = (7/3) c |q| q / h
-            const T k = dt * cf * qn * (T(7.0 / 6.0) * dh * A::rcp_(hi) - T(1));
+            const T k = dt * cf * qn * (T(7.0 / 6.0) * dh * rh - T(1));
             const T bx = dqx + k * qx, by = dqy + k * qy;
             // (1 + a|q|) I + a q q^T/|q| has eigenvalue 1 + 2a|q| along q
             // and 1 + a|q| across it
             const T d1 = T(1) + al * qn, d2 = d1 + al * qn;
-            const T proj = (bx * qx + by * qy) * al * A::rcp_(qn * d2);
-            const T rd1 = A::rcp_(d1);
+            T rqd2, rd1;                                    // 1/(|q| d2), 1/d1
+            if constexpr (kOneDivision<T>) {
+                const T qd2 = qn * d2, inv = A::rcp_(qd2 * d1);
+                rqd2 = d1 * inv;
+                rd1 = qd2 * inv;
+            } else {
+                rqd2 = A::rcp_(qn * d2);
+                rd1 = A::rcp_(d1);
+            }
+            const T proj = (bx * qx + by * qy) * al * rqd2;
             dqx = (bx - proj * qx) * rd1;
             dqy = (by - proj * qy) * rd1;
         }
@@ -673,10 +721,16 @@ __device__ __forceinline__ T update_cell(const Args& a, long long i, const V4<T>
     // next CFL candidate (Eq 15), R_i / (sqrt(g h) + |u|) on the new state
     T cand = inf_of<T>();
     if (gt_pos(out.x, h_dry)) {
-        const T r = A::rcp_(out.x);
-        const T u = out.y * r, v = out.z * r;
-        const T den = A::sqrt_(g * out.x) + A::sqrt_(u * u + v * v);
-        cand = A::div_(gB.w, den);
+        if constexpr (kOneDivision<T>) {
+            // R h / (h sqrt(g h) + |q|): the velocity's division folded into the candidate's
+            const T qm = A::sqrt_(out.y * out.y + out.z * out.z);
+            cand = A::div_(gB.w * out.x, out.x * A::sqrt_(g * out.x) + qm);
+        } else {
+            const T r = A::rcp_(out.x);
+            const T u = out.y * r, v = out.z * r;
+            const T den = A::sqrt_(g * out.x) + A::sqrt_(u * u + v * v);
+            cand = A::div_(gB.w, den);
+        }
     }
     return cand;
 }
