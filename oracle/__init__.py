@@ -78,6 +78,8 @@ def _load():
         lib.orc_rhs.argtypes = [vp, dp, dp, dp, dp, dp, dp]
         lib.orc_dt.restype = C.c_double
         lib.orc_dt.argtypes = [vp, dp, dp, dp, C.c_double]
+        lib.orc_set_threads.argtypes = [C.c_int]
+        lib.orc_max_threads.restype = C.c_int
         lib.orc_run.restype = C.c_int64
         lib.orc_run.argtypes = [vp, dp, dp, dp, C.c_int64, C.c_double, dp, dp]
         lib.orc_run_fixed_dt.restype = C.c_int64
@@ -88,6 +90,16 @@ def _load():
 
 def _d(a):
     return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's OpenMP loops (timing only; results do not depend on it)."""
+    _load().orc_set_threads(int(n))
+
+
+def max_threads() -> int:
+    """Threads the oracle's OpenMP loops use."""
+    return int(_load().orc_max_threads())
 
 
 def _f64(a):

@@ -39,6 +39,7 @@
  * point of view (left state = this cell, normal = this cell's outward normal).
  */
 #include <math.h>
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -469,6 +470,12 @@ static int orc_cell_update(const orc_mesh* M, int64_t i, const double* h, const 
     if (out[0] <= M->h_dry) { out[1] = 0.0; out[2] = 0.0; }
     return 0;
 }
+
+/* Threads of the OpenMP loops below, for timing the oracle on one core and
+ * on all of them; results do not depend on it (each cell's update is a
+ * separate computation, and the reductions are an integer sum and a min). */
+void orc_set_threads(int n) { omp_set_num_threads(n > 0 ? n : 1); }
+int orc_max_threads(void) { return omp_get_max_threads(); }
 
 /* One step for every cell.  Returns the number of clamped cells. */
 int64_t orc_step(const orc_mesh* M, const double* h, const double* hu, const double* hv,
