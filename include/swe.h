@@ -76,8 +76,8 @@ typedef struct swe_mesh swe_mesh;
 
 typedef struct swe_config {
     int precision;    /* SWE_FP64 (default) or SWE_FP32 */
-    double g;         /* gravitational acceleration, default 9.81 m/s^2 */
-    double h_dry;     /* wet/dry threshold, default 1e-6 m */
+    double g;         /* gravitational acceleration, default 9.81 m/s^2; finite and > 0 */
+    double h_dry;     /* wet/dry threshold, default 1e-6 m; finite and > 0 */
     int reorder;      /* SWE_REORDER_*, default SWE_REORDER_HILBERT */
     int block_size;   /* threads per block of the step kernel; 0 = library default */
     int graph_steps;  /* steps captured per CUDA graph; 0 = default, < 0 = no graphs */

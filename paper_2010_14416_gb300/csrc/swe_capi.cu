@@ -563,7 +563,10 @@ int swe_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* tris, i
     swe_config_default(&c);
     if (cfg) c = *cfg;
     if (c.precision != SWE_FP64 && c.precision != SWE_FP32) { set_error("swe_mesh_create: bad precision"); return SWE_EINVAL; }
-    if (!(c.g > 0.0) || !(c.h_dry > 0.0)) { set_error("swe_mesh_create: g and h_dry must be > 0"); return SWE_EINVAL; }
+    if (!(c.g > 0.0) || !(c.h_dry > 0.0) || !std::isfinite(c.g) || !std::isfinite(c.h_dry)) {
+        set_error("swe_mesh_create: g and h_dry must be finite and > 0");
+        return SWE_EINVAL;
+    }
     if (c.flux != SWE_FLUX_HLLC && c.flux != SWE_FLUX_HLL) { set_error("swe_mesh_create: unknown flux"); return SWE_EINVAL; }
     if (c.geometry_early != 0 && c.geometry_early != 1) {
         set_error("swe_mesh_create: geometry_early must be 0 or 1");

@@ -121,3 +121,16 @@ def test_malformed_meshes_rejected_by_host_preprocessing():
     with pytest.raises(capi.SWEError) as e:
         capi.mesh_preprocess(nodes, np.zeros((0, 3), np.int32))
     assert e.value.code == capi.SWE_EINVAL
+
+
+@pytest.mark.parametrize("kw", [dict(g=0.0), dict(g=float("inf")), dict(h_dry=-1e-6), dict(h_dry=float("nan")),
+                                dict(h_dry=float("inf")), dict(precision=7), dict(flux=5), dict(geometry_early=2),
+                                dict(activity=3), dict(edge_pass=2), dict(grid=-1), dict(activity=1, edge_pass=1),
+                                dict(block_size=96)])
+def test_invalid_configs_rejected_before_any_device_work(kw):
+    # swe_mesh_create validates its configuration before it touches the
+    # device, so these fail the same way with or without a GPU
+    mi = mg.dam_break_4k()
+    with pytest.raises(capi.SWEError) as e:
+        capi.Mesh(mi.nodes, mi.tris, mi.z, mi.manning, **kw)
+    assert e.value.code == capi.SWE_EINVAL
