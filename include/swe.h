@@ -425,7 +425,10 @@ typedef struct swe_tune {
  * edge_pass) shape (see swe_config) with several
  * grid sizes -- one or two resident waves looping over the cells, or 1, 2 or 4
  * cells per thread -- is timed with CUDA events over trial_steps steps
- * (>= 1; 0 = 8), twice, and the fastest is kept for all later steps.  The
+ * (>= 1; 0 = 8), twice; the shape in use and the (at most four) shapes within
+ * 5 % of the fastest are then timed again over max(32, 4 trial_steps) steps,
+ * and the first of them (in a fixed order, the shape in use first) within 1 %
+ * of the fastest there is kept for all later steps.  The
  * paper fixes no launch shape; every shape evaluates the same arithmetic on
  * every cell, so the choice changes the speed only: states, times and time
  * steps are bit for bit the same whatever is chosen.  The trial steps read the

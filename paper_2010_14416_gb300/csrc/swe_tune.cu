@@ -11,7 +11,12 @@
 // of the activity kernel also write the mesh's next activity buffers, with
 // exactly the bytes the next real step writes there.  Every shape evaluates
 // the same arithmetic on every cell, so the choice changes speed only, never
-// results (the GPU tests check this bit for bit).
+// results (the GPU tests check this bit for bit).  A runoff then times the
+// shape in use and the (at most four) candidates within 5 % of the fastest
+// again over at least 32 steps, and keeps the first of them in the fixed
+// candidate order within 1 % of the fastest there: short trials blur
+// differences of a few percent, and a tie keeps the same choice from run to
+// run.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -24,7 +29,10 @@ using namespace swe;
 
 namespace {
 
-constexpr double kTuneTolerance = 1.02;
+constexpr double kTuneTolerance = 1.02;    // first pass: ties within 2 %
+constexpr double kRunoffWindow = 1.05;     // candidates within 5 % of the fastest go to the runoff
+constexpr int kRunoffMax = 4;              // at most this many
+constexpr double kRunoffTolerance = 1.01;  // runoff: ties within 1 %
 
 struct Shape {
     int block, min_blocks, stages, geo_early, activity, edges;
@@ -139,51 +147,72 @@ int autotune_t(swe_mesh* m, int trial_steps, swe_tune* out) {
         return SWE_ENOMEM;
     }
     const int rounds = 2;
-    std::vector<cudaEvent_t> ev(2 * rounds * cand.size(), nullptr);
-    for (auto& x : ev)
-        if (e == cudaSuccess) e = cudaEventCreate(&x);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(small, m->small, kSmallWords * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st);
     const void* cur = m->state[m->nstep % 2];
-    for (int r = 0; r < rounds && e == cudaSuccess; ++r) {
-        for (size_t c = 0; c < cand.size() && e == cudaSuccess; ++c) {
-            apply_shape(m, cand[c]);
-            e = launch_step_raw(m, cur, scratch, small, m->nstep, 0.9, nullptr, nullptr, st, true);  // warm-up
-            if (e == cudaSuccess) e = cudaEventRecord(ev[2 * (r * cand.size() + c)], st);
-            for (int s = 0; s < trial_steps && e == cudaSuccess; ++s)
-                e = launch_step_raw(m, cur, scratch, small, m->nstep, 0.9, nullptr, nullptr, st, true);
-            if (e == cudaSuccess) e = cudaEventRecord(ev[2 * (r * cand.size() + c) + 1], st);
-        }
-    }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    // time the listed candidates over `steps` steps each, `rounds` times in
+    // turn; ms[c] = the best round's time per step
     std::vector<double> ms(cand.size(), 1e300);
-    for (int r = 0; r < rounds && e == cudaSuccess; ++r)
-        for (size_t c = 0; c < cand.size() && e == cudaSuccess; ++c) {
-            float t = 0.f;
-            e = cudaEventElapsedTime(&t, ev[2 * (r * cand.size() + c)], ev[2 * (r * cand.size() + c) + 1]);
-            ms[c] = std::min(ms[c], (double)t / trial_steps);
+    auto time_candidates = [&](const std::vector<size_t>& which, int steps) {
+        std::vector<cudaEvent_t> ev(2 * rounds * which.size(), nullptr);
+        for (auto& x : ev)
+            if (e == cudaSuccess) e = cudaEventCreate(&x);
+        for (int r = 0; r < rounds && e == cudaSuccess; ++r) {
+            for (size_t w = 0; w < which.size() && e == cudaSuccess; ++w) {
+                apply_shape(m, cand[which[w]]);
+                e = launch_step_raw(m, cur, scratch, small, m->nstep, 0.9, nullptr, nullptr, st, true);  // warm-up
+                if (e == cudaSuccess) e = cudaEventRecord(ev[2 * (r * which.size() + w)], st);
+                for (int k = 0; k < steps && e == cudaSuccess; ++k)
+                    e = launch_step_raw(m, cur, scratch, small, m->nstep, 0.9, nullptr, nullptr, st, true);
+                if (e == cudaSuccess) e = cudaEventRecord(ev[2 * (r * which.size() + w) + 1], st);
+            }
         }
-    for (auto& x : ev)
-        if (x) cudaEventDestroy(x);
-    cudaFree(scratch);
-    cudaFree(small);
-    // the first candidate (in the fixed order above) within kTuneTolerance of
-    // the fastest: timings within noise of each other then give the same choice
-    // from run to run
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        for (size_t w = 0; w < which.size(); ++w) ms[which[w]] = 1e300;
+        for (int r = 0; r < rounds && e == cudaSuccess; ++r)
+            for (size_t w = 0; w < which.size() && e == cudaSuccess; ++w) {
+                float t = 0.f;
+                e = cudaEventElapsedTime(&t, ev[2 * (r * which.size() + w)], ev[2 * (r * which.size() + w) + 1]);
+                ms[which[w]] = std::min(ms[which[w]], (double)t / steps);
+            }
+        for (auto& x : ev)
+            if (x) cudaEventDestroy(x);
+    };
+    std::vector<size_t> all(cand.size());
+    for (size_t c = 0; c < cand.size(); ++c) all[c] = c;
+    time_candidates(all, trial_steps);
+    // the first candidate (in the fixed order above) within a tolerance of the
+    // fastest of a set: timings within noise of each other then give the same
+    // choice from run to run
+    auto first_within = [&](const std::vector<size_t>& which, double tol, bool plain_only) {
+        double fastest = 1e300;
+        for (size_t c : which)
+            if (!plain_only || !cand[c].activity) fastest = std::min(fastest, ms[c]);
+        for (size_t c : which)
+            if ((!plain_only || !cand[c].activity) && ms[c] <= fastest * tol) return c;
+        return cand.size();
+    };
     size_t best = 0, best_plain = cand.size();
     if (e == cudaSuccess) {
-        double fastest = ms[0], fastest_plain = 1e300;
-        for (size_t c = 0; c < cand.size(); ++c) {
-            fastest = std::min(fastest, ms[c]);
-            if (!cand[c].activity) fastest_plain = std::min(fastest_plain, ms[c]);
-        }
-        best = cand.size();
-        for (size_t c = 0; c < cand.size(); ++c) {
-            if (best == cand.size() && ms[c] <= fastest * kTuneTolerance) best = c;
-            if (best_plain == cand.size() && !cand[c].activity && ms[c] <= fastest_plain * kTuneTolerance)
-                best_plain = c;
-        }
+        best_plain = first_within(all, kTuneTolerance, true);
+        // runoff: the candidates within kRunoffWindow of the fastest (at most
+        // kRunoffMax, the fastest first) timed again over runs long enough for
+        // the differences of a few percent that short trials blur
+        double fastest = 1e300;
+        for (size_t c : all) fastest = std::min(fastest, ms[c]);
+        std::vector<size_t> close;
+        for (size_t c : all)
+            if (ms[c] <= fastest * kRunoffWindow) close.push_back(c);
+        std::stable_sort(close.begin(), close.end(), [&](size_t x, size_t y) { return ms[x] < ms[y]; });
+        if (close.size() > (size_t)kRunoffMax) close.resize(kRunoffMax);
+        // the shape in use runs too: it is kept unless another is faster in the runoff
+        if (std::find(close.begin(), close.end(), (size_t)0) == close.end()) close.push_back(0);
+        std::sort(close.begin(), close.end());   // back to the fixed candidate order
+        if (close.size() > 1) time_candidates(close, std::max(32, 4 * trial_steps));
+        best = e == cudaSuccess ? first_within(close, kRunoffTolerance, false) : 0;
     }
+    cudaFree(scratch);
+    cudaFree(small);
     const Shape pick = e == cudaSuccess ? cand[best] : before;
     // launches without activity bytes take the fastest shape of the plain kernel
     if (e == cudaSuccess && best_plain < cand.size()) apply_shape(m, cand[best_plain]);
