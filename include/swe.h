@@ -449,9 +449,13 @@ SWE_API int swe_autotune(swe_mesh* mesh, int trial_steps, swe_tune* out);
  * (edge_pass 1: (256|128, 1, 1, 0)), times chunks of 4 to 64 tiles; and its
  * dynamically scheduled shapes (dynamic 1, stages 1: FP32 (128, 8) with
  * geometry_early 0|1, (256, 4) with 0; FP64 (128|256, 1) with 0) with chunks
- * of 1 to 32 tiles; then grids of half, one and two resident waves for the
- * best of those.  Members' states, times and
- * steps are unchanged by the call and by the choice.  trial_steps 0 = 4.
+ * of 1 to 32 tiles, each over trial_steps steps, twice; then, as for a mesh,
+ * a runoff of the shape in use and the (at most four) shapes within 5 % of the
+ * fastest over max(32, 4 trial_steps) steps, keeping the first within 1 % of
+ * the fastest there; then grids of half and two resident waves for the kept
+ * shape, over as many steps, one of which replaces it when 2 % faster.
+ * Members' states, times and steps are unchanged by the call and by the
+ * choice.  trial_steps 0 = 4.
  */
 SWE_API int swe_ensemble_autotune(swe_ensemble* ens, int trial_steps, swe_tune* out);
 

@@ -607,9 +607,33 @@ int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
     std::vector<EnsShape> cand2;
     std::vector<double> ms2;
     if (!rc) {
-        // the first candidate within 2 % of the fastest (stable from run to run)
+        // runoff, as for a mesh: the shape in use and the (at most four)
+        // candidates within 5 % of the fastest, timed again over at least 32
+        // steps; the first of them in candidate order within 1 % of the fastest
+        // there is kept (stable from run to run)
         const double fastest = *std::min_element(ms.begin(), ms.end());
-        while (ms[best] > fastest * 1.02) ++best;
+        std::vector<size_t> close;
+        for (size_t c = 0; c < cand.size(); ++c)
+            if (ms[c] <= fastest * 1.05) close.push_back(c);
+        std::stable_sort(close.begin(), close.end(), [&](size_t x, size_t y) { return ms[x] < ms[y]; });
+        if (close.size() > 4) close.resize(4);
+        if (std::find(close.begin(), close.end(), (size_t)0) == close.end()) close.push_back(0);
+        std::sort(close.begin(), close.end());
+        if (close.size() > 1) {
+            std::vector<EnsShape> rc_cand;
+            for (size_t c : close) rc_cand.push_back(cand[c]);
+            std::vector<double> rc_ms;
+            rc = ens_time_shapes<T>(E, rc_cand, std::max(32, 4 * trial_steps), scratch, small, act, rc_ms);
+            if (!rc)
+                for (size_t k = 0; k < close.size(); ++k) ms[close[k]] = rc_ms[k];
+        }
+        double fast2 = 1e300;
+        for (size_t c : close) fast2 = std::min(fast2, ms[c]);
+        best = close[0];
+        for (size_t c : close)
+            if (ms[c] <= fast2 * 1.01) { best = c; break; }
+    }
+    if (!rc) {
         long long wave = 0;
         const EnsShape b = cand[best];
         if (b.activity || b.edges || b.dynamic) {
@@ -631,7 +655,9 @@ int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
                 cand2.push_back(
                     {b.block, b.min_blocks, b.stages, b.geo_early, b.chunk_log2, gr, b.activity, b.edges, b.dynamic});
         }
-        if (!rc && !cand2.empty()) rc = ens_time_shapes<T>(E, cand2, trial_steps, scratch, small, act, ms2);
+        // grids of half and two waves for the kept shape, timed as long as the runoff
+        if (!rc && !cand2.empty())
+            rc = ens_time_shapes<T>(E, cand2, std::max(32, 4 * trial_steps), scratch, small, act, ms2);
     }
     for (void* p : {scratch, (void*)small, (void*)act}) cudaFree(p);
     // the trials consumed the dynamic kernels' counters: the steps start from zero
