@@ -131,11 +131,12 @@ SWE_API void swe_config_default(swe_config* cfg);
  * as a wall.
  *   nodes   [n_nodes][2] double, metres
  *   tris    [n_tris][3] int32, 0-based node indices, either orientation
- *   bathy   [n_tris] double, cell-centred bed elevation z (m)
- *   manning [n_tris] double, Manning coefficient m (s m^-1/3), >= 0
+ *   bathy   [n_tris] double, cell-centred bed elevation z (m), finite
+ *   manning [n_tris] double, Manning coefficient m (s m^-1/3), finite and >= 0
  *   cfg     NULL for defaults
  *   out     receives the new mesh (owned by the caller; free with swe_mesh_destroy)
- * Errors: SWE_EINVAL (NULL pointers, n < 1, n_tris >= 2^30, negative Manning),
+ * Errors: SWE_EINVAL (NULL pointers, n < 1, n_tris >= 2^30, a negative or
+ * non-finite Manning coefficient, a non-finite bed),
  * SWE_EMESH, SWE_ENOMEM, SWE_ECUDA.
  */
 SWE_API int swe_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* tris, int64_t n_tris,
@@ -297,7 +298,8 @@ SWE_API int swe_step_dt(swe_mesh* mesh, int64_t nsteps, const double* dts, doubl
 
 /* Replaces the bed elevation and/or Manning coefficients ([n_tris] host
  * doubles in the caller's order; NULL keeps the current field).  The state's
- * h, hu, hv are kept.  Waits for the mesh stream. */
+ * h, hu, hv are kept.  Waits for the mesh stream.  Errors: SWE_EINVAL (a
+ * non-finite bed, a negative or non-finite Manning coefficient). */
 SWE_API int swe_set_fields(swe_mesh* mesh, const double* bathy, const double* manning);
 
 /* ---- batched ensemble (uncertainty propagation: many runs of the same solver) ---- */

@@ -525,7 +525,10 @@ int swe_set_fields(swe_mesh* m, const double* bathy, const double* manning) {
     const int64_t n = m->hm.n_cells;
     if (manning)
         for (int64_t c = 0; c < n; ++c)
-            if (!(manning[c] >= 0.0)) { set_error("swe_set_fields: negative Manning coefficient"); return SWE_EINVAL; }
+            if (!(manning[c] >= 0.0) || !std::isfinite(manning[c])) {
+                set_error("swe_set_fields: negative or non-finite Manning coefficient");
+                return SWE_EINVAL;
+            }
     if (bathy)
         for (int64_t c = 0; c < n; ++c)
             if (!std::isfinite(bathy[c])) { set_error("swe_set_fields: non-finite bed"); return SWE_EINVAL; }

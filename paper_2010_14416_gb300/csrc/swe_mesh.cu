@@ -176,7 +176,7 @@ int build_host_mesh(const double* nodes, int64_t n_nodes, const int32_t* tris, i
         const double qx = nodes[2 * v2], qy = nodes[2 * v2 + 1];
         const double a2 = (bx - ax) * (qy - ay) - (qx - ax) * (by - ay);
         if (!(a2 != 0.0) || !std::isfinite(a2)) { bad |= 2; continue; }
-        if (!(manning[i] >= 0.0) || !std::isfinite(bathy[i])) { bad |= 4; continue; }
+        if (!(manning[i] >= 0.0) || !std::isfinite(manning[i]) || !std::isfinite(bathy[i])) { bad |= 4; continue; }
         if (a2 < 0.0) std::swap(v1, v2);
         t[3 * i] = v0; t[3 * i + 1] = v1; t[3 * i + 2] = v2;
         cx[i] = (ax + bx + qx) / 3.0;
@@ -184,7 +184,7 @@ int build_host_mesh(const double* nodes, int64_t n_nodes, const int32_t* tris, i
     }
     if (bad & 1) { err = "swe_mesh_create: triangle with an out-of-range or repeated node"; return SWE_EMESH; }
     if (bad & 2) { err = "swe_mesh_create: triangle with zero or non-finite area"; return SWE_EMESH; }
-    if (bad & 4) { err = "swe_mesh_create: negative Manning coefficient or non-finite bed"; return SWE_EINVAL; }
+    if (bad & 4) { err = "swe_mesh_create: negative or non-finite Manning coefficient, or non-finite bed"; return SWE_EINVAL; }
 
     // neighbours: bucket half-edges by their lower node, match within buckets
     std::vector<int64_t> start(n_nodes + 1, 0);

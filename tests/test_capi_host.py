@@ -134,3 +134,14 @@ def test_invalid_configs_rejected_before_any_device_work(kw):
     with pytest.raises(capi.SWEError) as e:
         capi.Mesh(mi.nodes, mi.tris, mi.z, mi.manning, **kw)
     assert e.value.code == capi.SWE_EINVAL
+
+
+@pytest.mark.parametrize("field,value", [("manning", -0.01), ("manning", float("inf")), ("manning", float("nan")),
+                                         ("z", float("inf")), ("z", float("nan"))])
+def test_invalid_fields_rejected_before_any_device_work(field, value):
+    mi = mg.dam_break_4k()
+    z, manning = mi.z.copy(), mi.manning.copy()
+    (manning if field == "manning" else z)[17] = value
+    with pytest.raises(capi.SWEError) as e:
+        capi.Mesh(mi.nodes, mi.tris, z, manning)
+    assert e.value.code == capi.SWE_EINVAL
