@@ -451,7 +451,9 @@ SWE_API int swe_autotune(swe_mesh* mesh, int trial_steps, swe_tune* out);
  * (edge_pass 1: (256|128, 1, 1, 0)), times chunks of 4 to 64 tiles; and its
  * dynamically scheduled shapes (dynamic 1, stages 1: FP32 (128, 8) with
  * geometry_early 0|1, (256, 4) with 0; FP64 (128|256, 1) with 0) with chunks
- * of 1 to 32 tiles, each over trial_steps steps, twice; then, as for a mesh,
+ * of 1 to 32 tiles; and the activity-mode shapes with dynamically taken
+ * chunks (activity 1, dynamic 1) of 4 to 32 tiles; each over trial_steps
+ * steps, twice; then, as for a mesh,
  * a runoff of the shape in use and the (at most four) shapes within 5 % of the
  * fastest over max(32, 4 trial_steps) steps, keeping the first within 1 % of
  * the fastest there; then grids of half and two resident waves for the kept
@@ -466,7 +468,8 @@ SWE_API int swe_ensemble_autotune(swe_ensemble* ens, int trial_steps, swe_tune* 
  * swe_ensemble_autotune chose earlier): block_size, min_blocks, stages,
  * geometry_early, activity, edge_pass and dynamic must name a compiled shape
  * (listed above; stages is ignored with activity; edge_pass only for FP64
- * ensembles; at most one of activity, edge_pass, dynamic), chunk a power of
+ * ensembles; edge_pass excludes activity and dynamic; activity with dynamic
+ * needs chunks of at least 4 tiles), chunk a power of
  * two up to 4096 tiles,
  * grid the blocks to launch (0 = one resident wave); other fields are
  * ignored.  Results do not depend on the shape.  Errors: SWE_EINVAL.

@@ -199,7 +199,8 @@ cudaError_t ens_launch(swe_ensemble* E, int64_t step_index, const EnsPhysics& ph
     EnsArgs<T> a = ens_args<T>(E, step_index);
     a.g = (T)ph.g;
     a.h_dry = (T)ph.h_dry;
-    if (a.act_in) return Launch<T>::ensemble_step_act(a, E->block, E->min_blocks, E->geo_early, E->grid, st);
+    if (a.act_in)
+        return Launch<T>::ensemble_step_act(a, E->block, E->min_blocks, E->geo_early, E->grid, st, E->dynamic);
     if (E->dynamic) return Launch<T>::ensemble_step_dyn(a, E->block, E->min_blocks, E->geo_early, E->grid, st);
     return Launch<T>::ensemble_step(a, E->block, E->min_blocks, E->stages, E->geo_early, E->grid, st);
 }
@@ -508,7 +509,8 @@ int ens_time_shapes(swe_ensemble* E, const std::vector<EnsShape>& cand, int tria
                 a.sched_reset = (launch_no + 2) % 3;
                 ++launch_no;
                 if (sh.activity)
-                    return Launch<T>::ensemble_step_act(a, sh.block, sh.min_blocks, sh.geo_early, sh.grid, st);
+                    return Launch<T>::ensemble_step_act(a, sh.block, sh.min_blocks, sh.geo_early, sh.grid, st,
+                                                        sh.dynamic);
                 if (sh.dynamic)
                     return Launch<T>::ensemble_step_dyn(a, sh.block, sh.min_blocks, sh.geo_early, sh.grid, st);
                 return Launch<T>::ensemble_step(a, sh.block, sh.min_blocks, sh.stages, sh.geo_early, sh.grid, st);
@@ -566,6 +568,13 @@ int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
         const long long wave = (long long)std::max(per_sm, 1) * std::max(sms, 1);
         const unsigned gr = (unsigned)std::max(1LL, std::min((long long)(E->n_total / w[k][0]), wave));
         for (int cl2 = 2; cl2 <= 6; ++cl2) cand.push_back({w[k][0], w[k][1], 3, w[k][2], cl2, gr, 1, 0, 0});
+        // and with dynamically taken chunks (at least 4 tiles each)
+        int per_sm_d = 0;
+        e = Launch<T>::ensemble_act_resident_blocks(w[k][0], w[k][1], w[k][2], &per_sm_d, 1);
+        if (e != cudaSuccess) return efail(e, "swe_ensemble_autotune: occupancy");
+        const long long wave_d = (long long)std::max(per_sm_d, 1) * std::max(sms, 1);
+        const unsigned gr_d = (unsigned)std::max(1LL, std::min((long long)(E->n_total / w[k][0]), wave_d));
+        for (int cl2 = 2; cl2 <= 5; ++cl2) cand.push_back({w[k][0], w[k][1], 3, w[k][2], cl2, gr_d, 1, 0, 1});
     }
     int y[16][3];
     const int ny = std::min(Launch<T>::ensemble_dyn_variants(y, 16), 16);
@@ -638,7 +647,8 @@ int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
         const EnsShape b = cand[best];
         if (b.activity || b.edges || b.dynamic) {
             int per_sm = 0, sms = 0;
-            e = b.activity  ? Launch<T>::ensemble_act_resident_blocks(b.block, b.min_blocks, b.geo_early, &per_sm)
+            e = b.activity  ? Launch<T>::ensemble_act_resident_blocks(b.block, b.min_blocks, b.geo_early, &per_sm,
+                                                                      b.dynamic)
                 : b.dynamic ? Launch<T>::ensemble_dyn_resident_blocks(b.block, b.min_blocks, b.geo_early, &per_sm)
                             : Launch<T>::ensemble_edge_resident_blocks(b.block, b.min_blocks, b.stages, b.geo_early,
                                                                        &per_sm);
@@ -834,8 +844,9 @@ int swe_ensemble_step(swe_ensemble* E, int64_t nsteps, const double* cfl, double
 
 int swe_ensemble_set_shape(swe_ensemble* E, const swe_tune* shape) {
     if (!E || !shape || (shape->activity != 0 && shape->activity != 1) || (shape->edge_pass != 0 && shape->edge_pass != 1) ||
-        (shape->dynamic != 0 && shape->dynamic != 1) || shape->activity + shape->edge_pass + shape->dynamic > 1 ||
-        (shape->edge_pass && !E->eflux) ||
+        (shape->dynamic != 0 && shape->dynamic != 1) || shape->activity + shape->edge_pass > 1 ||
+        shape->edge_pass + shape->dynamic > 1 || (shape->edge_pass && !E->eflux) ||
+        (shape->activity && shape->dynamic && shape->chunk < 4) ||
         shape->chunk < 1 || (shape->chunk & (shape->chunk - 1)) || shape->chunk > 4096 || shape->grid < 0) {
         set_error("swe_ensemble_set_shape: bad arguments");
         return SWE_EINVAL;
@@ -849,12 +860,12 @@ int swe_ensemble_set_shape(swe_ensemble* E, const swe_tune* shape) {
     cudaError_t e;
     const int B = shape->block_size, M = shape->min_blocks, S = shape->stages, Gx = shape->geometry_early;
     if (E->precision == SWE_FP32) {
-        if (shape->dynamic) e = Launch<float>::ensemble_dyn_resident_blocks(B, M, Gx, &per_sm);
-        else if (shape->activity) e = Launch<float>::ensemble_act_resident_blocks(B, M, Gx, &per_sm);
+        if (shape->activity) e = Launch<float>::ensemble_act_resident_blocks(B, M, Gx, &per_sm, shape->dynamic);
+        else if (shape->dynamic) e = Launch<float>::ensemble_dyn_resident_blocks(B, M, Gx, &per_sm);
         else e = Launch<float>::ensemble_resident_blocks(B, M, S, Gx, &per_sm);
     } else {
-        if (shape->dynamic) e = Launch<double>::ensemble_dyn_resident_blocks(B, M, Gx, &per_sm);
-        else if (shape->activity) e = Launch<double>::ensemble_act_resident_blocks(B, M, Gx, &per_sm);
+        if (shape->activity) e = Launch<double>::ensemble_act_resident_blocks(B, M, Gx, &per_sm, shape->dynamic);
+        else if (shape->dynamic) e = Launch<double>::ensemble_dyn_resident_blocks(B, M, Gx, &per_sm);
         else if (shape->edge_pass) e = Launch<double>::ensemble_edge_resident_blocks(B, M, S, Gx, &per_sm);
         else e = Launch<double>::ensemble_resident_blocks(B, M, S, Gx, &per_sm);
     }

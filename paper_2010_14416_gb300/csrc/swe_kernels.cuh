@@ -1155,22 +1155,46 @@ __global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel_dyn(const En
 // tile by tile in the ensemble's round-robin chunk order.  Tiles are whole
 // (members are padded), so a tile is valid for every lane or for none.  Cells
 // are indexed with 32 bits (the host allows this kernel below 2^29 cells).
-template <typename T, int BLOCK, int MINB, bool GEO_EARLY>
+//
+// DYN takes the chunks dynamically, as ensemble_step_kernel_dyn does: the
+// block's j-th chunk is s_ch[j mod 3], drawn from the step's counter two
+// chunks ahead by thread 0 at the start of chunk j - 2 and published by the
+// barrier that starts chunk j - 1, so the pipeline's look-ahead of three
+// cells (into chunk j + 1 at most, chunks being at least 4 tiles) always
+// finds its tile.  The slot refilled at the start of chunk j held chunk
+// j - 1, which nothing reads after that barrier.
+template <typename T, int BLOCK, int MINB, bool GEO_EARLY, bool DYN = false>
 __global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel_act(const EnsArgs<T> a) {
     static_assert(kEnsPad % BLOCK == 0, "a tile must not straddle two members");
     constexpr unsigned kNone = 0xFFFFFFFFu;
     const unsigned G = gridDim.x, b = blockIdx.x;
-    const int cl2 = a.chunk_log2;
+    const int cl2 = a.chunk_log2;                   // >= 2 with DYN (the host checks)
     const unsigned n_tiles = (unsigned)(a.n_total / BLOCK);
     const unsigned n_chunks = (n_tiles + (1u << cl2) - 1) >> cl2;
     const unsigned my_chunks = b < n_chunks ? (n_chunks - 1 - b) / G + 1 : 0;
-    const unsigned k_end = my_chunks << cl2;
+    const unsigned k_end = DYN ? kNone : my_chunks << cl2;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __shared__ unsigned s_ch[3];
+    if constexpr (DYN) {
+        if (b == 0 && tid == 0) a.sched[a.sched_reset] = 0u;   // the counter of the step after next
+        if (tid == 0) {
+            s_ch[0] = atomicAdd(&a.sched[a.sched_slot], 1u);
+            s_ch[1] = atomicAdd(&a.sched[a.sched_slot], 1u);
+        }
+        __syncthreads();
+    }
     // this thread's cell in the block's k-th tile (kNone past the end)
     auto cell_of = [&](unsigned k) -> unsigned {
-        if (k >= k_end) return kNone;
-        const unsigned t = ((b + (k >> cl2) * G) << cl2) + (k & ((1u << cl2) - 1));
-        return t < n_tiles ? t * BLOCK + tid : kNone;
+        if constexpr (DYN) {
+            const unsigned ch = s_ch[(k >> cl2) % 3];
+            if (ch >= n_chunks) return kNone;
+            const unsigned t = (ch << cl2) + (k & ((1u << cl2) - 1));
+            return t < n_tiles ? t * BLOCK + tid : kNone;
+        } else {
+            if (k >= k_end) return kNone;
+            const unsigned t = ((b + (k >> cl2) * G) << cl2) + (k & ((1u << cl2) - 1));
+            return t < n_tiles ? t * BLOCK + tid : kNone;
+        }
     };
     __shared__ V4<T> st_own[3][BLOCK];
     __shared__ int4 st_topo[2][BLOCK];
@@ -1211,6 +1235,12 @@ __global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel_act(const En
     cp_async_commit();                                           // H_{-1} (empty)
     int k3 = 0, k2 = 0;
     for (unsigned k = 0; k < k_end; ++k) {
+        if constexpr (DYN) {
+            if ((k & ((1u << cl2) - 1)) == 0) {                  // a chunk starts (block-uniform)
+                if (k) __syncthreads();
+                if (tid == 0) s_ch[((k >> cl2) + 2) % 3] = atomicAdd(&a.sched[a.sched_slot], 1u);
+            }
+        }
         const unsigned c = cell_of(k);
         if (c == kNone) break;                                   // ragged last chunk (block-uniform)
         const int mk = a.tile_member[(c - tid) / kEnsPad];       // uniform across the block
@@ -1359,10 +1389,12 @@ struct Launch {
                                      unsigned grid, cudaStream_t st);
     static cudaError_t ensemble_resident_blocks(int block, int min_blocks, int stages, int geo_early, int* per_sm);
     static int ensemble_variants(int (*out)[4], int max);
-    // activity kernel of the ensemble: compiled (block, min_blocks, geo_early) shapes
+    // activity kernel of the ensemble: compiled (block, min_blocks, geo_early) shapes,
+    // with round-robin (dynamic 0) or dynamically taken (dynamic 1) chunks
     static cudaError_t ensemble_step_act(const EnsArgs<T>& a, int block, int min_blocks, int geo_early,
-                                         unsigned grid, cudaStream_t st);
-    static cudaError_t ensemble_act_resident_blocks(int block, int min_blocks, int geo_early, int* per_sm);
+                                         unsigned grid, cudaStream_t st, int dynamic = 0);
+    static cudaError_t ensemble_act_resident_blocks(int block, int min_blocks, int geo_early, int* per_sm,
+                                                    int dynamic = 0);
     static int ensemble_act_variants(int (*out)[3], int max);
     // edge pass of the ensemble (a.eflux set): edge kernel, then the cell pass of
     // one of its compiled (block, min_blocks, stages, geo_early) shapes

@@ -330,11 +330,12 @@ cudaError_t Launch<T>::ensemble_resident_blocks(int block, int min_blocks, int s
 
 template <typename T>
 cudaError_t Launch<T>::ensemble_step_act(const EnsArgs<T>& a, int block, int min_blocks, int geo_early,
-                                         unsigned grid, cudaStream_t st) {
-    if (grid == 0 || !a.act_in) return cudaErrorInvalidValue;
+                                         unsigned grid, cudaStream_t st, int dynamic) {
+    if (grid == 0 || !a.act_in || (dynamic && (!a.sched || a.chunk_log2 < 2))) return cudaErrorInvalidValue;
 #define SWE_LAUNCH(B, M, G) \
     if (block == B && min_blocks == M && geo_early == G) {                        \
-        ensemble_step_kernel_act<T, B, M, G != 0><<<grid, B, 0, st>>>(a);        \
+        if (dynamic) ensemble_step_kernel_act<T, B, M, G != 0, true><<<grid, B, 0, st>>>(a); \
+        else ensemble_step_kernel_act<T, B, M, G != 0><<<grid, B, 0, st>>>(a);   \
         return cudaGetLastError();                                                \
     }
     if constexpr (sizeof(T) == 4) {
@@ -347,10 +348,14 @@ cudaError_t Launch<T>::ensemble_step_act(const EnsArgs<T>& a, int block, int min
 }
 
 template <typename T>
-cudaError_t Launch<T>::ensemble_act_resident_blocks(int block, int min_blocks, int geo_early, int* per_sm) {
+cudaError_t Launch<T>::ensemble_act_resident_blocks(int block, int min_blocks, int geo_early, int* per_sm,
+                                                    int dynamic) {
 #define SWE_OCC(B, M, G) \
     if (block == B && min_blocks == M && geo_early == G)                          \
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, ensemble_step_kernel_act<T, B, M, G != 0>, B, 0);
+        return dynamic ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(             \
+                             per_sm, ensemble_step_kernel_act<T, B, M, G != 0, true>, B, 0) \
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(             \
+                             per_sm, ensemble_step_kernel_act<T, B, M, G != 0>, B, 0);
     if constexpr (sizeof(T) == 4) {
         SWE_ENS_ACT_VARIANTS_F32(SWE_OCC)
     } else {

@@ -114,6 +114,11 @@ def test_ensemble_launch_shapes_are_bitwise_neutral(precision):
     shapes += [dict(block_size=128, min_blocks=8 if f32 else 1, dynamic=1, chunk=1),
                dict(block_size=256, min_blocks=4 if f32 else 1, stages=3 if f32 else 1, chunk=4),
                dict(block_size=256, min_blocks=4 if f32 else 1, dynamic=1, chunk=8, grid=17)]
+    # activity bytes with dynamically taken chunks (at least 4 tiles)
+    shapes += [dict(block_size=128, min_blocks=8 if f32 else 1, activity=1, dynamic=1, chunk=4),
+               dict(block_size=256, min_blocks=4 if f32 else 1, activity=1, dynamic=1, chunk=32, grid=23),
+               dict(block_size=128, min_blocks=8 if f32 else 1, geometry_early=1 if f32 else 0, activity=1,
+                    dynamic=1, chunk=8, grid=3)]
     if not f32:   # the edge pass of FP64 ensembles
         shapes += [dict(block_size=256, min_blocks=1, edge_pass=1, chunk=8),
                    dict(block_size=128, min_blocks=1, edge_pass=1, chunk=4, grid=11)]
@@ -131,8 +136,10 @@ def test_ensemble_launch_shapes_are_bitwise_neutral(precision):
         ens.set_shape(block_size=512, min_blocks=2, activity=1)
     with pytest.raises(capi.SWEError):
         ens.set_shape(block_size=256, min_blocks=4 if f32 else 1, activity=1, edge_pass=1)
+    with pytest.raises(capi.SWEError):   # dynamic activity chunks hold at least 4 tiles
+        ens.set_shape(block_size=128, min_blocks=8 if f32 else 1, activity=1, dynamic=1, chunk=2)
     with pytest.raises(capi.SWEError):
-        ens.set_shape(block_size=128, min_blocks=8 if f32 else 1, activity=1, dynamic=1)
+        ens.set_shape(block_size=256, min_blocks=4 if f32 else 1, dynamic=1, edge_pass=1)
     ens.close()
     for m in meshes:
         m.close()
