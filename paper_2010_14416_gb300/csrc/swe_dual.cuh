@@ -63,12 +63,15 @@ __device__ __forceinline__ Dual<N> operator*(const Dual<N>& a, const Dual<N>& b)
     for (int k = 0; k < N; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k];
     return r;
 }
+// a / b: one division (1/b, which the derivative needs anyway) and a
+// multiplication for the value; the value may differ from the quotient
+// rounded once by an ulp, which the derivative does not notice.
 template <int N>
 __device__ __forceinline__ Dual<N> operator/(const Dual<N>& a, const Dual<N>& b) {
     Dual<N> r;
-    const double q = a.v / b.v;
-    r.v = q;
     const double rb = 1.0 / b.v;
+    const double q = a.v * rb;
+    r.v = q;
 #pragma unroll
     for (int k = 0; k < N; ++k) r.d[k] = (a.d[k] - q * b.d[k]) * rb;
     return r;
