@@ -392,7 +392,12 @@ def run_gpu(args, name):
                      "layout_bytes_per_launch": layout_bytes,
                      "layout_achieved": layout_achieved,
                      "layout_frac": layout_achieved / peak,
-                     "traffic_frac": (traffic / (kernel_ms * 1e-3) / 1e9 / peak) if traffic else None},
+                     "traffic_frac": (traffic / (kernel_ms * 1e-3) / 1e9 / peak) if traffic else None,
+                     "note": f"achieved/frac: {ab} B per cell-update for every cell (each array element "
+                             "read or written once); a quiet cell (dry, dry neighbours) needs less, so frac "
+                             "exceeds 1 on a mostly dry mesh; layout_frac: the bytes this launch's kernel "
+                             "must move at the measured active fraction; traffic_frac: ncu DRAM bytes per "
+                             "launch of the same kernel source and shape"},
         "e2e": {"value": ws * n * args.steps / e2e_s, "unit": "cell-updates/s",
                 "h2d_bytes_per_step": 3 * n * np.dtype(npdt).itemsize / args.steps,
                 "d2h_bytes_per_step": 3 * n * np.dtype(npdt).itemsize / args.steps,
