@@ -172,6 +172,19 @@ __device__ __forceinline__ T tmin(T a, T b) { return a < b ? a : b; }
 template <typename T>
 constexpr bool kOneDivision = std::is_same<T, double>::value;
 
+// h^(-1/3) in double without a division or a double cube root, for the
+// friction factor h^(-7/3) = r^7 and 1/h = r^3 (Eq 33-35): Newton's iteration
+// for r^-3 = h, r <- r (4 - h r^3) / 3, started from the FP32 reciprocal cube
+// root (relative error about 2^-22) and taken twice (the error squares each
+// time, to the rounding of the last step).  For positive normal h in the FP32
+// range; friction calls it for wet cells only (h > h_dry).
+__device__ __forceinline__ double inv_cbrt_newton(double h) {
+    double r = (double)rcbrtf((float)h);
+    r = r * fma(-h, r * r * r, 4.0) * (1.0 / 3.0);
+    r = r * fma(-h, r * r * r, 4.0) * (1.0 / 3.0);
+    return r;
+}
+
 // ---- comparisons of the flux path ------------------------------------------------
 // On GB300 the FP64 unit (2 operations per clock per SM) executes compares and
 // min/max of doubles as well as their arithmetic, and it bounds the FP64 step.
@@ -553,9 +566,9 @@ __device__ __forceinline__ void friction_update(T hi, T qx, T qy, T gm2, T Rh, T
             const T qn = A::sqrt_(qq);
             T cf, rh;                                       // c = g m^2 h^(-7/3), 1/h
             if constexpr (kOneDivision<T>) {
-                const T c3 = cbrt(hi), p = A::rcp_(hi * hi * c3);   // h^(-7/3); 1/h = h cbrt(h) h^(-7/3)
-                cf = gm2 * p;
-                rh = hi * c3 * p;
+                const T r = inv_cbrt_newton(hi), r3 = r * r * r;   // h^(-1/3), 1/h
+                cf = gm2 * (r3 * r3 * r);                            // h^(-7/3) = r^7
+                rh = r3;
             } else {
                 cf = gm2 * A::pow_m73(hi);
                 rh = A::rcp_(hi);

@@ -6,6 +6,11 @@
 // range, infinities, quiet NaNs of both signs, the dry threshold and its
 // neighbours) and seeded random bit patterns and magnitudes.  Prints one line
 // per helper with its mismatch count and exits 0 when all are zero.
+//
+// It also checks inv_cbrt_newton (the FP64 friction's h^(-1/3)) against
+// CUDA's double cube root over depths from 1e-6 to 1e5 m: the largest
+// relative errors of r, r^3 (= 1/h) and r^7 (= h^(-7/3)), in units of 2^-52,
+// printed as "ulps_r", "ulps_r3", "ulps_r7"; the run fails above 4, 8 and 16.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -41,6 +46,17 @@ __global__ void check(const double* xs, int n, const double* cs, int nc, unsigne
     if (le_zero(x) != (x <= 0.0)) atomicAdd(bad + 8, 1ULL);
     if (lt_zero(x) != (x < 0.0)) atomicAdd(bad + 9, 1ULL);
     if (!same_bits(max_zero(x), 0.0 > x ? 0.0 : x)) atomicAdd(bad + 10, 1ULL);
+}
+
+__global__ void check_cbrt(int n, double* worst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double h = exp(log(1e-6) + (log(1e5) - log(1e-6)) * (i + 0.5) / n);   // log-spaced depths
+    const double r = inv_cbrt_newton(h), r3 = r * r * r, r7 = r3 * r3 * r;
+    const double c = cbrt(h);
+    const double e[3] = {fabs(r * c - 1.0), fabs(r3 * h - 1.0), fabs(r7 * (h * h * c) - 1.0)};
+    for (int k = 0; k < 3; ++k)   // non-negative doubles order like their bit patterns
+        atomicMax((unsigned long long*)&worst[k], (unsigned long long)__double_as_longlong(e[k] / 2.220446049250313e-16));
 }
 
 static double from_bits(unsigned long long b) {
@@ -94,6 +110,16 @@ int main() {
         failed += bad[k] != 0;
     }
     std::printf("values %d\n", n);
+    double* dworst = nullptr;
+    const int nh = 1 << 20;
+    double worst[3] = {0.0, 0.0, 0.0};
+    if (cudaMalloc(&dworst, sizeof worst) != cudaSuccess) return 2;
+    cudaMemcpy(dworst, worst, sizeof worst, cudaMemcpyHostToDevice);
+    check_cbrt<<<nh / 256, 256>>>(nh, dworst);
+    if (cudaMemcpy(worst, dworst, sizeof worst, cudaMemcpyDeviceToHost) != cudaSuccess) return 2;
+    cudaFree(dworst);
+    std::printf("ulps_r %.2f\nulps_r3 %.2f\nulps_r7 %.2f\n", worst[0], worst[1], worst[2]);
+    failed += !(worst[0] <= 4.0) + !(worst[1] <= 8.0) + !(worst[2] <= 16.0);
     cudaFree(dx);
     cudaFree(dc);
     cudaFree(dbad);
