@@ -38,7 +38,7 @@ ALG_BYTES = {"f32": 16 * 4 + 12, "f64": 16 * 8 + 12}
 # by ncu on the 1M-cell canal (profiles/step_kernel_canal1m_fp64.md): the
 # cell-centric step evaluates every interior flux twice, the edge pass once;
 # quiet cells take no flux path and do no FP64 arithmetic
-FP64_FLOPS_PER_ACTIVE_CELL = {"cell": 761, "edge": 517}
+FP64_FLOPS_PER_ACTIVE_CELL = {"cell": 748, "edge": 505}
 # GB300 FP64: 2 DFMA per clock per SM, 152 SMs
 FP64_DFMA_PER_CLK_SM, N_SM = 2, 152
 
