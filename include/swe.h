@@ -51,7 +51,9 @@ extern "C" {
 #define SWE_ECUDA 4      /* a CUDA runtime call failed */
 #define SWE_ENONFINITE 5 /* a step produced a non-finite state */
 #define SWE_EDRY 6       /* every cell is dry: the CFL step (Eq 15) does not exist */
-#define SWE_ETIMEOUT 7   /* a bounded device-side wait gave up */
+#define SWE_ETIMEOUT 7   /* a bounded device-side wait gave up; reserved: no kernel of this
+                            library waits on another block or device (each step is one
+                            or two kernel launches, ordered by the stream) */
 
 /* ---- enums ---- */
 #define SWE_FP64 0
