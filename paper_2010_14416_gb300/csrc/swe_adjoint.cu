@@ -481,6 +481,7 @@ extern "C" {
 int swe_adjoint(swe_mesh* m, int64_t nsteps, double cfl, const int32_t* gauge_cells, int n_gauges,
                 const double* target_h, int checkpoint_every, double* loss, double* grad_manning,
                 double* grad_bathy, int where, double* dts_out) {
+    NvtxRange nvtx_range("swe_adjoint");
     return adjoint_impl(m, nsteps, cfl, gauge_cells, n_gauges, target_h, nsteps, checkpoint_every, loss,
                         grad_manning, grad_bathy, where, dts_out);
 }
@@ -488,11 +489,13 @@ int swe_adjoint(swe_mesh* m, int64_t nsteps, double cfl, const int32_t* gauge_ce
 int swe_adjoint_series(swe_mesh* m, int64_t nsteps, double cfl, const int32_t* gauge_cells, int n_gauges,
                        const double* targets, int64_t obs_every, int checkpoint_every, double* loss,
                        double* grad_manning, double* grad_bathy, int where, double* dts_out) {
+    NvtxRange nvtx_range("swe_adjoint_series");
     return adjoint_impl(m, nsteps, cfl, gauge_cells, n_gauges, targets, obs_every, checkpoint_every, loss,
                         grad_manning, grad_bathy, where, dts_out);
 }
 
 int swe_step_dt(swe_mesh* m, int64_t nsteps, const double* dts, double* t_out) {
+    NvtxRange nvtx_range("swe_step_dt");
     if (!m || nsteps < 0 || (nsteps > 0 && !dts)) { set_error("swe_step_dt: bad arguments"); return SWE_EINVAL; }
     if (!m->have_state) { set_error("swe_step_dt: no state set"); return SWE_EINVAL; }
     for (int64_t s = 0; s < nsteps; ++s)

@@ -742,6 +742,7 @@ int swe_set_state(swe_mesh* m, const void* h, const void* hu, const void* hv, in
 }
 
 int swe_step(swe_mesh* m, int64_t nsteps, double cfl, double* t_out) {
+    NvtxRange nvtx_range("swe_step");
     if (!m || nsteps < 0 || !(cfl > 0.0) || !std::isfinite(cfl)) { set_error("swe_step: bad arguments"); return SWE_EINVAL; }
     if (!m->have_state) { set_error("swe_step: no state set"); return SWE_EINVAL; }
     DeviceGuard dg(m->cfg.device);

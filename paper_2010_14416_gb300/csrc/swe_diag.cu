@@ -203,6 +203,7 @@ int swe_diagnostics(swe_mesh* m, swe_diag* out) {
 
 int swe_run_to_steady(swe_mesh* m, double cfl, double tol, int64_t check_every, int64_t max_steps,
                       int64_t* steps_done, int* converged, double* t_out) {
+    NvtxRange nvtx_range("swe_run_to_steady");
     if (!m || !(tol > 0.0) || check_every < 1 || max_steps < 0) {
         set_error("swe_run_to_steady: bad arguments");
         return SWE_EINVAL;

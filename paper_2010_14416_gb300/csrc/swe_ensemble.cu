@@ -782,6 +782,7 @@ int swe_ensemble_set_stream(swe_ensemble* E, void* stream) {
 }
 
 int swe_ensemble_step(swe_ensemble* E, int64_t nsteps, const double* cfl, double* t_out) {
+    NvtxRange nvtx_range("swe_ensemble_step");
     if (!E || nsteps < 0) { set_error("swe_ensemble_step: bad arguments"); return SWE_EINVAL; }
     EnsDeviceGuard dg(E->device);
     std::vector<double> c(E->n_members, 0.9);
@@ -898,6 +899,7 @@ int swe_ensemble_set_shape(swe_ensemble* E, const swe_tune* shape) {
 }
 
 int swe_ensemble_autotune(swe_ensemble* E, int trial_steps, swe_tune* out) {
+    NvtxRange nvtx_range("swe_ensemble_autotune");
     if (!E || trial_steps < 0) { set_error("swe_ensemble_autotune: bad arguments"); return SWE_EINVAL; }
     if (trial_steps == 0) trial_steps = 4;
     EnsDeviceGuard dg(E->device);

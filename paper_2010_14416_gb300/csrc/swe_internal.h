@@ -8,10 +8,21 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/swe.h"
 #include "swe_kernels.cuh"
 
 namespace swe {
+
+// A named NVTX range over a public call (swe_step, swe_adjoint, ...), for
+// timeline tools; a no-op costing a few nanoseconds when none is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Result of the host preprocessing (Section 3.1 geometry, neighbours across
 // shared edges, locality order), in the internal cell order.

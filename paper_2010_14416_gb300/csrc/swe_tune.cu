@@ -246,6 +246,7 @@ int autotune_t(swe_mesh* m, int trial_steps, swe_tune* out) {
 extern "C" {
 
 int swe_autotune(swe_mesh* m, int trial_steps, swe_tune* out) {
+    NvtxRange nvtx_range("swe_autotune");
     if (!m || trial_steps < 0) { set_error("swe_autotune: bad arguments"); return SWE_EINVAL; }
     if (!m->have_state) { set_error("swe_autotune: no state set"); return SWE_EINVAL; }
     if (trial_steps == 0) trial_steps = 8;
