@@ -308,6 +308,18 @@ def test_edge_cases():
         assert e.value.code == capi.SWE_EDRY
         assert np.array_equal(m.get_state()[0], zero)
         m.close()
+    # a non-finite depth in a wet cell: the step flags it (SWE_ENONFINITE), in
+    # every mode and precision (the failure is made on the host, in the input)
+    bad = mi.h.copy()
+    k = int(np.flatnonzero(mi.h > 5.0)[mi.n_cells // 8])
+    bad[k] = np.nan
+    for kw in (dict(), dict(activity=1), dict(edge_pass=1), dict(precision=capi.SWE_FP32)):
+        m = _gpu_mesh(mi, **kw)
+        m.set_state(*(a.astype(m.dtype) for a in (bad, mi.hu, mi.hv)))
+        with pytest.raises(capi.SWEError) as e:
+            m.step(3)
+        assert e.value.code == capi.SWE_ENONFINITE, kw
+        m.close()
     # bad arguments are rejected on the host
     m = _gpu_mesh(mi)
     with pytest.raises(capi.SWEError) as e:
