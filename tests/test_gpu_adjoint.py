@@ -153,14 +153,16 @@ def test_full_size_adjoint_1m_cells_2000_steps():
         return float(((h[gauges] - target) ** 2).sum())
 
     errs = []
-    for _ in range(3):
+    for _ in range(32):   # 32 random directions, as the workload asks
         vz = rng.standard_normal(mi.n_cells)
         vm = 0.01 * rng.standard_normal(mi.n_cells)
         eps = 1e-6
         fd = (loss(mi.z + eps * vz, mi.manning + eps * vm) - loss(mi.z - eps * vz, mi.manning - eps * vm)) / (2 * eps)
         ad = float(gz @ vz + gm @ vm)
         errs.append(abs(fd - ad) / abs(ad))
+    errs = np.array(errs)
     assert np.median(errs) <= 1e-5, errs
+    assert (errs <= 1e-4).mean() >= 0.9, errs
     m.close()
 
 
