@@ -415,11 +415,14 @@ typedef struct swe_tune {
     int edge_pass;           /* chosen edge-pass mode (swe_config.edge_pass) */
     int dynamic;             /* ensembles: 1 = blocks take chunks from a per-step counter as they
                                 finish, 0 = fixed round-robin chunks; 0 for a mesh */
-    int chunk;               /* ensembles: tiles per round-robin chunk; 0 for a mesh */
+    int chunk;               /* ensembles: tiles per chunk (round-robin or taken dynamically);
+                                0 for a mesh */
     int64_t grid;            /* blocks launched per step */
     double cells_per_thread; /* cells each thread updates per step: cells / (grid * block_size) */
-    double ms_best;          /* measured time per step of the chosen shape (ms) */
-    double ms_before;        /* measured time per step of the shape in use before the call (ms) */
+    double ms_best;          /* measured time per step of the chosen shape (ms; from the runoff
+                                when one ran) */
+    double ms_before;        /* measured time per step of the shape in use before the call (ms;
+                                from the runoff, which always includes it, when one ran) */
     int n_candidates;        /* shapes timed */
 } swe_tune;
 
