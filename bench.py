@@ -8,7 +8,10 @@ boundary fluxes, semi-implicit friction, update and the CFL min-reduction
 Default workload: the 12,999,168-cell synthetic river reach (20 km x 2 km,
 partially dry, Q = 2000 m^3/s inflow, fixed-stage outflow), FP32 state with
 FP64 time step.  Its working set (~1 GB) is far larger than L2, so no flush
-is needed between steps.
+is needed between steps.  The default run also measures every other
+workload (the fully wet river, the FP64 canal, the FP32 and FP64 ensembles,
+the adjoint) with short step counts and reports each as a sub-record of the
+same line; ``--workload`` runs one workload alone.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
 oracle instead, on the host cores.
@@ -34,10 +37,11 @@ import numpy as np  # noqa: E402
 # 1/|Omega|, inscribed radius (4) + L n of three edges (6) values, plus three
 # int32 neighbour indices
 ALG_BYTES = {"f32": 16 * 4 + 12, "f64": 16 * 8 + 12}
-# FP64 flops (2 x DFMA + DADD + DMUL) per cell that runs the flux path, counted
-# by ncu on the 1M-cell canal (profiles/step_kernel_canal1m_fp64.md): the
-# cell-centric step evaluates every interior flux twice, the edge pass once;
-# quiet cells take no flux path and do no FP64 arithmetic
+# FP64 flops (2 x DFMA + DADD + DMUL) per cell that runs the flux path, from
+# ncu's instruction counts of the two FP64 step kernels on the 1M-cell
+# dry-bed canal divided by the cells that ran the flux path: the cell-centric
+# step evaluates every interior flux twice, the edge pass once; quiet cells
+# take no flux path and do no FP64 arithmetic
 FP64_FLOPS_PER_ACTIVE_CELL = {"cell": 748, "edge": 505}
 # GB300 FP64: 2 DFMA per clock per SM, 152 SMs
 FP64_DFMA_PER_CLK_SM, N_SM = 2, 152
@@ -46,6 +50,10 @@ WORKLOADS = {
     "river13m_fp32": dict(maker="river_13m", precision="f32", steps=1000,
                           desc="synthetic river reach 20 km x 2 km, 12,999,168 triangles, partially dry, "
                                "Q=2000 m3/s inflow, stage outflow, Manning U[0.02,0.06]; FP32 state, FP64 dt"),
+    "river13m_wet_fp32": dict(maker="river_13m_wet", precision="f32", steps=1000,
+                              desc="synthetic river reach 20 km x 2 km, 12,999,168 triangles, fully wet (depth >= "
+                                   "0.5 m), Q=2000 m3/s inflow, stage outflow, Manning U[0.02,0.06]; FP32 state, "
+                                   "FP64 dt"),
     "canal1m_fp64": dict(maker="dam_break_dry_1m", precision="f64", steps=2000,
                          desc="dry-bed dam break, canal 200 m x 10 m, 1,000,000 triangles, n=0.03; FP64"),
     "canal1m_fp32": dict(maker="dam_break_dry_1m", precision="f32", steps=2000,
@@ -249,227 +257,243 @@ def run_reference(args, name):
     return 0
 
 
-def run_gpu(args, name):
-    import torch
+class GpuContext:
+    """Device, stream, rank and library of one bench process."""
 
-    from paper_2010_14416_gb300 import build as libbuild
-    from paper_2010_14416_gb300 import capi
+    def __init__(self):
+        import torch
 
-    dist, rank, ws, local = _dist()
+        from paper_2010_14416_gb300 import build as libbuild
+        from paper_2010_14416_gb300 import capi
+
+        self.torch, self.capi = torch, capi
+        self.dist, self.rank, self.ws, self.local = _dist()
+        torch.cuda.set_device(self.local)
+        self.dev = torch.device("cuda", self.local)
+        if self.rank == 0:
+            libbuild.build()
+        if self.dist:
+            self.dist.barrier()
+        self.stream = torch.cuda.Stream(device=self.dev)
+        self.inputs = {}
+
+    def make_input(self, name):
+        # workloads sharing a generator share its (seeded, deterministic) input
+        maker = WORKLOADS[name]["maker"]
+        if maker not in self.inputs:
+            self.inputs[maker] = _make_input(name)
+        return self.inputs[maker]
+
+    def timed(self, fn):
+        """CUDA-event time (ms) of fn() on the bench stream, synchronised on both
+        sides after a barrier, with nvidia-smi clocks sampled meanwhile; the
+        slowest rank's time."""
+        torch = self.torch
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        clocks = ClockSampler(self.local)
+        if self.rank == 0:
+            clocks.start()
+        if self.dist:
+            self.dist.barrier()
+        torch.cuda.synchronize(self.dev)
+        ev0.record(self.stream)
+        fn()
+        ev1.record(self.stream)
+        torch.cuda.synchronize(self.dev)
+        ms = ev0.elapsed_time(ev1)
+        clk = clocks.stop() if self.rank == 0 else None
+        return max_over_ranks(self.dist, [ms])[0], clk
+
+
+def _warmup_for(steps, warmup, graph_steps=48):
+    """Warm-up steps actually run before a timed region of `steps` steps: the
+    requested number, raised when the timed call will replay a CUDA graph so
+    that the graph is captured before the timed region (captures start at a
+    step index that is a multiple of six)."""
+    return max(warmup, graph_steps + 6) if steps >= graph_steps else warmup
+
+
+def _hbm_roofline(wl, n, kernel_ms, active_frac, activity, name, shape, peak, peak_kind):
+    """HBM roofline of an FP32 step: bytes this kernel's data layout must move
+    per launch at the measured active fraction (frac), the ncu DRAM bytes of
+    the same kernel source and launch shape when a committed record has them
+    (traffic_frac), and the dense per-cell model for reference."""
+    ab = ALG_BYTES[wl["precision"]]
+    rec = 16 if wl["precision"] == "f32" else 32
+    act_bytes = 2 if activity else 0
+    # an active cell reads its state, topology and geometry records and writes
+    # its state; a quiet cell (dry, dry neighbours, no inflow/stage edge)
+    # needs no geometry, and with activity bytes no topology either
+    layout_bytes = n * (active_frac * (4 * rec + 16 + (0 if wl["precision"] == "f32" else 8) + act_bytes) +
+                        (1 - active_frac) * (2 * rec + (act_bytes if act_bytes else 16)))
+    s = kernel_ms * 1e-3
+    traffic = _traffic(name, shape)
+    dense = ab * n / s / 1e9
+    return {"bound": "hbm", "achieved": layout_bytes / s / 1e9, "peak": peak, "unit": "GB/s",
+            "frac": layout_bytes / s / 1e9 / peak, "traffic": traffic,
+            "traffic_frac": (traffic / s / 1e9 / peak) if traffic else None,
+            "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
+            "bytes_per_launch": layout_bytes, "active_cell_fraction": active_frac,
+            "bytes_per_active_cell": 4 * rec + 16 + act_bytes, "bytes_per_quiet_cell": 2 * rec + (act_bytes or 16),
+            "dense_model_bytes_per_cell": ab, "dense_model_frac": dense / peak,
+            "note": "achieved/frac: the bytes this launch's kernel must move at the measured fraction of cells "
+                    "that run the flux path (bytes_per_active_cell, bytes_per_quiet_cell); traffic_frac: ncu "
+                    "DRAM bytes per launch of the same kernel source and shape; dense_model_frac: "
+                    f"{ab} B for every cell, which a quiet cell (dry among dry neighbours) does not need, so it "
+                    "exceeds 1 on a mostly dry mesh"}
+
+
+def _fp64_roofline(n, kernel_ms, active_frac, edge_pass, hbm):
+    """FP64 steps are bound by the FP64 pipe: FP64 flops per cell that ran the
+    flux path (ncu counts) against the pipe's rate from its unit count and the
+    maximum SM clock."""
+    sm_mhz = _peak_clock()
+    peak64 = FP64_DFMA_PER_CLK_SM * 2 * N_SM * sm_mhz * 1e6 / 1e12
+    per_cell = FP64_FLOPS_PER_ACTIVE_CELL["edge" if edge_pass else "cell"]
+    ach64 = per_cell * active_frac * n / (kernel_ms * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": ach64, "peak": peak64, "unit": "TFLOP/s", "frac": ach64 / peak64,
+            "traffic": None,
+            "peak_source": f"nominal, not measured: {FP64_DFMA_PER_CLK_SM} DFMA/clk/SM x 2 flops x {N_SM} SMs "
+                           f"x {sm_mhz:.0f} MHz (the FP64 pipe's unit count at the maximum SM clock; "
+                           "MEASURED_PEAKS.json has no FP64 figure)",
+            "flops_per_active_cell": per_cell, "active_cell_fraction": active_frac,
+            "flops_counted": "2 x DFMA + DADD + DMUL per cell that ran the flux path (ncu instruction counts)",
+            "hbm": {k: v for k, v in hbm.items() if k not in ("bound", "traffic")}}
+
+
+def _traffic(name, shape):
+    tpath = os.path.join(ROOT, "profiles", f"traffic_{name}.json")
+    if not os.path.exists(tpath):
+        return None
+    with open(tpath) as f:
+        tr = json.load(f)
+    if tr.get("kernel_hash") != _kernel_hash():
+        return None
+    for cap in tr.get("captures", []):
+        if cap.get("shape") == _shape_key(shape):
+            return cap.get("bytes_per_launch")
+    return None
+
+
+def measure_mesh(ctx, name, steps, warmup, shape_spec=None, e2e=True):
+    """One mesh workload: W warm-up steps, the library's autotuner (outside
+    the timed region; its trials leave the state untouched), K timed steps
+    replayed from CUDA graphs, and (e2e) three whole jobs through the C ABI
+    from pinned host arrays."""
+    torch, capi = ctx.torch, ctx.capi
     wl = WORKLOADS[name]
     prec = capi.SWE_FP32 if wl["precision"] == "f32" else capi.SWE_FP64
     npdt = np.float32 if prec == capi.SWE_FP32 else np.float64
     tdt = torch.float32 if prec == capi.SWE_FP32 else torch.float64
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    if rank == 0:
-        libbuild.build()
-    if dist:
-        dist.barrier()
-    mi = _make_input(name)
-    fixed = _shape_kwargs(args.shape)
-    m = capi.Mesh(mi.nodes, mi.tris, mi.z, mi.manning, precision=prec, device=local, **fixed)
+    mi = ctx.make_input(name)
+    fixed = _shape_kwargs(shape_spec)
+    m = capi.Mesh(mi.nodes, mi.tris, mi.z, mi.manning, precision=prec, device=ctx.local, **fixed)
     for pairs, kind, value in mi.bcs:
         m.set_bc(pairs, kind, value)
-    stream = torch.cuda.Stream(device=dev)
-    m.set_stream(stream)
-    h0 = torch.tensor(mi.h.astype(npdt), device=dev)
-    hu0 = torch.tensor(mi.hu.astype(npdt), device=dev)
-    hv0 = torch.tensor(mi.hv.astype(npdt), device=dev)
-    torch.cuda.synchronize(dev)
+    m.set_stream(ctx.stream)
+    h0 = torch.tensor(mi.h.astype(npdt), device=ctx.dev)
+    hu0 = torch.tensor(mi.hu.astype(npdt), device=ctx.dev)
+    hv0 = torch.tensor(mi.hv.astype(npdt), device=ctx.dev)
+    torch.cuda.synchronize(ctx.dev)
     m.set_state(h0, hu0, hv0)
-    # warm-up: at least two graph lengths, so the CUDA graph is captured and
-    # replayed before the timed region
-    args.warmup = max(args.warmup, 96)
-    m.step(args.warmup, 0.9, sync=True)
-    # launch shape chosen by the library's autotuner on the warmed-up state
-    # (the tuning call leaves the state untouched), then the graph is recaptured
     if fixed:
         shape = dict(block_size=fixed["block_size"], min_blocks=fixed["min_blocks"], stages=fixed["stages"],
                      geometry_early=fixed["geometry_early"], activity=fixed["activity"],
-                     edge_pass=fixed["edge_pass"], grid=fixed["grid"], chunk=0, fixed=True)
+                     edge_pass=fixed["edge_pass"], grid=fixed["grid"], chunk=0,
+                     cell_pairs=fixed.get("cell_pairs", 0), fixed=True)
     else:
-        shape = m.autotune(8)
-    m.step(96, 0.9, sync=True)
+        shape = m.autotune(8)   # on the initial state, which the trials leave untouched
+    warm = _warmup_for(steps, warmup)
+    m.step(warm, 0.9, sync=True)
     n = mi.n_cells
-
-    # ---- device-resident timed region ----
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    clocks = ClockSampler(local)
-    if rank == 0:
-        clocks.start()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
     active0 = m.info()["n_active"]
-    ev0.record(stream)
-    m.step(args.steps, 0.9, sync=False)
-    ev1.record(stream)
-    torch.cuda.synchronize(dev)
-    ms = ev0.elapsed_time(ev1)
-    clk = clocks.stop() if rank == 0 else None
+    ms, clk = ctx.timed(lambda: m.step(steps, 0.9, sync=False))
     info = m.info()
-    t_sim = info["t"]
-    active_frac = (info["n_active"] - active0) / float(n * args.steps)
+    active_frac = (info["n_active"] - active0) / float(n * steps)
     m.synchronize()
-    ms = max_over_ranks(dist, [ms])[0]
-
+    peak, peak_kind = _peaks()
+    kernel_ms = ms / steps
+    roof = _hbm_roofline(wl, n, kernel_ms, active_frac, shape.get("activity"), name, shape, peak, peak_kind)
+    if wl["precision"] == "f64":
+        roof = _fp64_roofline(n, kernel_ms, active_frac, shape.get("edge_pass"), roof)
+    rec = {
+        "metric": "cell-updates/s", "value": ctx.ws * n * steps / (ms * 1e-3), "unit": "cell-updates/s",
+        "n_gpus": ctx.ws, "steps": steps, "warmup": warm, "ms_per_step": kernel_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": wl["precision"], "data": "synthetic",
+        "config": {"workload": wl["desc"], "cells": n, "parallelism": f"replicas{ctx.ws}",
+                   "l2": "working set ~%.2f GB > 129 MB L2, no flush needed" % (
+                       (2 * 4 + 8) * n * (4 if wl["precision"] == "f32" else 8) / 1e9 + 16 * n / 1e9),
+                   "steps_before_timed": warm, "simulated_time_s": info["t"], "reorder": "hilbert",
+                   "graph_steps": 48, "launch_shape": _shape_key(shape), "autotune": shape},
+        "roofline": roof,
+        "gpu_launches": steps * (2 if shape.get("edge_pass") else 1),
+        "clocks": clk,
+    }
+    m.close()
+    if not e2e:
+        return rec, mi
     # ---- end to end through the C ABI with pinned host buffers ----
     hp = [torch.from_numpy(a.astype(npdt)).pin_memory() for a in (mi.h, mi.hu, mi.hv)]
     out = [torch.empty(n, dtype=tdt).pin_memory() for _ in range(3)]
-    # the mesh of the timed device run's launch shape (tuned once above, as a
-    # user would tune once and create later meshes with the chosen shape)
-    keys = ("block_size", "min_blocks", "stages", "geometry_early", "activity", "edge_pass", "grid")
-    m2 = capi.Mesh(mi.nodes, mi.tris, mi.z, mi.manning, precision=prec, device=local,
+    # a mesh with the timed run's launch shape (tuned once above, as a user
+    # would tune once and create later meshes with the chosen shape)
+    keys = ("block_size", "min_blocks", "stages", "geometry_early", "activity", "edge_pass", "grid", "cell_pairs")
+    m2 = capi.Mesh(mi.nodes, mi.tris, mi.z, mi.manning, precision=prec, device=ctx.local,
                    **{k: int(shape[k]) for k in keys})
     for pairs, kind, value in mi.bcs:
         m2.set_bc(pairs, kind, value)
-    m2.set_stream(stream)
+    m2.set_stream(ctx.stream)
     m2.set_state(*hp)
-    m2.step(max(args.warmup, 6) + 96, 0.9)   # warm-up: the step graph is captured before the timed job
+    m2.step(warm, 0.9)   # the same warm-up: any step graph is captured before the timed jobs
     m2.get_state(out)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    # three identical jobs, each timed whole; the median is reported
+    for _ in range(2):   # two untimed jobs: first-use costs of the copies stay out of the timed ones
+        m2.set_state(*hp)
+        m2.step(steps, 0.9, sync=False)
+        m2.get_state(out)
+    if ctx.dist:
+        ctx.dist.barrier()
+    torch.cuda.synchronize(ctx.dev)
     jobs = []
-    for _ in range(3):
+    for _ in range(3):   # three identical jobs, each timed whole; the median is reported
         t0 = time.perf_counter()
         m2.set_state(*hp)
-        m2.step(args.steps, 0.9, sync=False)
+        m2.step(steps, 0.9, sync=False)
         m2.get_state(out)
         jobs.append(time.perf_counter() - t0)
     m2.close()
-    e2e_s = max_over_ranks(dist, [sorted(jobs)[1]])[0]
-
-    peak, peak_kind = _peaks()
-    ab = ALG_BYTES[wl["precision"]]
-    kernel_ms = ms / args.steps
-    achieved = ab * n / (kernel_ms * 1e-3) / 1e9
-    # bytes this layout must move per launch: an active cell reads its state,
-    # topology and geometry records and writes its state; a quiet cell (dry,
-    # all neighbours dry, no inflow/stage edge) needs no geometry
-    # With activity bytes a quiet cell reads its state record and its own
-    # activity byte and writes its state and one cleared byte: no topology.
-    rec = 16 if wl["precision"] == "f32" else 32
-    act_bytes = 2 if shape.get("activity") else 0
-    layout_bytes = n * (active_frac * (4 * rec + 16 + (0 if wl["precision"] == "f32" else 8) + act_bytes) +
-                        (1 - active_frac) * (2 * rec + (act_bytes if act_bytes else 16)))
-    layout_achieved = layout_bytes / (kernel_ms * 1e-3) / 1e9
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", f"traffic_{name}.json")
-    if os.path.exists(tpath):
-        with open(tpath) as f:
-            tr = json.load(f)
-        if tr.get("kernel_hash") == _kernel_hash():
-            for cap in tr.get("captures", []):
-                if cap.get("shape") == _shape_key(shape):
-                    traffic = cap.get("bytes_per_launch")
-    line = {
-        "metric": "cell-updates/s",
-        "value": ws * n * args.steps / (ms * 1e-3),
-        "unit": "cell-updates/s",
-        "n_gpus": ws,
-        "steps": args.steps,
-        "warmup": args.warmup,
-        "ms_per_step": kernel_ms,
-        "higher_is_better": True,
-        "scaling": "weak",
-        "vs_baseline": None,
-        "dtype": wl["precision"],
-        "data": "synthetic",
-        "config": {"workload": wl["desc"], "cells": n, "parallelism": f"replicas{ws}",
-                   "l2": "working set ~%.2f GB > 129 MB L2, no flush needed" % (
-                       (2 * 4 + 8) * n * (4 if wl["precision"] == "f32" else 8) / 1e9 + 16 * n / 1e9),
-                   "simulated_time_s": t_sim, "reorder": "hilbert", "graph_steps": 48,
-                   "launch_shape": _shape_key(shape), "autotune": shape},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic,
-                     "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
-                     "alg_bytes_per_cell": ab,
-                     "active_cell_fraction": active_frac,
-                     "layout_bytes_per_launch": layout_bytes,
-                     "layout_achieved": layout_achieved,
-                     "layout_frac": layout_achieved / peak,
-                     "traffic_frac": (traffic / (kernel_ms * 1e-3) / 1e9 / peak) if traffic else None,
-                     "note": f"achieved/frac: {ab} B per cell-update for every cell (each array element "
-                             "read or written once); a quiet cell (dry, dry neighbours) needs less, so frac "
-                             "exceeds 1 on a mostly dry mesh; layout_frac: the bytes this launch's kernel "
-                             "must move at the measured active fraction; traffic_frac: ncu DRAM bytes per "
-                             "launch of the same kernel source and shape"},
-        "e2e": {"value": ws * n * args.steps / e2e_s, "unit": "cell-updates/s",
-                "h2d_bytes_per_step": 3 * n * np.dtype(npdt).itemsize / args.steps,
-                "d2h_bytes_per_step": 3 * n * np.dtype(npdt).itemsize / args.steps,
-                "jobs_s": jobs,
-                "note": "one job: swe_set_state from pinned host arrays, swe_step(steps), swe_get_state to "
-                        "pinned host arrays, timed whole; median of three jobs; bytes averaged per step; a "
-                        "second mesh created with the device run's launch shape"},
-        "gpu_launches": args.steps * (2 if shape.get("edge_pass") else 1),
-        "clocks": clk,
-    }
-    if wl["precision"] == "f64":
-        # the FP64 step is bound by the FP64 pipe, not HBM: report it against
-        # the FP64 ALU peak at the maximum SM clock; the HBM figures stay as context
-        sm_mhz = _peak_clock()
-        peak64 = FP64_DFMA_PER_CLK_SM * 2 * N_SM * sm_mhz * 1e6 / 1e12
-        per_cell = FP64_FLOPS_PER_ACTIVE_CELL["edge" if shape.get("edge_pass") else "cell"]
-        flops = per_cell * active_frac * n
-        ach64 = flops / (kernel_ms * 1e-3) / 1e12
-        hbm = line["roofline"]
-        line["roofline"] = {"bound": "alu", "achieved": ach64, "peak": peak64, "unit": "TFLOP/s",
-                            "frac": ach64 / peak64, "traffic": traffic,
-                            "peak_source": f"derived: {FP64_DFMA_PER_CLK_SM} DFMA/clk/SM x 2 flops x {N_SM} SMs x "
-                                           f"{sm_mhz:.0f} MHz (FP64 pipe)",
-                            "flops_per_active_cell": per_cell,
-                            "active_cell_fraction": active_frac,
-                            "hbm": {k: v for k, v in hbm.items() if k not in ("bound", "traffic")}}
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(mi, args.cpu_budget)
-    m.close()
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    if dist:
-        dist.barrier()
-        dist.destroy_process_group()
-    return 0
+    e2e_s = max_over_ranks(ctx.dist, [sorted(jobs)[1]])[0]
+    rec["e2e"] = {"value": ctx.ws * n * steps / e2e_s, "unit": "cell-updates/s",
+                  "h2d_bytes_per_step": 3 * n * np.dtype(npdt).itemsize / steps,
+                  "d2h_bytes_per_step": 3 * n * np.dtype(npdt).itemsize / steps, "jobs_s": jobs,
+                  "note": "one job: swe_set_state from pinned host arrays, swe_step(steps), swe_get_state to "
+                          "pinned host arrays, timed whole; median of three jobs; bytes averaged per step; a "
+                          "second mesh created with the device run's launch shape"}
+    return rec, mi
 
 
-def run_gpu_ensemble(args, name):
+def measure_ensemble(ctx, name, steps, warmup, ens_shape=None):
     """All members in one CUDA-graph launch per call, against the plain
-    solver launched member after member on the same stream."""
-    import torch
-
-    from paper_2010_14416_gb300 import build as libbuild
-    from paper_2010_14416_gb300 import capi
-
-    dist, rank, ws, local = _dist()
+    solver launched member after member on the same stream (first with the
+    library's default launch shapes, then with every member autotuned)."""
+    torch, capi = ctx.torch, ctx.capi
     wl = WORKLOADS[name]
     prec = capi.SWE_FP32 if wl["precision"] == "f32" else capi.SWE_FP64
     npdt = np.float32 if prec == capi.SWE_FP32 else np.float64
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    if rank == 0:
-        libbuild.build()
-    if dist:
-        dist.barrier()
-    mis = _make_input(name)
-    stream = torch.cuda.Stream(device=dev)
+    mis = ctx.make_input(name)
     meshes = []
     for mi in mis:
-        m = capi.Mesh(mi.nodes, mi.tris, mi.z, mi.manning, precision=prec, device=local)
+        m = capi.Mesh(mi.nodes, mi.tris, mi.z, mi.manning, precision=prec, device=ctx.local)
         for pairs, kind, value in mi.bcs:
             m.set_bc(pairs, kind, value)
-        m.set_stream(stream)
+        m.set_stream(ctx.stream)
         m.set_state(mi.h.astype(npdt), mi.hu.astype(npdt), mi.hv.astype(npdt))
         meshes.append(m)
     n = sum(mi.n_cells for mi in mis)
     ens = capi.Ensemble(meshes)
-    ens.set_stream(stream)
-    args.warmup = max(args.warmup, 6)
-    ens.step(args.warmup)
-    if args.ens_shape:
-        v = [int(x) for x in args.ens_shape.split(",")]
+    ens.set_stream(ctx.stream)
+    if ens_shape:
+        v = [int(x) for x in ens_shape.split(",")]
         keys = ("block_size", "min_blocks", "stages", "geometry_early", "activity", "edge_pass", "dynamic", "chunk",
                 "grid")
         if len(v) != len(keys):
@@ -478,201 +502,173 @@ def run_gpu_ensemble(args, name):
         ens.set_shape(**shape)
         shape["fixed"] = True
     else:
-        shape = ens.autotune(4)   # launch shape chosen by the library's autotuner
-    ens.step(6)
-    # the timed call is captured once (untimed) for its step phase, then replayed
-    ens.step(args.steps)
-    realign = (-args.steps) % 6          # back to the same step phase mod 6
+        shape = ens.autotune(4)   # on the initial states, which the trials leave untouched
+    # warm-up: the timed call's graph is captured (for its step phase mod 6)
+    # before the timed region, which then starts at the same phase
+    warm = max(warmup, 6)
+    warm += (-warm) % 6
+    ens.step(warm)
+    ens.step(steps)
+    realign = (-steps) % 6
     if realign:
         ens.step(realign)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    clocks = ClockSampler(local)
-    if rank == 0:
-        clocks.start()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
+    warm_total = warm + steps + realign
     active0 = ens.info(0)["n_active"]
-    ev0.record(stream)
-    ens.step(args.steps, sync=False)
-    ev1.record(stream)
-    torch.cuda.synchronize(dev)
-    ms = ev0.elapsed_time(ev1)
-    clk = clocks.stop() if rank == 0 else None
-    active_frac = (ens.info(0)["n_active"] - active0) / float(n * args.steps)
-    # per-member launches of the plain solver, same steps: first with the
-    # library's default launch shapes (the solver as created), then with each
-    # member's launch shape autotuned on its own mesh
+    ms, clk = ctx.timed(lambda: ens.step(steps, sync=False))
+    active_frac = (ens.info(0)["n_active"] - active0) / float(n * steps)
+    # per-member launches of the plain solver, the same number of steps
     for m in meshes:
         m.step(48)
-    torch.cuda.synchronize(dev)
-    ev0.record(stream)
-    for m in meshes:
-        m.step(args.steps, 0.9, sync=False)
-    ev1.record(stream)
-    torch.cuda.synchronize(dev)
-    ms_default = ev0.elapsed_time(ev1)
+    ms_default, _ = ctx.timed(lambda: [m.step(steps, 0.9, sync=False) for m in meshes])
     member_shapes = []
     for m in meshes:
         m.step(96)
         member_shapes.append(m.autotune(4))
         m.step(48)
-    torch.cuda.synchronize(dev)
-    ev0.record(stream)
-    for m in meshes:
-        m.step(args.steps, 0.9, sync=False)
-    ev1.record(stream)
-    torch.cuda.synchronize(dev)
-    ms_plain = ev0.elapsed_time(ev1)
-    ms, ms_plain, ms_default = max_over_ranks(dist, [ms, ms_plain, ms_default])
+    ms_plain, _ = ctx.timed(lambda: [m.step(steps, 0.9, sync=False) for m in meshes])
     peak, peak_kind = _peaks()
-    ab = ALG_BYTES[wl["precision"]]
-    kernel_ms = ms / args.steps
-    achieved = ab * n / (kernel_ms * 1e-3) / 1e9
-    line = {
-        "metric": "cell-updates/s",
-        "value": ws * n * args.steps / (ms * 1e-3),
-        "unit": "cell-updates/s",
-        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": kernel_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": wl["precision"], "data": "synthetic",
-        "config": {"workload": wl["desc"], "cells": n, "members": len(mis), "parallelism": f"replicas{ws}",
-                   "l2": "working set > 129 MB L2, no flush needed",
+    kernel_ms = ms / steps
+    roof = _hbm_roofline(wl, n, kernel_ms, active_frac, shape.get("activity"), name, shape, peak, peak_kind)
+    roof["traffic"], roof["traffic_frac"] = None, None
+    if wl["precision"] == "f64":
+        roof = _fp64_roofline(n, kernel_ms, active_frac, shape.get("edge_pass"), roof)
+    rec = {
+        "metric": "cell-updates/s", "value": ctx.ws * n * steps / (ms * 1e-3), "unit": "cell-updates/s",
+        "n_gpus": ctx.ws, "steps": steps, "warmup": warm_total, "ms_per_step": kernel_ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": wl["precision"],
+        "data": "synthetic",
+        "config": {"workload": wl["desc"], "cells": n, "members": len(mis), "parallelism": f"replicas{ctx.ws}",
+                   "l2": "working set > 129 MB L2, no flush needed", "steps_before_timed": warm_total,
                    "launch_shape": _shape_key(shape), "autotune": shape,
                    "member_shapes": sorted({tuple(_shape_key(t)[:6]) for t in member_shapes})},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
-                     "alg_bytes_per_cell": ab},
-        "per_member_launches": {"value": ws * n * args.steps / (ms_plain * 1e-3), "unit": "cell-updates/s",
-                                "ms_per_step": ms_plain / args.steps},
+        "roofline": roof,
+        "per_member_launches": {"value": ctx.ws * n * steps / (ms_plain * 1e-3), "unit": "cell-updates/s",
+                                "ms_per_step": ms_plain / steps,
+                                "note": "the plain solver on each member in turn, each member autotuned"},
         "speedup_vs_per_member": ms_plain / ms,
-        "per_member_launches_default_shapes": {"value": ws * n * args.steps / (ms_default * 1e-3),
-                                               "unit": "cell-updates/s", "ms_per_step": ms_default / args.steps,
+        "per_member_launches_default_shapes": {"value": ctx.ws * n * steps / (ms_default * 1e-3),
+                                               "unit": "cell-updates/s", "ms_per_step": ms_default / steps,
                                                "speedup": ms_default / ms},
-        "gpu_launches": args.steps * (2 if shape.get("edge_pass") else 1),
+        "gpu_launches": steps * (2 if shape.get("edge_pass") else 1),
         "clocks": clk,
     }
-    if wl["precision"] == "f64":
-        # bound by the FP64 pipe, as the plain FP64 step (the HBM figures stay as context)
-        sm_mhz = _peak_clock()
-        peak64 = FP64_DFMA_PER_CLK_SM * 2 * N_SM * sm_mhz * 1e6 / 1e12
-        per_cell = FP64_FLOPS_PER_ACTIVE_CELL["edge" if shape.get("edge_pass") else "cell"]
-        ach64 = per_cell * active_frac * n / (kernel_ms * 1e-3) / 1e12
-        hbm = line["roofline"]
-        line["roofline"] = {"bound": "alu", "achieved": ach64, "peak": peak64, "unit": "TFLOP/s",
-                            "frac": ach64 / peak64, "traffic": None,
-                            "peak_source": f"derived: {FP64_DFMA_PER_CLK_SM} DFMA/clk/SM x 2 flops x {N_SM} SMs x "
-                                           f"{sm_mhz:.0f} MHz (FP64 pipe)",
-                            "flops_per_active_cell": per_cell, "active_cell_fraction": active_frac,
-                            "hbm": {k: v for k, v in hbm.items() if k not in ("bound", "traffic")}}
     ens.close()
     for m in meshes:
         m.close()
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    if dist:
-        dist.barrier()
-        dist.destroy_process_group()
-    return 0
+    return rec
 
 
-def run_gpu_adjoint(args, name):
-    """Forward run plus reverse sweep of the discrete adjoint, timed with
-    CUDA events; a bench step is one time step of the forward and its
-    reverse (recompute + two adjoint kernels)."""
-    import torch
-
-    from paper_2010_14416_gb300 import build as libbuild
-    from paper_2010_14416_gb300 import capi, meshgen
-
-    dist, rank, ws, local = _dist()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    if rank == 0:
-        libbuild.build()
-    if dist:
-        dist.barrier()
-    mi = _make_input(name)
+def measure_adjoint(ctx, name, steps, warmup, shape_spec=None):
+    """Forward run plus reverse sweep of the discrete adjoint; a bench step is
+    one time step of the forward and its reverse (recompute + two adjoint
+    kernels)."""
+    torch, capi = ctx.torch, ctx.capi
+    from paper_2010_14416_gb300 import meshgen
+    mi = ctx.make_input(name)
     n = mi.n_cells
     gauges = meshgen.gauge_cells(n, 64, seed=1)
     xi = meshgen.perturbation(n, 101)
-    stream = torch.cuda.Stream(device=dev)
-
-    fixed = _shape_kwargs(args.shape)
+    fixed = _shape_kwargs(shape_spec)
 
     def mesh(z, man):
-        m = capi.Mesh(mi.nodes, mi.tris, z, man, precision=capi.SWE_FP64, device=local, **fixed)
+        m = capi.Mesh(mi.nodes, mi.tris, z, man, precision=capi.SWE_FP64, device=ctx.local, **fixed)
         for pairs, kind, value in mi.bcs:
             m.set_bc(pairs, kind, value)
-        m.set_stream(stream)
+        m.set_stream(ctx.stream)
         m.set_state(mi.h, mi.hu, mi.hv)
         return m
 
     # seeded target: the same run with perturbed Manning and bed
     tm = mesh(mi.z + 0.05 * xi, mi.manning * (1 + 0.1 * xi))
-    tm.step(args.steps, 0.9)
+    tm.step(steps, 0.9)
     target = tm.get_state()[0][gauges]
     tm.close()
     m = mesh(mi.z, mi.manning)
-    gm = torch.empty(n, dtype=torch.float64, device=dev)
-    gz = torch.empty(n, dtype=torch.float64, device=dev)
-    warm = max(args.warmup, 3)
+    gm = torch.empty(n, dtype=torch.float64, device=ctx.dev)
+    gz = torch.empty(n, dtype=torch.float64, device=ctx.dev)
+    # launch shape of the forward and recomputed steps, chosen by the autotuner
+    shape = dict(fixed, chunk=0, fixed=True) if fixed else m.autotune(4)
+    warm = max(warmup, 3)
     m.adjoint(warm, gauges, target, checkpoint_every=50, out=(gm, gz))
     m.set_state(mi.h, mi.hu, mi.hv)
-    # launch shape of the forward and recomputed steps, chosen by the autotuner
-    if fixed:
-        shape = dict(fixed, chunk=0, fixed=True)
-    else:
-        shape = m.autotune(4)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    clocks = ClockSampler(local)
-    if rank == 0:
-        clocks.start()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    ev0.record(stream)
-    loss, _, _, dts = m.adjoint(args.steps, gauges, target, checkpoint_every=50, out=(gm, gz))
-    ev1.record(stream)
-    torch.cuda.synchronize(dev)
-    ms = ev0.elapsed_time(ev1)
-    clk = clocks.stop() if rank == 0 else None
-    # forward alone, same steps, for the ratio
+    res = {}
+    ms, clk = ctx.timed(lambda: res.update(r=m.adjoint(steps, gauges, target, checkpoint_every=50, out=(gm, gz))))
+    loss = res["r"][0]
+    # the forward alone, the same steps from the same state, for the ratio
     m.set_state(mi.h, mi.hu, mi.hv)
-    m.step(96, 0.9)
+    m.step(_warmup_for(steps, 0), 0.9)
     m.set_state(mi.h, mi.hu, mi.hv)
-    torch.cuda.synchronize(dev)
-    ev0.record(stream)
-    m.step(args.steps, 0.9, sync=False)
-    ev1.record(stream)
-    torch.cuda.synchronize(dev)
-    ms_fwd = ev0.elapsed_time(ev1)
-    ms, ms_fwd = max_over_ranks(dist, [ms, ms_fwd])
-    line = {
-        "metric": "cell-updates/s", "value": ws * n * args.steps / (ms * 1e-3), "unit": "cell-updates/s",
-        "n_gpus": ws, "steps": args.steps, "warmup": warm, "ms_per_step": ms / args.steps,
+    ms_fwd, _ = ctx.timed(lambda: m.step(steps, 0.9, sync=False))
+    rec = {
+        "metric": "cell-updates/s", "value": ctx.ws * n * steps / (ms * 1e-3), "unit": "cell-updates/s",
+        "n_gpus": ctx.ws, "steps": steps, "warmup": warm, "ms_per_step": ms / steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOADS[name]["desc"], "cells": n, "parallelism": f"replicas{ws}",
-                   "checkpoint_every": 50, "gauges": 64, "autotune": shape},
+        "config": {"workload": WORKLOADS[name]["desc"], "cells": n, "parallelism": f"replicas{ctx.ws}",
+                   "checkpoint_every": 50, "gauges": 64, "autotune": shape,
+                   "steps_before_timed": warm, "note": "the warm-up is an adjoint call of `warmup` steps"},
         "loss": loss,
         "grad_norms": {"manning": float(gm.norm()), "bathy": float(gz.norm())},
-        "forward_only": {"value": n * args.steps / (ms_fwd * 1e-3), "ms_per_step": ms_fwd / args.steps},
+        "forward_only": {"value": n * steps / (ms_fwd * 1e-3), "ms_per_step": ms_fwd / steps},
         "adjoint_over_forward": ms / ms_fwd,
-        "roofline": {"bound": "alu", "note": "FP64 arithmetic on forward-mode duals: the adjoint kernels and "
-                                             "the forward steps are bound by the FP64 pipe"},
+        "roofline": {"bound": "alu", "note": "FP64 arithmetic on forward-mode duals and hand-written "
+                                             "transposes: the adjoint kernels and the forward steps are bound "
+                                             "by the FP64 pipe"},
         # per step: the forward step and its recomputation (two kernels each with the
         # edge pass), then the two adjoint kernels
-        "gpu_launches": args.steps * (2 * (2 if shape.get("edge_pass") else 1) + 2),
+        "gpu_launches": steps * (2 * (2 if shape.get("edge_pass") else 1) + 2),
         "clocks": clk,
     }
     m.close()
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    if dist:
-        dist.barrier()
-        dist.destroy_process_group()
+    return rec
+
+
+def _measure(ctx, name, steps, warmup, args, e2e):
+    if WORKLOADS[name]["maker"] == "ensemble":
+        return measure_ensemble(ctx, name, steps, warmup, args.ens_shape), None
+    if name.startswith("adjoint"):
+        return measure_adjoint(ctx, name, steps, warmup, args.shape), None
+    return measure_mesh(ctx, name, steps, warmup, args.shape, e2e=e2e)
+
+
+# the other workloads, reported beside the headline in the default run with
+# step counts that keep the whole command within a few minutes
+SUBRECORDS = {
+    "river13m_wet_fp32": dict(steps=200, warmup=6),
+    "canal1m_fp64": dict(steps=200, warmup=6),
+    "ensemble256_fp32": dict(steps=96, warmup=6),
+    "ensemble256_fp64": dict(steps=24, warmup=6),
+    "adjoint1m_fp64": dict(steps=200, warmup=3),
+}
+
+
+def _compact(rec):
+    keep = ("value", "unit", "ms_per_step", "steps", "warmup", "dtype", "roofline", "speedup_vs_per_member",
+            "per_member_launches", "per_member_launches_default_shapes", "adjoint_over_forward", "forward_only",
+            "grad_norms", "loss", "gpu_launches", "clocks")
+    out = {k: rec[k] for k in keep if k in rec}
+    cfg = rec.get("config", {})
+    out["config"] = {k: cfg[k] for k in ("workload", "cells", "members", "launch_shape", "steps_before_timed",
+                                         "checkpoint_every", "gauges") if k in cfg}
+    return out
+
+
+def run_gpu(args, name, subrecords):
+    ctx = GpuContext()
+    rec, mi = _measure(ctx, name, args.steps, args.warmup, args, e2e=True)
+    if mi is not None and ctx.rank == 0 and ctx.ws == 1 and not args.no_cpu_baseline:
+        rec["cpu_baseline"] = cpu_baseline(mi, args.cpu_budget)
+    if subrecords:
+        rec["subrecords"] = {}
+        for sub, sp in SUBRECORDS.items():
+            if sub == name:
+                continue
+            r, _ = _measure(ctx, sub, sp["steps"], sp["warmup"], args, e2e=False)
+            rec["subrecords"][sub] = _compact(r)
+    if ctx.rank == 0:
+        print(json.dumps(rec), flush=True)
+    if ctx.dist:
+        ctx.dist.barrier()
+        ctx.dist.destroy_process_group()
     return 0
 
 
@@ -681,9 +677,9 @@ def _shape_kwargs(spec):
     if not spec:
         return {}
     v = [int(x) for x in spec.split(",")]
-    if len(v) != 7:
-        raise SystemExit("--shape needs block,min_blocks,stages,geometry_early,activity,edge_pass,grid")
-    keys = ("block_size", "min_blocks", "stages", "geometry_early", "activity", "edge_pass", "grid")
+    if len(v) not in (7, 8):
+        raise SystemExit("--shape needs block,min_blocks,stages,geometry_early,activity,edge_pass,grid[,cell_pairs]")
+    keys = ("block_size", "min_blocks", "stages", "geometry_early", "activity", "edge_pass", "grid", "cell_pairs")
     return dict(zip(keys, v))
 
 
@@ -692,7 +688,9 @@ def _shape_key(t):
     choice."""
     k = [t["block_size"], t["min_blocks"], t["stages"], t["geometry_early"], t["activity"], t["edge_pass"],
          t["grid"]]
-    return k + [t["chunk"], t.get("dynamic", 0)] if t.get("chunk") else k
+    if t.get("chunk"):
+        return k + [t["chunk"], t.get("dynamic", 0)]
+    return k + [1] if t.get("cell_pairs") else k
 
 
 def _kernel_hash():
@@ -710,7 +708,10 @@ def main():
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=12)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="river13m_fp32")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=None,
+                    help="one workload alone (default: the 13M river, with every other workload as a sub-record)")
+    ap.add_argument("--no-subrecords", action="store_true",
+                    help="the default run without the other workloads' sub-records")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--members", type=int, default=256, help="ensemble workloads: number of members")
@@ -721,18 +722,17 @@ def main():
                     help="mesh workloads: block,min_blocks,stages,geometry_early,activity,edge_pass,grid -- use "
                          "this launch shape instead of autotuning (for profiling the shape a tuned run chose)")
     args = ap.parse_args()
+    explicit = args.workload is not None
+    name = args.workload or "river13m_fp32"
     if args.steps is None:
-        args.steps = WORKLOADS[args.workload]["steps"]
+        args.steps = WORKLOADS[name]["steps"]
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
-        return run_reference(args, args.workload)
+        return run_reference(args, name)
     MEMBERS[0] = args.members
-    if WORKLOADS[args.workload]["maker"] == "ensemble":
-        return run_gpu_ensemble(args, args.workload)
-    if args.workload.startswith("adjoint"):
-        return run_gpu_adjoint(args, args.workload)
-    return run_gpu(args, args.workload)
+    subrecords = not explicit and not args.no_subrecords
+    return run_gpu(args, name, subrecords)
 
 
 if __name__ == "__main__":

@@ -74,12 +74,17 @@ extern "C" {
 #define SWE_FLUX_HLLC 0       /* Eq 17-25 with the HLLC third component (Eq 24), the paper's scheme */
 #define SWE_FLUX_HLL 1        /* Eq 17-18 for all three components (the HLL flux the paper starts from) */
 
+#define SWE_ADJOINT_TRANSPOSE 0 /* reverse step by hand-written transposes, each interior edge once */
+#define SWE_ADJOINT_DUAL 1      /* reverse step on forward-mode dual numbers, each edge from both cells */
+
 typedef struct swe_mesh swe_mesh;
 
 typedef struct swe_config {
     int precision;    /* SWE_FP64 (default) or SWE_FP32 */
     double g;         /* gravitational acceleration, default 9.81 m/s^2; finite and > 0 */
-    double h_dry;     /* wet/dry threshold, default 1e-6 m; finite and > 0 */
+    double h_dry;     /* wet/dry threshold, default 1e-6 m; finite and >= FLT_MIN (1.18e-38): a wet
+                         depth is then a normal float, which the FP32 kernels and the FP64 friction
+                         term's h^(-1/3) iteration (started from the float cube root) need */
     int reorder;      /* SWE_REORDER_*, default SWE_REORDER_HILBERT */
     int block_size;   /* threads per block of the step kernel; 0 = library default */
     int graph_steps;  /* steps captured per CUDA graph; 0 = default, < 0 = no graphs */
@@ -120,10 +125,37 @@ typedef struct swe_config {
     int grid;         /* blocks launched per step by the step kernel (each block loops over its
                          share of the cells); 0 = default, one resident wave; larger values are
                          clamped to one cell per thread.  Results do not depend on it */
+    int debug_checks; /* 1: every step, ensemble and adjoint kernel checks each neighbour index,
+                         edge index and boundary group it is about to use against the mesh's
+                         sizes (swe_debug_code_ok) before the access; an out-of-range one is not
+                         used (the edge is taken as a wall) and sets a bit of the device status
+                         word, which the next synchronising call returns as SWE_EMESH.  A stand-in
+                         for a memory checker on the library's own index tables; it costs one
+                         branch per cell when off.  0 (default): no checks.  Results of a valid
+                         mesh do not depend on it */
+    int cell_pairs;   /* FP32 only: 1 = each thread updates two cells at once (cells 64 t + l and
+                         64 t + 32 + l for warp tile t and lane l), every FP32 multiply, add and
+                         fused multiply-add one paired instruction for both; 0 (default) = one
+                         cell per thread.  Compiled (block_size, min_blocks): (128, 3|4|5),
+                         (256, 2); stages and geometry_early are ignored.  Not with activity or
+                         edge_pass.  Results do not depend on it (the one-cell kernels round
+                         every operation the same way) */
 } swe_config;
 
 /* Fills *cfg with the defaults listed above. */
 SWE_API void swe_config_default(swe_config* cfg);
+
+/*
+ * The check that swe_config.debug_checks applies to each neighbour code
+ * before it is used (the paper keeps each cell's neighbours in a table,
+ * Section 4.2; here a code >= 0 names a neighbour cell, bit 30 marking the
+ * edge's right side, and a code < 0 names boundary group -1 - code).
+ * Returns 1 when the code can be used on a mesh of n_cells cells with
+ * n_groups boundary groups: an interior code whose cell index (bits 0-29) is
+ * below n_cells, or a boundary code whose group is below n_groups; else 0.
+ * Host-callable, touches no device.
+ */
+SWE_API int swe_debug_code_ok(int32_t code, int64_t n_cells, int n_groups);
 
 /*
  * Builds a mesh (Section 3.1): orients every triangle counter-clockwise, finds
@@ -272,13 +304,35 @@ SWE_API int swe_run_to_steady(swe_mesh* mesh, double cfl, double tol, int64_t ch
  *   loss        one host double
  *   grad_manning, grad_bathy: [n_tris] doubles in the caller's cell order, on
  *               the host (where = SWE_HOST) or device (SWE_DEVICE); either may be NULL
- * Device memory: about (nsteps/checkpoint_every + checkpoint_every + 4) x 32 B per cell.
+ * Each reverse step recomputes the forward right-hand side, transposes the
+ * cell update (friction solve, Eq 33-37) and then every interior edge's flux
+ * and bed source terms (Eq 12-30) once per edge for both of its cells
+ * (swe_adjoint_method).
+ * Device memory: about (nsteps/checkpoint_every + checkpoint_every + 4) x 32 B per cell,
+ * plus 64 B per interior edge.
  * Errors: SWE_EINVAL (FP32 mesh, no state, bad gauge), SWE_ENOMEM, SWE_ECUDA,
- * SWE_ENONFINITE, SWE_EDRY.
+ * SWE_ENONFINITE, SWE_EDRY, SWE_EMESH (debug checks).
  */
 SWE_API int swe_adjoint(swe_mesh* mesh, int64_t nsteps, double cfl, const int32_t* gauge_cells, int n_gauges,
                         const double* target_h, int checkpoint_every, double* loss, double* grad_manning,
                         double* grad_bathy, int where, double* dts_out);
+
+/*
+ * Chooses how swe_adjoint and swe_adjoint_series form each reverse step's
+ * edge terms (not in the paper, which gives no adjoint):
+ *   SWE_ADJOINT_TRANSPOSE (default): one pass over the interior edges runs
+ *     each edge's flux forward once and then backwards through its
+ *     operations (hand-written transposes of Eq 12-30), giving the adjoints
+ *     of both cells' states and beds; a cell pass adds them up in a fixed
+ *     order.
+ *   SWE_ADJOINT_DUAL: every cell differentiates its own and its neighbours'
+ *     edge terms by running the forward's device functions on
+ *     four-component forward-mode dual numbers (each edge from both sides);
+ *     slower, and kept as an independent check of the transposes.
+ * Both give the gradient of the same discrete map (to rounding).
+ * Errors: SWE_EINVAL (NULL mesh, unknown method).
+ */
+SWE_API int swe_adjoint_method(swe_mesh* mesh, int method);
 
 /*
  * Same as swe_adjoint for a time-series misfit: observations every obs_every
@@ -389,8 +443,10 @@ SWE_API int swe_mesh_preprocess(const double* nodes, int64_t n_nodes, const int3
  *   dt_out     one device double; written in stream order on `cuda_stream`
  * Runs on the calling thread's current device.  Its scratch is a 512 KiB
  * static device array that every GPU loading the library holds until the
- * process exits; the first call on each device looks up that array's
- * address, so make the first call on a device before any stream capture.
+ * process exits.  Every call looks up that array's address on the current
+ * device (which allocates nothing, and stays right after a cudaDeviceReset);
+ * the first call on a device also loads the library's device code there, so
+ * make the first call on a device before any stream capture.
  * All calls share the array: calls that overlap on the GPU (for instance on
  * two streams) race and may return wrong values.
  * Errors: SWE_EINVAL, SWE_ECUDA.
@@ -424,6 +480,8 @@ typedef struct swe_tune {
     double ms_before;        /* measured time per step of the shape in use before the call (ms;
                                 from the runoff, which always includes it, when one ran) */
     int n_candidates;        /* shapes timed */
+    int cell_pairs;          /* chosen two-cells-per-thread mode (swe_config.cell_pairs); 0 for an
+                                ensemble */
 } swe_tune;
 
 /*

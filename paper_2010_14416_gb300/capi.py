@@ -22,6 +22,7 @@ SWE_REORDER_NONE, SWE_REORDER_RCM, SWE_REORDER_HILBERT = 0, 1, 2
 SWE_BC_WALL, SWE_BC_INFLOW, SWE_BC_TRANSMISSIVE, SWE_BC_STAGE = 0, 1, 2, 3
 SWE_HOST, SWE_DEVICE = 0, 1
 SWE_FLUX_HLLC, SWE_FLUX_HLL = 0, 1
+SWE_ADJOINT_TRANSPOSE, SWE_ADJOINT_DUAL = 0, 1
 
 ERROR_NAMES = {1: "SWE_EINVAL", 2: "SWE_EMESH", 3: "SWE_ENOMEM", 4: "SWE_ECUDA",
                5: "SWE_ENONFINITE", 6: "SWE_EDRY", 7: "SWE_ETIMEOUT"}
@@ -34,14 +35,16 @@ EXPORTS = ["swe_config_default", "swe_mesh_create", "swe_mesh_destroy", "swe_set
            "swe_ensemble_step", "swe_ensemble_get_state", "swe_ensemble_get_info", "swe_adjoint",
            "swe_adjoint_series",
            "swe_step_dt", "swe_set_fields", "swe_diagnostics", "swe_run_to_steady", "swe_autotune",
-           "swe_ensemble_autotune", "swe_ensemble_set_shape", "swe_last_error"]
+           "swe_ensemble_autotune", "swe_ensemble_set_shape", "swe_debug_code_ok", "swe_adjoint_method",
+           "swe_last_error"]
 
 
 class swe_config(C.Structure):
     _fields_ = [("precision", C.c_int), ("g", C.c_double), ("h_dry", C.c_double),
                 ("reorder", C.c_int), ("block_size", C.c_int), ("graph_steps", C.c_int),
                 ("device", C.c_int), ("min_blocks", C.c_int), ("stages", C.c_int), ("flux", C.c_int),
-                ("geometry_early", C.c_int), ("activity", C.c_int), ("edge_pass", C.c_int), ("grid", C.c_int)]
+                ("geometry_early", C.c_int), ("activity", C.c_int), ("edge_pass", C.c_int), ("grid", C.c_int),
+                ("debug_checks", C.c_int), ("cell_pairs", C.c_int)]
 
 
 class swe_info(C.Structure):
@@ -60,7 +63,7 @@ class swe_tune(C.Structure):
     _fields_ = [("block_size", C.c_int), ("min_blocks", C.c_int), ("stages", C.c_int), ("geometry_early", C.c_int),
                 ("activity", C.c_int), ("edge_pass", C.c_int), ("dynamic", C.c_int), ("chunk", C.c_int),
                 ("grid", C.c_int64), ("cells_per_thread", C.c_double), ("ms_best", C.c_double),
-                ("ms_before", C.c_double), ("n_candidates", C.c_int)]
+                ("ms_before", C.c_double), ("n_candidates", C.c_int), ("cell_pairs", C.c_int)]
 
 
 class SWEError(RuntimeError):
@@ -101,6 +104,7 @@ def load():
     lib.swe_riemann_flux_kind.argtypes = [C.c_int, C.c_int, C.c_int64] + [vp] * 6 + [C.c_double, C.c_double] + \
         [vp] * 4 + [vp]
     lib.swe_mesh_preprocess.argtypes = [vp, C.c_int64, vp, C.c_int64, C.c_int, vp, vp, vp, vp, vp]
+    lib.swe_debug_code_ok.argtypes = [C.c_int32, C.c_int64, C.c_int]
     lib.swe_cfl_dt_noalloc.argtypes = [C.c_int, C.c_int64, vp, vp, vp, vp, C.c_double, C.c_double,
                                        C.c_double, vp, vp]
     lib.swe_ensemble_create.argtypes = [vp, C.c_int, C.POINTER(vp)]
@@ -165,7 +169,8 @@ class Mesh:
 
     def __init__(self, nodes, tris, bathy, manning, precision=SWE_FP64, reorder=None,
                  block_size=0, graph_steps=0, device=0, g=9.81, h_dry=1e-6, min_blocks=0, stages=0,
-                 flux=SWE_FLUX_HLLC, geometry_early=0, activity=0, edge_pass=0, grid=0):
+                 flux=SWE_FLUX_HLLC, geometry_early=0, activity=0, edge_pass=0, grid=0, debug_checks=0,
+                 cell_pairs=0):
         lib = load()
         cfg = config_default()
         cfg.precision = precision
@@ -178,6 +183,8 @@ class Mesh:
         cfg.activity = activity
         cfg.edge_pass = edge_pass
         cfg.grid = grid
+        cfg.debug_checks = debug_checks
+        cfg.cell_pairs = cell_pairs
         cfg.flux = flux
         cfg.g, cfg.h_dry = g, h_dry
         nodes = np.ascontiguousarray(nodes, dtype=np.float64).reshape(-1, 2)
@@ -255,6 +262,11 @@ class Mesh:
         inf = swe_info()
         check(load().swe_get_info(self._h, C.byref(inf)))
         return {k: getattr(inf, k) for k, _ in swe_info._fields_}
+
+    def adjoint_method(self, method):
+        """SWE_ADJOINT_TRANSPOSE (default) or SWE_ADJOINT_DUAL: how the reverse
+        step forms its edge terms (see swe_adjoint_method)."""
+        check(load().swe_adjoint_method(self._h, int(method)))
 
     def adjoint(self, nsteps, gauges, target, cfl=0.9, checkpoint_every=50, out=None):
         """Gauge-misfit loss after nsteps and its gradient w.r.t. (manning,
@@ -406,6 +418,12 @@ def mesh_preprocess(nodes, tris, reorder=SWE_REORDER_HILBERT):
                                      perm.ctypes.data, code.ctypes.data, ln.ctypes.data, ia.ctypes.data,
                                      rin.ctypes.data))
     return dict(perm=perm, code=code, ln=ln, inv_area=ia, rin=rin)
+
+
+def debug_code_ok(code, n_cells, n_groups):
+    """swe_debug_code_ok: whether a neighbour code is usable on a mesh of
+    n_cells cells with n_groups boundary groups (the debug-checks predicate)."""
+    return bool(load().swe_debug_code_ok(int(np.int32(code)), int(n_cells), int(n_groups)))
 
 
 def riemann_flux(precision, hL, unL, utL, hR, unR, utR, G1, G2, G3, S=None, g=9.81, h_dry=1e-6,

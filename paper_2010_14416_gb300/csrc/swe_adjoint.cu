@@ -55,11 +55,32 @@ struct AdjArgs {
     const V4<double>* __restrict__ eflux;
     const double* __restrict__ esrc;
     const int4* __restrict__ eidx;
+    long long n_edges;
+    // phase 2 on transposes: the interior edges (canonical orientation), their
+    // L n and 1/|L n|, and per edge the adjoints of its two cells' states
+    const int2* __restrict__ ecells;
+    const double* __restrict__ eln;
+    const double* __restrict__ erl;
+    V4<double>* __restrict__ ed;
+    // debug checks: neighbour codes and edge indices are checked before use
+    int debug;
+    int n_groups;
+    unsigned* status;
 };
+
+// a neighbour code of cell i checked before use when debug checks are on: an
+// unusable one is flagged and taken as a wall (group 0)
+__device__ __forceinline__ int adj_code(const AdjArgs& a, int c) {
+    if (a.debug && !code_ok(c, a.n, a.n_groups)) {
+        atomicOr(a.status, kStatusBadIndex);
+        return -1;
+    }
+    return c;
+}
 
 // the forward's unit normal and length of an edge, from its 1/|L n|
 __device__ __forceinline__ void unit_normal(double lx, double ly, double rl, double& n1, double& n2, double& len) {
-    const double l2 = lx * lx + ly * ly;
+    const double l2 = edge_l2(lx, ly);
     len = l2 * rl;
     n1 = lx * rl;
     n2 = ly * rl;
@@ -80,7 +101,7 @@ __global__ void __launch_bounds__(128) adj_phase1_kernel(const AdjArgs a) {
     const V4<double> own = a.U[i];
     const V4<double> gA = a.geoA[i], gB = a.geoB[i], gR = a.geoR[i];
     const int4 tp = a.topo[i];
-    const int code[3] = {tp.x, tp.y, tp.z};
+    const int code[3] = {adj_code(a, tp.x), adj_code(a, tp.y), adj_code(a, tp.z)};
     const double hi = own.x, zi = own.w;
     double ui, vi;
     cell_velocity<double>(hi, own.y, own.z, h_dry, ui, vi);
@@ -104,7 +125,11 @@ __global__ void __launch_bounds__(128) adj_phase1_kernel(const AdjArgs a) {
                     F0 = 0.0; F1 = 0.0; F2 = 0.0;
                     src = 0.5 * g * (hsi * hsi - hi * hi);
                 } else {
-                    const int e = j == 0 ? ei.x : (j == 1 ? ei.y : ei.z);
+                    int e = j == 0 ? ei.x : (j == 1 ? ei.y : ei.z);
+                    if (a.debug && !(e >= 0 && e < a.n_edges)) {
+                        atomicOr(a.status, kStatusBadIndex);
+                        e = 0;
+                    }
                     const V4<double> fl = a.eflux[e];
                     if (c & kFlipBit) {
                         F0 = -fl.x; F1 = -fl.y; F2 = -fl.z;
@@ -166,7 +191,7 @@ __global__ void __launch_bounds__(128) adj_phase2_kernel(const AdjArgs a) {
     const V4<double> own = a.U[jc];
     const V4<double> gA = a.geoA[jc], gB = a.geoB[jc], gR = a.geoR[jc];
     const int4 tp = a.topo[jc];
-    const int code[3] = {tp.x, tp.y, tp.z};
+    const int code[3] = {adj_code(a, tp.x), adj_code(a, tp.y), adj_code(a, tp.z)};
     const V4<double> nuj = a.nu[jc];
     const D4 H = D4::seed(own.x, 0), QX = D4::seed(own.y, 1), QY = D4::seed(own.z, 2), Z = D4::seed(own.w, 3);
     D4 U, V;
@@ -204,6 +229,290 @@ __global__ void __launch_bounds__(128) adj_phase2_kernel(const AdjArgs a) {
             }
         } else {
             const int grp = -1 - c;
+            edge_boundary<D4>(a.bc.kind[grp], a.bc.value[grp], H, U, V, Z, D4(n1), D4(n2), D4(g), D4(h_dry), F0, F1,
+                              F2, a.hll != 0);
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                acc[k] += -len * (nuj.x * F0.d[k] + nuj.y * F1.d[k] + nuj.z * F2.d[k]);
+        }
+    }
+    const V4<double> aw = a.aw[jc];
+    V4<double> out;
+    out.x = aw.x + acc[0];
+    out.y = aw.y + acc[1];
+    out.z = aw.z + acc[2];
+    out.w = 0.0;
+    a.lam[jc] = out;
+    a.gz[jc] += acc[3];
+}
+
+// ---- hand-written transposes of the edge flux (the default reverse step) ----------
+// The reverse of one interior edge's contribution to both of its cells:
+// with E_L = (-len F0, -len F1 + src_L lx, -len F2 + src_L ly) the edge's term
+// in the left cell's (-f0, sx - f1, sy - f2) and E_R the right cell's
+// (its flux is -F, its L n is -(lx, ly)), the step's adjoint needs
+// d(nu_L . E_L + nu_R . E_R) / d(h, hu, hv, z) of both cells.  One forward
+// evaluation of the edge and one reverse sweep through it give both, where
+// the dual-number kernels evaluate the edge from each side on four-component
+// duals.  The forward is recomputed here with the literal formulas of
+// Eq 12-30 (the ones the dual-number kernels differentiate) and every branch
+// is taken as the forward takes it; the derivative of a max at a tie is that
+// of the operand the forward returns.
+
+// Reverse of riemann_hllc (Eq 17-26) at (hL, unL, utL, hR, unR, utR): adds
+// the adjoints of the six inputs for the flux adjoints (bG1, bG2, bG3).
+__device__ void riemann_rev(double hL, double unL, double utL, double hR, double unR, double utR, double g,
+                            double h_dry, bool hll_only, double bG1, double bG2, double bG3, double& bhL,
+                            double& bunL, double& butL, double& bhR, double& bunR, double& butR) {
+    const bool wetL = gt_pos(hL, h_dry), wetR = gt_pos(hR, h_dry);
+    if (!wetL && !wetR) return;   // no flux on either side
+    // ---- forward values
+    const double aL = sqrt(g * hL), aR = sqrt(g * hR);
+    double SL, SR, Ss, h0 = 0.0, hs = 0.0, pL = 1.0, pR = 1.0, gL = 0.0, gR = 0.0, b = 0.0;
+    const double hsum = hL + hR, asum = aL + aR, du = unR - unL;
+    bool rare = false, shL = false, shR = false, base_pos = false;
+    if (!wetL) {
+        SL = unR - 2.0 * aR; SR = unR + aR; Ss = SL;
+    } else if (!wetR) {
+        SL = unL - aL; SR = unL + 2.0 * aL; Ss = SR;
+    } else {
+        h0 = 0.5 * hsum - 0.25 * du * hsum / asum;                              // Eq 21
+        rare = le_pos(h0, min_nonneg(hL, hR));
+        if (rare) {                                                            // Eq 22
+            const double base = 0.5 * asum + 0.25 * (unL - unR);
+            base_pos = !lt_zero(base);
+            b = base_pos ? base : 0.0;
+            hs = b * b / g;
+        } else {                                                               // Eq 23
+            gL = sqrt(g * (h0 + hL) / (2.0 * h0 * hL));
+            gR = sqrt(g * (h0 + hR) / (2.0 * h0 * hR));
+            hs = (hL * gL + hR * gR + unL - unR) / (gL + gR);
+        }
+        shL = gt_pos(hs, hL);                                                  // Eq 20
+        shR = gt_pos(hs, hR);
+        if (shL) pL = sqrt(0.5 * hs * (hs + hL)) / hL;
+        if (shR) pR = sqrt(0.5 * hs * (hs + hR)) / hR;
+        SL = unL - aL * pL;                                                    // Eq 19
+        SR = unR + aR * pR;
+        const double mL = hL * (unL - SL), mR = hR * (unR - SR);
+        Ss = (SL * mR - SR * mL) / (mR - mL);                                  // Eq 25
+    }
+    const double qL = hL * unL, qR = hR * unR;
+    const double PL = qL * unL + 0.5 * g * hL * hL, PR = qR * unR + 0.5 * g * hR * hR;
+    const bool supL = ge_zero(SL), supR = !supL && le_zero(SR);              // Eq 17
+    const double D = SR - SL;
+    double G1;
+    if (supL) G1 = qL;
+    else if (supR) G1 = qR;
+    else G1 = (SR * qL - SL * qR + SR * SL * (hR - hL)) / D;
+    // ---- reverse
+    double bSL = 0.0, bSR = 0.0, bqL = 0.0, bqR = 0.0, bPL = 0.0, bPR = 0.0;
+    if (!hll_only) {                                                           // Eq 24
+        const bool up = ge_zero(Ss);
+        bG1 += bG3 * (up ? utL : utR);
+        if (up) butL += bG3 * G1;
+        else butR += bG3 * G1;
+    } else if (supL) {
+        bqL += bG3 * utL; butL += bG3 * qL;
+    } else if (supR) {
+        bqR += bG3 * utR; butR += bG3 * qR;
+    } else {
+        const double N3 = SR * qL * utL - SL * qR * utR + SR * SL * (hR * utR - hL * utL);
+        const double bN3 = bG3 / D;
+        const double dh = hR * utR - hL * utL;
+        bSR += bN3 * (qL * utL + SL * dh) - bG3 * N3 / (D * D);
+        bSL += bN3 * (-qR * utR + SR * dh) + bG3 * N3 / (D * D);
+        bqL += bN3 * SR * utL;
+        bqR -= bN3 * SL * utR;
+        butL += bN3 * (SR * qL - SR * SL * hL);
+        butR += bN3 * (-SL * qR + SR * SL * hR);
+        bhR += bN3 * SR * SL * utR;
+        bhL -= bN3 * SR * SL * utL;
+    }
+    if (supL) {                                                                // Eq 17-18
+        bqL += bG1; bPL += bG2;
+    } else if (supR) {
+        bqR += bG1; bPR += bG2;
+    } else {
+        const double G2 = (SR * PL - SL * PR + SR * SL * (qR - qL)) / D;
+        const double bN1 = bG1 / D, bN2 = bG2 / D, bD = -(bG1 * G1 + bG2 * G2) / D;
+        bSR += bN1 * (qL + SL * (hR - hL)) + bN2 * (PL + SL * (qR - qL)) + bD;
+        bSL += bN1 * (-qR + SR * (hR - hL)) + bN2 * (-PR + SR * (qR - qL)) - bD;
+        bqL += bN1 * SR - bN2 * SR * SL;
+        bqR += -bN1 * SL + bN2 * SR * SL;
+        bPL += bN2 * SR;
+        bPR -= bN2 * SL;
+        bhR += bN1 * SR * SL;
+        bhL -= bN1 * SR * SL;
+    }
+    // P_K = q_K un_K + g h_K^2 / 2, q_K = h_K un_K
+    bqL += bPL * unL; bunL += bPL * qL; bhL += bPL * g * hL;
+    bqR += bPR * unR; bunR += bPR * qR; bhR += bPR * g * hR;
+    bhL += bqL * unL; bunL += bqL * hL;
+    bhR += bqR * unR; bunR += bqR * hR;
+    double baL = 0.0, baR = 0.0;
+    if (!wetL) {                                                               // Eq 26
+        bunR += bSL + bSR; baR += -2.0 * bSL + bSR;
+    } else if (!wetR) {
+        bunL += bSL + bSR; baL += -bSL + 2.0 * bSR;
+    } else {
+        bunL += bSL; baL -= bSL * pL;
+        bunR += bSR; baR += bSR * pR;
+        const double bpL = -bSL * aL, bpR = bSR * aR;
+        double bhs = 0.0;
+        if (shL) {   // p_L = r / h_L, r = sqrt(h* (h* + h_L) / 2)
+            const double r = pL * hL;
+            bhs += bpL * (hs + 0.5 * hL) / (2.0 * r * hL);
+            bhL += bpL * (hs / (4.0 * r * hL) - pL / hL);
+        }
+        if (shR) {
+            const double r = pR * hR;
+            bhs += bpR * (hs + 0.5 * hR) / (2.0 * r * hR);
+            bhR += bpR * (hs / (4.0 * r * hR) - pR / hR);
+        }
+        if (rare) {
+            if (base_pos) {
+                const double bb = bhs * 2.0 * b / g;
+                baL += 0.5 * bb; baR += 0.5 * bb;
+                bunL += 0.25 * bb; bunR -= 0.25 * bb;
+            }
+        } else {
+            // h* = N / (g_L + g_R), N = h_L g_L + h_R g_R + un_L - un_R
+            const double Dg = gL + gR;
+            const double bN = bhs / Dg, bDg = -bhs * hs / Dg;
+            bhL += bN * gL; bhR += bN * gR;
+            bunL += bN; bunR -= bN;
+            const double bgL = bN * hL + bDg, bgR = bN * hR + bDg;
+            // g_K = sqrt(X_K), X_K = g (h0 + h_K) / (2 h0 h_K) = (g/2)(1/h_K + 1/h0)
+            const double bXL = bgL / (2.0 * gL), bXR = bgR / (2.0 * gR);
+            const double bh0 = -(bXL + bXR) * 0.5 * g / (h0 * h0);
+            bhL -= bXL * 0.5 * g / (hL * hL);
+            bhR -= bXR * 0.5 * g / (hR * hR);
+            // h0 = hsum/2 - du hsum / (4 asum)
+            const double bhsum = bh0 * (0.5 - 0.25 * du / asum);
+            const double bdu = -bh0 * 0.25 * hsum / asum;
+            const double basum = bh0 * 0.25 * du * hsum / (asum * asum);
+            bhL += bhsum; bhR += bhsum;
+            bunR += bdu; bunL -= bdu;
+            baL += basum; baR += basum;
+        }
+    }
+    if (aL > 0.0) bhL += baL * g / (2.0 * aL);                                 // a_K = sqrt(g h_K)
+    if (aR > 0.0) bhR += baR * g / (2.0 * aR);
+}
+
+// Reverse of one interior edge in canonical orientation (left cell L, its
+// outward unit normal (n1, n2)): for the adjoints (wF0, wF1, wF2) of the flux
+// leaving L and (sL, sR) of the two cells' bed source factors, adds the
+// adjoints of (h, hu, hv, z) of L to dL and of R to dR.
+__device__ void edge_interior_rev(const V4<double>& L, const V4<double>& R, double n1, double n2, double g,
+                                  double h_dry, bool hll_only, double wF0, double wF1, double wF2, double sL,
+                                  double sR, V4<double>& dL, V4<double>& dR) {
+    // forward: velocities (R9), hydrostatic reconstruction (Eq 28), rotation (Eq 12)
+    const bool wL = gt_pos(L.x, h_dry), wR = gt_pos(R.x, h_dry);
+    const double rL = wL ? 1.0 / L.x : 0.0, rR = wR ? 1.0 / R.x : 0.0;
+    const double uL = L.y * rL, vL = L.z * rL, uR = R.y * rR, vR = R.z * rR;
+    const bool zleft = L.w > R.w;   // z* = max(z_L, z_R); a tie takes z_R, as the forward
+    const double zs = zleft ? L.w : R.w;
+    const double xL = L.x + L.w - zs, xR = R.x + R.w - zs;
+    const bool pL = !lt_zero(xL), pR = !lt_zero(xR);
+    const double hL = pL ? xL : 0.0, hR = pR ? xR : 0.0;
+    const double unL = uL * n1 + vL * n2, utL = vL * n1 - uL * n2;
+    const double unR = uR * n1 + vR * n2, utR = vR * n1 - uR * n2;
+    // reverse: back from (x, y) (Eq 12 inverse)
+    const double bG1 = wF0, bG2 = wF1 * n1 + wF2 * n2, bG3 = -wF1 * n2 + wF2 * n1;
+    double bhL = 0.0, bunL = 0.0, butL = 0.0, bhR = 0.0, bunR = 0.0, butR = 0.0;
+    riemann_rev(hL, unL, utL, hR, unR, utR, g, h_dry, hll_only, bG1, bG2, bG3, bhL, bunL, butL, bhR, bunR, butR);
+    // bed source factors (Eq 30 with 1/2): src_K = (g/2)(h**_K^2 - h_K^2)
+    bhL += sL * g * hL;
+    bhR += sR * g * hR;
+    double bh0L = -sL * g * L.x, bh0R = -sR * g * R.x;
+    // rotation
+    const double buL = bunL * n1 - butL * n2, bvL = bunL * n2 + butL * n1;
+    const double buR = bunR * n1 - butR * n2, bvR = bunR * n2 + butR * n1;
+    double bqxL = 0.0, bqyL = 0.0, bqxR = 0.0, bqyR = 0.0;
+    if (wL) { bqxL = buL * rL; bqyL = bvL * rL; bh0L -= (buL * uL + bvL * vL) * rL; }
+    if (wR) { bqxR = buR * rR; bqyR = bvR * rR; bh0R -= (buR * uR + bvR * vR) * rR; }
+    // reconstruction
+    double bzL = 0.0, bzR = 0.0, bzs = 0.0;
+    if (pL) { bh0L += bhL; bzL += bhL; bzs -= bhL; }
+    if (pR) { bh0R += bhR; bzR += bhR; bzs -= bhR; }
+    if (zleft) bzL += bzs;
+    else bzR += bzs;
+    dL.x += bh0L; dL.y += bqxL; dL.z += bqyL; dL.w += bzL;
+    dR.x += bh0R; dR.y += bqxR; dR.z += bqyR; dR.w += bzR;
+}
+
+// Phase 2, edges: each interior edge once, the adjoints of both cells' states
+// through it, into ed[2 e] (left cell) and ed[2 e + 1] (right cell).
+__global__ void __launch_bounds__(128) adj_edge_kernel(const AdjArgs a) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < a.n_edges; e += stride) {
+        int2 lr = a.ecells[e];
+        V4<double> dl, dr;
+        dl.x = dl.y = dl.z = dl.w = 0.0;
+        dr.x = dr.y = dr.z = dr.w = 0.0;
+        if (a.debug && !(lr.x >= 0 && lr.x < a.n && lr.y >= 0 && lr.y < a.n)) {
+            atomicOr(a.status, kStatusBadIndex);
+            a.ed[2 * e] = dl;
+            a.ed[2 * e + 1] = dr;
+            continue;
+        }
+        const V4<double> L = a.U[lr.x], R = a.U[lr.y];
+        const double lx = a.eln[2 * e], ly = a.eln[2 * e + 1];
+        double n1, n2, len;
+        unit_normal(lx, ly, a.erl[e], n1, n2, len);
+        const V4<double> nl = a.nu[lr.x], nr = a.nu[lr.y];
+        const double sL = nl.y * lx + nl.z * ly, sR = -(nr.y * lx + nr.z * ly);
+        edge_interior_rev(L, R, n1, n2, a.g, a.h_dry, a.hll != 0, len * (nr.x - nl.x), len * (nr.y - nl.y),
+                          len * (nr.z - nl.z), sL, sR, dl, dr);
+        a.ed[2 * e] = dl;
+        a.ed[2 * e + 1] = dr;
+    }
+}
+
+// Phase 2, cells: lambda^n_j = own term + the contributions of j's interior
+// edges (in local edge order) + its boundary edges' (on duals, own state
+// only); dL/dz_j likewise.
+__global__ void __launch_bounds__(128) adj_cell_kernel(const AdjArgs a) {
+    const long long jc = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (jc >= a.n) return;
+    const int4 tp = a.topo[jc];
+    const int code[3] = {adj_code(a, tp.x), adj_code(a, tp.y), adj_code(a, tp.z)};
+    const int4 ei = a.eidx[jc];
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    bool any_boundary = false;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const int c = code[j];
+        if (c >= 0) {
+            int e = j == 0 ? ei.x : (j == 1 ? ei.y : ei.z);
+            if (a.debug && !(e >= 0 && e < a.n_edges)) {
+                atomicOr(a.status, kStatusBadIndex);
+                continue;
+            }
+            const V4<double> d = a.ed[2 * (long long)e + ((c & kFlipBit) ? 1 : 0)];
+            acc[0] += d.x; acc[1] += d.y; acc[2] += d.z; acc[3] += d.w;
+        } else {
+            any_boundary = true;
+        }
+    }
+    if (any_boundary) {
+        const double g = a.g, h_dry = a.h_dry;
+        const V4<double> own = a.U[jc];
+        const V4<double> gA = a.geoA[jc], gB = a.geoB[jc], gR = a.geoR[jc];
+        const V4<double> nuj = a.nu[jc];
+        const D4 H = D4::seed(own.x, 0), QX = D4::seed(own.y, 1), QY = D4::seed(own.z, 2), Z = D4::seed(own.w, 3);
+        D4 U, V;
+        cell_velocity<D4>(H, QX, QY, D4(h_dry), U, V);
+        for (int j = 0; j < 3; ++j) {
+            const int c = code[j];
+            if (c >= 0) continue;
+            double lx, ly, n1, n2, len;
+            edge_ln(gA, gB, j, lx, ly);
+            unit_normal(lx, ly, j == 0 ? gR.x : (j == 1 ? gR.y : gR.z), n1, n2, len);
+            const int grp = -1 - c;
+            D4 F0, F1, F2;
             edge_boundary<D4>(a.bc.kind[grp], a.bc.value[grp], H, U, V, Z, D4(n1), D4(n2), D4(g), D4(h_dry), F0, F1,
                               F2, a.hll != 0);
 #pragma unroll
@@ -320,7 +629,12 @@ int adjoint_impl(swe_mesh* m, int64_t nsteps, double cfl, const int32_t* gauge_c
     if (rc) return rc;
     cudaStream_t st = m->stream;
     const size_t sb = (size_t)n * sizeof(V4<double>);
-    DevBuf ckpt, seg, dtlog, small, lam, aw, nu, gmv, gzv, dg_idx, dtarget, dloss;
+    DevBuf ckpt, seg, dtlog, small, lam, aw, nu, gmv, gzv, dg_idx, dtarget, dloss, ed;
+    const bool transposes = m->adjoint_method == SWE_ADJOINT_TRANSPOSE;
+    if (transposes) {   // the interior edge list of the edge-by-edge reverse step
+        rc = build_edges(m);
+        if (rc) return rc;
+    }
     cudaError_t e = cudaSuccess;
     auto alloc = [&](DevBuf& b, size_t bytes) {
         if (e == cudaSuccess) e = cudaMalloc(&b.p, bytes ? bytes : 16);
@@ -337,6 +651,7 @@ int adjoint_impl(swe_mesh* m, int64_t nsteps, double cfl, const int32_t* gauge_c
     alloc(dg_idx, n_gauges * sizeof(long long));
     alloc(dtarget, (size_t)n_obs * n_gauges * sizeof(double));
     alloc(dloss, sizeof(double));
+    if (transposes) alloc(ed, (size_t)std::max<int64_t>(m->n_edges, 1) * 2 * sizeof(V4<double>));
     if (e != cudaSuccess) {
         set_error(std::string("swe_adjoint: device allocation failed: ") + cudaGetErrorString(e));
         return SWE_ENOMEM;
@@ -370,6 +685,10 @@ int adjoint_impl(swe_mesh* m, int64_t nsteps, double cfl, const int32_t* gauge_c
     if (e == cudaSuccess) e = cudaMemcpyAsync(fstat.data(), m->small, kSmallWords * 8, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return afail(e, "swe_adjoint: forward");
+    if (fstat[kSlotStatus] & kStatusBadIndex) {
+        set_error("swe_adjoint: an index or boundary group out of range in the forward run (debug checks)");
+        return SWE_EMESH;
+    }
     if (fstat[kSlotStatus] & kStatusNonFinite) { set_error("swe_adjoint: forward run is not finite"); return SWE_ENONFINITE; }
     for (double d : dts)
         if (!std::isfinite(d)) { set_error("swe_adjoint: forward run went dry"); return SWE_EDRY; }
@@ -401,11 +720,19 @@ int adjoint_impl(swe_mesh* m, int64_t nsteps, double cfl, const int32_t* gauge_c
     a.h_dry = m->cfg.h_dry;
     a.hll = m->cfg.flux == SWE_FLUX_HLL ? 1 : 0;
     a.bc = m->bc;
+    a.n_edges = m->n_edges;
+    a.debug = m->cfg.debug_checks;
+    a.n_groups = m->n_groups;
+    a.status = (unsigned*)((unsigned long long*)small.p + kSlotStatus);
     // with the edge pass, phase 1 takes R's interior fluxes from one evaluation per edge
     const bool edges = m->plain.edges && m->eflux;
     a.eflux = edges ? (const V4<double>*)m->eflux : nullptr;
     a.esrc = edges ? (const double*)m->esrc : nullptr;
-    a.eidx = edges ? m->eidx : nullptr;
+    a.eidx = m->eidx;
+    a.ecells = m->ecells;
+    a.eln = (const double*)m->eln;
+    a.erl = (const double*)m->erl;
+    a.ed = (V4<double>*)ed.p;
     StepArgs<double> ea{};
     if (edges) {
         ea.ecells = m->ecells;
@@ -417,7 +744,12 @@ int adjoint_impl(swe_mesh* m, int64_t nsteps, double cfl, const int32_t* gauge_c
         ea.g = m->cfg.g;
         ea.h_dry = m->cfg.h_dry;
         ea.hll = a.hll;
+        ea.n = n;
+        ea.debug = a.debug;
+        ea.n_groups = a.n_groups;
+        ea.status = a.status;
     }
+    const unsigned egrid = (unsigned)std::min<int64_t>((std::max<int64_t>(m->n_edges, 1) + 127) / 128, 65535);
     const unsigned grid = (unsigned)((n + 127) / 128);
     // reverse sweep, segment by segment
     for (int64_t sgi = nseg - 1; sgi >= 0 && e == cudaSuccess; --sgi) {
@@ -438,7 +770,12 @@ int adjoint_impl(swe_mesh* m, int64_t nsteps, double cfl, const int32_t* gauge_c
             } else {
                 adj_phase1_kernel<false><<<grid, 128, 0, st>>>(a);
             }
-            adj_phase2_kernel<<<grid, 128, 0, st>>>(a);
+            if (transposes) {
+                adj_edge_kernel<<<egrid, 128, 0, st>>>(a);
+                adj_cell_kernel<<<grid, 128, 0, st>>>(a);
+            } else {
+                adj_phase2_kernel<<<grid, 128, 0, st>>>(a);
+            }
             const int64_t nn = n0 + k;  // lambda now holds lambda^nn
             if (nn > 0 && nn % obs_every == 0)
                 adj_inject_kernel<<<1, 32, 0, st>>>(a.U, gi, tg + (nn / obs_every - 1) * n_gauges, n_gauges, a.lam);
@@ -446,6 +783,16 @@ int adjoint_impl(swe_mesh* m, int64_t nsteps, double cfl, const int32_t* gauge_c
         }
     }
     if (e != cudaSuccess) return afail(e, "swe_adjoint: reverse sweep");
+    if (m->cfg.debug_checks) {
+        unsigned long long rs[kSmallWords];
+        e = cudaMemcpyAsync(rs, small.p, sizeof rs, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return afail(e, "swe_adjoint: reverse sweep status");
+        if (rs[kSlotStatus] & kStatusBadIndex) {
+            set_error("swe_adjoint: an index or boundary group out of range in the reverse sweep (debug checks)");
+            return SWE_EMESH;
+        }
+    }
     // outputs
     if (where == SWE_DEVICE) {
         adj_output_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((const double*)gmv.p, (const double*)gzv.p,
@@ -519,7 +866,21 @@ int swe_step_dt(swe_mesh* m, int64_t nsteps, const double* dts, double* t_out) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return afail(e, "swe_step_dt");
     if (t_out) std::memcpy(t_out, &sm[kSlotT], sizeof(double));
+    if (sm[kSlotStatus] & kStatusBadIndex) {
+        set_error("swe_step_dt: an index or boundary group out of range (debug checks)");
+        return SWE_EMESH;
+    }
     if (sm[kSlotStatus] & kStatusNonFinite) { set_error("swe_step_dt: non-finite state"); return SWE_ENONFINITE; }
+    return SWE_OK;
+}
+
+int swe_adjoint_method(swe_mesh* m, int method) {
+    if (!m) { set_error("swe_adjoint_method: NULL mesh"); return SWE_EINVAL; }
+    if (method != SWE_ADJOINT_TRANSPOSE && method != SWE_ADJOINT_DUAL) {
+        set_error("swe_adjoint_method: unknown method");
+        return SWE_EINVAL;
+    }
+    m->adjoint_method = method;
     return SWE_OK;
 }
 

@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -217,6 +218,9 @@ StepArgs<T> make_args(swe_mesh* m, int64_t step_index, double cfl) {
     a.g = (T)m->cfg.g;
     a.h_dry = (T)m->cfg.h_dry;
     a.bc = m->bc;
+    a.debug = m->cfg.debug_checks;
+    a.n_groups = m->n_groups;
+    a.pairs = m->cfg.cell_pairs;
     return a;
 }
 
@@ -295,6 +299,10 @@ int read_small(swe_mesh* m, unsigned long long out[kSmallWords]) {
 }
 
 int status_code(unsigned long long st) {
+    if (st & kStatusBadIndex) {
+        set_error("swe_step: a neighbour index, edge index or boundary group out of range (debug checks)");
+        return SWE_EMESH;
+    }
     if (st & kStatusNonFinite) { set_error("swe_step: non-finite state"); return SWE_ENONFINITE; }
     if (st & kStatusDry) { set_error("swe_step: every cell is dry, no CFL time step"); return SWE_EDRY; }
     return SWE_OK;
@@ -399,6 +407,7 @@ cudaError_t launch_raw_t(swe_mesh* m, const void* in, void* out, unsigned long l
     a.esrc = edges ? (T*)m->esrc : nullptr;
     a.eidx = edges ? m->eidx : nullptr;
     a.n_edges = edges ? m->n_edges : 0;
+    a.pairs = m->plain.pairs;
     a.grid = m->plain.grid;
     return Launch<T>::step(a, m->plain.block, m->plain.min_blocks, m->plain.stages, m->plain.geo, st);
 }
@@ -536,10 +545,16 @@ void swe_config_default(swe_config* cfg) {
     cfg->activity = 0;
     cfg->edge_pass = 0;
     cfg->grid = 0;
+    cfg->debug_checks = 0;
+    cfg->cell_pairs = 0;
     cfg->flux = SWE_FLUX_HLLC;
 }
 
 const char* swe_last_error(void) { return g_last_error.c_str(); }
+
+int swe_debug_code_ok(int32_t code, int64_t n_cells, int n_groups) {
+    return code_ok(code, (long long)n_cells, n_groups) ? 1 : 0;
+}
 
 void swe_mesh_destroy(swe_mesh* m) {
     if (!m) return;
@@ -567,6 +582,12 @@ int swe_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* tris, i
         set_error("swe_mesh_create: g and h_dry must be finite and > 0");
         return SWE_EINVAL;
     }
+    if (c.h_dry < (double)FLT_MIN) {
+        // a wet depth must stay a normal float: FP32 kernels hold it as one, and the
+        // FP64 friction term starts its h^(-1/3) iteration from the float reciprocal cube root
+        set_error("swe_mesh_create: h_dry must be at least FLT_MIN (1.18e-38)");
+        return SWE_EINVAL;
+    }
     if (c.flux != SWE_FLUX_HLLC && c.flux != SWE_FLUX_HLL) { set_error("swe_mesh_create: unknown flux"); return SWE_EINVAL; }
     if (c.geometry_early != 0 && c.geometry_early != 1) {
         set_error("swe_mesh_create: geometry_early must be 0 or 1");
@@ -582,6 +603,18 @@ int swe_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* tris, i
     }
     if (c.grid < 0) {
         set_error("swe_mesh_create: grid must be >= 0");
+        return SWE_EINVAL;
+    }
+    if (c.debug_checks != 0 && c.debug_checks != 1) {
+        set_error("swe_mesh_create: debug_checks must be 0 or 1");
+        return SWE_EINVAL;
+    }
+    if (c.cell_pairs != 0 && c.cell_pairs != 1) {
+        set_error("swe_mesh_create: cell_pairs must be 0 or 1");
+        return SWE_EINVAL;
+    }
+    if (c.cell_pairs && (c.precision != SWE_FP32 || c.activity || c.edge_pass)) {
+        set_error("swe_mesh_create: cell_pairs needs an FP32 mesh without activity or edge_pass");
         return SWE_EINVAL;
     }
     if (c.edge_pass && c.activity) {
@@ -643,13 +676,13 @@ int swe_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* tris, i
         int per_sm = 0, sms = 0;
         e = c.precision == SWE_FP32
                 ? Launch<float>::resident_blocks(c.block_size, c.min_blocks, c.stages, c.geometry_early, c.activity,
-                                                 c.edge_pass, &per_sm)
+                                                 c.cell_pairs ? 2 : c.edge_pass, &per_sm)
                 : Launch<double>::resident_blocks(c.block_size, c.min_blocks, c.stages, c.geometry_early, c.activity,
                                                   c.edge_pass, &per_sm);
         if (e == cudaErrorInvalidValue) {
             swe_mesh_destroy(m);
             set_error("swe_mesh_create: no compiled step kernel for this block_size / min_blocks / stages / "
-                      "geometry_early / activity / edge_pass");
+                      "geometry_early / activity / edge_pass / cell_pairs");
             return SWE_EINVAL;
         }
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device);
@@ -659,7 +692,8 @@ int swe_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* tris, i
         m->grid = (unsigned)std::min(need, c.grid > 0 ? (long long)c.grid : wave);
         // launches without activity bytes: the same shape, or the default one
         // when the configured shape exists only as an activity kernel
-        m->plain = LaunchShape{c.block_size, c.min_blocks, c.stages, c.geometry_early, c.edge_pass, m->grid};
+        m->plain = LaunchShape{c.block_size, c.min_blocks, c.stages, c.geometry_early, c.edge_pass, c.cell_pairs,
+                               m->grid};
         if (c.activity) {
             LaunchShape d;
             d.block = c.precision == SWE_FP32 ? 256 : 128;
@@ -801,7 +835,8 @@ int swe_get_info(swe_mesh* m, swe_info* info) {
     info->dt_next = bits_to_double(s[m->nstep % 3]);
     info->n_clamped = (int64_t)s[kSlotClamp];
     info->n_active = (int64_t)s[kSlotActive];
-    info->status = s[kSlotStatus] & kStatusNonFinite ? SWE_ENONFINITE
+    info->status = s[kSlotStatus] & kStatusBadIndex    ? SWE_EMESH
+                   : s[kSlotStatus] & kStatusNonFinite ? SWE_ENONFINITE
                    : (s[kSlotStatus] & kStatusDry ? SWE_EDRY : SWE_OK);
     return SWE_OK;
 }

@@ -96,7 +96,7 @@ __global__ void diag_boundary_kernel(const V4<T>* __restrict__ cur, const V4<T>*
     const V4<T> gA = geoA[i], gB = geoB[i];
     const T lx = j == 0 ? gA.x : (j == 1 ? gA.z : gB.x);
     const T ly = j == 0 ? gA.y : (j == 1 ? gA.w : gB.y);
-    const T l2 = lx * lx + ly * ly;
+    const T l2 = edge_l2(lx, ly);
     T pre = T(0);
     if constexpr (sizeof(T) == 8) {
         const V4<T> gR = geoR[i];

@@ -34,6 +34,8 @@ struct swe_ensemble {
     cudaStream_t cap_stream = nullptr;
     std::vector<int64_t> base, n_cells, first_tile;
     int64_t n_total = 0, n_tiles = 0;    // n_tiles counts kEnsPad-cell spans
+    int n_groups = 1;                    // global boundary groups
+    int debug = 0;                       // debug checks (any member created with them)
     void* state[2] = {nullptr, nullptr};
     void* geoA = nullptr;
     void* geoB = nullptr;
@@ -187,6 +189,8 @@ EnsArgs<T> ens_args(swe_ensemble* E, int64_t step_index) {
     a.hll = E->hll;
     a.g = (T)9.81;
     a.h_dry = (T)1e-6;
+    a.debug = E->debug;
+    a.n_groups = E->n_groups;
     return a;
 }
 
@@ -272,6 +276,8 @@ int ens_build(swe_ensemble* E, swe_mesh* const* M) {
     e = cudaMemcpy(E->kind, kinds.data(), kinds.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(E->value, values.data(), values.size() * sizeof(double), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return efail(e, "swe_ensemble_create: boundary groups");
+    E->n_groups = (int)kinds.size();
+    for (int k = 0; k < nm; ++k) E->debug = E->debug || M[k]->cfg.debug_checks;
     // per-member device copies and host-built topology / tile tables
     std::vector<int4> topo(off);
     std::vector<long long> perm(off, 0);
@@ -699,6 +705,7 @@ int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
         out->stages = pick.stages;
         out->geometry_early = pick.geo_early;
         out->activity = pick.activity;
+        out->cell_pairs = 0;
         out->edge_pass = pick.edges;
         out->dynamic = pick.dynamic;
         out->chunk = 1 << pick.chunk_log2;
@@ -830,7 +837,11 @@ int swe_ensemble_step(swe_ensemble* E, int64_t nsteps, const double* cfl, double
         int rc = SWE_OK;
         for (int k = 0; k < E->n_members; ++k) {
             std::memcpy(&t_out[k], &s[8 * k + kSlotT], sizeof(double));
-            if ((s[8 * k + kSlotStatus] & kStatusNonFinite) && !rc) {
+            if ((s[8 * k + kSlotStatus] & kStatusBadIndex) && !rc) {
+                set_error("swe_ensemble_step: member " + std::to_string(k) +
+                          ": an index or boundary group out of range (debug checks)");
+                rc = SWE_EMESH;
+            } else if ((s[8 * k + kSlotStatus] & kStatusNonFinite) && !rc) {
                 set_error("swe_ensemble_step: member " + std::to_string(k) + " has a non-finite state");
                 rc = SWE_ENONFINITE;
             } else if ((s[8 * k + kSlotStatus] & kStatusDry) && !rc) {
@@ -936,7 +947,9 @@ int swe_ensemble_get_info(swe_ensemble* E, int member, swe_info* info) {
     std::memcpy(&info->t, &s[kSlotT], sizeof(double));
     std::memcpy(&info->dt_next, &s[E->nstep % 3], sizeof(double));
     info->precision = E->precision;
-    info->status = (s[kSlotStatus] & kStatusNonFinite) ? SWE_ENONFINITE : ((s[kSlotStatus] & kStatusDry) ? SWE_EDRY : SWE_OK);
+    info->status = (s[kSlotStatus] & kStatusBadIndex)     ? SWE_EMESH
+                   : (s[kSlotStatus] & kStatusNonFinite) ? SWE_ENONFINITE
+                   : ((s[kSlotStatus] & kStatusDry) ? SWE_EDRY : SWE_OK);
     info->device_bytes = E->device_bytes;
     info->n_active = (int64_t)act;  // all members together
     return SWE_OK;

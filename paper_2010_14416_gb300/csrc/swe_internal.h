@@ -55,7 +55,7 @@ void set_error(const std::string& msg);
 
 // A launch shape of the step kernel.
 struct LaunchShape {
-    int block = 0, min_blocks = 0, stages = 0, geo = 0, edges = 0;
+    int block = 0, min_blocks = 0, stages = 0, geo = 0, edges = 0, pairs = 0;
     unsigned grid = 0;
 };
 
@@ -141,6 +141,8 @@ struct swe_mesh {
     void* eflux = nullptr;             // V4<T>[E]
     void* esrc = nullptr;              // T[E]
     int4* eidx = nullptr;              // per cell, the edge of each local edge (-1: boundary)
+    // reverse step of swe_adjoint: SWE_ADJOINT_TRANSPOSE or SWE_ADJOINT_DUAL
+    int adjoint_method = SWE_ADJOINT_TRANSPOSE;
 };
 
 

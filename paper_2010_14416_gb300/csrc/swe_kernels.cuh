@@ -20,6 +20,8 @@
 
 #include <type_traits>
 
+#include "swe_f32.cuh"
+
 namespace swe {
 
 constexpr int kMaxGroups = 64;
@@ -31,6 +33,15 @@ constexpr unsigned long long kInfBits = 0x7FF0000000000000ULL;  // +inf as doubl
 // status word bits
 constexpr unsigned kStatusNonFinite = 1u;
 constexpr unsigned kStatusDry = 2u;
+constexpr unsigned kStatusBadIndex = 4u;   // debug checks: an index or boundary group out of range
+
+// Debug checks: whether a neighbour code can be used on a mesh of n cells with
+// n_groups boundary groups -- an interior code (>= 0) whose cell index is below
+// n, or a boundary code (< 0) whose group -1 - code is below n_groups.
+__host__ __device__ __forceinline__ bool code_ok(int code, long long n, int n_groups) {
+    if (code >= 0) return (long long)(code & 0x3FFFFFFF) < n;
+    return -1 - (long long)code < (long long)n_groups;
+}
 
 constexpr int kBcWall = 0, kBcInflow = 1, kBcTransmissive = 2, kBcStage = 3;
 
@@ -86,8 +97,12 @@ struct StepArgs {
     long long n_edges;
     T g, h_dry;
     BcTable bc;
+    int debug;                         // 1: check indices and groups before use (kStatusBadIndex)
+    int n_groups;                      // boundary groups in use
+    int pairs;                         // FP32: two cells per thread (step_kernel_x2)
     __device__ __forceinline__ int bc_kind(int grp) const { return bc.kind[grp]; }
     __device__ __forceinline__ double bc_value(int grp) const { return bc.value[grp]; }
+    __device__ __forceinline__ long long cell_bound() const { return n; }
 };
 
 // Arguments of the batched ensemble step: the members' cells are concatenated,
@@ -131,8 +146,11 @@ struct EnsArgs {
     int slot_read, slot_write, slot_reset;
     int hll;
     T g, h_dry;
+    int debug;                         // 1: check indices and groups before use (kStatusBadIndex)
+    int n_groups;                      // global boundary groups in use
     __device__ __forceinline__ int bc_kind(int grp) const { return kind_[grp]; }
     __device__ __forceinline__ double bc_value(int grp) const { return value_[grp]; }
+    __device__ __forceinline__ long long cell_bound() const { return n_total; }
 };
 
 // ---- precision-specific arithmetic ------------------------------------------------
@@ -307,6 +325,12 @@ __device__ __forceinline__ T edge_rl(T pre, T l2) {
     else return Ar<T>::rsqrt_(l2);
 }
 
+// |L n|^2 of an edge, written as one fused multiply-add so that every kernel
+// (and both cells of an edge, whose L n differ only in sign) forms the same
+// value.
+template <typename T>
+__device__ __forceinline__ T edge_l2(T lx, T ly) { return fma(lx, lx, ly * ly); }
+
 // ---- Riemann flux in the edge-normal frame (Eq 14, 17-26) -------------------------
 // Input U_K = (h_K, h_K un_K, h_K ut_K) given as depth and normal/tangential
 // velocity.  Readings: Eq 20 p_K = sqrt(h*(h*+h_K)/2)/h_K; Eq 21-22 use the
@@ -318,6 +342,10 @@ __device__ __forceinline__ T edge_rl(T pre, T l2) {
 template <typename T>
 __device__ __forceinline__ void riemann_hllc(T hL, T unL, T utL, T hR, T unR, T utR, T g, T h_dry,
                                              T& G1, T& G2, T& G3, T* speeds = nullptr, bool hll_only = false) {
+    if constexpr (std::is_same<T, float>::value) {   // FP32: swe_f32.cuh, branch-free and explicitly rounded
+        f32::riemann<float>(hL, unL, utL, hR, unR, utR, g, f32::mul(0.5f, g), h_dry, G1, G2, G3, speeds, hll_only);
+        return;
+    }
     using A = Ar<T>;
     const bool wetL = gt_pos(hL, h_dry), wetR = gt_pos(hR, h_dry);
     if (!wetL && !wetR) {
@@ -503,6 +531,11 @@ template <typename T>
 __device__ __forceinline__ void edge_interior(T hi, T ui, T vi, T zi, T hk, T huk, T hvk, T zk, T n1, T n2,
                                               bool flip, T g, T h_dry, T& F0, T& F1, T& F2, T& src,
                                               bool hll_only = false, T* src_k = nullptr) {
+    if constexpr (std::is_same<T, float>::value) {   // FP32: swe_f32.cuh
+        f32::edge_interior<float>(hi, ui, vi, zi, hk, huk, hvk, zk, n1, n2, flip, g, f32::mul(0.5f, g), h_dry, F0, F1,
+                                  F2, src, hll_only, src_k);
+        return;
+    }
     T uk, vk;
     cell_velocity<T>(hk, huk, hvk, h_dry, uk, vk);
     // hydrostatic reconstruction (Eq 28): z* = max(z_i, z_k)
@@ -532,6 +565,10 @@ __device__ __forceinline__ void edge_interior(T hi, T ui, T vi, T zi, T hk, T hu
 template <typename T>
 __device__ __forceinline__ void edge_boundary(int kind, double value, T hi, T ui, T vi, T zi, T n1, T n2, T g,
                                               T h_dry, T& F0, T& F1, T& F2, bool hll_only = false) {
+    if constexpr (std::is_same<T, float>::value) {   // FP32: swe_f32.cuh
+        f32::edge_boundary(kind, value, hi, ui, vi, zi, n1, n2, g, f32::mul(0.5f, g), h_dry, F0, F1, F2, hll_only);
+        return;
+    }
     const T un = ui * n1 + vi * n2, ut = vi * n1 - ui * n2;
     T G1, G2, G3;
     if (kind == kBcWall) {
@@ -597,6 +634,291 @@ __device__ __forceinline__ void friction_update(T hi, T qx, T qy, T gm2, T Rh, T
     }
 }
 
+// ---- the end of one cell update -----------------------------------------------------
+// From the summed edge terms (f = sum of L_ij F_ij, s = sum of the bed source
+// factors times L_ij n_ij) to the new state (Eq 37 with friction, Eq 33-36),
+// its checks, and the cell's next CFL candidate R_i/(sqrt(g h)+|u|) (Eq 15;
+// +inf when the new state is dry).  Every cell kernel ends here, so their
+// arithmetic is the same.
+template <typename T, typename Args>
+__device__ __forceinline__ T finish_cell(const Args& a, long long i, const V4<T>& own, T f0, T f1, T f2, T sx, T sy,
+                                         T ia, T rin, T gm2, T dt, unsigned long long* n_clamped, unsigned* status) {
+    using A = Ar<T>;
+    const T g = a.g, h_dry = a.h_dry;
+    const T hi = own.x;
+    V4<T> out;
+    out.w = own.w;
+    const T Rh = -f0 * ia;
+    const T Rx = (sx - f1) * ia;
+    const T Ry = (sy - f2) * ia;
+    const T qx = own.y, qy = own.z;
+    T dh, dqx, dqy;
+    friction_update<T>(hi, qx, qy, gm2, Rh, Rx, Ry, dt, h_dry, dh, dqx, dqy);
+    out.x = hi + dh;
+    out.y = qx + dqx;
+    out.z = qy + dqy;
+    if (lt_zero(out.x)) {
+        out.x = T(0); out.y = T(0); out.z = T(0);
+        atomicAdd(n_clamped, 1ULL);
+    } else if (le_pos(out.x, h_dry)) {
+        out.y = T(0); out.z = T(0);
+    }
+    const T big = T(3.0e38);
+    if (!lt_pos(out.x, big) || !abs_lt_pos(out.y, big) || !abs_lt_pos(out.z, big))
+        atomicOr(status, kStatusNonFinite);
+    a.s_out[i] = out;
+    // next CFL candidate (Eq 15), R_i / (sqrt(g h) + |u|) on the new state
+    T cand = inf_of<T>();
+    if (gt_pos(out.x, h_dry)) {
+        if constexpr (kOneDivision<T>) {
+            // R h / (h sqrt(g h) + |q|): the velocity's division folded into the candidate's
+            const T qm = A::sqrt_(out.y * out.y + out.z * out.z);
+            cand = A::div_(rin * out.x, out.x * A::sqrt_(g * out.x) + qm);
+        } else {
+            const T r = A::rcp_(out.x);
+            const T u = out.y * r, v = out.z * r;
+            const T den = A::sqrt_(g * out.x) + A::sqrt_(u * u + v * v);
+            cand = A::div_(rin, den);
+        }
+    }
+    return cand;
+}
+
+// ---- one FP32 cell of the fused step -------------------------------------------------
+// update_cell for FP32: the same loads, quiet test and edge loop, with the
+// arithmetic of swe_f32.cuh on one lane (every operation explicitly rounded,
+// so that the two-cell kernel below, which runs the same functions on float2,
+// gives the same bits).
+template <bool GEO_EARLY, bool EDGES, typename Args>
+__device__ __forceinline__ float update_cell_f32(const Args& a, long long i, const V4<float>& own, const int4& tp,
+                                                 float dt, unsigned& active, unsigned long long* n_clamped,
+                                                 unsigned* status) {
+    const float g = a.g, h_dry = a.h_dry, g2 = f32::mul(0.5f, g);
+    const float hi = own.x, zi = own.w;
+    int code[3] = {tp.x, tp.y, tp.z};
+    if (a.debug) {   // an unusable code is flagged and taken as a wall (group 0)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            if (!code_ok(code[j], a.cell_bound(), a.n_groups)) {
+                atomicOr(status, kStatusBadIndex);
+                code[j] = -1;
+            }
+    }
+    V4<float> nb[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) nb[j] = code[j] >= 0 ? a.s_in[code[j] & kNbrMask] : own;
+    V4<float> gA, gB;
+    float gm2;
+    if constexpr (GEO_EARLY) {
+        gA = a.geoA[i];
+        gB = a.geoB[i];
+        gm2 = load_gm2(a, i, tp, 0.0f);
+    }
+    bool quiet = !(hi > h_dry);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        if (code[j] >= 0) {
+            quiet = quiet && !(nb[j].x > h_dry);
+        } else {
+            const int kind = a.bc_kind(-1 - code[j]);
+            quiet = quiet && (kind == kBcWall || kind == kBcTransmissive);
+        }
+    }
+    V4<float> out;
+    out.w = zi;
+    if (quiet) {
+        out.x = hi; out.y = 0.0f; out.z = 0.0f;
+        a.s_out[i] = out;
+        return inf_of<float>();
+    }
+    active += 1u;
+    if constexpr (!GEO_EARLY) {
+        gA = a.geoA[i];
+        gB = a.geoB[i];
+        gm2 = load_gm2(a, i, tp, 0.0f);
+    }
+    float ui, vi;
+    f32::velocity(hi, own.y, own.z, h_dry, ui, vi);
+    float f0 = 0.0f, f1 = 0.0f, f2 = 0.0f, sx = 0.0f, sy = 0.0f;
+    int4 ei = make_int4(-1, -1, -1, 0);
+    if constexpr (EDGES) ei = a.eidx[i];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const int c = j == 0 ? code[0] : (j == 1 ? code[1] : code[2]);
+        const V4<float> o = j == 0 ? nb[0] : (j == 1 ? nb[1] : nb[2]);
+        const float lx = j == 0 ? gA.x : (j == 1 ? gA.z : gB.x);
+        const float ly = j == 0 ? gA.y : (j == 1 ? gA.w : gB.y);
+        const float l2 = edge_l2(lx, ly);
+        const float rl = rsqrtf(l2);
+        const float len = f32::mul(l2, rl);
+        const float n1 = f32::mul(lx, rl), n2 = f32::mul(ly, rl);   // this cell's outward unit normal
+        float F0, F1, F2;
+        if (c >= 0) {
+            float src;
+            if constexpr (EDGES) {
+                if (!(hi > h_dry) && !(o.x > h_dry)) {
+                    const float zs = f32::sel(f32::gt(zi, o.w), zi, o.w);
+                    const float hsi = f32::max0(f32::sub(f32::add(hi, zi), zs));
+                    F0 = 0.0f; F1 = 0.0f; F2 = 0.0f;
+                    f32::bed_src(hsi, hi, g2, src);
+                } else {
+                    int e = j == 0 ? ei.x : (j == 1 ? ei.y : ei.z);
+                    if (a.debug && !(e >= 0 && e < a.n_edges)) {
+                        atomicOr(status, kStatusBadIndex);
+                        e = 0;
+                    }
+                    const V4<float> fl = a.eflux[e];
+                    if (c & kFlipBit) {
+                        F0 = -fl.x; F1 = -fl.y; F2 = -fl.z;
+                        src = a.esrc[e];
+                    } else {
+                        F0 = fl.x; F1 = fl.y; F2 = fl.z;
+                        src = fl.w;
+                    }
+                }
+            } else {
+                f32::edge_interior<float>(hi, ui, vi, zi, o.x, o.y, o.z, o.w, n1, n2, (c & kFlipBit) != 0, g, g2,
+                                          h_dry, F0, F1, F2, src, a.hll != 0);
+            }
+            sx = f32::fma(src, lx, sx);
+            sy = f32::fma(src, ly, sy);
+        } else {
+            const int grp = -1 - c;
+            f32::edge_boundary(a.bc_kind(grp), a.bc_value(grp), hi, ui, vi, zi, n1, n2, g, g2, h_dry, F0, F1, F2,
+                               a.hll != 0);
+        }
+        f0 = f32::fma(len, F0, f0);
+        f1 = f32::fma(len, F1, f1);
+        f2 = f32::fma(len, F2, f2);
+    }
+    bool clamped, nonfinite;
+    const float cand = f32::finish<float>(hi, f32::rcp_(hi), own.y, own.z, f0, f1, f2, sx, sy, gB.z, gB.w, gm2, dt, g,
+                                          h_dry, out.x, out.y, out.z, clamped, nonfinite);
+    if (clamped) atomicAdd(n_clamped, 1ULL);
+    if (nonfinite) atomicOr(status, kStatusNonFinite);
+    a.s_out[i] = out;
+    return cand;
+}
+
+// ---- two FP32 cells of the fused step at once ---------------------------------------------
+// The update of cells iA and iB by one thread: the arithmetic of
+// update_cell_f32 on float2 lanes (x = cell A, y = cell B), so each paired
+// multiply, add or fused multiply-add is one instruction for both cells, and
+// each cell gets the bits update_cell_f32 gives it.  An edge that is interior
+// for one cell and a boundary for the other is evaluated as interior for
+// both (the boundary cell against its own state) and the boundary cell's flux
+// is then replaced by its boundary flux; a quiet cell (dry among dry
+// neighbours) gets (h, 0, 0), as in update_cell_f32.
+template <typename Args>
+__device__ __forceinline__ float update_pair_f32(const Args& a, long long iA, long long iB, const V4<float>& A,
+                                                 const V4<float>& B, const int4& tpA, const int4& tpB, float dt,
+                                                 unsigned& active, unsigned long long* n_clamped, unsigned* status) {
+    const float g = a.g, h_dry = a.h_dry, g2 = f32::mul(0.5f, g);
+    int cA[3] = {tpA.x, tpA.y, tpA.z}, cB[3] = {tpB.x, tpB.y, tpB.z};
+    if (a.debug) {   // an unusable code is flagged and taken as a wall (group 0)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            if (!code_ok(cA[j], a.cell_bound(), a.n_groups)) { atomicOr(status, kStatusBadIndex); cA[j] = -1; }
+            if (!code_ok(cB[j], a.cell_bound(), a.n_groups)) { atomicOr(status, kStatusBadIndex); cB[j] = -1; }
+        }
+    }
+    V4<float> nA[3], nB[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        nA[j] = cA[j] >= 0 ? a.s_in[cA[j] & kNbrMask] : A;
+        nB[j] = cB[j] >= 0 ? a.s_in[cB[j] & kNbrMask] : B;
+    }
+    const V4<float> gAa = a.geoA[iA], gBa = a.geoB[iA], gAb = a.geoA[iB], gBb = a.geoB[iB];
+    const float gm2a = load_gm2(a, iA, tpA, 0.0f), gm2b = load_gm2(a, iB, tpB, 0.0f);
+    bool qA = !(A.x > h_dry), qB = !(B.x > h_dry);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        if (cA[j] >= 0) qA = qA && !(nA[j].x > h_dry);
+        else { const int k = a.bc_kind(-1 - cA[j]); qA = qA && (k == kBcWall || k == kBcTransmissive); }
+        if (cB[j] >= 0) qB = qB && !(nB[j].x > h_dry);
+        else { const int k = a.bc_kind(-1 - cB[j]); qB = qB && (k == kBcWall || k == kBcTransmissive); }
+    }
+    if (qA && qB) {
+        V4<float> o;
+        o.x = A.x; o.y = 0.0f; o.z = 0.0f; o.w = A.w;
+        a.s_out[iA] = o;
+        o.x = B.x; o.w = B.w;
+        a.s_out[iB] = o;
+        return inf_of<float>();
+    }
+    active += (qA ? 0u : 1u) + (qB ? 0u : 1u);
+    const float2 h = make_float2(A.x, B.x), qx = make_float2(A.y, B.y), qy = make_float2(A.z, B.z);
+    const float2 z = make_float2(A.w, B.w);
+    const float2 G = f32::splat<float2>(g), G2 = f32::splat<float2>(g2), HD = f32::splat<float2>(h_dry);
+    float2 u, v;
+    f32::velocity(h, qx, qy, HD, u, v);
+    const float2 zero = f32::splat<float2>(0.0f);
+    float2 f0 = zero, f1 = zero, f2 = zero, sx = zero, sy = zero;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const float2 lx = j == 0 ? make_float2(gAa.x, gAb.x) : (j == 1 ? make_float2(gAa.z, gAb.z) : make_float2(gBa.x, gBb.x));
+        const float2 ly = j == 0 ? make_float2(gAa.y, gAb.y) : (j == 1 ? make_float2(gAa.w, gAb.w) : make_float2(gBa.y, gBb.y));
+        const float2 l2 = f32::fma(lx, lx, f32::mul(ly, ly));
+        const float2 rl = f32::rsqrt_(l2);
+        const float2 len = f32::mul(l2, rl);
+        const float2 n1 = f32::mul(lx, rl), n2 = f32::mul(ly, rl);
+        const int ca = cA[j], cb = cB[j];
+        const bool ia = ca >= 0, ib = cb >= 0;
+        float2 F0 = zero, F1 = zero, F2 = zero;
+        if (ia || ib) {
+            const V4<float> oa = j == 0 ? nA[0] : (j == 1 ? nA[1] : nA[2]);
+            const V4<float> ob = j == 0 ? nB[0] : (j == 1 ? nB[1] : nB[2]);
+            const f32::M2 flip{ia && (ca & kFlipBit) != 0, ib && (cb & kFlipBit) != 0};
+            float2 src;
+            f32::edge_interior<float2>(h, u, v, z, make_float2(oa.x, ob.x), make_float2(oa.y, ob.y),
+                                       make_float2(oa.z, ob.z), make_float2(oa.w, ob.w), n1, n2, flip, G, G2, HD, F0,
+                                       F1, F2, src, a.hll != 0);
+            const f32::M2 in{ia, ib};
+            sx = f32::sel(in, f32::fma(src, lx, sx), sx);
+            sy = f32::sel(in, f32::fma(src, ly, sy), sy);
+        }
+        if (!ia) {
+            const int grp = -1 - ca;
+            f32::edge_boundary(a.bc_kind(grp), a.bc_value(grp), A.x, u.x, v.x, A.w, n1.x, n2.x, g, g2, h_dry, F0.x,
+                               F1.x, F2.x, a.hll != 0);
+        }
+        if (!ib) {
+            const int grp = -1 - cb;
+            f32::edge_boundary(a.bc_kind(grp), a.bc_value(grp), B.x, u.y, v.y, B.w, n1.y, n2.y, g, g2, h_dry, F0.y,
+                               F1.y, F2.y, a.hll != 0);
+        }
+        f0 = f32::fma(len, F0, f0);
+        f1 = f32::fma(len, F1, f1);
+        f2 = f32::fma(len, F2, f2);
+    }
+    float2 oh, ou, ov;
+    f32::M2 clamped, nonfinite;
+    const float2 cand = f32::finish<float2>(h, f32::rcp_(h), qx, qy, f0, f1, f2, sx, sy, make_float2(gBa.z, gBb.z),
+                                            make_float2(gBa.w, gBb.w), make_float2(gm2a, gm2b),
+                                            f32::splat<float2>(dt), G, HD, oh, ou, ov, clamped, nonfinite);
+    V4<float> o;
+    if (qA) {
+        o.x = A.x; o.y = 0.0f; o.z = 0.0f;
+    } else {
+        o.x = oh.x; o.y = ou.x; o.z = ov.x;
+        if (clamped.x) atomicAdd(n_clamped, 1ULL);
+        if (nonfinite.x) atomicOr(status, kStatusNonFinite);
+    }
+    o.w = A.w;
+    a.s_out[iA] = o;
+    if (qB) {
+        o.x = B.x; o.y = 0.0f; o.z = 0.0f;
+    } else {
+        o.x = oh.y; o.y = ou.y; o.z = ov.y;
+        if (clamped.y) atomicAdd(n_clamped, 1ULL);
+        if (nonfinite.y) atomicOr(status, kStatusNonFinite);
+    }
+    o.w = B.w;
+    a.s_out[iB] = o;
+    const float inf = inf_of<float>();
+    return min_nonneg(qA ? inf : cand.x, qB ? inf : cand.y);
+}
+
 // ---- one cell of the fused step -----------------------------------------------------
 // Returns the cell's CFL candidate R_i/(sqrt(g h)+|u|) of the new state (+inf
 // when the new state is dry); sets `active` when the full flux path ran.
@@ -620,10 +942,21 @@ __device__ __forceinline__ void friction_update(T hi, T qx, T qy, T gm2, T Rh, T
 template <typename T, bool GEO_EARLY, bool EDGES = false, typename Args>
 __device__ __forceinline__ T update_cell(const Args& a, long long i, const V4<T>& own, const int4& tp, T dt,
                                          unsigned& active, unsigned long long* n_clamped, unsigned* status) {
+    if constexpr (std::is_same<T, float>::value) {
+        return update_cell_f32<GEO_EARLY, EDGES>(a, i, own, tp, dt, active, n_clamped, status);
+    } else {
     using A = Ar<T>;
     const T g = a.g, h_dry = a.h_dry;
     const T hi = own.x, zi = own.w;
-    const int code[3] = {tp.x, tp.y, tp.z};
+    int code[3] = {tp.x, tp.y, tp.z};
+    if (a.debug) {   // an unusable code is flagged and taken as a wall (group 0)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            if (!code_ok(code[j], a.cell_bound(), a.n_groups)) {
+                atomicOr(status, kStatusBadIndex);
+                code[j] = -1;
+            }
+    }
     // issue the three neighbour gathers before any arithmetic
     V4<T> nb[3];
 #pragma unroll
@@ -672,7 +1005,7 @@ __device__ __forceinline__ T update_cell(const Args& a, long long i, const V4<T>
         const V4<T> o = j == 0 ? nb[0] : (j == 1 ? nb[1] : nb[2]);
         const T lx = j == 0 ? gA.x : (j == 1 ? gA.z : gB.x);
         const T ly = j == 0 ? gA.y : (j == 1 ? gA.w : gB.y);
-        const T l2 = lx * lx + ly * ly;
+        const T l2 = edge_l2(lx, ly);
         const T rl = edge_rl<T>(j == 0 ? gR.x : (j == 1 ? gR.y : gR.z), l2);
         const T len = l2 * rl;
         const T n1 = lx * rl, n2 = ly * rl;     // this cell's outward unit normal
@@ -686,7 +1019,11 @@ __device__ __forceinline__ T update_cell(const Args& a, long long i, const V4<T>
                     F0 = T(0); F1 = T(0); F2 = T(0);
                     src = T(0.5) * g * (hsi * hsi - hi * hi);
                 } else {
-                    const int e = j == 0 ? ei.x : (j == 1 ? ei.y : ei.z);
+                    int e = j == 0 ? ei.x : (j == 1 ? ei.y : ei.z);
+                    if (a.debug && !(e >= 0 && e < a.n_edges)) {
+                        atomicOr(status, kStatusBadIndex);
+                        e = 0;
+                    }
                     const V4<T> fl = a.eflux[e];
                     if (c & kFlipBit) {
                         F0 = -fl.x; F1 = -fl.y; F2 = -fl.z;
@@ -711,41 +1048,8 @@ __device__ __forceinline__ T update_cell(const Args& a, long long i, const V4<T>
         f1 += len * F1;
         f2 += len * F2;
     }
-    const T ia = gB.z;
-    const T Rh = -f0 * ia;
-    const T Rx = (sx - f1) * ia;
-    const T Ry = (sy - f2) * ia;
-    const T qx = own.y, qy = own.z;
-    T dh, dqx, dqy;
-    friction_update<T>(hi, qx, qy, gm2, Rh, Rx, Ry, dt, h_dry, dh, dqx, dqy);
-    out.x = hi + dh;
-    out.y = qx + dqx;
-    out.z = qy + dqy;
-    if (lt_zero(out.x)) {
-        out.x = T(0); out.y = T(0); out.z = T(0);
-        atomicAdd(n_clamped, 1ULL);
-    } else if (le_pos(out.x, h_dry)) {
-        out.y = T(0); out.z = T(0);
+    return finish_cell<T>(a, i, own, f0, f1, f2, sx, sy, gB.z, gB.w, gm2, dt, n_clamped, status);
     }
-    const T big = T(3.0e38);
-    if (!lt_pos(out.x, big) || !abs_lt_pos(out.y, big) || !abs_lt_pos(out.z, big))
-        atomicOr(status, kStatusNonFinite);
-    a.s_out[i] = out;
-    // next CFL candidate (Eq 15), R_i / (sqrt(g h) + |u|) on the new state
-    T cand = inf_of<T>();
-    if (gt_pos(out.x, h_dry)) {
-        if constexpr (kOneDivision<T>) {
-            // R h / (h sqrt(g h) + |q|): the velocity's division folded into the candidate's
-            const T qm = A::sqrt_(out.y * out.y + out.z * out.z);
-            cand = A::div_(gB.w * out.x, out.x * A::sqrt_(g * out.x) + qm);
-        } else {
-            const T r = A::rcp_(out.x);
-            const T u = out.y * r, v = out.z * r;
-            const T den = A::sqrt_(g * out.x) + A::sqrt_(u * u + v * v);
-            cand = A::div_(gB.w, den);
-        }
-    }
-    return cand;
 }
 
 // ---- the fused step: fluxes + bed source + BCs + friction + update + next dt ------
@@ -811,6 +1115,48 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_kernel(const StepArgs<T> a) 
     block_min_publish<BLOCK>(cand, a.dt_write, active, a.n_active);
 }
 
+// ---- the fused FP32 step, two cells per thread ------------------------------------------
+// One warp per 64 consecutive cells (grid-stride over such tiles): lane l
+// updates cells 64 t + l and 64 t + 32 + l together (update_pair_f32), so every
+// load is coalesced and every paired FP32 instruction serves two cells; a
+// ragged last tile's unpaired cells take update_cell_f32.  The same bits as
+// step_kernel.
+template <int BLOCK, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) step_kernel_x2(const StepArgs<float> a) {
+    static_assert(BLOCK % 32 == 0, "whole warps");
+    constexpr int W = BLOCK / 32;
+    const WarpDt<float> wdt = warp_step_dt<float>(a.cfl, a.dt_read, a.dt_fixed);
+    const double dt_d = wdt.d;
+    const bool have_dt = wdt.have;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *a.dt_reset = kInfBits;
+        if (have_dt) *a.t += dt_d;
+        else atomicOr(a.status, kStatusDry);
+        if (a.dt_log) *a.dt_log = dt_d;
+    }
+    float cand = inf_of<float>();
+    unsigned active = 0u;
+    if (!have_dt) {
+        for (long long i = (long long)blockIdx.x * BLOCK + threadIdx.x; i < a.n; i += (long long)gridDim.x * BLOCK)
+            a.s_out[i] = a.s_in[i];
+    } else {
+        const float dt = wdt.t;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const long long n_tiles = (a.n + 63) / 64;
+        const long long stride = (long long)gridDim.x * W;
+        for (long long t = (long long)blockIdx.x * W + warp; t < n_tiles; t += stride) {
+            const long long iA = t * 64 + lane, iB = iA + 32;
+            if (iB < a.n)
+                cand = min_nonneg(cand, update_pair_f32(a, iA, iB, a.s_in[iA], a.s_in[iB], a.topo[iA], a.topo[iB], dt,
+                                                        active, a.n_clamped, a.status));
+            else if (iA < a.n)
+                cand = min_nonneg(cand, update_cell_f32<true, false>(a, iA, a.s_in[iA], a.topo[iA], dt, active,
+                                                                     a.n_clamped, a.status));
+        }
+    }
+    block_min_publish<BLOCK>(cand, a.dt_write, active, a.n_active);
+}
+
 // ---- edge pass: each interior edge's flux once per step ----------------------------
 // The canonical evaluation of an interior edge (from its left cell, Eq 12-30)
 // is the one both of its cells make in step_kernel; here one thread makes it
@@ -825,10 +1171,14 @@ __global__ void __launch_bounds__(BLOCK) edge_flux_kernel(const StepArgs<T> a) {
     const long long stride = (long long)gridDim.x * BLOCK;
     for (long long e = (long long)blockIdx.x * BLOCK + threadIdx.x; e < a.n_edges; e += stride) {
         const int2 lr = a.ecells[e];
+        if (a.debug && !(lr.x >= 0 && lr.x < a.n && lr.y >= 0 && lr.y < a.n)) {
+            atomicOr(a.status, kStatusBadIndex);
+            continue;
+        }
         const V4<T> L = a.s_in[lr.x], R = a.s_in[lr.y];
         if (!gt_pos(L.x, h_dry) && !gt_pos(R.x, h_dry)) continue;
         const T lx = a.eln[2 * e], ly = a.eln[2 * e + 1];
-        const T l2 = lx * lx + ly * ly;
+        const T l2 = edge_l2(lx, ly);
         T pre = T(0);
         if constexpr (sizeof(T) == 8) pre = a.erl[e];
         const T rl = edge_rl<T>(pre, l2);
@@ -958,7 +1308,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_kernel_act(const StepArgs<T>
 #pragma unroll
                         for (int j = 0; j < 3; ++j) {
                             const int code = tv[j];
-                            if (code >= 0) a.act_next[code & kNbrMask] = 1;
+                            if (code >= 0 && (!a.debug || code_ok(code, a.n, a.n_groups)))
+                                a.act_next[code & kNbrMask] = 1;
                         }
                     }
                 }
@@ -983,10 +1334,10 @@ __global__ void act_init_kernel(const V4<T>* __restrict__ s, const int4* __restr
     const bool wet = s[c].x > h_dry;
     const int4 tp = topo[c];
     if (wet || (tp.w & kStaticBit)) act[c] = 1;
-    if (wet) {
-        if (tp.x >= 0) act[tp.x & kNbrMask] = 1;
-        if (tp.y >= 0) act[tp.y & kNbrMask] = 1;
-        if (tp.z >= 0) act[tp.z & kNbrMask] = 1;
+    if (wet) {   // (an out-of-range index is skipped here; the step's debug checks report it)
+        if (tp.x >= 0 && (tp.x & kNbrMask) < n) act[tp.x & kNbrMask] = 1;
+        if (tp.y >= 0 && (tp.y & kNbrMask) < n) act[tp.y & kNbrMask] = 1;
+        if (tp.z >= 0 && (tp.z & kNbrMask) < n) act[tp.z & kNbrMask] = 1;
     }
 }
 
@@ -1302,7 +1653,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel_act(const En
 #pragma unroll
                 for (int j = 0; j < 3; ++j) {
                     const int code = tv[j];
-                    if (code >= 0) a.act_next[code & kNbrMask] = 1;
+                    if (code >= 0 && (!a.debug || code_ok(code, a.n_total, a.n_groups)))
+                        a.act_next[code & kNbrMask] = 1;
                 }
             }
         }
@@ -1389,6 +1741,9 @@ struct Launch {
                                        int edges, int* per_sm);
     // compiled (block, min_blocks, stages, geo_early) shapes of the cell pass of the edge-pass step
     static int edge_variants(int (*out)[4], int max);
+    // compiled (block, min_blocks) shapes of the two-cells-per-thread step (FP32; a.pairs set;
+    // resident_blocks with edges = 2)
+    static int pair_variants(int (*out)[2], int max);
     // the edge pass alone (interior fluxes of a.s_in into a.eflux, a.esrc)
     static cudaError_t edge_flux(const StepArgs<T>& a, cudaStream_t st);
     // compiled (block, min_blocks, geo_early, stages = prefetch distance + 1) shapes of the activity kernel

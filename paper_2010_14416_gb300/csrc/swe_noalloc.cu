@@ -11,7 +11,6 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
-#include <mutex>
 #include <string>
 
 #include "swe_internal.h"
@@ -21,14 +20,10 @@ namespace {
 
 constexpr int kNoallocBlock = 256;
 constexpr int kNoallocMaxBlocks = 65536;  // 512 KiB of scratch
-constexpr int kNoallocMaxDevices = 64;
 
 // per-block minima of R_i / (sqrt(g h_i) + |u_i|); every call rewrites the
 // slots of the blocks it launches, so nothing has to be cleared between calls
 static __device__ __align__(256) double g_noalloc_scratch[kNoallocMaxBlocks];
-
-std::mutex g_addr_mutex;
-void* g_addr[kNoallocMaxDevices] = {nullptr};
 
 template <typename T>
 __global__ void __launch_bounds__(kNoallocBlock)
@@ -73,30 +68,19 @@ cfl_final_kernel(const double* __restrict__ partial, int n_blocks, double cfl, d
     }
 }
 
-// Device address of the scratch array on the current device, looked up once
-// per device (the array's name in host code is only a host-side stand-in).
+// Device address of the scratch array on the current device.  The array's
+// name in host code is only a host-side stand-in, so the address is asked for
+// on every call (the lookup allocates nothing): a cached address would point
+// at freed memory once cudaDeviceReset has replaced the device's context.
+// The first lookup on a device loads this library's device code there.
 int scratch_address(double** out) {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) {
-        set_error(std::string("swe_cfl_dt_noalloc: cudaGetDevice: ") + cudaGetErrorString(e));
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        set_error(std::string("swe_cfl_dt_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
         return SWE_ECUDA;
     }
-    if (dev < 0 || dev >= kNoallocMaxDevices) {
-        set_error("swe_cfl_dt_noalloc: device ordinal out of range");
-        return SWE_EINVAL;
-    }
-    std::lock_guard<std::mutex> lock(g_addr_mutex);
-    if (!g_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            set_error(std::string("swe_cfl_dt_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-            return SWE_ECUDA;
-        }
-        g_addr[dev] = p;
-    }
-    *out = (double*)g_addr[dev];
+    *out = (double*)p;
     return SWE_OK;
 }
 

@@ -208,9 +208,35 @@ def river_13m(seed=1) -> MeshInput:
     return river(8064, 806, seed=seed)
 
 
+def river_13m_wet(seed=1) -> MeshInput:
+    """The 12,999,168-cell river, fully wet (depth >= 0.5 m): every cell runs
+    the flux path in every step."""
+    return river(8064, 806, seed=seed, fully_wet=True)
+
+
+def river_adjoint(nx, ny, seed=1, u0=0.5) -> MeshInput:
+    """The adjoint workload's reach: the river generator on the 20 km x 2 km
+    domain at nx x ny quads, fully wet, with the free surface inclined from
+    eta0 + 1 m at x = 0 to eta0 = max(z) + 0.5 m at the outflow (Section 6.5.1's
+    initialisation) and the water moving downstream at u0 m/s, so that it flows
+    past the gauges from the first step and the loss depends on the Manning
+    coefficients as well as on the bed."""
+    mi = river(nx, ny, seed=seed, fully_wet=True)
+    eta0 = mi.meta["eta0"]
+    mi = inclined_plane(mi, eta_up=eta0 + 1.0, eta_down=eta0)
+    mi.hu = u0 * mi.h
+    mi.meta.update(u0=u0)
+    return mi
+
+
 def river_adjoint_1m(seed=1) -> MeshInput:
-    """1,001,728-cell synthetic river, fully wet (depth >= 0.5 m)."""
-    return river(2236, 224, seed=seed, fully_wet=True)
+    """1,001,728-cell adjoint reach (river_adjoint at 2236 x 224 quads)."""
+    return river_adjoint(2236, 224, seed=seed)
+
+
+def river_adjoint_20k(seed=1) -> MeshInput:
+    """20,224-cell copy of the adjoint reach (316 x 32 quads, the same 20 km x 2 km)."""
+    return river_adjoint(316, 32, seed=seed)
 
 
 def river_cells(n_cells, seed=1, **kw) -> MeshInput:

@@ -124,8 +124,10 @@ def test_malformed_meshes_rejected_by_host_preprocessing():
 
 
 @pytest.mark.parametrize("kw", [dict(g=0.0), dict(g=float("inf")), dict(h_dry=-1e-6), dict(h_dry=float("nan")),
-                                dict(h_dry=float("inf")), dict(precision=7), dict(flux=5), dict(geometry_early=2),
-                                dict(activity=3), dict(edge_pass=2), dict(grid=-1), dict(activity=1, edge_pass=1),
+                                dict(h_dry=float("inf")), dict(h_dry=1e-40), dict(precision=7), dict(flux=5), dict(geometry_early=2),
+                                dict(activity=3), dict(edge_pass=2), dict(edge_pass=-1), dict(grid=-1), dict(debug_checks=2),
+                                dict(activity=1, edge_pass=1), dict(cell_pairs=2), dict(cell_pairs=1),
+                                dict(cell_pairs=1, precision=1, activity=1), dict(cell_pairs=1, precision=1, edge_pass=1),
                                 dict(block_size=96)])
 def test_invalid_configs_rejected_before_any_device_work(kw):
     # swe_mesh_create validates its configuration before it touches the
@@ -145,3 +147,21 @@ def test_invalid_fields_rejected_before_any_device_work(field, value):
     with pytest.raises(capi.SWEError) as e:
         capi.Mesh(mi.nodes, mi.tris, z, manning)
     assert e.value.code == capi.SWE_EINVAL
+
+
+def test_debug_check_predicate():
+    # the check debug_checks applies to each neighbour code before use: an
+    # interior code names a cell below n (bit 30 marks the edge's right side),
+    # a boundary code -1 - g names a group below n_groups
+    ok = capi.debug_code_ok
+    n, ng = 1000, 3
+    flip = 1 << 30
+    assert ok(0, n, ng) and ok(n - 1, n, ng) and ok((n - 1) | flip, n, ng)
+    assert not ok(n, n, ng) and not ok(n | flip, n, ng) and not ok((1 << 30) - 1, n, ng)
+    assert ok(-1, n, ng) and ok(-ng, n, ng)
+    assert not ok(-ng - 1, n, ng) and not ok(-(2 ** 31), n, ng)
+    assert not ok(0, 0, ng) and not ok(-1, n, 0)
+    # every code of a valid mesh passes, with the mesh's own sizes
+    mi = mg.river(30, 6, seed=2)
+    P = capi.mesh_preprocess(mi.nodes, mi.tris)
+    assert all(ok(int(c), mi.n_cells, 1) for c in P["code"].ravel())

@@ -26,8 +26,8 @@ def _members(n=8, seed=3):
     return mg.ensemble_members(n, seed=seed, lo=1500, hi=30000)
 
 
-def _mesh(mi, precision):
-    m = capi.Mesh(mi.nodes, mi.tris, mi.z, mi.manning, precision=precision)
+def _mesh(mi, precision, **kw):
+    m = capi.Mesh(mi.nodes, mi.tris, mi.z, mi.manning, precision=precision, **kw)
     for pairs, kind, value in mi.bcs:
         m.set_bc(pairs, kind, value)
     dt = m.dtype
@@ -142,4 +142,36 @@ def test_ensemble_launch_shapes_are_bitwise_neutral(precision):
         ens.set_shape(block_size=256, min_blocks=4 if f32 else 1, dynamic=1, edge_pass=1)
     ens.close()
     for m in meshes:
+        m.close()
+
+
+@pytest.mark.parametrize("precision", [capi.SWE_FP64, capi.SWE_FP32])
+def test_ensemble_debug_checks_change_nothing(precision):
+    # members created with debug checks: the batched kernels check every
+    # index and boundary group before use; a valid ensemble steps exactly as
+    # without them, with status 0
+    mis = _members(4, seed=9)
+    ref_meshes = [_mesh(mi, precision) for mi in mis]
+    ref = capi.Ensemble(ref_meshes)
+    t_ref = ref.step(120)
+    dbg_meshes = [_mesh(mi, precision, debug_checks=1) for mi in mis]
+    dbg = capi.Ensemble(dbg_meshes)
+    shapes = [None, dict(block_size=128, min_blocks=8 if precision == capi.SWE_FP32 else 1, activity=1, chunk=4)]
+    if precision == capi.SWE_FP64:
+        shapes.append(dict(block_size=256, min_blocks=1, edge_pass=1, chunk=4))
+    for shape in shapes:
+        for k, m in enumerate(dbg_meshes):
+            m.set_state(*(a.astype(m.dtype) for a in (mis[k].h, mis[k].hu, mis[k].hv)))
+        dbg.close()
+        dbg = capi.Ensemble(dbg_meshes)
+        if shape:
+            dbg.set_shape(**shape)
+        t = dbg.step(120)
+        assert np.array_equal(t, t_ref), shape
+        for k in range(len(mis)):
+            assert dbg.info(k)["status"] == 0
+            assert all(np.array_equal(a, b) for a, b in zip(dbg.get_state(k), ref.get_state(k))), (shape, k)
+    for e in (ref, dbg):
+        e.close()
+    for m in ref_meshes + dbg_meshes:
         m.close()

@@ -183,3 +183,38 @@ def test_hll_conservation_symmetry():
         assert Gb[0] == pytest.approx(-Gf[0], rel=1e-11, abs=1e-11)
         assert Gb[1] == pytest.approx(Gf[1], rel=1e-11, abs=1e-11)
         assert Gb[2] == pytest.approx(Gf[2], rel=1e-11, abs=1e-11)
+
+
+# ---------------------------------------------------------------------------
+# Eq 19-25 worked by hand on asymmetric wet states (tests/golden/sstar_asym.txt)
+# ---------------------------------------------------------------------------
+
+from tests.golden_cases import read_cases  # noqa: E402
+
+SSTAR = read_cases("sstar_asym.txt")
+
+
+@pytest.mark.parametrize("name", sorted(SSTAR))
+def test_hllc_speeds_and_flux_match_hand_worked_asymmetric_states(name):
+    c = SSTAR[name]
+    hs, h0 = oracle.hstar(c["hL"], c["unL"], c["hR"], c["unR"])
+    assert h0 == pytest.approx(c["h0"], rel=1e-13)
+    assert hs == pytest.approx(c["hstar"], rel=1e-13)
+    G, S = oracle.hllc(c["hL"], c["unL"], c["utL"], c["hR"], c["unR"], c["utR"])
+    assert S[0] == pytest.approx(c["SL"], rel=1e-13)
+    assert S[1] == pytest.approx(c["SR"], rel=1e-13)
+    assert S[2] == pytest.approx(c["Sstar"], rel=1e-12)
+    for k in range(3):
+        assert G[k] == pytest.approx(c[f"G{k + 1}"], rel=1e-12)
+
+
+def test_hand_worked_states_cover_both_contact_sides_and_both_estimates():
+    # the golden cases exercise S* of either sign, a shock on either side and
+    # both star-depth estimates (Eq 22 and Eq 23)
+    signs = {math.copysign(1.0, c["Sstar"]) for c in SSTAR.values()}
+    assert signs == {1.0, -1.0}
+    assert any(c["pL"] > 1 for c in SSTAR.values()) and any(c["pR"] > 1 for c in SSTAR.values())
+    two_rare = [c for c in SSTAR.values() if c["h0"] <= min(c["hL"], c["hR"])]
+    assert two_rare and len(two_rare) < len(SSTAR)
+    for c in SSTAR.values():
+        assert c["hL"] != c["hR"] and c["unL"] != c["unR"]
