@@ -133,13 +133,6 @@ typedef struct swe_config {
                          for a memory checker on the library's own index tables; it costs one
                          branch per cell when off.  0 (default): no checks.  Results of a valid
                          mesh do not depend on it */
-    int cell_pairs;   /* FP32 only: 1 = each thread updates two cells at once (cells 64 t + l and
-                         64 t + 32 + l for warp tile t and lane l), every FP32 multiply, add and
-                         fused multiply-add one paired instruction for both; 0 (default) = one
-                         cell per thread.  Compiled (block_size, min_blocks): (128, 3|4|5),
-                         (256, 2); stages and geometry_early are ignored.  Not with activity or
-                         edge_pass.  Results do not depend on it (the one-cell kernels round
-                         every operation the same way) */
 } swe_config;
 
 /* Fills *cfg with the defaults listed above. */
@@ -480,8 +473,6 @@ typedef struct swe_tune {
     double ms_before;        /* measured time per step of the shape in use before the call (ms;
                                 from the runoff, which always includes it, when one ran) */
     int n_candidates;        /* shapes timed */
-    int cell_pairs;          /* chosen two-cells-per-thread mode (swe_config.cell_pairs); 0 for an
-                                ensemble */
 } swe_tune;
 
 /*

@@ -91,9 +91,73 @@ __device__ __forceinline__ void edge_ln(const V4<double>& gA, const V4<double>& 
     ly = j == 0 ? gA.y : (j == 1 ? gA.w : gB.y);
 }
 
+// Reverse of the semi-implicit friction update (friction_update, Eq 33-37,
+// the literal formulas) at (h, qx, qy, g m^2, Rh, Rx, Ry): for the adjoints
+// (bdh, bdqx, bdqy) of (dh, dqx, dqy), the adjoints w[0..6] of the seven
+// inputs, in the order of the dual-number seeds.
+__device__ void friction_rev(double hi, double qx, double qy, double gm2, double Rh, double Rx, double Ry, double dt,
+                             double h_dry, double bdh, double bdqx, double bdqy, double w[7]) {
+    const double dh = dt * Rh, dqx0 = dt * Rx, dqy0 = dt * Ry;
+    const double qq = qx * qx + qy * qy;
+    const bool act = gt_pos(hi, h_dry) && gt_zero(gm2) && gt_zero(qq);
+#pragma unroll
+    for (int k = 0; k < 7; ++k) w[k] = 0.0;
+    if (!act) {
+        w[4] = bdh * dt; w[5] = bdqx * dt; w[6] = bdqy * dt;
+        return;
+    }
+    // forward
+    const double qn = sqrt(qq);
+    const double p = 1.0 / (hi * hi * cbrt(hi));                // h^(-7/3)
+    const double cf = gm2 * p, rh = 1.0 / hi;
+    const double al = 0.5 * dt * cf;
+    const double P = 7.0 / 6.0 * dh * rh - 1.0;
+    const double k = dt * cf * qn * P;
+    const double bx = dqx0 + k * qx, by = dqy0 + k * qy;
+    const double d1 = 1.0 + al * qn, d2 = d1 + al * qn;
+    const double rqd2 = 1.0 / (qn * d2), rd1 = 1.0 / d1;
+    const double S = bx * qx + by * qy;
+    const double proj = S * al * rqd2;
+    // reverse: dq = (b - proj q) / d1
+    const double b_rd1 = bdqx * (bx - proj * qx) + bdqy * (by - proj * qy);
+    double b_bx = bdqx * rd1, b_by = bdqy * rd1;
+    const double b_proj = -(bdqx * qx + bdqy * qy) * rd1;
+    double b_qx = -bdqx * proj * rd1, b_qy = -bdqy * proj * rd1;
+    // proj = S al / (|q| d2)
+    const double b_S = b_proj * al * rqd2;
+    double b_al = b_proj * S * rqd2;
+    const double b_rqd2 = b_proj * S * al;
+    b_bx += b_S * qx; b_qx += b_S * bx;
+    b_by += b_S * qy; b_qy += b_S * by;
+    double b_qn = -b_rqd2 * rqd2 * rqd2 * d2;
+    const double b_d2 = -b_rqd2 * rqd2 * rqd2 * qn;
+    double b_d1 = -b_rd1 * rd1 * rd1 + b_d2;
+    b_al += b_d2 * qn + b_d1 * qn;
+    b_qn += b_d2 * al + b_d1 * al;
+    // b = dt R_q + k q
+    const double b_k = b_bx * qx + b_by * qy;
+    b_qx += b_bx * k; b_qy += b_by * k;
+    // k = dt c |q| P, P = (7/6) dh / h - 1
+    double b_cf = b_k * dt * qn * P + b_al * 0.5 * dt;
+    b_qn += b_k * dt * cf * P;
+    const double b_P = b_k * dt * cf * qn;
+    const double b_dh = bdh + b_P * 7.0 / 6.0 * rh;
+    const double b_rh = b_P * 7.0 / 6.0 * dh;
+    // c = g m^2 h^(-7/3), 1/h, |q| = sqrt(qx^2 + qy^2)
+    const double b_h = -b_rh * rh * rh - b_cf * gm2 * (7.0 / 3.0) * p * rh;
+    const double b_gm2 = b_cf * p;
+    const double b_qq = b_qn / (2.0 * qn);
+    b_qx += 2.0 * b_qq * qx;
+    b_qy += 2.0 * b_qq * qy;
+    w[0] = b_h; w[1] = b_qx; w[2] = b_qy; w[3] = b_gm2;
+    w[4] = b_dh * dt; w[5] = b_bx * dt; w[6] = b_by * dt;
+}
+
 // EDGES reads R_i's interior fluxes from the edge pass (the forward's own
 // edge-pass arithmetic) instead of evaluating them; R_i is the same bit for bit.
-template <bool EDGES>
+// TRANSPOSE transposes the friction update by hand (friction_rev) instead of
+// running it on seven-component duals.
+template <bool EDGES, bool TRANSPOSE>
 __global__ void __launch_bounds__(128) adj_phase1_kernel(const AdjArgs a) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
@@ -156,19 +220,28 @@ __global__ void __launch_bounds__(128) adj_phase1_kernel(const AdjArgs a) {
     }
     const double ia = gB.z;
     const double Rh = -f0 * ia, Rx = (sx - f1) * ia, Ry = (sy - f2) * ia;
-    // Phi on duals: seeds h, hu, hv, g m^2, Rh, Rx, Ry
-    D7 dh, dqx, dqy;
-    friction_update<D7>(D7::seed(hi, 0), D7::seed(own.y, 1), D7::seed(own.z, 2), D7::seed(a.gm2[i], 3),
-                        D7::seed(Rh, 4), D7::seed(Rx, 5), D7::seed(Ry, 6), D7(a.dt), D7(h_dry), dh, dqx, dqy);
-    // the forward's clamps: h < 0 zeroes the cell, h <= h_dry zeroes momentum
     const V4<double> L = a.lam[i];
     double lh = L.x, lx_ = L.y, ly_ = L.z;
-    const double hn = hi + dh.v;
-    if (hn < 0.0) { lh = 0.0; lx_ = 0.0; ly_ = 0.0; }
-    else if (hn <= h_dry) { lx_ = 0.0; ly_ = 0.0; }
     double w[7];
+    if constexpr (TRANSPOSE) {
+        // the forward's clamps (h < 0 zeroes the cell, h <= h_dry zeroes momentum) on
+        // the new depth, then the friction update's transpose
+        const double hn = hi + a.dt * Rh;
+        if (hn < 0.0) { lh = 0.0; lx_ = 0.0; ly_ = 0.0; }
+        else if (hn <= h_dry) { lx_ = 0.0; ly_ = 0.0; }
+        friction_rev(hi, own.y, own.z, a.gm2[i], Rh, Rx, Ry, a.dt, h_dry, lh, lx_, ly_, w);
+    } else {
+        // Phi on duals: seeds h, hu, hv, g m^2, Rh, Rx, Ry
+        D7 dh, dqx, dqy;
+        friction_update<D7>(D7::seed(hi, 0), D7::seed(own.y, 1), D7::seed(own.z, 2), D7::seed(a.gm2[i], 3),
+                            D7::seed(Rh, 4), D7::seed(Rx, 5), D7::seed(Ry, 6), D7(a.dt), D7(h_dry), dh, dqx, dqy);
+        // the forward's clamps: h < 0 zeroes the cell, h <= h_dry zeroes momentum
+        const double hn = hi + dh.v;
+        if (hn < 0.0) { lh = 0.0; lx_ = 0.0; ly_ = 0.0; }
+        else if (hn <= h_dry) { lx_ = 0.0; ly_ = 0.0; }
 #pragma unroll
-    for (int k = 0; k < 7; ++k) w[k] = lh * dh.d[k] + lx_ * dqx.d[k] + ly_ * dqy.d[k];
+        for (int k = 0; k < 7; ++k) w[k] = lh * dh.d[k] + lx_ * dqx.d[k] + ly_ * dqy.d[k];
+    }
     V4<double> own_term;
     own_term.x = lh + w[0];
     own_term.y = lx_ + w[1];
@@ -751,6 +824,20 @@ int adjoint_impl(swe_mesh* m, int64_t nsteps, double cfl, const int32_t* gauge_c
     }
     const unsigned egrid = (unsigned)std::min<int64_t>((std::max<int64_t>(m->n_edges, 1) + 127) / 128, 65535);
     const unsigned grid = (unsigned)((n + 127) / 128);
+    // With the edge pass, the recomputation of a segment keeps each step's edge
+    // fluxes (64 B per interior edge and step), so phase 1 reads the fluxes of
+    // U^n that the recomputed step n -> n+1 formed instead of running the edge
+    // pass again; without room for them, phase 1 runs it.
+    DevBuf segflux, segsrc;
+    const size_t Eb = (size_t)std::max<int64_t>(m->n_edges, 1);
+    bool keep = edges && transposes;
+    if (keep) {
+        keep = cudaMalloc(&segflux.p, (size_t)K * Eb * sizeof(V4<double>)) == cudaSuccess &&
+               cudaMalloc(&segsrc.p, (size_t)K * Eb * sizeof(double)) == cudaSuccess;
+        if (!keep) (void)cudaGetLastError();   // clear the failed allocation's error
+    }
+    V4<double>* const sflux = (V4<double>*)segflux.p;
+    double* const ssrc = (double*)segsrc.p;
     // reverse sweep, segment by segment
     for (int64_t sgi = nseg - 1; sgi >= 0 && e == cudaSuccess; --sgi) {
         const int64_t n0 = sgi * K, n1 = std::min<int64_t>(n0 + K, nsteps);
@@ -758,17 +845,31 @@ int adjoint_impl(swe_mesh* m, int64_t nsteps, double cfl, const int32_t* gauge_c
         e = cudaMemcpyAsync(segp, (char*)ckpt.p + sgi * sb, sb, cudaMemcpyDeviceToDevice, st);
         for (int64_t k = 0; k + 1 < n1 - n0 && e == cudaSuccess; ++k)
             e = launch_step_raw(m, segp + k * sb, segp + (k + 1) * sb, (unsigned long long*)small.p, k, cfl,
-                                (const double*)dtlog.p + n0 + k, nullptr, st);
+                                (const double*)dtlog.p + n0 + k, nullptr, st, false,
+                                keep ? (void*)(sflux + k * Eb) : nullptr, keep ? (void*)(ssrc + k * Eb) : nullptr);
+        if (keep && e == cudaSuccess) {   // the segment's last state has no recomputed step
+            const int64_t k = n1 - n0 - 1;
+            ea.s_in = (const V4<double>*)(segp + k * sb);
+            ea.eflux = sflux + k * Eb;
+            ea.esrc = ssrc + k * Eb;
+            e = Launch<double>::edge_flux(ea, st);
+        }
         for (int64_t k = n1 - n0 - 1; k >= 0 && e == cudaSuccess; --k) {
             a.U = (const V4<double>*)(segp + k * sb);
             a.dt = dts[n0 + k];
-            if (edges) {
+            if (keep) {
+                a.eflux = sflux + k * Eb;
+                a.esrc = ssrc + k * Eb;
+                adj_phase1_kernel<true, true><<<grid, 128, 0, st>>>(a);
+            } else if (edges) {
                 ea.s_in = a.U;
                 e = Launch<double>::edge_flux(ea, st);
                 if (e != cudaSuccess) break;
-                adj_phase1_kernel<true><<<grid, 128, 0, st>>>(a);
+                if (transposes) adj_phase1_kernel<true, true><<<grid, 128, 0, st>>>(a);
+                else adj_phase1_kernel<true, false><<<grid, 128, 0, st>>>(a);
             } else {
-                adj_phase1_kernel<false><<<grid, 128, 0, st>>>(a);
+                if (transposes) adj_phase1_kernel<false, true><<<grid, 128, 0, st>>>(a);
+                else adj_phase1_kernel<false, false><<<grid, 128, 0, st>>>(a);
             }
             if (transposes) {
                 adj_edge_kernel<<<egrid, 128, 0, st>>>(a);

@@ -220,7 +220,6 @@ StepArgs<T> make_args(swe_mesh* m, int64_t step_index, double cfl) {
     a.bc = m->bc;
     a.debug = m->cfg.debug_checks;
     a.n_groups = m->n_groups;
-    a.pairs = m->cfg.cell_pairs;
     return a;
 }
 
@@ -381,7 +380,8 @@ namespace swe {
 
 template <typename T>
 cudaError_t launch_raw_t(swe_mesh* m, const void* in, void* out, unsigned long long* small, int64_t step_index,
-                         double cfl, const double* dt_fixed, double* dt_log, cudaStream_t st, bool with_activity) {
+                         double cfl, const double* dt_fixed, double* dt_log, cudaStream_t st, bool with_activity,
+                         void* eflux_out, void* esrc_out) {
     StepArgs<T> a = make_args<T>(m, step_index, cfl);
     a.s_in = (const V4<T>*)in;
     a.s_out = (V4<T>*)out;
@@ -403,11 +403,10 @@ cudaError_t launch_raw_t(swe_mesh* m, const void* in, void* out, unsigned long l
     const bool edges = m->plain.edges && m->eflux;
     a.ecells = edges ? m->ecells : nullptr;
     a.eln = edges ? (const T*)m->eln : nullptr;
-    a.eflux = edges ? (V4<T>*)m->eflux : nullptr;
-    a.esrc = edges ? (T*)m->esrc : nullptr;
+    a.eflux = edges ? (V4<T>*)(eflux_out ? eflux_out : m->eflux) : nullptr;
+    a.esrc = edges ? (T*)(esrc_out ? esrc_out : m->esrc) : nullptr;
     a.eidx = edges ? m->eidx : nullptr;
     a.n_edges = edges ? m->n_edges : 0;
-    a.pairs = m->plain.pairs;
     a.grid = m->plain.grid;
     return Launch<T>::step(a, m->plain.block, m->plain.min_blocks, m->plain.stages, m->plain.geo, st);
 }
@@ -415,10 +414,13 @@ cudaError_t launch_raw_t(swe_mesh* m, const void* in, void* out, unsigned long l
 // One step of mesh m from buffer `in` to buffer `out` with the given status
 // block and step index (dt slot rotation), taking dt from *dt_fixed when set.
 cudaError_t launch_step_raw(swe_mesh* m, const void* in, void* out, unsigned long long* small, int64_t step_index,
-                            double cfl, const double* dt_fixed, double* dt_log, cudaStream_t st, bool with_activity) {
+                            double cfl, const double* dt_fixed, double* dt_log, cudaStream_t st, bool with_activity,
+                            void* eflux_out, void* esrc_out) {
     return m->cfg.precision == SWE_FP32
-               ? launch_raw_t<float>(m, in, out, small, step_index, cfl, dt_fixed, dt_log, st, with_activity)
-               : launch_raw_t<double>(m, in, out, small, step_index, cfl, dt_fixed, dt_log, st, with_activity);
+               ? launch_raw_t<float>(m, in, out, small, step_index, cfl, dt_fixed, dt_log, st, with_activity,
+                                     eflux_out, esrc_out)
+               : launch_raw_t<double>(m, in, out, small, step_index, cfl, dt_fixed, dt_log, st, with_activity,
+                                      eflux_out, esrc_out);
 }
 
 double host_edge_rl(double lx, double ly) { return 1.0 / std::sqrt(std::fma(lx, lx, ly * ly)); }
@@ -546,7 +548,6 @@ void swe_config_default(swe_config* cfg) {
     cfg->edge_pass = 0;
     cfg->grid = 0;
     cfg->debug_checks = 0;
-    cfg->cell_pairs = 0;
     cfg->flux = SWE_FLUX_HLLC;
 }
 
@@ -609,14 +610,7 @@ int swe_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* tris, i
         set_error("swe_mesh_create: debug_checks must be 0 or 1");
         return SWE_EINVAL;
     }
-    if (c.cell_pairs != 0 && c.cell_pairs != 1) {
-        set_error("swe_mesh_create: cell_pairs must be 0 or 1");
-        return SWE_EINVAL;
-    }
-    if (c.cell_pairs && (c.precision != SWE_FP32 || c.activity || c.edge_pass)) {
-        set_error("swe_mesh_create: cell_pairs needs an FP32 mesh without activity or edge_pass");
-        return SWE_EINVAL;
-    }
+
     if (c.edge_pass && c.activity) {
         set_error("swe_mesh_create: edge_pass and activity exclude each other");
         return SWE_EINVAL;
@@ -676,13 +670,13 @@ int swe_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* tris, i
         int per_sm = 0, sms = 0;
         e = c.precision == SWE_FP32
                 ? Launch<float>::resident_blocks(c.block_size, c.min_blocks, c.stages, c.geometry_early, c.activity,
-                                                 c.cell_pairs ? 2 : c.edge_pass, &per_sm)
+                                                 c.edge_pass, &per_sm)
                 : Launch<double>::resident_blocks(c.block_size, c.min_blocks, c.stages, c.geometry_early, c.activity,
                                                   c.edge_pass, &per_sm);
         if (e == cudaErrorInvalidValue) {
             swe_mesh_destroy(m);
             set_error("swe_mesh_create: no compiled step kernel for this block_size / min_blocks / stages / "
-                      "geometry_early / activity / edge_pass / cell_pairs");
+                      "geometry_early / activity / edge_pass");
             return SWE_EINVAL;
         }
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device);
@@ -692,8 +686,7 @@ int swe_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* tris, i
         m->grid = (unsigned)std::min(need, c.grid > 0 ? (long long)c.grid : wave);
         // launches without activity bytes: the same shape, or the default one
         // when the configured shape exists only as an activity kernel
-        m->plain = LaunchShape{c.block_size, c.min_blocks, c.stages, c.geometry_early, c.edge_pass, c.cell_pairs,
-                               m->grid};
+        m->plain = LaunchShape{c.block_size, c.min_blocks, c.stages, c.geometry_early, c.edge_pass, m->grid};
         if (c.activity) {
             LaunchShape d;
             d.block = c.precision == SWE_FP32 ? 256 : 128;

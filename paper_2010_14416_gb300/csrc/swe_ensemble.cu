@@ -705,7 +705,6 @@ int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
         out->stages = pick.stages;
         out->geometry_early = pick.geo_early;
         out->activity = pick.activity;
-        out->cell_pairs = 0;
         out->edge_pass = pick.edges;
         out->dynamic = pick.dynamic;
         out->chunk = 1 << pick.chunk_log2;

@@ -1,15 +1,15 @@
-// swe_f32.cuh -- the FP32 arithmetic of one cell update (Eq 12-37), written
-// once for one cell at a time (lanes of type float) and for two cells at a
-// time (float2: Blackwell's paired FP32 multiply, add and fused multiply-add,
-// one instruction for both cells).
+// swe_f32.cuh -- the FP32 arithmetic of one cell update (Eq 12-37).
 //
 // Every product, sum and fused multiply-add is written out with a rounded
 // operation that the compiler may not fuse or reorder (mul, add, sub, fma
-// below), and every decision is a select, so the one-cell and two-cell forms
-// round each cell identically: a kernel that updates two cells per thread
-// gives the same bits as the kernels that update one.  Square roots and
-// reciprocals are the hardware approximations (the FP32 step is compiled with
-// fast-math intrinsics), applied lane by lane.
+// below), so that every FP32 kernel and launch shape that inlines these
+// functions rounds each cell identically: the kernels differ in how they
+// load and schedule cells, and their results agree bit for bit.  (Left to
+// itself, the compiler fuses multiply-adds differently under different
+// register limits.)  Square roots and reciprocals are the hardware
+// approximations (the FP32 step is compiled with fast-math intrinsics).
+// The functions are written on a lane type V (float) with its mask type, and
+// decisions in the Riemann solver are selects.
 //
 // Readings of the garbled equations are those of riemann_hllc and the oracle.
 #pragma once
@@ -20,64 +20,39 @@ namespace swe {
 namespace f32 {
 
 // ---- lanes and masks -----------------------------------------------------------------
-struct M2 {
-    bool x, y;
-};
 __device__ __forceinline__ bool any(bool m) { return m; }
-__device__ __forceinline__ bool any(M2 m) { return m.x || m.y; }
 __device__ __forceinline__ bool all(bool m) { return m; }
-__device__ __forceinline__ bool all(M2 m) { return m.x && m.y; }
 __device__ __forceinline__ bool mand(bool a, bool b) { return a && b; }
-__device__ __forceinline__ M2 mand(M2 a, M2 b) { return {a.x && b.x, a.y && b.y}; }
 __device__ __forceinline__ bool mor(bool a, bool b) { return a || b; }
-__device__ __forceinline__ M2 mor(M2 a, M2 b) { return {a.x || b.x, a.y || b.y}; }
 __device__ __forceinline__ bool mnot(bool a) { return !a; }
-__device__ __forceinline__ M2 mnot(M2 a) { return {!a.x, !a.y}; }
 
 template <typename V> struct Mask;
 template <> struct Mask<float> { using type = bool; };
-template <> struct Mask<float2> { using type = M2; };
 template <typename V> using MaskT = typename Mask<V>::type;
 
 template <typename V> __device__ __forceinline__ V splat(float c);
 template <> __device__ __forceinline__ float splat<float>(float c) { return c; }
-template <> __device__ __forceinline__ float2 splat<float2>(float c) { return make_float2(c, c); }
 
 // ---- rounded operations (never fused, never reordered) ------------------------------
 __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
-__device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float neg(float a) { return -a; }
-__device__ __forceinline__ float2 neg(float2 a) { return make_float2(-a.x, -a.y); }
 // a - b = a + (-b) exactly (IEEE subtraction), signed zeros included
 __device__ __forceinline__ float sub(float a, float b) { return __fadd_rn(a, -b); }
-__device__ __forceinline__ float2 sub(float2 a, float2 b) { return __fadd2_rn(a, neg(b)); }
 __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-__device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-// hardware approximations, lane by lane
+// hardware approximations
 __device__ __forceinline__ float sqrt_(float a) { return sqrtf(a); }
-__device__ __forceinline__ float2 sqrt_(float2 a) { return make_float2(sqrtf(a.x), sqrtf(a.y)); }
 __device__ __forceinline__ float rsqrt_(float a) { return rsqrtf(a); }
-__device__ __forceinline__ float2 rsqrt_(float2 a) { return make_float2(rsqrtf(a.x), rsqrtf(a.y)); }
 __device__ __forceinline__ float div_(float a, float b) { return __fdividef(a, b); }
-__device__ __forceinline__ float2 div_(float2 a, float2 b) { return make_float2(__fdividef(a.x, b.x), __fdividef(a.y, b.y)); }
 __device__ __forceinline__ float rcp_(float a) { return __fdividef(1.0f, a); }
-__device__ __forceinline__ float2 rcp_(float2 a) { return make_float2(__fdividef(1.0f, a.x), __fdividef(1.0f, a.y)); }
 // h^(-7/3) through the hardware base-2 exponential and logarithm
 __device__ __forceinline__ float pow_m73(float h) { return exp2f(-7.0f / 3.0f * __log2f(h)); }
-__device__ __forceinline__ float2 pow_m73(float2 h) { return make_float2(pow_m73(h.x), pow_m73(h.y)); }
 // comparisons (plain IEEE: false with a NaN operand) and selects
 __device__ __forceinline__ bool gt(float a, float b) { return a > b; }
-__device__ __forceinline__ M2 gt(float2 a, float2 b) { return {a.x > b.x, a.y > b.y}; }
 __device__ __forceinline__ bool ge(float a, float b) { return a >= b; }
-__device__ __forceinline__ M2 ge(float2 a, float2 b) { return {a.x >= b.x, a.y >= b.y}; }
 __device__ __forceinline__ bool le(float a, float b) { return a <= b; }
-__device__ __forceinline__ M2 le(float2 a, float2 b) { return {a.x <= b.x, a.y <= b.y}; }
 __device__ __forceinline__ bool lt(float a, float b) { return a < b; }
-__device__ __forceinline__ M2 lt(float2 a, float2 b) { return {a.x < b.x, a.y < b.y}; }
 __device__ __forceinline__ float sel(bool m, float a, float b) { return m ? a : b; }
-__device__ __forceinline__ float2 sel(M2 m, float2 a, float2 b) { return make_float2(m.x ? a.x : b.x, m.y ? a.y : b.y); }
 // max(0, x) as (0 > x ? 0 : x): a NaN passes through
 template <typename V>
 __device__ __forceinline__ V max0(V x) { return sel(gt(splat<V>(0.0f), x), splat<V>(0.0f), x); }

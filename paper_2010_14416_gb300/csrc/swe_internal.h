@@ -55,7 +55,7 @@ void set_error(const std::string& msg);
 
 // A launch shape of the step kernel.
 struct LaunchShape {
-    int block = 0, min_blocks = 0, stages = 0, geo = 0, edges = 0, pairs = 0;
+    int block = 0, min_blocks = 0, stages = 0, geo = 0, edges = 0;
     unsigned grid = 0;
 };
 
@@ -71,9 +71,11 @@ namespace swe {
 // One step of mesh m from state buffer `in` to `out` (see swe_capi.cu).  With
 // with_activity (and the mesh's activity mode on) the step reads and maintains
 // the mesh's activity bytes: only for `in` = the mesh's current state.
+// With the edge pass, eflux_out / esrc_out (when set) receive the step's edge
+// fluxes instead of the mesh's own buffers.
 cudaError_t launch_step_raw(swe_mesh* m, const void* in, void* out, unsigned long long* small, int64_t step_index,
                             double cfl, const double* dt_fixed, double* dt_log, cudaStream_t st,
-                            bool with_activity = false);
+                            bool with_activity = false, void* eflux_out = nullptr, void* esrc_out = nullptr);
 // Allocates (once) and fills the activity bytes of m's current state.
 int init_activity(swe_mesh* m);
 // Builds (once) the interior-edge list of the edge-pass step.

@@ -99,7 +99,6 @@ struct StepArgs {
     BcTable bc;
     int debug;                         // 1: check indices and groups before use (kStatusBadIndex)
     int n_groups;                      // boundary groups in use
-    int pairs;                         // FP32: two cells per thread (step_kernel_x2)
     __device__ __forceinline__ int bc_kind(int grp) const { return bc.kind[grp]; }
     __device__ __forceinline__ double bc_value(int grp) const { return bc.value[grp]; }
     __device__ __forceinline__ long long cell_bound() const { return n; }
@@ -686,9 +685,8 @@ __device__ __forceinline__ T finish_cell(const Args& a, long long i, const V4<T>
 
 // ---- one FP32 cell of the fused step -------------------------------------------------
 // update_cell for FP32: the same loads, quiet test and edge loop, with the
-// arithmetic of swe_f32.cuh on one lane (every operation explicitly rounded,
-// so that the two-cell kernel below, which runs the same functions on float2,
-// gives the same bits).
+// arithmetic of swe_f32.cuh, every operation explicitly rounded, so that every
+// FP32 kernel and launch shape gives the same bits.
 template <bool GEO_EARLY, bool EDGES, typename Args>
 __device__ __forceinline__ float update_cell_f32(const Args& a, long long i, const V4<float>& own, const int4& tp,
                                                  float dt, unsigned& active, unsigned long long* n_clamped,
@@ -798,125 +796,6 @@ __device__ __forceinline__ float update_cell_f32(const Args& a, long long i, con
     if (nonfinite) atomicOr(status, kStatusNonFinite);
     a.s_out[i] = out;
     return cand;
-}
-
-// ---- two FP32 cells of the fused step at once ---------------------------------------------
-// The update of cells iA and iB by one thread: the arithmetic of
-// update_cell_f32 on float2 lanes (x = cell A, y = cell B), so each paired
-// multiply, add or fused multiply-add is one instruction for both cells, and
-// each cell gets the bits update_cell_f32 gives it.  An edge that is interior
-// for one cell and a boundary for the other is evaluated as interior for
-// both (the boundary cell against its own state) and the boundary cell's flux
-// is then replaced by its boundary flux; a quiet cell (dry among dry
-// neighbours) gets (h, 0, 0), as in update_cell_f32.
-template <typename Args>
-__device__ __forceinline__ float update_pair_f32(const Args& a, long long iA, long long iB, const V4<float>& A,
-                                                 const V4<float>& B, const int4& tpA, const int4& tpB, float dt,
-                                                 unsigned& active, unsigned long long* n_clamped, unsigned* status) {
-    const float g = a.g, h_dry = a.h_dry, g2 = f32::mul(0.5f, g);
-    int cA[3] = {tpA.x, tpA.y, tpA.z}, cB[3] = {tpB.x, tpB.y, tpB.z};
-    if (a.debug) {   // an unusable code is flagged and taken as a wall (group 0)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            if (!code_ok(cA[j], a.cell_bound(), a.n_groups)) { atomicOr(status, kStatusBadIndex); cA[j] = -1; }
-            if (!code_ok(cB[j], a.cell_bound(), a.n_groups)) { atomicOr(status, kStatusBadIndex); cB[j] = -1; }
-        }
-    }
-    V4<float> nA[3], nB[3];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        nA[j] = cA[j] >= 0 ? a.s_in[cA[j] & kNbrMask] : A;
-        nB[j] = cB[j] >= 0 ? a.s_in[cB[j] & kNbrMask] : B;
-    }
-    const V4<float> gAa = a.geoA[iA], gBa = a.geoB[iA], gAb = a.geoA[iB], gBb = a.geoB[iB];
-    const float gm2a = load_gm2(a, iA, tpA, 0.0f), gm2b = load_gm2(a, iB, tpB, 0.0f);
-    bool qA = !(A.x > h_dry), qB = !(B.x > h_dry);
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        if (cA[j] >= 0) qA = qA && !(nA[j].x > h_dry);
-        else { const int k = a.bc_kind(-1 - cA[j]); qA = qA && (k == kBcWall || k == kBcTransmissive); }
-        if (cB[j] >= 0) qB = qB && !(nB[j].x > h_dry);
-        else { const int k = a.bc_kind(-1 - cB[j]); qB = qB && (k == kBcWall || k == kBcTransmissive); }
-    }
-    if (qA && qB) {
-        V4<float> o;
-        o.x = A.x; o.y = 0.0f; o.z = 0.0f; o.w = A.w;
-        a.s_out[iA] = o;
-        o.x = B.x; o.w = B.w;
-        a.s_out[iB] = o;
-        return inf_of<float>();
-    }
-    active += (qA ? 0u : 1u) + (qB ? 0u : 1u);
-    const float2 h = make_float2(A.x, B.x), qx = make_float2(A.y, B.y), qy = make_float2(A.z, B.z);
-    const float2 z = make_float2(A.w, B.w);
-    const float2 G = f32::splat<float2>(g), G2 = f32::splat<float2>(g2), HD = f32::splat<float2>(h_dry);
-    float2 u, v;
-    f32::velocity(h, qx, qy, HD, u, v);
-    const float2 zero = f32::splat<float2>(0.0f);
-    float2 f0 = zero, f1 = zero, f2 = zero, sx = zero, sy = zero;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        const float2 lx = j == 0 ? make_float2(gAa.x, gAb.x) : (j == 1 ? make_float2(gAa.z, gAb.z) : make_float2(gBa.x, gBb.x));
-        const float2 ly = j == 0 ? make_float2(gAa.y, gAb.y) : (j == 1 ? make_float2(gAa.w, gAb.w) : make_float2(gBa.y, gBb.y));
-        const float2 l2 = f32::fma(lx, lx, f32::mul(ly, ly));
-        const float2 rl = f32::rsqrt_(l2);
-        const float2 len = f32::mul(l2, rl);
-        const float2 n1 = f32::mul(lx, rl), n2 = f32::mul(ly, rl);
-        const int ca = cA[j], cb = cB[j];
-        const bool ia = ca >= 0, ib = cb >= 0;
-        float2 F0 = zero, F1 = zero, F2 = zero;
-        if (ia || ib) {
-            const V4<float> oa = j == 0 ? nA[0] : (j == 1 ? nA[1] : nA[2]);
-            const V4<float> ob = j == 0 ? nB[0] : (j == 1 ? nB[1] : nB[2]);
-            const f32::M2 flip{ia && (ca & kFlipBit) != 0, ib && (cb & kFlipBit) != 0};
-            float2 src;
-            f32::edge_interior<float2>(h, u, v, z, make_float2(oa.x, ob.x), make_float2(oa.y, ob.y),
-                                       make_float2(oa.z, ob.z), make_float2(oa.w, ob.w), n1, n2, flip, G, G2, HD, F0,
-                                       F1, F2, src, a.hll != 0);
-            const f32::M2 in{ia, ib};
-            sx = f32::sel(in, f32::fma(src, lx, sx), sx);
-            sy = f32::sel(in, f32::fma(src, ly, sy), sy);
-        }
-        if (!ia) {
-            const int grp = -1 - ca;
-            f32::edge_boundary(a.bc_kind(grp), a.bc_value(grp), A.x, u.x, v.x, A.w, n1.x, n2.x, g, g2, h_dry, F0.x,
-                               F1.x, F2.x, a.hll != 0);
-        }
-        if (!ib) {
-            const int grp = -1 - cb;
-            f32::edge_boundary(a.bc_kind(grp), a.bc_value(grp), B.x, u.y, v.y, B.w, n1.y, n2.y, g, g2, h_dry, F0.y,
-                               F1.y, F2.y, a.hll != 0);
-        }
-        f0 = f32::fma(len, F0, f0);
-        f1 = f32::fma(len, F1, f1);
-        f2 = f32::fma(len, F2, f2);
-    }
-    float2 oh, ou, ov;
-    f32::M2 clamped, nonfinite;
-    const float2 cand = f32::finish<float2>(h, f32::rcp_(h), qx, qy, f0, f1, f2, sx, sy, make_float2(gBa.z, gBb.z),
-                                            make_float2(gBa.w, gBb.w), make_float2(gm2a, gm2b),
-                                            f32::splat<float2>(dt), G, HD, oh, ou, ov, clamped, nonfinite);
-    V4<float> o;
-    if (qA) {
-        o.x = A.x; o.y = 0.0f; o.z = 0.0f;
-    } else {
-        o.x = oh.x; o.y = ou.x; o.z = ov.x;
-        if (clamped.x) atomicAdd(n_clamped, 1ULL);
-        if (nonfinite.x) atomicOr(status, kStatusNonFinite);
-    }
-    o.w = A.w;
-    a.s_out[iA] = o;
-    if (qB) {
-        o.x = B.x; o.y = 0.0f; o.z = 0.0f;
-    } else {
-        o.x = oh.y; o.y = ou.y; o.z = ov.y;
-        if (clamped.y) atomicAdd(n_clamped, 1ULL);
-        if (nonfinite.y) atomicOr(status, kStatusNonFinite);
-    }
-    o.w = B.w;
-    a.s_out[iB] = o;
-    const float inf = inf_of<float>();
-    return min_nonneg(qA ? inf : cand.x, qB ? inf : cand.y);
 }
 
 // ---- one cell of the fused step -----------------------------------------------------
@@ -1111,48 +990,6 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_kernel(const StepArgs<T> a) 
             slot = slot == STAGES - 1 ? 0 : slot + 1;
         }
         cp_async_wait<0>();
-    }
-    block_min_publish<BLOCK>(cand, a.dt_write, active, a.n_active);
-}
-
-// ---- the fused FP32 step, two cells per thread ------------------------------------------
-// One warp per 64 consecutive cells (grid-stride over such tiles): lane l
-// updates cells 64 t + l and 64 t + 32 + l together (update_pair_f32), so every
-// load is coalesced and every paired FP32 instruction serves two cells; a
-// ragged last tile's unpaired cells take update_cell_f32.  The same bits as
-// step_kernel.
-template <int BLOCK, int MINB>
-__global__ void __launch_bounds__(BLOCK, MINB) step_kernel_x2(const StepArgs<float> a) {
-    static_assert(BLOCK % 32 == 0, "whole warps");
-    constexpr int W = BLOCK / 32;
-    const WarpDt<float> wdt = warp_step_dt<float>(a.cfl, a.dt_read, a.dt_fixed);
-    const double dt_d = wdt.d;
-    const bool have_dt = wdt.have;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        *a.dt_reset = kInfBits;
-        if (have_dt) *a.t += dt_d;
-        else atomicOr(a.status, kStatusDry);
-        if (a.dt_log) *a.dt_log = dt_d;
-    }
-    float cand = inf_of<float>();
-    unsigned active = 0u;
-    if (!have_dt) {
-        for (long long i = (long long)blockIdx.x * BLOCK + threadIdx.x; i < a.n; i += (long long)gridDim.x * BLOCK)
-            a.s_out[i] = a.s_in[i];
-    } else {
-        const float dt = wdt.t;
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        const long long n_tiles = (a.n + 63) / 64;
-        const long long stride = (long long)gridDim.x * W;
-        for (long long t = (long long)blockIdx.x * W + warp; t < n_tiles; t += stride) {
-            const long long iA = t * 64 + lane, iB = iA + 32;
-            if (iB < a.n)
-                cand = min_nonneg(cand, update_pair_f32(a, iA, iB, a.s_in[iA], a.s_in[iB], a.topo[iA], a.topo[iB], dt,
-                                                        active, a.n_clamped, a.status));
-            else if (iA < a.n)
-                cand = min_nonneg(cand, update_cell_f32<true, false>(a, iA, a.s_in[iA], a.topo[iA], dt, active,
-                                                                     a.n_clamped, a.status));
-        }
     }
     block_min_publish<BLOCK>(cand, a.dt_write, active, a.n_active);
 }
@@ -1741,9 +1578,6 @@ struct Launch {
                                        int edges, int* per_sm);
     // compiled (block, min_blocks, stages, geo_early) shapes of the cell pass of the edge-pass step
     static int edge_variants(int (*out)[4], int max);
-    // compiled (block, min_blocks) shapes of the two-cells-per-thread step (FP32; a.pairs set;
-    // resident_blocks with edges = 2)
-    static int pair_variants(int (*out)[2], int max);
     // the edge pass alone (interior fluxes of a.s_in into a.eflux, a.esrc)
     static cudaError_t edge_flux(const StepArgs<T>& a, cudaStream_t st);
     // compiled (block, min_blocks, geo_early, stages = prefetch distance + 1) shapes of the activity kernel

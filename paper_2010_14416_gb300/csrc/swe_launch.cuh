@@ -31,10 +31,6 @@ static inline unsigned grid_for(long long n, int block) {
 #define SWE_EDGE_VARIANTS_F64(X) X(128, 1, 1, 0) X(256, 1, 1, 0)
 constexpr int kEdgeBlock = 256;
 
-// (block, min blocks per SM) shapes of the two-cells-per-thread FP32 step
-// (about 126 registers at 128 x 4: no local-memory spills below 5 blocks)
-#define SWE_PAIR_VARIANTS_F32(X) X(128, 4) X(256, 2) X(128, 3) X(128, 5)
-
 // (block, min blocks per SM, geometry early, stages) shapes of the activity
 // kernel; stages = the state's prefetch distance + 1.  Shared memory per
 // thread: `stages` state records and activity bytes, 2 topology records.
@@ -67,18 +63,6 @@ cudaError_t Launch<T>::step(const StepArgs<T>& a, int block, int min_blocks, int
         }
 #undef SWE_LAUNCH_ACT
         return cudaErrorInvalidValue;
-    }
-    if constexpr (sizeof(T) == 4) {
-        if (a.pairs) {
-#define SWE_LAUNCH_PAIR(B, M) \
-    if (block == B && min_blocks == M) {                                          \
-        step_kernel_x2<B, M><<<grid, B, 0, st>>>(a);                              \
-        return cudaGetLastError();                                                \
-    }
-            SWE_PAIR_VARIANTS_F32(SWE_LAUNCH_PAIR)
-#undef SWE_LAUNCH_PAIR
-            return cudaErrorInvalidValue;
-        }
     }
     if (a.eflux) {
         cudaError_t e = edge_flux(a, st);
@@ -113,16 +97,6 @@ cudaError_t Launch<T>::step(const StepArgs<T>& a, int block, int min_blocks, int
 template <typename T>
 cudaError_t Launch<T>::resident_blocks(int block, int min_blocks, int stages, int geo_early, int activity,
                                        int edges, int* per_sm) {
-    if (edges == 2) {   // the two-cells-per-thread step
-        if constexpr (sizeof(T) == 4) {
-#define SWE_OCC_PAIR(B, M) \
-    if (block == B && min_blocks == M && !activity)                               \
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, step_kernel_x2<B, M>, B, 0);
-            SWE_PAIR_VARIANTS_F32(SWE_OCC_PAIR)
-#undef SWE_OCC_PAIR
-        }
-        return cudaErrorInvalidValue;
-    }
     if (edges) {
 #define SWE_OCC_EDGE(B, M, S, G) \
     if (block == B && min_blocks == M && stages == S && geo_early == G)          \
@@ -195,19 +169,6 @@ int Launch<T>::edge_variants(int (*out)[4], int max) {
         SWE_EDGE_VARIANTS_F64(SWE_LIST)
     }
 #undef SWE_LIST
-    return k;
-}
-
-template <typename T>
-int Launch<T>::pair_variants(int (*out)[2], int max) {
-    int k = 0;
-    if constexpr (sizeof(T) == 4) {
-#define SWE_LIST(B, M) \
-    if (k < max) { out[k][0] = B; out[k][1] = M; } \
-    ++k;
-        SWE_PAIR_VARIANTS_F32(SWE_LIST)
-#undef SWE_LIST
-    }
     return k;
 }
 

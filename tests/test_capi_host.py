@@ -126,8 +126,7 @@ def test_malformed_meshes_rejected_by_host_preprocessing():
 @pytest.mark.parametrize("kw", [dict(g=0.0), dict(g=float("inf")), dict(h_dry=-1e-6), dict(h_dry=float("nan")),
                                 dict(h_dry=float("inf")), dict(h_dry=1e-40), dict(precision=7), dict(flux=5), dict(geometry_early=2),
                                 dict(activity=3), dict(edge_pass=2), dict(edge_pass=-1), dict(grid=-1), dict(debug_checks=2),
-                                dict(activity=1, edge_pass=1), dict(cell_pairs=2), dict(cell_pairs=1),
-                                dict(cell_pairs=1, precision=1, activity=1), dict(cell_pairs=1, precision=1, edge_pass=1),
+                                dict(activity=1, edge_pass=1),
                                 dict(block_size=96)])
 def test_invalid_configs_rejected_before_any_device_work(kw):
     # swe_mesh_create validates its configuration before it touches the

@@ -346,31 +346,6 @@ def test_debug_checks_change_nothing_on_valid_meshes(precision):
         assert all(np.array_equal(x, y) for x, y in zip(ref, got)), kw
 
 
-@pytest.mark.parametrize("maker", ["river", "dry_canal", "dam", "transmissive"])
-def test_cell_pairs_are_bitwise_neutral(maker):
-    # two cells per thread on paired FP32 instructions: the same states, times,
-    # active and clamp counts as one cell per thread, through wet/dry fronts,
-    # every boundary kind, and cell counts that leave a ragged last tile
-    if maker == "river":
-        mi = mg.river(101, 21, seed=8)
-    elif maker == "dry_canal":
-        mi = mg.canal(401, 20, Lx=200.0, Ly=10.0, hR=0.0, seed=3, manning=0.03)
-    elif maker == "dam":
-        mi = mg.dam_break_4k()
-    else:
-        mi = mg.canal(51, 7, 51.0, 7.0, 0.2, 6, side_bc=mg.BC_TRANSMISSIVE, hL=3.0, hR=1.0, manning=0.05)
-    assert mi.n_cells % 64 != 0
-    ref, tref, iref = _gpu_run(mi, 301, precision=capi.SWE_FP32)
-    for kw in (dict(block_size=128, min_blocks=4), dict(block_size=256, min_blocks=2, graph_steps=-1),
-               dict(block_size=128, min_blocks=3, grid=3), dict(block_size=128, min_blocks=5, grid=100000),
-               dict(block_size=128, min_blocks=4, debug_checks=1)):
-        got, t, info = _gpu_run(mi, 301, precision=capi.SWE_FP32, cell_pairs=1, **kw)
-        assert t == tref, kw
-        assert all(np.array_equal(x, y) for x, y in zip(ref, got)), kw
-        assert info["n_active"] == iref["n_active"] and info["n_clamped"] == iref["n_clamped"], kw
-        assert info["status"] == 0, kw
-
-
 def test_edge_pass_and_activity_exclude_each_other():
     mi = mg.dam_break_4k()
     with pytest.raises(capi.SWEError):
