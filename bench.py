@@ -693,7 +693,7 @@ def _shape_key(t):
 def _kernel_hash():
     import hashlib
     hsh = hashlib.sha1()
-    for f in ("swe_kernels.cuh", "swe_launch.cuh"):
+    for f in ("swe_kernels.cuh", "swe_launch.cuh", "swe_f32.cuh"):
         with open(os.path.join(ROOT, "paper_2010_14416_gb300", "csrc", f), "rb") as fh:
             hsh.update(fh.read())
     return hsh.hexdigest()[:12]

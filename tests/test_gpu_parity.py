@@ -484,6 +484,50 @@ def test_full_size_dry_canal_1m_fp64_against_oracle():
     assert all(np.array_equal(x, y) for x, y in ((eh, gh), (ehu, ghu), (ehv, ghv)))
 
 
+def _oracle_to_time(mi, T):
+    """The oracle's state at time T (CFL 0.9 steps, the last one shortened)."""
+    M = _orc_mesh(mi)
+    h, hu, hv, t = mi.h.copy(), mi.hu.copy(), mi.hv.copy(), 0.0
+    while t < T:
+        dt = min(M.dt(h, hu, hv, 0.9), T - t)
+        h, hu, hv, _ = M.step(h, hu, hv, dt)
+        t += dt
+    return h
+
+
+def _cell_areas(mi):
+    p = mi.nodes[mi.tris]
+    return 0.5 * np.abs((p[:, 1, 0] - p[:, 0, 0]) * (p[:, 2, 1] - p[:, 0, 1]) -
+                        (p[:, 2, 0] - p[:, 0, 0]) * (p[:, 1, 1] - p[:, 0, 1]))
+
+
+def test_full_size_ritter_dam_break_against_exact_solution():
+    # the 1M dry-bed canal's frictionless twin (Ritter, Section 6.3), 2000 FP64
+    # steps on the GPU: the L1 depth error against the exact solution at the
+    # run's time is below the oracle's own error on the 800 x 40 canal of the
+    # convergence pin at that time (the scheme converges at first order, so
+    # the 2.5x finer mesh must do better), and the front lies behind 2 c0 t
+    from oracle import analytic
+    mi = mg.dam_break_dry_1m(manning=0.0)
+    (gh, _, _), t, info = _gpu_run(mi, 2000)
+    assert info["status"] == 0
+    area = _cell_areas(mi)
+    cx = mi.centroids()[:, 0]
+    he, _ = analytic.dam_break(cx, t, 10.0, 0.0, 100.0)
+    err = float(np.sum(np.abs(gh - he) * area) / area.sum())
+    coarse = mg.canal(800, 40, 200.0, 10.0, 0.2, 1, 10.0, 0.0, 100.0, 0.0)
+    oh = _oracle_to_time(coarse, t)
+    ca, ccx = _cell_areas(coarse), coarse.centroids()[:, 0]
+    hc, _ = analytic.dam_break(ccx, t, 10.0, 0.0, 100.0)
+    err_coarse = float(np.sum(np.abs(oh - hc) * ca) / ca.sum())
+    print(f"Ritter at t = {t:.3f} s: L1 depth error {err:.4e} (1M cells, GPU) against {err_coarse:.4e} "
+          f"(64k cells, oracle)")
+    assert err < err_coarse, (err, err_coarse)
+    c0 = math.sqrt(9.81 * 10.0)
+    front = cx[gh > 1e-3].max() - 100.0
+    assert 0.8 * 2 * c0 * t < front <= 2 * c0 * t + 0.2, (front, 2 * c0 * t)
+
+
 def test_full_size_wet_river_1m_fp64_against_oracle():
     # the 1,001,728-cell fully wet river of the adjoint workload, 1000 FP64 steps
     mi = mg.river_adjoint_1m()
