@@ -329,7 +329,7 @@ cudaError_t Launch<T>::ensemble_resident_blocks(int block, int min_blocks, int s
 }
 
 // (block, min blocks per SM, geometry early) shapes of the ensemble's activity kernel
-#define SWE_ENS_ACT_VARIANTS_F32(X) X(128, 8, 1) X(128, 8, 0) X(256, 4, 1) X(256, 4, 0)
+#define SWE_ENS_ACT_VARIANTS_F32(X) X(128, 8, 1) X(128, 8, 0) X(256, 4, 1) X(256, 4, 0) X(128, 7, 1)
 #define SWE_ENS_ACT_VARIANTS_F64(X) X(256, 1, 0) X(128, 1, 0)
 
 template <typename T>
@@ -385,7 +385,7 @@ int Launch<T>::ensemble_act_variants(int (*out)[3], int max) {
 }
 
 // (block, min blocks per SM, geometry early) shapes of the dynamically scheduled ensemble kernel
-#define SWE_ENS_DYN_VARIANTS_F32(X) X(128, 8, 0) X(128, 8, 1) X(256, 4, 0)
+#define SWE_ENS_DYN_VARIANTS_F32(X) X(128, 8, 0) X(128, 8, 1) X(256, 4, 0) X(128, 7, 1) X(128, 6, 1)
 #define SWE_ENS_DYN_VARIANTS_F64(X) X(128, 1, 0) X(256, 1, 0)
 
 template <typename T>
