@@ -400,7 +400,8 @@ def measure_mesh(ctx, name, steps, warmup, shape_spec=None, e2e=True):
     if fixed:
         shape = dict(block_size=fixed["block_size"], min_blocks=fixed["min_blocks"], stages=fixed["stages"],
                      geometry_early=fixed["geometry_early"], activity=fixed["activity"],
-                     edge_pass=fixed["edge_pass"], grid=fixed["grid"], chunk=0, fixed=True)
+                     edge_pass=fixed["edge_pass"], grid=fixed["grid"], cell_pairs=fixed.get("cell_pairs", 0),
+                     chunk=0, fixed=True)
     else:
         shape = m.autotune(8)   # on the initial state, which the trials leave untouched
     warm = _warmup_for(steps, warmup)
@@ -437,7 +438,7 @@ def measure_mesh(ctx, name, steps, warmup, shape_spec=None, e2e=True):
     out = [torch.empty(n, dtype=tdt).pin_memory() for _ in range(3)]
     # a mesh with the timed run's launch shape (tuned once above, as a user
     # would tune once and create later meshes with the chosen shape)
-    keys = ("block_size", "min_blocks", "stages", "geometry_early", "activity", "edge_pass", "grid")
+    keys = ("block_size", "min_blocks", "stages", "geometry_early", "activity", "edge_pass", "grid", "cell_pairs")
     m2 = capi.Mesh(mi.nodes, mi.tris, mi.z, mi.manning, precision=prec, device=ctx.local,
                    **{k: int(shape[k]) for k in keys})
     for pairs, kind, value in mi.bcs:
@@ -676,18 +677,20 @@ def _shape_kwargs(spec):
     if not spec:
         return {}
     v = [int(x) for x in spec.split(",")]
-    if len(v) != 7:
-        raise SystemExit("--shape needs block,min_blocks,stages,geometry_early,activity,edge_pass,grid")
-    keys = ("block_size", "min_blocks", "stages", "geometry_early", "activity", "edge_pass", "grid")
+    if len(v) not in (7, 8):
+        raise SystemExit("--shape needs block,min_blocks,stages,geometry_early,activity,edge_pass,grid[,cell_pairs]")
+    keys = ("block_size", "min_blocks", "stages", "geometry_early", "activity", "edge_pass", "grid", "cell_pairs")
     return dict(zip(keys, v))
 
 
 def _shape_key(t):
-    """(block, min_blocks, stages, geometry_early, activity, edge_pass, grid[, chunk, dynamic]) of an autotuner
-    choice."""
+    """(block, min_blocks, stages, geometry_early, activity, edge_pass, grid[, chunk, dynamic | , 1 for the
+    cell-pair kernel]) of an autotuner choice."""
     k = [t["block_size"], t["min_blocks"], t["stages"], t["geometry_early"], t["activity"], t["edge_pass"],
          t["grid"]]
-    return k + [t["chunk"], t.get("dynamic", 0)] if t.get("chunk") else k
+    if t.get("chunk"):
+        return k + [t["chunk"], t.get("dynamic", 0)]
+    return k + [1] if t.get("cell_pairs") else k
 
 
 def _kernel_hash():

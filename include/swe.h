@@ -85,7 +85,10 @@ typedef struct swe_config {
     double h_dry;     /* wet/dry threshold, default 1e-6 m; finite and >= FLT_MIN (1.18e-38): a wet
                          depth is then a normal float, which the FP32 kernels and the FP64 friction
                          term's h^(-1/3) iteration (started from the float cube root) need */
-    int reorder;      /* SWE_REORDER_*, default SWE_REORDER_HILBERT */
+    int reorder;      /* SWE_REORDER_*, default SWE_REORDER_HILBERT.  With RCM or HILBERT the
+                         cells of the order are then arranged in pairs (2p, 2p+1) that share
+                         an edge, made the local edge 0 of both, wherever a greedy matching
+                         along the order finds one (cell_pairs uses them) */
     int block_size;   /* threads per block of the step kernel; 0 = library default */
     int graph_steps;  /* steps captured per CUDA graph; 0 = default, < 0 = no graphs */
     int device;       /* CUDA device ordinal, default 0 */
@@ -133,6 +136,13 @@ typedef struct swe_config {
                          for a memory checker on the library's own index tables; it costs one
                          branch per cell when off.  0 (default): no checks.  Results of a valid
                          mesh do not depend on it */
+    int cell_pairs;   /* FP32 only, not with activity or edge_pass.  1: each thread of the step
+                         kernel updates the cell pair (2p, 2p+1); when the two share their local
+                         edge 0, its flux is evaluated once for both (five Riemann problems per
+                         pair instead of six).  stages must then be 0 or 1 (records read
+                         directly).  Compiled (block_size, min_blocks, geometry_early): (256, 4,
+                         0|1), (128, 8, 0|1), (256, 3, 1).  0 (default): one cell per thread.
+                         Results do not depend on it */
 } swe_config;
 
 /* Fills *cfg with the defaults listed above. */
@@ -473,6 +483,7 @@ typedef struct swe_tune {
     double ms_before;        /* measured time per step of the shape in use before the call (ms;
                                 from the runoff, which always includes it, when one ran) */
     int n_candidates;        /* shapes timed */
+    int cell_pairs;          /* chosen pair mode (swe_config.cell_pairs); 0 for an ensemble */
 } swe_tune;
 
 /*

@@ -44,7 +44,7 @@ class swe_config(C.Structure):
                 ("reorder", C.c_int), ("block_size", C.c_int), ("graph_steps", C.c_int),
                 ("device", C.c_int), ("min_blocks", C.c_int), ("stages", C.c_int), ("flux", C.c_int),
                 ("geometry_early", C.c_int), ("activity", C.c_int), ("edge_pass", C.c_int), ("grid", C.c_int),
-                ("debug_checks", C.c_int)]
+                ("debug_checks", C.c_int), ("cell_pairs", C.c_int)]
 
 
 class swe_info(C.Structure):
@@ -63,7 +63,7 @@ class swe_tune(C.Structure):
     _fields_ = [("block_size", C.c_int), ("min_blocks", C.c_int), ("stages", C.c_int), ("geometry_early", C.c_int),
                 ("activity", C.c_int), ("edge_pass", C.c_int), ("dynamic", C.c_int), ("chunk", C.c_int),
                 ("grid", C.c_int64), ("cells_per_thread", C.c_double), ("ms_best", C.c_double),
-                ("ms_before", C.c_double), ("n_candidates", C.c_int)]
+                ("ms_before", C.c_double), ("n_candidates", C.c_int), ("cell_pairs", C.c_int)]
 
 
 class SWEError(RuntimeError):
@@ -169,7 +169,8 @@ class Mesh:
 
     def __init__(self, nodes, tris, bathy, manning, precision=SWE_FP64, reorder=None,
                  block_size=0, graph_steps=0, device=0, g=9.81, h_dry=1e-6, min_blocks=0, stages=0,
-                 flux=SWE_FLUX_HLLC, geometry_early=0, activity=0, edge_pass=0, grid=0, debug_checks=0):
+                 flux=SWE_FLUX_HLLC, geometry_early=0, activity=0, edge_pass=0, grid=0, debug_checks=0,
+                 cell_pairs=0):
         lib = load()
         cfg = config_default()
         cfg.precision = precision
@@ -183,6 +184,7 @@ class Mesh:
         cfg.edge_pass = edge_pass
         cfg.grid = grid
         cfg.debug_checks = debug_checks
+        cfg.cell_pairs = cell_pairs
         cfg.flux = flux
         cfg.g, cfg.h_dry = g, h_dry
         nodes = np.ascontiguousarray(nodes, dtype=np.float64).reshape(-1, 2)

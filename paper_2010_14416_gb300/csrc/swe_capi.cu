@@ -225,6 +225,9 @@ StepArgs<T> make_args(swe_mesh* m, int64_t step_index, double cfl) {
 
 template <typename T>
 cudaError_t launch_one(swe_mesh* m, int64_t step_index, double cfl, cudaStream_t st) {
+    if (m->cfg.cell_pairs)
+        return Launch<T>::step_pair(make_args<T>(m, step_index, cfl), m->cfg.block_size, m->cfg.min_blocks,
+                                    m->cfg.geometry_early, m->cfg.stages, st);
     return Launch<T>::step(make_args<T>(m, step_index, cfl), m->cfg.block_size, m->cfg.min_blocks,
                            m->cfg.stages, m->cfg.geometry_early, st);
 }
@@ -408,6 +411,8 @@ cudaError_t launch_raw_t(swe_mesh* m, const void* in, void* out, unsigned long l
     a.eidx = edges ? m->eidx : nullptr;
     a.n_edges = edges ? m->n_edges : 0;
     a.grid = m->plain.grid;
+    if (m->plain.pairs)
+        return Launch<T>::step_pair(a, m->plain.block, m->plain.min_blocks, m->plain.geo, m->plain.stages, st);
     return Launch<T>::step(a, m->plain.block, m->plain.min_blocks, m->plain.stages, m->plain.geo, st);
 }
 
@@ -548,6 +553,7 @@ void swe_config_default(swe_config* cfg) {
     cfg->edge_pass = 0;
     cfg->grid = 0;
     cfg->debug_checks = 0;
+    cfg->cell_pairs = 0;
     cfg->flux = SWE_FLUX_HLLC;
 }
 
@@ -611,6 +617,14 @@ int swe_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* tris, i
         return SWE_EINVAL;
     }
 
+    if (c.cell_pairs != 0 && c.cell_pairs != 1) {
+        set_error("swe_mesh_create: cell_pairs must be 0 or 1");
+        return SWE_EINVAL;
+    }
+    if (c.cell_pairs && (c.precision != SWE_FP32 || c.activity || c.edge_pass)) {
+        set_error("swe_mesh_create: cell_pairs needs FP32, without activity or edge_pass");
+        return SWE_EINVAL;
+    }
     if (c.edge_pass && c.activity) {
         set_error("swe_mesh_create: edge_pass and activity exclude each other");
         return SWE_EINVAL;
@@ -623,7 +637,7 @@ int swe_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* tris, i
     if (c.min_blocks == 0)
         c.min_blocks = c.precision == SWE_FP32 ? Launch<float>::default_min_blocks(c.block_size)
                                                : Launch<double>::default_min_blocks(c.block_size);
-    if (c.stages == 0) c.stages = (c.precision == SWE_FP32 || c.activity) ? 3 : 1;
+    if (c.stages == 0) c.stages = (c.precision == SWE_FP32 || c.activity) && !c.cell_pairs ? 3 : 1;
     if (c.graph_steps == 0) c.graph_steps = kDefaultGraphSteps;
     if (c.graph_steps > 0) c.graph_steps = std::max(6, (c.graph_steps / 6) * 6);
     if (c.activity && n_tris >= kActivityMaxCells) {
@@ -668,7 +682,9 @@ int swe_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* tris, i
     }
     {
         int per_sm = 0, sms = 0;
-        e = c.precision == SWE_FP32
+        e = c.cell_pairs ? Launch<float>::pair_resident_blocks(c.block_size, c.min_blocks, c.geometry_early, c.stages,
+                                                               &per_sm)
+            : c.precision == SWE_FP32
                 ? Launch<float>::resident_blocks(c.block_size, c.min_blocks, c.stages, c.geometry_early, c.activity,
                                                  c.edge_pass, &per_sm)
                 : Launch<double>::resident_blocks(c.block_size, c.min_blocks, c.stages, c.geometry_early, c.activity,
@@ -676,17 +692,19 @@ int swe_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* tris, i
         if (e == cudaErrorInvalidValue) {
             swe_mesh_destroy(m);
             set_error("swe_mesh_create: no compiled step kernel for this block_size / min_blocks / stages / "
-                      "geometry_early / activity / edge_pass");
+                      "geometry_early / activity / edge_pass / cell_pairs");
             return SWE_EINVAL;
         }
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device);
         if (e != cudaSuccess) { swe_mesh_destroy(m); return cuda_fail(e, "swe_mesh_create: occupancy"); }
-        const long long need = (n + c.block_size - 1) / c.block_size;
+        const long long units = c.cell_pairs ? (n + 1) / 2 : n;   // a thread's work item: a cell or a pair
+        const long long need = (units + c.block_size - 1) / c.block_size;
         const long long wave = (long long)std::max(per_sm, 1) * std::max(sms, 1);
         m->grid = (unsigned)std::min(need, c.grid > 0 ? (long long)c.grid : wave);
         // launches without activity bytes: the same shape, or the default one
         // when the configured shape exists only as an activity kernel
-        m->plain = LaunchShape{c.block_size, c.min_blocks, c.stages, c.geometry_early, c.edge_pass, m->grid};
+        m->plain = LaunchShape{c.block_size, c.min_blocks, c.stages, c.geometry_early, c.edge_pass, m->grid,
+                               c.cell_pairs};
         if (c.activity) {
             LaunchShape d;
             d.block = c.precision == SWE_FP32 ? 256 : 128;

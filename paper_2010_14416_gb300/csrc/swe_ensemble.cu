@@ -713,6 +713,7 @@ int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
         out->ms_best = ms_pick;
         out->ms_before = ms[0];
         out->n_candidates = (int)(cand.size() + cand2.size());
+        out->cell_pairs = 0;
     }
     return SWE_OK;
 }

@@ -53,11 +53,16 @@ __device__ __forceinline__ bool ge(float a, float b) { return a >= b; }
 __device__ __forceinline__ bool le(float a, float b) { return a <= b; }
 __device__ __forceinline__ bool lt(float a, float b) { return a < b; }
 __device__ __forceinline__ float sel(bool m, float a, float b) { return m ? a : b; }
-// max(0, x) as (0 > x ? 0 : x): a NaN passes through
+// max(0, x), min and max on the min/max unit (one instruction each): a NaN
+// operand gives the other operand (IEEE maxNum/minNum).  A NaN depth or
+// momentum still reaches its own cell's new state, which the non-finite
+// check reads, since the cell's update adds to its own h and q.
 template <typename V>
-__device__ __forceinline__ V max0(V x) { return sel(gt(splat<V>(0.0f), x), splat<V>(0.0f), x); }
+__device__ __forceinline__ V max0(V x) { return fmaxf(x, splat<V>(0.0f)); }
 template <typename V>
-__device__ __forceinline__ V vmin(V a, V b) { return sel(lt(a, b), a, b); }
+__device__ __forceinline__ V vmin(V a, V b) { return fminf(a, b); }
+template <typename V>
+__device__ __forceinline__ V vmax(V a, V b) { return fmaxf(a, b); }
 
 // Wave speeds of two wet sides (Eq 19-25): the star depth by Eq 22 or Eq 23 as
 // Eq 21's h0 decides, the shock factors of Eq 20 and S*.
@@ -88,60 +93,51 @@ __device__ __forceinline__ void wet_speeds(V hL, V unL, V hR, V unR, V aL, V aR,
 // (ut_L when S* >= 0); Eq 26 line 2 is the right-dry case; both dry gives no
 // flux.  Lanes of one warp take different sides of the star-depth choice
 // (Eq 22 or Eq 23, by the sign of h0 - min(h_L, h_R)) in most flows, so both
-// estimates, both shock factors (Eq 20), the three wet/dry speed cases and
-// the star-region HLL flux (Eq 18) are formed and the decisions are selects;
-// a value formed on a rejected side may be infinite or NaN and is never
-// passed on.  Eq 23's g_K = sqrt(g (h0 + h_K)/(2 h0 h_K)) is formed as
+// estimates, both shock factors (Eq 20) and the star-region HLL flux (Eq 18)
+// are formed and the decisions are selects; a value formed on a rejected
+// side may be infinite or NaN and is never passed on.  Both sides wet is the
+// one branch; the one-dry speed cases (Eq 26) are selects within the other.  Eq 23's g_K = sqrt(g (h0 + h_K)/(2 h0 h_K)) is formed as
 // sqrt(g/2 (1/h0 + 1/h_K)), and 1/h_K is shared with Eq 20.  With hll_only the
 // third component is the HLL flux of U_3 = h ut (Eq 18 applied to it).
 template <typename V>
 __device__ __forceinline__ void riemann(V hL, V unL, V utL, V hR, V unR, V utR, V g, V g2, V h_dry, V& G1, V& G2,
                                         V& G3, V* speeds, bool hll_only) {
-    using M = MaskT<V>;
     const V zero = splat<V>(0.0f);
-    const M wetL = gt(hL, h_dry), wetR = gt(hR, h_dry);
-    const M wet_any = mor(wetL, wetR);
-    if (!any(wet_any)) {
-        G1 = zero; G2 = zero; G3 = zero;
-        if (speeds) { speeds[0] = zero; speeds[1] = zero; speeds[2] = zero; }
-        return;
-    }
+    const bool wetL = gt(hL, h_dry), wetR = gt(hR, h_dry);
     const V aL = sqrt_(mul(g, hL)), aR = sqrt_(mul(g, hR));
-    const M both = mand(wetL, wetR);
     V SL, SR, Ss;
-    if (all(both)) {
+    if (wetL && wetR) {
         wet_speeds(hL, unL, hR, unR, aL, aR, g, g2, SL, SR, Ss);
     } else {
-        V SLw = zero, SRw = zero, Ssw = zero;
-        if (any(both)) wet_speeds(hL, unL, hR, unR, aL, aR, g, g2, SLw, SRw, Ssw);
+        if (!wetL && !wetR) {                                                 // both dry: no flux
+            G1 = zero; G2 = zero; G3 = zero;
+            if (speeds) { speeds[0] = zero; speeds[1] = zero; speeds[2] = zero; }
+            return;
+        }
         // one side dry (Eq 26)
         const V SLl = fma(splat<V>(-2.0f), aR, unR), SRl = add(unR, aR);     // left dry
         const V SLr = sub(unL, aL), SRr = fma(splat<V>(2.0f), aL, unL);      // right dry
-        SL = sel(both, SLw, sel(wetL, SLr, SLl));
-        SR = sel(both, SRw, sel(wetL, SRr, SRl));
-        Ss = sel(both, Ssw, sel(wetL, SRr, SLl));
+        SL = sel(wetL, SLr, SLl);
+        SR = sel(wetL, SRr, SRl);
+        Ss = sel(wetL, SRr, SLl);
     }
     const V qL = mul(hL, unL), qR = mul(hR, unR);
     const V PL = fma(qL, unL, mul(mul(g2, hL), hL));
     const V PR = fma(qR, unR, mul(mul(g2, hR), hR));
     const V r = rcp_(sub(SR, SL)), ss = mul(SR, SL);                                                  // Eq 18
-    const M supL = ge(SL, zero), supR = le(SR, zero);                                                 // Eq 17
+    const bool supL = ge(SL, zero), supR = le(SR, zero);                                              // Eq 17
     const V G1s = mul(fma(SR, qL, fma(neg(SL), qR, mul(ss, sub(hR, hL)))), r);
     const V G2s = mul(fma(SR, PL, fma(neg(SL), PR, mul(ss, sub(qR, qL)))), r);
-    G1 = sel(wet_any, sel(supL, qL, sel(supR, qR, G1s)), zero);
-    G2 = sel(wet_any, sel(supL, PL, sel(supR, PR, G2s)), zero);
+    G1 = sel(supL, qL, sel(supR, qR, G1s));
+    G2 = sel(supL, PL, sel(supR, PR, G2s));
     if (hll_only) {
         const V qtL = mul(qL, utL), qtR = mul(qR, utR);
         const V G3s = mul(fma(SR, qtL, fma(neg(SL), qtR, mul(ss, sub(mul(hR, utR), mul(hL, utL))))), r);
-        G3 = sel(wet_any, sel(supL, qtL, sel(supR, qtR, G3s)), zero);
+        G3 = sel(supL, qtL, sel(supR, qtR, G3s));
     } else {
-        G3 = sel(wet_any, mul(G1, sel(ge(Ss, zero), utL, utR)), zero);                               // Eq 24
+        G3 = mul(G1, sel(ge(Ss, zero), utL, utR));                                                    // Eq 24
     }
-    if (speeds) {
-        speeds[0] = sel(wet_any, SL, zero);
-        speeds[1] = sel(wet_any, SR, zero);
-        speeds[2] = sel(wet_any, Ss, zero);
-    }
+    if (speeds) { speeds[0] = SL; speeds[1] = SR; speeds[2] = Ss; }
 }
 
 // ---- one interior edge (Eq 12, 28, 30) ---------------------------------------------------
@@ -171,8 +167,8 @@ __device__ __forceinline__ void edge_interior(V hi, V ui, V vi, V zi, V hk, V hu
                                               bool hll_only, V* src_k = nullptr) {
     V uk, vk;
     velocity(hk, huk, hvk, h_dry, uk, vk);
-    // hydrostatic reconstruction (Eq 28): z* = max(z_i, z_k), a tie taking z_k
-    const V zs = sel(gt(zi, zk), zi, zk);
+    // hydrostatic reconstruction (Eq 28): z* = max(z_i, z_k)
+    const V zs = vmax(zi, zk);
     const V hsi = max0(sub(add(hi, zi), zs));
     const V hsk = max0(sub(add(hk, zk), zs));
     // both sides in cell i's edge frame (Eq 12): normal n, tangent (-n2, n1)
@@ -272,8 +268,8 @@ __device__ __forceinline__ V finish(V hi, V ri, V qx, V qy, V f0, V f1, V f2, V 
     const V big = splat<V>(3.0e38f);
     // finite and below 3e38 in magnitude (NaN fails every comparison)
     const auto okh = lt(h, big);
-    const auto oku = lt(sel(lt(u, zero), neg(u), u), big);
-    const auto okv = lt(sel(lt(v, zero), neg(v), v), big);
+    const auto oku = lt(fabsf(u), big);
+    const auto okv = lt(fabsf(v), big);
     nonfinite = mnot(mand(okh, mand(oku, okv)));
     oh = h; ou = u; ov = v;
     const V qm = sqrt_(fma(u, u, mul(v, v)));

@@ -49,6 +49,15 @@ int build_host_mesh(const double* nodes, int64_t n_nodes, const int32_t* tris, i
 // Locality orderings of the cells; each returns order[new] = old.
 std::vector<int64_t> order_hilbert(const std::vector<double>& cx, const std::vector<double>& cy);
 std::vector<int64_t> order_rcm(int64_t n, const std::vector<int64_t>& nbr /* [n][3], -1 = none */);
+// Cells of a locality order rearranged so that positions (2p, 2p+1) hold two
+// cells sharing an edge wherever a greedy matching along the order finds one
+// (a partner at most 256 places later); rot[c] is the local edge of cell c
+// (caller numbering, counter-clockwise nodes t) that its partner shares, 0
+// when unmatched.  Unmatched cells go in segments of 64 of their own, kept
+// near their place in the order, so that a warp's 32 pairs are all matched or
+// all unmatched.  Deterministic.
+std::vector<int64_t> pair_cells(const std::vector<int64_t>& order, const std::vector<int64_t>& nbr,
+                                const std::vector<int32_t>& t, std::vector<int>& rot);
 
 // Thread-local error message of the C ABI.
 void set_error(const std::string& msg);
@@ -57,6 +66,7 @@ void set_error(const std::string& msg);
 struct LaunchShape {
     int block = 0, min_blocks = 0, stages = 0, geo = 0, edges = 0;
     unsigned grid = 0;
+    int pairs = 0;   // the cell-pair kernel (FP32): grid blocks over (n + 1) / 2 pairs
 };
 
 // Words of a mesh's device status block.

@@ -687,10 +687,18 @@ __device__ __forceinline__ T finish_cell(const Args& a, long long i, const V4<T>
 // update_cell for FP32: the same loads, quiet test and edge loop, with the
 // arithmetic of swe_f32.cuh, every operation explicitly rounded, so that every
 // FP32 kernel and launch shape gives the same bits.
-template <bool GEO_EARLY, bool EDGES, typename Args>
+// Pairs of cells sharing their local edge 0 (step_kernel_pair): with PAIR 1
+// the first cell hands the flux of that edge to the second (pmode kPairGive ->
+// kPairGiven, pe = the flux leaving the first cell); with PAIR 2 the second
+// takes its negative (pmode kPairTake) instead of evaluating the edge.
+struct PairEdge { float F0, F1, F2; };
+constexpr int kPairNone = 0, kPairGive = 1, kPairGiven = 2, kPairTake = 3;
+
+template <bool GEO_EARLY, bool EDGES, int PAIR = 0, typename Args>
 __device__ __forceinline__ float update_cell_f32(const Args& a, long long i, const V4<float>& own, const int4& tp,
                                                  float dt, unsigned& active, unsigned long long* n_clamped,
-                                                 unsigned* status) {
+                                                 unsigned* status, int* pmode = nullptr,
+                                                 volatile PairEdge* pe = nullptr) {
     const float g = a.g, h_dry = a.h_dry, g2 = f32::mul(0.5f, g);
     const float hi = own.x, zi = own.w;
     int code[3] = {tp.x, tp.y, tp.z};
@@ -755,7 +763,7 @@ __device__ __forceinline__ float update_cell_f32(const Args& a, long long i, con
             float src;
             if constexpr (EDGES) {
                 if (!(hi > h_dry) && !(o.x > h_dry)) {
-                    const float zs = f32::sel(f32::gt(zi, o.w), zi, o.w);
+                    const float zs = f32::vmax(zi, o.w);
                     const float hsi = f32::max0(f32::sub(f32::add(hi, zi), zs));
                     F0 = 0.0f; F1 = 0.0f; F2 = 0.0f;
                     f32::bed_src(hsi, hi, g2, src);
@@ -774,9 +782,20 @@ __device__ __forceinline__ float update_cell_f32(const Args& a, long long i, con
                         src = fl.w;
                     }
                 }
+            } else if (PAIR == 2 && j == 0 && *pmode == kPairTake) {
+                // the first cell's evaluation of this edge, seen from this side;
+                // the bed source factor is this cell's own (Eq 30)
+                const float zs = f32::vmax(zi, o.w);
+                const float hsi = f32::max0(f32::sub(f32::add(hi, zi), zs));
+                f32::bed_src(hsi, hi, g2, src);
+                F0 = -pe->F0; F1 = -pe->F1; F2 = -pe->F2;
             } else {
                 f32::edge_interior<float>(hi, ui, vi, zi, o.x, o.y, o.z, o.w, n1, n2, (c & kFlipBit) != 0, g, g2,
                                           h_dry, F0, F1, F2, src, a.hll != 0);
+                if (PAIR == 1 && j == 0 && *pmode == kPairGive) {
+                    pe->F0 = F0; pe->F1 = F1; pe->F2 = F2;
+                    *pmode = kPairGiven;
+                }
             }
             sx = f32::fma(src, lx, sx);
             sy = f32::fma(src, ly, sy);
@@ -990,6 +1009,64 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_kernel(const StepArgs<T> a) 
             slot = slot == STAGES - 1 ? 0 : slot + 1;
         }
         cp_async_wait<0>();
+    }
+    block_min_publish<BLOCK>(cand, a.dt_write, active, a.n_active);
+}
+
+// ---- the fused step over pairs of adjacent cells (FP32) -----------------------------
+// Thread work item p is the cell pair (2p, 2p+1).  The mesh's pairing order
+// puts two cells that share an edge at such positions, with that edge as
+// local edge 0 of both, for most cells.  The edge's flux is then evaluated
+// once, by the first cell, and the second takes its negative: bit for bit
+// what it would evaluate itself (the edge's canonical evaluation, rotated with
+// the exactly opposite normal), while each cell still sums its edges in local
+// order, so the results equal the one-cell kernels'.  Five Riemann problems
+// per pair instead of six.  Unmatched cells come in whole warps of their own.
+template <int BLOCK, int MINB, bool GEO_EARLY>
+__global__ void __launch_bounds__(BLOCK, MINB) step_kernel_pair(const StepArgs<float> a) {
+    const WarpDt<float> wdt = warp_step_dt<float>(a.cfl, a.dt_read, a.dt_fixed);
+    const bool have_dt = wdt.have;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *a.dt_reset = kInfBits;
+        if (have_dt) *a.t += wdt.d;
+        else atomicOr(a.status, kStatusDry);
+        if (a.dt_log) *a.dt_log = wdt.d;
+    }
+    float cand = inf_of<float>();
+    unsigned active = 0u;
+    // 32-bit pair indices (a mesh has fewer than 2^30 cells): fewer live registers
+    const unsigned stride = gridDim.x * BLOCK;
+    const unsigned np = (unsigned)((a.n + 1) >> 1);
+    unsigned p = blockIdx.x * BLOCK + threadIdx.x;
+    __shared__ PairEdge slot[BLOCK];
+    volatile PairEdge* pe = &slot[threadIdx.x];
+    if (!have_dt) {
+        for (long long i = p; i < a.n; i += (long long)gridDim.x * BLOCK) a.s_out[i] = a.s_in[i];
+    } else {
+        const float dt = wdt.t;
+        for (; p < np; p += stride) {
+            const long long iA = 2 * (long long)p, iB = iA + 1;
+            const bool hasB = iB < a.n;
+            const V4<float> ownA = a.s_in[iA];
+            const int4 tpA = a.topo[iA];
+            const int cB = hasB ? __ldg(&a.topo[iB].x) : -1;
+            const bool shared = tpA.x >= 0 && cB >= 0 && (long long)(tpA.x & kNbrMask) == iB &&
+                                (long long)(cB & kNbrMask) == iA;
+            // the first cell gives its edge 0; the handed-over flux waits in shared
+            // memory, not in registers, through the first cell's other edges
+            int mode = shared ? kPairGive : kPairNone;
+            cand = min_nonneg(cand, update_cell_f32<GEO_EARLY, false, 1>(a, iA, ownA, tpA, dt, active, a.n_clamped,
+                                                                         a.status, &mode, pe));
+            if (hasB) {
+                // the second cell's records are read after the first cell's update
+                // (fewer live registers)
+                const V4<float> ownB = a.s_in[iB];
+                const int4 tpB = a.topo[iB];
+                int modeB = mode == kPairGiven ? kPairTake : kPairNone;
+                cand = min_nonneg(cand, update_cell_f32<GEO_EARLY, false, 2>(a, iB, ownB, tpB, dt, active,
+                                                                             a.n_clamped, a.status, &modeB, pe));
+            }
+        }
     }
     block_min_publish<BLOCK>(cand, a.dt_write, active, a.n_active);
 }
@@ -1586,6 +1663,13 @@ struct Launch {
                                 cudaStream_t st);
     // compiled (block, min_blocks, stages, geo_early) shapes of the step kernel; returns their number
     static int step_variants(int (*out)[4], int max);
+    // the step over cell pairs (FP32 only; cudaErrorInvalidValue otherwise) with one of its
+    // compiled (block, min_blocks, geo_early, stages) shapes; a.grid blocks of `block` threads,
+    // each thread a pair at a time
+    static cudaError_t step_pair(const StepArgs<T>& a, int block, int min_blocks, int geo_early, int stages,
+                                 cudaStream_t st);
+    static cudaError_t pair_resident_blocks(int block, int min_blocks, int geo_early, int stages, int* per_sm);
+    static int pair_variants(int (*out)[4], int max);
     // batched ensemble step with one of its compiled (block, min_blocks, stages, geo_early) shapes
     static cudaError_t ensemble_step(const EnsArgs<T>& a, int block, int min_blocks, int stages, int geo_early,
                                      unsigned grid, cudaStream_t st);

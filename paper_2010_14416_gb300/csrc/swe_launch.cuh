@@ -148,6 +148,54 @@ int Launch<T>::step_variants(int (*out)[4], int max) {
     return k;
 }
 
+// (block, min blocks per SM, geometry early, stages) shapes of the cell-pair
+// step (FP32); stages is 1 (records read directly).  A cp.async pipeline of
+// pair records (2 or 3 stages, 64 bytes per thread each) measured slower on
+// the fully wet 13M river (0.285-0.353 against 0.267 ms per step: at 64
+// registers it spills), so the pair kernel has none.
+#define SWE_PAIR_VARIANTS_F32(X) X(256, 4, 0, 1) X(256, 4, 1, 1) X(128, 8, 1, 1) X(128, 8, 0, 1) X(256, 3, 1, 1)
+
+template <typename T>
+cudaError_t Launch<T>::step_pair(const StepArgs<T>& a, int block, int min_blocks, int geo_early, int stages,
+                                 cudaStream_t st) {
+    if constexpr (sizeof(T) == 4) {
+        if (a.grid == 0) return cudaErrorInvalidValue;
+#define SWE_LAUNCH_PAIR(B, M, G, S) \
+    if (block == B && min_blocks == M && geo_early == G && stages == S) {      \
+        step_kernel_pair<B, M, G != 0><<<a.grid, B, 0, st>>>(a);            \
+        return cudaGetLastError();                                              \
+    }
+        SWE_PAIR_VARIANTS_F32(SWE_LAUNCH_PAIR)
+#undef SWE_LAUNCH_PAIR
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t Launch<T>::pair_resident_blocks(int block, int min_blocks, int geo_early, int stages, int* per_sm) {
+    if constexpr (sizeof(T) == 4) {
+#define SWE_OCC_PAIR(B, M, G, S) \
+    if (block == B && min_blocks == M && geo_early == G && stages == S)        \
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, step_kernel_pair<B, M, G != 0>, B, 0);
+        SWE_PAIR_VARIANTS_F32(SWE_OCC_PAIR)
+#undef SWE_OCC_PAIR
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+int Launch<T>::pair_variants(int (*out)[4], int max) {
+    int k = 0;
+    if constexpr (sizeof(T) == 4) {
+#define SWE_LIST(B, M, G, S) \
+    if (k < max) { out[k][0] = B; out[k][1] = M; out[k][2] = G; out[k][3] = S; } \
+    ++k;
+        SWE_PAIR_VARIANTS_F32(SWE_LIST)
+#undef SWE_LIST
+    }
+    return k;
+}
+
 template <typename T>
 cudaError_t Launch<T>::edge_flux(const StepArgs<T>& a, cudaStream_t st) {
     if (a.n_edges <= 0) return cudaSuccess;

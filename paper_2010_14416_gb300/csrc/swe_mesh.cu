@@ -146,6 +146,57 @@ std::vector<int64_t> order_rcm(int64_t n, const std::vector<int64_t>& nbr) {
     return order;
 }
 
+std::vector<int64_t> pair_cells(const std::vector<int64_t>& order, const std::vector<int64_t>& nbr,
+                                const std::vector<int32_t>& t, std::vector<int>& rot) {
+    const int64_t n = (int64_t)order.size();
+    constexpr int64_t kWindow = 256;   // a partner comes at most this many places later
+    constexpr size_t kSegment = 64;    // cells per segment of only pairs or only unmatched cells
+    std::vector<int64_t> pos(n);
+    for (int64_t p = 0; p < n; ++p) pos[order[p]] = p;
+    std::vector<int64_t> mate(n, -1);
+    rot.assign(n, 0);
+    for (int64_t p = 0; p < n; ++p) {
+        const int64_t c = order[p];
+        if (mate[c] >= 0) continue;
+        int64_t best = -1;
+        int jc = 0;
+        for (int j = 0; j < 3; ++j) {
+            const int64_t k = nbr[3 * c + j];
+            if (k < 0 || mate[k] >= 0 || pos[k] <= p || pos[k] > p + kWindow) continue;
+            if (best < 0 || pos[k] < pos[best]) { best = k; jc = j; }
+        }
+        if (best < 0) continue;
+        // the same edge in the partner, traversed the other way (both counter-clockwise)
+        const int32_t a = t[3 * c + jc], b = t[3 * c + (jc + 1) % 3];
+        int jk = -1;
+        for (int j = 0; j < 3; ++j)
+            if (t[3 * best + j] == b && t[3 * best + (j + 1) % 3] == a) jk = j;
+        if (jk < 0) continue;
+        mate[c] = best;
+        mate[best] = c;
+        rot[c] = jc;
+        rot[best] = jk;
+    }
+    std::vector<int64_t> out;
+    out.reserve(n);
+    std::vector<int64_t> single;
+    size_t taken = 0;
+    for (int64_t p = 0; p < n; ++p) {
+        const int64_t c = order[p];
+        if (mate[c] >= 0) {
+            if (pos[mate[c]] > p) { out.push_back(c); out.push_back(mate[c]); }
+        } else {
+            single.push_back(c);
+        }
+        if (out.size() % kSegment == 0 && single.size() - taken >= kSegment) {
+            out.insert(out.end(), single.begin() + taken, single.begin() + taken + kSegment);
+            taken += kSegment;
+        }
+    }
+    out.insert(out.end(), single.begin() + taken, single.end());
+    return out;
+}
+
 int build_host_mesh(const double* nodes, int64_t n_nodes, const int32_t* tris, int64_t n,
                     const double* bathy, const double* manning, int reorder, HostMesh& M,
                     std::string& err) {
@@ -240,6 +291,10 @@ int build_host_mesh(const double* nodes, int64_t n_nodes, const int32_t* tris, i
         err = "swe_mesh_create: unknown reorder mode";
         return SWE_EINVAL;
     }
+    // pairs of adjacent cells at (2p, 2p+1), their shared edge first in both
+    std::vector<int> rot;
+    if (reorder != SWE_REORDER_NONE) order = pair_cells(order, nbr_old, t, rot);
+    else rot.assign(n, 0);
     M.perm = order;
     M.inv.assign(n, 0);
     for (int64_t c = 0; c < n; ++c) M.inv[order[c]] = c;
@@ -257,7 +312,8 @@ int build_host_mesh(const double* nodes, int64_t n_nodes, const int32_t* tris, i
         const int64_t o = order[c];
         double perim = 0.0;
         for (int j = 0; j < 3; ++j) {
-            const int32_t a = t[3 * o + j], b = t[3 * o + (j + 1) % 3];
+            const int jo = (j + rot[o]) % 3;   // local edge j is the caller's edge jo
+            const int32_t a = t[3 * o + jo], b = t[3 * o + (jo + 1) % 3];
             M.tri[3 * c + j] = a;
             const double dx = nodes[2 * b] - nodes[2 * a];
             const double dy = nodes[2 * b + 1] - nodes[2 * a + 1];
@@ -267,7 +323,7 @@ int build_host_mesh(const double* nodes, int64_t n_nodes, const int32_t* tris, i
             const double L = std::sqrt(dx * dx + dy * dy);
             M.len[3 * c + j] = L;
             perim += L;
-            const int64_t k = nbr_old[3 * o + j];
+            const int64_t k = nbr_old[3 * o + jo];
             if (k >= 0) {
                 int32_t code = (int32_t)M.inv[k];
                 if (k < o) code |= kFlipBit;  // the neighbour is the edge's left state

@@ -3,8 +3,8 @@
 // The paper fixes one thread per cell (Section 5.3.2) and no block size; here
 // the shape of the fused step kernel is a measured choice per mesh: every
 // compiled (block, min_blocks, stages, geometry early) shape of the step
-// kernel and every (block, min_blocks, geometry early) shape of the activity
-// kernel, each with several grid sizes (one or two resident waves looping
+// kernel, every (block, min_blocks, geometry early) shape of the cell-pair
+// step (FP32) and of the activity kernel, each with several grid sizes (one or two resident waves looping
 // over the cells, or 1, 2 or 4 cells per thread), is timed with CUDA events
 // on the mesh's current state.  The trial steps read the current state and
 // write a scratch state buffer and a scratch copy of the status block; trials
@@ -37,11 +37,12 @@ constexpr double kRunoffTolerance = 1.01;  // runoff: ties within 1 %
 struct Shape {
     int block, min_blocks, stages, geo_early, activity, edges;
     unsigned grid;
+    int pairs;
 };
 
 bool same_shape(const Shape& a, const Shape& b) {
     return a.block == b.block && a.min_blocks == b.min_blocks && a.stages == b.stages && a.geo_early == b.geo_early &&
-           a.activity == b.activity && a.edges == b.edges && a.grid == b.grid;
+           a.activity == b.activity && a.edges == b.edges && a.grid == b.grid && a.pairs == b.pairs;
 }
 
 int tfail(cudaError_t e, const char* what) {
@@ -69,16 +70,19 @@ int candidate_shapes(const swe_mesh* m, std::vector<Shape>& cand) {
     if (e != cudaSuccess) return tfail(e, "swe_autotune: device attribute");
     // the shape in use first
     cand.push_back({m->cfg.block_size, m->cfg.min_blocks, m->cfg.stages, m->cfg.geometry_early, m->cfg.activity,
-                    m->cfg.edge_pass, m->grid});
-    auto add = [&](int block, int minb, int stages, int geo, int act, int edges) -> int {
+                    m->cfg.edge_pass, m->grid, m->cfg.cell_pairs});
+    auto add = [&](int block, int minb, int stages, int geo, int act, int edges, int pairs = 0) -> int {
         int per_sm = 0;
-        cudaError_t er = Launch<T>::resident_blocks(block, minb, stages, geo, act, edges, &per_sm);
+        cudaError_t er = pairs ? Launch<T>::pair_resident_blocks(block, minb, geo, stages, &per_sm)
+                               : Launch<T>::resident_blocks(block, minb, stages, geo, act, edges, &per_sm);
         if (er != cudaSuccess) return tfail(er, "swe_autotune: occupancy");
-        const long long need = (n + block - 1) / block;
+        const long long units = pairs ? (n + 1) / 2 : n;
+        const long long need = (units + block - 1) / block;
         const long long wave = (long long)std::max(per_sm, 1) * std::max(sms, 1);
         const long long grids[] = {wave, 2 * wave, need, (need + 1) / 2, (need + 3) / 4};
         for (long long gsz : grids) {
-            const Shape sh{block, minb, stages, geo, act, edges, (unsigned)std::max(1LL, std::min(gsz, need))};
+            const Shape sh{block, minb, stages, geo, act, edges,
+                           (unsigned)std::max(1LL, std::min(gsz, need)), pairs};
             bool seen = false;
             for (const Shape& c : cand) seen = seen || same_shape(c, sh);
             if (!seen) cand.push_back(sh);
@@ -94,6 +98,12 @@ int candidate_shapes(const swe_mesh* m, std::vector<Shape>& cand) {
     const int ne = std::min(Launch<T>::edge_variants(v, 64), 64);
     for (int k = 0; k < ne; ++k) {
         const int rc = add(v[k][0], v[k][1], v[k][2], v[k][3], 0, 1);
+        if (rc) return rc;
+    }
+    int q[64][4];
+    const int nq = std::min(Launch<T>::pair_variants(q, 64), 64);
+    for (int k = 0; k < nq; ++k) {
+        const int rc = add(q[k][0], q[k][1], q[k][3], q[k][2], 0, 0, 1);
         if (rc) return rc;
     }
     int w[64][4];
@@ -112,8 +122,10 @@ void apply_shape(swe_mesh* m, const Shape& sh) {
     m->cfg.geometry_early = sh.geo_early;
     m->cfg.activity = sh.activity;
     m->cfg.edge_pass = sh.edges;
+    m->cfg.cell_pairs = sh.pairs;
     m->grid = sh.grid;
-    if (!sh.activity) m->plain = LaunchShape{sh.block, sh.min_blocks, sh.stages, sh.geo_early, sh.edges, sh.grid};
+    if (!sh.activity)
+        m->plain = LaunchShape{sh.block, sh.min_blocks, sh.stages, sh.geo_early, sh.edges, sh.grid, sh.pairs};
 }
 
 template <typename T>
@@ -237,6 +249,7 @@ int autotune_t(swe_mesh* m, int trial_steps, swe_tune* out) {
         out->ms_best = ms[best];
         out->ms_before = ms[0];
         out->n_candidates = (int)cand.size();
+        out->cell_pairs = pick.pairs;
     }
     return SWE_OK;
 }

@@ -279,6 +279,43 @@ def test_kernel_variants_are_bitwise_identical(precision, variants):
         assert all(np.array_equal(x, y) for x, y in zip(ref, got)), (b, mb, st, ge)
 
 
+def _odd_canal():
+    # a dam-break canal with its last triangle removed: an odd cell count, so
+    # the last pair has one cell; walls all round
+    mi = mg.canal(201, 10, Lx=100.0, Ly=5.0, hR=0.0, seed=5, manning=0.03)
+    keep = mi.n_cells - 1
+    mi.tris, mi.z, mi.manning = mi.tris[:keep], mi.z[:keep], mi.manning[:keep]
+    mi.h, mi.hu, mi.hv = mi.h[:keep], mi.hu[:keep], mi.hv[:keep]
+    mi.bcs = []
+    return mi
+
+
+@pytest.mark.parametrize("maker", ["river", "odd_canal"])
+def test_cell_pair_kernel_is_bitwise_identical(maker):
+    # the pair kernel hands each shared edge 0 from the first cell of a pair to
+    # the second; states, times and the count of cells that ran the flux path
+    # equal the one-cell kernel's for every shape, grid, flux, reorder and with
+    # the debug checks, through wetting fronts, an inflow and a fixed stage
+    mi = mg.river(101, 21, seed=8) if maker == "river" else _odd_canal()
+    if maker == "odd_canal":
+        assert mi.n_cells % 2 == 1
+    f32 = capi.SWE_FP32
+    for extra in (dict(), dict(flux=capi.SWE_FLUX_HLL), dict(reorder=capi.SWE_REORDER_RCM),
+                  dict(reorder=capi.SWE_REORDER_NONE)):
+        ref, tref, iref = _gpu_run(mi, 301, precision=f32, **extra)
+        shapes = [dict(), dict(block_size=128, min_blocks=8, geometry_early=1), dict(block_size=128, min_blocks=8),
+                  dict(block_size=256, min_blocks=4, geometry_early=1),
+                  dict(block_size=256, min_blocks=4, grid=3),
+                  dict(block_size=256, min_blocks=3, geometry_early=1, grid=100000, graph_steps=-1),
+                  dict(block_size=256, min_blocks=4, geometry_early=1, debug_checks=1)]
+        for kw in shapes:
+            got, t, info = _gpu_run(mi, 301, precision=f32, cell_pairs=1, **kw, **extra)
+            assert t == tref, (kw, extra)
+            assert all(np.array_equal(x, y) for x, y in zip(ref, got)), (kw, extra)
+            assert info["n_active"] == iref["n_active"], (kw, extra)
+            assert info["status"] == 0
+
+
 @pytest.mark.parametrize("precision", [capi.SWE_FP64, capi.SWE_FP32])
 @pytest.mark.parametrize("maker", ["river", "dry_canal"])
 def test_activity_mode_is_bitwise_neutral(precision, maker):

@@ -15,7 +15,8 @@ CSRC = os.path.join(HERE, "..", "paper_2010_14416_gb300", "csrc")
 INCLUDE = os.path.join(HERE, "..", "include")
 
 # (translation unit, mangled-name fragment) of the kernels the tuned runs use:
-# the 13M river's activity kernel, the fully wet river's step kernel, the FP32
+# the 13M river's activity kernel, the fully wet river's step kernels (one
+# cell and cell pairs per thread), the FP32
 # ensemble's activity kernel with dynamically taken chunks, the FP64 edge pass
 # (edge kernel and cell pass) and the FP64 ensemble's cell pass
 KERNELS = [
@@ -23,6 +24,8 @@ KERNELS = [
     ("swe_step_f32.cu", "11step_kernelIfLi256ELi4ELi3ELb1ELb0E"),
     ("swe_step_f32.cu", "11step_kernelIfLi128ELi8ELi3ELb1ELb0E"),
     ("swe_step_f32.cu", "24ensemble_step_kernel_actIfLi128ELi8ELb1ELb1E"),
+    ("swe_step_f32.cu", "16step_kernel_pairILi256ELi4ELb1EE"),
+    ("swe_step_f32.cu", "16step_kernel_pairILi128ELi8ELb1EE"),
     ("swe_step_f64.cu", "16edge_flux_kernelIdLi256E"),
     ("swe_step_f64.cu", "11step_kernelIdLi128ELi1ELi1ELb0ELb1E"),
     ("swe_step_f64.cu", "20ensemble_step_kernelIdLi128ELi1ELi1ELb0ELb1E"),
