@@ -540,7 +540,8 @@ def measure_ensemble(ctx, name, steps, warmup, ens_shape=None):
         "config": {"workload": wl["desc"], "cells": n, "members": len(mis), "parallelism": f"replicas{ctx.ws}",
                    "l2": "working set > 129 MB L2, no flush needed", "steps_before_timed": warm_total,
                    "launch_shape": _shape_key(shape), "autotune": shape,
-                   "member_shapes": sorted({tuple(_shape_key(t)[:6]) for t in member_shapes})},
+                   "member_shapes": sorted({tuple(_shape_key(t)[:6]) + ((1,) if t.get("cell_pairs") else ())
+                                            for t in member_shapes})},
         "roofline": roof,
         "per_member_launches": {"value": ctx.ws * n * steps / (ms_plain * 1e-3), "unit": "cell-updates/s",
                                 "ms_per_step": ms_plain / steps,
@@ -684,13 +685,14 @@ def _shape_kwargs(spec):
 
 
 def _shape_key(t):
-    """(block, min_blocks, stages, geometry_early, activity, edge_pass, grid[, chunk, dynamic | , 1 for the
+    """(block, min_blocks, stages, geometry_early, activity, edge_pass, grid[, chunk, dynamic][, 1 for the
     cell-pair kernel]) of an autotuner choice."""
     k = [t["block_size"], t["min_blocks"], t["stages"], t["geometry_early"], t["activity"], t["edge_pass"],
          t["grid"]]
+    pairs = [1] if t.get("cell_pairs") else []
     if t.get("chunk"):
-        return k + [t["chunk"], t.get("dynamic", 0)]
-    return k + [1] if t.get("cell_pairs") else k
+        return k + [t["chunk"], t.get("dynamic", 0)] + pairs
+    return k + pairs
 
 
 def _kernel_hash():

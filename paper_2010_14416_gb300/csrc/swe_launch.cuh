@@ -149,10 +149,12 @@ int Launch<T>::step_variants(int (*out)[4], int max) {
 }
 
 // (block, min blocks per SM, geometry early, stages) shapes of the cell-pair
-// step (FP32); stages is 1 (records read directly).  A cp.async pipeline of
-// pair records (2 or 3 stages, 64 bytes per thread each) measured slower on
-// the fully wet 13M river (0.285-0.353 against 0.267 ms per step: at 64
-// registers it spills), so the pair kernel has none.
+// step (FP32); stages is 1 (records read directly).  On the fully wet 13M
+// river (0.270 ms per step at 256 x 4) a cp.async pipeline of pair records
+// measured slower (2 or 3 pairs ahead: 0.285-0.353 ms, spilling at 64
+// registers), and so did copying the second cell's records, or those and the
+// next pair's first, into shared memory during the first cell's update
+// (0.272 and 0.280 ms): the pair kernel has none.
 #define SWE_PAIR_VARIANTS_F32(X) X(256, 4, 0, 1) X(256, 4, 1, 1) X(128, 8, 1, 1) X(128, 8, 0, 1) X(256, 3, 1, 1)
 
 template <typename T>
