@@ -49,15 +49,18 @@ int build_host_mesh(const double* nodes, int64_t n_nodes, const int32_t* tris, i
 // Locality orderings of the cells; each returns order[new] = old.
 std::vector<int64_t> order_hilbert(const std::vector<double>& cx, const std::vector<double>& cy);
 std::vector<int64_t> order_rcm(int64_t n, const std::vector<int64_t>& nbr /* [n][3], -1 = none */);
-// Cells of a locality order rearranged so that positions (2p, 2p+1) hold two
-// cells sharing an edge wherever a greedy matching along the order finds one
-// (a partner at most 256 places later); rot[c] is the local edge of cell c
-// (caller numbering, counter-clockwise nodes t) that its partner shares, 0
-// when unmatched.  Unmatched cells go in segments of 64 of their own, kept
-// near their place in the order, so that a warp's 32 pairs are all matched or
-// all unmatched.  Deterministic.
-std::vector<int64_t> pair_cells(const std::vector<int64_t>& order, const std::vector<int64_t>& nbr,
-                                const std::vector<int32_t>& t, std::vector<int>& rot);
+// A matching of adjacent cells: a greedy pass along `along` (order[new] =
+// old) matches each unmatched cell with its unmatched neighbour that comes
+// soonest after it, at most 256 places later; mate[c] = the partner of cell c
+// (caller numbering) or -1, rot[c] = the local edge of c (counter-clockwise
+// nodes t) that it shares with its partner, 0 when unmatched.  Deterministic.
+void match_cells(const std::vector<int64_t>& along, const std::vector<int64_t>& nbr, const std::vector<int32_t>& t,
+                 std::vector<int64_t>& mate, std::vector<int>& rot);
+// A locality order rearranged so that positions (2p, 2p+1) hold matched
+// pairs, each at its first cell's place; unmatched cells go in segments of 64
+// of their own, kept near their place, so that a warp's 32 pairs are all
+// matched or all unmatched.
+std::vector<int64_t> place_pairs(const std::vector<int64_t>& order, const std::vector<int64_t>& mate);
 
 // Thread-local error message of the C ABI.
 void set_error(const std::string& msg);

@@ -146,17 +146,16 @@ std::vector<int64_t> order_rcm(int64_t n, const std::vector<int64_t>& nbr) {
     return order;
 }
 
-std::vector<int64_t> pair_cells(const std::vector<int64_t>& order, const std::vector<int64_t>& nbr,
-                                const std::vector<int32_t>& t, std::vector<int>& rot) {
-    const int64_t n = (int64_t)order.size();
+void match_cells(const std::vector<int64_t>& along, const std::vector<int64_t>& nbr, const std::vector<int32_t>& t,
+                 std::vector<int64_t>& mate, std::vector<int>& rot) {
+    const int64_t n = (int64_t)along.size();
     constexpr int64_t kWindow = 256;   // a partner comes at most this many places later
-    constexpr size_t kSegment = 64;    // cells per segment of only pairs or only unmatched cells
     std::vector<int64_t> pos(n);
-    for (int64_t p = 0; p < n; ++p) pos[order[p]] = p;
-    std::vector<int64_t> mate(n, -1);
+    for (int64_t p = 0; p < n; ++p) pos[along[p]] = p;
+    mate.assign(n, -1);
     rot.assign(n, 0);
     for (int64_t p = 0; p < n; ++p) {
-        const int64_t c = order[p];
+        const int64_t c = along[p];
         if (mate[c] >= 0) continue;
         int64_t best = -1;
         int jc = 0;
@@ -177,16 +176,26 @@ std::vector<int64_t> pair_cells(const std::vector<int64_t>& order, const std::ve
         rot[c] = jc;
         rot[best] = jk;
     }
+}
+
+std::vector<int64_t> place_pairs(const std::vector<int64_t>& order, const std::vector<int64_t>& mate) {
+    const int64_t n = (int64_t)order.size();
+    constexpr size_t kSegment = 64;    // cells per segment of only pairs or only unmatched cells
+    std::vector<char> placed(n, 0);
     std::vector<int64_t> out;
     out.reserve(n);
     std::vector<int64_t> single;
     size_t taken = 0;
     for (int64_t p = 0; p < n; ++p) {
         const int64_t c = order[p];
+        if (placed[c]) continue;
         if (mate[c] >= 0) {
-            if (pos[mate[c]] > p) { out.push_back(c); out.push_back(mate[c]); }
+            out.push_back(c);
+            out.push_back(mate[c]);
+            placed[c] = placed[mate[c]] = 1;
         } else {
             single.push_back(c);
+            placed[c] = 1;
         }
         if (out.size() % kSegment == 0 && single.size() - taken >= kSegment) {
             out.insert(out.end(), single.begin() + taken, single.begin() + taken + kSegment);
@@ -291,10 +300,14 @@ int build_host_mesh(const double* nodes, int64_t n_nodes, const int32_t* tris, i
         err = "swe_mesh_create: unknown reorder mode";
         return SWE_EINVAL;
     }
-    // pairs of adjacent cells at (2p, 2p+1), their shared edge first in both
+    // pairs of adjacent cells, matched along the Hilbert order whatever the
+    // mode, with their shared edge as local edge 0 of both: every mode numbers
+    // each cell's edges alike (so sums them in the same order); the RCM and
+    // Hilbert orders then place the pairs at (2p, 2p+1)
+    std::vector<int64_t> mate;
     std::vector<int> rot;
-    if (reorder != SWE_REORDER_NONE) order = pair_cells(order, nbr_old, t, rot);
-    else rot.assign(n, 0);
+    match_cells(reorder == SWE_REORDER_HILBERT ? order : order_hilbert(cx, cy), nbr_old, t, mate, rot);
+    if (reorder != SWE_REORDER_NONE) order = place_pairs(order, mate);
     M.perm = order;
     M.inv.assign(n, 0);
     for (int64_t c = 0; c < n; ++c) M.inv[order[c]] = c;

@@ -94,6 +94,36 @@ def test_shared_edges_have_bitwise_opposite_normals():
             assert ln[k, jj[0], 0] == -ln[c, j, 0] and ln[k, jj[0], 1] == -ln[c, j, 1]
 
 
+def test_cell_pairs_share_local_edge_zero():
+    # the pairing of mesh preprocessing: for the RCM and Hilbert orders most
+    # positions (2p, 2p+1) hold two cells whose local edge 0 is their shared
+    # edge, whole warps (32 pairs) are all paired or all unpaired, and every
+    # mode numbers a cell's edges alike (same caller neighbour and L n at each
+    # local edge)
+    mi = mg.river(160, 32, seed=3, shuffle=True)
+    n = mi.n_cells
+    per_mode = {}
+    for r in (capi.SWE_REORDER_NONE, capi.SWE_REORDER_RCM, capi.SWE_REORDER_HILBERT):
+        P = capi.mesh_preprocess(mi.nodes, mi.tris, r)
+        perm, code, ln = P["perm"], P["code"], P["ln"]
+        inv = np.empty(n, np.int64)
+        inv[perm] = np.arange(n)
+        nb = np.where(code >= 0, perm[np.where(code >= 0, code & 0x3FFFFFFF, 0)], -1)   # caller numbering
+        per_mode[r] = (nb[inv], ln[inv])
+        if r == capi.SWE_REORDER_NONE:
+            continue
+        a, b = np.arange(0, n - 1, 2), np.arange(1, n, 2)
+        shared = (code[a, 0] >= 0) & (code[b, 0] >= 0) & ((code[a, 0] & 0x3FFFFFFF) == b) & \
+                 ((code[b, 0] & 0x3FFFFFFF) == a)
+        assert shared.mean() > 0.85, (r, shared.mean())
+        w = shared[: len(shared) // 32 * 32].reshape(-1, 32).sum(axis=1)
+        assert np.mean((w == 0) | (w == 32)) > 0.95, r
+    ref_nb, ref_ln = per_mode[capi.SWE_REORDER_NONE]
+    for r in (capi.SWE_REORDER_RCM, capi.SWE_REORDER_HILBERT):
+        assert np.array_equal(per_mode[r][0], ref_nb)
+        assert np.array_equal(per_mode[r][1], ref_ln)
+
+
 def test_locality_orders_shrink_neighbour_distance():
     mi = mg.river(200, 40, seed=1, shuffle=True)
     spans = {}
