@@ -85,10 +85,11 @@ typedef struct swe_config {
     double h_dry;     /* wet/dry threshold, default 1e-6 m; finite and >= FLT_MIN (1.18e-38): a wet
                          depth is then a normal float, which the FP32 kernels and the FP64 friction
                          term's h^(-1/3) iteration (started from the float cube root) need */
-    int reorder;      /* SWE_REORDER_*, default SWE_REORDER_HILBERT.  With RCM or HILBERT the
-                         cells of the order are then arranged in pairs (2p, 2p+1) that share
-                         an edge, made the local edge 0 of both, wherever a greedy matching
-                         along the order finds one (cell_pairs uses them) */
+    int reorder;      /* SWE_REORDER_*, default SWE_REORDER_HILBERT.  FP32 meshes: with RCM or
+                         HILBERT the cells of the order are then arranged in pairs (2p, 2p+1)
+                         that share an edge, made the local edge 0 of both, wherever a greedy
+                         matching along the Hilbert order finds one (cell_pairs uses them);
+                         FP64 meshes keep the caller's local edge numbering */
     int block_size;   /* threads per block of the step kernel; 0 = library default */
     int graph_steps;  /* steps captured per CUDA graph; 0 = default, < 0 = no graphs */
     int device;       /* CUDA device ordinal, default 0 */
@@ -413,8 +414,9 @@ SWE_API int swe_riemann_flux(int precision, int64_t n, const void* hL, const voi
 
 /*
  * Runs only the host preprocessing of swe_mesh_create (validation,
- * orientation, neighbours, geometry, locality order) and returns its result
- * in the internal order, without touching a GPU.  Any output may be NULL.
+ * orientation, neighbours, geometry, locality order, and for SWE_FP32 the
+ * cell pairs) for a mesh of the given precision and returns its result in the
+ * internal order, without touching a GPU.  Any output may be NULL.
  *   perm     [n_tris] int64: caller index of internal cell c
  *   code     [n_tris][3] int32: per local edge j (edge from vertex j to j+1 of
  *            the counter-clockwise triangle), the internal index of the
@@ -426,8 +428,8 @@ SWE_API int swe_riemann_flux(int precision, int64_t n, const void* hL, const voi
  * Errors: as swe_mesh_create, without SWE_ECUDA.
  */
 SWE_API int swe_mesh_preprocess(const double* nodes, int64_t n_nodes, const int32_t* tris, int64_t n_tris,
-                                int reorder, int64_t* perm, int32_t* code, double* ln, double* inv_area,
-                                double* rin);
+                                int reorder, int precision, int64_t* perm, int32_t* code, double* ln,
+                                double* inv_area, double* rin);
 
 /*
  * Allocation-free CFL time step.  The paper has no counterpart: this entry

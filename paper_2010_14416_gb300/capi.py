@@ -103,7 +103,7 @@ def load():
         [vp] * 4 + [vp]
     lib.swe_riemann_flux_kind.argtypes = [C.c_int, C.c_int, C.c_int64] + [vp] * 6 + [C.c_double, C.c_double] + \
         [vp] * 4 + [vp]
-    lib.swe_mesh_preprocess.argtypes = [vp, C.c_int64, vp, C.c_int64, C.c_int, vp, vp, vp, vp, vp]
+    lib.swe_mesh_preprocess.argtypes = [vp, C.c_int64, vp, C.c_int64, C.c_int, C.c_int, vp, vp, vp, vp, vp]
     lib.swe_debug_code_ok.argtypes = [C.c_int32, C.c_int64, C.c_int]
     lib.swe_cfl_dt_noalloc.argtypes = [C.c_int, C.c_int64, vp, vp, vp, vp, C.c_double, C.c_double,
                                        C.c_double, vp, vp]
@@ -404,8 +404,9 @@ class Ensemble:
         return {k: getattr(inf, k) for k, _ in swe_info._fields_}
 
 
-def mesh_preprocess(nodes, tris, reorder=SWE_REORDER_HILBERT):
-    """Host-only preprocessing (no GPU): perm, code, ln, inv_area, rin in internal order."""
+def mesh_preprocess(nodes, tris, reorder=SWE_REORDER_HILBERT, precision=SWE_FP64):
+    """Host-only preprocessing (no GPU) of a mesh of the given precision: perm,
+    code, ln, inv_area, rin in internal order."""
     nodes = np.ascontiguousarray(nodes, dtype=np.float64).reshape(-1, 2)
     tris = np.ascontiguousarray(tris, dtype=np.int32).reshape(-1, 3)
     n = tris.shape[0]
@@ -415,7 +416,7 @@ def mesh_preprocess(nodes, tris, reorder=SWE_REORDER_HILBERT):
     ia = np.empty(n)
     rin = np.empty(n)
     check(load().swe_mesh_preprocess(nodes.ctypes.data, nodes.shape[0], tris.ctypes.data, n, int(reorder),
-                                     perm.ctypes.data, code.ctypes.data, ln.ctypes.data, ia.ctypes.data,
+                                     int(precision), perm.ctypes.data, code.ctypes.data, ln.ctypes.data, ia.ctypes.data,
                                      rin.ctypes.data))
     return dict(perm=perm, code=code, ln=ln, inv_area=ia, rin=rin)
 

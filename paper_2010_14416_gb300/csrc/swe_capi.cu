@@ -651,7 +651,8 @@ int swe_mesh_create(const double* nodes, int64_t n_nodes, const int32_t* tris, i
     std::string err;
     int rc;
     try {
-        rc = build_host_mesh(nodes, n_nodes, tris, n_tris, bathy, manning, c.reorder, m->hm, err);
+        rc = build_host_mesh(nodes, n_nodes, tris, n_tris, bathy, manning, c.reorder, c.precision == SWE_FP32, m->hm,
+                             err);
     } catch (const std::bad_alloc&) {
         rc = SWE_ENOMEM;
         err = "swe_mesh_create: out of host memory";
@@ -859,14 +860,16 @@ int swe_get_permutation(swe_mesh* m, int64_t* perm) {
 }
 
 int swe_mesh_preprocess(const double* nodes, int64_t n_nodes, const int32_t* tris, int64_t n_tris, int reorder,
-                        int64_t* perm, int32_t* code, double* ln, double* inv_area, double* rin) {
+                        int precision, int64_t* perm, int32_t* code, double* ln, double* inv_area, double* rin) {
     if (n_tris < 1) { set_error("swe_mesh_preprocess: empty mesh"); return SWE_EINVAL; }
+    if (precision != SWE_FP32 && precision != SWE_FP64) { set_error("swe_mesh_preprocess: bad precision"); return SWE_EINVAL; }
     HostMesh H;
     std::string err;
     int rc;
     try {
         std::vector<double> zeros((size_t)n_tris, 0.0);
-        rc = build_host_mesh(nodes, n_nodes, tris, n_tris, zeros.data(), zeros.data(), reorder, H, err);
+        rc = build_host_mesh(nodes, n_nodes, tris, n_tris, zeros.data(), zeros.data(), reorder, precision == SWE_FP32, H,
+                             err);
     } catch (const std::bad_alloc&) {
         rc = SWE_ENOMEM;
         err = "swe_mesh_preprocess: out of host memory";

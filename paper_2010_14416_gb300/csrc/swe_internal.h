@@ -43,8 +43,8 @@ struct HostMesh {
 
 // Builds the host mesh; returns SWE_OK or an error code with a message.
 int build_host_mesh(const double* nodes, int64_t n_nodes, const int32_t* tris, int64_t n_tris,
-                    const double* bathy, const double* manning, int reorder, HostMesh& out,
-                    std::string& err);
+                    const double* bathy, const double* manning, int reorder, bool pair_cells,
+                    HostMesh& out, std::string& err);
 
 // Locality orderings of the cells; each returns order[new] = old.
 std::vector<int64_t> order_hilbert(const std::vector<double>& cx, const std::vector<double>& cy);

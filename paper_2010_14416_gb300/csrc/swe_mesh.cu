@@ -207,7 +207,7 @@ std::vector<int64_t> place_pairs(const std::vector<int64_t>& order, const std::v
 }
 
 int build_host_mesh(const double* nodes, int64_t n_nodes, const int32_t* tris, int64_t n,
-                    const double* bathy, const double* manning, int reorder, HostMesh& M,
+                    const double* bathy, const double* manning, int reorder, bool pair_cells, HostMesh& M,
                     std::string& err) {
     if (!nodes || !tris || !bathy || !manning || n_nodes < 3 || n < 1) {
         err = "swe_mesh_create: null array or empty mesh";
@@ -300,14 +300,17 @@ int build_host_mesh(const double* nodes, int64_t n_nodes, const int32_t* tris, i
         err = "swe_mesh_create: unknown reorder mode";
         return SWE_EINVAL;
     }
-    // pairs of adjacent cells, matched along the Hilbert order whatever the
-    // mode, with their shared edge as local edge 0 of both: every mode numbers
-    // each cell's edges alike (so sums them in the same order); the RCM and
-    // Hilbert orders then place the pairs at (2p, 2p+1)
-    std::vector<int64_t> mate;
-    std::vector<int> rot;
-    match_cells(reorder == SWE_REORDER_HILBERT ? order : order_hilbert(cx, cy), nbr_old, t, mate, rot);
-    if (reorder != SWE_REORDER_NONE) order = place_pairs(order, mate);
+    // FP32 meshes: pairs of adjacent cells, matched along the Hilbert order
+    // whatever the mode, with their shared edge as local edge 0 of both: every
+    // mode numbers each cell's edges alike (so sums them in the same order);
+    // the RCM and Hilbert orders then place the pairs at (2p, 2p+1).  FP64
+    // meshes (no pair kernel) keep the caller's local edge numbering.
+    std::vector<int64_t> mate(n, -1);
+    std::vector<int> rot(n, 0);
+    if (pair_cells) {
+        match_cells(reorder == SWE_REORDER_HILBERT ? order : order_hilbert(cx, cy), nbr_old, t, mate, rot);
+        if (reorder != SWE_REORDER_NONE) order = place_pairs(order, mate);
+    }
     M.perm = order;
     M.inv.assign(n, 0);
     for (int64_t c = 0; c < n; ++c) M.inv[order[c]] = c;
@@ -333,9 +336,7 @@ int build_host_mesh(const double* nodes, int64_t n_nodes, const int32_t* tris, i
             // outward normal of a counter-clockwise triangle, times the length
             M.ln[6 * c + 2 * j] = dy;
             M.ln[6 * c + 2 * j + 1] = -dx;
-            const double L = std::sqrt(dx * dx + dy * dy);
-            M.len[3 * c + j] = L;
-            perim += L;
+            M.len[3 * c + j] = std::sqrt(dx * dx + dy * dy);
             const int64_t k = nbr_old[3 * o + jo];
             if (k >= 0) {
                 int32_t code = (int32_t)M.inv[k];
@@ -349,6 +350,8 @@ int build_host_mesh(const double* nodes, int64_t n_nodes, const int32_t* tris, i
         const double a2 = (nodes[2 * v1] - nodes[2 * v0]) * (nodes[2 * v2 + 1] - nodes[2 * v0 + 1]) -
                           (nodes[2 * v2] - nodes[2 * v0]) * (nodes[2 * v1 + 1] - nodes[2 * v0 + 1]);
         const double area = 0.5 * a2;
+        // the perimeter summed in the caller's edge order, whatever the rotation
+        for (int j = 0; j < 3; ++j) perim += M.len[3 * c + (j + 3 - rot[o]) % 3];
         M.inv_area[c] = 1.0 / area;
         M.rin[c] = 2.0 * area / perim;
         M.z[c] = bathy[o];
