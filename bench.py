@@ -495,9 +495,9 @@ def measure_ensemble(ctx, name, steps, warmup, ens_shape=None):
     if ens_shape:
         v = [int(x) for x in ens_shape.split(",")]
         keys = ("block_size", "min_blocks", "stages", "geometry_early", "activity", "edge_pass", "dynamic", "chunk",
-                "grid")
-        if len(v) != len(keys):
-            raise SystemExit("--ens-shape needs " + ",".join(keys))
+                "grid", "cell_pairs")
+        if len(v) not in (len(keys) - 1, len(keys)):
+            raise SystemExit("--ens-shape needs " + ",".join(keys[:-1]) + "[,cell_pairs]")
         shape = dict(zip(keys, v))
         ens.set_shape(**shape)
         shape["fixed"] = True
@@ -550,7 +550,8 @@ def measure_ensemble(ctx, name, steps, warmup, ens_shape=None):
         "per_member_launches_default_shapes": {"value": ctx.ws * n * steps / (ms_default * 1e-3),
                                                "unit": "cell-updates/s", "ms_per_step": ms_default / steps,
                                                "speedup": ms_default / ms},
-        "gpu_launches": steps * (2 if shape.get("edge_pass") else 1),
+        # the edge pass and the split step launch two kernels per step
+        "gpu_launches": steps * (2 if shape.get("edge_pass") or shape.get("cell_pairs") else 1),
         "clocks": clk,
     }
     ens.close()
@@ -718,7 +719,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--members", type=int, default=256, help="ensemble workloads: number of members")
     ap.add_argument("--ens-shape", default=None,
-                    help="ensemble workloads: block,min_blocks,stages,geometry_early,activity,edge_pass,dynamic,chunk,grid "
+                    help="ensemble workloads: block,min_blocks,stages,geometry_early,activity,edge_pass,dynamic,chunk,grid"
+                         "[,cell_pairs] "
                          "-- use this launch shape instead of autotuning (for profiling)")
     ap.add_argument("--shape", default=None,
                     help="mesh workloads: block,min_blocks,stages,geometry_early,activity,edge_pass,grid -- use "

@@ -372,8 +372,11 @@ typedef struct swe_ensemble swe_ensemble;
  * copied into one concatenated layout; the member meshes are not modified and
  * may be destroyed afterwards.  Each member keeps its own CFL time step and
  * time, continuing from its current state, and receives exactly the updates
- * the plain solver (swe_step) would give it.  The ensemble uses the first
- * member's stream until swe_ensemble_set_stream.
+ * the plain solver (swe_step) would give it.  FP32 ensembles place the
+ * members with at least half their cells wet (h > h_dry) at creation first in
+ * the layout, for the split step (swe_tune.cell_pairs); the placement changes
+ * no member's results.  The ensemble uses the first member's stream until
+ * swe_ensemble_set_stream.
  * Errors: SWE_EINVAL, SWE_ENOMEM, SWE_ECUDA.
  */
 SWE_API int swe_ensemble_create(swe_mesh* const* members, int n_members, swe_ensemble** out);
@@ -485,7 +488,11 @@ typedef struct swe_tune {
     double ms_before;        /* measured time per step of the shape in use before the call (ms;
                                 from the runoff, which always includes it, when one ran) */
     int n_candidates;        /* shapes timed */
-    int cell_pairs;          /* chosen pair mode (swe_config.cell_pairs); 0 for an ensemble */
+    int cell_pairs;          /* meshes: chosen pair mode (swe_config.cell_pairs); FP32 ensembles:
+                                1 = split step: the members placed first (mostly wet at
+                                creation) are updated by a cell-pair kernel (128-thread blocks,
+                                one pair of cells per thread, one resident wave), the others by
+                                the kernel of this shape, in the same step */
 } swe_tune;
 
 /*
@@ -519,12 +526,15 @@ SWE_API int swe_autotune(swe_mesh* mesh, int trial_steps, swe_tune* out);
  * dynamically scheduled shapes (dynamic 1, stages 1: FP32 (128, 8) with
  * geometry_early 0|1, (256, 4) with 0; FP64 (128|256, 1) with 0) with chunks
  * of 1 to 32 tiles; and the activity-mode shapes with dynamically taken
- * chunks (activity 1, dynamic 1) of 4 to 32 tiles; each over trial_steps
- * steps, twice; then, as for a mesh,
+ * chunks (activity 1, dynamic 1) of 4 to 32 tiles; for FP32 ensembles with
+ * members placed for the split step, every activity or dynamically scheduled
+ * shape also as the second kernel of a split step (cell_pairs 1); each over
+ * trial_steps steps, twice; then, as for a mesh,
  * a runoff of the shape in use and the (at most four) shapes within 5 % of the
  * fastest over max(32, 4 trial_steps) steps, keeping the first within 1 % of
  * the fastest there; then grids of half and two resident waves for the kept
- * shape, over as many steps, one of which replaces it when 2 % faster.
+ * shape (and for a split step, the cell-pair kernel's other shapes and two
+ * waves of it), over as many steps, one of which replaces it when 2 % faster.
  * Members' states, times and steps are unchanged by the call and by the
  * choice.  trial_steps 0 = 4.
  */
@@ -538,7 +548,9 @@ SWE_API int swe_ensemble_autotune(swe_ensemble* ens, int trial_steps, swe_tune* 
  * ensembles; edge_pass excludes activity and dynamic; activity with dynamic
  * needs chunks of at least 4 tiles), chunk a power of
  * two up to 4096 tiles,
- * grid the blocks to launch (0 = one resident wave); other fields are
+ * grid the blocks to launch (0 = one resident wave), cell_pairs 0 or 1 (a
+ * split step, FP32 without edge_pass; its cell-pair kernel runs one resident
+ * wave of (128, 8) blocks with geometry_early 1); other fields are
  * ignored.  Results do not depend on the shape.  Errors: SWE_EINVAL.
  */
 SWE_API int swe_ensemble_set_shape(swe_ensemble* ens, const swe_tune* shape);

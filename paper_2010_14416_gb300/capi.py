@@ -392,10 +392,12 @@ class Ensemble:
         return {k: getattr(t, k) for k, _ in swe_tune._fields_}
 
     def set_shape(self, block_size, min_blocks, stages=1, geometry_early=0, activity=0, chunk=4, grid=0,
-                  edge_pass=0, dynamic=0):
-        """Sets the batched kernel's launch shape (see swe_ensemble_set_shape)."""
+                  edge_pass=0, dynamic=0, cell_pairs=0):
+        """Sets the batched kernel's launch shape (see swe_ensemble_set_shape);
+        cell_pairs=1: the split step (FP32)."""
         t = swe_tune(block_size=block_size, min_blocks=min_blocks, stages=stages, geometry_early=geometry_early,
-                     activity=activity, edge_pass=edge_pass, dynamic=dynamic, chunk=chunk, grid=grid)
+                     activity=activity, edge_pass=edge_pass, dynamic=dynamic, chunk=chunk, grid=grid,
+                     cell_pairs=cell_pairs)
         check(load().swe_ensemble_set_shape(self._h, C.byref(t)))
 
     def info(self, member):

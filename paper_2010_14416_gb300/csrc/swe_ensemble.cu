@@ -14,6 +14,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <numeric>
 #include <new>
 #include <string>
 #include <tuple>
@@ -63,6 +64,13 @@ struct swe_ensemble {
     int64_t n_edges = 0;
     // dynamic chunks: three rotating per-step counters
     int dynamic = 0;
+    // split step (FP32): the members mostly wet at creation come first in the
+    // layout (pair_spans kEnsPad-cell spans) and run on the cell-pair kernel,
+    // the others on the kernel of the shape above, in the same step
+    int split = 0;
+    int64_t pair_spans = 0;
+    int pair_minb = 8, pair_geo = 1;
+    unsigned pair_grid = 0;
     unsigned* sched = nullptr;
     int2* ecells = nullptr;
     void* eln = nullptr;
@@ -126,6 +134,16 @@ __global__ void ens_init_small_kernel(unsigned long long* small, const unsigned 
     }
 }
 
+// Cells of a member's state deeper than h_dry (the split step's placement).
+template <typename T>
+__global__ void count_wet_kernel(const V4<T>* __restrict__ s, long long n, T h_dry, unsigned long long* out) {
+    unsigned c = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        c += s[i].x > h_dry ? 1u : 0u;
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, (unsigned long long)c);
+}
+
 template <typename T>
 __global__ void ens_unpack_kernel(const V4<T>* __restrict__ s, const long long* __restrict__ perm, long long base,
                                   T* __restrict__ h, T* __restrict__ hu, T* __restrict__ hv, long long n) {
@@ -157,6 +175,8 @@ EnsArgs<T> ens_args(swe_ensemble* E, int64_t step_index) {
     a.value_ = E->value;
     a.n_active = E->n_active;
     a.n_total = E->n_total;
+    a.cell_lo = 0;
+    a.pair_spans = 0;
     a.chunk_log2 = E->chunk_log2;
     a.sched = E->sched;
     a.sched_slot = p3;
@@ -203,6 +223,12 @@ cudaError_t ens_launch(swe_ensemble* E, int64_t step_index, const EnsPhysics& ph
     EnsArgs<T> a = ens_args<T>(E, step_index);
     a.g = (T)ph.g;
     a.h_dry = (T)ph.h_dry;
+    if (E->split && E->pair_spans > 0) {   // the paired members, then the others from cell_lo on
+        a.pair_spans = (unsigned)E->pair_spans;
+        const cudaError_t e = Launch<T>::ensemble_step_pair(a, E->pair_minb, E->pair_geo, E->pair_grid, st);
+        if (e != cudaSuccess) return e;
+        a.cell_lo = E->pair_spans * kEnsPad;
+    }
     if (a.act_in)
         return Launch<T>::ensemble_step_act(a, E->block, E->min_blocks, E->geo_early, E->grid, st, E->dynamic);
     if (E->dynamic) return Launch<T>::ensemble_step_dyn(a, E->block, E->min_blocks, E->geo_early, E->grid, st);
@@ -223,16 +249,44 @@ template <typename T>
 int ens_build(swe_ensemble* E, swe_mesh* const* M) {
     const int nm = E->n_members;
     const size_t v4 = sizeof(V4<T>);
-    // offsets, padded to whole tiles
+    // FP32: the members with at least half their cells wet now come first in
+    // the layout (the split step's cell-pair kernel takes them); otherwise the
+    // members' order.  The placement changes no member's arithmetic.
+    std::vector<int> order(nm);
+    std::iota(order.begin(), order.end(), 0);
+    std::vector<char> wet_member(nm, 0);
+    if (sizeof(T) == 4) {
+        unsigned long long* d_cnt = nullptr;
+        cudaError_t e = cudaMalloc(&d_cnt, nm * sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, nm * sizeof(unsigned long long), E->stream);
+        for (int k = 0; k < nm && e == cudaSuccess; ++k) {
+            const long long n = M[k]->hm.n_cells;
+            const unsigned grid = (unsigned)std::min<long long>((n + 255) / 256, 1024);
+            count_wet_kernel<T><<<grid, 256, 0, E->stream>>>((const V4<T>*)M[k]->state[M[k]->nstep % 2], n,
+                                                              (T)E->h_dry, d_cnt + k);
+            e = cudaGetLastError();
+        }
+        std::vector<unsigned long long> cnt(nm, 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(cnt.data(), d_cnt, nm * sizeof(unsigned long long), cudaMemcpyDeviceToHost, E->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(E->stream);
+        if (d_cnt) cudaFree(d_cnt);
+        if (e != cudaSuccess) return efail(e, "swe_ensemble_create: wet cells");
+        for (int k = 0; k < nm; ++k) wet_member[k] = 2 * cnt[k] >= (unsigned long long)M[k]->hm.n_cells;
+        std::stable_partition(order.begin(), order.end(), [&](int k) { return wet_member[k] != 0; });
+    }
+    // offsets in layout order, padded to whole tiles
     E->base.resize(nm);
     E->n_cells.resize(nm);
     E->first_tile.resize(nm);
     int64_t off = 0;
-    for (int k = 0; k < nm; ++k) {
+    E->pair_spans = 0;
+    for (int k : order) {
         E->base[k] = off;
         E->n_cells[k] = M[k]->hm.n_cells;
         E->first_tile[k] = off / kEnsPad;
         off += (M[k]->hm.n_cells + kEnsPad - 1) / kEnsPad * kEnsPad;
+        if (wet_member[k]) E->pair_spans = off / kEnsPad;
     }
     E->n_total = off;
     E->n_tiles = off / kEnsPad;
@@ -355,6 +409,14 @@ int ens_build(swe_ensemble* E, swe_mesh* const* M) {
     e = ens_wave<T>(E, E->block, E->min_blocks, E->stages, E->geo_early, &wave);
     if (e != cudaSuccess) return efail(e, "swe_ensemble_create: occupancy");
     E->grid = (unsigned)std::min<long long>((long long)(E->n_total / E->block), wave);
+    if (sizeof(T) == 4) {   // the split step's cell-pair kernel: one resident wave
+        int per_sm = 0, sms = 0;
+        e = Launch<T>::ensemble_pair_resident_blocks(E->pair_minb, E->pair_geo, &per_sm);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, E->device);
+        if (e != cudaSuccess) return efail(e, "swe_ensemble_create: occupancy");
+        E->pair_grid = (unsigned)std::max<long long>(
+            1, std::min<long long>(E->pair_spans, (long long)std::max(per_sm, 1) * std::max(sms, 1)));
+    }
     E->cfl_host.assign(nm, -1.0);
     // FP64: the members' interior edges for the edge pass (the FP64 pipe bounds
     // the step, so evaluating each edge once pays; FP32 steps are bound by memory)
@@ -474,6 +536,10 @@ struct EnsShape {
     int activity;
     int edges;
     int dynamic;
+    // split step: the cell-pair kernel's (min_blocks, geometry early, grid) first
+    int split = 0;
+    int pair_minb = 8, pair_geo = 1;
+    unsigned pair_grid = 0;
 };
 
 template <typename T>
@@ -514,6 +580,14 @@ int ens_time_shapes(swe_ensemble* E, const std::vector<EnsShape>& cand, int tria
                 a.sched_slot = launch_no % 3;
                 a.sched_reset = (launch_no + 2) % 3;
                 ++launch_no;
+                a.cell_lo = 0;
+                a.pair_spans = 0;
+                if (sh.split && E->pair_spans > 0) {
+                    a.pair_spans = (unsigned)E->pair_spans;
+                    const cudaError_t pe = Launch<T>::ensemble_step_pair(a, sh.pair_minb, sh.pair_geo, sh.pair_grid, st);
+                    if (pe != cudaSuccess) return pe;
+                    a.cell_lo = E->pair_spans * kEnsPad;
+                }
                 if (sh.activity)
                     return Launch<T>::ensemble_step_act(a, sh.block, sh.min_blocks, sh.geo_early, sh.grid, st,
                                                         sh.dynamic);
@@ -541,8 +615,8 @@ int ens_time_shapes(swe_ensemble* E, const std::vector<EnsShape>& cand, int tria
 
 template <typename T>
 int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
-    const EnsShape before{E->block, E->min_blocks, E->stages,   E->geo_early, E->chunk_log2,
-                          E->grid,  E->activity,   E->edges,    E->dynamic};
+    const EnsShape before{E->block, E->min_blocks, E->stages, E->geo_early, E->chunk_log2, E->grid,
+                          E->activity, E->edges, E->dynamic, E->split, E->pair_minb, E->pair_geo, E->pair_grid};
     std::vector<EnsShape> cand{before};
     const bool with_act = E->n_total < kActivityMaxCells;
     if (with_act) {
@@ -560,7 +634,7 @@ int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
             const EnsShape sh{v[k][0], v[k][1], v[k][2], v[k][3], cl2, gr, 0, 0, 0};
             if (!(sh.block == before.block && sh.min_blocks == before.min_blocks && sh.stages == before.stages &&
                   sh.geo_early == before.geo_early && sh.chunk_log2 == before.chunk_log2 && sh.grid == before.grid &&
-                  !before.activity && !before.edges && !before.dynamic))
+                  !before.activity && !before.edges && !before.dynamic && !before.split))
                 cand.push_back(sh);
         }
     }
@@ -603,6 +677,31 @@ int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
         const long long wave = (long long)std::max(per_sm, 1) * std::max(sms, 1);
         const unsigned gr = (unsigned)std::max(1LL, std::min((long long)(E->n_total / x[k][0]), wave));
         for (int cl2 = 2; cl2 <= 6; ++cl2) cand.push_back({x[k][0], x[k][1], x[k][2], x[k][3], cl2, gr, 0, 1, 0});
+    }
+    // FP32 with members placed for the cell-pair kernel: every activity and
+    // dynamically scheduled shape also as the second kernel of a split step
+    int pq[8][2];
+    const int npq = E->pair_spans > 0 ? std::min(Launch<T>::ensemble_pair_variants(pq, 8), 8) : 0;
+    std::vector<unsigned> pair_wave(npq, 0);
+    for (int q = 0; q < npq; ++q) {
+        int per_sm = 0, sms = 0;
+        cudaError_t e = Launch<T>::ensemble_pair_resident_blocks(pq[q][0], pq[q][1], &per_sm);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, E->device);
+        if (e != cudaSuccess) return efail(e, "swe_ensemble_autotune: occupancy");
+        pair_wave[q] = (unsigned)std::max<long long>(
+            1, std::min<long long>(E->pair_spans, (long long)std::max(per_sm, 1) * std::max(sms, 1)));
+    }
+    if (npq > 0) {
+        const size_t n0 = cand.size();
+        for (size_t c = 1; c < n0; ++c)
+            if (cand[c].activity || cand[c].dynamic) {
+                EnsShape sh = cand[c];
+                sh.split = 1;
+                sh.pair_minb = pq[0][0];
+                sh.pair_geo = pq[0][1];
+                sh.pair_grid = pair_wave[0];
+                cand.push_back(sh);
+            }
     }
     void* scratch = nullptr;
     unsigned long long *small = nullptr, *act = nullptr;
@@ -667,9 +766,24 @@ int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
         const long long tiles = (long long)(E->n_total / b.block);
         for (long long gsz : {wave / 2, 2 * wave}) {
             const unsigned gr = (unsigned)std::max(1LL, std::min(tiles, gsz));
-            if (!rc && gr != b.grid)
-                cand2.push_back(
-                    {b.block, b.min_blocks, b.stages, b.geo_early, b.chunk_log2, gr, b.activity, b.edges, b.dynamic});
+            if (!rc && gr != b.grid) {
+                EnsShape sh = b;
+                sh.grid = gr;
+                cand2.push_back(sh);
+            }
+        }
+        // a split step: the other cell-pair kernel shapes, and two waves of the first
+        if (!rc && b.split) {
+            for (int q = 1; q < npq; ++q) {
+                EnsShape sh = b;
+                sh.pair_minb = pq[q][0];
+                sh.pair_geo = pq[q][1];
+                sh.pair_grid = pair_wave[q];
+                cand2.push_back(sh);
+            }
+            EnsShape sh = b;
+            sh.pair_grid = (unsigned)std::min<long long>(E->pair_spans, 2LL * pair_wave[0]);
+            if (sh.pair_grid != b.pair_grid) cand2.push_back(sh);
         }
         // grids of half and two waves for the kept shape, timed as long as the runoff
         if (!rc && !cand2.empty())
@@ -693,9 +807,13 @@ int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
     E->activity = pick.activity;
     E->edges = pick.edges;
     E->dynamic = pick.dynamic;
-    // the bytes describe the current state (the trials rewrote the next buffer with
-    // what the next step writes there); without activity they would go stale
-    E->act_valid = pick.activity != 0 && E->act[0] != nullptr;
+    E->split = pick.split;
+    E->pair_minb = pick.pair_minb;
+    E->pair_geo = pick.pair_geo;
+    E->pair_grid = pick.pair_grid;
+    // the activity bytes are rebuilt from the state before the next step: trials
+    // of split steps leave the paired members' next bytes unwritten
+    E->act_valid = false;
     E->chunk_log2 = pick.chunk_log2;
     E->grid = pick.grid;
     drop_graphs(E);
@@ -713,7 +831,7 @@ int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
         out->ms_best = ms_pick;
         out->ms_before = ms[0];
         out->n_candidates = (int)(cand.size() + cand2.size());
-        out->cell_pairs = 0;
+        out->cell_pairs = pick.split;
     }
     return SWE_OK;
 }
@@ -867,6 +985,11 @@ int swe_ensemble_set_shape(swe_ensemble* E, const swe_tune* shape) {
         set_error("swe_ensemble_set_shape: activity needs fewer than 2^29 cells");
         return SWE_EINVAL;
     }
+    if ((shape->cell_pairs != 0 && shape->cell_pairs != 1) ||
+        (shape->cell_pairs && (E->precision != SWE_FP32 || shape->edge_pass))) {
+        set_error("swe_ensemble_set_shape: cell_pairs (a split step) needs FP32 and no edge pass");
+        return SWE_EINVAL;
+    }
     EnsDeviceGuard dg(E->device);
     int per_sm = 0, sms = 0;
     cudaError_t e;
@@ -897,10 +1020,11 @@ int swe_ensemble_set_shape(swe_ensemble* E, const swe_tune* shape) {
     E->geo_early = shape->geometry_early;
     E->chunk_log2 = (int)cl2;
     E->grid = (unsigned)std::max(1LL, std::min(tiles, shape->grid > 0 ? (long long)shape->grid : wave));
-    if (E->activity != shape->activity) E->act_valid = false;
+    if (E->activity != shape->activity || E->split != shape->cell_pairs) E->act_valid = false;
     E->activity = shape->activity;
     E->edges = shape->edge_pass;
     E->dynamic = shape->dynamic;
+    E->split = shape->cell_pairs;   // the cell-pair kernel keeps its shape and one-wave grid
     if (E->dynamic) {   // counters from zero (earlier steps may have left them used)
         e = cudaMemsetAsync(E->sched, 0, 3 * sizeof(unsigned), E->stream);
         if (e != cudaSuccess) return efail(e, "swe_ensemble_set_shape: counters");

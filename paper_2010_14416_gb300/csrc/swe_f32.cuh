@@ -65,9 +65,13 @@ template <typename V>
 __device__ __forceinline__ V vmax(V a, V b) { return fmaxf(a, b); }
 
 // Wave speeds of two wet sides (Eq 19-25): the star depth by Eq 22 or Eq 23 as
-// Eq 21's h0 decides, the shock factors of Eq 20 and S*.
+// Eq 21's h0 decides, the shock factors of Eq 20, and S* as the quotient
+// num / den of Eq 25.  Here m_L = h_L (un_L - S_L) > 0 > m_R = h_R (un_R - S_R),
+// so den = m_R - m_L < 0 and S* >= 0 exactly when num <= 0: the flux needs
+// only that sign (Eq 24), and the quotient is formed only on request.
 template <typename V>
-__device__ __forceinline__ void wet_speeds(V hL, V unL, V hR, V unR, V aL, V aR, V g, V g2, V& SL, V& SR, V& Ss) {
+__device__ __forceinline__ void wet_speeds(V hL, V unL, V hR, V unR, V aL, V aR, V g, V g2, V& SL, V& SR, V& num,
+                                           V& den) {
     const V one = splat<V>(1.0f);
     const V rhL = rcp_(hL), rhR = rcp_(hR);
     const V hsum = add(hL, hR), asum = add(aL, aR);
@@ -84,7 +88,8 @@ __device__ __forceinline__ void wet_speeds(V hL, V unL, V hR, V unR, V aL, V aR,
     SL = fma(neg(aL), pL, unL);                                                                       // Eq 19
     SR = fma(aR, pR, unR);
     const V mL = mul(hL, sub(unL, SL)), mR = mul(hR, sub(unR, SR));
-    Ss = div_(fma(SL, mR, neg(mul(SR, mL))), sub(mR, mL));                                            // Eq 25
+    num = fma(SL, mR, neg(mul(SR, mL)));                                                              // Eq 25
+    den = sub(mR, mL);
 }
 
 // ---- Riemann flux in the edge-normal frame (Eq 14, 17-26) ------------------------------
@@ -106,8 +111,12 @@ __device__ __forceinline__ void riemann(V hL, V unL, V utL, V hR, V unR, V utR, 
     const bool wetL = gt(hL, h_dry), wetR = gt(hR, h_dry);
     const V aL = sqrt_(mul(g, hL)), aR = sqrt_(mul(g, hR));
     V SL, SR, Ss;
+    bool upL;   // S* >= 0: the tangential velocity of the left side (Eq 24)
     if (wetL && wetR) {
-        wet_speeds(hL, unL, hR, unR, aL, aR, g, g2, SL, SR, Ss);
+        V num, den;
+        wet_speeds(hL, unL, hR, unR, aL, aR, g, g2, SL, SR, num, den);
+        upL = le(num, zero);
+        if (speeds) Ss = div_(num, den);
     } else {
         if (!wetL && !wetR) {                                                 // both dry: no flux
             G1 = zero; G2 = zero; G3 = zero;
@@ -120,6 +129,7 @@ __device__ __forceinline__ void riemann(V hL, V unL, V utL, V hR, V unR, V utR, 
         SL = sel(wetL, SLr, SLl);
         SR = sel(wetL, SRr, SRl);
         Ss = sel(wetL, SRr, SLl);
+        upL = ge(Ss, zero);
     }
     const V qL = mul(hL, unL), qR = mul(hR, unR);
     const V PL = fma(qL, unL, mul(mul(g2, hL), hL));
@@ -135,7 +145,7 @@ __device__ __forceinline__ void riemann(V hL, V unL, V utL, V hR, V unR, V utR, 
         const V G3s = mul(fma(SR, qtL, fma(neg(SL), qtR, mul(ss, sub(mul(hR, utR), mul(hL, utL))))), r);
         G3 = sel(supL, qtL, sel(supR, qtR, G3s));
     } else {
-        G3 = mul(G1, sel(ge(Ss, zero), utL, utR));                                                    // Eq 24
+        G3 = mul(G1, sel(upL, utL, utR));                                                             // Eq 24
     }
     if (speeds) { speeds[0] = SL; speeds[1] = SR; speeds[2] = Ss; }
 }

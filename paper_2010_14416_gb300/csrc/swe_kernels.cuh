@@ -125,6 +125,11 @@ struct EnsArgs {
     const double* __restrict__ value_;
     unsigned long long* n_active;      // all members (diagnostic)
     long long n_total;                 // cells of the padded layout (a multiple of kEnsPad)
+    // split step: the first pair_spans kEnsPad-cell spans belong to the members
+    // the cell-pair kernel updates; the other kernels then update the cells
+    // from cell_lo = pair_spans * kEnsPad on (otherwise both are 0)
+    long long cell_lo;
+    unsigned pair_spans;
     int chunk_log2;                    // tiles per round-robin chunk = 2^chunk_log2
     // dynamic chunks (ensemble_step_kernel_dyn): three rotating counters; the
     // step takes chunks from sched[sched_slot] and zeroes sched[sched_reset]
@@ -1284,7 +1289,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel(const EnsArg
     static_assert(kEnsPad % BLOCK == 0, "a tile must not straddle two members");
     const long long G = gridDim.x, b = blockIdx.x;
     const int cl2 = a.chunk_log2;
-    const long long n_tiles = a.n_total / BLOCK;
+    const long long t_lo = a.cell_lo / BLOCK;              // tiles from cell_lo on
+    const long long n_tiles = (a.n_total - a.cell_lo) / BLOCK;
     const long long n_chunks = (n_tiles + (1LL << cl2) - 1) >> cl2;
     // this block's chunks: b, b + G, b + 2G, ... ; k counts its tiles
     const long long my_chunks = b < n_chunks ? (n_chunks - 1 - b) / G + 1 : 0;
@@ -1303,7 +1309,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel(const EnsArg
         for (int s = 0; s < STAGES - 1; ++s) {
             const long long tile = ens_tile_of(s, G, b, cl2);
             if (s < k_end && tile < n_tiles) {
-                const long long c = tile * BLOCK + tid;
+                const long long c = (tile + t_lo) * BLOCK + tid;
                 cp_async_record<sizeof(V4<T>)>(&st_own[s][tid], &a.s_in[c]);
                 cp_async_record<16>(&st_topo[s][tid], &a.topo[c]);
             }
@@ -1314,7 +1320,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel(const EnsArg
     for (long long k = 0; k < k_end; ++k) {
         const long long tile = ens_tile_of(k, G, b, cl2);
         if (tile >= n_tiles) break;                        // ragged last chunk
-        const long long cell0 = tile * BLOCK;
+        const long long cell0 = (tile + t_lo) * BLOCK;
         const int mk = a.tile_member[cell0 / kEnsPad];     // uniform across the block
         if (mk != member) {
             if (member >= 0) warp_min_publish<T>(cand, sm + a.slot_write);
@@ -1332,7 +1338,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel(const EnsArg
                 else atomicOr((unsigned*)(sm + 4), kStatusDry);
             }
         }
-        const long long i = tile * BLOCK + tid;
+        const long long i = cell0 + tid;
         V4<T> own;
         int4 tp;
         if constexpr (STAGES > 1) {
@@ -1340,7 +1346,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel(const EnsArg
             const long long nt = ens_tile_of(kn, G, b, cl2);
             const int fill = slot == 0 ? STAGES - 1 : slot - 1;
             if (kn < k_end && nt < n_tiles) {
-                const long long c = nt * BLOCK + tid;
+                const long long c = (nt + t_lo) * BLOCK + tid;
                 cp_async_record<sizeof(V4<T>)>(&st_own[fill][tid], &a.s_in[c]);
                 cp_async_record<16>(&st_topo[fill][tid], &a.topo[c]);
             }
@@ -1375,7 +1381,8 @@ template <typename T, int BLOCK, int MINB, bool GEO_EARLY>
 __global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel_dyn(const EnsArgs<T> a) {
     static_assert(kEnsPad % BLOCK == 0, "a tile must not straddle two members");
     const int cl2 = a.chunk_log2;
-    const long long n_tiles = a.n_total / BLOCK;
+    const long long t_lo = a.cell_lo / BLOCK;              // tiles from cell_lo on
+    const long long n_tiles = (a.n_total - a.cell_lo) / BLOCK;
     const unsigned n_chunks = (unsigned)((n_tiles + (1LL << cl2) - 1) >> cl2);
     const int tid = threadIdx.x;
     __shared__ unsigned s_chunk[2];
@@ -1395,7 +1402,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel_dyn(const En
         for (int q = 0; q < (1 << cl2); ++q) {
             const long long tile = t0 + q;
             if (tile >= n_tiles) break;                    // ragged last chunk
-            const long long cell0 = tile * BLOCK;
+            const long long cell0 = (tile + t_lo) * BLOCK;
             const int mk = a.tile_member[cell0 / kEnsPad];  // uniform across the block
             if (mk != member) {
                 if (member >= 0) warp_min_publish<T>(cand, sm + a.slot_write);
@@ -1447,7 +1454,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel_act(const En
     constexpr unsigned kNone = 0xFFFFFFFFu;
     const unsigned G = gridDim.x, b = blockIdx.x;
     const int cl2 = a.chunk_log2;                   // >= 2 with DYN (the host checks)
-    const unsigned n_tiles = (unsigned)(a.n_total / BLOCK);
+    const unsigned t_lo = (unsigned)(a.cell_lo / BLOCK);           // tiles from cell_lo on
+    const unsigned n_tiles = (unsigned)((a.n_total - a.cell_lo) / BLOCK);
     const unsigned n_chunks = (n_tiles + (1u << cl2) - 1) >> cl2;
     const unsigned my_chunks = b < n_chunks ? (n_chunks - 1 - b) / G + 1 : 0;
     const unsigned k_end = DYN ? kNone : my_chunks << cl2;
@@ -1467,11 +1475,11 @@ __global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel_act(const En
             const unsigned ch = s_ch[(k >> cl2) % 3];
             if (ch >= n_chunks) return kNone;
             const unsigned t = (ch << cl2) + (k & ((1u << cl2) - 1));
-            return t < n_tiles ? t * BLOCK + tid : kNone;
+            return t < n_tiles ? (t + t_lo) * BLOCK + tid : kNone;
         } else {
             if (k >= k_end) return kNone;
             const unsigned t = ((b + (k >> cl2) * G) << cl2) + (k & ((1u << cl2) - 1));
-            return t < n_tiles ? t * BLOCK + tid : kNone;
+            return t < n_tiles ? (t + t_lo) * BLOCK + tid : kNone;
         }
     };
     __shared__ V4<T> st_own[3][BLOCK];
@@ -1579,6 +1587,72 @@ __global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel_act(const En
     }
     cp_async_wait<0>();
     if (member >= 0) warp_min_publish<T>(cand, sm + a.slot_write);
+    active = __reduce_add_sync(0xffffffffu, active);
+    if ((tid & 31) == 0 && active) atomicAdd(a.n_active, (unsigned long long)active);
+}
+
+// ---- batched ensemble step over cell pairs (FP32) ------------------------------------
+// A split ensemble places the members that are mostly wet at creation first in
+// its layout; this kernel updates their spans [0, pair_spans), and one of the
+// other ensemble kernels the rest (from cell_lo on) in the same step.  A block
+// takes a contiguous run of spans (the wet members cost about the same per
+// cell, so equal runs balance, and a block changes member rarely); its thread
+// t updates the pair (2t, 2t+1) of the span (BLOCK pairs = kEnsPad cells)
+// exactly as step_kernel_pair does, so the members' results are those of the
+// plain solver bit for bit.
+template <int BLOCK, int MINB, bool GEO_EARLY>
+__global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel_pair(const EnsArgs<float> a) {
+    static_assert(2 * BLOCK == kEnsPad, "a block's pairs are one span");
+    const unsigned ns = a.pair_spans;
+    const unsigned lo = (unsigned)((unsigned long long)ns * blockIdx.x / gridDim.x);
+    const unsigned hi = (unsigned)((unsigned long long)ns * (blockIdx.x + 1) / gridDim.x);
+    const int tid = threadIdx.x;
+    __shared__ PairEdge slot[BLOCK];
+    volatile PairEdge* pe = &slot[tid];
+    unsigned active = 0u;
+    // runs of spans of one member: the member's step size, then its spans; the
+    // member's status block is addressed from its index where used
+    for (unsigned t = lo; t < hi;) {
+        const int mk = a.tile_member[t];       // uniform across the block
+        unsigned long long* sm = a.small + 8 * mk;
+        const WarpDt<float> wdt = warp_step_dt<float>(a.cfl[mk], (const double*)(sm + a.slot_read), nullptr);
+        if ((long long)t == a.member_first_tile[mk] && tid == 0) {
+            sm[a.slot_reset] = kInfBits;
+            if (wdt.have) *(double*)(sm + 3) += wdt.d;
+            else atomicOr((unsigned*)(sm + 4), kStatusDry);
+        }
+        if (!wdt.have) {
+            for (; t < hi && a.tile_member[t] == mk; ++t) {
+                const unsigned iA = t * kEnsPad + 2 * tid;
+                a.s_out[iA] = a.s_in[iA];
+                a.s_out[iA + 1] = a.s_in[iA + 1];
+            }
+            continue;
+        }
+        const float dt = wdt.t;
+        float cand = inf_of<float>();
+        for (; t < hi && a.tile_member[t] == mk; ++t) {
+            const unsigned iA = t * kEnsPad + 2 * tid, iB = iA + 1;
+            const V4<float> ownA = a.s_in[iA];
+            const int4 tpA = a.topo[iA];
+            const int cB = __ldg(&a.topo[iB].x);
+            const bool shared = tpA.x >= 0 && cB >= 0 && (unsigned)(tpA.x & kNbrMask) == iB &&
+                                (unsigned)(cB & kNbrMask) == iA;
+            int mode = shared ? kPairGive : kPairNone;
+            cand = min_nonneg(cand, update_cell_f32<GEO_EARLY, false, 1>(a, iA, ownA, tpA, dt, active,
+                                                                         a.small + 8 * mk + 5,
+                                                                         (unsigned*)(a.small + 8 * mk + 4), &mode,
+                                                                         pe));
+            const V4<float> ownB = a.s_in[iB];
+            const int4 tpB = a.topo[iB];
+            int modeB = mode == kPairGiven ? kPairTake : kPairNone;
+            cand = min_nonneg(cand, update_cell_f32<GEO_EARLY, false, 2>(a, iB, ownB, tpB, dt, active,
+                                                                         a.small + 8 * mk + 5,
+                                                                         (unsigned*)(a.small + 8 * mk + 4), &modeB,
+                                                                         pe));
+        }
+        warp_min_publish<float>(cand, a.small + 8 * mk + a.slot_write);
+    }
     active = __reduce_add_sync(0xffffffffu, active);
     if ((tid & 31) == 0 && active) atomicAdd(a.n_active, (unsigned long long)active);
 }
@@ -1692,6 +1766,12 @@ struct Launch {
     static int ensemble_dyn_variants(int (*out)[3], int max);
     static cudaError_t ensemble_edge_resident_blocks(int block, int min_blocks, int stages, int geo_early,
                                                      int* per_sm);
+    // cell-pair kernel of a split ensemble (FP32 only): 128-thread blocks, compiled
+    // (min_blocks, geo_early) shapes
+    static cudaError_t ensemble_step_pair(const EnsArgs<T>& a, int min_blocks, int geo_early, unsigned grid,
+                                          cudaStream_t st);
+    static cudaError_t ensemble_pair_resident_blocks(int min_blocks, int geo_early, int* per_sm);
+    static int ensemble_pair_variants(int (*out)[2], int max);
     static void ensemble_default(int* block, int* min_blocks, int* stages, int* geo_early);
     static int default_min_blocks(int block);
     static cudaError_t dt(const V4<T>* s, const V4<T>* geoB, long long n, T g, T h_dry,

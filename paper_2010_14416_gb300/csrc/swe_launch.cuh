@@ -154,7 +154,9 @@ int Launch<T>::step_variants(int (*out)[4], int max) {
 // measured slower (2 or 3 pairs ahead: 0.285-0.353 ms, spilling at 64
 // registers), and so did copying the second cell's records, or those and the
 // next pair's first, into shared memory during the first cell's update
-// (0.272 and 0.280 ms): the pair kernel has none.
+// (0.272 and 0.280 ms), and so did an L2 bulk prefetch of each warp's records
+// one or two grid-stride iterations ahead (0.275 and 0.282 against 0.265 ms at
+// 256 x 4): the pair kernel has none.
 #define SWE_PAIR_VARIANTS_F32(X) X(256, 4, 0, 1) X(256, 4, 1, 1) X(128, 8, 1, 1) X(128, 8, 0, 1) X(256, 3, 1, 1)
 
 template <typename T>
@@ -482,6 +484,52 @@ int Launch<T>::ensemble_dyn_variants(int (*out)[3], int max) {
         SWE_ENS_DYN_VARIANTS_F64(SWE_LIST)
     }
 #undef SWE_LIST
+    return k;
+}
+
+// (min blocks per SM, geometry early) shapes of the split ensemble's
+// cell-pair kernel (128-thread blocks: 128 pairs are one kEnsPad span)
+#define SWE_ENS_PAIR_VARIANTS_F32(X) X(8, 1) X(8, 0) X(7, 1)
+
+template <typename T>
+cudaError_t Launch<T>::ensemble_step_pair(const EnsArgs<T>& a, int min_blocks, int geo_early, unsigned grid,
+                                          cudaStream_t st) {
+    if constexpr (sizeof(T) == 4) {
+        if (grid == 0) return cudaErrorInvalidValue;
+        if (a.pair_spans == 0) return cudaSuccess;
+#define SWE_LAUNCH(M, G) \
+    if (min_blocks == M && geo_early == G) {                                             \
+        ensemble_step_kernel_pair<128, M, G != 0><<<grid, 128, 0, st>>>(a);             \
+        return cudaGetLastError();                                                       \
+    }
+        SWE_ENS_PAIR_VARIANTS_F32(SWE_LAUNCH)
+#undef SWE_LAUNCH
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t Launch<T>::ensemble_pair_resident_blocks(int min_blocks, int geo_early, int* per_sm) {
+    if constexpr (sizeof(T) == 4) {
+#define SWE_OCC(M, G) \
+    if (min_blocks == M && geo_early == G)                                               \
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, ensemble_step_kernel_pair<128, M, G != 0>, 128, 0);
+        SWE_ENS_PAIR_VARIANTS_F32(SWE_OCC)
+#undef SWE_OCC
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+int Launch<T>::ensemble_pair_variants(int (*out)[2], int max) {
+    int k = 0;
+    if constexpr (sizeof(T) == 4) {
+#define SWE_LIST(M, G) \
+    if (k < max) { out[k][0] = M; out[k][1] = G; } \
+    ++k;
+        SWE_ENS_PAIR_VARIANTS_F32(SWE_LIST)
+#undef SWE_LIST
+    }
     return k;
 }
 
