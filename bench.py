@@ -73,7 +73,7 @@ WORKLOADS = {
 }
 
 
-MEMBERS = [256]
+MEMBERS = [256, "all"]   # ensemble workloads: number of members, which of them
 
 
 def _peak_clock():
@@ -321,12 +321,17 @@ def _hbm_roofline(wl, n, kernel_ms, active_frac, activity, name, shape, peak, pe
     (traffic_frac), and the dense per-cell model for reference."""
     ab = ALG_BYTES[wl["precision"]]
     rec = 16 if wl["precision"] == "f32" else 32
-    act_bytes = 2 if activity else 0
+    # activity kernels read a cell's byte and the previous step's, and clear the latter
+    act_bytes = 3 if activity else 0
     # an active cell reads its state, topology and geometry records and writes
     # its state; a quiet cell (dry, dry neighbours, no inflow/stage edge)
-    # needs no geometry, and with activity bytes no topology either
+    # needs no geometry, and with activity bytes no topology either, nor a
+    # store when it was quiet in the previous step too (its state is then in
+    # place; one that is written moves another record, so this is the lower
+    # bound of the layout's bytes and the fraction is the conservative one)
+    quiet_bytes = rec + act_bytes if activity else 2 * rec + 16
     layout_bytes = n * (active_frac * (4 * rec + 16 + (0 if wl["precision"] == "f32" else 8) + act_bytes) +
-                        (1 - active_frac) * (2 * rec + (act_bytes if act_bytes else 16)))
+                        (1 - active_frac) * quiet_bytes)
     s = kernel_ms * 1e-3
     traffic = _traffic(name, shape)
     dense = ab * n / s / 1e9
@@ -335,10 +340,13 @@ def _hbm_roofline(wl, n, kernel_ms, active_frac, activity, name, shape, peak, pe
             "traffic_frac": (traffic / s / 1e9 / peak) if traffic else None,
             "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
             "bytes_per_launch": layout_bytes, "active_cell_fraction": active_frac,
-            "bytes_per_active_cell": 4 * rec + 16 + act_bytes, "bytes_per_quiet_cell": 2 * rec + (act_bytes or 16),
+            "bytes_per_active_cell": 4 * rec + 16 + (0 if wl["precision"] == "f32" else 8) + act_bytes,
+            "bytes_per_quiet_cell": quiet_bytes,
             "dense_model_bytes_per_cell": ab, "dense_model_frac": dense / peak,
             "note": "achieved/frac: the bytes this launch's kernel must move at the measured fraction of cells "
-                    "that run the flux path (bytes_per_active_cell, bytes_per_quiet_cell); traffic_frac: ncu "
+                    "that run the flux path (bytes_per_active_cell, bytes_per_quiet_cell; with activity bytes a "
+                    "quiet cell quiet in the previous step too needs no store, and one that is written moves "
+                    "another state record); traffic_frac: ncu "
                     "DRAM bytes per launch of the same kernel source and shape; dense_model_frac: "
                     f"{ab} B for every cell, which a quiet cell (dry among dry neighbours) does not need, so it "
                     "exceeds 1 on a mostly dry mesh"}
@@ -481,6 +489,8 @@ def measure_ensemble(ctx, name, steps, warmup, ens_shape=None):
     prec = capi.SWE_FP32 if wl["precision"] == "f32" else capi.SWE_FP64
     npdt = np.float32 if prec == capi.SWE_FP32 else np.float64
     mis = ctx.make_input(name)
+    if MEMBERS[1] != "all":   # the canal (even) or river (odd) members alone, for profiling
+        mis = [mi for mi in mis if (mi.meta["member"] % 2 == 1) == (MEMBERS[1] == "river")]
     meshes = []
     for mi in mis:
         m = capi.Mesh(mi.nodes, mi.tris, mi.z, mi.manning, precision=prec, device=ctx.local)
@@ -495,9 +505,9 @@ def measure_ensemble(ctx, name, steps, warmup, ens_shape=None):
     if ens_shape:
         v = [int(x) for x in ens_shape.split(",")]
         keys = ("block_size", "min_blocks", "stages", "geometry_early", "activity", "edge_pass", "dynamic", "chunk",
-                "grid", "cell_pairs")
-        if len(v) not in (len(keys) - 1, len(keys)):
-            raise SystemExit("--ens-shape needs " + ",".join(keys[:-1]) + "[,cell_pairs]")
+                "grid", "cell_pairs", "queue")
+        if len(v) not in (len(keys) - 2, len(keys) - 1, len(keys)):
+            raise SystemExit("--ens-shape needs " + ",".join(keys[:-2]) + "[,cell_pairs[,queue]]")
         shape = dict(zip(keys, v))
         ens.set_shape(**shape)
         shape["fixed"] = True
@@ -537,7 +547,8 @@ def measure_ensemble(ctx, name, steps, warmup, ens_shape=None):
         "n_gpus": ctx.ws, "steps": steps, "warmup": warm_total, "ms_per_step": kernel_ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": wl["precision"],
         "data": "synthetic",
-        "config": {"workload": wl["desc"], "cells": n, "members": len(mis), "parallelism": f"replicas{ctx.ws}",
+        "config": {"workload": wl["desc"] + ("" if MEMBERS[1] == "all" else f" (the {MEMBERS[1]} members only)"),
+                   "cells": n, "members": len(mis), "parallelism": f"replicas{ctx.ws}",
                    "l2": "working set > 129 MB L2, no flush needed", "steps_before_timed": warm_total,
                    "launch_shape": _shape_key(shape), "autotune": shape,
                    "member_shapes": sorted({tuple(_shape_key(t)[:6]) + ((1,) if t.get("cell_pairs") else ())
@@ -718,9 +729,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--members", type=int, default=256, help="ensemble workloads: number of members")
+    ap.add_argument("--member-kind", choices=["all", "canal", "river"], default="all",
+                    help="ensemble workloads: all members, or only the canal (even) or river (odd) ones")
     ap.add_argument("--ens-shape", default=None,
                     help="ensemble workloads: block,min_blocks,stages,geometry_early,activity,edge_pass,dynamic,chunk,grid"
-                         "[,cell_pairs] "
+                         "[,cell_pairs[,queue]] "
                          "-- use this launch shape instead of autotuning (for profiling)")
     ap.add_argument("--shape", default=None,
                     help="mesh workloads: block,min_blocks,stages,geometry_early,activity,edge_pass,grid -- use "
@@ -735,6 +748,7 @@ def main():
     if args.impl == "reference":
         return run_reference(args, name)
     MEMBERS[0] = args.members
+    MEMBERS[1] = args.member_kind
     subrecords = not explicit and not args.no_subrecords
     return run_gpu(args, name, subrecords)
 

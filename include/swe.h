@@ -493,6 +493,11 @@ typedef struct swe_tune {
                                 creation) are updated by a cell-pair kernel (128-thread blocks,
                                 one pair of cells per thread, one resident wave), the others by
                                 the kernel of this shape, in the same step */
+    int queue;               /* FP32 ensembles with activity: 1 = each warp gathers the cells that
+                                run the flux path into a queue in shared memory and updates them
+                                32 at a time (full warps where wet cells are scattered), the
+                                quiet cells at once; compiled (block_size, min_blocks,
+                                geometry_early): (128, 7, 0|1), (128, 6, 1); 0 otherwise */
 } swe_tune;
 
 /*
@@ -526,7 +531,9 @@ SWE_API int swe_autotune(swe_mesh* mesh, int trial_steps, swe_tune* out);
  * dynamically scheduled shapes (dynamic 1, stages 1: FP32 (128, 8) with
  * geometry_early 0|1, (256, 4) with 0; FP64 (128|256, 1) with 0) with chunks
  * of 1 to 32 tiles; and the activity-mode shapes with dynamically taken
- * chunks (activity 1, dynamic 1) of 4 to 32 tiles; for FP32 ensembles with
+ * chunks (activity 1, dynamic 1) of 4 to 32 tiles; for FP32 ensembles the
+ * activity shapes with per-warp queues (queue 1) with either chunk order; for
+ * FP32 ensembles with
  * members placed for the split step, every activity or dynamically scheduled
  * shape also as the second kernel of a split step (cell_pairs 1); each over
  * trial_steps steps, twice; then, as for a mesh,
@@ -550,7 +557,8 @@ SWE_API int swe_ensemble_autotune(swe_ensemble* ens, int trial_steps, swe_tune* 
  * two up to 4096 tiles,
  * grid the blocks to launch (0 = one resident wave), cell_pairs 0 or 1 (a
  * split step, FP32 without edge_pass; its cell-pair kernel runs one resident
- * wave of (128, 8) blocks with geometry_early 1); other fields are
+ * wave of (128, 8) blocks with geometry_early 1), queue 0 or 1 (FP32 with
+ * activity); other fields are
  * ignored.  Results do not depend on the shape.  Errors: SWE_EINVAL.
  */
 SWE_API int swe_ensemble_set_shape(swe_ensemble* ens, const swe_tune* shape);

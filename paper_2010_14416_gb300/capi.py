@@ -63,7 +63,7 @@ class swe_tune(C.Structure):
     _fields_ = [("block_size", C.c_int), ("min_blocks", C.c_int), ("stages", C.c_int), ("geometry_early", C.c_int),
                 ("activity", C.c_int), ("edge_pass", C.c_int), ("dynamic", C.c_int), ("chunk", C.c_int),
                 ("grid", C.c_int64), ("cells_per_thread", C.c_double), ("ms_best", C.c_double),
-                ("ms_before", C.c_double), ("n_candidates", C.c_int), ("cell_pairs", C.c_int)]
+                ("ms_before", C.c_double), ("n_candidates", C.c_int), ("cell_pairs", C.c_int), ("queue", C.c_int)]
 
 
 class SWEError(RuntimeError):
@@ -392,12 +392,12 @@ class Ensemble:
         return {k: getattr(t, k) for k, _ in swe_tune._fields_}
 
     def set_shape(self, block_size, min_blocks, stages=1, geometry_early=0, activity=0, chunk=4, grid=0,
-                  edge_pass=0, dynamic=0, cell_pairs=0):
+                  edge_pass=0, dynamic=0, cell_pairs=0, queue=0):
         """Sets the batched kernel's launch shape (see swe_ensemble_set_shape);
-        cell_pairs=1: the split step (FP32)."""
+        cell_pairs=1: the split step, queue=1: per-warp queues (FP32)."""
         t = swe_tune(block_size=block_size, min_blocks=min_blocks, stages=stages, geometry_early=geometry_early,
                      activity=activity, edge_pass=edge_pass, dynamic=dynamic, chunk=chunk, grid=grid,
-                     cell_pairs=cell_pairs)
+                     cell_pairs=cell_pairs, queue=queue)
         check(load().swe_ensemble_set_shape(self._h, C.byref(t)))
 
     def info(self, member):

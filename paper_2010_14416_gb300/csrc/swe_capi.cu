@@ -516,8 +516,11 @@ int init_activity(swe_mesh* m) {
         m->device_bytes += 3 * len;
     }
     const int p3 = (int)(m->nstep % 3);
-    e = cudaMemsetAsync(m->act[p3], 0, m->act_len, m->stream);
+    e = cudaMemsetAsync(m->act[p3], 2, m->act_len, m->stream);   // bit 1: rebuilt (act_init_kernel)
     if (e == cudaSuccess) e = cudaMemsetAsync(m->act[(p3 + 1) % 3], 0, m->act_len, m->stream);
+    // the previous step's bytes: all 1, so the next step writes every cell's
+    // state (its output buffer holds no step's result yet)
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->act[(p3 + 2) % 3], 1, m->act_len, m->stream);
     if (e == cudaSuccess)
         e = m->cfg.precision == SWE_FP32
                 ? Launch<float>::act_init((const V4<float>*)m->state[m->nstep % 2], m->topo, n, (float)m->cfg.h_dry,

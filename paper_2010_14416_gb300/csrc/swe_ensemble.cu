@@ -68,6 +68,8 @@ struct swe_ensemble {
     // layout (pair_spans kEnsPad-cell spans) and run on the cell-pair kernel,
     // the others on the kernel of the shape above, in the same step
     int split = 0;
+    // activity kernel with per-warp queues of the cells that run the flux path
+    int queue = 0;
     int64_t pair_spans = 0;
     int pair_minb = 8, pair_geo = 1;
     unsigned pair_grid = 0;
@@ -230,7 +232,8 @@ cudaError_t ens_launch(swe_ensemble* E, int64_t step_index, const EnsPhysics& ph
         a.cell_lo = E->pair_spans * kEnsPad;
     }
     if (a.act_in)
-        return Launch<T>::ensemble_step_act(a, E->block, E->min_blocks, E->geo_early, E->grid, st, E->dynamic);
+        return Launch<T>::ensemble_step_act(a, E->block, E->min_blocks, E->geo_early, E->grid, st, E->dynamic,
+                                            E->queue);
     if (E->dynamic) return Launch<T>::ensemble_step_dyn(a, E->block, E->min_blocks, E->geo_early, E->grid, st);
     return Launch<T>::ensemble_step(a, E->block, E->min_blocks, E->stages, E->geo_early, E->grid, st);
 }
@@ -466,8 +469,10 @@ int ens_init_activity(swe_ensemble* E) {
         E->device_bytes += 3 * len;
     }
     const int p3 = (int)(E->nstep % 3);
-    e = cudaMemsetAsync(E->act[p3], 0, E->act_len, E->stream);
+    e = cudaMemsetAsync(E->act[p3], 2, E->act_len, E->stream);   // bit 1: rebuilt (act_init_kernel)
     if (e == cudaSuccess) e = cudaMemsetAsync(E->act[(p3 + 1) % 3], 0, E->act_len, E->stream);
+    // the previous step's bytes: all 1, so the next step writes every cell's state
+    if (e == cudaSuccess) e = cudaMemsetAsync(E->act[(p3 + 2) % 3], 1, E->act_len, E->stream);
     if (e == cudaSuccess)
         e = Launch<T>::act_init((const V4<T>*)E->state[E->nstep % 2], E->topo, E->n_total, (T)E->h_dry, E->act[p3],
                                 E->stream);
@@ -540,6 +545,7 @@ struct EnsShape {
     int split = 0;
     int pair_minb = 8, pair_geo = 1;
     unsigned pair_grid = 0;
+    int queue = 0;   // activity kernel with per-warp queues (FP32)
 };
 
 template <typename T>
@@ -590,7 +596,7 @@ int ens_time_shapes(swe_ensemble* E, const std::vector<EnsShape>& cand, int tria
                 }
                 if (sh.activity)
                     return Launch<T>::ensemble_step_act(a, sh.block, sh.min_blocks, sh.geo_early, sh.grid, st,
-                                                        sh.dynamic);
+                                                        sh.dynamic, sh.queue);
                 if (sh.dynamic)
                     return Launch<T>::ensemble_step_dyn(a, sh.block, sh.min_blocks, sh.geo_early, sh.grid, st);
                 return Launch<T>::ensemble_step(a, sh.block, sh.min_blocks, sh.stages, sh.geo_early, sh.grid, st);
@@ -616,7 +622,8 @@ int ens_time_shapes(swe_ensemble* E, const std::vector<EnsShape>& cand, int tria
 template <typename T>
 int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
     const EnsShape before{E->block, E->min_blocks, E->stages, E->geo_early, E->chunk_log2, E->grid,
-                          E->activity, E->edges, E->dynamic, E->split, E->pair_minb, E->pair_geo, E->pair_grid};
+                          E->activity, E->edges, E->dynamic, E->split, E->pair_minb, E->pair_geo, E->pair_grid,
+                          E->queue};
     std::vector<EnsShape> cand{before};
     const bool with_act = E->n_total < kActivityMaxCells;
     if (with_act) {
@@ -655,6 +662,27 @@ int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
         const long long wave_d = (long long)std::max(per_sm_d, 1) * std::max(sms, 1);
         const unsigned gr_d = (unsigned)std::max(1LL, std::min((long long)(E->n_total / w[k][0]), wave_d));
         for (int cl2 = 2; cl2 <= 5; ++cl2) cand.push_back({w[k][0], w[k][1], 3, w[k][2], cl2, gr_d, 1, 0, 1});
+    }
+    // FP32: the activity kernel with per-warp queues of the cells that run the
+    // flux path, round-robin and dynamic chunks
+    int wq[8][3];
+    const int nwq = with_act ? std::min(Launch<T>::ensemble_actq_variants(wq, 8), 8) : 0;
+    for (int k = 0; k < nwq; ++k) {
+        int sms = 0;
+        cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, E->device);
+        for (int dyn = 0; dyn <= 1 && e == cudaSuccess; ++dyn) {
+            int per_sm = 0;
+            e = Launch<T>::ensemble_act_resident_blocks(wq[k][0], wq[k][1], wq[k][2], &per_sm, dyn, 1);
+            if (e != cudaSuccess) break;
+            const long long wave = (long long)std::max(per_sm, 1) * std::max(sms, 1);
+            const unsigned gr = (unsigned)std::max(1LL, std::min((long long)(E->n_total / wq[k][0]), wave));
+            for (int cl2 = 2; cl2 <= (dyn ? 5 : 6); ++cl2) {
+                EnsShape sh{wq[k][0], wq[k][1], 3, wq[k][2], cl2, gr, 1, 0, dyn};
+                sh.queue = 1;
+                cand.push_back(sh);
+            }
+        }
+        if (e != cudaSuccess) return efail(e, "swe_ensemble_autotune: occupancy");
     }
     int y[16][3];
     const int ny = std::min(Launch<T>::ensemble_dyn_variants(y, 16), 16);
@@ -753,7 +781,7 @@ int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
         if (b.activity || b.edges || b.dynamic) {
             int per_sm = 0, sms = 0;
             e = b.activity  ? Launch<T>::ensemble_act_resident_blocks(b.block, b.min_blocks, b.geo_early, &per_sm,
-                                                                      b.dynamic)
+                                                                      b.dynamic, b.queue)
                 : b.dynamic ? Launch<T>::ensemble_dyn_resident_blocks(b.block, b.min_blocks, b.geo_early, &per_sm)
                             : Launch<T>::ensemble_edge_resident_blocks(b.block, b.min_blocks, b.stages, b.geo_early,
                                                                        &per_sm);
@@ -808,6 +836,7 @@ int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
     E->edges = pick.edges;
     E->dynamic = pick.dynamic;
     E->split = pick.split;
+    E->queue = pick.queue;
     E->pair_minb = pick.pair_minb;
     E->pair_geo = pick.pair_geo;
     E->pair_grid = pick.pair_grid;
@@ -832,6 +861,7 @@ int ens_autotune_t(swe_ensemble* E, int trial_steps, swe_tune* out) {
         out->ms_before = ms[0];
         out->n_candidates = (int)(cand.size() + cand2.size());
         out->cell_pairs = pick.split;
+        out->queue = pick.queue;
     }
     return SWE_OK;
 }
@@ -990,12 +1020,18 @@ int swe_ensemble_set_shape(swe_ensemble* E, const swe_tune* shape) {
         set_error("swe_ensemble_set_shape: cell_pairs (a split step) needs FP32 and no edge pass");
         return SWE_EINVAL;
     }
+    if ((shape->queue != 0 && shape->queue != 1) ||
+        (shape->queue && (E->precision != SWE_FP32 || !shape->activity))) {
+        set_error("swe_ensemble_set_shape: queue needs FP32 and activity");
+        return SWE_EINVAL;
+    }
     EnsDeviceGuard dg(E->device);
     int per_sm = 0, sms = 0;
     cudaError_t e;
     const int B = shape->block_size, M = shape->min_blocks, S = shape->stages, Gx = shape->geometry_early;
     if (E->precision == SWE_FP32) {
-        if (shape->activity) e = Launch<float>::ensemble_act_resident_blocks(B, M, Gx, &per_sm, shape->dynamic);
+        if (shape->activity)
+            e = Launch<float>::ensemble_act_resident_blocks(B, M, Gx, &per_sm, shape->dynamic, shape->queue);
         else if (shape->dynamic) e = Launch<float>::ensemble_dyn_resident_blocks(B, M, Gx, &per_sm);
         else e = Launch<float>::ensemble_resident_blocks(B, M, S, Gx, &per_sm);
     } else {
@@ -1025,6 +1061,7 @@ int swe_ensemble_set_shape(swe_ensemble* E, const swe_tune* shape) {
     E->edges = shape->edge_pass;
     E->dynamic = shape->dynamic;
     E->split = shape->cell_pairs;   // the cell-pair kernel keeps its shape and one-wave grid
+    E->queue = shape->queue;
     if (E->dynamic) {   // counters from zero (earlier steps may have left them used)
         e = cudaMemsetAsync(E->sched, 0, 3 * sizeof(unsigned), E->stream);
         if (e != cudaSuccess) return efail(e, "swe_ensemble_set_shape: counters");

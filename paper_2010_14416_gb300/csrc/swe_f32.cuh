@@ -75,12 +75,14 @@ __device__ __forceinline__ void wet_speeds(V hL, V unL, V hR, V unR, V aL, V aR,
     const V one = splat<V>(1.0f);
     const V rhL = rcp_(hL), rhR = rcp_(hR);
     const V hsum = add(hL, hR), asum = add(aL, aR);
-    const V h0 = mul(hsum, fma(mul(splat<V>(-0.25f), sub(unR, unL)), rcp_(asum), splat<V>(0.5f)));     // Eq 21
-    const V b = max0(fma(splat<V>(0.25f), sub(unL, unR), mul(splat<V>(0.5f), asum)));                  // Eq 22
+    // du = un_R - un_L; un_L - un_R is exactly -du (rounding is symmetric in sign)
+    const V du = sub(unR, unL);
+    const V h0 = mul(hsum, fma(mul(splat<V>(-0.25f), du), rcp_(asum), splat<V>(0.5f)));                // Eq 21
+    const V b = max0(fma(splat<V>(-0.25f), du, mul(splat<V>(0.5f), asum)));                            // Eq 22
     const V hs_rare = div_(mul(b, b), g);
     const V rh0 = rcp_(h0);                                                                           // Eq 23
     const V gL = sqrt_(mul(g2, add(rh0, rhL))), gR = sqrt_(mul(g2, add(rh0, rhR)));
-    const V hs_shock = div_(fma(hL, gL, fma(hR, gR, sub(unL, unR))), add(gL, gR));
+    const V hs_shock = div_(fma(hL, gL, fma(hR, gR, neg(du))), add(gL, gR));
     const V hs = sel(le(h0, vmin(hL, hR)), hs_rare, hs_shock);
     const V half_hs = mul(splat<V>(0.5f), hs);
     const V pL = sel(gt(hs, hL), mul(sqrt_(mul(half_hs, add(hs, hL))), rhL), one);                   // Eq 20

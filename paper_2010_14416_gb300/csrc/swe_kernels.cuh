@@ -1165,18 +1165,28 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_kernel_act(const StepArgs<T>
         __shared__ V4<T> st_own[NS][BLOCK];
         __shared__ int4 st_topo[2][BLOCK];
         __shared__ unsigned st_act[NS][BLOCK / 4];  // 32 activity bytes per warp per stage
+        __shared__ unsigned st_prev[NS][BLOCK / 4]; // and the previous step's (act_clear) bytes
         const T dt = wdt.t;
         // warp w of the block owns st_act[.][8 w .. 8 w + 7]; lanes 0..7 copy 4 bytes each
         auto act_copy = [&](int slot, unsigned c) {
             const unsigned base = c - lane;
-            if (lane < 8 && base < n)
+            if (lane < 8 && base < n) {
                 asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(
                                  (unsigned)__cvta_generic_to_shared(&st_act[slot][warp * 8 + lane])),
                              "l"(a.act_in + base + 4 * lane)
                              : "memory");
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(
+                                 (unsigned)__cvta_generic_to_shared(&st_prev[slot][warp * 8 + lane])),
+                             "l"(a.act_clear + base + 4 * lane)
+                             : "memory");
+            }
         };
+        // bit 0: the cell runs the flux path in this step (bit 0 of its byte);
+        // bit 1: the previous step's byte is not 0 (the cell ran the flux path
+        // then, or the bytes were rebuilt less than two steps ago)
         auto act_byte = [&](int slot) -> unsigned {
-            return ((const unsigned char*)&st_act[slot][warp * 8])[lane];
+            return (((const unsigned char*)&st_act[slot][warp * 8])[lane] & 1u) |
+                   (((const unsigned char*)&st_prev[slot][warp * 8])[lane] ? 2u : 0u);
         };
         // prologue: activity of c_0 .. c_PF and states of c_0 .. c_{PF-1}; then topology of c_0
 #pragma unroll
@@ -1188,7 +1198,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_kernel_act(const StepArgs<T>
         cp_async_wait<0>();
         __syncwarp();
         unsigned f_cur = act_byte(0);
-        if (f_cur && i0 < n) cp_async_record<16>(&st_topo[0][tid], &a.topo[i0]);
+        if ((f_cur & 1u) && i0 < n) cp_async_record<16>(&st_topo[0][tid], &a.topo[i0]);
         cp_async_commit();                                       // T_{-1}
         cp_async_commit();                                       // H_{-1} (empty: its copies were in the first group)
         int ks = 0, k2 = 0;  // k mod NS, k mod 2
@@ -1201,7 +1211,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_kernel_act(const StepArgs<T>
             __syncwarp();
             const unsigned f_next = act_byte(ks1);
             const unsigned c1 = c + stride, cp = c + PF * stride, cp1 = c + (PF + 1) * stride;
-            if (f_next && c1 < n) cp_async_record<16>(&st_topo[k2 ^ 1][tid], &a.topo[c1]);
+            if ((f_next & 1u) && c1 < n) cp_async_record<16>(&st_topo[k2 ^ 1][tid], &a.topo[c1]);
             cp_async_commit();                                   // T_k
             __syncwarp();                                        // every lane has read slot ks before it refills
             act_copy(ks, cp1);
@@ -1210,10 +1220,15 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_kernel_act(const StepArgs<T>
             cp_async_wait<3>();                                  // T_{k-1}: the topology of c_k
             if (c < n) {
                 const V4<T> own = st_own[ks][tid];
-                if (!f_cur) {
-                    V4<T> out;
-                    out.x = own.x; out.y = T(0); out.z = T(0); out.w = own.w;
-                    a.s_out[c] = out;
+                if (!(f_cur & 1u)) {
+                    // quiet: the new state is (h, 0, 0); if the cell was quiet in the
+                    // previous step too, the output buffer (the state of two steps
+                    // ago, itself dry at rest with the same h) holds it already
+                    if (f_cur & 2u) {
+                        V4<T> out;
+                        out.x = own.x; out.y = T(0); out.z = T(0); out.w = own.w;
+                        a.s_out[c] = out;
+                    }
                 } else {
                     const T r = update_cell<T, GEO_EARLY>(a, c, own, st_topo[k2][tid], dt, active, a.n_clamped,
                                                           a.status);
@@ -1243,8 +1258,11 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_kernel_act(const StepArgs<T>
     block_min_publish<BLOCK>(cand, a.dt_write, active, a.n_active);
 }
 
-// Activity bytes of a state (into a zeroed buffer): a wet cell marks itself and
-// its neighbours, a cell with an inflow/stage edge marks itself.
+// Activity bytes of a state (into a buffer filled with 2): a wet cell marks
+// itself and its neighbours, a cell with an inflow/stage edge marks itself.
+// Bit 0 says that the cell runs the flux path; bit 1, set in every rebuilt
+// byte, keeps the step after next from leaving a quiet state in place (its
+// output buffer holds the state that was set, not a step's result).
 template <typename T>
 __global__ void act_init_kernel(const V4<T>* __restrict__ s, const int4* __restrict__ topo, long long n, T h_dry,
                                 unsigned char* __restrict__ act) {
@@ -1252,11 +1270,11 @@ __global__ void act_init_kernel(const V4<T>* __restrict__ s, const int4* __restr
     if (c >= n) return;
     const bool wet = s[c].x > h_dry;
     const int4 tp = topo[c];
-    if (wet || (tp.w & kStaticBit)) act[c] = 1;
+    if (wet || (tp.w & kStaticBit)) act[c] = 3;
     if (wet) {   // (an out-of-range index is skipped here; the step's debug checks report it)
-        if (tp.x >= 0 && (tp.x & kNbrMask) < n) act[tp.x & kNbrMask] = 1;
-        if (tp.y >= 0 && (tp.y & kNbrMask) < n) act[tp.y & kNbrMask] = 1;
-        if (tp.z >= 0 && (tp.z & kNbrMask) < n) act[tp.z & kNbrMask] = 1;
+        if (tp.x >= 0 && (tp.x & kNbrMask) < n) act[tp.x & kNbrMask] = 3;
+        if (tp.y >= 0 && (tp.y & kNbrMask) < n) act[tp.y & kNbrMask] = 3;
+        if (tp.z >= 0 && (tp.z & kNbrMask) < n) act[tp.z & kNbrMask] = 3;
     }
 }
 
@@ -1448,7 +1466,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel_dyn(const En
 // cells (into chunk j + 1 at most, chunks being at least 4 tiles) always
 // finds its tile.  The slot refilled at the start of chunk j held chunk
 // j - 1, which nothing reads after that barrier.
-template <typename T, int BLOCK, int MINB, bool GEO_EARLY, bool DYN = false>
+template <typename T, int BLOCK, int MINB, bool GEO_EARLY, bool DYN = false, bool QUEUE = false>
 __global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel_act(const EnsArgs<T> a) {
     static_assert(kEnsPad % BLOCK == 0, "a tile must not straddle two members");
     constexpr unsigned kNone = 0xFFFFFFFFu;
@@ -1483,17 +1501,32 @@ __global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel_act(const En
         }
     };
     __shared__ V4<T> st_own[3][BLOCK];
-    __shared__ int4 st_topo[2][BLOCK];
+    __shared__ int4 st_topo[QUEUE ? 1 : 2][BLOCK];
+    // QUEUE: each warp's cells that run the flux path, a ring of 64 slots
+    __shared__ unsigned s_q[QUEUE ? BLOCK / 32 : 1][64];
+    unsigned qh = 0u, qt = 0u;                               // warp-uniform head and tail
+    // per warp: the 32 activity bytes of its cells in 3 stages (copied by lanes
+    // 0..7), and the previous step's (act_clear) bytes in a ring of 4 (lanes
+    // 8..15), so that the slot refilled in iteration k is never cell k's
     __shared__ unsigned st_act[3][BLOCK / 4];
-    auto act_copy = [&](int slot, unsigned c) {
-        if (lane < 8 && c != kNone)
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(
-                             (unsigned)__cvta_generic_to_shared(&st_act[slot][warp * 8 + lane])),
-                         "l"(a.act_in + (c - lane) + 4 * lane)
-                         : "memory");
+    __shared__ unsigned st_prev[4][BLOCK / 4];
+    auto act_copy = [&](int slot, int pslot, unsigned c) {
+        if (lane < 16 && c != kNone) {
+            const unsigned w0 = c - lane;   // the warp's first cell
+            const unsigned dst = lane < 8 ? (unsigned)__cvta_generic_to_shared(&st_act[slot][warp * 8 + lane])
+                                          : (unsigned)__cvta_generic_to_shared(&st_prev[pslot][warp * 8 + lane - 8]);
+            const unsigned char* src = lane < 8 ? a.act_in + w0 + 4 * lane : a.act_clear + w0 + 4 * (lane - 8);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
+        }
     };
+    // whether the cell runs the flux path (bit 0 of its byte)
     auto act_byte = [&](int slot) -> unsigned {
-        return ((const unsigned char*)&st_act[slot][warp * 8])[lane];
+        return ((const unsigned char*)&st_act[slot][warp * 8])[lane] & 1u;
+    };
+    // whether cell k's byte of the previous step is not 0 (it ran the flux path
+    // then, or the bytes were rebuilt less than two steps ago)
+    auto prev_byte = [&](unsigned k) -> unsigned {
+        return ((const unsigned char*)&st_prev[k & 3u][warp * 8])[lane];
     };
     int member = -1;
     unsigned long long* sm = nullptr;
@@ -1501,11 +1534,36 @@ __global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel_act(const En
     T dt = T(0);
     T cand = inf_of<T>();
     unsigned active = 0u;
+    // QUEUE: the full update of one queued cell (topology read here), its marks
+    auto run_queued = [&](unsigned cq) {
+        const V4<T> own = a.s_in[cq];
+        const int4 tp = a.topo[cq];
+        const T r = update_cell<T, GEO_EARLY>(a, cq, own, tp, dt, active, sm + 5, (unsigned*)(sm + 4));
+        cand = min_nonneg(cand, r);
+        const bool wet = r < inf_of<T>();
+        if (wet || (tp.w & kStaticBit)) a.act_next[cq] = 1;
+        if (wet) {
+            const int code[3] = {tp.x, tp.y, tp.z};
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                if (code[j] >= 0 && (!a.debug || code_ok(code[j], a.n_total, a.n_groups)))
+                    a.act_next[code[j] & kNbrMask] = 1;
+        }
+    };
+    // QUEUE: the queued cells left, on as many lanes (warp-uniform call)
+    auto flush = [&]() {
+        if constexpr (QUEUE) {
+            const unsigned nq = qh - qt;
+            if (lane < nq) run_queued(s_q[warp][(qt + lane) & 63]);
+            qt = qh;
+            __syncwarp();
+        }
+    };
     {
         const unsigned c0 = cell_of(0), c1 = cell_of(1), c2 = cell_of(2);
-        act_copy(0, c0);
-        act_copy(1, c1);
-        act_copy(2, c2);
+        act_copy(0, 0, c0);
+        act_copy(1, 1, c1);
+        act_copy(2, 2, c2);
         if (c0 != kNone) cp_async_record<sizeof(V4<T>)>(&st_own[0][tid], &a.s_in[c0]);
         if (c1 != kNone) cp_async_record<sizeof(V4<T>)>(&st_own[1][tid], &a.s_in[c1]);
         cp_async_commit();
@@ -1515,7 +1573,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel_act(const En
     unsigned f_cur = act_byte(0);
     {
         const unsigned c0 = cell_of(0);
-        if (f_cur && c0 != kNone) cp_async_record<16>(&st_topo[0][tid], &a.topo[c0]);
+        if (!QUEUE && f_cur && c0 != kNone) cp_async_record<16>(&st_topo[0][tid], &a.topo[c0]);
     }
     cp_async_commit();                                           // T_{-1}
     cp_async_commit();                                           // H_{-1} (empty)
@@ -1531,7 +1589,10 @@ __global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel_act(const En
         if (c == kNone) break;                                   // ragged last chunk (block-uniform)
         const int mk = a.tile_member[(c - tid) / kEnsPad];       // uniform across the block
         if (mk != member) {
-            if (member >= 0) warp_min_publish<T>(cand, sm + a.slot_write);
+            if (member >= 0) {
+                flush();   // with the member's own step and status block
+                warp_min_publish<T>(cand, sm + a.slot_write);
+            }
             cand = inf_of<T>();
             member = mk;
             sm = a.small + 8 * (long long)mk;
@@ -1549,10 +1610,10 @@ __global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel_act(const En
         __syncwarp();
         const unsigned f_next = act_byte(k3n);
         const unsigned c1 = cell_of(k + 1), c2 = cell_of(k + 2), c3 = cell_of(k + 3);
-        if (f_next && c1 != kNone) cp_async_record<16>(&st_topo[k2 ^ 1][tid], &a.topo[c1]);
+        if (!QUEUE && f_next && c1 != kNone) cp_async_record<16>(&st_topo[k2 ^ 1][tid], &a.topo[c1]);
         cp_async_commit();                                       // T_k
         __syncwarp();
-        act_copy(k3, c3);
+        act_copy(k3, (int)((k + 3u) & 3u), c3);
         if (c2 != kNone) cp_async_record<sizeof(V4<T>)>(&st_own[k3nn][tid], &a.s_in[c2]);
         cp_async_commit();                                       // H_k
         cp_async_wait<3>();                                      // T_{k-1}: the topology of c_k
@@ -1560,10 +1621,34 @@ __global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel_act(const En
         if (!have_dt) {
             a.s_out[c] = own;
             a.act_next[c] = (unsigned char)f_cur;
+        } else if constexpr (QUEUE) {
+            // quiet cells now; the others join the warp's queue, which runs
+            // whenever it holds a full warp of cells
+            if (!f_cur && prev_byte(k)) {   // quiet, and not in place already
+                V4<T> out;
+                out.x = own.x; out.y = T(0); out.z = T(0); out.w = own.w;
+                a.s_out[c] = out;
+            }
+            const bool runs = f_cur != 0u;
+            const unsigned m = __ballot_sync(0xffffffffu, runs);
+            if (runs) s_q[warp][(qh + __popc(m & ((1u << lane) - 1u))) & 63] = c;
+            qh += __popc(m);
+            __syncwarp();
+            if (qh - qt >= 32u) {
+                const unsigned cq = s_q[warp][(qt + lane) & 63];
+                qt += 32u;
+                __syncwarp();   // read before later appends reuse the slot
+                run_queued(cq);
+            }
         } else if (!f_cur) {
-            V4<T> out;
-            out.x = own.x; out.y = T(0); out.z = T(0); out.w = own.w;
-            a.s_out[c] = out;
+            // quiet: the new state is (h, 0, 0); if the cell was quiet in the
+            // previous step too, the output buffer (the state of two steps ago)
+            // holds it already
+            if (prev_byte(k)) {
+                V4<T> out;
+                out.x = own.x; out.y = T(0); out.z = T(0); out.w = own.w;
+                a.s_out[c] = out;
+            }
         } else {
             const T r = update_cell<T, GEO_EARLY>(a, c, own, st_topo[k2][tid], dt, active, sm + 5,
                                                   (unsigned*)(sm + 4));
@@ -1586,7 +1671,10 @@ __global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel_act(const En
         k2 ^= 1;
     }
     cp_async_wait<0>();
-    if (member >= 0) warp_min_publish<T>(cand, sm + a.slot_write);
+    if (member >= 0) {
+        flush();
+        warp_min_publish<T>(cand, sm + a.slot_write);
+    }
     active = __reduce_add_sync(0xffffffffu, active);
     if ((tid & 31) == 0 && active) atomicAdd(a.n_active, (unsigned long long)active);
 }
@@ -1751,11 +1839,14 @@ struct Launch {
     static int ensemble_variants(int (*out)[4], int max);
     // activity kernel of the ensemble: compiled (block, min_blocks, geo_early) shapes,
     // with round-robin (dynamic 0) or dynamically taken (dynamic 1) chunks
+    // (queue 1, FP32: the cells that run the flux path are gathered per warp into
+    // full warps first; compiled shapes from ensemble_actq_variants)
     static cudaError_t ensemble_step_act(const EnsArgs<T>& a, int block, int min_blocks, int geo_early,
-                                         unsigned grid, cudaStream_t st, int dynamic = 0);
+                                         unsigned grid, cudaStream_t st, int dynamic = 0, int queue = 0);
     static cudaError_t ensemble_act_resident_blocks(int block, int min_blocks, int geo_early, int* per_sm,
-                                                    int dynamic = 0);
+                                                    int dynamic = 0, int queue = 0);
     static int ensemble_act_variants(int (*out)[3], int max);
+    static int ensemble_actq_variants(int (*out)[3], int max);
     // edge pass of the ensemble (a.eflux set): edge kernel, then the cell pass of
     // one of its compiled (block, min_blocks, stages, geo_early) shapes
     static int ensemble_edge_variants(int (*out)[4], int max);

@@ -384,10 +384,28 @@ cudaError_t Launch<T>::ensemble_resident_blocks(int block, int min_blocks, int s
 #define SWE_ENS_ACT_VARIANTS_F32(X) X(128, 8, 1) X(128, 8, 0) X(256, 4, 1) X(256, 4, 0) X(128, 7, 1)
 #define SWE_ENS_ACT_VARIANTS_F64(X) X(256, 1, 0) X(128, 1, 0)
 
+// (block, min blocks per SM, geometry early) shapes of the ensemble's activity
+// kernel with per-warp queues of the cells that run the flux path (FP32); at
+// 8 blocks of 128 (64 registers) the queue's state spills 40-60 B
+#define SWE_ENS_ACTQ_VARIANTS_F32(X) X(128, 7, 1) X(128, 7, 0) X(128, 6, 1)
+
 template <typename T>
 cudaError_t Launch<T>::ensemble_step_act(const EnsArgs<T>& a, int block, int min_blocks, int geo_early,
-                                         unsigned grid, cudaStream_t st, int dynamic) {
+                                         unsigned grid, cudaStream_t st, int dynamic, int queue) {
     if (grid == 0 || !a.act_in || (dynamic && (!a.sched || a.chunk_log2 < 2))) return cudaErrorInvalidValue;
+    if (queue) {
+        if constexpr (sizeof(T) == 4) {
+#define SWE_LAUNCH(B, M, G) \
+    if (block == B && min_blocks == M && geo_early == G) {                                       \
+        if (dynamic) ensemble_step_kernel_act<T, B, M, G != 0, true, true><<<grid, B, 0, st>>>(a); \
+        else ensemble_step_kernel_act<T, B, M, G != 0, false, true><<<grid, B, 0, st>>>(a);     \
+        return cudaGetLastError();                                                               \
+    }
+            SWE_ENS_ACTQ_VARIANTS_F32(SWE_LAUNCH)
+#undef SWE_LAUNCH
+        }
+        return cudaErrorInvalidValue;
+    }
 #define SWE_LAUNCH(B, M, G) \
     if (block == B && min_blocks == M && geo_early == G) {                        \
         if (dynamic) ensemble_step_kernel_act<T, B, M, G != 0, true><<<grid, B, 0, st>>>(a); \
@@ -405,7 +423,20 @@ cudaError_t Launch<T>::ensemble_step_act(const EnsArgs<T>& a, int block, int min
 
 template <typename T>
 cudaError_t Launch<T>::ensemble_act_resident_blocks(int block, int min_blocks, int geo_early, int* per_sm,
-                                                    int dynamic) {
+                                                    int dynamic, int queue) {
+    if (queue) {
+        if constexpr (sizeof(T) == 4) {
+#define SWE_OCC(B, M, G) \
+    if (block == B && min_blocks == M && geo_early == G)                                         \
+        return dynamic ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(                           \
+                             per_sm, ensemble_step_kernel_act<T, B, M, G != 0, true, true>, B, 0)  \
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(                           \
+                             per_sm, ensemble_step_kernel_act<T, B, M, G != 0, false, true>, B, 0);
+            SWE_ENS_ACTQ_VARIANTS_F32(SWE_OCC)
+#undef SWE_OCC
+        }
+        return cudaErrorInvalidValue;
+    }
 #define SWE_OCC(B, M, G) \
     if (block == B && min_blocks == M && geo_early == G)                          \
         return dynamic ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(             \
@@ -419,6 +450,19 @@ cudaError_t Launch<T>::ensemble_act_resident_blocks(int block, int min_blocks, i
     }
 #undef SWE_OCC
     return cudaErrorInvalidValue;
+}
+
+template <typename T>
+int Launch<T>::ensemble_actq_variants(int (*out)[3], int max) {
+    int k = 0;
+    if constexpr (sizeof(T) == 4) {
+#define SWE_LIST(B, M, G) \
+    if (k < max) { out[k][0] = B; out[k][1] = M; out[k][2] = G; } \
+    ++k;
+        SWE_ENS_ACTQ_VARIANTS_F32(SWE_LIST)
+#undef SWE_LIST
+    }
+    return k;
 }
 
 template <typename T>

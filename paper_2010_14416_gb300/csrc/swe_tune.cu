@@ -230,9 +230,9 @@ int autotune_t(swe_mesh* m, int trial_steps, swe_tune* out) {
     if (e == cudaSuccess && best_plain < cand.size()) apply_shape(m, cand[best_plain]);
     else m->plain = plain_before;
     apply_shape(m, pick);
-    // the activity bytes describe the current state (the trials rewrote the next
-    // buffers with the bytes the next step writes); without activity they go stale
-    m->act_valid = pick.activity != 0 && e == cudaSuccess;
+    // the activity bytes are rebuilt before the next step: the trials cleared the
+    // previous step's bytes, which tell the next step whose state it may leave
+    m->act_valid = false;
     drop_mesh_graph(m);
     if (e != cudaSuccess) return tfail(e, "swe_autotune: trial steps");
     if (out) {
@@ -250,6 +250,7 @@ int autotune_t(swe_mesh* m, int trial_steps, swe_tune* out) {
         out->ms_before = ms[0];
         out->n_candidates = (int)cand.size();
         out->cell_pairs = pick.pairs;
+        out->queue = 0;
     }
     return SWE_OK;
 }

@@ -104,6 +104,7 @@ def test_ensemble_autotune_keeps_state_and_results(precision):
     assert ch["dynamic"] in (0, 1) and not (ch["edge_pass"] and (ch["activity"] or ch["dynamic"]))
     assert not (ch["activity"] and ch["dynamic"]) or ch["chunk"] >= 4
     assert ch["cell_pairs"] in (0, 1) and (ch["cell_pairs"] == 0 or precision == capi.SWE_FP32)
+    assert ch["queue"] in (0, 1) and (ch["queue"] == 0 or (precision == capi.SWE_FP32 and ch["activity"]))
     assert ch["n_candidates"] >= 20 and 0 < ch["ms_best"] <= ch["ms_before"]
     t_ens = ens.step(90, cfl)
     for k, m in enumerate(meshes):

@@ -99,9 +99,9 @@ def test_ensemble_device_output_and_errors():
 @pytest.mark.parametrize("precision", [capi.SWE_FP64, capi.SWE_FP32])
 def test_ensemble_launch_shapes_are_bitwise_neutral(precision):
     # every batched kernel shape -- tile size, staging, geometry placement,
-    # activity bytes, chunk, grid and (FP32) the split step over cell pairs --
-    # gives each member the plain solver's updates bit for bit, also when the
-    # shape changes between calls
+    # activity bytes, chunk, grid and (FP32) the split step over cell pairs and
+    # the per-warp queues -- gives each member the plain solver's updates bit
+    # for bit, also when the shape changes between calls
     mis = _members(6, seed=13)
     meshes = [_mesh(mi, precision) for mi in mis]
     ens = capi.Ensemble(meshes)
@@ -129,6 +129,12 @@ def test_ensemble_launch_shapes_are_bitwise_neutral(precision):
                    dict(block_size=128, min_blocks=8, dynamic=1, chunk=1, cell_pairs=1),
                    dict(block_size=256, min_blocks=4, stages=3, chunk=8, cell_pairs=1),
                    dict(block_size=128, min_blocks=8, geometry_early=1, activity=1, chunk=64, grid=5, cell_pairs=1)]
+        # per-warp queues of the cells that run the flux path, alone and in split steps
+        shapes += [dict(block_size=128, min_blocks=7, geometry_early=1, activity=1, chunk=8, queue=1),
+                   dict(block_size=128, min_blocks=7, activity=1, dynamic=1, chunk=4, grid=9, queue=1, cell_pairs=1),
+                   dict(block_size=128, min_blocks=6, geometry_early=1, activity=1, dynamic=1, chunk=16, queue=1),
+                   dict(block_size=128, min_blocks=7, geometry_early=1, activity=1, chunk=4, grid=3, queue=1,
+                        cell_pairs=1)]
     steps = 0
     for k, sh in enumerate(shapes):
         ens.set_shape(**sh)
@@ -147,9 +153,14 @@ def test_ensemble_launch_shapes_are_bitwise_neutral(precision):
         ens.set_shape(block_size=128, min_blocks=8 if f32 else 1, activity=1, dynamic=1, chunk=2)
     with pytest.raises(capi.SWEError):
         ens.set_shape(block_size=256, min_blocks=4 if f32 else 1, dynamic=1, edge_pass=1)
-    if not f32:   # the split step is FP32 only
+    if not f32:   # the split step and the queues are FP32 only
         with pytest.raises(capi.SWEError):
             ens.set_shape(block_size=128, min_blocks=1, activity=1, chunk=4, cell_pairs=1)
+        with pytest.raises(capi.SWEError):
+            ens.set_shape(block_size=128, min_blocks=1, activity=1, chunk=4, queue=1)
+    else:   # queues need the activity kernel
+        with pytest.raises(capi.SWEError):
+            ens.set_shape(block_size=128, min_blocks=7, dynamic=1, chunk=4, queue=1)
     ens.close()
     for m in meshes:
         m.close()
@@ -171,6 +182,7 @@ def test_ensemble_debug_checks_change_nothing(precision):
         shapes.append(dict(block_size=256, min_blocks=1, edge_pass=1, chunk=4))
     else:
         shapes.append(dict(block_size=128, min_blocks=8, activity=1, dynamic=1, chunk=4, cell_pairs=1))
+        shapes.append(dict(block_size=128, min_blocks=7, geometry_early=1, activity=1, chunk=4, queue=1))
     for shape in shapes:
         for k, m in enumerate(dbg_meshes):
             m.set_state(*(a.astype(m.dtype) for a in (mis[k].h, mis[k].hu, mis[k].hv)))

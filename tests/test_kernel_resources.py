@@ -23,10 +23,12 @@ KERNELS = [
     ("swe_step_f32.cu", "15step_kernel_actIfLi128ELi8ELb1ELi2E"),
     ("swe_step_f32.cu", "11step_kernelIfLi256ELi4ELi3ELb1ELb0E"),
     ("swe_step_f32.cu", "11step_kernelIfLi128ELi8ELi3ELb1ELb0E"),
-    ("swe_step_f32.cu", "24ensemble_step_kernel_actIfLi128ELi8ELb1ELb1E"),
+    ("swe_step_f32.cu", "24ensemble_step_kernel_actIfLi128ELi8ELb1ELb1ELb0E"),
     ("swe_step_f32.cu", "16step_kernel_pairILi256ELi4ELb1EE"),
     ("swe_step_f32.cu", "16step_kernel_pairILi128ELi8ELb1EE"),
     ("swe_step_f32.cu", "25ensemble_step_kernel_pairILi128ELi8ELb1EE"),
+    ("swe_step_f32.cu", "24ensemble_step_kernel_actIfLi128ELi7ELb1ELb1ELb1E"),
+    ("swe_step_f32.cu", "24ensemble_step_kernel_actIfLi128ELi7ELb1ELb0ELb1E"),
     ("swe_step_f64.cu", "16edge_flux_kernelIdLi256E"),
     ("swe_step_f64.cu", "11step_kernelIdLi128ELi1ELi1ELb0ELb1E"),
     ("swe_step_f64.cu", "20ensemble_step_kernelIdLi128ELi1ELi1ELb0ELb1E"),
