@@ -314,22 +314,27 @@ def _warmup_for(steps, warmup, graph_steps=48):
     return max(warmup, graph_steps + 6) if steps >= graph_steps else warmup
 
 
-def _hbm_roofline(wl, n, kernel_ms, active_frac, activity, name, shape, peak, peak_kind):
+def _hbm_roofline(wl, n, kernel_ms, active_frac, activity, name, shape, peak, peak_kind, ensemble=False):
     """HBM roofline of an FP32 step: bytes this kernel's data layout must move
     per launch at the measured active fraction (frac), the ncu DRAM bytes of
     the same kernel source and launch shape when a committed record has them
     (traffic_frac), and the dense per-cell model for reference."""
     ab = ALG_BYTES[wl["precision"]]
     rec = 16 if wl["precision"] == "f32" else 32
-    # activity kernels read a cell's byte and the previous step's, and clear the latter
-    act_bytes = 3 if activity else 0
+    # activity kernels read a cell's byte and clear the previous step's byte
+    # (the mesh's kernel also reads the latter)
+    act_bytes = (2 if ensemble else 3) if activity else 0
     # an active cell reads its state, topology and geometry records and writes
     # its state; a quiet cell (dry, dry neighbours, no inflow/stage edge)
-    # needs no geometry, and with activity bytes no topology either, nor a
-    # store when it was quiet in the previous step too (its state is then in
-    # place; one that is written moves another record, so this is the lower
-    # bound of the layout's bytes and the fraction is the conservative one)
-    quiet_bytes = rec + act_bytes if activity else 2 * rec + 16
+    # needs no geometry, and with activity bytes no topology either, and with
+    # the mesh's activity kernel no store when it was quiet in the previous
+    # step too (its state is then in place; a quiet cell that is written
+    # moves another record, so this is the lower bound of the layout's bytes
+    # and the fraction is the conservative one)
+    if not activity:
+        quiet_bytes = 2 * rec + 16
+    else:
+        quiet_bytes = (2 * rec if ensemble else rec) + act_bytes
     layout_bytes = n * (active_frac * (4 * rec + 16 + (0 if wl["precision"] == "f32" else 8) + act_bytes) +
                         (1 - active_frac) * quiet_bytes)
     s = kernel_ms * 1e-3
@@ -344,8 +349,8 @@ def _hbm_roofline(wl, n, kernel_ms, active_frac, activity, name, shape, peak, pe
             "bytes_per_quiet_cell": quiet_bytes,
             "dense_model_bytes_per_cell": ab, "dense_model_frac": dense / peak,
             "note": "achieved/frac: the bytes this launch's kernel must move at the measured fraction of cells "
-                    "that run the flux path (bytes_per_active_cell, bytes_per_quiet_cell; with activity bytes a "
-                    "quiet cell quiet in the previous step too needs no store, and one that is written moves "
+                    "that run the flux path (bytes_per_active_cell, bytes_per_quiet_cell; with the mesh's activity "
+                    "kernel a cell quiet in the previous step too needs no store, and one that is written moves "
                     "another state record); traffic_frac: ncu "
                     "DRAM bytes per launch of the same kernel source and shape; dense_model_frac: "
                     f"{ab} B for every cell, which a quiet cell (dry among dry neighbours) does not need, so it "
@@ -538,7 +543,8 @@ def measure_ensemble(ctx, name, steps, warmup, ens_shape=None):
     ms_plain, _ = ctx.timed(lambda: [m.step(steps, 0.9, sync=False) for m in meshes])
     peak, peak_kind = _peaks()
     kernel_ms = ms / steps
-    roof = _hbm_roofline(wl, n, kernel_ms, active_frac, shape.get("activity"), name, shape, peak, peak_kind)
+    roof = _hbm_roofline(wl, n, kernel_ms, active_frac, shape.get("activity"), name, shape, peak, peak_kind,
+                         ensemble=True)
     roof["traffic"], roof["traffic_frac"] = None, None
     if wl["precision"] == "f64":
         roof = _fp64_roofline(n, kernel_ms, active_frac, shape.get("edge_pass"), roof)

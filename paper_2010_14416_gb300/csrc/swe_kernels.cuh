@@ -1505,28 +1505,21 @@ __global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel_act(const En
     // QUEUE: each warp's cells that run the flux path, a ring of 64 slots
     __shared__ unsigned s_q[QUEUE ? BLOCK / 32 : 1][64];
     unsigned qh = 0u, qt = 0u;                               // warp-uniform head and tail
-    // per warp: the 32 activity bytes of its cells in 3 stages (copied by lanes
-    // 0..7), and the previous step's (act_clear) bytes in a ring of 4 (lanes
-    // 8..15), so that the slot refilled in iteration k is never cell k's
+    // per warp: the 32 activity bytes of its cells in 3 stages (lanes 0..7 copy
+    // 4 each).  Unlike step_kernel_act, this kernel writes every quiet state:
+    // leaving those quiet in two steps in place measured slower here (the
+    // kernel is bound by instruction issue, not by its bytes).
     __shared__ unsigned st_act[3][BLOCK / 4];
-    __shared__ unsigned st_prev[4][BLOCK / 4];
-    auto act_copy = [&](int slot, int pslot, unsigned c) {
-        if (lane < 16 && c != kNone) {
-            const unsigned w0 = c - lane;   // the warp's first cell
-            const unsigned dst = lane < 8 ? (unsigned)__cvta_generic_to_shared(&st_act[slot][warp * 8 + lane])
-                                          : (unsigned)__cvta_generic_to_shared(&st_prev[pslot][warp * 8 + lane - 8]);
-            const unsigned char* src = lane < 8 ? a.act_in + w0 + 4 * lane : a.act_clear + w0 + 4 * (lane - 8);
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
-        }
+    auto act_copy = [&](int slot, unsigned c) {
+        if (lane < 8 && c != kNone)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(
+                             (unsigned)__cvta_generic_to_shared(&st_act[slot][warp * 8 + lane])),
+                         "l"(a.act_in + (c - lane) + 4 * lane)
+                         : "memory");
     };
     // whether the cell runs the flux path (bit 0 of its byte)
     auto act_byte = [&](int slot) -> unsigned {
         return ((const unsigned char*)&st_act[slot][warp * 8])[lane] & 1u;
-    };
-    // whether cell k's byte of the previous step is not 0 (it ran the flux path
-    // then, or the bytes were rebuilt less than two steps ago)
-    auto prev_byte = [&](unsigned k) -> unsigned {
-        return ((const unsigned char*)&st_prev[k & 3u][warp * 8])[lane];
     };
     int member = -1;
     unsigned long long* sm = nullptr;
@@ -1561,9 +1554,9 @@ __global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel_act(const En
     };
     {
         const unsigned c0 = cell_of(0), c1 = cell_of(1), c2 = cell_of(2);
-        act_copy(0, 0, c0);
-        act_copy(1, 1, c1);
-        act_copy(2, 2, c2);
+        act_copy(0, c0);
+        act_copy(1, c1);
+        act_copy(2, c2);
         if (c0 != kNone) cp_async_record<sizeof(V4<T>)>(&st_own[0][tid], &a.s_in[c0]);
         if (c1 != kNone) cp_async_record<sizeof(V4<T>)>(&st_own[1][tid], &a.s_in[c1]);
         cp_async_commit();
@@ -1613,7 +1606,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel_act(const En
         if (!QUEUE && f_next && c1 != kNone) cp_async_record<16>(&st_topo[k2 ^ 1][tid], &a.topo[c1]);
         cp_async_commit();                                       // T_k
         __syncwarp();
-        act_copy(k3, (int)((k + 3u) & 3u), c3);
+        act_copy(k3, c3);
         if (c2 != kNone) cp_async_record<sizeof(V4<T>)>(&st_own[k3nn][tid], &a.s_in[c2]);
         cp_async_commit();                                       // H_k
         cp_async_wait<3>();                                      // T_{k-1}: the topology of c_k
@@ -1624,7 +1617,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel_act(const En
         } else if constexpr (QUEUE) {
             // quiet cells now; the others join the warp's queue, which runs
             // whenever it holds a full warp of cells
-            if (!f_cur && prev_byte(k)) {   // quiet, and not in place already
+            if (!f_cur) {
                 V4<T> out;
                 out.x = own.x; out.y = T(0); out.z = T(0); out.w = own.w;
                 a.s_out[c] = out;
@@ -1641,14 +1634,9 @@ __global__ void __launch_bounds__(BLOCK, MINB) ensemble_step_kernel_act(const En
                 run_queued(cq);
             }
         } else if (!f_cur) {
-            // quiet: the new state is (h, 0, 0); if the cell was quiet in the
-            // previous step too, the output buffer (the state of two steps ago)
-            // holds it already
-            if (prev_byte(k)) {
-                V4<T> out;
-                out.x = own.x; out.y = T(0); out.z = T(0); out.w = own.w;
-                a.s_out[c] = out;
-            }
+            V4<T> out;
+            out.x = own.x; out.y = T(0); out.z = T(0); out.w = own.w;
+            a.s_out[c] = out;
         } else {
             const T r = update_cell<T, GEO_EARLY>(a, c, own, st_topo[k2][tid], dt, active, sm + 5,
                                                   (unsigned*)(sm + 4));
