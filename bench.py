@@ -73,7 +73,7 @@ WORKLOADS = {
 }
 
 
-MEMBERS = [256, "all"]   # ensemble workloads: number of members, which of them
+MEMBERS = [256, "all", False]   # ensemble workloads: number of members, which of them, batched only
 
 
 def _peak_clock():
@@ -531,16 +531,19 @@ def measure_ensemble(ctx, name, steps, warmup, ens_shape=None):
     active0 = ens.info(0)["n_active"]
     ms, clk = ctx.timed(lambda: ens.step(steps, sync=False))
     active_frac = (ens.info(0)["n_active"] - active0) / float(n * steps)
-    # per-member launches of the plain solver, the same number of steps
-    for m in meshes:
-        m.step(48)
-    ms_default, _ = ctx.timed(lambda: [m.step(steps, 0.9, sync=False) for m in meshes])
     member_shapes = []
-    for m in meshes:
-        m.step(96)
-        member_shapes.append(m.autotune(4))
-        m.step(48)
-    ms_plain, _ = ctx.timed(lambda: [m.step(steps, 0.9, sync=False) for m in meshes])
+    if MEMBERS[2]:   # profiling the batched kernel alone: no per-member launches
+        ms_default = ms_plain = float("nan")
+    else:
+        # per-member launches of the plain solver, the same number of steps
+        for m in meshes:
+            m.step(48)
+        ms_default, _ = ctx.timed(lambda: [m.step(steps, 0.9, sync=False) for m in meshes])
+        for m in meshes:
+            m.step(96)
+            member_shapes.append(m.autotune(4))
+            m.step(48)
+        ms_plain, _ = ctx.timed(lambda: [m.step(steps, 0.9, sync=False) for m in meshes])
     peak, peak_kind = _peaks()
     kernel_ms = ms / steps
     roof = _hbm_roofline(wl, n, kernel_ms, active_frac, shape.get("activity"), name, shape, peak, peak_kind,
@@ -571,6 +574,9 @@ def measure_ensemble(ctx, name, steps, warmup, ens_shape=None):
         "gpu_launches": steps * (2 if shape.get("edge_pass") or shape.get("cell_pairs") else 1),
         "clocks": clk,
     }
+    if MEMBERS[2]:
+        for k in ("per_member_launches", "speedup_vs_per_member", "per_member_launches_default_shapes"):
+            rec[k] = None
     ens.close()
     for m in meshes:
         m.close()
@@ -737,6 +743,9 @@ def main():
     ap.add_argument("--members", type=int, default=256, help="ensemble workloads: number of members")
     ap.add_argument("--member-kind", choices=["all", "canal", "river"], default="all",
                     help="ensemble workloads: all members, or only the canal (even) or river (odd) ones")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="ensemble workloads: time the batched step alone, without the per-member launches "
+                         "(for profiling)")
     ap.add_argument("--ens-shape", default=None,
                     help="ensemble workloads: block,min_blocks,stages,geometry_early,activity,edge_pass,dynamic,chunk,grid"
                          "[,cell_pairs[,queue]] "
@@ -755,6 +764,7 @@ def main():
         return run_reference(args, name)
     MEMBERS[0] = args.members
     MEMBERS[1] = args.member_kind
+    MEMBERS[2] = args.batched_only
     subrecords = not explicit and not args.no_subrecords
     return run_gpu(args, name, subrecords)
 
