@@ -110,8 +110,12 @@ typedef struct swe_config {
     int activity;     /* 1: keep one activity byte per cell (three rotating buffers, 3 bytes per
                          cell of device memory): a cell is active when it or a neighbour is wet
                          or it has an inflow/stage edge, and an inactive cell takes its update
-                         (h, 0, 0) without reading its topology or its neighbours; each step
-                         marks the cells that the next one must treat as active.  0 (default):
+                         (h, 0, 0) without reading its topology or its neighbours, and with no
+                         store when it was inactive in the previous step too (the state in the
+                         output buffer, two steps old, is then already the new one); each step
+                         marks the cells that the next one must treat as active, and the two
+                         steps after a change from outside (set_state, set_bc, the tuner)
+                         store every state.  0 (default):
                          every cell tests its neighbours.  With activity, stages is the
                          prefetch distance of the streamed state plus one (default 3).
                          Compiled (block_size, min_blocks, geometry_early, stages) with 1:
