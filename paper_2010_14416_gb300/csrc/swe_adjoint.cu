@@ -735,14 +735,39 @@ int adjoint_impl(swe_mesh* m, int64_t nsteps, double cfl, const int32_t* gauge_c
         e = cudaMemcpyAsync(dtarget.p, targets, (size_t)n_obs * n_gauges * sizeof(double), cudaMemcpyHostToDevice, st);
     const long long* gi = (const long long*)dg_idx.p;
     const double* tg = (const double*)dtarget.p;
+    // With the edge pass, the recomputation of a segment keeps each step's edge
+    // fluxes (64 B per interior edge and step), so phase 1 reads the fluxes of
+    // U^n that the recomputed step n -> n+1 formed instead of running the edge
+    // pass again; without room for them, phase 1 runs it.
+    const bool edges = m->plain.edges && m->eflux;
+    DevBuf segflux, segsrc;
+    const size_t Eb = (size_t)std::max<int64_t>(m->n_edges, 1);
+    bool keep = edges && transposes;
+    if (keep) {
+        keep = cudaMalloc(&segflux.p, (size_t)K * Eb * sizeof(V4<double>)) == cudaSuccess &&
+               cudaMalloc(&segsrc.p, (size_t)K * Eb * sizeof(double)) == cudaSuccess;
+        if (!keep) (void)cudaGetLastError();   // clear the failed allocation's error
+    }
+    V4<double>* const sflux = (V4<double>*)segflux.p;
+    double* const ssrc = (double*)segsrc.p;
     // forward run: checkpoints every K steps, step sizes logged, loss summed
-    // over the observations
+    // over the observations.  The last segment's states (and, with the edge
+    // pass, the fluxes its steps form) are kept as the reverse sweep's segment
+    // buffer: recomputing them would give the same bits (the same kernels and
+    // step sizes), so the reverse sweep starts without a recomputation.
+    const int64_t last0 = (nseg - 1) * K;   // first step of the last segment
+    char* const segp = (char*)seg.p;
     for (int64_t s = 0; s < nsteps && e == cudaSuccess; ++s) {
         void* cur = m->state[m->nstep % 2];
         void* nxt = m->state[(m->nstep + 1) % 2];
         if (s % K == 0) e = cudaMemcpyAsync((char*)ckpt.p + (s / K) * sb, cur, sb, cudaMemcpyDeviceToDevice, st);
+        const bool in_last = s >= last0;
+        if (e == cudaSuccess && in_last)
+            e = cudaMemcpyAsync(segp + (s - last0) * sb, cur, sb, cudaMemcpyDeviceToDevice, st);
         if (e == cudaSuccess)
-            e = launch_step_raw(m, cur, nxt, m->small, m->nstep, cfl, nullptr, (double*)dtlog.p + s, st);
+            e = launch_step_raw(m, cur, nxt, m->small, m->nstep, cfl, nullptr, (double*)dtlog.p + s, st, false,
+                                keep && in_last ? (void*)(sflux + (s - last0) * Eb) : nullptr,
+                                keep && in_last ? (void*)(ssrc + (s - last0) * Eb) : nullptr);
         ++m->nstep;
         m->act_valid = false;   // stepped without the activity bytes
         if (e == cudaSuccess && (s + 1) % obs_every == 0) {
@@ -798,7 +823,6 @@ int adjoint_impl(swe_mesh* m, int64_t nsteps, double cfl, const int32_t* gauge_c
     a.n_groups = m->n_groups;
     a.status = (unsigned*)((unsigned long long*)small.p + kSlotStatus);
     // with the edge pass, phase 1 takes R's interior fluxes from one evaluation per edge
-    const bool edges = m->plain.edges && m->eflux;
     a.eflux = edges ? (const V4<double>*)m->eflux : nullptr;
     a.esrc = edges ? (const double*)m->esrc : nullptr;
     a.eidx = m->eidx;
@@ -824,30 +848,17 @@ int adjoint_impl(swe_mesh* m, int64_t nsteps, double cfl, const int32_t* gauge_c
     }
     const unsigned egrid = (unsigned)std::min<int64_t>((std::max<int64_t>(m->n_edges, 1) + 127) / 128, 65535);
     const unsigned grid = (unsigned)((n + 127) / 128);
-    // With the edge pass, the recomputation of a segment keeps each step's edge
-    // fluxes (64 B per interior edge and step), so phase 1 reads the fluxes of
-    // U^n that the recomputed step n -> n+1 formed instead of running the edge
-    // pass again; without room for them, phase 1 runs it.
-    DevBuf segflux, segsrc;
-    const size_t Eb = (size_t)std::max<int64_t>(m->n_edges, 1);
-    bool keep = edges && transposes;
-    if (keep) {
-        keep = cudaMalloc(&segflux.p, (size_t)K * Eb * sizeof(V4<double>)) == cudaSuccess &&
-               cudaMalloc(&segsrc.p, (size_t)K * Eb * sizeof(double)) == cudaSuccess;
-        if (!keep) (void)cudaGetLastError();   // clear the failed allocation's error
-    }
-    V4<double>* const sflux = (V4<double>*)segflux.p;
-    double* const ssrc = (double*)segsrc.p;
     // reverse sweep, segment by segment
     for (int64_t sgi = nseg - 1; sgi >= 0 && e == cudaSuccess; --sgi) {
         const int64_t n0 = sgi * K, n1 = std::min<int64_t>(n0 + K, nsteps);
-        char* segp = (char*)seg.p;
-        e = cudaMemcpyAsync(segp, (char*)ckpt.p + sgi * sb, sb, cudaMemcpyDeviceToDevice, st);
-        for (int64_t k = 0; k + 1 < n1 - n0 && e == cudaSuccess; ++k)
+        const bool from_forward = sgi == nseg - 1;   // the forward run kept this segment
+        if (!from_forward)
+            e = cudaMemcpyAsync(segp, (char*)ckpt.p + sgi * sb, sb, cudaMemcpyDeviceToDevice, st);
+        for (int64_t k = 0; !from_forward && k + 1 < n1 - n0 && e == cudaSuccess; ++k)
             e = launch_step_raw(m, segp + k * sb, segp + (k + 1) * sb, (unsigned long long*)small.p, k, cfl,
                                 (const double*)dtlog.p + n0 + k, nullptr, st, false,
                                 keep ? (void*)(sflux + k * Eb) : nullptr, keep ? (void*)(ssrc + k * Eb) : nullptr);
-        if (keep && e == cudaSuccess) {   // the segment's last state has no recomputed step
+        if (keep && !from_forward && e == cudaSuccess) {   // the segment's last state has no recomputed step
             const int64_t k = n1 - n0 - 1;
             ea.s_in = (const V4<double>*)(segp + k * sb);
             ea.eflux = sflux + k * Eb;
